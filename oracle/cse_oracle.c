@@ -1,0 +1,855 @@
+/*
+ * cse_oracle.c -- CPU oracle of the parallel heuristic CSE search.
+ *
+ * TEST INFRASTRUCTURE ONLY (see cse_oracle.h).  Plain C11, written for a
+ * reader checking it against the paper, not for speed:
+ *   - an expression set is a dense ternary coefficient matrix coef[r][v]
+ *     (the alpha_ij of Section 3.2.1), one row per expression, one column per
+ *     variable x_v (0-based; fresh variable t is column n_x + t);
+ *   - every step recounts all canonical pairs from the rows (Algorithm 1,
+ *     Analysis) with a sort, instead of updating counts incrementally;
+ *   - Greedy-Intersections scores every candidate against every other one,
+ *     the O(m^2) loop the paper describes (Section 3.4.2).
+ *
+ * Readings taken where the paper is silent (all documented in the design doc):
+ *   R1 canonical pair (i, j, s): i < j, s = alpha_i * alpha_j, i.e. the
+ *      coefficient of x_i normalised to +1 (Section 3.3.1).  Canonical ORDER
+ *      is ascending key ((j << 10 | i) << 1) | (s < 0): by the larger index
+ *      first, then the smaller, '+' before '-'.
+ *   R2 random numbers: Philox4x32-10 keyed by the 64-bit seed; counter
+ *      (process, step t, matrix<<24 | purpose<<20 | extra_hi, extra_lo).
+ *      A draw u is lane 0 unless stated.
+ *   R3 g and gi break ties by the lowest canonical key.
+ *   R4 ga: index (u * n_ties) >> 32 among the ties in canonical order.
+ *   R5 wr: x = (u * T) >> 32 with T = sum(c - 1); the first candidate whose
+ *      running sum of (c - 1) exceeds x.
+ *   R6 gr: ga when u < 3 * 2^30 (p = 0.75), else wr, separate draws.
+ *   R7 mix: per step, (u * 15) >> 32 in [0,8) gi, [8,12) ga, [12,14) gr,
+ *      [14,15) wr (weights 8/4/2/1 of Section 3.4.3).
+ *   R8 alpha = a / 2^16 with a = (u * 32769) >> 32 in [0, 32768];
+ *      beta = b / 2^16 with b = 32768 + ((u * 32769) >> 32) in [32768, 65536];
+ *      both drawn at the start of every run.  gi score
+ *      S_p = (c_p - 1) * 2^32 + a * (2^16 * D_p + b * X_p)  (= H * 2^32).
+ *   R9 gi coins: for candidate p = (i, j, s) the other candidates sharing a
+ *      variable with it fall in slot 0 (they contain x_i) or slot 1 (they
+ *      contain x_j but not x_i); within a slot they are ranked rho = 0, 1, ...
+ *      in canonical order.  The coin of the rho-th is bit (rho mod 64) of
+ *      the 64-bit word (lane 0 | lane 1 << 32) for slot 0 or (lane 2 | lane 3
+ *      << 32) for slot 1 of the draw with purpose GI, extra_hi = rho >> 6,
+ *      extra_lo = key(p).  Coin 1 means the pair survives with weight beta.
+ *   R10 the step clock: every process performs one step per t.  A step
+ *      first (re)starts the run if t == 0 or the previous run ended, then
+ *      makes one substitution if a pair with c > 1 exists and a free column
+ *      is left; after the substitution the run ends if no such pair remains
+ *      or the columns are used up.  A fresh run with nothing to substitute
+ *      ends at once (its step makes no substitution).
+ *   R11 run start: close the old run into the process best (strictly lower
+ *      cost replaces); strategy = g for process 0's first run, else drawn
+ *      from the weights (u * sum) >> 32 against cumulative weights in the
+ *      order gi, ga, gr, wr, mix, g; if a snapshot exists and
+ *      u < floor(permille * 2^32 / 1000), L = snapshot length, K = floor(3L/4),
+ *      and if K >= 1 the first k = 1 + ((u' * K) >> 32) substitutions of the
+ *      snapshot are replayed (Section 3.5.2).  Replays are not steps.
+ *   R12 sharing boundary after step t when (t + 1) % interval == 0: each
+ *      process folds its current run into its best (strictly lower cost),
+ *      then per matrix the lowest (best cost, process) replaces the snapshot
+ *      if its cost is strictly lower.  Runs started in the next round read
+ *      that snapshot.
+ *   R13 end of budget: every process folds its current run; the result per
+ *      matrix is the lowest (best cost, process).
+ */
+#include "cse_oracle.h"
+
+#include <pthread.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define KEY(i, j, neg) (((((uint32_t)(j)) << 10 | (uint32_t)(i)) << 1) | (uint32_t)(neg))
+#define KEY_I(k) (((k) >> 1) & 0x3FFu)
+#define KEY_J(k) (((k) >> 11) & 0x3FFu)
+#define KEY_NEG(k) ((k) & 1u)
+#define ENTRY(i, j, neg) ((int32_t)((uint32_t)(i) | ((uint32_t)(j) << 10) | ((uint32_t)(neg) << 20)))
+#define ENT_I(e) ((int32_t)((uint32_t)(e) & 0x3FFu))
+#define ENT_J(e) ((int32_t)(((uint32_t)(e) >> 10) & 0x3FFu))
+#define ENT_NEG(e) ((int32_t)(((uint32_t)(e) >> 20) & 1u))
+
+enum { PU_STRAT = 0, PU_ALPHA = 1, PU_BETA = 2, PU_SHARE = 3, PU_SHAREK = 4, PU_MIX = 5,
+       PU_GA = 6, PU_GR = 7, PU_WR = 8, PU_GI = 9 };
+
+/* ------------------------------------------------------------------ */
+/* Philox4x32-10, from the definition in Salmon et al., SC'11:          */
+/* round: (hi0,lo0) = M0*c0, (hi1,lo1) = M1*c2,                         */
+/*        c' = (hi1 ^ c1 ^ k0, lo1, hi0 ^ c3 ^ k1, lo0);                 */
+/* the key is bumped by the Weyl constants between rounds.              */
+/* ------------------------------------------------------------------ */
+void oracle_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int r = 0; r < 10; r++) {
+        if (r > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        uint64_t p0 = (uint64_t)0xD2511F53u * c0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * c2;
+        uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
+        uint32_t n1 = (uint32_t)p1;
+        uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+        uint32_t n3 = (uint32_t)p0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+static void draw4(uint64_t seed, int32_t proc, int64_t t, int32_t mat, int32_t purpose,
+                  uint32_t extra_hi, uint32_t extra_lo, uint32_t out[4]) {
+    uint32_t ctr[4] = {(uint32_t)proc, (uint32_t)t,
+                       ((uint32_t)mat & 0xFFu) << 24 | ((uint32_t)purpose & 0xFu) << 20 |
+                           (extra_hi & 0xFFFFFu),
+                       extra_lo};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    oracle_philox(ctr, key, out);
+}
+
+static uint32_t draw(uint64_t seed, int32_t proc, int64_t t, int32_t mat, int32_t purpose) {
+    uint32_t o[4];
+    draw4(seed, proc, t, mat, purpose, 0, 0, o);
+    return o[0];
+}
+
+/* (u * n) >> 32: an integer in [0, n) for a 32-bit draw u. */
+static uint32_t scale(uint32_t u, uint64_t n) { return (uint32_t)(((uint64_t)u * n) >> 32); }
+
+/* FNV-1a over 32-bit words (test digest only). */
+static uint64_t fnv(uint64_t h, uint32_t w) {
+    h ^= w;
+    return h * 0x100000001B3ull;
+}
+#define FNV0 0xCBF29CE484222325ull
+
+/* ------------------------------------------------------------------ */
+/* Definitions of Section 3.2.1                                        */
+/* ------------------------------------------------------------------ */
+static int64_t naive_rows(const int8_t* coef, int32_t rows, int32_t ncols, int32_t stride) {
+    int64_t s = 0;
+    for (int32_t r = 0; r < rows; r++) {
+        int32_t nnz = 0;
+        for (int32_t v = 0; v < ncols; v++) nnz += coef[(int64_t)r * stride + v] != 0;
+        s += nnz - 1;
+    }
+    return s;
+}
+
+int64_t oracle_naive(const int8_t* mat, int32_t rows, int32_t cols) {
+    return naive_rows(mat, rows, cols, cols);
+}
+
+static int cmp_u32(const void* a, const void* b) {
+    uint32_t x = *(const uint32_t*)a, y = *(const uint32_t*)b;
+    return (x > y) - (x < y);
+}
+
+/* Analysis step of Algorithm 1: every pair of nonzeros of every row gives one
+ * occurrence of its canonical pair; equal keys are counted after a sort.
+ * Candidates (c >= min_c) come out in canonical (ascending key) order. */
+static int32_t count_pairs(const int8_t* coef, int32_t rows, int32_t ncols, int32_t stride,
+                           int32_t min_c, uint32_t* scratch, int32_t* nzbuf, uint32_t* keys,
+                           int32_t* cnt, int32_t max_out) {
+    int64_t n = 0;
+    for (int32_t r = 0; r < rows; r++) {
+        const int8_t* row = coef + (int64_t)r * stride;
+        int32_t nz = 0;
+        for (int32_t v = 0; v < ncols; v++)
+            if (row[v]) nzbuf[nz++] = v;
+        for (int32_t x = 0; x < nz; x++)
+            for (int32_t y = x + 1; y < nz; y++) {
+                int32_t i = nzbuf[x], j = nzbuf[y];
+                scratch[n++] = KEY(i, j, row[i] * row[j] < 0);
+            }
+    }
+    qsort(scratch, (size_t)n, sizeof(uint32_t), cmp_u32);
+    int32_t m = 0;
+    for (int64_t a = 0; a < n;) {
+        int64_t b = a;
+        while (b < n && scratch[b] == scratch[a]) b++;
+        if (b - a >= min_c) {
+            if (m < max_out) {
+                keys[m] = scratch[a];
+                cnt[m] = (int32_t)(b - a);
+            }
+            m++;
+        }
+        a = b;
+    }
+    return m;
+}
+
+static int64_t max_pair_occurrences(const int8_t* coef, int32_t rows, int32_t ncols, int32_t stride) {
+    int64_t s = 0;
+    for (int32_t r = 0; r < rows; r++) {
+        int64_t nnz = 0;
+        for (int32_t v = 0; v < ncols; v++) nnz += coef[(int64_t)r * stride + v] != 0;
+        s += nnz * (nnz - 1) / 2;
+    }
+    return s;
+}
+
+int32_t oracle_pairs(const int8_t* mat, int32_t rows, int32_t cols, int32_t min_c,
+                     uint32_t* keys, int32_t* counts, int32_t max_out) {
+    int64_t occ = max_pair_occurrences(mat, rows, cols, cols);
+    uint32_t* scratch = (uint32_t*)malloc((size_t)(occ + 1) * sizeof(uint32_t));
+    int32_t* nz = (int32_t*)malloc((size_t)(cols + 1) * sizeof(int32_t));
+    int32_t m = count_pairs(mat, rows, cols, cols, min_c, scratch, nz, keys, counts, max_out);
+    free(scratch);
+    free(nz);
+    return m;
+}
+
+/* Substitution (Section 3.2.1, Algorithm 1): fresh x_k = x_i + s x_j.  In
+ * every row where x_i and x_j occur as (x_i + s x_j) or -(x_i + s x_j), both
+ * coefficients become 0 and alpha_k becomes +1 or -1.  Returns c, the number
+ * of rows rewritten. */
+static int32_t substitute(int8_t* coef, int32_t rows, int32_t stride, int32_t k, int32_t i,
+                          int32_t j, int32_t neg) {
+    int32_t s = neg ? -1 : 1, c = 0;
+    for (int32_t r = 0; r < rows; r++) {
+        int8_t* row = coef + (int64_t)r * stride;
+        if (row[i] != 0 && row[j] == s * row[i]) {
+            row[k] = row[i];
+            row[i] = 0;
+            row[j] = 0;
+            c++;
+        }
+    }
+    return c;
+}
+
+int64_t oracle_apply(const int8_t* mat, int32_t rows, int32_t cols, const int32_t* list,
+                     int32_t n, int8_t* out) {
+    int32_t stride = cols + n;
+    memset(out, 0, (size_t)rows * (size_t)stride);
+    for (int32_t r = 0; r < rows; r++)
+        for (int32_t v = 0; v < cols; v++) out[(int64_t)r * stride + v] = mat[(int64_t)r * cols + v];
+    for (int32_t t = 0; t < n; t++) {
+        int32_t i = ENT_I(list[t]), j = ENT_J(list[t]);
+        if (!(i < j && j < cols + t)) return -1;
+        substitute(out, rows, stride, cols + t, i, j, ENT_NEG(list[t]));
+    }
+    return n + naive_rows(out, rows, stride, stride);
+}
+
+/* ------------------------------------------------------------------ */
+/* Selection strategies (Section 3.4)                                  */
+/* ------------------------------------------------------------------ */
+static int32_t sel_g(const int32_t* cnt, int32_t m) {
+    int32_t best = 0;
+    for (int32_t t = 1; t < m; t++)
+        if (cnt[t] > cnt[best]) best = t;
+    return best;
+}
+
+static int32_t sel_ga(const int32_t* cnt, int32_t m, uint32_t u) {
+    int32_t cmax = 0, ties = 0;
+    for (int32_t t = 0; t < m; t++)
+        if (cnt[t] > cmax) cmax = cnt[t];
+    for (int32_t t = 0; t < m; t++) ties += cnt[t] == cmax;
+    uint32_t want = scale(u, (uint64_t)ties);
+    for (int32_t t = 0; t < m; t++)
+        if (cnt[t] == cmax) {
+            if (want == 0) return t;
+            want--;
+        }
+    return -1;
+}
+
+static int32_t sel_wr(const int32_t* cnt, int32_t m, uint32_t u) {
+    uint64_t total = 0;
+    for (int32_t t = 0; t < m; t++) total += (uint64_t)(cnt[t] - 1);
+    uint64_t x = scale(u, total), acc = 0;
+    for (int32_t t = 0; t < m; t++) {
+        acc += (uint64_t)(cnt[t] - 1);
+        if (acc > x) return t;
+    }
+    return -1;
+}
+
+static int32_t sel_gr(const int32_t* cnt, int32_t m, uint32_t coin, uint32_t u_ga, uint32_t u_wr) {
+    return coin < 0xC0000000u ? sel_ga(cnt, m, u_ga) : sel_wr(cnt, m, u_wr);
+}
+
+int32_t oracle_select_basic(int32_t kind, const int32_t* counts, int32_t m, const uint32_t* u) {
+    if (m <= 0) return -1;
+    switch (kind) {
+        case OR_G: return sel_g(counts, m);
+        case OR_GA: return sel_ga(counts, m, u[0]);
+        case OR_WR: return sel_wr(counts, m, u[0]);
+        case OR_GR: return sel_gr(counts, m, u[0], u[1], u[1]);
+        default: return -1;
+    }
+}
+
+/* Coin source for Greedy-Intersections. */
+typedef struct {
+    /* Philox mode */
+    uint64_t seed;
+    int32_t proc, mat;
+    int64_t t;
+    const uint32_t* keys;
+    uint32_t block[4];
+    int32_t block_idx, block_p;
+    int64_t philox_calls;
+    /* explicit mode */
+    const uint8_t* bits;
+    int32_t m;
+} coin_src;
+
+static int coin_at(coin_src* cs, int32_t p, int32_t q, int32_t slot, int32_t rho) {
+    if (cs->bits) return cs->bits[(int64_t)p * cs->m + q] != 0;
+    int32_t blk = rho >> 6;
+    if (cs->block_p != p || cs->block_idx != blk) {
+        draw4(cs->seed, cs->proc, cs->t, cs->mat, PU_GI, (uint32_t)blk, cs->keys[p], cs->block);
+        cs->block_p = p;
+        cs->block_idx = blk;
+    }
+    uint64_t w = slot == 0 ? ((uint64_t)cs->block[0] | (uint64_t)cs->block[1] << 32)
+                           : ((uint64_t)cs->block[2] | (uint64_t)cs->block[3] << 32);
+    return (int)((w >> (rho & 63)) & 1u);
+}
+
+/* Greedy-Intersections (Section 3.4.2):
+ *   H(s_p) = (c_p - 1) + alpha * sum_{q != p} I(s_p, s_q),
+ *   I = c_q - 1 for q disjoint from p; 0 or beta (c_q - 1), each with
+ *   probability 1/2, for q sharing a variable with p.
+ * In integers: S_p = (c_p-1) 2^32 + a (2^16 D_p + b X_p), with D_p the sum over
+ * disjoint q and X_p the sum over intersecting q whose coin is 1.  Pairs with
+ * c = 1 contribute 0, so only candidates enter the sums.  Returns the argmax
+ * (lowest key on ties).  *ops_out receives the algorithmic op count. */
+static int32_t sel_gi(const uint32_t* keys, const int32_t* cnt, int32_t m, uint32_t a, uint32_t b,
+                      coin_src* cs, int64_t* score, int64_t* ops_out) {
+    int64_t total = 0;
+    for (int32_t q = 0; q < m; q++) total += cnt[q] - 1;
+    int32_t best = -1;
+    int64_t best_s = 0, ops = 0;
+    for (int32_t p = 0; p < m; p++) {
+        uint32_t i = KEY_I(keys[p]), j = KEY_J(keys[p]);
+        int64_t wp = cnt[p] - 1, inter = 0, x = 0;
+        int32_t rho0 = 0, rho1 = 0;
+        for (int32_t q = 0; q < m; q++) {
+            if (q == p) continue;
+            uint32_t qi = KEY_I(keys[q]), qj = KEY_J(keys[q]);
+            int coin;
+            if (qi == i || qj == i)
+                coin = coin_at(cs, p, q, 0, rho0++);
+            else if (qi == j || qj == j)
+                coin = coin_at(cs, p, q, 1, rho1++);
+            else
+                continue;
+            inter += cnt[q] - 1;
+            if (coin) x += cnt[q] - 1;
+        }
+        int64_t d = total - wp - inter;
+        int64_t s = (wp << 32) + (int64_t)a * ((d << 16) + (int64_t)b * x);
+        if (score) score[p] = s;
+        if (best < 0 || s > best_s) {
+            best = p;
+            best_s = s;
+        }
+        int32_t b0 = (rho0 + 63) >> 6, b1 = (rho1 + 63) >> 6;
+        ops += 3 * (int64_t)(rho0 + rho1) + 8 + 40 * (int64_t)(b0 > b1 ? b0 : b1);
+    }
+    if (ops_out) *ops_out = ops;
+    return best;
+}
+
+int32_t oracle_gi_scores_coins(const uint32_t* keys, const int32_t* counts, int32_t m,
+                               uint32_t a, uint32_t b, const uint8_t* coin_bits, int64_t* score) {
+    coin_src cs;
+    memset(&cs, 0, sizeof cs);
+    cs.bits = coin_bits;
+    cs.m = m;
+    if (m <= 0) return -1;
+    return sel_gi(keys, counts, m, a, b, &cs, score, NULL);
+}
+
+/* ------------------------------------------------------------------ */
+/* Brute force over Algorithm 1 sequences (tiny matrices, test pin)     */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    int32_t rows, cap;
+    uint64_t* hkeys;
+    int64_t* hval;
+    uint8_t* hused;
+    int64_t hsize, hcount;
+    int overflow;
+} bf_ctx;
+
+static uint64_t state_hash(const int8_t* coef, int32_t rows, int32_t ncols, int32_t stride) {
+    uint64_t h = fnv(FNV0, (uint32_t)ncols);
+    for (int32_t r = 0; r < rows; r++)
+        for (int32_t v = 0; v < ncols; v++) h = fnv(h, (uint32_t)(coef[(int64_t)r * stride + v] + 1));
+    return h;
+}
+
+static int64_t bf_rec(bf_ctx* bc, int8_t* coef, int32_t ncols, int32_t nf) {
+    int32_t rows = bc->rows, stride = bc->cap;
+    uint64_t h = state_hash(coef, rows, ncols, stride);
+    int64_t slot = (int64_t)(h % (uint64_t)bc->hsize);
+    while (bc->hused[slot]) {
+        if (bc->hkeys[slot] == h) return bc->hval[slot] + nf;
+        slot = (slot + 1) % bc->hsize;
+    }
+    int64_t occ = max_pair_occurrences(coef, rows, ncols, stride);
+    uint32_t* scratch = (uint32_t*)malloc((size_t)(occ + 1) * 4);
+    uint32_t* keys = (uint32_t*)malloc((size_t)(occ + 1) * 4);
+    int32_t* cnt = (int32_t*)malloc((size_t)(occ + 1) * 4);
+    int32_t nz[1024];
+    int32_t m = count_pairs(coef, rows, ncols, stride, 2, scratch, nz, keys, cnt, (int32_t)occ + 1);
+    /* remaining cost measured from this state: fresh additions still to be
+     * made plus the final naive count */
+    int64_t best;
+    if (m == 0 || ncols >= stride) {
+        best = naive_rows(coef, rows, ncols, stride);
+    } else {
+        best = -1;
+        int8_t* next = (int8_t*)malloc((size_t)rows * (size_t)stride);
+        for (int32_t p = 0; p < m; p++) {
+            memcpy(next, coef, (size_t)rows * (size_t)stride);
+            substitute(next, rows, stride, ncols, (int32_t)KEY_I(keys[p]), (int32_t)KEY_J(keys[p]),
+                       (int32_t)KEY_NEG(keys[p]));
+            int64_t v = bf_rec(bc, next, ncols + 1, 0) + 1;
+            if (best < 0 || v < best) best = v;
+        }
+        free(next);
+    }
+    free(scratch);
+    free(keys);
+    free(cnt);
+    if (bc->hcount * 2 >= bc->hsize) {
+        bc->overflow = 1;
+    } else {
+        slot = (int64_t)(h % (uint64_t)bc->hsize);
+        while (bc->hused[slot]) slot = (slot + 1) % bc->hsize;
+        bc->hused[slot] = 1;
+        bc->hkeys[slot] = h;
+        bc->hval[slot] = best;
+        bc->hcount++;
+    }
+    return best + nf;
+}
+
+int64_t oracle_bruteforce(const int8_t* mat, int32_t rows, int32_t cols, int32_t cap) {
+    if (rows <= 0 || cols <= 0 || cap <= cols || cap > 1024) return -1;
+    bf_ctx bc;
+    memset(&bc, 0, sizeof bc);
+    bc.rows = rows;
+    bc.cap = cap;
+    bc.hsize = 1 << 22;
+    bc.hkeys = (uint64_t*)calloc((size_t)bc.hsize, 8);
+    bc.hval = (int64_t*)calloc((size_t)bc.hsize, 8);
+    bc.hused = (uint8_t*)calloc((size_t)bc.hsize, 1);
+    int8_t* coef = (int8_t*)calloc((size_t)rows * (size_t)cap, 1);
+    for (int32_t r = 0; r < rows; r++)
+        for (int32_t v = 0; v < cols; v++) coef[(int64_t)r * cap + v] = mat[(int64_t)r * cols + v];
+    int64_t v = bf_rec(&bc, coef, cols, 0);
+    free(coef);
+    free(bc.hkeys);
+    free(bc.hval);
+    free(bc.hused);
+    return bc.overflow ? -1 : v;
+}
+
+/* ------------------------------------------------------------------ */
+/* The parallel search (Sections 3.3 and 3.5)                          */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    int8_t* coef;      /* rows x cap: current expressions                */
+    int32_t ncols;     /* n_x + n_f                                      */
+    int32_t* run;      /* current run's substitution list F              */
+    int32_t nf;
+    int32_t strategy, a, b;
+    int32_t ended;     /* run has ended; the next step starts a new one  */
+    uint32_t* keys;    /* current candidates (c >= 2), canonical order   */
+    int32_t* cnt;
+    int32_t m;
+    int64_t best_cost;
+    int32_t best_len;
+    int32_t* best;
+    int32_t runs;
+    uint64_t traj;
+    int64_t ops, substeps;
+} proc_t;
+
+typedef struct {
+    const int8_t* orig;
+    int32_t rows, cols, w32;
+    int64_t naive, max_occ;
+    int64_t snap_cost;
+    int32_t snap_len;
+    int32_t* snap;
+    proc_t* procs;
+} mat_t;
+
+typedef struct {
+    int32_t n_mats, n_proc, interval, permille, cap;
+    uint64_t seed;
+    uint32_t w[OR_NSTRAT];
+    uint64_t wsum;
+    mat_t* mats;
+    const int32_t* subset;
+    int32_t n_sub;
+} search_t;
+
+typedef struct {
+    uint32_t* scratch;
+    int32_t* nz;
+} work_t;
+
+static int64_t run_cost(const search_t* S, const mat_t* M, const proc_t* P) {
+    return P->nf + naive_rows(P->coef, M->rows, P->ncols, S->cap);
+}
+
+static void recount(const search_t* S, const mat_t* M, proc_t* P, work_t* wk) {
+    P->m = count_pairs(P->coef, M->rows, P->ncols, S->cap, 2, wk->scratch, wk->nz, P->keys, P->cnt,
+                       (int32_t)M->max_occ + 1);
+}
+
+/* Candidates whose count a substitution of (i, j) can change: those that
+ * contain x_i or x_j (counted for the algorithmic op total). */
+static int64_t touching(const proc_t* P, int32_t i, int32_t j) {
+    int64_t n = 0;
+    for (int32_t q = 0; q < P->m; q++) {
+        int32_t qi = (int32_t)KEY_I(P->keys[q]), qj = (int32_t)KEY_J(P->keys[q]);
+        n += (qi == i || qj == i || qi == j || qj == j);
+    }
+    return n;
+}
+
+static int32_t live_columns_below(const search_t* S, const mat_t* M, const proc_t* P, int32_t k) {
+    int32_t n = 0;
+    for (int32_t v = 0; v < k; v++) {
+        int32_t any = 0;
+        for (int32_t r = 0; r < M->rows && !any; r++) any = P->coef[(int64_t)r * S->cap + v] != 0;
+        n += any;
+    }
+    return n;
+}
+
+/* One substitution of canonical pair key into process P; the candidate list
+ * is recounted afterwards.  Algorithmic ops: the rewrite (10 per 32-bit word
+ * of a column) plus 5 per word for every pair count that can change: the
+ * candidates containing x_i or x_j, and x_k against every live column. */
+static int32_t do_subst(const search_t* S, const mat_t* M, proc_t* P, work_t* wk, uint32_t key) {
+    int32_t i = (int32_t)KEY_I(key), j = (int32_t)KEY_J(key), neg = (int32_t)KEY_NEG(key);
+    int64_t nij = touching(P, i, j);
+    int32_t k = P->ncols;
+    int32_t c = substitute(P->coef, M->rows, S->cap, k, i, j, neg);
+    P->ncols++;
+    P->run[P->nf++] = ENTRY(i, j, neg);
+    int64_t nu = live_columns_below(S, M, P, k);
+    P->ops += 10 * (int64_t)M->w32 + 5 * (int64_t)M->w32 * (nij + nu);
+    recount(S, M, P, wk);
+    return c;
+}
+
+static void fold(const search_t* S, const mat_t* M, proc_t* P) {
+    int64_t c = run_cost(S, M, P);
+    if (c < P->best_cost) {
+        P->best_cost = c;
+        P->best_len = P->nf;
+        memcpy(P->best, P->run, (size_t)P->nf * sizeof(int32_t));
+    }
+}
+
+static void start_run(const search_t* S, int32_t mi, int32_t pi, int64_t t, work_t* wk) {
+    mat_t* M = &S->mats[mi];
+    proc_t* P = &M->procs[pi];
+    if (t > 0) fold(S, M, P);
+    P->runs++;
+    if (pi == 0 && t == 0) {
+        P->strategy = OR_G;
+    } else {
+        uint32_t x = scale(draw(S->seed, pi, t, mi, PU_STRAT), S->wsum);
+        uint64_t acc = 0;
+        P->strategy = -1;
+        for (int32_t s = 0; s < OR_NSTRAT; s++) {
+            acc += S->w[s];
+            if (x < acc) {
+                P->strategy = s;
+                break;
+            }
+        }
+    }
+    P->a = (int32_t)scale(draw(S->seed, pi, t, mi, PU_ALPHA), 32769);
+    P->b = 32768 + (int32_t)scale(draw(S->seed, pi, t, mi, PU_BETA), 32769);
+    /* fresh copy of the original expressions */
+    memset(P->coef, 0, (size_t)M->rows * (size_t)S->cap);
+    for (int32_t r = 0; r < M->rows; r++)
+        for (int32_t v = 0; v < M->cols; v++)
+            P->coef[(int64_t)r * S->cap + v] = M->orig[(int64_t)r * M->cols + v];
+    P->ncols = M->cols;
+    P->nf = 0;
+    P->ops += 5 * (int64_t)M->w32 * ((int64_t)M->cols * (M->cols - 1) / 2);
+    recount(S, M, P, wk);
+    int32_t k = 0;
+    if (M->snap_cost < INT64_MAX) {
+        uint64_t thr = ((uint64_t)S->permille << 32) / 1000u;
+        if ((uint64_t)draw(S->seed, pi, t, mi, PU_SHARE) < thr) {
+            int32_t big_k = (3 * M->snap_len) / 4;
+            if (big_k >= 1) k = 1 + (int32_t)scale(draw(S->seed, pi, t, mi, PU_SHAREK), (uint64_t)big_k);
+        }
+    }
+    for (int32_t e = 0; e < k; e++) {
+        int32_t ent = M->snap[e];
+        do_subst(S, M, P, wk, KEY(ENT_I(ent), ENT_J(ent), ENT_NEG(ent)));
+    }
+    P->ended = 0;
+    P->traj = fnv(P->traj, (uint32_t)t);
+    P->traj = fnv(P->traj, 0xA0000000u | (uint32_t)P->strategy << 12 | (uint32_t)k);
+}
+
+static int32_t choose(const search_t* S, int32_t mi, int32_t pi, int64_t t, proc_t* P) {
+    int32_t strat = P->strategy;
+    uint64_t seed = S->seed;
+    if (strat == OR_MIX) {
+        uint32_t r = scale(draw(seed, pi, t, mi, PU_MIX), 15);
+        strat = r < 8 ? OR_GI : r < 12 ? OR_GA : r < 14 ? OR_GR : OR_WR;
+    }
+    switch (strat) {
+        case OR_G: P->ops += 2 * (int64_t)P->m; return sel_g(P->cnt, P->m);
+        case OR_GA: P->ops += 2 * (int64_t)P->m; return sel_ga(P->cnt, P->m, draw(seed, pi, t, mi, PU_GA));
+        case OR_WR: P->ops += 2 * (int64_t)P->m; return sel_wr(P->cnt, P->m, draw(seed, pi, t, mi, PU_WR));
+        case OR_GR:
+            P->ops += 2 * (int64_t)P->m;
+            return sel_gr(P->cnt, P->m, draw(seed, pi, t, mi, PU_GR), draw(seed, pi, t, mi, PU_GA),
+                          draw(seed, pi, t, mi, PU_WR));
+        case OR_GI: {
+            coin_src cs;
+            memset(&cs, 0, sizeof cs);
+            cs.seed = seed;
+            cs.proc = pi;
+            cs.mat = mi;
+            cs.t = t;
+            cs.keys = P->keys;
+            cs.block_p = -1;
+            int64_t ops = 0;
+            int32_t sel = sel_gi(P->keys, P->cnt, P->m, (uint32_t)P->a, (uint32_t)P->b, &cs, NULL, &ops);
+            P->ops += ops;
+            return sel;
+        }
+        default: return -1;
+    }
+}
+
+static void step(const search_t* S, int32_t mi, int32_t pi, int64_t t, work_t* wk) {
+    mat_t* M = &S->mats[mi];
+    proc_t* P = &M->procs[pi];
+    if (t == 0 || P->ended) start_run(S, mi, pi, t, wk);
+    if (P->m == 0 || P->ncols >= S->cap) {
+        P->ended = 1;
+        return;
+    }
+    int32_t sel = choose(S, mi, pi, t, P);
+    uint32_t key = P->keys[sel];
+    do_subst(S, M, P, wk, key);
+    P->substeps++;
+    P->traj = fnv(P->traj, (uint32_t)t);
+    P->traj = fnv(P->traj, (uint32_t)P->run[P->nf - 1]);
+    if (P->m == 0 || P->ncols >= S->cap) P->ended = 1;
+}
+
+typedef struct {
+    const search_t* S;
+    int64_t t0, t1;
+    int64_t u0, u1; /* unit range: unit = mi * n_sub + subset index */
+    work_t wk;
+} job_t;
+
+static void* run_job(void* arg) {
+    job_t* J = (job_t*)arg;
+    const search_t* S = J->S;
+    for (int64_t u = J->u0; u < J->u1; u++) {
+        int32_t mi = (int32_t)(u / S->n_sub);
+        int32_t pi = S->subset[u % S->n_sub];
+        for (int64_t t = J->t0; t < J->t1; t++) step(S, mi, pi, t, &J->wk);
+    }
+    return NULL;
+}
+
+static int valid_matrix(const int8_t* m, int32_t rows, int32_t cols) {
+    for (int32_t r = 0; r < rows; r++) {
+        int32_t nnz = 0;
+        for (int32_t v = 0; v < cols; v++) {
+            int8_t x = m[(int64_t)r * cols + v];
+            if (x < -1 || x > 1) return 0;
+            nnz += x != 0;
+        }
+        if (nnz == 0) return 0;
+    }
+    return 1;
+}
+
+int oracle_search(int32_t n_mats, const int8_t* const* mats, const int32_t* rows,
+                  const int32_t* cols, const uint32_t* weights6, int32_t n_proc, uint64_t seed,
+                  int64_t budget, int32_t interval, int32_t permille, int32_t cap,
+                  int32_t n_threads, const int32_t* proc_subset, int32_t n_subset,
+                  int64_t* out_cost, int32_t* out_len, int32_t* out_list, oracle_digest* dig) {
+    if (n_mats < 1 || n_mats > 256 || n_proc < 1 || budget < 0 || interval < 1 ||
+        permille < 0 || permille > 1000 || cap < 2 || cap > 1024)
+        return -1;
+    search_t S;
+    memset(&S, 0, sizeof S);
+    S.n_mats = n_mats;
+    S.n_proc = n_proc;
+    S.interval = interval;
+    S.permille = permille;
+    S.cap = cap;
+    S.seed = seed;
+    for (int32_t s = 0; s < OR_NSTRAT; s++) {
+        S.w[s] = weights6[s];
+        S.wsum += weights6[s];
+    }
+    if (S.wsum == 0 || S.wsum > 0xFFFFFFFFull) return -1;
+    for (int32_t mi = 0; mi < n_mats; mi++)
+        if (rows[mi] < 1 || rows[mi] > 256 || cols[mi] < 1 || cols[mi] >= cap ||
+            !valid_matrix(mats[mi], rows[mi], cols[mi]))
+            return -1;
+    int32_t* all = NULL;
+    if (proc_subset) {
+        for (int32_t s = 0; s < n_subset; s++)
+            if (proc_subset[s] < 0 || proc_subset[s] >= n_proc) return -1;
+        S.subset = proc_subset;
+        S.n_sub = n_subset;
+    } else {
+        all = (int32_t*)malloc((size_t)n_proc * sizeof(int32_t));
+        for (int32_t p = 0; p < n_proc; p++) all[p] = p;
+        S.subset = all;
+        S.n_sub = n_proc;
+    }
+    if (n_threads < 1) n_threads = 1;
+
+    S.mats = (mat_t*)calloc((size_t)n_mats, sizeof(mat_t));
+    int64_t max_occ_all = 0;
+    int32_t max_cols = 0;
+    for (int32_t mi = 0; mi < n_mats; mi++) {
+        mat_t* M = &S.mats[mi];
+        M->orig = mats[mi];
+        M->rows = rows[mi];
+        M->cols = cols[mi];
+        M->w32 = (rows[mi] + 31) / 32;
+        M->naive = oracle_naive(mats[mi], rows[mi], cols[mi]);
+        M->max_occ = max_pair_occurrences(mats[mi], rows[mi], cols[mi], cols[mi]);
+        if (M->max_occ > max_occ_all) max_occ_all = M->max_occ;
+        if (cols[mi] > max_cols) max_cols = cols[mi];
+        M->snap_cost = INT64_MAX;
+        M->snap = (int32_t*)calloc((size_t)cap, sizeof(int32_t));
+        M->procs = (proc_t*)calloc((size_t)n_proc, sizeof(proc_t));
+        for (int32_t s = 0; s < S.n_sub; s++) {
+            proc_t* P = &M->procs[S.subset[s]];
+            P->coef = (int8_t*)calloc((size_t)M->rows * (size_t)cap, 1);
+            P->run = (int32_t*)calloc((size_t)cap, sizeof(int32_t));
+            P->best = (int32_t*)calloc((size_t)cap, sizeof(int32_t));
+            P->keys = (uint32_t*)calloc((size_t)M->max_occ + 1, sizeof(uint32_t));
+            P->cnt = (int32_t*)calloc((size_t)M->max_occ + 1, sizeof(int32_t));
+            P->best_cost = M->naive;
+            P->best_len = 0;
+            P->traj = FNV0;
+        }
+    }
+
+    int64_t units = (int64_t)n_mats * S.n_sub;
+    if (n_threads > units) n_threads = (int32_t)(units > 0 ? units : 1);
+    job_t* jobs = (job_t*)calloc((size_t)n_threads, sizeof(job_t));
+    pthread_t* th = (pthread_t*)calloc((size_t)n_threads, sizeof(pthread_t));
+    for (int32_t k = 0; k < n_threads; k++) {
+        jobs[k].S = &S;
+        jobs[k].wk.scratch = (uint32_t*)malloc((size_t)(max_occ_all + 1) * sizeof(uint32_t));
+        jobs[k].wk.nz = (int32_t*)malloc((size_t)(cap + 1) * sizeof(int32_t));
+        jobs[k].u0 = units * k / n_threads;
+        jobs[k].u1 = units * (k + 1) / n_threads;
+    }
+
+    for (int64_t t0 = 0; t0 < budget; t0 += interval) {
+        int64_t t1 = t0 + interval < budget ? t0 + interval : budget;
+        for (int32_t k = 0; k < n_threads; k++) {
+            jobs[k].t0 = t0;
+            jobs[k].t1 = t1;
+        }
+        if (n_threads == 1) {
+            run_job(&jobs[0]);
+        } else {
+            for (int32_t k = 0; k < n_threads; k++) pthread_create(&th[k], NULL, run_job, &jobs[k]);
+            for (int32_t k = 0; k < n_threads; k++) pthread_join(th[k], NULL);
+        }
+        /* sharing boundary (or end of budget): fold, then publish */
+        for (int32_t mi = 0; mi < n_mats; mi++) {
+            mat_t* M = &S.mats[mi];
+            int32_t win = -1;
+            for (int32_t s = 0; s < S.n_sub; s++) {
+                int32_t p = S.subset[s];
+                fold(&S, M, &M->procs[p]);
+            }
+            for (int32_t p = 0; p < n_proc; p++) {
+                if (!M->procs[p].coef) continue;
+                if (win < 0 || M->procs[p].best_cost < M->procs[win].best_cost) win = p;
+            }
+            if (t1 % interval == 0 && win >= 0 && M->procs[win].best_cost < M->snap_cost) {
+                M->snap_cost = M->procs[win].best_cost;
+                M->snap_len = M->procs[win].best_len;
+                memcpy(M->snap, M->procs[win].best, (size_t)M->snap_len * sizeof(int32_t));
+            }
+        }
+    }
+    /* budget == 0: results are the inputs */
+
+    for (int32_t mi = 0; mi < n_mats; mi++) {
+        mat_t* M = &S.mats[mi];
+        int32_t win = -1;
+        for (int32_t p = 0; p < n_proc; p++) {
+            proc_t* P = &M->procs[p];
+            if (!P->coef) continue;
+            if (win < 0 || P->best_cost < M->procs[win].best_cost) win = p;
+            if (dig) {
+                oracle_digest* d = &dig[(int64_t)mi * n_proc + p];
+                d->best_cost = P->best_cost;
+                d->best_len = P->best_len;
+                d->runs = P->runs;
+                uint64_t h = FNV0;
+                for (int32_t e = 0; e < P->best_len; e++) h = fnv(h, (uint32_t)P->best[e]);
+                d->best_hash = h;
+                d->traj_hash = P->traj;
+                d->ops = P->ops;
+                d->substeps = P->substeps;
+            }
+        }
+        if (out_cost) out_cost[mi] = M->procs[win].best_cost;
+        if (out_len) out_len[mi] = M->procs[win].best_len;
+        if (out_list) {
+            memset(out_list + (int64_t)mi * cap, 0, (size_t)cap * sizeof(int32_t));
+            memcpy(out_list + (int64_t)mi * cap, M->procs[win].best,
+                   (size_t)M->procs[win].best_len * sizeof(int32_t));
+        }
+    }
+
+    for (int32_t k = 0; k < n_threads; k++) {
+        free(jobs[k].wk.scratch);
+        free(jobs[k].wk.nz);
+    }
+    free(jobs);
+    free(th);
+    for (int32_t mi = 0; mi < n_mats; mi++) {
+        mat_t* M = &S.mats[mi];
+        for (int32_t p = 0; p < n_proc; p++) {
+            proc_t* P = &M->procs[p];
+            free(P->coef);
+            free(P->run);
+            free(P->best);
+            free(P->keys);
+            free(P->cnt);
+        }
+        free(M->procs);
+        free(M->snap);
+    }
+    free(S.mats);
+    free(all);
+    return 0;
+}

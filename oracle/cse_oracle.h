@@ -1,0 +1,88 @@
+/*
+ * cse_oracle.h -- CPU oracle of the parallel heuristic CSE search.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This is a plain, slow, single-purpose C
+ * restatement of the method of "Parallel Heuristic Exploration for Additive
+ * Complexity Reduction in Fast Matrix Multiplication" (Perminov), used to
+ * check the CUDA library.  Only the tests, the smoke check and the CPU
+ * baseline leg of the benchmark may call it; the library never does.  It
+ * shares no code, header or table with the CUDA path.
+ *
+ * Readings of points the paper leaves open (random generator, canonical
+ * order, tie breaks, fixed-point alpha/beta, sharing clock) are stated next to
+ * the code that takes them in cse_oracle.c.
+ */
+#ifndef CSE_ORACLE_H
+#define CSE_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Strategy indices (Section 3.4); weights are given in this order. */
+enum { OR_GI = 0, OR_GA = 1, OR_GR = 2, OR_WR = 3, OR_MIX = 4, OR_G = 5, OR_NSTRAT = 6 };
+
+/* Per-process summary used by the parity tests. */
+typedef struct {
+    int64_t best_cost;   /* Cost(E) of the process's best record            */
+    int32_t best_len;    /* substitutions in that record                    */
+    int32_t runs;        /* runs started                                    */
+    uint64_t best_hash;  /* FNV-1a over the 32-bit entries of the record    */
+    uint64_t traj_hash;  /* FNV-1a over the trajectory events               */
+    int64_t ops;         /* algorithmic integer-op count of the trajectory  */
+    int64_t substeps;    /* steps that made a substitution                  */
+} oracle_digest;
+
+/* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11). */
+void oracle_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+
+/* A_naive(E) = sum over rows of (nnz - 1)  (Section 3.2.1). */
+int64_t oracle_naive(const int8_t* mat, int32_t rows, int32_t cols);
+
+/* Canonical pair frequencies of a matrix (Algorithm 1, Analysis).
+ * Writes up to max_out candidates (c >= min_c) in canonical order:
+ * keys[t] = ((j << 10 | i) << 1) | (s < 0) with i < j, counts[t] = c.
+ * Returns the number of candidates (may exceed max_out). */
+int32_t oracle_pairs(const int8_t* mat, int32_t rows, int32_t cols, int32_t min_c,
+                     uint32_t* keys, int32_t* counts, int32_t max_out);
+
+/* Applies a substitution list (entries i | j<<10 | (s<0)<<20) to a matrix.
+ * out has rows x (cols + n) entries.  Returns Cost = n + A_naive(E_final), or
+ * -1 if an entry is not a valid pair of existing variables. */
+int64_t oracle_apply(const int8_t* mat, int32_t rows, int32_t cols, const int32_t* list,
+                     int32_t n, int8_t* out);
+
+/* Basic selection strategies on an explicit candidate list (canonical order)
+ * with explicit 32-bit draws: kind in {OR_G, OR_GA, OR_WR, OR_GR}; u[] holds
+ * the draws the strategy reads (ga: u[0]; wr: u[0]; gr: u[0] coin, u[1] ga or
+ * wr draw).  Returns the selected index. */
+int32_t oracle_select_basic(int32_t kind, const int32_t* counts, int32_t m, const uint32_t* u);
+
+/* Greedy-Intersections scores (Section 3.4.2) with explicit coins:
+ * coin_bits[p*m + q] is the coin of candidate q as seen from candidate p.
+ * Writes score[p] = H(s_p) * 2^32 in exact integers and returns argmax. */
+int32_t oracle_gi_scores_coins(const uint32_t* keys, const int32_t* counts, int32_t m,
+                               uint32_t a, uint32_t b, const uint8_t* coin_bits, int64_t* score);
+
+/* Exhaustive minimum of Cost over all sequences of Algorithm 1 on a tiny
+ * matrix (rows * cols small).  Returns the optimum, or -1 on overflow. */
+int64_t oracle_bruteforce(const int8_t* mat, int32_t rows, int32_t cols, int32_t cap);
+
+/* The full search (Sections 3.3-3.5, Algorithm 1) over n_mats expression sets.
+ * weights6: gi, ga, gr, wr, mix, g.  Outputs per matrix: best cost, length,
+ * list (cap entries per matrix).  dig: n_mats * n_proc digests or NULL.
+ * proc_subset: if non-NULL, only these processes are simulated (exact only
+ * while no snapshot is published, i.e. budget <= interval).
+ * Returns 0, or a negative error code for invalid arguments. */
+int oracle_search(int32_t n_mats, const int8_t* const* mats, const int32_t* rows,
+                  const int32_t* cols, const uint32_t* weights6, int32_t n_proc, uint64_t seed,
+                  int64_t budget, int32_t interval, int32_t permille, int32_t cap,
+                  int32_t n_threads, const int32_t* proc_subset, int32_t n_subset,
+                  int64_t* out_cost, int32_t* out_len, int32_t* out_list, oracle_digest* dig);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,201 @@
+"""ctypes binding of the C oracle (cse_oracle.c).
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the CPU
+baseline leg of ``bench.py`` use it to check and time the CUDA library.  The
+library itself never imports it.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "cse_oracle.c")
+_LIB = os.path.join(_HERE, "_build", "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+G, GI, GA, GR, WR, MIX = 5, 0, 1, 2, 3, 4
+
+
+class Digest(ctypes.Structure):
+    _fields_ = [("best_cost", ctypes.c_int64), ("best_len", ctypes.c_int32), ("runs", ctypes.c_int32),
+                ("best_hash", ctypes.c_uint64), ("traj_hash", ctypes.c_uint64), ("ops", ctypes.c_int64),
+                ("substeps", ctypes.c_int64)]
+
+
+DIGEST_DTYPE = np.dtype([("best_cost", "<i8"), ("best_len", "<i4"), ("runs", "<i4"),
+                         ("best_hash", "<u8"), ("traj_hash", "<u8"), ("ops", "<i8"),
+                         ("substeps", "<i8")])
+assert DIGEST_DTYPE.itemsize == ctypes.sizeof(Digest)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc into oracle/_build (plain -O2, no SIMD flags)."""
+    with _lock:
+        if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+            return _LIB
+        os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lpthread"])
+        os.replace(tmp, _LIB)
+        return _LIB
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        L = ctypes.CDLL(build())
+        i8p = ctypes.POINTER(ctypes.c_int8)
+        i32p = ctypes.POINTER(ctypes.c_int32)
+        i64p = ctypes.POINTER(ctypes.c_int64)
+        u32p = ctypes.POINTER(ctypes.c_uint32)
+        L.oracle_philox.argtypes = [u32p, u32p, u32p]
+        L.oracle_philox.restype = None
+        L.oracle_naive.argtypes = [i8p, ctypes.c_int32, ctypes.c_int32]
+        L.oracle_naive.restype = ctypes.c_int64
+        L.oracle_pairs.argtypes = [i8p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, u32p, i32p, ctypes.c_int32]
+        L.oracle_pairs.restype = ctypes.c_int32
+        L.oracle_apply.argtypes = [i8p, ctypes.c_int32, ctypes.c_int32, i32p, ctypes.c_int32, i8p]
+        L.oracle_apply.restype = ctypes.c_int64
+        L.oracle_select_basic.argtypes = [ctypes.c_int32, i32p, ctypes.c_int32, u32p]
+        L.oracle_select_basic.restype = ctypes.c_int32
+        L.oracle_gi_scores_coins.argtypes = [u32p, i32p, ctypes.c_int32, ctypes.c_uint32, ctypes.c_uint32,
+                                             ctypes.POINTER(ctypes.c_uint8), i64p]
+        L.oracle_gi_scores_coins.restype = ctypes.c_int32
+        L.oracle_bruteforce.argtypes = [i8p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]
+        L.oracle_bruteforce.restype = ctypes.c_int64
+        L.oracle_search.argtypes = [ctypes.c_int32, ctypes.POINTER(i8p), i32p, i32p, u32p, ctypes.c_int32,
+                                    ctypes.c_uint64, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                    ctypes.c_int32, ctypes.c_int32, i32p, ctypes.c_int32, i64p, i32p, i32p,
+                                    ctypes.POINTER(Digest)]
+        L.oracle_search.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray, ct):
+    return a.ctypes.data_as(ctypes.POINTER(ct))
+
+
+def philox(ctr: Sequence[int], key: Sequence[int]) -> List[int]:
+    c = np.array(ctr, dtype=np.uint32)
+    k = np.array(key, dtype=np.uint32)
+    o = np.zeros(4, dtype=np.uint32)
+    lib().oracle_philox(_p(c, ctypes.c_uint32), _p(k, ctypes.c_uint32), _p(o, ctypes.c_uint32))
+    return [int(x) for x in o]
+
+
+def naive(mat: np.ndarray) -> int:
+    m = np.ascontiguousarray(mat, dtype=np.int8)
+    return int(lib().oracle_naive(_p(m, ctypes.c_int8), m.shape[0], m.shape[1]))
+
+
+def key(i: int, j: int, s: int) -> int:
+    """Canonical key of pair (x_i + s x_j), i < j (0-based)."""
+    return (((j << 10) | i) << 1) | (1 if s < 0 else 0)
+
+
+def unkey(k: int):
+    return (k >> 1) & 0x3FF, (k >> 11) & 0x3FF, -1 if k & 1 else 1
+
+
+def entry(i: int, j: int, s: int) -> int:
+    return i | (j << 10) | ((1 if s < 0 else 0) << 20)
+
+
+def unentry(e: int):
+    return e & 0x3FF, (e >> 10) & 0x3FF, -1 if (e >> 20) & 1 else 1
+
+
+def pairs(mat: np.ndarray, min_c: int = 2):
+    """Canonical pairs with count >= min_c, in canonical order: list of (key, c)."""
+    m = np.ascontiguousarray(mat, dtype=np.int8)
+    cap = m.shape[0] * m.shape[1] * m.shape[1] + 1
+    keys = np.zeros(cap, dtype=np.uint32)
+    cnt = np.zeros(cap, dtype=np.int32)
+    n = lib().oracle_pairs(_p(m, ctypes.c_int8), m.shape[0], m.shape[1], min_c, _p(keys, ctypes.c_uint32),
+                           _p(cnt, ctypes.c_int32), cap)
+    return [(int(keys[t]), int(cnt[t])) for t in range(n)]
+
+
+def apply(mat: np.ndarray, entries: Sequence[int]):
+    """Apply a substitution list; returns (final matrix, Cost) (Cost -1 if invalid)."""
+    m = np.ascontiguousarray(mat, dtype=np.int8)
+    lst = np.ascontiguousarray(np.array(list(entries), dtype=np.int32))
+    out = np.zeros((m.shape[0], m.shape[1] + len(lst)), dtype=np.int8)
+    c = lib().oracle_apply(_p(m, ctypes.c_int8), m.shape[0], m.shape[1], _p(lst, ctypes.c_int32), len(lst),
+                           _p(out, ctypes.c_int8))
+    return out, int(c)
+
+
+def select_basic(kind: int, counts: Sequence[int], u: Sequence[int]) -> int:
+    c = np.ascontiguousarray(np.array(counts, dtype=np.int32))
+    uu = np.zeros(2, dtype=np.uint32)
+    uu[:len(u)] = u
+    return int(lib().oracle_select_basic(kind, _p(c, ctypes.c_int32), len(c), _p(uu, ctypes.c_uint32)))
+
+
+def gi_scores(keys: Sequence[int], counts: Sequence[int], a: int, b: int, coins: np.ndarray):
+    k = np.ascontiguousarray(np.array(keys, dtype=np.uint32))
+    c = np.ascontiguousarray(np.array(counts, dtype=np.int32))
+    m = len(k)
+    cb = np.ascontiguousarray(np.asarray(coins, dtype=np.uint8).reshape(m, m))
+    sc = np.zeros(m, dtype=np.int64)
+    best = lib().oracle_gi_scores_coins(_p(k, ctypes.c_uint32), _p(c, ctypes.c_int32), m, a, b,
+                                        _p(cb, ctypes.c_uint8), _p(sc, ctypes.c_int64))
+    return int(best), [int(x) for x in sc]
+
+
+def bruteforce(mat: np.ndarray, cap: Optional[int] = None) -> int:
+    m = np.ascontiguousarray(mat, dtype=np.int8)
+    if cap is None:
+        cap = m.shape[1] + 64
+    return int(lib().oracle_bruteforce(_p(m, ctypes.c_int8), m.shape[0], m.shape[1], cap))
+
+
+class SearchResult:
+    def __init__(self, cost, length, lists, digests):
+        self.cost = cost            # per matrix best Cost
+        self.length = length        # per matrix best list length
+        self.lists = lists          # per matrix list of packed entries
+        self.digests = digests      # (n_mats, n_proc) structured array or None
+
+    @property
+    def total(self) -> int:
+        return int(sum(self.cost))
+
+
+def search(mats: Sequence[np.ndarray], weights, n_proc: int, seed: int, budget: int, interval: int,
+           permille: int, cap: int, n_threads: int = 1, subset: Optional[Sequence[int]] = None,
+           digests: bool = True) -> SearchResult:
+    ms = [np.ascontiguousarray(m, dtype=np.int8) for m in mats]
+    n = len(ms)
+    ptrs = (ctypes.POINTER(ctypes.c_int8) * n)(*[_p(m, ctypes.c_int8) for m in ms])
+    rows = np.array([m.shape[0] for m in ms], dtype=np.int32)
+    cols = np.array([m.shape[1] for m in ms], dtype=np.int32)
+    w = np.array(list(weights), dtype=np.uint32)
+    cost = np.zeros(n, dtype=np.int64)
+    length = np.zeros(n, dtype=np.int32)
+    lists = np.zeros((n, cap), dtype=np.int32)
+    dig = np.zeros((n, n_proc), dtype=DIGEST_DTYPE) if digests else None
+    sub = None if subset is None else np.ascontiguousarray(np.array(subset, dtype=np.int32))
+    rc = lib().oracle_search(n, ptrs, _p(rows, ctypes.c_int32), _p(cols, ctypes.c_int32),
+                             _p(w, ctypes.c_uint32), n_proc, seed, budget, interval, permille, cap, n_threads,
+                             None if sub is None else _p(sub, ctypes.c_int32), 0 if sub is None else len(sub),
+                             _p(cost, ctypes.c_int64), _p(length, ctypes.c_int32), _p(lists, ctypes.c_int32),
+                             None if dig is None else dig.ctypes.data_as(ctypes.POINTER(Digest)))
+    if rc != 0:
+        raise ValueError(f"oracle_search rejected its arguments (rc={rc})")
+    return SearchResult([int(x) for x in cost], [int(x) for x in length],
+                        [[int(e) for e in lists[k, :length[k]]] for k in range(n)], dig)
+
+
+def search_obj(s, **kw) -> SearchResult:
+    """Run the oracle on a synth.Search description."""
+    return search(s.mats, s.weights, s.n_proc, s.seed, s.budget, s.interval, s.permille, s.cap, **kw)

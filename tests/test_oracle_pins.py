@@ -1,0 +1,416 @@
+"""Pins of the CPU oracle to facts the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: published
+known-answer vectors, the paper's worked example (Section 3.2.2), hand-derived
+scores, closed forms of the step clock, exhaustive search on tiny inputs, and
+invariants checked by independent numpy code.
+"""
+import itertools
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2512_13365_gb300 import synth
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _lines(name):
+    with open(os.path.join(GOLD, name)) as f:
+        for ln in f:
+            ln = ln.strip()
+            if ln and not ln.startswith("#"):
+                yield ln
+
+
+# ---------------------------------------------------------------- helpers
+def expand(mat, entries):
+    """Independent check of a substitution list: express every fresh variable
+    over the original ones and rebuild each final row from them."""
+    rows, nx = mat.shape
+    cur = np.zeros((rows, nx + len(entries)), dtype=np.int64)
+    cur[:, :nx] = mat
+    defs = [np.eye(nx, dtype=np.int64)[v] for v in range(nx)]
+    for t, e in enumerate(entries):
+        i, j, s = O.unentry(e)
+        k = nx + t
+        assert i < j < k
+        defs.append(defs[i] + s * defs[j])
+        hit = (cur[:, i] != 0) & (cur[:, j] == s * cur[:, i])
+        cur[hit, k] = cur[hit, i]
+        cur[hit, i] = 0
+        cur[hit, j] = 0
+    D = np.stack(defs)
+    return cur, cur @ D
+
+
+def cost_of(cur, n_f):
+    return int(n_f + sum(np.count_nonzero(r) - 1 for r in cur))
+
+
+# ---------------------------------------------------------------- Philox
+def test_philox_known_answers():
+    n = 0
+    for ln in _lines("philox4x32_10_kat.txt"):
+        w = [int(x, 16) for x in ln.split()]
+        assert O.philox(w[0:4], w[4:6]) == w[6:10]
+        n += 1
+    assert n == 3
+
+
+# ---------------------------------------------------------------- worked example
+def _example():
+    mat, final, subst, pairs = [], [], [], []
+    sec = None
+    vals = {}
+    for ln in _lines("paper_example.txt"):
+        f = ln.split()
+        if f[0] in ("matrix", "final"):
+            sec = f[0]
+            continue
+        if f[0] in ("naive", "cost", "optimum"):
+            vals[f[0]] = int(f[1])
+            sec = None
+        elif f[0] == "subst":
+            subst.append(tuple(int(x) for x in f[1:]))
+        elif f[0] == "pair":
+            pairs.append(tuple(int(x) for x in f[1:]))
+        elif sec == "matrix":
+            mat.append([int(x) for x in f])
+        elif sec == "final":
+            final.append([int(x) for x in f])
+    return np.array(mat, np.int8), np.array(final, np.int8), subst, pairs, vals
+
+
+def test_paper_example_naive_and_cost():
+    mat, final, subst, _, vals = _example()
+    assert O.naive(mat) == vals["naive"] == 8
+    out, cost = O.apply(mat, [O.entry(*s) for s in subst])
+    assert cost == vals["cost"] == 6
+    assert np.array_equal(out, final)
+
+
+def test_paper_example_pair_counts():
+    mat, _, _, pairs, _ = _example()
+    got = [(O.unkey(k), c) for k, c in O.pairs(mat)]
+    assert got == [((i, j, s), c) for i, j, s, c in pairs]
+    # all other pairs occur exactly once
+    allp = O.pairs(mat, min_c=1)
+    assert sum(c for _, c in allp) == sum(3 * 2 if n == 4 else 3 for n in (4, 3, 4)) == 15
+    assert all(c == 1 for k, c in allp if O.unkey(k) not in [(i, j, s) for i, j, s, _ in pairs])
+
+
+def test_paper_example_optimum_and_greedy():
+    mat, _, _, _, vals = _example()
+    assert O.bruteforce(mat) == vals["optimum"] == 6
+    # Greedy (max c, lowest canonical key) takes (x1 - x2) first, then
+    # (x3 - x4) (derived by hand from the rows), and reaches 6.
+    r = O.search([mat], (0, 0, 0, 0, 0, 1), 1, 0, 2, 64, 0, 16)
+    assert r.cost == [6]
+    assert [O.unentry(e) for e in r.lists[0]] == [(0, 1, -1), (2, 3, -1)]
+
+
+# ---------------------------------------------------------------- Strassen
+def test_strassen_textbook():
+    U, V, W = synth.strassen_uvw()
+    # Brent equations: sum_l U[l,(i,j)] V[l,(j',k)] W[l,(i',k')] = d_jj' d_ii' d_kk'
+    T = np.einsum("la,lb,lc->abc", U.astype(int), V.astype(int), W.astype(int))
+    ref = np.zeros((4, 4, 4), dtype=int)
+    for i, j, k in itertools.product(range(2), repeat=3):
+        ref[i * 2 + j, j * 2 + k, i * 2 + k] = 1
+    assert np.array_equal(T, ref)
+    sides = synth.scheme_sides(U, V, W)
+    # Strassen's algorithm takes 18 additions (Section 2.2)
+    assert sum(O.naive(m) for m in sides) == 18
+    # no signed pair repeats in any side, so Algorithm 1 cannot improve it
+    for m in sides:
+        assert O.pairs(m) == []
+        assert O.bruteforce(m) == O.naive(m)
+    r = O.search(sides, synth.PAPER_WEIGHTS, 8, 3, 20, 4, 400, 32)
+    assert r.total == 18 and r.length == [0, 0, 0]
+
+
+# ---------------------------------------------------------------- brute force
+def _py_bruteforce(mat):
+    """Exhaustive search without memo, over every sequence of substitutions of
+    pairs with c >= 2 (Algorithm 1), for a second route to the optimum."""
+    rows, nx = mat.shape
+
+    def rec(cur):
+        nz = [np.nonzero(r)[0] for r in cur]
+        cnt = {}
+        for r, idx in zip(cur, nz):
+            for a, b in itertools.combinations(idx, 2):
+                kk = (a, b, int(r[a] * r[b]))
+                cnt[kk] = cnt.get(kk, 0) + 1
+        best = sum(len(x) - 1 for x in nz)
+        for (a, b, s), c in cnt.items():
+            if c < 2:
+                continue
+            nxt = np.zeros((rows, cur.shape[1] + 1), dtype=np.int64)
+            nxt[:, :-1] = cur
+            hit = (cur[:, a] != 0) & (cur[:, b] == s * cur[:, a])
+            nxt[hit, -1] = cur[hit, a]
+            nxt[hit, a] = 0
+            nxt[hit, b] = 0
+            best = min(best, 1 + rec(nxt))
+        return best
+
+    return rec(mat.astype(np.int64))
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_bruteforce_matches_plain_enumeration(seed):
+    mat = synth.random_matrix(seed, 4, 5, 2, 4, n_planted=2, frac=(0.5, 0.75))
+    assert O.bruteforce(mat) == _py_bruteforce(mat)
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_search_never_beats_optimum_and_usually_reaches_it(seed):
+    mat = synth.random_matrix(100 + seed, 5, 6, 2, 4, n_planted=2, frac=(0.4, 0.8))
+    opt = O.bruteforce(mat)
+    r = O.search([mat], synth.PAPER_WEIGHTS, 256, seed, 64, 8, 400, 32)
+    assert r.cost[0] >= opt
+    assert r.cost[0] == opt  # 256 processes x 64 steps on 5 x 6 reach the optimum
+
+
+# ---------------------------------------------------------------- invariants
+@pytest.mark.parametrize("seed", range(4))
+def test_result_lists_are_valid_programs(seed):
+    mats = [synth.random_matrix(200 + seed, 12, 8, 2, 5, n_planted=4),
+            synth.random_matrix(300 + seed, 8, 12, 2, 5, n_planted=3)]
+    r = O.search(mats, synth.PAPER_WEIGHTS, 32, seed, 96, 16, 400, 64)
+    for mi, (m, lst, cost) in enumerate(zip(mats, r.lists, r.cost)):
+        cur, back = expand(m, lst)
+        assert np.array_equal(back, m.astype(np.int64))       # expansion reproduces E
+        assert cost_of(cur, len(lst)) == cost                 # Cost = n_f + A_naive(E_final)
+        # each substitution saved c - 1 >= 1: replay and count rows
+        c_sum, cur2 = 0, np.zeros((m.shape[0], m.shape[1] + len(lst)), dtype=np.int64)
+        cur2[:, :m.shape[1]] = m
+        for t, e in enumerate(lst):
+            i, j, s = O.unentry(e)
+            hit = (cur2[:, i] != 0) & (cur2[:, j] == s * cur2[:, i])
+            c = int(hit.sum())
+            assert c >= 2
+            c_sum += c - 1
+            k = m.shape[1] + t
+            cur2[hit, k] = cur2[hit, i]
+            cur2[hit, i] = 0
+            cur2[hit, j] = 0
+        assert cost == O.naive(m) - c_sum
+        # per-process records are valid too
+        assert (r.digests[mi]["best_cost"] >= cost).all()
+
+
+def test_digest_records_match_lists():
+    mats = [synth.random_matrix(7, 10, 7, 2, 5, n_planted=3)]
+    r = O.search(mats, synth.PAPER_WEIGHTS, 16, 5, 64, 8, 400, 48)
+    d = r.digests[0]
+    win = int(np.argmin(d["best_cost"]))
+    assert d["best_cost"][win] == r.cost[0] and d["best_len"][win] == r.length[0]
+    assert (d["substeps"] <= 64).all()
+
+
+# ---------------------------------------------------------------- step clock
+def test_step_clock_closed_form_greedy():
+    mat, *_ = _example()
+    # g only, no sharing: every run is (0,1,-), (2,3,-) and ends after its
+    # second step, so B steps give ceil(B/2) runs and B substitutions.
+    for B in (1, 2, 7, 10):
+        r = O.search([mat], (0, 0, 0, 0, 0, 1), 1, 0, B, 1000, 0, 16)
+        d = r.digests[0][0]
+        assert d["runs"] == (B + 1) // 2 and d["substeps"] == B
+        assert d["best_cost"] == (6 if B >= 2 else 7)
+
+
+def test_sharing_replay_closed_form():
+    mat, *_ = _example()
+    # interval 4, permille 1000: the snapshot after step 3 is the g run
+    # (L = 2, K = floor(3*2/4) = 1), so every later run replays k = 1
+    # substitution and finishes in one step.  12 steps: 2 + 8 runs.
+    r = O.search([mat], (0, 0, 0, 0, 0, 1), 1, 0, 12, 4, 1000, 16)
+    d = r.digests[0][0]
+    assert d["runs"] == 10 and d["substeps"] == 12 and r.cost == [6]
+    # permille 0: no replays, 6 runs
+    r0 = O.search([mat], (0, 0, 0, 0, 0, 1), 1, 0, 12, 4, 0, 16)
+    assert r0.digests[0][0]["runs"] == 6
+
+
+def test_column_cap_ends_runs():
+    mat = synth.random_matrix(11, 16, 6, 4, 6, n_planted=6, frac=(0.4, 0.6))
+    # cap = n_x + 2: at most two substitutions per run
+    r = O.search([mat], synth.PAPER_WEIGHTS, 8, 1, 40, 1000, 0, 8)
+    assert max(r.length) <= 2
+    assert (r.digests[0]["best_len"] <= 2).all()
+
+
+def test_permille_zero_is_independent_of_interval():
+    mats = [synth.random_matrix(21, 12, 8, 2, 5, n_planted=3)]
+    a = O.search(mats, synth.PAPER_WEIGHTS, 16, 9, 80, 8, 0, 64)
+    b = O.search(mats, synth.PAPER_WEIGHTS, 16, 9, 80, 1000, 0, 64)
+    assert np.array_equal(a.digests["traj_hash"], b.digests["traj_hash"])
+
+
+def test_thread_count_does_not_change_results():
+    s = synth.config2(n_proc=64, budget=96)
+    a = O.search_obj(s, n_threads=1)
+    b = O.search_obj(s, n_threads=7)
+    assert np.array_equal(a.digests, b.digests) and a.lists == b.lists
+
+
+def test_subset_matches_full_run_before_first_boundary():
+    s = synth.config2(n_proc=64, budget=32)
+    full = O.search_obj(s)
+    sub = [0, 5, 17, 63]
+    part = O.search_obj(s, subset=sub)
+    for mi in range(3):
+        assert np.array_equal(full.digests[mi][sub], part.digests[mi][sub])
+
+
+def test_first_run_of_process_zero_is_greedy():
+    mat = synth.random_matrix(31, 14, 8, 2, 5, n_planted=4)
+    g = O.search([mat], (0, 0, 0, 0, 0, 1), 1, 0, 6, 1000, 0, 64)
+    mixed = O.search([mat], synth.GI_ONLY, 1, 0, 6, 1000, 0, 64)
+    # process 0 starts with g whatever the weights
+    assert g.digests[0][0]["traj_hash"] == mixed.digests[0][0]["traj_hash"]
+
+
+def test_invalid_arguments_rejected():
+    mat = np.array([[1, 1], [1, 0]], np.int8)
+    with pytest.raises(ValueError):
+        O.search([np.array([[2, 1]], np.int8)], synth.PAPER_WEIGHTS, 1, 0, 1, 1, 0, 8)
+    with pytest.raises(ValueError):
+        O.search([np.array([[0, 0]], np.int8)], synth.PAPER_WEIGHTS, 1, 0, 1, 1, 0, 8)
+    with pytest.raises(ValueError):
+        O.search([mat], (0,) * 6, 1, 0, 1, 1, 0, 8)
+    with pytest.raises(ValueError):
+        O.search([mat], synth.PAPER_WEIGHTS, 1, 0, 1, 1, 0, 2)  # cols >= cap
+
+
+# ---------------------------------------------------------------- strategies
+def test_greedy_takes_first_maximum():
+    assert O.select_basic(O.G, [2, 5, 3, 5, 1 + 1], []) == 1
+
+
+def test_ga_uniform_over_ties():
+    counts = [3, 7, 2, 7, 7, 5, 7]
+    ties = [1, 3, 4, 6]
+    u = np.random.default_rng(0).integers(0, 2**32, 200000, dtype=np.uint64)
+    hist = np.zeros(len(counts))
+    for x in u[:40000]:
+        hist[O.select_basic(O.GA, counts, [int(x)])] += 1
+    assert set(np.nonzero(hist)[0]) == set(ties)
+    exp = 40000 / 4
+    chi2 = sum((hist[t] - exp) ** 2 / exp for t in ties)
+    assert chi2 < 16.3  # 3 dof, p = 0.001
+    # exact map: index (u * n_ties) >> 32 among ties in canonical order
+    assert O.select_basic(O.GA, counts, [0]) == 1
+    assert O.select_basic(O.GA, counts, [2**32 - 1]) == 6
+    assert O.select_basic(O.GA, counts, [2**31]) == 4
+
+
+def test_wr_proportional_to_profit():
+    counts = [2, 5, 3, 2, 9]
+    w = np.array(counts) - 1
+    hist = np.zeros(len(counts))
+    n = 40000
+    for x in np.random.default_rng(1).integers(0, 2**32, n, dtype=np.uint64):
+        hist[O.select_basic(O.WR, counts, [int(x)])] += 1
+    exp = n * w / w.sum()
+    chi2 = float(((hist - exp) ** 2 / exp).sum())
+    assert chi2 < 18.5  # 4 dof, p = 0.001
+    assert O.select_basic(O.WR, counts, [0]) == 0
+    assert O.select_basic(O.WR, counts, [2**32 - 1]) == 4
+
+
+def test_gr_mixes_ga_and_wr():
+    counts = [2, 4, 4, 3]
+    # coin below 3*2^30 -> ga on (u[1]); else wr on u[1]
+    assert O.select_basic(O.GR, counts, [0, 0]) == 1
+    assert O.select_basic(O.GR, counts, [3 * 2**30 - 1, 2**32 - 1]) == 2
+    assert O.select_basic(O.GR, counts, [3 * 2**30, 0]) == 0
+    assert O.select_basic(O.GR, counts, [2**32 - 1, 2**32 - 1]) == 3
+
+
+# ---------------------------------------------------------------- gi
+def _gi_cases():
+    a = b = None
+    cases = []
+    for ln in _lines("gi_example.txt"):
+        f = ln.split()
+        if f[0] == "a":
+            a = int(f[1])
+        elif f[0] == "b":
+            b = int(f[1])
+        elif f[0] == "case":
+            cases.append([f[1], None, None])
+        elif f[0] == "scores":
+            cases[-1][1] = [int(x) for x in f[1:]]
+        elif f[0] == "argmax":
+            cases[-1][2] = int(f[1])
+    return a, b, cases
+
+
+def test_gi_hand_derived_scores():
+    mat, *_ = _example()
+    keys, counts = zip(*O.pairs(mat))
+    a, b, cases = _gi_cases()
+    m = len(keys)
+    for name, scores, arg in cases:
+        if name == "zeros":
+            coins = np.zeros((m, m), np.uint8)
+        elif name == "ones":
+            coins = np.ones((m, m), np.uint8)
+        else:
+            coins = np.zeros((m, m), np.uint8)
+            coins[2, :] = 1
+        best, sc = O.gi_scores(keys, counts, a, b, coins)
+        assert sc == scores, name
+        assert best == arg, name
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_gi_with_alpha_zero_is_greedy(seed):
+    mat = synth.random_matrix(400 + seed, 20, 9, 2, 5, n_planted=6)
+    keys, counts = zip(*O.pairs(mat))
+    m = len(keys)
+    coins = np.random.default_rng(seed).integers(0, 2, (m, m)).astype(np.uint8)
+    best, _ = O.gi_scores(keys, counts, 0, 50000, coins)
+    assert best == O.select_basic(O.G, counts, [])
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_gi_score_structure(seed):
+    """Disjoint candidates add alpha (c_q - 1) regardless of coins; a
+    candidate sharing a variable adds alpha beta (c_q - 1) exactly when its
+    coin is 1."""
+    mat = synth.random_matrix(500 + seed, 18, 8, 2, 5, n_planted=5)
+    keys, counts = zip(*O.pairs(mat))
+    m = len(keys)
+    a, b = 12345, 40000
+    base = np.zeros((m, m), np.uint8)
+    _, s0 = O.gi_scores(keys, counts, a, b, base)
+    rng = np.random.default_rng(seed)
+    for _ in range(5):
+        p, q = rng.integers(0, m, 2)
+        if p == q:
+            continue
+        flip = base.copy()
+        flip[p, q] = 1
+        _, s1 = O.gi_scores(keys, counts, a, b, flip)
+        ip, jp, _ = O.unkey(keys[p])
+        iq, jq, _ = O.unkey(keys[q])
+        shares = len({ip, jp} & {iq, jq}) > 0
+        delta = s1[p] - s0[p]
+        assert delta == (a * b * (counts[q] - 1) if shares else 0)
+        assert [x for t, x in enumerate(s1) if t != p] == [x for t, x in enumerate(s0) if t != p]
+    # disjoint part: D_p = T - (c_p - 1) - sum over intersecting
+    T = sum(c - 1 for c in counts)
+    for p in range(m):
+        ip, jp, _ = O.unkey(keys[p])
+        inter = sum(counts[q] - 1 for q in range(m)
+                    if q != p and ({ip, jp} & set(O.unkey(keys[q])[:2])))
+        d = T - (counts[p] - 1) - inter
+        assert s0[p] == ((counts[p] - 1) << 32) + a * (d << 16)
