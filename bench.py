@@ -1,0 +1,291 @@
+"""Benchmark: CSE process-steps/s of the GB300 library on a synthetic
+(3,3,3:23)-shaped scheme (E_U, E_V 23 x 9, E_W 9 x 23; 4096 processes per
+matrix, mixed strategies, sharing every 32 steps, 1024 steps).
+
+One benchmark step = one complete search (cse_search) over that workload.
+`value` is timed on the device with CUDA events, inputs resident in HBM;
+`e2e` times the public C-ABI sequence a user runs (load from host buffers,
+search, fetch results to the host).  `--impl reference` times the CPU oracle
+on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "CSE process-steps/s & best additions @ fixed budget vs oracle; p50/p99 latency"
+UNIT = "process-steps/s"
+SM_COUNT_NOMINAL = 152
+LANES_PER_SM = 128  # 4 schedulers x 32 lanes: one warp instruction per scheduler per clock
+
+
+def workload(name: str):
+    from paper_2512_13365_gb300 import synth
+    if name == "cfg1":
+        return synth.config1()
+    if name == "cfg2":
+        return synth.config2()
+    raise SystemExit(f"unknown workload {name}")
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, out_path: str, index: int):
+        self.path = out_path
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(out_path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in open(self.path):
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def flush_l2(buf):
+    buf.zero_()
+
+
+def run_ours(args):
+    import torch
+    from paper_2512_13365_gb300 import cse
+
+    rank, world, local = dist_env()
+    if world > 1:
+        torch.cuda.set_device(local)
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    s = workload(args.workload)
+    s.seed = s.seed + rank  # weak scaling: each rank searches its own seed, no data-path collective
+    stream = torch.cuda.Stream(device=dev)
+    scheme = cse.Scheme(s.mats)
+    l2 = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2
+
+    def one():
+        return cse.search(scheme, s.weights, s.n_proc, s.seed, s.budget, s.interval, s.permille, s.cap,
+                          stream=stream, procs_per_cta=args.ppc)
+
+    for _ in range(args.warmup):
+        r = one()
+        r.fetch(0)
+        r.free()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = Clocks(os.path.join(args.out, f"clocks_rank{rank}.csv"), local)
+    evs = []
+    results = []
+    t_wall = time.perf_counter()
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush_l2(l2)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        r = one()
+        b.record(stream)
+        evs.append((a, b))
+        results.append(r)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    round_ms, n_rounds, ops_total = [], 0, 0
+    for r in results:
+        rm, tm, nr = r.timing()
+        round_ms.append(rm)
+        n_rounds = nr
+        steps, sub, ops = r.counters()
+        ops_total = ops
+    total = results[-1].total
+    costs = results[-1].costs
+    for r in results:
+        r.free()
+    ms = statistics.mean(step_ms)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    psteps = s.process_steps()
+    value = psteps * world / (ms / 1000.0)
+
+    # end to end through the public API: host buffers in, results to the host
+    e2e_ms = []
+    h2d = sum(m.nbytes for m in s.mats)
+    d2h = 0
+    for it in range(max(1, min(args.steps, 3))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sc = cse.Scheme(s.mats)
+        r = cse.search(sc, s.weights, s.n_proc, s.seed, s.budget, s.interval, s.permille, s.cap, stream=stream,
+                       procs_per_cta=args.ppc)
+        lists = [r.fetch(k) for k in range(len(s.mats))]
+        e2e_ms.append((time.perf_counter() - t0) * 1000.0)
+        d2h = sum(4 * len(l) + 16 for l, _, _ in lists)
+        r.free()
+        sc.free()
+    e2e_value = psteps * world / (statistics.mean(e2e_ms) / 1000.0)
+
+    # roofline of the dominant kernel (the round kernel)
+    pk = peaks()
+    props = torch.cuda.get_device_properties(dev)
+    sm_mhz = float(pk.get("sm_max_mhz", 2070.0))
+    peak_ops = props.multi_processor_count * LANES_PER_SM * sm_mhz * 1e6 / 1e12  # T int-ops/s
+    avg_round_ms = statistics.mean(round_ms) / n_rounds
+    ops_per_launch = ops_total / n_rounds
+    achieved = ops_per_launch / (avg_round_ms / 1000.0) / 1e12
+    launches_per_search = 1 + n_rounds * 2
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": s.name, "matrices": [list(m.shape) for m in s.mats], "n_processes": s.n_proc,
+                   "step_budget": s.budget, "share_interval": s.interval, "share_permille": s.permille,
+                   "col_cap": s.cap, "strategy_weights_gi_ga_gr_wr_mix_g": list(s.weights),
+                   "process_steps_per_step": psteps, "l2": "flushed (256 MB write) between timed steps",
+                   "parallelism": f"{world} independent searches (one per GPU)"},
+        "best_additions": total, "best_additions_per_matrix": costs,
+        "wall_s": wall,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "ms_per_step": statistics.mean(e2e_ms)},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "Tops/s",
+                     "frac": achieved / peak_ops, "traffic": None,
+                     "kernel": "round_kernel<1>", "alg_ops_per_launch": ops_per_launch,
+                     "avg_launch_ms": avg_round_ms,
+                     "peak_source": f"{props.multi_processor_count} SMs x {LANES_PER_SM} lanes x {sm_mhz:.0f} MHz"},
+        "clocks": clk,
+        "gpu_launches": launches_per_search * args.steps,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(s, args.cpu_budget)
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line))
+
+
+def cpu_baseline(s, budget):
+    """The oracle, as it stands, on a bounded sample of the same workload:
+    all processes, the first `budget` steps, on every host core."""
+    from oracle import oracle as O
+    import copy
+    cores = len(os.sched_getaffinity(0))
+    smp = copy.copy(s)
+    smp.budget = budget
+    t0 = time.perf_counter()
+    O.search_obj(smp, n_threads=cores, digests=False)
+    dt = time.perf_counter() - t0
+    return {"value": smp.process_steps() / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{s.name}: all {s.n_proc} processes x {len(s.mats)} matrices, first {budget} of "
+                      f"{s.budget} steps ({smp.process_steps()} process-steps, {dt:.1f} s)"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    s = workload(args.workload)
+    cores = len(os.sched_getaffinity(0))
+    import copy
+    smp = copy.copy(s)
+    smp.budget = args.cpu_budget
+    for _ in range(args.warmup):
+        w = copy.copy(smp)
+        w.budget = min(8, smp.budget)
+        O.search_obj(w, n_threads=cores, digests=False)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        O.search_obj(smp, n_threads=cores, digests=False)
+        times.append(time.perf_counter() - t0)
+    ms = statistics.mean(times) * 1000.0
+    v = smp.process_steps() / (ms / 1000.0)
+    sample = (f"{s.name}: all {s.n_proc} processes x {len(s.mats)} matrices, first {smp.budget} of {s.budget} "
+              f"steps per benchmark step")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int32", "data": "synthetic",
+        "config": {"workload": s.name, "n_processes": s.n_proc, "step_budget": s.budget},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="cfg2")
+    ap.add_argument("--ppc", type=int, default=0, help="processes per CTA (0 = library default)")
+    ap.add_argument("--cpu-budget", type=int, default=128, help="steps of the oracle sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--out", default=os.path.join(ROOT, "gpurun_out"))
+    args = ap.parse_args()
+    os.makedirs(args.out, exist_ok=True)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

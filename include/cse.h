@@ -1,0 +1,170 @@
+/*
+ * cse.h -- C ABI of the GB300 library for parallel heuristic common
+ * subexpression elimination (CSE) on ternary linear forms.
+ *
+ * Method: "Parallel Heuristic Exploration for Additive Complexity Reduction
+ * in Fast Matrix Multiplication" (A. I. Perminov, arXiv 2512.13365).
+ *   - an expression set E is a ternary matrix: one row per expression e_i,
+ *     one column per variable x_j, entries alpha_ij in {-1, 0, 1}
+ *     (Section 3.2.1); a fast-matmul scheme (m,n,p:r) gives three such sets,
+ *     E_U = U (r x mn), E_V = V (r x np) and E_W = W^T (mp x r) (Section 3.2);
+ *   - A_naive(E) = sum_i (nnz_i - 1); Cost(E) = n_f + A_naive(E_final)
+ *     (Section 3.2.1);
+ *   - each of n_processes independent processes per matrix repeats
+ *     Algorithm 1: count canonical signed pairs (x_i + s x_j, i < j), select a
+ *     pair with c > 1 by its strategy (g, ga, wr, gr, gi, mix; Section 3.4),
+ *     introduce x_k = x_i + s x_j and rewrite every row containing the pair;
+ *   - processes share their best substitution prefixes (Section 3.5.2).
+ *
+ * All arithmetic is exact integer and every random draw is a Philox4x32-10
+ * value keyed by (seed, process, step, matrix, purpose), so a search's
+ * result is a pure function of (matrices, strategy mix, n_processes, seed,
+ * step_budget, share_interval, share_permille, col_cap): it does not depend
+ * on launch configuration or on other searches running at the same time.
+ *
+ * Conventions
+ *   - Matrices are int8, row-major, rows = expressions, cols = variables.
+ *   - Variables are 0-based; fresh variable t (0-based) is x_{cols + t}.
+ *   - A substitution entry is packed as  i | j << 10 | (s < 0) << 20  with
+ *     i < j: it defines x_{cols+t} = x_i + s * x_j.
+ *   - Every function returns CSE_OK (0) or an error code; on error
+ *     cse_last_error() returns a message for the calling thread.
+ *   - Handles are owned by the library until the matching *_free call.
+ *     Functions copy their host inputs; output buffers belong to the caller.
+ *   - There is no CPU fallback: without a CUDA device, calls that need one
+ *     return CSE_ECUDA.
+ */
+#ifndef CSE_GB300_H
+#define CSE_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    CSE_OK = 0,
+    CSE_EINVAL = 1,   /* invalid argument (non-ternary entry, zero row, sizes) */
+    CSE_ENOMEM = 2,   /* host or device allocation failed                      */
+    CSE_ECUDA = 3,    /* CUDA runtime error (including: no device)             */
+    CSE_ETIMEOUT = 4, /* a bounded wait expired                                */
+    CSE_EBUSY = 5,    /* server admission refused (no room), non-blocking      */
+    CSE_ESTATE = 6    /* internal consistency check failed on the device       */
+};
+
+/* Limits of this implementation. */
+#define CSE_MAX_ROWS 256   /* rows (expressions) per matrix                    */
+#define CSE_MAX_COLS 512   /* column capacity: original plus fresh variables   */
+#define CSE_MAX_MATS 16    /* matrices per scheme                              */
+
+typedef struct cse_scheme cse_scheme;
+typedef struct cse_result cse_result;
+typedef struct cse_server cse_server;
+
+/* Integer strategy weights (Section 3.5.1): the paper's gi 8, ga 4, gr 2,
+ * wr 1, mix 0.1, gp 0.01 become 800, 400, 200, 100, 10 and 1 here.  w_g is
+ * Greedy (the paper gives it weight 0 apart from process 0's first run).
+ * Greedy-Potential is not implemented: w_gp must be 0.  At least one weight
+ * must be nonzero; the sum must fit in 32 bits. */
+typedef struct {
+    uint32_t w_gi, w_ga, w_gr, w_wr, w_mix, w_g, w_gp;
+} cse_strategy_mix;
+
+/* Search options.  Fields that change results: share_interval,
+ * share_permille, col_cap.  The rest only change how the work is launched. */
+typedef struct {
+    uint32_t share_interval;  /* steps between sharing boundaries, >= 1      */
+    uint32_t share_permille;  /* share probability at a run start, 0..1000
+                                 (paper default 40%: 400)                     */
+    uint32_t col_cap;         /* column capacity, cols < col_cap <= 512       */
+    uint32_t patience_rounds; /* reserved, must be 0                         */
+    uint64_t max_spin;        /* reserved for bounded device waits (unused)  */
+    uint32_t procs_per_cta;   /* processes (warps) per CTA; 0 = automatic    */
+    uint32_t flags;           /* reserved, must be 0                         */
+} cse_opts;
+
+/* Default options: share_interval 32, share_permille 400, col_cap 128. */
+void cse_opts_default(cse_opts* opts);
+
+/* Loads n_mats expression sets.  mats[k] points to rows[k] x cols[k] int8
+ * entries (row-major) in host memory; every entry must be -1, 0 or 1 and
+ * every row must have at least one nonzero (A_naive counts nnz - 1 per row,
+ * Section 3.2.1).  1 <= rows <= 256, 1 <= cols < 512, n_mats <= 16.  The data
+ * is copied to the device (synchronously) and packed there into column
+ * bitsets.  On success *out owns the device copy. */
+int cse_scheme_load(const int8_t* const* mats, const int32_t* rows, const int32_t* cols,
+                    int32_t n_mats, cse_scheme** out);
+
+/* Loads a scheme (m,n,p:r) from its coefficient tensors (Section 3.1):
+ * U is r x (m*n), V is r x (n*p), W is r x (m*p), each row-major with the
+ * matrix entries in row-major order.  The three sets are E_U = U, E_V = V and
+ * E_W = W^T (Section 3.2).  The Brent equations are not checked. */
+int cse_scheme_load_uvw(int32_t m, int32_t n, int32_t p, int32_t r, const int8_t* U,
+                        const int8_t* V, const int8_t* W, cse_scheme** out);
+
+/* Shape of a loaded matrix. */
+int cse_scheme_shape(const cse_scheme* s, int32_t mat, int32_t* rows, int32_t* cols);
+
+/* Runs the search: n_processes processes per matrix, step_budget steps each
+ * (one step = at most one substitution, Algorithm 1), sharing every
+ * opts->share_interval steps (Section 3.5.2).  The work is enqueued on
+ * cuda_stream (a cudaStream_t, or NULL for the legacy default stream) and the
+ * call returns without waiting; *out owns the device state and results.
+ * n_processes <= 2^20, 0 <= step_budget < 2^31. */
+int cse_search(const cse_scheme* s, const cse_strategy_mix* mix, int32_t n_processes,
+               uint64_t seed, int64_t step_budget, const cse_opts* opts, void* cuda_stream,
+               cse_result** out);
+
+/* Waits for the search and copies the best substitution list of matrix mat:
+ * up to cap_entries packed entries into subst (may be NULL), its length into
+ * *n_subst, its Cost into *additions, and the sum of the best Cost over all
+ * matrices into *total_additions (any pointer may be NULL).  The best list
+ * is the lowest (Cost, process index) over all processes. */
+int cse_result_fetch(const cse_result* r, int32_t mat, int32_t* subst, int32_t cap_entries,
+                     int32_t* n_subst, int64_t* additions, int64_t* total_additions);
+
+/* Per-process record of a finished search (for checking and analysis). */
+typedef struct {
+    int64_t best_cost;  /* Cost of the process's best substitution list      */
+    int32_t best_len;   /* its length                                        */
+    int32_t runs;       /* runs started (Algorithm 1 executions)             */
+    uint64_t best_hash; /* FNV-1a over the 32-bit entries of the best list   */
+    uint64_t traj_hash; /* FNV-1a over the trajectory: (t, 0xA0000000 |
+                           strategy << 12 | replayed) at each run start and
+                           (t, entry) at each substitution step              */
+    int64_t ops;        /* algorithmic integer operations (see the counters
+                           of cse_result_counters)                           */
+    int64_t substeps;   /* steps that made a substitution                    */
+} cse_proc_record;
+
+/* Waits for the search and writes n_processes records of matrix mat. */
+int cse_result_procs(const cse_result* r, int32_t mat, cse_proc_record* out);
+
+/* Waits for the search and reports, summed over all matrices and processes:
+ * *process_steps = n_mats * n_processes * step_budget, *substeps = steps
+ * that made a substitution, *alg_ops = algorithmic integer operations.
+ * An algorithmic op count is defined per step from the method's quantities:
+ * 10 W for a rewrite plus 5 W per pair count that can change (candidates
+ * holding x_i or x_j, and x_k against every live column), W = ceil(rows/32);
+ * 2 m for a g/ga/wr/gr selection over m candidates; for gi, per candidate p
+ * 3 |I_p| + 8 plus 40 per 128-bit Philox block its coins use, I_p being the
+ * candidates sharing a variable with p. */
+int cse_result_counters(const cse_result* r, int64_t* process_steps, int64_t* substeps,
+                        int64_t* alg_ops);
+
+/* Device time of the search's kernels in milliseconds, from CUDA events
+ * recorded around the round kernels on the search's stream: *round_ms sums
+ * the step-engine launches, *total_ms spans the whole search. */
+int cse_result_timing(const cse_result* r, float* round_ms, float* total_ms, int32_t* n_rounds);
+
+void cse_result_free(cse_result* r);
+void cse_scheme_free(cse_scheme* s);
+
+/* Message of the last error on the calling thread ("" if none). */
+const char* cse_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -588,7 +588,6 @@ static void start_run(const search_t* S, int32_t mi, int32_t pi, int64_t t, work
             P->coef[(int64_t)r * S->cap + v] = M->orig[(int64_t)r * M->cols + v];
     P->ncols = M->cols;
     P->nf = 0;
-    P->ops += 5 * (int64_t)M->w32 * ((int64_t)M->cols * (M->cols - 1) / 2);
     recount(S, M, P, wk);
     int32_t k = 0;
     if (M->snap_cost < INT64_MAX) {

@@ -1,0 +1,227 @@
+"""Python binding of the GB300 CSE library (include/cse.h).
+
+Argument marshalling only: every step of the search runs in the library's
+CUDA kernels.  There is no CPU fallback: if the compiled library is missing
+the import of the binding fails loudly with the build command to run.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import List, Optional, Sequence, Tuple
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libcse_gb300.so")
+
+CSE_OK, CSE_EINVAL, CSE_ENOMEM, CSE_ECUDA, CSE_ETIMEOUT, CSE_EBUSY, CSE_ESTATE = range(7)
+
+
+class CseError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"cse error {code}: {msg}")
+        self.code = code
+
+
+class Mix(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint32) for n in ("w_gi", "w_ga", "w_gr", "w_wr", "w_mix", "w_g", "w_gp")]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("share_interval", ctypes.c_uint32), ("share_permille", ctypes.c_uint32),
+                ("col_cap", ctypes.c_uint32), ("patience_rounds", ctypes.c_uint32),
+                ("max_spin", ctypes.c_uint64), ("procs_per_cta", ctypes.c_uint32), ("flags", ctypes.c_uint32)]
+
+
+class ProcRecord(ctypes.Structure):
+    _fields_ = [("best_cost", ctypes.c_int64), ("best_len", ctypes.c_int32), ("runs", ctypes.c_int32),
+                ("best_hash", ctypes.c_uint64), ("traj_hash", ctypes.c_uint64), ("ops", ctypes.c_int64),
+                ("substeps", ctypes.c_int64)]
+
+
+PROC_DTYPE = np.dtype([("best_cost", "<i8"), ("best_len", "<i4"), ("runs", "<i4"), ("best_hash", "<u8"),
+                       ("traj_hash", "<u8"), ("ops", "<i8"), ("substeps", "<i8")])
+assert PROC_DTYPE.itemsize == ctypes.sizeof(ProcRecord)
+
+_lib = None
+
+# every symbol include/cse.h declares
+EXPORTS = ["cse_opts_default", "cse_scheme_load", "cse_scheme_load_uvw", "cse_scheme_shape", "cse_search",
+           "cse_result_fetch", "cse_result_procs", "cse_result_counters", "cse_result_timing",
+           "cse_result_free", "cse_scheme_free", "cse_last_error"]
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"CUDA library {LIB_PATH} is not built: run "
+                          "`python -c 'import __graft_entry__ as g; g.build()'`")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i32, i64, u64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64
+    pi32, pi64 = ctypes.POINTER(i32), ctypes.POINTER(i64)
+    L.cse_last_error.restype = ctypes.c_char_p
+    L.cse_opts_default.argtypes = [ctypes.POINTER(Opts)]
+    L.cse_opts_default.restype = None
+    L.cse_scheme_load.argtypes = [ctypes.POINTER(ctypes.POINTER(ctypes.c_int8)), pi32, pi32, i32,
+                                  ctypes.POINTER(vp)]
+    L.cse_scheme_load_uvw.argtypes = [i32, i32, i32, i32, vp, vp, vp, ctypes.POINTER(vp)]
+    L.cse_scheme_shape.argtypes = [vp, i32, pi32, pi32]
+    L.cse_search.argtypes = [vp, ctypes.POINTER(Mix), i32, u64, i64, ctypes.POINTER(Opts), vp,
+                             ctypes.POINTER(vp)]
+    L.cse_result_fetch.argtypes = [vp, i32, pi32, i32, pi32, pi64, pi64]
+    L.cse_result_procs.argtypes = [vp, i32, ctypes.POINTER(ProcRecord)]
+    L.cse_result_counters.argtypes = [vp, pi64, pi64, pi64]
+    L.cse_result_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float), pi32]
+    L.cse_result_free.argtypes = [vp]
+    L.cse_result_free.restype = None
+    L.cse_scheme_free.argtypes = [vp]
+    L.cse_scheme_free.restype = None
+    for n in EXPORTS:
+        if n not in ("cse_opts_default", "cse_result_free", "cse_scheme_free", "cse_last_error"):
+            getattr(L, n).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _check(rc: int):
+    if rc != CSE_OK:
+        raise CseError(rc, lib().cse_last_error().decode())
+
+
+def _stream_ptr(stream) -> Optional[int]:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)  # torch.cuda.Stream
+
+
+class Scheme:
+    """Expression sets loaded on the device (cse_scheme_load)."""
+
+    def __init__(self, mats: Sequence[np.ndarray]):
+        self.mats = [np.ascontiguousarray(m, dtype=np.int8) for m in mats]
+        n = len(self.mats)
+        ptrs = (ctypes.POINTER(ctypes.c_int8) * n)(*[m.ctypes.data_as(ctypes.POINTER(ctypes.c_int8))
+                                                       for m in self.mats])
+        rows = (ctypes.c_int32 * n)(*[m.shape[0] for m in self.mats])
+        cols = (ctypes.c_int32 * n)(*[m.shape[1] for m in self.mats])
+        h = ctypes.c_void_p()
+        _check(lib().cse_scheme_load(ptrs, rows, cols, n, ctypes.byref(h)))
+        self.handle = h
+
+    @classmethod
+    def from_uvw(cls, m: int, n: int, p: int, U: np.ndarray, V: np.ndarray, W: np.ndarray) -> "Scheme":
+        self = cls.__new__(cls)
+        U, V, W = (np.ascontiguousarray(x, dtype=np.int8) for x in (U, V, W))
+        r = U.shape[0]
+        h = ctypes.c_void_p()
+        _check(lib().cse_scheme_load_uvw(m, n, p, r, U.ctypes.data, V.ctypes.data, W.ctypes.data,
+                                         ctypes.byref(h)))
+        self.handle = h
+        self.mats = [U, V, np.ascontiguousarray(W.T)]
+        return self
+
+    def shape(self, k: int) -> Tuple[int, int]:
+        r, c = ctypes.c_int32(), ctypes.c_int32()
+        _check(lib().cse_scheme_shape(self.handle, k, ctypes.byref(r), ctypes.byref(c)))
+        return r.value, c.value
+
+    def free(self):
+        if getattr(self, "handle", None):
+            lib().cse_scheme_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Result:
+    """A running or finished search (cse_result)."""
+
+    def __init__(self, handle, n_mats: int, n_proc: int, cap: int):
+        self.handle = handle
+        self.n_mats, self.n_proc, self.cap = n_mats, n_proc, cap
+
+    def fetch(self, mat: int) -> Tuple[List[int], int, int]:
+        """(best substitution list of matrix mat, its Cost, total over matrices)."""
+        buf = (ctypes.c_int32 * self.cap)()
+        n, add, tot = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().cse_result_fetch(self.handle, mat, buf, self.cap, ctypes.byref(n), ctypes.byref(add),
+                                      ctypes.byref(tot)))
+        return [int(buf[x]) for x in range(n.value)], int(add.value), int(tot.value)
+
+    @property
+    def costs(self) -> List[int]:
+        return [self.fetch(k)[1] for k in range(self.n_mats)]
+
+    @property
+    def lists(self) -> List[List[int]]:
+        return [self.fetch(k)[0] for k in range(self.n_mats)]
+
+    @property
+    def total(self) -> int:
+        return self.fetch(0)[2]
+
+    def procs(self, mat: int) -> np.ndarray:
+        out = np.zeros(self.n_proc, dtype=PROC_DTYPE)
+        _check(lib().cse_result_procs(self.handle, mat, out.ctypes.data_as(ctypes.POINTER(ProcRecord))))
+        return out
+
+    def counters(self) -> Tuple[int, int, int]:
+        a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().cse_result_counters(self.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return a.value, b.value, c.value
+
+    def timing(self) -> Tuple[float, float, int]:
+        a, b, n = ctypes.c_float(), ctypes.c_float(), ctypes.c_int32()
+        _check(lib().cse_result_timing(self.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(n)))
+        return a.value, b.value, n.value
+
+    def free(self):
+        if getattr(self, "handle", None):
+            lib().cse_result_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def make_mix(weights) -> Mix:
+    w = list(weights) + [0] * (7 - len(weights))
+    return Mix(*[int(x) for x in w])
+
+
+def make_opts(interval: int = 32, permille: int = 400, cap: int = 128, procs_per_cta: int = 0) -> Opts:
+    o = Opts()
+    lib().cse_opts_default(ctypes.byref(o))
+    o.share_interval, o.share_permille, o.col_cap, o.procs_per_cta = interval, permille, cap, procs_per_cta
+    return o
+
+
+def search(scheme: Scheme, weights, n_proc: int, seed: int, budget: int, interval: int = 32,
+           permille: int = 400, cap: int = 128, stream=None, procs_per_cta: int = 0) -> Result:
+    """cse_search: enqueue the search and return its Result handle."""
+    mix = make_mix(weights)
+    opts = make_opts(interval, permille, cap, procs_per_cta)
+    h = ctypes.c_void_p()
+    _check(lib().cse_search(scheme.handle, ctypes.byref(mix), n_proc, seed, budget, ctypes.byref(opts),
+                            _stream_ptr(stream), ctypes.byref(h)))
+    return Result(h, len(scheme.mats), n_proc, cap)
+
+
+def search_obj(s, scheme: Optional[Scheme] = None, **kw) -> Result:
+    """Run a synth.Search description on the device."""
+    sc = scheme if scheme is not None else Scheme(s.mats)
+    r = search(sc, s.weights, s.n_proc, s.seed, s.budget, s.interval, s.permille, s.cap, **kw)
+    r._scheme = sc  # keep the device inputs alive while the search runs
+    return r

@@ -1,0 +1,84 @@
+// Internal declarations shared by the kernels and the C-ABI host code of the
+// GB300 CSE library.  Not part of the public interface (include/cse.h).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace cse {
+
+// Strategy indices, in the order of the weights of cse_strategy_mix.
+enum Strategy : int { ST_GI = 0, ST_GA = 1, ST_GR = 2, ST_WR = 3, ST_MIX = 4, ST_G = 5, ST_N = 6 };
+
+// Purposes of the Philox draws (third counter word, bits 20..23).
+enum Purpose : uint32_t {
+    PU_STRAT = 0, PU_ALPHA = 1, PU_BETA = 2, PU_SHARE = 3, PU_SHAREK = 4,
+    PU_MIX = 5, PU_GA = 6, PU_GR = 7, PU_WR = 8, PU_GI = 9
+};
+
+// Per-process state header, in 32-bit words at the start of the process's
+// state region in global memory.
+enum Hdr : int {
+    H_NCOLS = 0, H_NF, H_M, H_COST, H_STRAT, H_A, H_B, H_ENDED, H_RUNS, H_SUBSTEPS,
+    H_BEST_COST, H_BEST_LEN, H_TRAJ_LO, H_TRAJ_HI, H_OPS_LO, H_OPS_HI, H_WORDS = 16
+};
+
+constexpr int kMaxW = 8;          // 32-bit words per column (256 rows)
+constexpr int kMaxCap = 512;      // column capacity
+constexpr uint64_t kFnv0 = 0xCBF29CE484222325ull;
+
+// One matrix of one search, as the kernels see it.
+struct DevMat {
+    const uint2* pn0;        // original columns [nx][W]: x = rows with +1, y = rows with -1
+    const uint32_t* cand0;   // initial candidate list, canonical order
+    const int32_t* meta0;    // [0] A_naive of the input, [1] initial candidate count
+    int32_t rows, nx, W, cap, mmax;
+    int32_t mat_index;       // index of the matrix within its search (Philox counter)
+    int32_t n_proc;
+    int32_t search;          // index into the DevSearch array
+    int32_t unit_base;       // first work unit of this matrix in its launch
+    int32_t state_words;     // 32-bit words per process state region
+    uint32_t* state;         // [n_proc][state_words]
+    int32_t* best_list;      // [n_proc][cap]
+    int32_t* snap;           // [cap]: published best prefix source
+    int32_t* snap_meta;      // [0] cost (INT32_MAX = none), [1] length
+    unsigned long long* round_min;  // (best cost << 32 | process), min over the round
+    int32_t* result;         // [cap] best list of the search
+    int32_t* result_meta;    // [0] cost, [1] length
+    unsigned long long* counters;   // [0] algorithmic ops, [1] substitution steps
+};
+
+struct DevSearch {
+    uint64_t seed;
+    uint32_t w[ST_N];
+    uint32_t wsum;
+    int32_t budget, interval;
+    uint64_t share_thr;      // draw < share_thr => copy a prefix of the snapshot
+    int32_t* clock;          // first step of the next round
+    int32_t mat_begin, n_mats;
+    int32_t* status;         // nonzero: a device-side consistency check failed
+};
+
+// Shared-memory carve-up of one process (one warp), in bytes.
+struct WarpLayout {
+    int32_t off_pn, off_cand, off_f, off_ladj, off_hs, off_he, off_loff, off_lcur;
+    int32_t per_warp;
+};
+
+WarpLayout make_layout(int W, int cap, int mmax);
+int state_words(int W, int cap, int mmax);
+
+// Launchers (cse_kernels.cu).  All enqueue on `stream` and return the
+// launch error, if any.
+cudaError_t launch_ingest(const int8_t* raw, int rows, int nx, int W, uint2* pn0, uint32_t* cand0,
+                          int32_t* meta0, int mmax, cudaStream_t stream);
+cudaError_t launch_init(const DevMat* mats, int n_mats, const DevSearch* searches, int n_searches,
+                        cudaStream_t stream);
+cudaError_t launch_round(int W, const DevMat* mats, int n_mats, const DevSearch* searches,
+                         int total_units, const WarpLayout& L, int procs_per_cta,
+                         cudaStream_t stream);
+cudaError_t launch_share(const DevMat* mats, const DevSearch* searches, int n_searches,
+                         cudaStream_t stream);
+int max_smem_per_block();
+
+}  // namespace cse

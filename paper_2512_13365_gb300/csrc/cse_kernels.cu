@@ -1,0 +1,837 @@
+// Step engine of the parallel heuristic CSE search on sm_103a.
+//
+// One warp runs one process (Section 3.5.1).  Its expression set lives in
+// shared memory as column bitsets: column v holds W 32-bit words of "rows
+// with alpha_rv = +1" and W words of "rows with alpha_rv = -1" (uint2 x / y).
+// Pair frequencies (Algorithm 1, Analysis) are AND + popc over those words:
+// for columns a, b with rows-present masks A = Pa|Na, B = Pb|Nb,
+//   c(a,b,-) = popc((Pa ^ Pb) & A & B),  c(a,b,+) = popc(A & B) - c(a,b,-).
+// The candidate set (canonical pairs with c >= 2) is kept as a list sorted by
+// key = hi << 11 | lo << 1 | (s < 0), i.e. by the larger index first.  A
+// substitution x_k = x_i + s x_j only changes pairs that contain x_i, x_j or
+// the new x_k, and x_k is the largest index so far, so after each step the
+// list is updated in place: candidates containing x_i or x_j are recounted
+// (a stable compaction drops those that fell below 2) and the pairs (u, k)
+// are appended in order.  No step recounts the whole matrix.
+//
+// Every random draw is Philox4x32-10 (Salmon et al., SC'11) with key = seed
+// and counter (process, t, matrix << 24 | purpose << 20 | extra_hi,
+// extra_lo); all lanes of a warp evaluate the same draw, so no shuffles are
+// needed to share it.
+
+#include <climits>
+#include <cstdint>
+
+#include "cse_internal.h"
+
+namespace cse {
+
+#define FULL_MASK 0xFFFFFFFFu
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Philox4x32-10: round (hi0,lo0) = M0*c0, (hi1,lo1) = M1*c2,
+// c' = (hi1 ^ c1 ^ k0, lo1, hi0 ^ c3 ^ k1, lo0); key += Weyl constants.
+__device__ __forceinline__ void philox(uint32_t& c0, uint32_t& c1, uint32_t& c2, uint32_t& c3,
+                                       uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; r++) {
+        if (r) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+        const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+        const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+    }
+}
+
+__device__ __forceinline__ uint32_t scale32(uint32_t u, uint32_t n) {
+    return (uint32_t)(((uint64_t)u * n) >> 32);
+}
+
+__device__ __forceinline__ uint64_t fnv(uint64_t h, uint32_t w) { return (h ^ w) * 0x100000001B3ull; }
+
+__device__ __forceinline__ int key_lo(uint32_t e) { return (int)((e >> 1) & 1023u); }
+__device__ __forceinline__ int key_hi(uint32_t e) { return (int)((e >> 11) & 1023u); }
+__device__ __forceinline__ int cand_c(uint32_t e) { return (int)(e >> 21); }
+__device__ __forceinline__ uint32_t make_cand(int lo, int hi, int neg, int c) {
+    return ((uint32_t)hi << 11) | ((uint32_t)lo << 1) | (uint32_t)neg | ((uint32_t)c << 21);
+}
+
+__device__ __forceinline__ int warp_incl_scan(int v, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(FULL_MASK, v, o);
+        if (lane >= o) v += y;
+    }
+    return v;
+}
+
+__device__ __forceinline__ long long warp_sum64(long long v) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(FULL_MASK, v, o);
+    return v;
+}
+
+// ---------------------------------------------------------------------------
+// Ingest (step a1): int8 rows -> column bitsets; initial candidate list.
+// One warp per matrix.
+// ---------------------------------------------------------------------------
+__global__ void ingest_kernel(const int8_t* __restrict__ raw, int rows, int nx, int W,
+                              uint2* __restrict__ pn0, uint32_t* __restrict__ cand0,
+                              int32_t* __restrict__ meta0, int mmax) {
+    const int lane = threadIdx.x & 31;
+    // columns
+    for (int x = lane; x < nx * W; x += 32) {
+        const int v = x / W, w = x % W;
+        uint32_t p = 0, n = 0;
+        for (int b = 0; b < 32; b++) {
+            const int r = w * 32 + b;
+            if (r >= rows) break;
+            const int8_t a = raw[(size_t)r * nx + v];
+            p |= (uint32_t)(a == 1) << b;
+            n |= (uint32_t)(a == -1) << b;
+        }
+        pn0[x] = make_uint2(p, n);
+    }
+    // naive additions: sum over rows of (nnz - 1)
+    int part = 0;
+    for (int r = lane; r < rows; r += 32) {
+        int nnz = 0;
+        for (int v = 0; v < nx; v++) nnz += raw[(size_t)r * nx + v] != 0;
+        part += nnz - 1;
+    }
+    const int naive = __reduce_add_sync(FULL_MASK, part);
+    __syncwarp();
+    // all pairs (u, v), u < v, in canonical order: v ascending, then u, '+' first
+    const uint32_t lt = lanemask_lt();
+    int m = 0;
+    for (int v = 1; v < nx; v++) {
+        for (int base = 0; base < v; base += 32) {
+            const int u = base + lane;
+            int cp = 0, cm = 0;
+            if (u < v) {
+                for (int w = 0; w < W; w++) {
+                    const uint2 A = pn0[u * W + w], B = pn0[v * W + w];
+                    const uint32_t bt = (A.x | A.y) & (B.x | B.y);
+                    const int ng = __popc((A.x ^ B.x) & bt);
+                    cm += ng;
+                    cp += __popc(bt) - ng;
+                }
+            }
+            const bool ep = cp >= 2, em = cm >= 2;
+            const uint32_t bp = __ballot_sync(FULL_MASK, ep), bm = __ballot_sync(FULL_MASK, em);
+            int pos = m + __popc(bp & lt) + __popc(bm & lt);
+            if (ep && pos < mmax) cand0[pos] = make_cand(u, v, 0, cp);
+            if (ep) pos++;
+            if (em && pos < mmax) cand0[pos] = make_cand(u, v, 1, cm);
+            m += __popc(bp) + __popc(bm);
+        }
+    }
+    if (lane == 0) {
+        meta0[0] = naive;
+        meta0[1] = m;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The per-process engine.
+// ---------------------------------------------------------------------------
+template <int W>
+struct Engine {
+    // shared memory of this warp
+    uint2* pn;
+    uint32_t* cand;
+    int32_t* F;
+    uint16_t* ladj;
+    uint16_t* hs;
+    uint16_t* he;
+    uint16_t* loff;
+    uint16_t* lcur;
+    // context
+    const DevMat* M;
+    const DevSearch* S;
+    int proc, lane, cap, mmax;
+    uint32_t lt;
+    // warp-uniform state
+    int ncols, nf, m, cost, strat, a, b, ended, runs, substeps, best_cost, best_len;
+    uint64_t traj;
+    long long ops;       // warp-uniform part of the op count
+    long long ops_lane;  // per-lane part (gi scoring), reduced at the end
+    int overflow;
+
+    __device__ __forceinline__ uint32_t draw(int t, uint32_t purpose) const {
+        uint32_t c0 = (uint32_t)proc, c1 = (uint32_t)t,
+                 c2 = ((uint32_t)M->mat_index & 0xFFu) << 24 | (purpose & 0xFu) << 20, c3 = 0;
+        philox(c0, c1, c2, c3, (uint32_t)S->seed, (uint32_t)(S->seed >> 32));
+        return c0;
+    }
+
+    // c(a, b, s) for columns a < b
+    __device__ __forceinline__ void counts(int a_, int b_, int& cp, int& cm) const {
+        int both = 0, ng = 0;
+#pragma unroll
+        for (int w = 0; w < W; w++) {
+            const uint2 A = pn[a_ * W + w], B = pn[b_ * W + w];
+            const uint32_t bt = (A.x | A.y) & (B.x | B.y);
+            both += __popc(bt);
+            ng += __popc((A.x ^ B.x) & bt);
+        }
+        cm = ng;
+        cp = both - ng;
+    }
+
+    // Substitution of (x_i + s x_j), i < j, by the fresh x_k, k = ncols
+    // (Section 3.2.1, Algorithm 1), with the candidate list update.
+    __device__ void subst(int i, int j, int neg) {
+        const int k = ncols;
+        int cpart = 0;
+        if (lane < W) {
+            uint2 A = pn[i * W + lane], B = pn[j * W + lane];
+            uint32_t rp, rn;
+            if (!neg) {  // rows with +x_i +x_j  /  -x_i -x_j
+                rp = A.x & B.x;
+                rn = A.y & B.y;
+                B.x &= ~rp;
+                B.y &= ~rn;
+            } else {     // rows with +x_i -x_j  /  -x_i +x_j
+                rp = A.x & B.y;
+                rn = A.y & B.x;
+                B.x &= ~rn;
+                B.y &= ~rp;
+            }
+            A.x &= ~rp;
+            A.y &= ~rn;
+            pn[i * W + lane] = A;
+            pn[j * W + lane] = B;
+            pn[k * W + lane] = make_uint2(rp, rn);
+            cpart = __popc(rp) + __popc(rn);
+        }
+        const int c = __reduce_add_sync(FULL_MASK, cpart);
+        __syncwarp();
+        // recount the candidates containing x_i or x_j; stable in-place compaction
+        int newm = 0, nij = 0;
+        for (int base = 0; base < m; base += 32) {
+            const int q = base + lane;
+            uint32_t e = 0;
+            bool keep = false, touch = false;
+            if (q < m) {
+                e = cand[q];
+                const int lo = key_lo(e), hi = key_hi(e);
+                touch = lo == i || lo == j || hi == i || hi == j;
+                keep = true;
+                if (touch) {
+                    int cp, cm;
+                    counts(lo, hi, cp, cm);
+                    const int cc = (e & 1u) ? cm : cp;
+                    keep = cc >= 2;
+                    e = (e & 0x1FFFFFu) | ((uint32_t)cc << 21);
+                }
+            }
+            const uint32_t kb = __ballot_sync(FULL_MASK, keep);
+            nij += __popc(__ballot_sync(FULL_MASK, touch));
+            __syncwarp();
+            if (keep) cand[newm + __popc(kb & lt)] = e;
+            newm += __popc(kb);
+        }
+        // the new pairs (u, k): x_k has the largest index, so they sort last
+        int nu = 0;
+        for (int base = 0; base < k; base += 32) {
+            const int u = base + lane;
+            int cp = 0, cm = 0;
+            bool live = false;
+            if (u < k) {
+                uint32_t sup = 0;
+                int both = 0, ng = 0;
+#pragma unroll
+                for (int w = 0; w < W; w++) {
+                    const uint2 A = pn[u * W + w], K = pn[k * W + w];
+                    sup |= A.x | A.y;
+                    const uint32_t bt = (A.x | A.y) & (K.x | K.y);
+                    both += __popc(bt);
+                    ng += __popc((A.x ^ K.x) & bt);
+                }
+                live = sup != 0;
+                cm = ng;
+                cp = both - ng;
+            }
+            nu += __popc(__ballot_sync(FULL_MASK, live));
+            const bool ep = cp >= 2, em = cm >= 2;
+            const uint32_t bp = __ballot_sync(FULL_MASK, ep), bm = __ballot_sync(FULL_MASK, em);
+            int pos = newm + __popc(bp & lt) + __popc(bm & lt);
+            if (ep) {
+                if (pos < mmax) cand[pos] = make_cand(u, k, 0, cp);
+                pos++;
+            }
+            if (em && pos < mmax) cand[pos] = make_cand(u, k, 1, cm);
+            newm += __popc(bp) + __popc(bm);
+        }
+        if (newm > mmax) {
+            overflow = 1;
+            newm = mmax;
+        }
+        if (lane == 0) F[nf] = (int32_t)((uint32_t)i | (uint32_t)j << 10 | (uint32_t)neg << 20);
+        nf++;
+        ncols++;
+        cost -= c - 1;
+        m = newm;
+        ops += 10LL * M->W + 5LL * M->W * (nij + nu);
+        __syncwarp();
+    }
+
+    // Closes the current run into the process's best record (strictly lower
+    // cost replaces).
+    __device__ void fold() {
+        if (cost < best_cost) {
+            int32_t* dst = M->best_list + (size_t)proc * cap;
+            for (int x = lane; x < nf; x += 32) dst[x] = F[x];
+            best_cost = cost;
+            best_len = nf;
+        }
+    }
+
+    // Run start at step t (Section 3.5.1-3.5.2): strategy, alpha, beta, fresh
+    // copy of the input, optional replay of a prefix of the snapshot.
+    __device__ void start_run(int t) {
+        if (t > 0) fold();
+        runs++;
+        if (proc == 0 && t == 0) {
+            strat = ST_G;
+        } else {
+            const uint32_t x = scale32(draw(t, PU_STRAT), S->wsum);
+            uint32_t acc = 0;
+            strat = ST_G;
+#pragma unroll
+            for (int s = 0; s < ST_N; s++) {
+                acc += S->w[s];
+                if (x < acc) {
+                    strat = s;
+                    break;
+                }
+            }
+        }
+        a = (int)scale32(draw(t, PU_ALPHA), 32769u);
+        b = 32768 + (int)scale32(draw(t, PU_BETA), 32769u);
+        const int nx = M->nx;
+        for (int x = lane; x < nx * W; x += 32) pn[x] = M->pn0[x];
+        const int m0 = M->meta0[1];
+        for (int x = lane; x < m0; x += 32) cand[x] = M->cand0[x];
+        m = m0 < mmax ? m0 : mmax;
+        ncols = nx;
+        nf = 0;
+        cost = M->meta0[0];
+        __syncwarp();
+        int k = 0;
+        const int scost = M->snap_meta[0];
+        if (scost != INT_MAX) {
+            if ((uint64_t)draw(t, PU_SHARE) < S->share_thr) {
+                const int L = M->snap_meta[1];
+                const int K = (3 * L) / 4;
+                if (K >= 1) k = 1 + (int)scale32(draw(t, PU_SHAREK), (uint32_t)K);
+            }
+        }
+        for (int e = 0; e < k; e++) {
+            const uint32_t ent = (uint32_t)M->snap[e];
+            subst((int)(ent & 1023u), (int)((ent >> 10) & 1023u), (int)((ent >> 20) & 1u));
+        }
+        ended = 0;
+        traj = fnv(fnv(traj, (uint32_t)t), 0xA0000000u | (uint32_t)strat << 12 | (uint32_t)k);
+    }
+
+    // Greedy: highest c, lowest key.
+    __device__ int sel_g() const {
+        uint32_t best = 0;
+        for (int q = lane; q < m; q += 32) {
+            const uint32_t v = (uint32_t)cand_c(cand[q]) << 16 | (uint32_t)(0xFFFF - q);
+            best = best > v ? best : v;
+        }
+        best = __reduce_max_sync(FULL_MASK, best);
+        return 0xFFFF - (int)(best & 0xFFFFu);
+    }
+
+    // Greedy-Alternative: uniform among the max-c ties, (u * n_ties) >> 32-th in order.
+    __device__ int sel_ga(uint32_t u) const {
+        int lmax = 0, lcnt = 0;
+        for (int q = lane; q < m; q += 32) {
+            const int c = cand_c(cand[q]);
+            if (c > lmax) {
+                lmax = c;
+                lcnt = 1;
+            } else if (c == lmax) {
+                lcnt++;
+            }
+        }
+        const int cmax = (int)__reduce_max_sync(FULL_MASK, (uint32_t)lmax);
+        const int nt = __reduce_add_sync(FULL_MASK, lmax == cmax ? lcnt : 0);
+        uint32_t want = scale32(u, (uint32_t)nt);
+        for (int base = 0; base < m; base += 32) {
+            const int q = base + lane;
+            const bool tie = q < m && cand_c(cand[q]) == cmax;
+            const uint32_t bt = __ballot_sync(FULL_MASK, tie);
+            const uint32_t n = (uint32_t)__popc(bt);
+            if (want < n) {
+                const uint32_t hit = __ballot_sync(FULL_MASK, tie && (uint32_t)__popc(bt & lt) == want);
+                return base + __ffs(hit) - 1;
+            }
+            want -= n;
+        }
+        return 0;
+    }
+
+    // Weighted-Random: first candidate whose running sum of (c - 1) exceeds
+    // (u * T) >> 32, T = sum (c - 1).
+    __device__ int sel_wr(uint32_t u) const {
+        int part = 0;
+        for (int q = lane; q < m; q += 32) part += cand_c(cand[q]) - 1;
+        const uint32_t total = (uint32_t)__reduce_add_sync(FULL_MASK, part);
+        const uint32_t x = scale32(u, total);
+        uint32_t acc = 0;
+        for (int base = 0; base < m; base += 32) {
+            const int q = base + lane;
+            const int w = q < m ? cand_c(cand[q]) - 1 : 0;
+            const int incl = warp_incl_scan(w, lane);
+            const uint32_t hit = __ballot_sync(FULL_MASK, q < m && acc + (uint32_t)incl > x);
+            if (hit) return base + __ffs(hit) - 1;
+            acc += (uint32_t)__shfl_sync(FULL_MASK, incl, 31);
+        }
+        return m - 1;
+    }
+
+    // Greedy-Intersections (Section 3.4.2), exact integer score
+    // S_p = (c_p - 1) 2^32 + a (2^16 D_p + b X_p); argmax, lowest key on ties.
+    __device__ int sel_gi(int t) {
+        int part = 0;
+        for (int q = lane; q < m; q += 32) part += cand_c(cand[q]) - 1;
+        const int T = __reduce_add_sync(FULL_MASK, part);
+        // adjacency: for each variable v, the candidates holding v in
+        // canonical order = [hi-block of v: contiguous in the list]
+        // followed by [candidates whose lo is v], gathered by a stable scatter.
+        for (int v = lane; v < ncols; v += 32) {
+            hs[v] = 0;
+            he[v] = 0;
+            lcur[v] = 0;
+        }
+        __syncwarp();
+        for (int base = 0; base < m; base += 32) {
+            const int q = base + lane;
+            const bool valid = q < m;
+            const uint32_t act = __ballot_sync(FULL_MASK, valid);
+            if (valid) {
+                const uint32_t e = cand[q];
+                const int hi = key_hi(e), lo = key_lo(e);
+                if (q == 0 || key_hi(cand[q - 1]) != hi) hs[hi] = (uint16_t)q;
+                if (q == m - 1 || key_hi(cand[q + 1]) != hi) he[hi] = (uint16_t)(q + 1);
+                const uint32_t peers = __match_any_sync(act, lo);
+                if ((peers & lt) == 0) lcur[lo] = (uint16_t)(lcur[lo] + __popc(peers));
+            }
+            __syncwarp();
+        }
+        int run = 0;
+        for (int base = 0; base < ncols; base += 32) {
+            const int v = base + lane;
+            const int cnt = v < ncols ? lcur[v] : 0;
+            const int incl = warp_incl_scan(cnt, lane);
+            if (v < ncols) {
+                loff[v] = (uint16_t)(run + incl - cnt);
+                lcur[v] = 0;
+            }
+            run += __shfl_sync(FULL_MASK, incl, 31);
+        }
+        __syncwarp();
+        for (int base = 0; base < m; base += 32) {
+            const int q = base + lane;
+            const bool valid = q < m;
+            const uint32_t act = __ballot_sync(FULL_MASK, valid);
+            uint32_t peers = 0;
+            int lo = 0;
+            if (valid) {
+                lo = key_lo(cand[q]);
+                peers = __match_any_sync(act, lo);
+                ladj[loff[lo] + lcur[lo] + __popc(peers & lt)] = (uint16_t)q;
+            }
+            __syncwarp();
+            if (valid && (peers & lt) == 0) lcur[lo] = (uint16_t)(lcur[lo] + __popc(peers));
+            __syncwarp();
+        }
+        // scoring: one candidate p per lane
+        const uint32_t k0 = (uint32_t)S->seed, k1 = (uint32_t)(S->seed >> 32);
+        const uint32_t c2base = ((uint32_t)M->mat_index & 0xFFu) << 24 | (PU_GI & 0xFu) << 20;
+        long long best_s = LLONG_MIN;
+        int best_q = -1;
+        for (int base = 0; base < m; base += 32) {
+            const int p = base + lane;
+            if (p < m) {
+                const uint32_t e = cand[p];
+                const int i = key_lo(e), j = key_hi(e), wp = cand_c(e) - 1;
+                const uint32_t key = e & 0x1FFFFFu;
+                uint32_t b0 = 0, b1 = 0, b2 = 0, b3 = 0;
+                int bidx = -1;
+                int inter = 0, X = 0, r0 = 0, r1 = 0;
+                auto coin = [&](int slot, int r) -> int {
+                    const int bi = r >> 6;
+                    if (bi != bidx) {
+                        b0 = (uint32_t)proc;
+                        b1 = (uint32_t)t;
+                        b2 = c2base | (uint32_t)bi;
+                        b3 = key;
+                        philox(b0, b1, b2, b3, k0, k1);
+                        bidx = bi;
+                    }
+                    const uint32_t word = slot == 0 ? ((r & 32) ? b1 : b0) : ((r & 32) ? b3 : b2);
+                    return (int)((word >> (r & 31)) & 1u);
+                };
+                // slot 0: candidates holding x_i (p itself excluded)
+                for (int x = hs[i]; x < he[i]; x++) {
+                    const int wq = cand_c(cand[x]) - 1;
+                    inter += wq;
+                    X += coin(0, r0++) ? wq : 0;
+                }
+                {
+                    const int o = loff[i], n = lcur[i];
+                    for (int x = o; x < o + n; x++) {
+                        const int q = ladj[x];
+                        if (q == p) continue;
+                        const int wq = cand_c(cand[q]) - 1;
+                        inter += wq;
+                        X += coin(0, r0++) ? wq : 0;
+                    }
+                }
+                // slot 1: candidates holding x_j but not x_i
+                for (int x = hs[j]; x < he[j]; x++) {
+                    const uint32_t eq = cand[x];
+                    if (key_lo(eq) == i) continue;
+                    const int wq = cand_c(eq) - 1;
+                    inter += wq;
+                    X += coin(1, r1++) ? wq : 0;
+                }
+                {
+                    const int o = loff[j], n = lcur[j];
+                    for (int x = o; x < o + n; x++) {
+                        const int wq = cand_c(cand[ladj[x]]) - 1;
+                        inter += wq;
+                        X += coin(1, r1++) ? wq : 0;
+                    }
+                }
+                const int D = T - wp - inter;
+                const long long s = ((long long)wp << 32) +
+                                    (long long)a * (((long long)D << 16) + (long long)b * (long long)X);
+                if (s > best_s) {
+                    best_s = s;
+                    best_q = p;
+                }
+                const int nb0 = (r0 + 63) >> 6, nb1 = (r1 + 63) >> 6;
+                ops_lane += 3LL * (r0 + r1) + 8 + 40LL * (nb0 > nb1 ? nb0 : nb1);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            const long long s2 = __shfl_xor_sync(FULL_MASK, best_s, o);
+            const int q2 = __shfl_xor_sync(FULL_MASK, best_q, o);
+            if (s2 > best_s || (s2 == best_s && (unsigned)q2 < (unsigned)best_q)) {
+                best_s = s2;
+                best_q = q2;
+            }
+        }
+        return best_q;
+    }
+
+    __device__ int choose(int t) {
+        int s = strat;
+        if (s == ST_MIX) {
+            const uint32_t r = scale32(draw(t, PU_MIX), 15u);
+            s = r < 8 ? ST_GI : r < 12 ? ST_GA : r < 14 ? ST_GR : ST_WR;
+        }
+        if (s == ST_GR) s = draw(t, PU_GR) < 0xC0000000u ? ST_GA : ST_WR;
+        switch (s) {
+            case ST_G: ops += 2LL * m; return sel_g();
+            case ST_GA: ops += 2LL * m; return sel_ga(draw(t, PU_GA));
+            case ST_WR: ops += 2LL * m; return sel_wr(draw(t, PU_WR));
+            default: return sel_gi(t);
+        }
+    }
+
+    // One step of the step clock (Algorithm 1 iteration).
+    __device__ void step(int t) {
+        if (t == 0 || ended) start_run(t);
+        if (m == 0 || ncols >= cap) {
+            ended = 1;
+            return;
+        }
+        const int sel = choose(t);
+        const uint32_t e = cand[sel];
+        __syncwarp();
+        subst(key_lo(e), key_hi(e), (int)(e & 1u));
+        substeps++;
+        traj = fnv(fnv(traj, (uint32_t)t), (uint32_t)F[nf - 1]);
+        if (m == 0 || ncols >= cap) ended = 1;
+    }
+};
+
+template <int W>
+__global__ void __launch_bounds__(256) round_kernel(const DevMat* __restrict__ mats, int n_mats,
+                                                    const DevSearch* __restrict__ searches,
+                                                    int total_units, WarpLayout L) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int unit = blockIdx.x * (blockDim.x >> 5) + warp;
+    if (unit >= total_units) return;
+    int mi = 0;
+    while (mi + 1 < n_mats && mats[mi + 1].unit_base <= unit) mi++;
+    const DevMat* M = &mats[mi];
+    const DevSearch* S = &searches[M->search];
+    const int t0 = *S->clock;
+    if (t0 >= S->budget) return;
+    const int t1 = min(t0 + S->interval, S->budget);
+
+    unsigned char* base = smem + (size_t)warp * L.per_warp;
+    Engine<W> E;
+    E.pn = reinterpret_cast<uint2*>(base + L.off_pn);
+    E.cand = reinterpret_cast<uint32_t*>(base + L.off_cand);
+    E.F = reinterpret_cast<int32_t*>(base + L.off_f);
+    E.ladj = reinterpret_cast<uint16_t*>(base + L.off_ladj);
+    E.hs = reinterpret_cast<uint16_t*>(base + L.off_hs);
+    E.he = reinterpret_cast<uint16_t*>(base + L.off_he);
+    E.loff = reinterpret_cast<uint16_t*>(base + L.off_loff);
+    E.lcur = reinterpret_cast<uint16_t*>(base + L.off_lcur);
+    E.M = M;
+    E.S = S;
+    E.proc = unit - M->unit_base;
+    E.lane = lane;
+    E.cap = M->cap;
+    E.mmax = M->mmax;
+    E.lt = lanemask_lt();
+    E.ops_lane = 0;
+    E.overflow = 0;
+
+    uint32_t* st = M->state + (size_t)E.proc * M->state_words;
+    long long ops_before;
+    int sub_before;
+    if (t0 == 0) {
+        E.ncols = M->nx;
+        E.nf = 0;
+        E.m = 0;
+        E.cost = M->meta0[0];
+        E.strat = ST_G;
+        E.a = 0;
+        E.b = 0;
+        E.ended = 1;
+        E.runs = 0;
+        E.substeps = 0;
+        E.best_cost = M->meta0[0];
+        E.best_len = 0;
+        E.traj = kFnv0;
+        E.ops = 0;
+    } else {
+        E.ncols = (int)st[H_NCOLS];
+        E.nf = (int)st[H_NF];
+        E.m = (int)st[H_M];
+        E.cost = (int)st[H_COST];
+        E.strat = (int)st[H_STRAT];
+        E.a = (int)st[H_A];
+        E.b = (int)st[H_B];
+        E.ended = (int)st[H_ENDED];
+        E.runs = (int)st[H_RUNS];
+        E.substeps = (int)st[H_SUBSTEPS];
+        E.best_cost = (int)st[H_BEST_COST];
+        E.best_len = (int)st[H_BEST_LEN];
+        E.traj = (uint64_t)st[H_TRAJ_LO] | (uint64_t)st[H_TRAJ_HI] << 32;
+        E.ops = (long long)((uint64_t)st[H_OPS_LO] | (uint64_t)st[H_OPS_HI] << 32);
+        const uint2* spn = reinterpret_cast<const uint2*>(st + H_WORDS);
+        for (int x = lane; x < E.ncols * W; x += 32) E.pn[x] = spn[x];
+        const uint32_t* sc = st + H_WORDS + 2 * M->cap * W;
+        for (int x = lane; x < E.m; x += 32) E.cand[x] = sc[x];
+        const int32_t* sf = reinterpret_cast<const int32_t*>(sc + M->mmax);
+        for (int x = lane; x < E.nf; x += 32) E.F[x] = sf[x];
+    }
+    ops_before = E.ops;
+    sub_before = E.substeps;
+    __syncwarp();
+
+    for (int t = t0; t < t1; t++) E.step(t);
+    E.fold();
+
+    E.ops += warp_sum64(E.ops_lane);
+    if (lane == 0) {
+        atomicMin(M->round_min, (unsigned long long)(uint32_t)E.best_cost << 32 | (uint32_t)E.proc);
+        atomicAdd(&M->counters[0], (unsigned long long)(E.ops - ops_before));
+        atomicAdd(&M->counters[1], (unsigned long long)(E.substeps - sub_before));
+        if (E.overflow) atomicExch(S->status, 1);
+        st[H_NCOLS] = (uint32_t)E.ncols;
+        st[H_NF] = (uint32_t)E.nf;
+        st[H_M] = (uint32_t)E.m;
+        st[H_COST] = (uint32_t)E.cost;
+        st[H_STRAT] = (uint32_t)E.strat;
+        st[H_A] = (uint32_t)E.a;
+        st[H_B] = (uint32_t)E.b;
+        st[H_ENDED] = (uint32_t)E.ended;
+        st[H_RUNS] = (uint32_t)E.runs;
+        st[H_SUBSTEPS] = (uint32_t)E.substeps;
+        st[H_BEST_COST] = (uint32_t)E.best_cost;
+        st[H_BEST_LEN] = (uint32_t)E.best_len;
+        st[H_TRAJ_LO] = (uint32_t)E.traj;
+        st[H_TRAJ_HI] = (uint32_t)(E.traj >> 32);
+        st[H_OPS_LO] = (uint32_t)(uint64_t)E.ops;
+        st[H_OPS_HI] = (uint32_t)((uint64_t)E.ops >> 32);
+    }
+    if (t1 < S->budget) {  // the state is needed by the next round
+        uint2* spn = reinterpret_cast<uint2*>(st + H_WORDS);
+        for (int x = lane; x < E.ncols * W; x += 32) spn[x] = E.pn[x];
+        uint32_t* sc = st + H_WORDS + 2 * M->cap * W;
+        for (int x = lane; x < E.m; x += 32) sc[x] = E.cand[x];
+        int32_t* sf = reinterpret_cast<int32_t*>(sc + M->mmax);
+        for (int x = lane; x < E.nf; x += 32) sf[x] = E.F[x];
+    }
+}
+
+// Sharing boundary (Section 3.5.2) and result publication.  One CTA per
+// search, one warp per matrix.
+__global__ void share_kernel(const DevMat* __restrict__ mats, const DevSearch* __restrict__ searches) {
+    const DevSearch* S = &searches[blockIdx.x];
+    const int t0 = *S->clock;
+    if (t0 >= S->budget) return;
+    const int t1 = min(t0 + S->interval, S->budget);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int k = warp; k < S->n_mats; k += nw) {
+        const DevMat* M = &mats[S->mat_begin + k];
+        const unsigned long long key = *M->round_min;
+        if (key == ~0ull) continue;  // no process reported (cannot happen when t0 < budget)
+        const int cost = (int)(key >> 32), win = (int)(key & 0xFFFFFFFFu);
+        const int len = (int)M->state[(size_t)win * M->state_words + H_BEST_LEN];
+        const int32_t* src = M->best_list + (size_t)win * M->cap;
+        if (t1 % S->interval == 0 && cost < M->snap_meta[0]) {
+            for (int x = lane; x < len; x += 32) M->snap[x] = src[x];
+            __syncwarp();
+            if (lane == 0) {
+                M->snap_meta[0] = cost;
+                M->snap_meta[1] = len;
+            }
+        }
+        if (t1 == S->budget) {
+            for (int x = lane; x < len; x += 32) M->result[x] = src[x];
+            if (lane == 0) {
+                M->result_meta[0] = cost;
+                M->result_meta[1] = len;
+            }
+        }
+        __syncwarp();
+        if (lane == 0) *M->round_min = ~0ull;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *S->clock = t1;
+}
+
+__global__ void init_kernel(const DevMat* __restrict__ mats, int n_mats,
+                            const DevSearch* __restrict__ searches, int n_searches) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x < n_mats) {
+        const DevMat* M = &mats[x];
+        *M->round_min = ~0ull;
+        M->snap_meta[0] = INT_MAX;
+        M->snap_meta[1] = 0;
+        M->result_meta[0] = M->meta0[0];
+        M->result_meta[1] = 0;
+        M->counters[0] = 0;
+        M->counters[1] = 0;
+    }
+    if (x < n_searches) {
+        *searches[x].clock = 0;
+        *searches[x].status = 0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host-side launchers
+// ---------------------------------------------------------------------------
+static int align16(int x) { return (x + 15) & ~15; }
+
+WarpLayout make_layout(int W, int cap, int mmax) {
+    WarpLayout L;
+    int o = 0;
+    L.off_pn = o;
+    o = align16(o + cap * W * 8);
+    L.off_cand = o;
+    o = align16(o + mmax * 4);
+    L.off_f = o;
+    o = align16(o + cap * 4);
+    L.off_ladj = o;
+    o = align16(o + mmax * 2);
+    L.off_hs = o;
+    o = align16(o + cap * 2);
+    L.off_he = o;
+    o = align16(o + cap * 2);
+    L.off_loff = o;
+    o = align16(o + cap * 2);
+    L.off_lcur = o;
+    o = align16(o + cap * 2);
+    L.per_warp = o;
+    return L;
+}
+
+int state_words(int W, int cap, int mmax) {
+    const int w = H_WORDS + 2 * cap * W + mmax + cap;
+    return (w + 3) & ~3;
+}
+
+cudaError_t launch_ingest(const int8_t* raw, int rows, int nx, int W, uint2* pn0, uint32_t* cand0,
+                          int32_t* meta0, int mmax, cudaStream_t stream) {
+    ingest_kernel<<<1, 32, 0, stream>>>(raw, rows, nx, W, pn0, cand0, meta0, mmax);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init(const DevMat* mats, int n_mats, const DevSearch* searches, int n_searches,
+                        cudaStream_t stream) {
+    const int n = n_mats > n_searches ? n_mats : n_searches;
+    init_kernel<<<(n + 127) / 128, 128, 0, stream>>>(mats, n_mats, searches, n_searches);
+    return cudaGetLastError();
+}
+
+template <int W>
+static cudaError_t launch_round_w(const DevMat* mats, int n_mats, const DevSearch* searches,
+                                  int total_units, const WarpLayout& L, int ppc, cudaStream_t stream) {
+    const size_t smem = (size_t)L.per_warp * ppc;
+    cudaError_t e = cudaFuncSetAttribute(round_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    const int grid = (total_units + ppc - 1) / ppc;
+    round_kernel<W><<<grid, 32 * ppc, smem, stream>>>(mats, n_mats, searches, total_units, L);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_round(int W, const DevMat* mats, int n_mats, const DevSearch* searches,
+                         int total_units, const WarpLayout& L, int ppc, cudaStream_t stream) {
+    switch (W) {
+        case 1: return launch_round_w<1>(mats, n_mats, searches, total_units, L, ppc, stream);
+        case 2: return launch_round_w<2>(mats, n_mats, searches, total_units, L, ppc, stream);
+        case 3: return launch_round_w<3>(mats, n_mats, searches, total_units, L, ppc, stream);
+        case 4: return launch_round_w<4>(mats, n_mats, searches, total_units, L, ppc, stream);
+        case 5: return launch_round_w<5>(mats, n_mats, searches, total_units, L, ppc, stream);
+        case 6: return launch_round_w<6>(mats, n_mats, searches, total_units, L, ppc, stream);
+        case 7: return launch_round_w<7>(mats, n_mats, searches, total_units, L, ppc, stream);
+        case 8: return launch_round_w<8>(mats, n_mats, searches, total_units, L, ppc, stream);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_share(const DevMat* mats, const DevSearch* searches, int n_searches,
+                         cudaStream_t stream) {
+    share_kernel<<<n_searches, 128, 0, stream>>>(mats, searches);
+    return cudaGetLastError();
+}
+
+int max_smem_per_block() {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return 0;
+    return v;
+}
+
+}  // namespace cse

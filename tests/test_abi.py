@@ -1,0 +1,77 @@
+"""Host-side checks of the C ABI that need no GPU: the library loads, exports
+every function include/cse.h declares, and rejects invalid arguments before
+touching the device."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2512_13365_gb300 import build as B
+from paper_2512_13365_gb300 import cse
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    B.build()
+    return cse.lib()
+
+
+def declared():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", f)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(cse_\w+)\s*\(", txt))
+    return names
+
+
+def test_exports_every_declared_symbol(L):
+    names = declared()
+    assert len(names) >= 12
+    for n in sorted(names):
+        assert hasattr(L, n), n
+    assert names == set(cse.EXPORTS)
+
+
+def _load(mats):
+    n = len(mats)
+    mats = [np.ascontiguousarray(m, dtype=np.int8) for m in mats]
+    ptrs = (ctypes.POINTER(ctypes.c_int8) * n)(*[m.ctypes.data_as(ctypes.POINTER(ctypes.c_int8)) for m in mats])
+    rows = (ctypes.c_int32 * n)(*[m.shape[0] for m in mats])
+    cols = (ctypes.c_int32 * n)(*[m.shape[1] for m in mats])
+    h = ctypes.c_void_p()
+    rc = cse.lib().cse_scheme_load(ptrs, rows, cols, n, ctypes.byref(h))
+    return rc, h
+
+
+@pytest.mark.parametrize("bad", [
+    [np.array([[2, 1]])],                      # not ternary
+    [np.array([[1, 1], [0, 0]])],              # zero row
+    [np.zeros((257, 3), np.int8) + 1],         # too many rows
+    [np.ones((2, 512), np.int8)],              # too many columns
+])
+def test_scheme_load_rejects_invalid(L, bad):
+    rc, h = _load(bad)
+    assert rc == cse.CSE_EINVAL and not h.value
+    assert L.cse_last_error()
+
+
+def test_search_rejects_invalid_arguments_without_device(L):
+    # argument checks come before any CUDA call; a NULL scheme is rejected
+    mix = cse.make_mix((1, 0, 0, 0, 0, 0))
+    opts = cse.make_opts()
+    h = ctypes.c_void_p()
+    assert L.cse_search(None, ctypes.byref(mix), 4, 0, 10, ctypes.byref(opts), None, ctypes.byref(h)) == \
+        cse.CSE_EINVAL
+    assert L.cse_result_fetch(None, 0, None, 0, None, None, None) == cse.CSE_EINVAL
+
+
+def test_opts_default(L):
+    o = cse.Opts()
+    L.cse_opts_default(ctypes.byref(o))
+    assert (o.share_interval, o.share_permille, o.col_cap, o.flags) == (32, 400, 128, 0)

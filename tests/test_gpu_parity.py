@@ -1,0 +1,158 @@
+"""Parity of the CUDA search (through the C ABI) with the CPU oracle.
+
+The method draws all its randomness from Philox keyed by (seed, process,
+step), so the bar is bit-exactness: every process's trajectory hash, best
+record, run count, op count and the per-matrix results must be identical.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2512_13365_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+FIELDS = ("best_cost", "best_len", "runs", "best_hash", "traj_hash", "ops", "substeps")
+
+
+@pytest.fixture(scope="module")
+def cse():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2512_13365_gb300 import cse as c
+    return c
+
+
+def assert_parity(cse, s, ref=None, procs_per_cta=0, check_procs=True):
+    r = cse.search_obj(s, procs_per_cta=procs_per_cta)
+    if ref is None:
+        ref = O.search_obj(s, n_threads=8)
+    assert r.costs == ref.cost
+    assert r.lists == ref.lists
+    if check_procs:
+        for k in range(len(s.mats)):
+            got, exp = r.procs(k), ref.digests[k]
+            for f in FIELDS:
+                bad = np.nonzero(got[f] != exp[f])[0]
+                assert bad.size == 0, f"matrix {k} field {f}: {bad.size} processes differ, first {bad[:5]}"
+    steps, sub, ops = r.counters()
+    assert steps == len(s.mats) * s.n_proc * s.budget
+    assert sub == int(sum(ref.digests[k]["substeps"].sum() for k in range(len(s.mats))))
+    assert ops == int(sum(ref.digests[k]["ops"].sum() for k in range(len(s.mats))))
+    r.free()
+    return ref
+
+
+def test_config1_full(cse):
+    assert_parity(cse, synth.config1())
+
+
+@pytest.mark.parametrize("ppc", [1, 3, 4, 8])
+def test_config2_reduced_any_launch_shape(cse, ppc):
+    s = synth.config2(n_proc=192, budget=160)
+    assert_parity(cse, s, procs_per_cta=ppc)
+
+
+@pytest.mark.parametrize("rows", [20, 33, 64, 65, 100, 130, 161, 200, 256])
+def test_word_widths(cse, rows):
+    # W = ceil(rows / 32) from 1 to 8; ragged process count
+    mats = [synth.random_matrix(rows, rows, 10, 2, 6, n_planted=5),
+            synth.random_matrix(rows + 1, 12, min(rows, 40), 2, 5, n_planted=3)]
+    s = synth.Search(f"w{rows}", mats, synth.PAPER_WEIGHTS, 37, 11, 70, 16, 400, 128)
+    assert_parity(cse, s)
+
+
+@pytest.mark.parametrize("weights", [synth.GI_ONLY, (0, 1, 0, 0, 0, 0), (0, 0, 1, 0, 0, 0), (0, 0, 0, 1, 0, 0),
+                                     (0, 0, 0, 0, 1, 0), (0, 0, 0, 0, 0, 1), synth.PAPER_WEIGHTS])
+def test_each_strategy(cse, weights):
+    s = synth.config2(n_proc=64, budget=96)
+    s.weights = weights
+    assert_parity(cse, s)
+
+
+@pytest.mark.parametrize("interval,permille", [(1, 400), (7, 1000), (32, 0), (1000, 400)])
+def test_sharing_settings(cse, interval, permille):
+    s = synth.config2(n_proc=48, budget=100)
+    s.interval, s.permille = interval, permille
+    assert_parity(cse, s)
+
+
+@pytest.mark.parametrize("budget", [0, 1, 2, 33])
+def test_small_budgets(cse, budget):
+    s = synth.config2(n_proc=20, budget=budget)
+    assert_parity(cse, s)
+
+
+def test_column_cap_termination(cse):
+    mats = [synth.random_matrix(5, 30, 9, 3, 7, n_planted=6, frac=(0.4, 0.7))]
+    for cap in (10, 11, 14):
+        s = synth.Search("cap", mats, synth.PAPER_WEIGHTS, 40, 3, 60, 8, 400, cap)
+        ref = assert_parity(cse, s)
+        assert max(ref.length) <= cap - 9
+
+
+def test_no_candidates_strassen(cse):
+    U, V, W = synth.strassen_uvw()
+    sc = cse.Scheme.from_uvw(2, 2, 2, U, V, W)
+    r = cse.search(sc, synth.PAPER_WEIGHTS, 16, 0, 40, 8, 400, 32)
+    assert r.total == 18 and r.costs == [5, 5, 8] and r.lists == [[], [], []]
+    assert sc.shape(2) == (4, 7)
+
+
+def test_paper_example(cse):
+    mat = np.array([[1, 1, -1, 1], [1, -1, 0, -1], [1, -1, -1, 1]], np.int8)
+    s = synth.Search("example", [mat], (0, 0, 0, 0, 0, 1), 1, 0, 2, 64, 0, 16)
+    ref = assert_parity(cse, s)
+    assert ref.cost == [6]
+
+
+def test_single_row_and_single_process(cse):
+    mats = [np.array([[1, -1, 1, 1, -1]], np.int8), synth.random_matrix(9, 6, 5, 2, 4)]
+    s = synth.Search("tiny", mats, synth.PAPER_WEIGHTS, 1, 5, 30, 4, 1000, 16)
+    assert_parity(cse, s)
+
+
+def test_seeds_differ(cse):
+    s = synth.config2(n_proc=32, budget=64)
+    a = cse.search_obj(s)
+    s.seed = 1
+    b = cse.search_obj(s)
+    assert not np.array_equal(a.procs(0)["traj_hash"], b.procs(0)["traj_hash"])
+
+
+def test_invalid_search_arguments(cse):
+    s = synth.config1()
+    sc = cse.Scheme(s.mats)
+    with pytest.raises(cse.CseError):
+        cse.search(sc, (0,) * 6, 4, 0, 10)                    # all weights zero
+    with pytest.raises(cse.CseError):
+        cse.search(sc, (1, 0, 0, 0, 0, 0, 1), 4, 0, 10)       # Greedy-Potential
+    with pytest.raises(cse.CseError):
+        cse.search(sc, synth.GI_ONLY, 4, 0, 10, cap=7)         # cap <= cols
+    with pytest.raises(cse.CseError):
+        cse.search(sc, synth.GI_ONLY, 0, 0, 10)                # no processes
+    with pytest.raises(cse.CseError):
+        cse.search(sc, synth.GI_ONLY, 4, 0, 10, interval=0)
+
+
+def test_config2_full_size(cse):
+    """The benchmark workload at full size (4096 processes x 3 matrices x 1024
+    steps) in the benchmark's launch configuration, against the full oracle."""
+    s = synth.config2()
+    assert_parity(cse, s)
+
+
+def test_results_are_valid_programs(cse):
+    s = synth.config2(n_proc=256, budget=256)
+    r = cse.search_obj(s)
+    for k, m in enumerate(s.mats):
+        lst, cost, _ = r.fetch(k)
+        out, c2 = O.apply(m, lst)
+        assert c2 == cost
+        # expansion of the fresh variables reproduces the input
+        nx = m.shape[1]
+        defs = [np.eye(nx, dtype=np.int64)[v] for v in range(nx)]
+        for e in lst:
+            i, j, sg = O.unentry(e)
+            defs.append(defs[i] + sg * defs[j])
+        assert np.array_equal(out.astype(np.int64) @ np.stack(defs), m.astype(np.int64))
