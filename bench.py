@@ -109,6 +109,8 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     s = workload(args.workload)
+    if args.budget:
+        s.budget = args.budget
     s.seed = s.seed + rank  # weak scaling: each rank searches its own seed, no data-path collective
     stream = torch.cuda.Stream(device=dev)
     scheme = cse.Scheme(s.mats)
@@ -166,7 +168,7 @@ def run_ours(args):
     e2e_ms = []
     h2d = sum(m.nbytes for m in s.mats)
     d2h = 0
-    for it in range(max(1, min(args.steps, 3))):
+    for it in range(0 if args.no_e2e else max(1, min(args.steps, 3))):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         sc = cse.Scheme(s.mats)
@@ -177,7 +179,7 @@ def run_ours(args):
         d2h = sum(4 * len(l) + 16 for l, _, _ in lists)
         r.free()
         sc.free()
-    e2e_value = psteps * world / (statistics.mean(e2e_ms) / 1000.0)
+    e2e_value = psteps * world / (statistics.mean(e2e_ms) / 1000.0) if e2e_ms else None
 
     # roofline of the dominant kernel (the round kernel)
     pk = peaks()
@@ -201,7 +203,7 @@ def run_ours(args):
         "best_additions": total, "best_additions_per_matrix": costs,
         "wall_s": wall,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "ms_per_step": statistics.mean(e2e_ms)},
+                "ms_per_step": statistics.mean(e2e_ms) if e2e_ms else None},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "Tops/s",
                      "frac": achieved / peak_ops, "traffic": None,
                      "kernel": "round_kernel<1>", "alg_ops_per_launch": ops_per_launch,
@@ -278,6 +280,8 @@ def main():
     ap.add_argument("--ppc", type=int, default=0, help="processes per CTA (0 = library default)")
     ap.add_argument("--cpu-budget", type=int, default=128, help="steps of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
+    ap.add_argument("--budget", type=int, default=0, help="override the step budget (profiling runs)")
     ap.add_argument("--out", default=os.path.join(ROOT, "gpurun_out"))
     args = ap.parse_args()
     os.makedirs(args.out, exist_ok=True)

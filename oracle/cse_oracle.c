@@ -18,7 +18,10 @@
  *      first, then the smaller, '+' before '-'.
  *   R2 random numbers: Philox4x32-10 keyed by the 64-bit seed; counter
  *      (process, step t, matrix<<24 | purpose<<20 | extra_hi, extra_lo).
- *      A draw u is lane 0 unless stated.
+ *      Purposes: RUN (drawn at a run start; lane 0 strategy, lane 1 alpha,
+ *      lane 2 beta, lane 3 share coin), SHAREK (lane 0: prefix length),
+ *      STEP (drawn per step when the strategy needs it; lane 0 mix, lane 1
+ *      gr coin, lane 2 ga, lane 3 wr) and GI (coins, R9).
  *   R3 g and gi break ties by the lowest canonical key.
  *   R4 ga: index (u * n_ties) >> 32 among the ties in canonical order.
  *   R5 wr: x = (u * T) >> 32 with T = sum(c - 1); the first candidate whose
@@ -30,13 +33,15 @@
  *      beta = b / 2^16 with b = 32768 + ((u * 32769) >> 32) in [32768, 65536];
  *      both drawn at the start of every run.  gi score
  *      S_p = (c_p - 1) * 2^32 + a * (2^16 * D_p + b * X_p)  (= H * 2^32).
- *   R9 gi coins: for candidate p = (i, j, s) the other candidates sharing a
- *      variable with it fall in slot 0 (they contain x_i) or slot 1 (they
- *      contain x_j but not x_i); within a slot they are ranked rho = 0, 1, ...
- *      in canonical order.  The coin of the rho-th is bit (rho mod 64) of
- *      the 64-bit word (lane 0 | lane 1 << 32) for slot 0 or (lane 2 | lane 3
- *      << 32) for slot 1 of the draw with purpose GI, extra_hi = rho >> 6,
- *      extra_lo = key(p).  Coin 1 means the pair survives with weight beta.
+ *   R9 gi coins: for candidate p = (i, j, s) let A_v be the list of all
+ *      candidates that contain x_v, in canonical order.  A candidate q != p
+ *      containing x_i (slot 0) takes the bit at its position x in A_i of the
+ *      64-bit word (lane 0 | lane 1 << 32); a candidate containing x_j but
+ *      not x_i (slot 1) takes the bit at its position x in A_j of the word
+ *      (lane 2 | lane 3 << 32); both words come from the draw with purpose
+ *      GI, extra_hi = x >> 6 (bit x & 63), extra_lo = key(p).  Positions
+ *      count every member of A_v, p and its sign twin included, so each
+ *      intersecting q gets its own bit.  Coin 1: q survives with weight beta.
  *   R10 the step clock: every process performs one step per t.  A step
  *      first (re)starts the run if t == 0 or the previous run ended, then
  *      makes one substitution if a pair with c > 1 exists and a free column
@@ -73,8 +78,7 @@
 #define ENT_J(e) ((int32_t)(((uint32_t)(e) >> 10) & 0x3FFu))
 #define ENT_NEG(e) ((int32_t)(((uint32_t)(e) >> 20) & 1u))
 
-enum { PU_STRAT = 0, PU_ALPHA = 1, PU_BETA = 2, PU_SHARE = 3, PU_SHAREK = 4, PU_MIX = 5,
-       PU_GA = 6, PU_GR = 7, PU_WR = 8, PU_GI = 9 };
+enum { PU_RUN = 0, PU_SHAREK = 1, PU_STEP = 2, PU_GI = 3 };
 
 /* ------------------------------------------------------------------ */
 /* Philox4x32-10, from the definition in Salmon et al., SC'11:          */
@@ -333,17 +337,21 @@ static int32_t sel_gi(const uint32_t* keys, const int32_t* cnt, int32_t m, uint3
     for (int32_t p = 0; p < m; p++) {
         uint32_t i = KEY_I(keys[p]), j = KEY_J(keys[p]);
         int64_t wp = cnt[p] - 1, inter = 0, x = 0;
-        int32_t rho0 = 0, rho1 = 0;
+        int32_t pos0 = 0, pos1 = 0, n_inter = 0; /* positions in A_i and A_j */
         for (int32_t q = 0; q < m; q++) {
-            if (q == p) continue;
             uint32_t qi = KEY_I(keys[q]), qj = KEY_J(keys[q]);
-            int coin;
-            if (qi == i || qj == i)
-                coin = coin_at(cs, p, q, 0, rho0++);
-            else if (qi == j || qj == j)
-                coin = coin_at(cs, p, q, 1, rho1++);
-            else
-                continue;
+            int hold_i = qi == i || qj == i, hold_j = qi == j || qj == j;
+            int coin = -1;
+            if (hold_i) {
+                if (q != p) coin = coin_at(cs, p, q, 0, pos0);
+                pos0++;
+                if (hold_j) pos1++; /* p or its sign twin: a place in A_j, no slot-1 coin */
+            } else if (hold_j) {
+                coin = coin_at(cs, p, q, 1, pos1);
+                pos1++;
+            }
+            if (coin < 0) continue;
+            n_inter++;
             inter += cnt[q] - 1;
             if (coin) x += cnt[q] - 1;
         }
@@ -354,8 +362,8 @@ static int32_t sel_gi(const uint32_t* keys, const int32_t* cnt, int32_t m, uint3
             best = p;
             best_s = s;
         }
-        int32_t b0 = (rho0 + 63) >> 6, b1 = (rho1 + 63) >> 6;
-        ops += 3 * (int64_t)(rho0 + rho1) + 8 + 40 * (int64_t)(b0 > b1 ? b0 : b1);
+        int32_t b0 = (pos0 + 63) >> 6, b1 = (pos1 + 63) >> 6;
+        ops += 3 * (int64_t)n_inter + 8 + (n_inter ? 40 * (int64_t)(b0 > b1 ? b0 : b1) : 0);
     }
     if (ops_out) *ops_out = ops;
     return best;
@@ -565,10 +573,12 @@ static void start_run(const search_t* S, int32_t mi, int32_t pi, int64_t t, work
     proc_t* P = &M->procs[pi];
     if (t > 0) fold(S, M, P);
     P->runs++;
+    uint32_t run[4];
+    draw4(S->seed, pi, t, mi, PU_RUN, 0, 0, run);
     if (pi == 0 && t == 0) {
         P->strategy = OR_G;
     } else {
-        uint32_t x = scale(draw(S->seed, pi, t, mi, PU_STRAT), S->wsum);
+        uint32_t x = scale(run[0], S->wsum);
         uint64_t acc = 0;
         P->strategy = -1;
         for (int32_t s = 0; s < OR_NSTRAT; s++) {
@@ -579,8 +589,8 @@ static void start_run(const search_t* S, int32_t mi, int32_t pi, int64_t t, work
             }
         }
     }
-    P->a = (int32_t)scale(draw(S->seed, pi, t, mi, PU_ALPHA), 32769);
-    P->b = 32768 + (int32_t)scale(draw(S->seed, pi, t, mi, PU_BETA), 32769);
+    P->a = (int32_t)scale(run[1], 32769);
+    P->b = 32768 + (int32_t)scale(run[2], 32769);
     /* fresh copy of the original expressions */
     memset(P->coef, 0, (size_t)M->rows * (size_t)S->cap);
     for (int32_t r = 0; r < M->rows; r++)
@@ -592,7 +602,7 @@ static void start_run(const search_t* S, int32_t mi, int32_t pi, int64_t t, work
     int32_t k = 0;
     if (M->snap_cost < INT64_MAX) {
         uint64_t thr = ((uint64_t)S->permille << 32) / 1000u;
-        if ((uint64_t)draw(S->seed, pi, t, mi, PU_SHARE) < thr) {
+        if ((uint64_t)run[3] < thr) {
             int32_t big_k = (3 * M->snap_len) / 4;
             if (big_k >= 1) k = 1 + (int32_t)scale(draw(S->seed, pi, t, mi, PU_SHAREK), (uint64_t)big_k);
         }
@@ -608,23 +618,21 @@ static void start_run(const search_t* S, int32_t mi, int32_t pi, int64_t t, work
 
 static int32_t choose(const search_t* S, int32_t mi, int32_t pi, int64_t t, proc_t* P) {
     int32_t strat = P->strategy;
-    uint64_t seed = S->seed;
+    uint32_t d[4] = {0, 0, 0, 0};
+    if (strat != OR_G && strat != OR_GI) draw4(S->seed, pi, t, mi, PU_STEP, 0, 0, d);
     if (strat == OR_MIX) {
-        uint32_t r = scale(draw(seed, pi, t, mi, PU_MIX), 15);
+        uint32_t r = scale(d[0], 15);
         strat = r < 8 ? OR_GI : r < 12 ? OR_GA : r < 14 ? OR_GR : OR_WR;
     }
     switch (strat) {
         case OR_G: P->ops += 2 * (int64_t)P->m; return sel_g(P->cnt, P->m);
-        case OR_GA: P->ops += 2 * (int64_t)P->m; return sel_ga(P->cnt, P->m, draw(seed, pi, t, mi, PU_GA));
-        case OR_WR: P->ops += 2 * (int64_t)P->m; return sel_wr(P->cnt, P->m, draw(seed, pi, t, mi, PU_WR));
-        case OR_GR:
-            P->ops += 2 * (int64_t)P->m;
-            return sel_gr(P->cnt, P->m, draw(seed, pi, t, mi, PU_GR), draw(seed, pi, t, mi, PU_GA),
-                          draw(seed, pi, t, mi, PU_WR));
+        case OR_GA: P->ops += 2 * (int64_t)P->m; return sel_ga(P->cnt, P->m, d[2]);
+        case OR_WR: P->ops += 2 * (int64_t)P->m; return sel_wr(P->cnt, P->m, d[3]);
+        case OR_GR: P->ops += 2 * (int64_t)P->m; return sel_gr(P->cnt, P->m, d[1], d[2], d[3]);
         case OR_GI: {
             coin_src cs;
             memset(&cs, 0, sizeof cs);
-            cs.seed = seed;
+            cs.seed = S->seed;
             cs.proc = pi;
             cs.mat = mi;
             cs.t = t;

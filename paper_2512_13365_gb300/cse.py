@@ -13,7 +13,7 @@ from typing import List, Optional, Sequence, Tuple
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "libcse_gb300.so")
+LIB_PATH = os.environ.get("CSE_GB300_LIB") or os.path.join(_HERE, "_build", "libcse_gb300.so")
 
 CSE_OK, CSE_EINVAL, CSE_ENOMEM, CSE_ECUDA, CSE_ETIMEOUT, CSE_EBUSY, CSE_ESTATE = range(7)
 

@@ -132,7 +132,7 @@ int cse_scheme_load(const int8_t* const* mats, const int32_t* rows, const int32_
         s->cols[k] = C;
         s->W[k] = (R + 31) / 32;
         // candidates have c >= 2 and row nnz never grows, so m <= occ / 2
-        s->mmax[k] = (int)std::max(1LL, std::min(occ / 2, 65535LL));
+        s->mmax[k] = (int)std::max(1LL, std::min(occ / 2, 32767LL));
         off_raw[k] = cv.take((size_t)R * C);
         off_pn[k] = cv.take((size_t)C * s->W[k] * sizeof(uint2));
         off_cand[k] = cv.take((size_t)s->mmax[k] * 4);
@@ -217,7 +217,7 @@ int cse_search(const cse_scheme* s, const cse_strategy_mix* mix, int32_t n_proc,
     for (int k = 0; k < s->n_mats; k++)
         if (s->cols[k] >= cap) return fail(CSE_EINVAL, "col_cap must exceed every matrix's column count");
     const int ppc_req = (int)opts.procs_per_cta;
-    if (ppc_req < 0 || ppc_req > 8) return fail(CSE_EINVAL, "procs_per_cta must be in [0, 8]");
+    if (ppc_req < 0 || ppc_req > 4) return fail(CSE_EINVAL, "procs_per_cta must be in [0, 4]");
     const int smem_max = max_smem_per_block();
     if (smem_max <= 0) return fail(CSE_ECUDA, "no CUDA device");
     set_pool_threshold_once();

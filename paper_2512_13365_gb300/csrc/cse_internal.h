@@ -11,10 +11,11 @@ namespace cse {
 enum Strategy : int { ST_GI = 0, ST_GA = 1, ST_GR = 2, ST_WR = 3, ST_MIX = 4, ST_G = 5, ST_N = 6 };
 
 // Purposes of the Philox draws (third counter word, bits 20..23).
-enum Purpose : uint32_t {
-    PU_STRAT = 0, PU_ALPHA = 1, PU_BETA = 2, PU_SHARE = 3, PU_SHAREK = 4,
-    PU_MIX = 5, PU_GA = 6, PU_GR = 7, PU_WR = 8, PU_GI = 9
-};
+//   RUN    at a run start: lane 0 strategy, 1 alpha, 2 beta, 3 share coin
+//   SHAREK prefix length of a shared start (lane 0)
+//   STEP   per step, when the strategy draws: lane 0 mix, 1 gr, 2 ga, 3 wr
+//   GI     Greedy-Intersections coins of one candidate (extra_lo = its key)
+enum Purpose : uint32_t { PU_RUN = 0, PU_SHAREK = 1, PU_STEP = 2, PU_GI = 3 };
 
 // Per-process state header, in 32-bit words at the start of the process's
 // state region in global memory.
@@ -61,7 +62,7 @@ struct DevSearch {
 
 // Shared-memory carve-up of one process (one warp), in bytes.
 struct WarpLayout {
-    int32_t off_pn, off_cand, off_f, off_ladj, off_hs, off_he, off_loff, off_lcur;
+    int32_t off_pn, off_cand, off_f, off_aw, off_poslo, off_hs, off_he, off_base, off_lc;
     int32_t per_warp;
 };
 

@@ -146,17 +146,19 @@ __global__ void ingest_kernel(const int8_t* __restrict__ raw, int rows, int nx, 
 // ---------------------------------------------------------------------------
 // The per-process engine.
 // ---------------------------------------------------------------------------
+
+// Out-of-line Philox for the per-run and per-step draws: one copy of the code
+// instead of one per call site keeps the kernel small in the instruction cache.
+__device__ __noinline__ uint4 philox_call(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
+                                          uint32_t k1) {
+    philox(c0, c1, c2, c3, k0, k1);
+    return make_uint4(c0, c1, c2, c3);
+}
+
 template <int W>
 struct Engine {
-    // shared memory of this warp
-    uint2* pn;
-    uint32_t* cand;
-    int32_t* F;
-    uint16_t* ladj;
-    uint16_t* hs;
-    uint16_t* he;
-    uint16_t* loff;
-    uint16_t* lcur;
+    unsigned char* sm;   // this warp's shared memory
+    const WarpLayout* L;
     // context
     const DevMat* M;
     const DevSearch* S;
@@ -169,19 +171,31 @@ struct Engine {
     long long ops_lane;  // per-lane part (gi scoring), reduced at the end
     int overflow;
 
-    __device__ __forceinline__ uint32_t draw(int t, uint32_t purpose) const {
-        uint32_t c0 = (uint32_t)proc, c1 = (uint32_t)t,
-                 c2 = ((uint32_t)M->mat_index & 0xFFu) << 24 | (purpose & 0xFu) << 20, c3 = 0;
-        philox(c0, c1, c2, c3, (uint32_t)S->seed, (uint32_t)(S->seed >> 32));
-        return c0;
+    __device__ __forceinline__ uint2* pn() const { return reinterpret_cast<uint2*>(sm + L->off_pn); }
+    __device__ __forceinline__ uint32_t* cand() const { return reinterpret_cast<uint32_t*>(sm + L->off_cand); }
+    __device__ __forceinline__ int32_t* F() const { return reinterpret_cast<int32_t*>(sm + L->off_f); }
+    __device__ __forceinline__ uint8_t* aw() const { return sm + L->off_aw; }
+    __device__ __forceinline__ uint16_t* poslo() const { return reinterpret_cast<uint16_t*>(sm + L->off_poslo); }
+    __device__ __forceinline__ uint16_t* hs() const { return reinterpret_cast<uint16_t*>(sm + L->off_hs); }
+    __device__ __forceinline__ uint16_t* he() const { return reinterpret_cast<uint16_t*>(sm + L->off_he); }
+    __device__ __forceinline__ uint16_t* vbase() const { return reinterpret_cast<uint16_t*>(sm + L->off_base); }
+    __device__ __forceinline__ uint16_t* lc() const { return reinterpret_cast<uint16_t*>(sm + L->off_lc); }
+
+    __device__ __forceinline__ uint32_t c2(uint32_t purpose, uint32_t extra_hi) const {
+        return ((uint32_t)M->mat_index & 0xFFu) << 24 | (purpose & 0xFu) << 20 | (extra_hi & 0xFFFFFu);
+    }
+    __device__ __forceinline__ uint4 draw(int t, uint32_t purpose) const {
+        return philox_call((uint32_t)proc, (uint32_t)t, c2(purpose, 0), 0u, (uint32_t)S->seed,
+                           (uint32_t)(S->seed >> 32));
     }
 
     // c(a, b, s) for columns a < b
     __device__ __forceinline__ void counts(int a_, int b_, int& cp, int& cm) const {
+        const uint2* P = pn();
         int both = 0, ng = 0;
 #pragma unroll
         for (int w = 0; w < W; w++) {
-            const uint2 A = pn[a_ * W + w], B = pn[b_ * W + w];
+            const uint2 A = P[a_ * W + w], B = P[b_ * W + w];
             const uint32_t bt = (A.x | A.y) & (B.x | B.y);
             both += __popc(bt);
             ng += __popc((A.x ^ B.x) & bt);
@@ -193,10 +207,12 @@ struct Engine {
     // Substitution of (x_i + s x_j), i < j, by the fresh x_k, k = ncols
     // (Section 3.2.1, Algorithm 1), with the candidate list update.
     __device__ void subst(int i, int j, int neg) {
+        uint2* P = pn();
+        uint32_t* C = cand();
         const int k = ncols;
         int cpart = 0;
         if (lane < W) {
-            uint2 A = pn[i * W + lane], B = pn[j * W + lane];
+            uint2 A = P[i * W + lane], B = P[j * W + lane];
             uint32_t rp, rn;
             if (!neg) {  // rows with +x_i +x_j  /  -x_i -x_j
                 rp = A.x & B.x;
@@ -211,12 +227,12 @@ struct Engine {
             }
             A.x &= ~rp;
             A.y &= ~rn;
-            pn[i * W + lane] = A;
-            pn[j * W + lane] = B;
-            pn[k * W + lane] = make_uint2(rp, rn);
+            P[i * W + lane] = A;
+            P[j * W + lane] = B;
+            P[k * W + lane] = make_uint2(rp, rn);
             cpart = __popc(rp) + __popc(rn);
         }
-        const int c = __reduce_add_sync(FULL_MASK, cpart);
+        const int c = W == 1 ? __shfl_sync(FULL_MASK, cpart, 0) : __reduce_add_sync(FULL_MASK, cpart);
         __syncwarp();
         // recount the candidates containing x_i or x_j; stable in-place compaction
         int newm = 0, nij = 0;
@@ -225,7 +241,7 @@ struct Engine {
             uint32_t e = 0;
             bool keep = false, touch = false;
             if (q < m) {
-                e = cand[q];
+                e = C[q];
                 const int lo = key_lo(e), hi = key_hi(e);
                 touch = lo == i || lo == j || hi == i || hi == j;
                 keep = true;
@@ -240,7 +256,7 @@ struct Engine {
             const uint32_t kb = __ballot_sync(FULL_MASK, keep);
             nij += __popc(__ballot_sync(FULL_MASK, touch));
             __syncwarp();
-            if (keep) cand[newm + __popc(kb & lt)] = e;
+            if (keep) C[newm + __popc(kb & lt)] = e;
             newm += __popc(kb);
         }
         // the new pairs (u, k): x_k has the largest index, so they sort last
@@ -254,7 +270,7 @@ struct Engine {
                 int both = 0, ng = 0;
 #pragma unroll
                 for (int w = 0; w < W; w++) {
-                    const uint2 A = pn[u * W + w], K = pn[k * W + w];
+                    const uint2 A = P[u * W + w], K = P[k * W + w];
                     sup |= A.x | A.y;
                     const uint32_t bt = (A.x | A.y) & (K.x | K.y);
                     both += __popc(bt);
@@ -269,17 +285,17 @@ struct Engine {
             const uint32_t bp = __ballot_sync(FULL_MASK, ep), bm = __ballot_sync(FULL_MASK, em);
             int pos = newm + __popc(bp & lt) + __popc(bm & lt);
             if (ep) {
-                if (pos < mmax) cand[pos] = make_cand(u, k, 0, cp);
+                if (pos < mmax) C[pos] = make_cand(u, k, 0, cp);
                 pos++;
             }
-            if (em && pos < mmax) cand[pos] = make_cand(u, k, 1, cm);
+            if (em && pos < mmax) C[pos] = make_cand(u, k, 1, cm);
             newm += __popc(bp) + __popc(bm);
         }
         if (newm > mmax) {
             overflow = 1;
             newm = mmax;
         }
-        if (lane == 0) F[nf] = (int32_t)((uint32_t)i | (uint32_t)j << 10 | (uint32_t)neg << 20);
+        if (lane == 0) F()[nf] = (int32_t)((uint32_t)i | (uint32_t)j << 10 | (uint32_t)neg << 20);
         nf++;
         ncols++;
         cost -= c - 1;
@@ -293,24 +309,26 @@ struct Engine {
     __device__ void fold() {
         if (cost < best_cost) {
             int32_t* dst = M->best_list + (size_t)proc * cap;
-            for (int x = lane; x < nf; x += 32) dst[x] = F[x];
+            const int32_t* f = F();
+            for (int x = lane; x < nf; x += 32) dst[x] = f[x];
             best_cost = cost;
             best_len = nf;
         }
     }
 
     // Run start at step t (Section 3.5.1-3.5.2): strategy, alpha, beta, fresh
-    // copy of the input, optional replay of a prefix of the snapshot.
-    __device__ void start_run(int t) {
+    // copy of the input.  Returns how many substitutions of the snapshot to
+    // replay (Section 3.5.2); the caller replays them.
+    __device__ int start_run(int t) {
         if (t > 0) fold();
         runs++;
+        const uint4 R = draw(t, PU_RUN);
         if (proc == 0 && t == 0) {
             strat = ST_G;
         } else {
-            const uint32_t x = scale32(draw(t, PU_STRAT), S->wsum);
+            const uint32_t x = scale32(R.x, S->wsum);
             uint32_t acc = 0;
             strat = ST_G;
-#pragma unroll
             for (int s = 0; s < ST_N; s++) {
                 acc += S->w[s];
                 if (x < acc) {
@@ -319,39 +337,35 @@ struct Engine {
                 }
             }
         }
-        a = (int)scale32(draw(t, PU_ALPHA), 32769u);
-        b = 32768 + (int)scale32(draw(t, PU_BETA), 32769u);
+        a = (int)scale32(R.y, 32769u);
+        b = 32768 + (int)scale32(R.z, 32769u);
         const int nx = M->nx;
-        for (int x = lane; x < nx * W; x += 32) pn[x] = M->pn0[x];
+        uint2* P = pn();
+        uint32_t* C = cand();
+        for (int x = lane; x < nx * W; x += 32) P[x] = M->pn0[x];
         const int m0 = M->meta0[1];
-        for (int x = lane; x < m0; x += 32) cand[x] = M->cand0[x];
+        for (int x = lane; x < m0; x += 32) C[x] = M->cand0[x];
         m = m0 < mmax ? m0 : mmax;
         ncols = nx;
         nf = 0;
         cost = M->meta0[0];
-        __syncwarp();
         int k = 0;
-        const int scost = M->snap_meta[0];
-        if (scost != INT_MAX) {
-            if ((uint64_t)draw(t, PU_SHARE) < S->share_thr) {
-                const int L = M->snap_meta[1];
-                const int K = (3 * L) / 4;
-                if (K >= 1) k = 1 + (int)scale32(draw(t, PU_SHAREK), (uint32_t)K);
-            }
-        }
-        for (int e = 0; e < k; e++) {
-            const uint32_t ent = (uint32_t)M->snap[e];
-            subst((int)(ent & 1023u), (int)((ent >> 10) & 1023u), (int)((ent >> 20) & 1u));
+        if (M->snap_meta[0] != INT_MAX && (uint64_t)R.w < S->share_thr) {
+            const int K = (3 * M->snap_meta[1]) / 4;
+            if (K >= 1) k = 1 + (int)scale32(draw(t, PU_SHAREK).x, (uint32_t)K);
         }
         ended = 0;
         traj = fnv(fnv(traj, (uint32_t)t), 0xA0000000u | (uint32_t)strat << 12 | (uint32_t)k);
+        __syncwarp();
+        return k;
     }
 
     // Greedy: highest c, lowest key.
     __device__ int sel_g() const {
+        const uint32_t* C = cand();
         uint32_t best = 0;
         for (int q = lane; q < m; q += 32) {
-            const uint32_t v = (uint32_t)cand_c(cand[q]) << 16 | (uint32_t)(0xFFFF - q);
+            const uint32_t v = (uint32_t)cand_c(C[q]) << 16 | (uint32_t)(0xFFFF - q);
             best = best > v ? best : v;
         }
         best = __reduce_max_sync(FULL_MASK, best);
@@ -360,9 +374,10 @@ struct Engine {
 
     // Greedy-Alternative: uniform among the max-c ties, (u * n_ties) >> 32-th in order.
     __device__ int sel_ga(uint32_t u) const {
+        const uint32_t* C = cand();
         int lmax = 0, lcnt = 0;
         for (int q = lane; q < m; q += 32) {
-            const int c = cand_c(cand[q]);
+            const int c = cand_c(C[q]);
             if (c > lmax) {
                 lmax = c;
                 lcnt = 1;
@@ -375,7 +390,7 @@ struct Engine {
         uint32_t want = scale32(u, (uint32_t)nt);
         for (int base = 0; base < m; base += 32) {
             const int q = base + lane;
-            const bool tie = q < m && cand_c(cand[q]) == cmax;
+            const bool tie = q < m && cand_c(C[q]) == cmax;
             const uint32_t bt = __ballot_sync(FULL_MASK, tie);
             const uint32_t n = (uint32_t)__popc(bt);
             if (want < n) {
@@ -390,14 +405,15 @@ struct Engine {
     // Weighted-Random: first candidate whose running sum of (c - 1) exceeds
     // (u * T) >> 32, T = sum (c - 1).
     __device__ int sel_wr(uint32_t u) const {
+        const uint32_t* C = cand();
         int part = 0;
-        for (int q = lane; q < m; q += 32) part += cand_c(cand[q]) - 1;
+        for (int q = lane; q < m; q += 32) part += cand_c(C[q]) - 1;
         const uint32_t total = (uint32_t)__reduce_add_sync(FULL_MASK, part);
         const uint32_t x = scale32(u, total);
         uint32_t acc = 0;
         for (int base = 0; base < m; base += 32) {
             const int q = base + lane;
-            const int w = q < m ? cand_c(cand[q]) - 1 : 0;
+            const int w = q < m ? cand_c(C[q]) - 1 : 0;
             const int incl = warp_incl_scan(w, lane);
             const uint32_t hit = __ballot_sync(FULL_MASK, q < m && acc + (uint32_t)incl > x);
             if (hit) return base + __ffs(hit) - 1;
@@ -408,17 +424,25 @@ struct Engine {
 
     // Greedy-Intersections (Section 3.4.2), exact integer score
     // S_p = (c_p - 1) 2^32 + a (2^16 D_p + b X_p); argmax, lowest key on ties.
+    // For every variable v the weights (c - 1) of the candidates holding x_v
+    // are gathered, in canonical order, into A_v = aw[base[v] ..): first the
+    // hi-block of v (contiguous in the sorted list), then the candidates whose
+    // lower index is v (a stable scatter).  A candidate's coin in a slot is the
+    // Philox bit at its position in A_v, so each lane scores its candidate with
+    // two straight loops over byte arrays.
     __device__ int sel_gi(int t) {
+        const uint32_t* C = cand();
+        uint16_t* HS = hs();
+        uint16_t* HE = he();
+        uint16_t* VB = vbase();
+        uint16_t* LC = lc();
+        uint8_t* AW = aw();
+        uint16_t* PL = poslo();
         int part = 0;
-        for (int q = lane; q < m; q += 32) part += cand_c(cand[q]) - 1;
-        const int T = __reduce_add_sync(FULL_MASK, part);
-        // adjacency: for each variable v, the candidates holding v in
-        // canonical order = [hi-block of v: contiguous in the list]
-        // followed by [candidates whose lo is v], gathered by a stable scatter.
         for (int v = lane; v < ncols; v += 32) {
-            hs[v] = 0;
-            he[v] = 0;
-            lcur[v] = 0;
+            HS[v] = 0;
+            HE[v] = 0;
+            LC[v] = 0;
         }
         __syncwarp();
         for (int base = 0; base < m; base += 32) {
@@ -426,23 +450,25 @@ struct Engine {
             const bool valid = q < m;
             const uint32_t act = __ballot_sync(FULL_MASK, valid);
             if (valid) {
-                const uint32_t e = cand[q];
+                const uint32_t e = C[q];
                 const int hi = key_hi(e), lo = key_lo(e);
-                if (q == 0 || key_hi(cand[q - 1]) != hi) hs[hi] = (uint16_t)q;
-                if (q == m - 1 || key_hi(cand[q + 1]) != hi) he[hi] = (uint16_t)(q + 1);
+                part += cand_c(e) - 1;
+                if (q == 0 || key_hi(C[q - 1]) != hi) HS[hi] = (uint16_t)q;
+                if (q == m - 1 || key_hi(C[q + 1]) != hi) HE[hi] = (uint16_t)(q + 1);
                 const uint32_t peers = __match_any_sync(act, lo);
-                if ((peers & lt) == 0) lcur[lo] = (uint16_t)(lcur[lo] + __popc(peers));
+                if ((peers & lt) == 0) LC[lo] = (uint16_t)(LC[lo] + __popc(peers));
             }
             __syncwarp();
         }
+        const int T = __reduce_add_sync(FULL_MASK, part);
         int run = 0;
         for (int base = 0; base < ncols; base += 32) {
             const int v = base + lane;
-            const int cnt = v < ncols ? lcur[v] : 0;
-            const int incl = warp_incl_scan(cnt, lane);
+            const int deg = v < ncols ? (HE[v] - HS[v]) + LC[v] : 0;
+            const int incl = warp_incl_scan(deg, lane);
             if (v < ncols) {
-                loff[v] = (uint16_t)(run + incl - cnt);
-                lcur[v] = 0;
+                VB[v] = (uint16_t)(run + incl - deg);
+                LC[v] = 0;
             }
             run += __shfl_sync(FULL_MASK, incl, 31);
         }
@@ -454,82 +480,99 @@ struct Engine {
             uint32_t peers = 0;
             int lo = 0;
             if (valid) {
-                lo = key_lo(cand[q]);
+                const uint32_t e = C[q];
+                const int hi = key_hi(e);
+                lo = key_lo(e);
+                const uint8_t w = (uint8_t)(cand_c(e) - 1);
+                AW[VB[hi] + (q - HS[hi])] = w;
                 peers = __match_any_sync(act, lo);
-                ladj[loff[lo] + lcur[lo] + __popc(peers & lt)] = (uint16_t)q;
+                const int pos = VB[lo] + (HE[lo] - HS[lo]) + LC[lo] + __popc(peers & lt);
+                AW[pos] = w;
+                PL[q] = (uint16_t)pos;
             }
             __syncwarp();
-            if (valid && (peers & lt) == 0) lcur[lo] = (uint16_t)(lcur[lo] + __popc(peers));
+            if (valid && (peers & lt) == 0) LC[lo] = (uint16_t)(LC[lo] + __popc(peers));
             __syncwarp();
         }
         // scoring: one candidate p per lane
         const uint32_t k0 = (uint32_t)S->seed, k1 = (uint32_t)(S->seed >> 32);
-        const uint32_t c2base = ((uint32_t)M->mat_index & 0xFFu) << 24 | (PU_GI & 0xFu) << 20;
+        const uint32_t c2g = c2(PU_GI, 0);
         long long best_s = LLONG_MIN;
         int best_q = -1;
         for (int base = 0; base < m; base += 32) {
             const int p = base + lane;
             if (p < m) {
-                const uint32_t e = cand[p];
+                const uint32_t e = C[p];
                 const int i = key_lo(e), j = key_hi(e), wp = cand_c(e) - 1;
                 const uint32_t key = e & 0x1FFFFFu;
-                uint32_t b0 = 0, b1 = 0, b2 = 0, b3 = 0;
-                int bidx = -1;
-                int inter = 0, X = 0, r0 = 0, r1 = 0;
-                auto coin = [&](int slot, int r) -> int {
-                    const int bi = r >> 6;
-                    if (bi != bidx) {
-                        b0 = (uint32_t)proc;
-                        b1 = (uint32_t)t;
-                        b2 = c2base | (uint32_t)bi;
-                        b3 = key;
-                        philox(b0, b1, b2, b3, k0, k1);
-                        bidx = bi;
-                    }
-                    const uint32_t word = slot == 0 ? ((r & 32) ? b1 : b0) : ((r & 32) ? b3 : b2);
-                    return (int)((word >> (r & 31)) & 1u);
-                };
-                // slot 0: candidates holding x_i (p itself excluded)
-                for (int x = hs[i]; x < he[i]; x++) {
-                    const int wq = cand_c(cand[x]) - 1;
-                    inter += wq;
-                    X += coin(0, r0++) ? wq : 0;
+                const int b0 = VB[i], n0 = (HE[i] - HS[i]) + LC[i];
+                const int b1 = VB[j], n1 = (HE[j] - HS[j]) + LC[j];
+                const int lp0 = PL[p] - b0;     // p's place in A_i
+                const int lp1 = p - HS[j];      // p's place in A_j
+                int sib = -1;                   // the sign twin (i, j, -s), if a candidate
+                if (!(e & 1u)) {
+                    if (p + 1 < m && (C[p + 1] & 0x1FFFFFu) == (key | 1u)) sib = p + 1;
+                } else {
+                    if (p >= 1 && (C[p - 1] & 0x1FFFFFu) == (key & ~1u)) sib = p - 1;
                 }
-                {
-                    const int o = loff[i], n = lcur[i];
-                    for (int x = o; x < o + n; x++) {
-                        const int q = ladj[x];
-                        if (q == p) continue;
-                        const int wq = cand_c(cand[q]) - 1;
-                        inter += wq;
-                        X += coin(0, r0++) ? wq : 0;
-                    }
-                }
-                // slot 1: candidates holding x_j but not x_i
-                for (int x = hs[j]; x < he[j]; x++) {
-                    const uint32_t eq = cand[x];
-                    if (key_lo(eq) == i) continue;
-                    const int wq = cand_c(eq) - 1;
-                    inter += wq;
-                    X += coin(1, r1++) ? wq : 0;
-                }
-                {
-                    const int o = loff[j], n = lcur[j];
-                    for (int x = o; x < o + n; x++) {
-                        const int wq = cand_c(cand[ladj[x]]) - 1;
-                        inter += wq;
-                        X += coin(1, r1++) ? wq : 0;
+                const int ls1 = sib - HS[j];
+                const int wsib = sib >= 0 ? cand_c(C[sib]) - 1 : 0;
+                const int nint = (n0 - 1) + (n1 - 1 - (sib >= 0 ? 1 : 0));
+                int inter = 0, X = 0, nb = 0;
+                if (nint > 0) {
+                    const int nb0 = (n0 + 63) >> 6, nb1 = (n1 + 63) >> 6;
+                    nb = nb0 > nb1 ? nb0 : nb1;
+                    for (int blk = 0; blk < nb; blk++) {
+                        uint32_t r0 = (uint32_t)proc, r1 = (uint32_t)t, r2 = c2g | (uint32_t)blk, r3 = key;
+                        philox(r0, r1, r2, r3, k0, k1);
+                        const int x0 = blk << 6;
+                        // slot 0: A_i, then take p itself out
+                        {
+                            const int x1 = min(n0, x0 + 64);
+#pragma unroll 4
+                            for (int x = x0; x < x1; x++) {
+                                const int w = AW[b0 + x];
+                                const uint32_t word = (x & 32) ? r1 : r0;
+                                inter += w;
+                                X += ((word >> (x & 31)) & 1u) ? w : 0;
+                            }
+                            if (lp0 >= x0 && lp0 < x1) {
+                                const uint32_t word = (lp0 & 32) ? r1 : r0;
+                                inter -= wp;
+                                X -= ((word >> (lp0 & 31)) & 1u) ? wp : 0;
+                            }
+                        }
+                        // slot 1: A_j, then take out p and its twin (they hold x_i)
+                        {
+                            const int x1 = min(n1, x0 + 64);
+#pragma unroll 4
+                            for (int x = x0; x < x1; x++) {
+                                const int w = AW[b1 + x];
+                                const uint32_t word = (x & 32) ? r3 : r2;
+                                inter += w;
+                                X += ((word >> (x & 31)) & 1u) ? w : 0;
+                            }
+                            if (lp1 >= x0 && lp1 < x1) {
+                                const uint32_t word = (lp1 & 32) ? r3 : r2;
+                                inter -= wp;
+                                X -= ((word >> (lp1 & 31)) & 1u) ? wp : 0;
+                            }
+                            if (sib >= 0 && ls1 >= x0 && ls1 < x1) {
+                                const uint32_t word = (ls1 & 32) ? r3 : r2;
+                                inter -= wsib;
+                                X -= ((word >> (ls1 & 31)) & 1u) ? wsib : 0;
+                            }
+                        }
                     }
                 }
                 const int D = T - wp - inter;
-                const long long s = ((long long)wp << 32) +
-                                    (long long)a * (((long long)D << 16) + (long long)b * (long long)X);
-                if (s > best_s) {
-                    best_s = s;
+                const long long sc = ((long long)wp << 32) +
+                                     (long long)a * (((long long)D << 16) + (long long)b * (long long)X);
+                if (sc > best_s) {
+                    best_s = sc;
                     best_q = p;
                 }
-                const int nb0 = (r0 + 63) >> 6, nb1 = (r1 + 63) >> 6;
-                ops_lane += 3LL * (r0 + r1) + 8 + 40LL * (nb0 > nb1 ? nb0 : nb1);
+                ops_lane += 3LL * nint + 8 + 40LL * nb;
             }
         }
 #pragma unroll
@@ -546,40 +589,62 @@ struct Engine {
 
     __device__ int choose(int t) {
         int s = strat;
+        uint4 d = make_uint4(0, 0, 0, 0);
+        if (s != ST_G && s != ST_GI) d = draw(t, PU_STEP);
         if (s == ST_MIX) {
-            const uint32_t r = scale32(draw(t, PU_MIX), 15u);
+            const uint32_t r = scale32(d.x, 15u);
             s = r < 8 ? ST_GI : r < 12 ? ST_GA : r < 14 ? ST_GR : ST_WR;
         }
-        if (s == ST_GR) s = draw(t, PU_GR) < 0xC0000000u ? ST_GA : ST_WR;
-        switch (s) {
-            case ST_G: ops += 2LL * m; return sel_g();
-            case ST_GA: ops += 2LL * m; return sel_ga(draw(t, PU_GA));
-            case ST_WR: ops += 2LL * m; return sel_wr(draw(t, PU_WR));
-            default: return sel_gi(t);
-        }
+        if (s == ST_GR) s = d.y < 0xC0000000u ? ST_GA : ST_WR;
+        if (s == ST_GI) return sel_gi(t);
+        ops += 2LL * m;
+        if (s == ST_GA) return sel_ga(d.z);
+        if (s == ST_WR) return sel_wr(d.w);
+        return sel_g();
     }
 
-    // One step of the step clock (Algorithm 1 iteration).
+    // One step of the step clock (one Algorithm 1 iteration).  A run start
+    // first replays its shared prefix; replays and the step's own
+    // substitution go through the one call site of subst().
     __device__ void step(int t) {
-        if (t == 0 || ended) start_run(t);
-        if (m == 0 || ncols >= cap) {
-            ended = 1;
-            return;
+        int replay = 0;
+        if (t == 0 || ended) replay = start_run(t);
+        for (int e = 0;; e++) {
+            int i, j, neg;
+            if (e < replay) {
+                const uint32_t ent = (uint32_t)M->snap[e];
+                i = (int)(ent & 1023u);
+                j = (int)((ent >> 10) & 1023u);
+                neg = (int)((ent >> 20) & 1u);
+            } else {
+                if (m == 0 || ncols >= cap) {
+                    ended = 1;
+                    return;
+                }
+                const int sel = choose(t);
+                const uint32_t ce = cand()[sel];
+                __syncwarp();
+                i = key_lo(ce);
+                j = key_hi(ce);
+                neg = (int)(ce & 1u);
+            }
+            subst(i, j, neg);
+            if (e >= replay) break;
         }
-        const int sel = choose(t);
-        const uint32_t e = cand[sel];
-        __syncwarp();
-        subst(key_lo(e), key_hi(e), (int)(e & 1u));
         substeps++;
-        traj = fnv(fnv(traj, (uint32_t)t), (uint32_t)F[nf - 1]);
+        traj = fnv(fnv(traj, (uint32_t)t), (uint32_t)F()[nf - 1]);
         if (m == 0 || ncols >= cap) ended = 1;
     }
 };
 
+#ifndef CSE_MIN_BLOCKS
+#define CSE_MIN_BLOCKS 8  // CTAs of 4 warps per SM the register budget must allow
+#endif
+
 template <int W>
-__global__ void __launch_bounds__(256) round_kernel(const DevMat* __restrict__ mats, int n_mats,
-                                                    const DevSearch* __restrict__ searches,
-                                                    int total_units, WarpLayout L) {
+__global__ void __launch_bounds__(128, CSE_MIN_BLOCKS) round_kernel(const DevMat* __restrict__ mats, int n_mats,
+                                                       const DevSearch* __restrict__ searches,
+                                                       int total_units, const __grid_constant__ WarpLayout L) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int unit = blockIdx.x * (blockDim.x >> 5) + warp;
@@ -592,16 +657,9 @@ __global__ void __launch_bounds__(256) round_kernel(const DevMat* __restrict__ m
     if (t0 >= S->budget) return;
     const int t1 = min(t0 + S->interval, S->budget);
 
-    unsigned char* base = smem + (size_t)warp * L.per_warp;
     Engine<W> E;
-    E.pn = reinterpret_cast<uint2*>(base + L.off_pn);
-    E.cand = reinterpret_cast<uint32_t*>(base + L.off_cand);
-    E.F = reinterpret_cast<int32_t*>(base + L.off_f);
-    E.ladj = reinterpret_cast<uint16_t*>(base + L.off_ladj);
-    E.hs = reinterpret_cast<uint16_t*>(base + L.off_hs);
-    E.he = reinterpret_cast<uint16_t*>(base + L.off_he);
-    E.loff = reinterpret_cast<uint16_t*>(base + L.off_loff);
-    E.lcur = reinterpret_cast<uint16_t*>(base + L.off_lcur);
+    E.sm = smem + (size_t)warp * L.per_warp;
+    E.L = &L;
     E.M = M;
     E.S = S;
     E.proc = unit - M->unit_base;
@@ -613,8 +671,6 @@ __global__ void __launch_bounds__(256) round_kernel(const DevMat* __restrict__ m
     E.overflow = 0;
 
     uint32_t* st = M->state + (size_t)E.proc * M->state_words;
-    long long ops_before;
-    int sub_before;
     if (t0 == 0) {
         E.ncols = M->nx;
         E.nf = 0;
@@ -646,14 +702,17 @@ __global__ void __launch_bounds__(256) round_kernel(const DevMat* __restrict__ m
         E.traj = (uint64_t)st[H_TRAJ_LO] | (uint64_t)st[H_TRAJ_HI] << 32;
         E.ops = (long long)((uint64_t)st[H_OPS_LO] | (uint64_t)st[H_OPS_HI] << 32);
         const uint2* spn = reinterpret_cast<const uint2*>(st + H_WORDS);
-        for (int x = lane; x < E.ncols * W; x += 32) E.pn[x] = spn[x];
+        uint2* P = E.pn();
+        for (int x = lane; x < E.ncols * W; x += 32) P[x] = spn[x];
         const uint32_t* sc = st + H_WORDS + 2 * M->cap * W;
-        for (int x = lane; x < E.m; x += 32) E.cand[x] = sc[x];
+        uint32_t* C = E.cand();
+        for (int x = lane; x < E.m; x += 32) C[x] = sc[x];
         const int32_t* sf = reinterpret_cast<const int32_t*>(sc + M->mmax);
-        for (int x = lane; x < E.nf; x += 32) E.F[x] = sf[x];
+        int32_t* F = E.F();
+        for (int x = lane; x < E.nf; x += 32) F[x] = sf[x];
     }
-    ops_before = E.ops;
-    sub_before = E.substeps;
+    const long long ops_before = E.ops;
+    const int sub_before = E.substeps;
     __syncwarp();
 
     for (int t = t0; t < t1; t++) E.step(t);
@@ -684,11 +743,14 @@ __global__ void __launch_bounds__(256) round_kernel(const DevMat* __restrict__ m
     }
     if (t1 < S->budget) {  // the state is needed by the next round
         uint2* spn = reinterpret_cast<uint2*>(st + H_WORDS);
-        for (int x = lane; x < E.ncols * W; x += 32) spn[x] = E.pn[x];
+        const uint2* P = E.pn();
+        for (int x = lane; x < E.ncols * W; x += 32) spn[x] = P[x];
         uint32_t* sc = st + H_WORDS + 2 * M->cap * W;
-        for (int x = lane; x < E.m; x += 32) sc[x] = E.cand[x];
+        const uint32_t* C = E.cand();
+        for (int x = lane; x < E.m; x += 32) sc[x] = C[x];
         int32_t* sf = reinterpret_cast<int32_t*>(sc + M->mmax);
-        for (int x = lane; x < E.nf; x += 32) sf[x] = E.F[x];
+        const int32_t* F = E.F();
+        for (int x = lane; x < E.nf; x += 32) sf[x] = F[x];
     }
 }
 
@@ -762,15 +824,17 @@ WarpLayout make_layout(int W, int cap, int mmax) {
     o = align16(o + mmax * 4);
     L.off_f = o;
     o = align16(o + cap * 4);
-    L.off_ladj = o;
+    L.off_aw = o;
+    o = align16(o + 2 * mmax);
+    L.off_poslo = o;
     o = align16(o + mmax * 2);
     L.off_hs = o;
     o = align16(o + cap * 2);
     L.off_he = o;
     o = align16(o + cap * 2);
-    L.off_loff = o;
+    L.off_base = o;
     o = align16(o + cap * 2);
-    L.off_lcur = o;
+    L.off_lc = o;
     o = align16(o + cap * 2);
     L.per_warp = o;
     return L;

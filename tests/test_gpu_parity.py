@@ -47,7 +47,7 @@ def test_config1_full(cse):
     assert_parity(cse, synth.config1())
 
 
-@pytest.mark.parametrize("ppc", [1, 3, 4, 8])
+@pytest.mark.parametrize("ppc", [1, 2, 3, 4])
 def test_config2_reduced_any_launch_shape(cse, ppc):
     s = synth.config2(n_proc=192, budget=160)
     assert_parity(cse, s, procs_per_cta=ppc)
