@@ -213,7 +213,7 @@ def run_ours(args):
         "gpu_launches": launches_per_search * args.steps,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(s, args.cpu_budget)
+        line["cpu_baseline"] = cpu_baseline(s, args.cpu_budget or s.budget)
     if world > 1:
         torch.distributed.barrier()
         torch.distributed.destroy_process_group()
@@ -230,11 +230,14 @@ def cpu_baseline(s, budget):
     smp = copy.copy(s)
     smp.budget = budget
     t0 = time.perf_counter()
-    O.search_obj(smp, n_threads=cores, digests=False)
+    ref = O.search_obj(smp, n_threads=cores, digests=False)
     dt = time.perf_counter() - t0
-    return {"value": smp.process_steps() / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{s.name}: all {s.n_proc} processes x {len(s.mats)} matrices, first {budget} of "
-                      f"{s.budget} steps ({smp.process_steps()} process-steps, {dt:.1f} s)"}
+    out = {"value": smp.process_steps() / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"{s.name}: all {s.n_proc} processes x {len(s.mats)} matrices, first {budget} of "
+                     f"{s.budget} steps ({smp.process_steps()} process-steps, {dt:.1f} s)"}
+    if budget == s.budget:
+        out["best_additions"] = ref.total  # the same search on the CPU: equal to the GPU's by parity
+    return out
 
 
 def run_reference(args):
@@ -246,7 +249,7 @@ def run_reference(args):
     cores = len(os.sched_getaffinity(0))
     import copy
     smp = copy.copy(s)
-    smp.budget = args.cpu_budget
+    smp.budget = args.cpu_budget or max(1, s.budget // 8)
     for _ in range(args.warmup):
         w = copy.copy(smp)
         w.budget = min(8, smp.budget)
@@ -278,7 +281,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="cfg2")
     ap.add_argument("--ppc", type=int, default=0, help="processes per CTA (0 = library default)")
-    ap.add_argument("--cpu-budget", type=int, default=128, help="steps of the oracle sample")
+    ap.add_argument("--cpu-budget", type=int, default=0,
+                    help="steps of the oracle sample (0 = the whole search, about 10 s on 16 cores)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--budget", type=int, default=0, help="override the step budget (profiling runs)")
