@@ -243,13 +243,36 @@ int cse_search(const cse_scheme* s, const cse_strategy_mix* mix, int32_t n_proc,
     r->pos_of_mat.assign(s->n_mats, 0);
     for (int q = 0; q < s->n_mats; q++) r->pos_of_mat[order[q]] = q;
 
+    // launch groups: equal W, one round kernel launch each; a group whose
+    // per-process arrays are too large for a shared-memory slice runs on HBM
+    struct Group { int W, begin, count, units, mmax; bool gm; WarpLayout L; int ppc; };
+    std::vector<Group> groups;
+    std::vector<int> group_of(s->n_mats);
+    for (int q = 0; q < s->n_mats; q++) {
+        const int k = order[q];
+        if (groups.empty() || groups.back().W != s->W[k]) groups.push_back({s->W[k], q, 0, 0, 0, false, {}, 0});
+        Group& g = groups.back();
+        g.count++;
+        g.units += n_proc;
+        g.mmax = std::max(g.mmax, s->mmax[k]);
+        group_of[q] = (int)groups.size() - 1;
+    }
+    for (Group& g : groups) {
+        g.L = make_layout(g.W, cap, g.mmax);
+        g.gm = g.L.per_warp > kSmemPerWarpLimit;
+        g.ppc = ppc_req ? ppc_req : 4;
+        if (!g.gm)
+            while (g.ppc > 1 && (long long)g.L.per_warp * g.ppc > smem_max) g.ppc--;
+    }
+
     Carve cv;
     struct Offs { size_t state, best, snap, snapm, rmin, res, resm, cnt; int sw; };
     std::vector<Offs> of(s->n_mats);
     for (int q = 0; q < s->n_mats; q++) {
         const int k = order[q];
         Offs& o = of[q];
-        o.sw = state_words(s->W[k], cap, s->mmax[k]);
+        const Group& g = groups[group_of[q]];
+        o.sw = g.gm ? state_words_gm(g.L) : state_words(s->W[k], cap, s->mmax[k]);
         o.state = cv.take((size_t)n_proc * o.sw * 4);
         o.best = cv.take((size_t)n_proc * cap * 4);
         o.snap = cv.take((size_t)cap * 4);
@@ -311,18 +334,9 @@ int cse_search(const cse_scheme* s, const cse_strategy_mix* mix, int32_t n_proc,
         M.result_meta = (int32_t*)(b + of[q].resm);
         M.counters = (unsigned long long*)(b + of[q].cnt);
     }
-    // groups of equal W: unit_base is relative to the group's launch
-    struct Group { int W, begin, count, units, mmax; };
-    std::vector<Group> groups;
-    for (int q = 0; q < s->n_mats; q++) {
-        const int Wq = r->hmats[q].W;
-        if (groups.empty() || groups.back().W != Wq) groups.push_back({Wq, q, 0, 0, 0});
-        Group& g = groups.back();
-        r->hmats[q].unit_base = g.units;
-        g.units += n_proc;
-        g.count++;
-        g.mmax = std::max(g.mmax, r->hmats[q].mmax);
-    }
+    // unit_base is relative to the group's launch
+    for (const Group& g : groups)
+        for (int q = g.begin; q < g.begin + g.count; q++) r->hmats[q].unit_base = (q - g.begin) * n_proc;
     DevMat* d_mats = (DevMat*)(b + off_mats);
     DevSearch* d_search = (DevSearch*)(b + off_search);
     cse_result* rr = r;
@@ -343,28 +357,13 @@ int cse_search(const cse_scheme* s, const cse_strategy_mix* mix, int32_t n_proc,
     for (auto& ev : r->ev_round)
         if ((e = cudaEventCreate(&ev)) != cudaSuccess) return bail(e, "event");
 
-    std::vector<WarpLayout> layouts;
-    std::vector<int> ppcs;
-    for (const Group& g : groups) {
-        WarpLayout L = make_layout(g.W, cap, g.mmax);
-        int ppc = ppc_req ? ppc_req : 4;
-        while (ppc > 1 && (long long)L.per_warp * ppc > smem_max) ppc--;
-        if ((long long)L.per_warp * ppc > smem_max) {
-            cudaFreeAsync(r->d_block, stream);
-            delete r;
-            return fail(CSE_ENOMEM, "one process needs " + std::to_string(L.per_warp) +
-                                        " bytes of shared memory, more than a CTA can have");
-        }
-        layouts.push_back(L);
-        ppcs.push_back(ppc);
-    }
     cudaEventRecord(r->ev_begin, stream);
     if ((e = launch_init(d_mats, s->n_mats, d_search, 1, stream)) != cudaSuccess) return bail(e, "init");
     for (int rd = 0; rd < r->rounds; rd++) {
         cudaEventRecord(r->ev_round[2 * rd], stream);
         for (size_t gi = 0; gi < groups.size(); gi++) {
             const Group& g = groups[gi];
-            e = launch_round(g.W, d_mats + g.begin, g.count, d_search, g.units, layouts[gi], ppcs[gi], stream);
+            e = launch_round(g.W, g.gm, d_mats + g.begin, g.count, d_search, g.units, g.L, g.ppc, stream);
             if (e != cudaSuccess) return bail(e, "round kernel");
         }
         cudaEventRecord(r->ev_round[2 * rd + 1], stream);

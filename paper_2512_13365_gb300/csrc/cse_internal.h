@@ -68,6 +68,11 @@ struct WarpLayout {
 
 WarpLayout make_layout(int W, int cap, int mmax);
 int state_words(int W, int cap, int mmax);
+int state_words_gm(const WarpLayout& L);
+
+// A process whose shared-memory slice would exceed this many bytes runs on
+// its HBM state region instead (round_kernel<W, true>).
+constexpr int kSmemPerWarpLimit = 24 * 1024;
 
 // Launchers (cse_kernels.cu).  All enqueue on `stream` and return the
 // launch error, if any.
@@ -75,7 +80,7 @@ cudaError_t launch_ingest(const int8_t* raw, int rows, int nx, int W, uint2* pn0
                           int32_t* meta0, int mmax, cudaStream_t stream);
 cudaError_t launch_init(const DevMat* mats, int n_mats, const DevSearch* searches, int n_searches,
                         cudaStream_t stream);
-cudaError_t launch_round(int W, const DevMat* mats, int n_mats, const DevSearch* searches,
+cudaError_t launch_round(int W, bool gm, const DevMat* mats, int n_mats, const DevSearch* searches,
                          int total_units, const WarpLayout& L, int procs_per_cta,
                          cudaStream_t stream);
 cudaError_t launch_share(const DevMat* mats, const DevSearch* searches, int n_searches,

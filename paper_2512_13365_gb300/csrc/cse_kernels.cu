@@ -641,7 +641,12 @@ struct Engine {
 #define CSE_MIN_BLOCKS 8  // CTAs of 4 warps per SM the register budget must allow
 #endif
 
-template <int W>
+// GM = false: the process's working arrays live in this warp's slice of
+// shared memory and are loaded from / stored to its HBM state region at the
+// round boundaries.  GM = true (matrices whose arrays are too large to share
+// an SM between enough warps): the arrays stay in the state region itself and
+// the engine works on them through the L1/L2 caches.
+template <int W, bool GM>
 __global__ void __launch_bounds__(128, CSE_MIN_BLOCKS) round_kernel(const DevMat* __restrict__ mats, int n_mats,
                                                        const DevSearch* __restrict__ searches,
                                                        int total_units, const __grid_constant__ WarpLayout L) {
@@ -657,8 +662,9 @@ __global__ void __launch_bounds__(128, CSE_MIN_BLOCKS) round_kernel(const DevMat
     if (t0 >= S->budget) return;
     const int t1 = min(t0 + S->interval, S->budget);
 
+    uint32_t* st = M->state + (size_t)(unit - M->unit_base) * M->state_words;
     Engine<W> E;
-    E.sm = smem + (size_t)warp * L.per_warp;
+    E.sm = GM ? reinterpret_cast<unsigned char*>(st + H_WORDS) : smem + (size_t)warp * L.per_warp;
     E.L = &L;
     E.M = M;
     E.S = S;
@@ -670,7 +676,6 @@ __global__ void __launch_bounds__(128, CSE_MIN_BLOCKS) round_kernel(const DevMat
     E.ops_lane = 0;
     E.overflow = 0;
 
-    uint32_t* st = M->state + (size_t)E.proc * M->state_words;
     if (t0 == 0) {
         E.ncols = M->nx;
         E.nf = 0;
@@ -701,6 +706,8 @@ __global__ void __launch_bounds__(128, CSE_MIN_BLOCKS) round_kernel(const DevMat
         E.best_len = (int)st[H_BEST_LEN];
         E.traj = (uint64_t)st[H_TRAJ_LO] | (uint64_t)st[H_TRAJ_HI] << 32;
         E.ops = (long long)((uint64_t)st[H_OPS_LO] | (uint64_t)st[H_OPS_HI] << 32);
+    }
+    if (t0 > 0 && !GM) {
         const uint2* spn = reinterpret_cast<const uint2*>(st + H_WORDS);
         uint2* P = E.pn();
         for (int x = lane; x < E.ncols * W; x += 32) P[x] = spn[x];
@@ -741,7 +748,7 @@ __global__ void __launch_bounds__(128, CSE_MIN_BLOCKS) round_kernel(const DevMat
         st[H_OPS_LO] = (uint32_t)(uint64_t)E.ops;
         st[H_OPS_HI] = (uint32_t)((uint64_t)E.ops >> 32);
     }
-    if (t1 < S->budget) {  // the state is needed by the next round
+    if (!GM && t1 < S->budget) {  // the state is needed by the next round
         uint2* spn = reinterpret_cast<uint2*>(st + H_WORDS);
         const uint2* P = E.pn();
         for (int x = lane; x < E.ncols * W; x += 32) spn[x] = P[x];
@@ -845,6 +852,8 @@ int state_words(int W, int cap, int mmax) {
     return (w + 3) & ~3;
 }
 
+int state_words_gm(const WarpLayout& L) { return H_WORDS + ((L.per_warp / 4 + 3) & ~3); }
+
 cudaError_t launch_ingest(const int8_t* raw, int rows, int nx, int W, uint2* pn0, uint32_t* cand0,
                           int32_t* meta0, int mmax, cudaStream_t stream) {
     ingest_kernel<<<1, 32, 0, stream>>>(raw, rows, nx, W, pn0, cand0, meta0, mmax);
@@ -858,31 +867,38 @@ cudaError_t launch_init(const DevMat* mats, int n_mats, const DevSearch* searche
     return cudaGetLastError();
 }
 
-template <int W>
+template <int W, bool GM>
 static cudaError_t launch_round_w(const DevMat* mats, int n_mats, const DevSearch* searches,
                                   int total_units, const WarpLayout& L, int ppc, cudaStream_t stream) {
-    const size_t smem = (size_t)L.per_warp * ppc;
-    cudaError_t e = cudaFuncSetAttribute(round_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    const size_t smem = GM ? 0 : (size_t)L.per_warp * ppc;
+    cudaError_t e = cudaFuncSetAttribute(round_kernel<W, GM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
     const int grid = (total_units + ppc - 1) / ppc;
-    round_kernel<W><<<grid, 32 * ppc, smem, stream>>>(mats, n_mats, searches, total_units, L);
+    round_kernel<W, GM><<<grid, 32 * ppc, smem, stream>>>(mats, n_mats, searches, total_units, L);
     return cudaGetLastError();
 }
 
-cudaError_t launch_round(int W, const DevMat* mats, int n_mats, const DevSearch* searches,
-                         int total_units, const WarpLayout& L, int ppc, cudaStream_t stream) {
+template <bool GM>
+static cudaError_t launch_round_gm(int W, const DevMat* mats, int n_mats, const DevSearch* searches,
+                                   int total_units, const WarpLayout& L, int ppc, cudaStream_t stream) {
     switch (W) {
-        case 1: return launch_round_w<1>(mats, n_mats, searches, total_units, L, ppc, stream);
-        case 2: return launch_round_w<2>(mats, n_mats, searches, total_units, L, ppc, stream);
-        case 3: return launch_round_w<3>(mats, n_mats, searches, total_units, L, ppc, stream);
-        case 4: return launch_round_w<4>(mats, n_mats, searches, total_units, L, ppc, stream);
-        case 5: return launch_round_w<5>(mats, n_mats, searches, total_units, L, ppc, stream);
-        case 6: return launch_round_w<6>(mats, n_mats, searches, total_units, L, ppc, stream);
-        case 7: return launch_round_w<7>(mats, n_mats, searches, total_units, L, ppc, stream);
-        case 8: return launch_round_w<8>(mats, n_mats, searches, total_units, L, ppc, stream);
+        case 1: return launch_round_w<1, GM>(mats, n_mats, searches, total_units, L, ppc, stream);
+        case 2: return launch_round_w<2, GM>(mats, n_mats, searches, total_units, L, ppc, stream);
+        case 3: return launch_round_w<3, GM>(mats, n_mats, searches, total_units, L, ppc, stream);
+        case 4: return launch_round_w<4, GM>(mats, n_mats, searches, total_units, L, ppc, stream);
+        case 5: return launch_round_w<5, GM>(mats, n_mats, searches, total_units, L, ppc, stream);
+        case 6: return launch_round_w<6, GM>(mats, n_mats, searches, total_units, L, ppc, stream);
+        case 7: return launch_round_w<7, GM>(mats, n_mats, searches, total_units, L, ppc, stream);
+        case 8: return launch_round_w<8, GM>(mats, n_mats, searches, total_units, L, ppc, stream);
         default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_round(int W, bool gm, const DevMat* mats, int n_mats, const DevSearch* searches,
+                         int total_units, const WarpLayout& L, int ppc, cudaStream_t stream) {
+    return gm ? launch_round_gm<true>(W, mats, n_mats, searches, total_units, L, ppc, stream)
+              : launch_round_gm<false>(W, mats, n_mats, searches, total_units, L, ppc, stream);
 }
 
 cudaError_t launch_share(const DevMat* mats, const DevSearch* searches, int n_searches,

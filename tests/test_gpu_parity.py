@@ -156,3 +156,21 @@ def test_results_are_valid_programs(cse):
             i, j, sg = O.unentry(e)
             defs.append(defs[i] + sg * defs[j])
         assert np.array_equal(out.astype(np.int64) @ np.stack(defs), m.astype(np.int64))
+
+
+def test_large_matrices_run_from_hbm(cse):
+    """(6,6,6:153)-shaped matrices (153 x 36 with W = 5 words per column and
+    36 x 153 with 153 original columns), columns grown towards 512: their
+    per-process arrays exceed a shared-memory slice, so the engine works on
+    the HBM state region.  Reduced process count and budget."""
+    s = synth.config4(n_proc=24, budget=48)
+    s.interval = 16
+    assert_parity(cse, s)
+
+
+def test_mid_size_both_paths(cse):
+    # the same search through shared memory (cap 64) and through HBM (cap 512)
+    mats = [synth.random_matrix(77, 60, 14, 3, 7, n_planted=8)]
+    for cap in (64, 512):
+        s = synth.Search("mid", mats, synth.PAPER_WEIGHTS, 40, 2, 80, 16, 400, cap)
+        assert_parity(cse, s)
