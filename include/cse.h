@@ -71,6 +71,11 @@ typedef struct {
     uint32_t w_gi, w_ga, w_gr, w_wr, w_mix, w_g, w_gp;
 } cse_strategy_mix;
 
+/* Option flags. */
+#define CSE_FLAG_GRAPH 1u  /* capture the whole launch sequence in one CUDA graph
+                              and launch it once; the round kernels of different
+                              matrix classes become parallel graph branches */
+
 /* Search options.  Fields that change results: share_interval,
  * share_permille, col_cap.  The rest only change how the work is launched. */
 typedef struct {
@@ -81,7 +86,7 @@ typedef struct {
     uint32_t patience_rounds; /* reserved, must be 0                         */
     uint64_t max_spin;        /* reserved for bounded device waits (unused)  */
     uint32_t procs_per_cta;   /* processes (warps) per CTA; 0 = automatic    */
-    uint32_t flags;           /* reserved, must be 0                         */
+    uint32_t flags;           /* CSE_FLAG_* bits; other bits must be 0       */
 } cse_opts;
 
 /* Default options: share_interval 32, share_permille 400, col_cap 128. */
@@ -115,6 +120,19 @@ int cse_scheme_shape(const cse_scheme* s, int32_t mat, int32_t* rows, int32_t* c
 int cse_search(const cse_scheme* s, const cse_strategy_mix* mix, int32_t n_processes,
                uint64_t seed, int64_t step_budget, const cse_opts* opts, void* cuda_stream,
                cse_result** out);
+
+/* Runs n_searches independent searches in one launch sequence (one CUDA
+ * graph with CSE_FLAG_GRAPH): search i is scheme schemes[i] with mixes[i],
+ * n_processes[i], seeds[i] and step_budgets[i]; all share *opts.  Every round
+ * runs all searches' processes together, one kernel per class of matrices
+ * with equal words per column.  Each search keeps its own step clock and
+ * sharing snapshot, so outs[i] is identical to what cse_search returns for
+ * search i alone (Sections 3.5.1-3.5.2 apply per search).  The schemes must
+ * stay loaded until the results are fetched.  outs[i] are freed one by one
+ * with cse_result_free; the device memory is released with the last one. */
+int cse_search_batch(int32_t n_searches, const cse_scheme* const* schemes, const cse_strategy_mix* mixes,
+                     const int32_t* n_processes, const uint64_t* seeds, const int64_t* step_budgets,
+                     const cse_opts* opts, void* cuda_stream, cse_result** outs);
 
 /* Waits for the search and copies the best substitution list of matrix mat:
  * up to cap_entries packed entries into subst (may be NULL), its length into
@@ -157,6 +175,10 @@ int cse_result_counters(const cse_result* r, int64_t* process_steps, int64_t* su
  * recorded around the round kernels on the search's stream: *round_ms sums
  * the step-engine launches, *total_ms spans the whole search. */
 int cse_result_timing(const cse_result* r, float* round_ms, float* total_ms, int32_t* n_rounds);
+
+/* Kernel launches of the search's launch sequence (shared by all searches of
+ * a batch) and the number of searches that shared it. */
+int cse_result_launches(const cse_result* r, int32_t* kernels, int32_t* searches_in_launch);
 
 void cse_result_free(cse_result* r);
 void cse_scheme_free(cse_scheme* s);

@@ -48,8 +48,10 @@ _lib = None
 
 # every symbol include/cse.h declares
 EXPORTS = ["cse_opts_default", "cse_scheme_load", "cse_scheme_load_uvw", "cse_scheme_shape", "cse_search",
-           "cse_result_fetch", "cse_result_procs", "cse_result_counters", "cse_result_timing",
-           "cse_result_free", "cse_scheme_free", "cse_last_error"]
+           "cse_search_batch", "cse_result_fetch", "cse_result_procs", "cse_result_counters", "cse_result_timing",
+           "cse_result_launches", "cse_result_free", "cse_scheme_free", "cse_last_error"]
+
+FLAG_GRAPH = 1
 
 
 def lib() -> ctypes.CDLL:
@@ -71,6 +73,9 @@ def lib() -> ctypes.CDLL:
     L.cse_scheme_shape.argtypes = [vp, i32, pi32, pi32]
     L.cse_search.argtypes = [vp, ctypes.POINTER(Mix), i32, u64, i64, ctypes.POINTER(Opts), vp,
                              ctypes.POINTER(vp)]
+    L.cse_search_batch.argtypes = [i32, ctypes.POINTER(vp), ctypes.POINTER(Mix), pi32, ctypes.POINTER(u64), pi64,
+                                   ctypes.POINTER(Opts), vp, ctypes.POINTER(vp)]
+    L.cse_result_launches.argtypes = [vp, pi32, pi32]
     L.cse_result_fetch.argtypes = [vp, i32, pi32, i32, pi32, pi64, pi64]
     L.cse_result_procs.argtypes = [vp, i32, ctypes.POINTER(ProcRecord)]
     L.cse_result_counters.argtypes = [vp, pi64, pi64, pi64]
@@ -184,6 +189,12 @@ class Result:
         _check(lib().cse_result_timing(self.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(n)))
         return a.value, b.value, n.value
 
+    def launches(self) -> Tuple[int, int]:
+        """(kernel launches of the launch sequence, searches that shared it)."""
+        k, n = ctypes.c_int32(), ctypes.c_int32()
+        _check(lib().cse_result_launches(self.handle, ctypes.byref(k), ctypes.byref(n)))
+        return k.value, n.value
+
     def free(self):
         if getattr(self, "handle", None):
             lib().cse_result_free(self.handle)
@@ -201,18 +212,20 @@ def make_mix(weights) -> Mix:
     return Mix(*[int(x) for x in w])
 
 
-def make_opts(interval: int = 32, permille: int = 400, cap: int = 128, procs_per_cta: int = 0) -> Opts:
+def make_opts(interval: int = 32, permille: int = 400, cap: int = 128, procs_per_cta: int = 0,
+              graph: bool = False) -> Opts:
     o = Opts()
     lib().cse_opts_default(ctypes.byref(o))
     o.share_interval, o.share_permille, o.col_cap, o.procs_per_cta = interval, permille, cap, procs_per_cta
+    o.flags = FLAG_GRAPH if graph else 0
     return o
 
 
 def search(scheme: Scheme, weights, n_proc: int, seed: int, budget: int, interval: int = 32,
-           permille: int = 400, cap: int = 128, stream=None, procs_per_cta: int = 0) -> Result:
+           permille: int = 400, cap: int = 128, stream=None, procs_per_cta: int = 0, graph: bool = False) -> Result:
     """cse_search: enqueue the search and return its Result handle."""
     mix = make_mix(weights)
-    opts = make_opts(interval, permille, cap, procs_per_cta)
+    opts = make_opts(interval, permille, cap, procs_per_cta, graph)
     h = ctypes.c_void_p()
     _check(lib().cse_search(scheme.handle, ctypes.byref(mix), n_proc, seed, budget, ctypes.byref(opts),
                             _stream_ptr(stream), ctypes.byref(h)))
@@ -225,3 +238,34 @@ def search_obj(s, scheme: Optional[Scheme] = None, **kw) -> Result:
     r = search(sc, s.weights, s.n_proc, s.seed, s.budget, s.interval, s.permille, s.cap, **kw)
     r._scheme = sc  # keep the device inputs alive while the search runs
     return r
+
+
+def search_batch(schemes: Sequence[Scheme], weights: Sequence, n_procs: Sequence[int], seeds: Sequence[int],
+                 budgets: Sequence[int], interval: int = 32, permille: int = 400, cap: int = 128, stream=None,
+                 procs_per_cta: int = 0, graph: bool = True) -> List[Result]:
+    """cse_search_batch: independent searches in one launch sequence."""
+    n = len(schemes)
+    hs = (ctypes.c_void_p * n)(*[s.handle for s in schemes])
+    mixes = (Mix * n)(*[make_mix(w) for w in weights])
+    np_ = (ctypes.c_int32 * n)(*n_procs)
+    sd = (ctypes.c_uint64 * n)(*seeds)
+    bd = (ctypes.c_int64 * n)(*budgets)
+    opts = make_opts(interval, permille, cap, procs_per_cta, graph)
+    outs = (ctypes.c_void_p * n)()
+    _check(lib().cse_search_batch(n, hs, mixes, np_, sd, bd, ctypes.byref(opts), _stream_ptr(stream), outs))
+    res = []
+    for i in range(n):
+        r = Result(ctypes.c_void_p(outs[i]), len(schemes[i].mats), n_procs[i], cap)
+        r._scheme = schemes[i]
+        res.append(r)
+    return res
+
+
+def search_batch_obj(searches, **kw) -> List[Result]:
+    """Run several synth.Search descriptions (same interval, permille and cap) as one batch."""
+    s0 = searches[0]
+    assert all((s.interval, s.permille, s.cap) == (s0.interval, s0.permille, s0.cap) for s in searches)
+    schemes = [Scheme(s.mats) for s in searches]
+    return search_batch(schemes, [s.weights for s in searches], [s.n_proc for s in searches],
+                        [s.seed for s in searches], [s.budget for s in searches], s0.interval, s0.permille,
+                        s0.cap, **kw)

@@ -5,7 +5,6 @@
 #include <climits>
 #include <cstdio>
 #include <cstring>
-#include <map>
 #include <new>
 #include <string>
 #include <vector>
@@ -67,18 +66,44 @@ struct cse_scheme {
     void* d_block = nullptr;
 };
 
-struct cse_result {
-    int n_mats = 0, n_proc = 0, cap = 0, rounds = 0;
-    int64_t budget = 0;
+// One launch: the device allocation, events and (optionally) the CUDA graph
+// shared by the results of the searches it ran.
+struct Batch {
+    int refs = 0;
+    int rounds = 0;
     cudaStream_t stream = nullptr;
     void* d_block = nullptr;
-    std::vector<DevMat> hmats;        // device order
-    std::vector<int> pos_of_mat;      // matrix index -> position in hmats
-    DevSearch hsearch{};
-    int32_t* d_status = nullptr;
+    std::vector<DevMat> hmats;       // device order
+    std::vector<DevSearch> hsearch;
     cudaEvent_t ev_begin = nullptr, ev_end = nullptr;
-    std::vector<cudaEvent_t> ev_round;
-    int rows[CSE_MAX_MATS], cols[CSE_MAX_MATS];
+    std::vector<cudaEvent_t> ev_round;   // begin/end of the round kernels of each round
+    std::vector<cudaEvent_t> ev_fork;    // fork/join events of concurrent groups
+    std::vector<cudaStream_t> aux;       // streams of concurrent groups
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    cudaStream_t cap_stream = nullptr;   // stream the graph is captured on
+    int launches_per_round = 0;
+
+    void release() {
+        if (ev_end) cudaEventSynchronize(ev_end);
+        if (d_block) cudaFreeAsync(d_block, stream);
+        for (auto ev : ev_round) cudaEventDestroy(ev);
+        for (auto ev : ev_fork) cudaEventDestroy(ev);
+        for (auto st : aux) cudaStreamDestroy(st);
+        if (ev_begin) cudaEventDestroy(ev_begin);
+        if (ev_end) cudaEventDestroy(ev_end);
+        if (gexec) cudaGraphExecDestroy(gexec);
+        if (graph) cudaGraphDestroy(graph);
+        if (cap_stream) cudaStreamDestroy(cap_stream);
+    }
+};
+
+struct cse_result {
+    Batch* batch = nullptr;
+    int search = 0;                   // index of the search in its batch
+    int n_mats = 0, n_proc = 0, cap = 0;
+    int64_t budget = 0;
+    std::vector<int> pos_of_mat;      // matrix index -> position in batch->hmats
 };
 
 extern "C" {
@@ -194,67 +219,79 @@ void cse_scheme_free(cse_scheme* s) {
     delete s;
 }
 
-int cse_search(const cse_scheme* s, const cse_strategy_mix* mix, int32_t n_proc, uint64_t seed,
-               int64_t budget, const cse_opts* opts_in, void* cuda_stream, cse_result** out) {
-    if (!out) return fail(CSE_EINVAL, "out is NULL");
-    *out = nullptr;
-    if (!s || !mix) return fail(CSE_EINVAL, "NULL scheme or strategy mix");
+static int check_mix(const cse_strategy_mix* mix, uint64_t* wsum_out) {
+    if (!mix) return fail(CSE_EINVAL, "NULL strategy mix");
+    if (mix->w_gp != 0) return fail(CSE_EINVAL, "Greedy-Potential (w_gp) is not implemented; set it to 0");
+    const uint64_t wsum = (uint64_t)mix->w_gi + mix->w_ga + mix->w_gr + mix->w_wr + mix->w_mix + mix->w_g;
+    if (wsum == 0 || wsum > 0xFFFFFFFFull) return fail(CSE_EINVAL, "strategy weights: sum must be in [1, 2^32)");
+    *wsum_out = wsum;
+    return CSE_OK;
+}
+
+// Builds and enqueues n independent searches as one launch sequence: per
+// round, one round kernel per class of equal words-per-column (and memory
+// path), then one share kernel over all searches.  Each search keeps its own
+// step clock, so its result does not depend on the others.
+static int run_batch(int n, const cse_scheme* const* schemes, const cse_strategy_mix* mixes,
+                     const int32_t* n_procs, const uint64_t* seeds, const int64_t* budgets,
+                     const cse_opts* opts_in, void* cuda_stream, cse_result** outs) {
+    if (!outs) return fail(CSE_EINVAL, "out is NULL");
+    if (n < 1 || !schemes || !mixes || !n_procs || !seeds || !budgets)
+        return fail(CSE_EINVAL, "n_searches must be >= 1 with non-NULL arrays");
+    for (int i = 0; i < n; i++) outs[i] = nullptr;
     cse_opts opts;
     if (opts_in)
         opts = *opts_in;
     else
         cse_opts_default(&opts);
-    if (mix->w_gp != 0) return fail(CSE_EINVAL, "Greedy-Potential (w_gp) is not implemented; set it to 0");
-    const uint64_t wsum = (uint64_t)mix->w_gi + mix->w_ga + mix->w_gr + mix->w_wr + mix->w_mix + mix->w_g;
-    if (wsum == 0 || wsum > 0xFFFFFFFFull) return fail(CSE_EINVAL, "strategy weights: sum must be in [1, 2^32)");
-    if (n_proc < 1 || n_proc > (1 << 20)) return fail(CSE_EINVAL, "n_processes must be in [1, 2^20]");
-    if (budget < 0 || budget >= INT32_MAX) return fail(CSE_EINVAL, "step_budget must be in [0, 2^31)");
     if (opts.share_interval < 1) return fail(CSE_EINVAL, "share_interval must be >= 1");
     if (opts.share_permille > 1000) return fail(CSE_EINVAL, "share_permille must be <= 1000");
-    if (opts.patience_rounds != 0 || opts.flags != 0) return fail(CSE_EINVAL, "reserved option fields must be 0");
+    if (opts.patience_rounds != 0 || (opts.flags & ~(uint32_t)CSE_FLAG_GRAPH) != 0)
+        return fail(CSE_EINVAL, "reserved option fields must be 0");
     const int cap = (int)opts.col_cap;
     if (cap > CSE_MAX_COLS) return fail(CSE_EINVAL, "col_cap must be <= 512");
-    for (int k = 0; k < s->n_mats; k++)
-        if (s->cols[k] >= cap) return fail(CSE_EINVAL, "col_cap must exceed every matrix's column count");
     const int ppc_req = (int)opts.procs_per_cta;
     if (ppc_req < 0 || ppc_req > 4) return fail(CSE_EINVAL, "procs_per_cta must be in [0, 4]");
+    std::vector<uint64_t> wsums(n);
+    int64_t max_budget = 0, total_mats = 0;
+    for (int i = 0; i < n; i++) {
+        const cse_scheme* s = schemes[i];
+        if (!s) return fail(CSE_EINVAL, "NULL scheme");
+        int rc = check_mix(&mixes[i], &wsums[i]);
+        if (rc) return rc;
+        if (n_procs[i] < 1 || n_procs[i] > (1 << 20)) return fail(CSE_EINVAL, "n_processes must be in [1, 2^20]");
+        if (budgets[i] < 0 || budgets[i] >= INT32_MAX) return fail(CSE_EINVAL, "step_budget must be in [0, 2^31)");
+        for (int k = 0; k < s->n_mats; k++)
+            if (s->cols[k] >= cap) return fail(CSE_EINVAL, "col_cap must exceed every matrix's column count");
+        max_budget = std::max(max_budget, budgets[i]);
+        total_mats += s->n_mats;
+    }
     const int smem_max = max_smem_per_block();
     if (smem_max <= 0) return fail(CSE_ECUDA, "no CUDA device");
     set_pool_threshold_once();
-
     cudaStream_t stream = (cudaStream_t)cuda_stream;
-    cse_result* r = new (std::nothrow) cse_result();
-    if (!r) return fail(CSE_ENOMEM, "host allocation");
-    r->n_mats = s->n_mats;
-    r->n_proc = n_proc;
-    r->cap = cap;
-    r->budget = budget;
-    r->stream = stream;
-    r->rounds = (int)((budget + opts.share_interval - 1) / opts.share_interval);
-    for (int k = 0; k < s->n_mats; k++) {
-        r->rows[k] = s->rows[k];
-        r->cols[k] = s->cols[k];
-    }
+    const bool use_graph = (opts.flags & CSE_FLAG_GRAPH) != 0;
 
-    // device order: matrices grouped by words per column (one launch per group)
-    std::vector<int> order(s->n_mats);
-    for (int k = 0; k < s->n_mats; k++) order[k] = k;
-    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return s->W[x] < s->W[y]; });
-    r->pos_of_mat.assign(s->n_mats, 0);
-    for (int q = 0; q < s->n_mats; q++) r->pos_of_mat[order[q]] = q;
+    // every matrix of every search, ordered by words per column
+    struct Ref { int search, mat, W, mmax, n_proc; };
+    std::vector<Ref> refs;
+    for (int i = 0; i < n; i++)
+        for (int k = 0; k < schemes[i]->n_mats; k++)
+            refs.push_back({i, k, schemes[i]->W[k], schemes[i]->mmax[k], n_procs[i]});
+    std::stable_sort(refs.begin(), refs.end(), [](const Ref& x, const Ref& y) { return x.W < y.W; });
+    const int nm = (int)refs.size();
 
     // launch groups: equal W, one round kernel launch each; a group whose
     // per-process arrays are too large for a shared-memory slice runs on HBM
     struct Group { int W, begin, count, units, mmax; bool gm; WarpLayout L; int ppc; };
     std::vector<Group> groups;
-    std::vector<int> group_of(s->n_mats);
-    for (int q = 0; q < s->n_mats; q++) {
-        const int k = order[q];
-        if (groups.empty() || groups.back().W != s->W[k]) groups.push_back({s->W[k], q, 0, 0, 0, false, {}, 0});
+    std::vector<int> group_of(nm);
+    for (int q = 0; q < nm; q++) {
+        if (groups.empty() || groups.back().W != refs[q].W) groups.push_back({refs[q].W, q, 0, 0, 0, false, {}, 0});
         Group& g = groups.back();
         g.count++;
-        g.units += n_proc;
-        g.mmax = std::max(g.mmax, s->mmax[k]);
+        g.units += refs[q].n_proc;
+        g.mmax = std::max(g.mmax, refs[q].mmax);
         group_of[q] = (int)groups.size() - 1;
     }
     for (Group& g : groups) {
@@ -263,18 +300,20 @@ int cse_search(const cse_scheme* s, const cse_strategy_mix* mix, int32_t n_proc,
         g.ppc = ppc_req ? ppc_req : 4;
         if (!g.gm)
             while (g.ppc > 1 && (long long)g.L.per_warp * g.ppc > smem_max) g.ppc--;
+        cudaError_t e = prepare_round(g.W, g.gm, g.L, g.ppc);
+        if (e != cudaSuccess) return fail(CSE_ECUDA, std::string("kernel attributes: ") + cudaGetErrorString(e));
     }
 
     Carve cv;
     struct Offs { size_t state, best, snap, snapm, rmin, res, resm, cnt; int sw; };
-    std::vector<Offs> of(s->n_mats);
-    for (int q = 0; q < s->n_mats; q++) {
-        const int k = order[q];
-        Offs& o = of[q];
+    std::vector<Offs> of(nm);
+    for (int q = 0; q < nm; q++) {
+        const Ref& rf = refs[q];
         const Group& g = groups[group_of[q]];
-        o.sw = g.gm ? state_words_gm(g.L) : state_words(s->W[k], cap, s->mmax[k]);
-        o.state = cv.take((size_t)n_proc * o.sw * 4);
-        o.best = cv.take((size_t)n_proc * cap * 4);
+        Offs& o = of[q];
+        o.sw = g.gm ? state_words_gm(g.L) : state_words(rf.W, cap, rf.mmax);
+        o.state = cv.take((size_t)rf.n_proc * o.sw * 4);
+        o.best = cv.take((size_t)rf.n_proc * cap * 4);
         o.snap = cv.take((size_t)cap * 4);
         o.snapm = cv.take(8);
         o.rmin = cv.take(8);
@@ -282,36 +321,78 @@ int cse_search(const cse_scheme* s, const cse_strategy_mix* mix, int32_t n_proc,
         o.resm = cv.take(8);
         o.cnt = cv.take(16);
     }
-    const size_t off_clock = cv.take(4), off_status = cv.take(4);
-    const size_t off_mats = cv.take(sizeof(DevMat) * s->n_mats), off_search = cv.take(sizeof(DevSearch));
-    cudaError_t e = cudaMallocAsync(&r->d_block, cv.off, stream);
+    const size_t off_clock = cv.take(4 * (size_t)n), off_status = cv.take(4 * (size_t)n);
+    const size_t off_pos = cv.take(4 * (size_t)nm);
+    const size_t off_mats = cv.take(sizeof(DevMat) * nm), off_search = cv.take(sizeof(DevSearch) * n);
+
+    Batch* B = new (std::nothrow) Batch();
+    if (!B) return fail(CSE_ENOMEM, "host allocation");
+    B->stream = stream;
+    B->rounds = 0;
+    for (int i = 0; i < n; i++)
+        B->rounds = std::max(B->rounds, (int)((budgets[i] + opts.share_interval - 1) / opts.share_interval));
+    cudaError_t e = cudaMallocAsync(&B->d_block, cv.off, stream);
     if (e != cudaSuccess) {
-        delete r;
+        B->d_block = nullptr;
+        delete B;
         return fail(e == cudaErrorMemoryAllocation ? CSE_ENOMEM : CSE_ECUDA,
                     std::string("device allocation: ") + cudaGetErrorString(e));
     }
-    char* b = (char*)r->d_block;
-    DevSearch& S = r->hsearch;
-    S.seed = seed;
-    S.w[ST_GI] = mix->w_gi;
-    S.w[ST_GA] = mix->w_ga;
-    S.w[ST_GR] = mix->w_gr;
-    S.w[ST_WR] = mix->w_wr;
-    S.w[ST_MIX] = mix->w_mix;
-    S.w[ST_G] = mix->w_g;
-    S.wsum = (uint32_t)wsum;
-    S.budget = (int32_t)budget;
-    S.interval = (int32_t)opts.share_interval;
-    S.share_thr = ((uint64_t)opts.share_permille << 32) / 1000u;
-    S.clock = (int32_t*)(b + off_clock);
-    S.status = (int32_t*)(b + off_status);
-    S.mat_begin = 0;
-    S.n_mats = s->n_mats;
-    r->d_status = S.status;
-    r->hmats.resize(s->n_mats);
-    for (int q = 0; q < s->n_mats; q++) {
-        const int k = order[q];
-        DevMat& M = r->hmats[q];
+    char* b = (char*)B->d_block;
+    auto bail = [&](cudaError_t err, const char* what) {
+        cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+        if (B->cap_stream && cudaStreamIsCapturing(B->cap_stream, &cst) == cudaSuccess &&
+            cst != cudaStreamCaptureStatusNone) {
+            cudaGraph_t g = nullptr;
+            cudaStreamEndCapture(B->cap_stream, &g);
+            if (g) cudaGraphDestroy(g);
+        }
+        B->ev_end = nullptr;
+        B->release();
+        delete B;
+        return fail(CSE_ECUDA, std::string(what) + ": " + cudaGetErrorString(err));
+    };
+
+    // per-search parameters; positions of each search's matrices
+    std::vector<int32_t> pos((size_t)nm);
+    std::vector<int> first_pos(n, 0), count(n, 0);
+    {
+        std::vector<std::vector<int>> by_search(n);
+        for (int q = 0; q < nm; q++) by_search[refs[q].search].push_back(q);
+        int o = 0;
+        for (int i = 0; i < n; i++) {
+            first_pos[i] = o;
+            count[i] = (int)by_search[i].size();
+            for (int q : by_search[i]) pos[o++] = q;
+        }
+    }
+    B->hsearch.resize(n);
+    for (int i = 0; i < n; i++) {
+        DevSearch& S = B->hsearch[i];
+        const cse_strategy_mix* mix = &mixes[i];
+        S.seed = seeds[i];
+        S.w[ST_GI] = mix->w_gi;
+        S.w[ST_GA] = mix->w_ga;
+        S.w[ST_GR] = mix->w_gr;
+        S.w[ST_WR] = mix->w_wr;
+        S.w[ST_MIX] = mix->w_mix;
+        S.w[ST_G] = mix->w_g;
+        S.wsum = (uint32_t)wsums[i];
+        S.budget = (int32_t)budgets[i];
+        S.interval = (int32_t)opts.share_interval;
+        S.share_thr = ((uint64_t)opts.share_permille << 32) / 1000u;
+        S.clock = (int32_t*)(b + off_clock) + i;
+        S.status = (int32_t*)(b + off_status) + i;
+        S.mat_pos = (const int32_t*)(b + off_pos) + first_pos[i];
+        S.n_mats = count[i];
+    }
+    B->hmats.resize(nm);
+    for (int q = 0; q < nm; q++) {
+        const Ref& rf = refs[q];
+        const cse_scheme* s = schemes[rf.search];
+        const int k = rf.mat;
+        const Group& g = groups[group_of[q]];
+        DevMat& M = B->hmats[q];
         M.pn0 = s->d_pn0[k];
         M.cand0 = s->d_cand0[k];
         M.meta0 = s->d_meta0[k];
@@ -321,8 +402,8 @@ int cse_search(const cse_scheme* s, const cse_strategy_mix* mix, int32_t n_proc,
         M.cap = cap;
         M.mmax = s->mmax[k];
         M.mat_index = k;
-        M.n_proc = n_proc;
-        M.search = 0;
+        M.n_proc = rf.n_proc;
+        M.search = rf.search;
         M.unit_base = 0;
         M.state_words = of[q].sw;
         M.state = (uint32_t*)(b + of[q].state);
@@ -333,52 +414,129 @@ int cse_search(const cse_scheme* s, const cse_strategy_mix* mix, int32_t n_proc,
         M.result = (int32_t*)(b + of[q].res);
         M.result_meta = (int32_t*)(b + of[q].resm);
         M.counters = (unsigned long long*)(b + of[q].cnt);
+        (void)g;
     }
-    // unit_base is relative to the group's launch
-    for (const Group& g : groups)
-        for (int q = g.begin; q < g.begin + g.count; q++) r->hmats[q].unit_base = (q - g.begin) * n_proc;
+    for (const Group& g : groups) {  // unit_base is relative to the group's launch
+        int u = 0;
+        for (int q = g.begin; q < g.begin + g.count; q++) {
+            B->hmats[q].unit_base = u;
+            u += refs[q].n_proc;
+        }
+    }
     DevMat* d_mats = (DevMat*)(b + off_mats);
     DevSearch* d_search = (DevSearch*)(b + off_search);
-    cse_result* rr = r;
-    auto bail = [&](cudaError_t err, const char* what) {
-        cudaFreeAsync(rr->d_block, stream);
-        for (auto ev : rr->ev_round) cudaEventDestroy(ev);
-        if (rr->ev_begin) cudaEventDestroy(rr->ev_begin);
-        if (rr->ev_end) cudaEventDestroy(rr->ev_end);
-        delete rr;
-        return fail(CSE_ECUDA, std::string(what) + ": " + cudaGetErrorString(err));
-    };
-    e = cudaMemcpyAsync(d_mats, r->hmats.data(), sizeof(DevMat) * s->n_mats, cudaMemcpyHostToDevice, stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d_search, &S, sizeof(DevSearch), cudaMemcpyHostToDevice, stream);
+    e = cudaMemcpyAsync(d_mats, B->hmats.data(), sizeof(DevMat) * nm, cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_search, B->hsearch.data(), sizeof(DevSearch) * n, cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b + off_pos, pos.data(), 4 * (size_t)nm, cudaMemcpyHostToDevice, stream);
     if (e != cudaSuccess) return bail(e, "parameter upload");
-    if ((e = cudaEventCreate(&r->ev_begin)) != cudaSuccess) return bail(e, "event");
-    if ((e = cudaEventCreate(&r->ev_end)) != cudaSuccess) return bail(e, "event");
-    r->ev_round.resize(2 * (size_t)r->rounds);
-    for (auto& ev : r->ev_round)
+    if ((e = cudaEventCreate(&B->ev_begin)) != cudaSuccess) return bail(e, "event");
+    if ((e = cudaEventCreate(&B->ev_end)) != cudaSuccess) return bail(e, "event");
+    B->ev_round.resize(2 * (size_t)B->rounds);
+    for (auto& ev : B->ev_round)
         if ((e = cudaEventCreate(&ev)) != cudaSuccess) return bail(e, "event");
-
-    cudaEventRecord(r->ev_begin, stream);
-    if ((e = launch_init(d_mats, s->n_mats, d_search, 1, stream)) != cudaSuccess) return bail(e, "init");
-    for (int rd = 0; rd < r->rounds; rd++) {
-        cudaEventRecord(r->ev_round[2 * rd], stream);
-        for (size_t gi = 0; gi < groups.size(); gi++) {
-            const Group& g = groups[gi];
-            e = launch_round(g.W, g.gm, d_mats + g.begin, g.count, d_search, g.units, g.L, g.ppc, stream);
-            if (e != cudaSuccess) return bail(e, "round kernel");
-        }
-        cudaEventRecord(r->ev_round[2 * rd + 1], stream);
-        if ((e = launch_share(d_mats, d_search, 1, stream)) != cudaSuccess) return bail(e, "share kernel");
+    const bool concurrent = use_graph && groups.size() > 1;
+    if (concurrent) {
+        B->aux.resize(groups.size());
+        B->ev_fork.resize(groups.size() + 1);
+        for (auto& st : B->aux)
+            if ((e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) != cudaSuccess) return bail(e, "stream");
+        for (auto& ev : B->ev_fork)
+            if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) return bail(e, "event");
     }
-    cudaEventRecord(r->ev_end, stream);
-    *out = r;
+    B->launches_per_round = (int)groups.size() + 1;
+
+    // With CSE_FLAG_GRAPH the sequence is captured on a private stream (the
+    // caller's may be the legacy default stream, which cannot be captured)
+    // and the instantiated graph is launched once on the caller's stream.
+    cudaStream_t ls = stream;
+    if (use_graph) {
+        if ((e = cudaStreamCreateWithFlags(&B->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
+            return bail(e, "stream");
+        ls = B->cap_stream;
+        if ((e = cudaStreamBeginCapture(ls, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+            return bail(e, "stream capture");
+    }
+    // timing events: inside a capture they must be external record nodes
+    auto rec = [&](cudaEvent_t ev) {
+        return use_graph ? cudaEventRecordWithFlags(ev, ls, cudaEventRecordExternal) : cudaEventRecord(ev, ls);
+    };
+    rec(B->ev_begin);
+    if ((e = launch_init(d_mats, nm, d_search, n, ls)) != cudaSuccess) return bail(e, "init");
+    for (int rd = 0; rd < B->rounds; rd++) {
+        rec(B->ev_round[2 * rd]);
+        if (concurrent) {  // the groups of a round are independent: parallel graph branches
+            cudaEventRecord(B->ev_fork[0], ls);
+            for (size_t gi = 0; gi < groups.size(); gi++) {
+                const Group& g = groups[gi];
+                cudaStreamWaitEvent(B->aux[gi], B->ev_fork[0], 0);
+                e = launch_round(g.W, g.gm, d_mats + g.begin, g.count, d_search, g.units, g.L, g.ppc, B->aux[gi]);
+                if (e != cudaSuccess) return bail(e, "round kernel");
+                cudaEventRecord(B->ev_fork[gi + 1], B->aux[gi]);
+                cudaStreamWaitEvent(ls, B->ev_fork[gi + 1], 0);
+            }
+        } else {
+            for (const Group& g : groups) {
+                e = launch_round(g.W, g.gm, d_mats + g.begin, g.count, d_search, g.units, g.L, g.ppc, ls);
+                if (e != cudaSuccess) return bail(e, "round kernel");
+            }
+        }
+        rec(B->ev_round[2 * rd + 1]);
+        if ((e = launch_share(d_mats, d_search, n, ls)) != cudaSuccess) return bail(e, "share kernel");
+    }
+    if ((e = rec(B->ev_end)) != cudaSuccess) return bail(e, "event record");
+    if (use_graph) {
+        if ((e = cudaStreamEndCapture(ls, &B->graph)) != cudaSuccess) return bail(e, "end capture");
+        if ((e = cudaGraphInstantiate(&B->gexec, B->graph, 0)) != cudaSuccess) return bail(e, "graph instantiate");
+        if ((e = cudaGraphLaunch(B->gexec, stream)) != cudaSuccess) return bail(e, "graph launch");
+    }
+
+    for (int i = 0; i < n; i++) {
+        cse_result* r = new (std::nothrow) cse_result();
+        if (!r) {
+            for (int j = 0; j < i; j++) {
+                delete outs[j];
+                outs[j] = nullptr;
+            }
+            B->release();
+            delete B;
+            return fail(CSE_ENOMEM, "host allocation");
+        }
+        r->batch = B;
+        r->search = i;
+        r->n_mats = schemes[i]->n_mats;
+        r->n_proc = n_procs[i];
+        r->cap = cap;
+        r->budget = budgets[i];
+        r->pos_of_mat.assign(r->n_mats, 0);
+        for (int q = 0; q < nm; q++)
+            if (refs[q].search == i) r->pos_of_mat[refs[q].mat] = q;
+        B->refs++;
+        outs[i] = r;
+    }
     return CSE_OK;
+}
+
+int cse_search(const cse_scheme* s, const cse_strategy_mix* mix, int32_t n_proc, uint64_t seed,
+               int64_t budget, const cse_opts* opts, void* cuda_stream, cse_result** out) {
+    if (!out) return fail(CSE_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!s || !mix) return fail(CSE_EINVAL, "NULL scheme or strategy mix");
+    return run_batch(1, &s, mix, &n_proc, &seed, &budget, opts, cuda_stream, out);
+}
+
+int cse_search_batch(int32_t n_searches, const cse_scheme* const* schemes, const cse_strategy_mix* mixes,
+                     const int32_t* n_processes, const uint64_t* seeds, const int64_t* step_budgets,
+                     const cse_opts* opts, void* cuda_stream, cse_result** outs) {
+    return run_batch(n_searches, schemes, mixes, n_processes, seeds, step_budgets, opts, cuda_stream, outs);
 }
 
 static int wait_result(const cse_result* r) {
     if (!r) return fail(CSE_EINVAL, "NULL result");
-    CUDA_TRY(cudaEventSynchronize(r->ev_end));
+    CUDA_TRY(cudaEventSynchronize(r->batch->ev_end));
     int32_t status = 0;
-    CUDA_TRY(cudaMemcpy(&status, r->d_status, 4, cudaMemcpyDeviceToHost));
+    CUDA_TRY(cudaMemcpy(&status, r->batch->hsearch[r->search].status, 4, cudaMemcpyDeviceToHost));
     if (status != 0) return fail(CSE_ESTATE, "device consistency check failed (candidate list overflow)");
     return CSE_OK;
 }
@@ -391,13 +549,13 @@ int cse_result_fetch(const cse_result* r, int32_t mat, int32_t* subst, int32_t c
     int64_t total = 0;
     int32_t meta[2] = {0, 0};
     for (int k = 0; k < r->n_mats; k++) {
-        const DevMat& M = r->hmats[r->pos_of_mat[k]];
+        const DevMat& M = r->batch->hmats[r->pos_of_mat[k]];
         int32_t mk[2];
         CUDA_TRY(cudaMemcpy(mk, M.result_meta, 8, cudaMemcpyDeviceToHost));
         total += mk[0];
         if (k == mat) std::memcpy(meta, mk, 8);
     }
-    const DevMat& M = r->hmats[r->pos_of_mat[mat]];
+    const DevMat& M = r->batch->hmats[r->pos_of_mat[mat]];
     if (subst && cap_entries > 0) {
         const int n = std::min(cap_entries, meta[1]);
         if (n > 0) CUDA_TRY(cudaMemcpy(subst, M.result, (size_t)n * 4, cudaMemcpyDeviceToHost));
@@ -412,8 +570,8 @@ int cse_result_procs(const cse_result* r, int32_t mat, cse_proc_record* out) {
     int rc = wait_result(r);
     if (rc) return rc;
     if (mat < 0 || mat >= r->n_mats || !out) return fail(CSE_EINVAL, "bad matrix index or output");
-    const DevMat& M = r->hmats[r->pos_of_mat[mat]];
-    if (r->rounds == 0) {  // no step ran: every record is the input itself
+    const DevMat& M = r->batch->hmats[r->pos_of_mat[mat]];
+    if (r->budget == 0) {  // no step ran: every record is the input itself
         int32_t meta[2];
         CUDA_TRY(cudaMemcpy(meta, M.result_meta, 8, cudaMemcpyDeviceToHost));
         for (int p = 0; p < r->n_proc; p++) {
@@ -452,7 +610,8 @@ int cse_result_counters(const cse_result* r, int64_t* process_steps, int64_t* su
     int rc = wait_result(r);
     if (rc) return rc;
     uint64_t ops = 0, sub = 0;
-    for (const DevMat& M : r->hmats) {
+    for (int k = 0; k < r->n_mats; k++) {
+        const DevMat& M = r->batch->hmats[r->pos_of_mat[k]];
         unsigned long long c[2];
         CUDA_TRY(cudaMemcpy(c, M.counters, 16, cudaMemcpyDeviceToHost));
         ops += c[0];
@@ -467,27 +626,36 @@ int cse_result_counters(const cse_result* r, int64_t* process_steps, int64_t* su
 int cse_result_timing(const cse_result* r, float* round_ms, float* total_ms, int32_t* n_rounds) {
     int rc = wait_result(r);
     if (rc) return rc;
+    const Batch* B = r->batch;
     float sum = 0.f, tot = 0.f;
-    for (int rd = 0; rd < r->rounds; rd++) {
+    for (int rd = 0; rd < B->rounds; rd++) {
         float x = 0.f;
-        CUDA_TRY(cudaEventElapsedTime(&x, r->ev_round[2 * rd], r->ev_round[2 * rd + 1]));
+        CUDA_TRY(cudaEventElapsedTime(&x, B->ev_round[2 * rd], B->ev_round[2 * rd + 1]));
         sum += x;
     }
-    CUDA_TRY(cudaEventElapsedTime(&tot, r->ev_begin, r->ev_end));
+    CUDA_TRY(cudaEventElapsedTime(&tot, B->ev_begin, B->ev_end));
     if (round_ms) *round_ms = sum;
     if (total_ms) *total_ms = tot;
-    if (n_rounds) *n_rounds = r->rounds;
+    if (n_rounds) *n_rounds = B->rounds;
+    return CSE_OK;
+}
+
+int cse_result_launches(const cse_result* r, int32_t* kernels, int32_t* searches_in_launch) {
+    if (!r) return fail(CSE_EINVAL, "NULL result");
+    const Batch* B = r->batch;
+    if (kernels) *kernels = 1 + B->rounds * B->launches_per_round;
+    if (searches_in_launch) *searches_in_launch = (int32_t)B->hsearch.size();
     return CSE_OK;
 }
 
 void cse_result_free(cse_result* r) {
     if (!r) return;
-    cudaEventSynchronize(r->ev_end);
-    cudaFreeAsync(r->d_block, r->stream);
-    for (auto ev : r->ev_round) cudaEventDestroy(ev);
-    cudaEventDestroy(r->ev_begin);
-    cudaEventDestroy(r->ev_end);
+    Batch* B = r->batch;
     delete r;
+    if (B && --B->refs == 0) {
+        B->release();
+        delete B;
+    }
 }
 
 }  // extern "C"

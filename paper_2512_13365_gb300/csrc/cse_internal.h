@@ -56,7 +56,8 @@ struct DevSearch {
     int32_t budget, interval;
     uint64_t share_thr;      // draw < share_thr => copy a prefix of the snapshot
     int32_t* clock;          // first step of the next round
-    int32_t mat_begin, n_mats;
+    const int32_t* mat_pos;  // positions of this search's matrices in the DevMat array
+    int32_t n_mats;
     int32_t* status;         // nonzero: a device-side consistency check failed
 };
 
@@ -85,6 +86,8 @@ cudaError_t launch_round(int W, bool gm, const DevMat* mats, int n_mats, const D
                          cudaStream_t stream);
 cudaError_t launch_share(const DevMat* mats, const DevSearch* searches, int n_searches,
                          cudaStream_t stream);
+// Sets the launch attributes of a round kernel (call outside stream capture).
+cudaError_t prepare_round(int W, bool gm, const WarpLayout& L, int procs_per_cta);
 int max_smem_per_block();
 
 }  // namespace cse

@@ -770,7 +770,7 @@ __global__ void share_kernel(const DevMat* __restrict__ mats, const DevSearch* _
     const int t1 = min(t0 + S->interval, S->budget);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     for (int k = warp; k < S->n_mats; k += nw) {
-        const DevMat* M = &mats[S->mat_begin + k];
+        const DevMat* M = &mats[S->mat_pos[k]];
         const unsigned long long key = *M->round_min;
         if (key == ~0ull) continue;  // no process reported (cannot happen when t0 < budget)
         const int cost = (int)(key >> 32), win = (int)(key & 0xFFFFFFFFu);
@@ -869,11 +869,11 @@ cudaError_t launch_init(const DevMat* mats, int n_mats, const DevSearch* searche
 
 template <int W, bool GM>
 static cudaError_t launch_round_w(const DevMat* mats, int n_mats, const DevSearch* searches,
-                                  int total_units, const WarpLayout& L, int ppc, cudaStream_t stream) {
+                                  int total_units, const WarpLayout& L, int ppc, cudaStream_t stream,
+                                  bool prepare_only) {
     const size_t smem = GM ? 0 : (size_t)L.per_warp * ppc;
-    cudaError_t e = cudaFuncSetAttribute(round_kernel<W, GM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
+    if (prepare_only)
+        return cudaFuncSetAttribute(round_kernel<W, GM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const int grid = (total_units + ppc - 1) / ppc;
     round_kernel<W, GM><<<grid, 32 * ppc, smem, stream>>>(mats, n_mats, searches, total_units, L);
     return cudaGetLastError();
@@ -881,24 +881,30 @@ static cudaError_t launch_round_w(const DevMat* mats, int n_mats, const DevSearc
 
 template <bool GM>
 static cudaError_t launch_round_gm(int W, const DevMat* mats, int n_mats, const DevSearch* searches,
-                                   int total_units, const WarpLayout& L, int ppc, cudaStream_t stream) {
+                                   int total_units, const WarpLayout& L, int ppc, cudaStream_t stream,
+                                   bool prep) {
     switch (W) {
-        case 1: return launch_round_w<1, GM>(mats, n_mats, searches, total_units, L, ppc, stream);
-        case 2: return launch_round_w<2, GM>(mats, n_mats, searches, total_units, L, ppc, stream);
-        case 3: return launch_round_w<3, GM>(mats, n_mats, searches, total_units, L, ppc, stream);
-        case 4: return launch_round_w<4, GM>(mats, n_mats, searches, total_units, L, ppc, stream);
-        case 5: return launch_round_w<5, GM>(mats, n_mats, searches, total_units, L, ppc, stream);
-        case 6: return launch_round_w<6, GM>(mats, n_mats, searches, total_units, L, ppc, stream);
-        case 7: return launch_round_w<7, GM>(mats, n_mats, searches, total_units, L, ppc, stream);
-        case 8: return launch_round_w<8, GM>(mats, n_mats, searches, total_units, L, ppc, stream);
+        case 1: return launch_round_w<1, GM>(mats, n_mats, searches, total_units, L, ppc, stream, prep);
+        case 2: return launch_round_w<2, GM>(mats, n_mats, searches, total_units, L, ppc, stream, prep);
+        case 3: return launch_round_w<3, GM>(mats, n_mats, searches, total_units, L, ppc, stream, prep);
+        case 4: return launch_round_w<4, GM>(mats, n_mats, searches, total_units, L, ppc, stream, prep);
+        case 5: return launch_round_w<5, GM>(mats, n_mats, searches, total_units, L, ppc, stream, prep);
+        case 6: return launch_round_w<6, GM>(mats, n_mats, searches, total_units, L, ppc, stream, prep);
+        case 7: return launch_round_w<7, GM>(mats, n_mats, searches, total_units, L, ppc, stream, prep);
+        case 8: return launch_round_w<8, GM>(mats, n_mats, searches, total_units, L, ppc, stream, prep);
         default: return cudaErrorInvalidValue;
     }
 }
 
 cudaError_t launch_round(int W, bool gm, const DevMat* mats, int n_mats, const DevSearch* searches,
                          int total_units, const WarpLayout& L, int ppc, cudaStream_t stream) {
-    return gm ? launch_round_gm<true>(W, mats, n_mats, searches, total_units, L, ppc, stream)
-              : launch_round_gm<false>(W, mats, n_mats, searches, total_units, L, ppc, stream);
+    return gm ? launch_round_gm<true>(W, mats, n_mats, searches, total_units, L, ppc, stream, false)
+              : launch_round_gm<false>(W, mats, n_mats, searches, total_units, L, ppc, stream, false);
+}
+
+cudaError_t prepare_round(int W, bool gm, const WarpLayout& L, int ppc) {
+    return gm ? launch_round_gm<true>(W, nullptr, 0, nullptr, 0, L, ppc, nullptr, true)
+              : launch_round_gm<false>(W, nullptr, 0, nullptr, 0, L, ppc, nullptr, true);
 }
 
 cudaError_t launch_share(const DevMat* mats, const DevSearch* searches, int n_searches,

@@ -174,3 +174,45 @@ def test_mid_size_both_paths(cse):
     for cap in (64, 512):
         s = synth.Search("mid", mats, synth.PAPER_WEIGHTS, 40, 2, 80, 16, 400, cap)
         assert_parity(cse, s)
+
+
+def _records(cse, r, n_mats):
+    return [r.procs(k) for k in range(n_mats)], r.lists, r.costs
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_batch_equals_each_search_alone(cse, graph):
+    """Uneven schemes (different shapes, W classes, process counts and budgets)
+    in one launch sequence give exactly the results of separate searches."""
+    searches = synth.config3(n_schemes=6, n_proc=40, budget=70, interval=16)
+    searches[1].n_proc, searches[2].budget, searches[3].seed = 23, 33, 99
+    searches.append(synth.config2(n_proc=30, budget=50))
+    searches[-1].interval, searches[-1].cap = 16, 256
+    batch = cse.search_batch_obj(searches, graph=graph)
+    kernels, shared = batch[0].launches()
+    assert shared == len(searches) and kernels >= 1 + 5  # init + rounds x (groups + share)
+    for s, rb in zip(searches, batch):
+        alone = cse.search_obj(s)
+        pb, lb, cb = _records(cse, rb, len(s.mats))
+        pa, la, ca = _records(cse, alone, len(s.mats))
+        assert lb == la and cb == ca
+        for x, y in zip(pb, pa):
+            assert np.array_equal(x, y)
+    # and against the oracle for two of them
+    for idx in (0, len(searches) - 1):
+        ref = O.search_obj(searches[idx], n_threads=8)
+        assert batch[idx].costs == ref.cost and batch[idx].lists == ref.lists
+        for k in range(len(searches[idx].mats)):
+            got, exp = batch[idx].procs(k), ref.digests[k]
+            for f in FIELDS:
+                assert np.array_equal(got[f], exp[f]), f
+    for r in batch:
+        r.free()
+
+
+def test_graph_single_search(cse):
+    s = synth.config2(n_proc=64, budget=96)
+    r = cse.search(cse.Scheme(s.mats), s.weights, s.n_proc, s.seed, s.budget, s.interval, s.permille, s.cap,
+                   graph=True)
+    ref = O.search_obj(s, n_threads=8)
+    assert r.costs == ref.cost and r.lists == ref.lists
