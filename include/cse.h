@@ -134,6 +134,38 @@ int cse_search_batch(int32_t n_searches, const cse_scheme* const* schemes, const
                      const int32_t* n_processes, const uint64_t* seeds, const int64_t* step_budgets,
                      const cse_opts* opts, void* cuda_stream, cse_result** outs);
 
+/* One class of matrices as the tuner saw it. */
+typedef struct {
+    int32_t words_per_column;  /* W = ceil(rows / 32)                          */
+    int32_t hbm_path;          /* 1: the process arrays live in HBM            */
+    int32_t candidate_bound;   /* bucket (power of two) of the candidate bound */
+    int32_t procs_per_cta;     /* chosen processes (warps) per CTA             */
+    float trial_ms[4];         /* round-kernel time with 1..4 per CTA          */
+} cse_tune_entry;
+
+/* Launch autotuner.  Runs the given searches (as in cse_search_batch) for
+ * min(step_budget, trial_steps) steps with 1, 2, 3 and 4 processes per CTA,
+ * times every class of matrices (equal words per column and memory path)
+ * with CUDA events, and caches the fastest choice per class in this process;
+ * later searches with opts->procs_per_cta == 0 use it.  Launch parameters
+ * never change results.  Writes up to max_entries entries and the number of
+ * classes into *n_entries.  Synchronous. */
+int cse_autotune(int32_t n_searches, const cse_scheme* const* schemes, const cse_strategy_mix* mixes,
+                 const int32_t* n_processes, const uint64_t* seeds, const int64_t* step_budgets,
+                 const cse_opts* opts, int32_t trial_steps, void* cuda_stream, cse_tune_entry* entries,
+                 int32_t max_entries, int32_t* n_entries);
+
+/* Sharing-interval tuner.  The interval changes the search (Section 3.5.2
+ * shares "from the second iteration onward"; here every share_interval
+ * steps), so this is an explicit choice: each candidate interval is run on
+ * the given searches for min(step_budget, trial_steps) steps and the one with
+ * the lowest total additions (sum over searches and matrices) is returned;
+ * ties keep the earlier candidate.  Synchronous. */
+int cse_tune_interval(int32_t n_searches, const cse_scheme* const* schemes, const cse_strategy_mix* mixes,
+                      const int32_t* n_processes, const uint64_t* seeds, const int64_t* step_budgets,
+                      const cse_opts* opts, const uint32_t* candidates, int32_t n_candidates,
+                      int32_t trial_steps, void* cuda_stream, uint32_t* best_interval, int64_t* best_total);
+
 /* Waits for the search and copies the best substitution list of matrix mat:
  * up to cap_entries packed entries into subst (may be NULL), its length into
  * *n_subst, its Cost into *additions, and the sum of the best Cost over all
@@ -182,6 +214,40 @@ int cse_result_launches(const cse_result* r, int32_t* kernels, int32_t* searches
 
 void cse_result_free(cse_result* r);
 void cse_scheme_free(cse_scheme* s);
+
+/* ---- Serving (continuous batching) ----------------------------------------
+ * A server owns a worker thread and a CUDA stream on the current device.
+ * Requests (a scheme and its search parameters) queue in FIFO order; at every
+ * round boundary the worker admits queued requests while the device memory
+ * of all active searches stays within hbm_budget_bytes (0 = no limit; a
+ * request larger than the budget runs alone), then runs one round (one
+ * kernel per class of matrices over every active search, then the share
+ * kernel).  Admitted searches therefore run concurrently with those already
+ * on the device and leave as soon as their step budget is done.  Each
+ * search keeps its own step clock, so a request's result is exactly what
+ * cse_search returns for it alone.  opts->flags is ignored. */
+int cse_server_create(const cse_opts* opts, uint64_t hbm_budget_bytes, cse_server** out);
+
+/* Queues a request; the scheme must stay loaded until its result is taken.
+ * Returns CSE_EINVAL for invalid parameters (checked here), CSE_EBUSY when
+ * 65536 requests are already waiting for admission.  *ticket identifies it. */
+int cse_server_submit(cse_server* s, const cse_scheme* scheme, const cse_strategy_mix* mix, int32_t n_processes,
+                      uint64_t seed, int64_t step_budget, uint64_t* ticket);
+
+/* Waits up to timeout_us microseconds (negative: no limit) for a request;
+ * CSE_ETIMEOUT if it is not done, else hands over its result (free it with
+ * cse_result_free; cse_result_timing reports the time from submission to
+ * completion).  Each ticket can be taken once. */
+int cse_server_wait(cse_server* s, uint64_t ticket, int64_t timeout_us, cse_result** out);
+
+/* Time-to-result percentiles (ms) over completed requests, process-steps
+ * per second from the first submission to the last completion, and the
+ * number of completed requests. */
+int cse_server_stats(cse_server* s, double* p50_ms, double* p99_ms, double* steps_per_s, int32_t* completed);
+
+/* Stops the worker (requests not yet finished are dropped) and frees the
+ * server.  No other call on it may be in progress. */
+void cse_server_free(cse_server* s);
 
 /* Message of the last error on the calling thread ("" if none). */
 const char* cse_last_error(void);

@@ -40,6 +40,12 @@ class ProcRecord(ctypes.Structure):
                 ("substeps", ctypes.c_int64)]
 
 
+class TuneEntry(ctypes.Structure):
+    _fields_ = [("words_per_column", ctypes.c_int32), ("hbm_path", ctypes.c_int32),
+                ("candidate_bound", ctypes.c_int32), ("procs_per_cta", ctypes.c_int32),
+                ("trial_ms", ctypes.c_float * 4)]
+
+
 PROC_DTYPE = np.dtype([("best_cost", "<i8"), ("best_len", "<i4"), ("runs", "<i4"), ("best_hash", "<u8"),
                        ("traj_hash", "<u8"), ("ops", "<i8"), ("substeps", "<i8")])
 assert PROC_DTYPE.itemsize == ctypes.sizeof(ProcRecord)
@@ -48,8 +54,9 @@ _lib = None
 
 # every symbol include/cse.h declares
 EXPORTS = ["cse_opts_default", "cse_scheme_load", "cse_scheme_load_uvw", "cse_scheme_shape", "cse_search",
-           "cse_search_batch", "cse_result_fetch", "cse_result_procs", "cse_result_counters", "cse_result_timing",
-           "cse_result_launches", "cse_result_free", "cse_scheme_free", "cse_last_error"]
+           "cse_search_batch", "cse_autotune", "cse_tune_interval", "cse_result_fetch", "cse_result_procs", "cse_result_counters", "cse_result_timing",
+           "cse_result_launches", "cse_result_free", "cse_scheme_free", "cse_last_error",
+           "cse_server_create", "cse_server_submit", "cse_server_wait", "cse_server_stats", "cse_server_free"]
 
 FLAG_GRAPH = 1
 
@@ -76,6 +83,10 @@ def lib() -> ctypes.CDLL:
     L.cse_search_batch.argtypes = [i32, ctypes.POINTER(vp), ctypes.POINTER(Mix), pi32, ctypes.POINTER(u64), pi64,
                                    ctypes.POINTER(Opts), vp, ctypes.POINTER(vp)]
     L.cse_result_launches.argtypes = [vp, pi32, pi32]
+    batch_args = [i32, ctypes.POINTER(vp), ctypes.POINTER(Mix), pi32, ctypes.POINTER(u64), pi64, ctypes.POINTER(Opts)]
+    L.cse_autotune.argtypes = batch_args + [i32, vp, ctypes.POINTER(TuneEntry), i32, pi32]
+    L.cse_tune_interval.argtypes = batch_args + [ctypes.POINTER(ctypes.c_uint32), i32, i32, vp,
+                                                 ctypes.POINTER(ctypes.c_uint32), pi64]
     L.cse_result_fetch.argtypes = [vp, i32, pi32, i32, pi32, pi64, pi64]
     L.cse_result_procs.argtypes = [vp, i32, ctypes.POINTER(ProcRecord)]
     L.cse_result_counters.argtypes = [vp, pi64, pi64, pi64]
@@ -84,8 +95,15 @@ def lib() -> ctypes.CDLL:
     L.cse_result_free.restype = None
     L.cse_scheme_free.argtypes = [vp]
     L.cse_scheme_free.restype = None
+    L.cse_server_create.argtypes = [ctypes.POINTER(Opts), ctypes.c_uint64, ctypes.POINTER(vp)]
+    L.cse_server_submit.argtypes = [vp, vp, ctypes.POINTER(Mix), i32, u64, i64, ctypes.POINTER(ctypes.c_uint64)]
+    L.cse_server_wait.argtypes = [vp, ctypes.c_uint64, i64, ctypes.POINTER(vp)]
+    L.cse_server_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                   ctypes.POINTER(ctypes.c_double), pi32]
+    L.cse_server_free.argtypes = [vp]
+    L.cse_server_free.restype = None
     for n in EXPORTS:
-        if n not in ("cse_opts_default", "cse_result_free", "cse_scheme_free", "cse_last_error"):
+        if n not in ("cse_opts_default", "cse_result_free", "cse_scheme_free", "cse_last_error", "cse_server_free"):
             getattr(L, n).restype = ctypes.c_int
     _lib = L
     return L
@@ -269,3 +287,76 @@ def search_batch_obj(searches, **kw) -> List[Result]:
     return search_batch(schemes, [s.weights for s in searches], [s.n_proc for s in searches],
                         [s.seed for s in searches], [s.budget for s in searches], s0.interval, s0.permille,
                         s0.cap, **kw)
+
+
+def _batch_args(schemes, weights, n_procs, seeds, budgets, interval, permille, cap, procs_per_cta=0, graph=False):
+    n = len(schemes)
+    return (n, (ctypes.c_void_p * n)(*[s.handle for s in schemes]), (Mix * n)(*[make_mix(w) for w in weights]),
+            (ctypes.c_int32 * n)(*n_procs), (ctypes.c_uint64 * n)(*seeds), (ctypes.c_int64 * n)(*budgets),
+            ctypes.byref(make_opts(interval, permille, cap, procs_per_cta, graph)))
+
+
+def autotune(schemes, weights, n_procs, seeds, budgets, interval=32, permille=400, cap=128, trial_steps=64,
+             stream=None) -> List[dict]:
+    """cse_autotune: time 1..4 processes per CTA per matrix class; cache the fastest."""
+    args = _batch_args(schemes, weights, n_procs, seeds, budgets, interval, permille, cap)
+    ent = (TuneEntry * 64)()
+    ne = ctypes.c_int32()
+    _check(lib().cse_autotune(*args, trial_steps, _stream_ptr(stream), ent, 64, ctypes.byref(ne)))
+    return [{"words_per_column": e.words_per_column, "hbm_path": e.hbm_path, "candidate_bound": e.candidate_bound,
+             "procs_per_cta": e.procs_per_cta, "trial_ms": list(e.trial_ms)} for e in ent[:ne.value]]
+
+
+def tune_interval(schemes, weights, n_procs, seeds, budgets, candidates=(16, 32, 64), permille=400, cap=128,
+                  trial_steps=128, stream=None) -> Tuple[int, int]:
+    """cse_tune_interval: the candidate interval with the lowest total additions after a trial."""
+    args = _batch_args(schemes, weights, n_procs, seeds, budgets, candidates[0], permille, cap)
+    c = (ctypes.c_uint32 * len(candidates))(*candidates)
+    best, tot = ctypes.c_uint32(), ctypes.c_int64()
+    _check(lib().cse_tune_interval(*args, c, len(candidates), trial_steps, _stream_ptr(stream), ctypes.byref(best),
+                                   ctypes.byref(tot)))
+    return best.value, tot.value
+
+
+class Server:
+    """Continuous-batching server (cse_server_*)."""
+
+    def __init__(self, interval: int = 32, permille: int = 400, cap: int = 128, hbm_budget: int = 0,
+                 procs_per_cta: int = 0):
+        h = ctypes.c_void_p()
+        _check(lib().cse_server_create(ctypes.byref(make_opts(interval, permille, cap, procs_per_cta)), hbm_budget,
+                                       ctypes.byref(h)))
+        self.handle = h
+        self.cap = cap
+        self._keep = {}
+
+    def submit(self, scheme: Scheme, weights, n_proc: int, seed: int, budget: int) -> int:
+        t = ctypes.c_uint64()
+        _check(lib().cse_server_submit(self.handle, scheme.handle, ctypes.byref(make_mix(weights)), n_proc, seed,
+                                       budget, ctypes.byref(t)))
+        self._keep[t.value] = (scheme, n_proc)
+        return t.value
+
+    def wait(self, ticket: int, timeout_us: int = -1) -> Result:
+        h = ctypes.c_void_p()
+        _check(lib().cse_server_wait(self.handle, ticket, timeout_us, ctypes.byref(h)))
+        scheme, n_proc = self._keep.pop(ticket)
+        r = Result(h, len(scheme.mats), n_proc, self.cap)
+        r._scheme = scheme
+        return r
+
+    def stats(self):
+        a, b, c, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_double(), ctypes.c_int32()
+        _check(lib().cse_server_stats(self.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(n)))
+        return {"p50_ms": a.value, "p99_ms": b.value, "steps_per_s": c.value, "completed": n.value}
+
+    def free(self):
+        if getattr(self, "handle", None):
+            lib().cse_server_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass

@@ -4,9 +4,16 @@
 #include <algorithm>
 #include <climits>
 #include <cstdio>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
 #include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "cse.h"
@@ -54,6 +61,35 @@ void set_pool_threshold_once() {
     }
 }
 
+// Launch-parameter cache filled by cse_autotune: processes per CTA for a
+// class of matrices (words per column, memory path, column cap, bucket of the
+// candidate bound).  Launch parameters never change results.
+struct ClassKey {
+    int W, gm, cap, mbucket;
+    bool operator<(const ClassKey& o) const {
+        if (W != o.W) return W < o.W;
+        if (gm != o.gm) return gm < o.gm;
+        if (cap != o.cap) return cap < o.cap;
+        return mbucket < o.mbucket;
+    }
+};
+std::mutex g_tune_mu;
+constexpr size_t kServerMaxPending = 1 << 16;
+std::map<ClassKey, int> g_tuned_ppc;
+
+int mbucket(int mmax) {
+    int b = 1;
+    while (b < mmax) b <<= 1;
+    return b;
+}
+
+// Trial-run controls used by the tuner.
+struct Trial {
+    int force_ppc = 0;                     // processes per CTA for every class
+    std::vector<float>* group_ms = nullptr;   // out: round-kernel time per class
+    std::vector<ClassKey>* keys = nullptr;    // out: class keys, same order
+};
+
 }  // namespace
 
 struct cse_scheme {
@@ -66,29 +102,65 @@ struct cse_scheme {
     void* d_block = nullptr;
 };
 
-// One launch: the device allocation, events and (optionally) the CUDA graph
-// shared by the results of the searches it ran.
+// ---------------------------------------------------------------------------
+// One search on the device: its own allocation (process states, best lists,
+// snapshot, round minimum, result, counters, clock, status) and the host
+// copies of the per-matrix and per-search kernel parameters.
+// ---------------------------------------------------------------------------
+struct SearchDev {
+    void* d_block = nullptr;
+    cudaStream_t stream = nullptr;
+    int n_mats = 0, n_proc = 0, cap = 0, rounds = 0, rounds_done = 0;
+    int64_t budget = 0;
+    size_t bytes = 0;
+    std::vector<DevMat> mats;   // matrix k at index k
+    std::vector<char> gm;       // matrix k runs on its HBM state region
+    DevSearch search{};
+    int rows[CSE_MAX_MATS], cols[CSE_MAX_MATS];
+};
+
+// Kernel parameters of one launch over a set of searches: matrices grouped
+// into classes of equal words per column and memory path (one round kernel
+// launch per class), then the share kernel over all searches.
+struct LaunchSet {
+    struct Group {
+        int W, begin, count, units, mmax, cap;
+        bool gm;
+        WarpLayout L;
+        int ppc;
+        ClassKey key;
+    };
+    std::vector<DevMat> mats;
+    std::vector<DevSearch> searches;
+    std::vector<int32_t> pos;
+    std::vector<Group> groups;
+    void* d_params = nullptr;
+    DevMat* d_mats = nullptr;
+    DevSearch* d_searches = nullptr;
+};
+
+// One static launch (cse_search / cse_search_batch): events, the parameter
+// block, and (optionally) the CUDA graph shared by the results it produced.
 struct Batch {
     int refs = 0;
     int rounds = 0;
     cudaStream_t stream = nullptr;
-    void* d_block = nullptr;
-    std::vector<DevMat> hmats;       // device order
-    std::vector<DevSearch> hsearch;
+    LaunchSet ls;
     cudaEvent_t ev_begin = nullptr, ev_end = nullptr;
     std::vector<cudaEvent_t> ev_round;   // begin/end of the round kernels of each round
     std::vector<cudaEvent_t> ev_fork;    // fork/join events of concurrent groups
+    std::vector<cudaEvent_t> ev_group;   // trial runs: begin/end of every class launch
     std::vector<cudaStream_t> aux;       // streams of concurrent groups
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
     cudaStream_t cap_stream = nullptr;   // stream the graph is captured on
-    int launches_per_round = 0;
 
     void release() {
         if (ev_end) cudaEventSynchronize(ev_end);
-        if (d_block) cudaFreeAsync(d_block, stream);
+        if (ls.d_params) cudaFreeAsync(ls.d_params, stream);
         for (auto ev : ev_round) cudaEventDestroy(ev);
         for (auto ev : ev_fork) cudaEventDestroy(ev);
+        for (auto ev : ev_group) cudaEventDestroy(ev);
         for (auto st : aux) cudaStreamDestroy(st);
         if (ev_begin) cudaEventDestroy(ev_begin);
         if (ev_end) cudaEventDestroy(ev_end);
@@ -99,11 +171,454 @@ struct Batch {
 };
 
 struct cse_result {
-    Batch* batch = nullptr;
-    int search = 0;                   // index of the search in its batch
-    int n_mats = 0, n_proc = 0, cap = 0;
+    SearchDev* sd = nullptr;     // owned
+    Batch* batch = nullptr;      // shared (static launches), or NULL (served)
+    double latency_ms = 0.0;     // served requests: submit to completion
+};
+
+static void search_free(SearchDev* sd) {
+    if (!sd) return;
+    if (sd->d_block) cudaFreeAsync(sd->d_block, sd->stream);
+    delete sd;
+}
+
+static int check_mix(const cse_strategy_mix* mix, uint64_t* wsum_out) {
+    if (!mix) return fail(CSE_EINVAL, "NULL strategy mix");
+    if (mix->w_gp != 0) return fail(CSE_EINVAL, "Greedy-Potential (w_gp) is not implemented; set it to 0");
+    const uint64_t wsum = (uint64_t)mix->w_gi + mix->w_ga + mix->w_gr + mix->w_wr + mix->w_mix + mix->w_g;
+    if (wsum == 0 || wsum > 0xFFFFFFFFull) return fail(CSE_EINVAL, "strategy weights: sum must be in [1, 2^32)");
+    *wsum_out = wsum;
+    return CSE_OK;
+}
+
+static int check_opts(const cse_opts* opts_in, cse_opts* opts) {
+    if (opts_in)
+        *opts = *opts_in;
+    else
+        cse_opts_default(opts);
+    if (opts->share_interval < 1) return fail(CSE_EINVAL, "share_interval must be >= 1");
+    if (opts->share_permille > 1000) return fail(CSE_EINVAL, "share_permille must be <= 1000");
+    if (opts->patience_rounds != 0 || (opts->flags & ~(uint32_t)CSE_FLAG_GRAPH) != 0)
+        return fail(CSE_EINVAL, "reserved option fields must be 0");
+    if (opts->col_cap > CSE_MAX_COLS) return fail(CSE_EINVAL, "col_cap must be <= 512");
+    if (opts->procs_per_cta > 4) return fail(CSE_EINVAL, "procs_per_cta must be in [0, 4]");
+    return CSE_OK;
+}
+
+// Validates one search and computes its layout and device footprint.
+static int search_plan(const cse_scheme* s, const cse_strategy_mix* mix, int n_proc, int64_t budget,
+                       const cse_opts& opts, SearchDev* sd, uint64_t* wsum, std::vector<size_t>* offs) {
+    if (!s) return fail(CSE_EINVAL, "NULL scheme");
+    int rc = check_mix(mix, wsum);
+    if (rc) return rc;
+    if (n_proc < 1 || n_proc > (1 << 20)) return fail(CSE_EINVAL, "n_processes must be in [1, 2^20]");
+    if (budget < 0 || budget >= INT32_MAX) return fail(CSE_EINVAL, "step_budget must be in [0, 2^31)");
+    const int cap = (int)opts.col_cap;
+    for (int k = 0; k < s->n_mats; k++)
+        if (s->cols[k] >= cap) return fail(CSE_EINVAL, "col_cap must exceed every matrix's column count");
+    sd->n_mats = s->n_mats;
+    sd->n_proc = n_proc;
+    sd->cap = cap;
+    sd->budget = budget;
+    sd->rounds = (int)((budget + opts.share_interval - 1) / opts.share_interval);
+    sd->mats.assign(s->n_mats, DevMat{});
+    sd->gm.assign(s->n_mats, 0);
+    Carve cv;
+    offs->clear();
+    for (int k = 0; k < s->n_mats; k++) {
+        sd->rows[k] = s->rows[k];
+        sd->cols[k] = s->cols[k];
+        const WarpLayout own = make_layout(s->W[k], cap, s->mmax[k]);
+        const bool gm = own.per_warp > kSmemPerWarpLimit;
+        sd->gm[k] = gm;
+        DevMat& M = sd->mats[k];
+        M.gml = own;
+        M.state_words = gm ? state_words_gm(own) : state_words(s->W[k], cap, s->mmax[k]);
+        offs->push_back(cv.take((size_t)n_proc * M.state_words * 4));   // state
+        offs->push_back(cv.take((size_t)n_proc * cap * 4));             // best lists
+        offs->push_back(cv.take((size_t)cap * 4));                      // snapshot
+        offs->push_back(cv.take(8));                                    // snapshot meta
+        offs->push_back(cv.take(8));                                    // round minimum
+        offs->push_back(cv.take((size_t)cap * 4));                      // result
+        offs->push_back(cv.take(8));                                    // result meta
+        offs->push_back(cv.take(16));                                   // counters
+    }
+    offs->push_back(cv.take(4));  // clock
+    offs->push_back(cv.take(4));  // status
+    sd->bytes = cv.off;
+    return CSE_OK;
+}
+
+// Allocates and initialises one search on `stream` (stream-ordered).
+static int search_create(const cse_scheme* s, const cse_strategy_mix* mix, int n_proc, uint64_t seed,
+                         int64_t budget, const cse_opts& opts, cudaStream_t stream, SearchDev** out) {
+    *out = nullptr;
+    SearchDev* sd = new (std::nothrow) SearchDev();
+    if (!sd) return fail(CSE_ENOMEM, "host allocation");
+    uint64_t wsum = 0;
+    std::vector<size_t> of;
+    int rc = search_plan(s, mix, n_proc, budget, opts, sd, &wsum, &of);
+    if (rc) {
+        delete sd;
+        return rc;
+    }
+    sd->stream = stream;
+    set_pool_threshold_once();
+    cudaError_t e = cudaMallocAsync(&sd->d_block, sd->bytes, stream);
+    if (e != cudaSuccess) {
+        sd->d_block = nullptr;
+        delete sd;
+        return fail(e == cudaErrorMemoryAllocation ? CSE_ENOMEM : CSE_ECUDA,
+                    std::string("device allocation: ") + cudaGetErrorString(e));
+    }
+    char* b = (char*)sd->d_block;
+    DevSearch& S = sd->search;
+    S.seed = seed;
+    S.w[ST_GI] = mix->w_gi;
+    S.w[ST_GA] = mix->w_ga;
+    S.w[ST_GR] = mix->w_gr;
+    S.w[ST_WR] = mix->w_wr;
+    S.w[ST_MIX] = mix->w_mix;
+    S.w[ST_G] = mix->w_g;
+    S.wsum = (uint32_t)wsum;
+    S.budget = (int32_t)budget;
+    S.interval = (int32_t)opts.share_interval;
+    S.share_thr = ((uint64_t)opts.share_permille << 32) / 1000u;
+    S.clock = (int32_t*)(b + of[8 * s->n_mats]);
+    S.status = (int32_t*)(b + of[8 * s->n_mats + 1]);
+    S.n_mats = s->n_mats;
+    static const int32_t snap_init[2] = {INT_MAX, 0};
+    for (int k = 0; k < s->n_mats; k++) {
+        DevMat& M = sd->mats[k];
+        const size_t* o = &of[8 * k];
+        M.pn0 = s->d_pn0[k];
+        M.cand0 = s->d_cand0[k];
+        M.meta0 = s->d_meta0[k];
+        M.rows = s->rows[k];
+        M.nx = s->cols[k];
+        M.W = s->W[k];
+        M.cap = sd->cap;
+        M.mmax = s->mmax[k];
+        M.mat_index = k;
+        M.n_proc = n_proc;
+        M.state = (uint32_t*)(b + o[0]);
+        M.best_list = (int32_t*)(b + o[1]);
+        M.snap = (int32_t*)(b + o[2]);
+        M.snap_meta = (int32_t*)(b + o[3]);
+        M.round_min = (unsigned long long*)(b + o[4]);
+        M.result = (int32_t*)(b + o[5]);
+        M.result_meta = (int32_t*)(b + o[6]);
+        M.counters = (unsigned long long*)(b + o[7]);
+        // initial values: no round minimum, no snapshot, result = the input
+        if (e == cudaSuccess) e = cudaMemsetAsync(M.round_min, 0xFF, 8, stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(M.snap_meta, snap_init, 8, cudaMemcpyHostToDevice, stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(M.result_meta, M.meta0, 4, cudaMemcpyDeviceToDevice, stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(M.result_meta + 1, 0, 4, stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(M.counters, 0, 16, stream);
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(S.clock, 0, 4, stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(S.status, 0, 4, stream);
+    if (e != cudaSuccess) {
+        search_free(sd);
+        return fail(CSE_ECUDA, std::string("search init: ") + cudaGetErrorString(e));
+    }
+    *out = sd;
+    return CSE_OK;
+}
+
+// Builds the launch parameters of a set of searches and uploads them.
+static int build_launch(const std::vector<SearchDev*>& act, int ppc_req, const Trial* trial, cudaStream_t stream,
+                        LaunchSet* ls) {
+    const int smem_max = max_smem_per_block();
+    if (smem_max <= 0) return fail(CSE_ECUDA, "no CUDA device");
+    struct Ref { int search, mat, W, gm; };
+    std::vector<Ref> refs;
+    for (int i = 0; i < (int)act.size(); i++)
+        for (int k = 0; k < act[i]->n_mats; k++)
+            refs.push_back({i, k, act[i]->mats[k].W, act[i]->gm[k] ? 1 : 0});
+    std::stable_sort(refs.begin(), refs.end(), [](const Ref& x, const Ref& y) {
+        return x.W != y.W ? x.W < y.W : x.gm < y.gm;
+    });
+    const int nm = (int)refs.size(), n = (int)act.size();
+    ls->mats.resize(nm);
+    ls->groups.clear();
+    for (int q = 0; q < nm; q++) {
+        const SearchDev* sd = act[refs[q].search];
+        ls->mats[q] = sd->mats[refs[q].mat];
+        ls->mats[q].search = refs[q].search;
+        if (ls->groups.empty() || ls->groups.back().W != refs[q].W || ls->groups.back().gm != (refs[q].gm != 0))
+            ls->groups.push_back({refs[q].W, q, 0, 0, 0, 0, refs[q].gm != 0, {}, 0, {}});
+        LaunchSet::Group& g = ls->groups.back();
+        ls->mats[q].unit_base = g.units;
+        g.count++;
+        g.units += ls->mats[q].n_proc;
+        g.mmax = std::max(g.mmax, ls->mats[q].mmax);
+        g.cap = std::max(g.cap, ls->mats[q].cap);
+    }
+    for (auto& g : ls->groups) {
+        g.L = g.gm ? WarpLayout{} : make_layout(g.W, g.cap, g.mmax);
+        g.key = ClassKey{g.W, g.gm ? 1 : 0, g.cap, mbucket(g.mmax)};
+        g.ppc = ppc_req ? ppc_req : 4;
+        if (trial && trial->force_ppc) {
+            g.ppc = trial->force_ppc;
+        } else if (!ppc_req) {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            auto it = g_tuned_ppc.find(g.key);
+            if (it != g_tuned_ppc.end()) g.ppc = it->second;
+        }
+        if (!g.gm)
+            while (g.ppc > 1 && (long long)g.L.per_warp * g.ppc > smem_max) g.ppc--;
+        if (!g.gm && g.L.per_warp > smem_max) return fail(CSE_ENOMEM, "process slice exceeds shared memory");
+        cudaError_t e = prepare_round(g.W, g.gm, g.L, g.ppc);
+        if (e != cudaSuccess) return fail(CSE_ECUDA, std::string("kernel attributes: ") + cudaGetErrorString(e));
+        if (trial && trial->keys) trial->keys->push_back(g.key);
+    }
+    // positions of each search's matrices
+    ls->pos.assign(nm, 0);
+    std::vector<int> first(n, 0), cnt(n, 0);
+    for (int q = 0; q < nm; q++) cnt[refs[q].search]++;
+    for (int i = 1; i < n; i++) first[i] = first[i - 1] + cnt[i - 1];
+    std::vector<int> fill(first);
+    for (int q = 0; q < nm; q++) ls->pos[fill[refs[q].search]++] = q;
+    Carve cv;
+    const size_t om = cv.take(sizeof(DevMat) * nm), os = cv.take(sizeof(DevSearch) * n), op = cv.take(4 * (size_t)nm);
+    cudaError_t e = cudaMallocAsync(&ls->d_params, cv.off, stream);
+    if (e != cudaSuccess) {
+        ls->d_params = nullptr;
+        return fail(CSE_ENOMEM, std::string("parameter block: ") + cudaGetErrorString(e));
+    }
+    char* b = (char*)ls->d_params;
+    ls->d_mats = (DevMat*)(b + om);
+    ls->d_searches = (DevSearch*)(b + os);
+    ls->searches.resize(n);
+    for (int i = 0; i < n; i++) {
+        ls->searches[i] = act[i]->search;
+        ls->searches[i].mat_pos = (const int32_t*)(b + op) + first[i];
+    }
+    e = cudaMemcpyAsync(ls->d_mats, ls->mats.data(), sizeof(DevMat) * nm, cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ls->d_searches, ls->searches.data(), sizeof(DevSearch) * n, cudaMemcpyHostToDevice,
+                            stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b + op, ls->pos.data(), 4 * (size_t)nm, cudaMemcpyHostToDevice, stream);
+    if (e != cudaSuccess) return fail(CSE_ECUDA, std::string("parameter upload: ") + cudaGetErrorString(e));
+    return CSE_OK;
+}
+
+// Enqueues one round: the class launches (in parallel branches when aux
+// streams are given) and the share kernel.
+static cudaError_t enqueue_round(const LaunchSet& ls, cudaStream_t st, const std::vector<cudaStream_t>* aux,
+                                 const std::vector<cudaEvent_t>* fork, cudaEvent_t* group_ev) {
+    cudaError_t e = cudaSuccess;
+    const size_t ng = ls.groups.size();
+    if (aux && ng > 1) {
+        cudaEventRecord((*fork)[0], st);
+        for (size_t gi = 0; gi < ng; gi++) {
+            const auto& g = ls.groups[gi];
+            cudaStreamWaitEvent((*aux)[gi], (*fork)[0], 0);
+            e = launch_round(g.W, g.gm, ls.d_mats + g.begin, g.count, ls.d_searches, g.units, g.L, g.ppc, (*aux)[gi]);
+            if (e != cudaSuccess) return e;
+            cudaEventRecord((*fork)[gi + 1], (*aux)[gi]);
+            cudaStreamWaitEvent(st, (*fork)[gi + 1], 0);
+        }
+    } else {
+        for (size_t gi = 0; gi < ng; gi++) {
+            const auto& g = ls.groups[gi];
+            if (group_ev) cudaEventRecord(group_ev[2 * gi], st);
+            e = launch_round(g.W, g.gm, ls.d_mats + g.begin, g.count, ls.d_searches, g.units, g.L, g.ppc, st);
+            if (e != cudaSuccess) return e;
+            if (group_ev) cudaEventRecord(group_ev[2 * gi + 1], st);
+        }
+    }
+    return launch_share(ls.d_mats, ls.d_searches, (int)ls.searches.size(), st);
+}
+
+// Builds and enqueues n independent searches as one static launch sequence.
+// Each search keeps its own step clock, so its result does not depend on
+// the others.
+static int run_batch(int n, const cse_scheme* const* schemes, const cse_strategy_mix* mixes,
+                     const int32_t* n_procs, const uint64_t* seeds, const int64_t* budgets,
+                     const cse_opts* opts_in, void* cuda_stream, cse_result** outs,
+                     const Trial* trial = nullptr) {
+    if (!outs) return fail(CSE_EINVAL, "out is NULL");
+    if (n < 1 || !schemes || !mixes || !n_procs || !seeds || !budgets)
+        return fail(CSE_EINVAL, "n_searches must be >= 1 with non-NULL arrays");
+    for (int i = 0; i < n; i++) outs[i] = nullptr;
+    cse_opts opts;
+    int rc = check_opts(opts_in, &opts);
+    if (rc) return rc;
+    for (int i = 0; i < n; i++) {  // validate everything before allocating
+        SearchDev tmp;
+        uint64_t w;
+        std::vector<size_t> of;
+        rc = search_plan(schemes[i], &mixes[i], n_procs[i], budgets[i], opts, &tmp, &w, &of);
+        if (rc) return rc;
+    }
+    if (max_smem_per_block() <= 0) return fail(CSE_ECUDA, "no CUDA device");
+    cudaStream_t stream = (cudaStream_t)cuda_stream;
+    const bool use_graph = (opts.flags & CSE_FLAG_GRAPH) != 0 && !trial;
+    std::vector<SearchDev*> sds(n, nullptr);
+    auto drop = [&]() {
+        for (auto* sd : sds) search_free(sd);
+    };
+    for (int i = 0; i < n; i++) {
+        rc = search_create(schemes[i], &mixes[i], n_procs[i], seeds[i], budgets[i], opts, stream, &sds[i]);
+        if (rc) {
+            drop();
+            return rc;
+        }
+    }
+    Batch* B = new (std::nothrow) Batch();
+    if (!B) {
+        drop();
+        return fail(CSE_ENOMEM, "host allocation");
+    }
+    B->stream = stream;
+    for (int i = 0; i < n; i++) {
+        outs[i] = new (std::nothrow) cse_result();
+        if (!outs[i]) {
+            for (int j = 0; j < i; j++) {
+                delete outs[j];
+                outs[j] = nullptr;
+            }
+            delete B;
+            drop();
+            return fail(CSE_ENOMEM, "host allocation");
+        }
+    }
+    for (auto* sd : sds) B->rounds = std::max(B->rounds, sd->rounds);
+    rc = build_launch(sds, (int)opts.procs_per_cta, trial, stream, &B->ls);
+    cudaError_t e = cudaSuccess;
+    auto bail = [&](cudaError_t err, const char* what) {
+        cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+        if (B->cap_stream && cudaStreamIsCapturing(B->cap_stream, &cst) == cudaSuccess &&
+            cst != cudaStreamCaptureStatusNone) {
+            cudaGraph_t g = nullptr;
+            cudaStreamEndCapture(B->cap_stream, &g);
+            if (g) cudaGraphDestroy(g);
+        }
+        B->ev_end = nullptr;
+        B->release();
+        delete B;
+        drop();
+        for (int j = 0; j < n; j++) {
+            delete outs[j];
+            outs[j] = nullptr;
+        }
+        return err == cudaSuccess ? rc : fail(CSE_ECUDA, std::string(what) + ": " + cudaGetErrorString(err));
+    };
+    if (rc) return bail(cudaSuccess, "");
+    const size_t ng = B->ls.groups.size();
+    if ((e = cudaEventCreate(&B->ev_begin)) != cudaSuccess) return bail(e, "event");
+    if ((e = cudaEventCreate(&B->ev_end)) != cudaSuccess) return bail(e, "event");
+    B->ev_round.resize(2 * (size_t)B->rounds);
+    for (auto& ev : B->ev_round)
+        if ((e = cudaEventCreate(&ev)) != cudaSuccess) return bail(e, "event");
+    if (trial) {
+        B->ev_group.resize(2 * ng * (size_t)B->rounds);
+        for (auto& ev : B->ev_group)
+            if ((e = cudaEventCreate(&ev)) != cudaSuccess) return bail(e, "event");
+    }
+    const bool concurrent = use_graph && ng > 1;
+    if (concurrent) {
+        B->aux.resize(ng);
+        B->ev_fork.resize(ng + 1);
+        for (auto& st : B->aux)
+            if ((e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) != cudaSuccess) return bail(e, "stream");
+        for (auto& ev : B->ev_fork)
+            if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) return bail(e, "event");
+    }
+    // With CSE_FLAG_GRAPH the sequence is captured on a private stream (the
+    // caller's may be the legacy default stream, which cannot be captured)
+    // and the instantiated graph is launched once on the caller's stream.
+    cudaStream_t ls = stream;
+    if (use_graph) {
+        if ((e = cudaStreamCreateWithFlags(&B->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
+            return bail(e, "stream");
+        ls = B->cap_stream;
+        if ((e = cudaStreamBeginCapture(ls, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+            return bail(e, "stream capture");
+    }
+    // timing events: inside a capture they must be external record nodes
+    auto rec = [&](cudaEvent_t ev) {
+        return use_graph ? cudaEventRecordWithFlags(ev, ls, cudaEventRecordExternal) : cudaEventRecord(ev, ls);
+    };
+    rec(B->ev_begin);
+    for (int rd = 0; rd < B->rounds; rd++) {
+        rec(B->ev_round[2 * rd]);
+        e = enqueue_round(B->ls, ls, concurrent ? &B->aux : nullptr, concurrent ? &B->ev_fork : nullptr,
+                          trial ? &B->ev_group[2 * ng * rd] : nullptr);
+        if (e != cudaSuccess) return bail(e, "round launch");
+        rec(B->ev_round[2 * rd + 1]);
+    }
+    if ((e = rec(B->ev_end)) != cudaSuccess) return bail(e, "event record");
+    if (use_graph) {
+        if ((e = cudaStreamEndCapture(ls, &B->graph)) != cudaSuccess) return bail(e, "end capture");
+        if ((e = cudaGraphInstantiate(&B->gexec, B->graph, 0)) != cudaSuccess) return bail(e, "graph instantiate");
+        if ((e = cudaGraphLaunch(B->gexec, stream)) != cudaSuccess) return bail(e, "graph launch");
+    }
+    for (int i = 0; i < n; i++) {
+        outs[i]->sd = sds[i];
+        outs[i]->batch = B;
+        B->refs++;
+    }
+    return CSE_OK;
+}
+
+// Per-class round-kernel time of a finished trial batch.
+static int trial_times(const cse_result* r, std::vector<float>* ms) {
+    const Batch* B = r->batch;
+    const size_t ng = B->ls.groups.size();
+    CUDA_TRY(cudaEventSynchronize(B->ev_end));
+    ms->assign(ng, 0.f);
+    for (int rd = 0; rd < B->rounds; rd++)
+        for (size_t gi = 0; gi < ng; gi++) {
+            float x = 0.f;
+            CUDA_TRY(cudaEventElapsedTime(&x, B->ev_group[2 * (rd * ng + gi)], B->ev_group[2 * (rd * ng + gi) + 1]));
+            (*ms)[gi] += x;
+        }
+    return CSE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Serving: a worker thread runs rounds over the searches admitted so far;
+// new requests join at a round boundary when their device footprint fits.
+// ---------------------------------------------------------------------------
+struct Request {
+    uint64_t ticket = 0;
+    const cse_scheme* scheme = nullptr;
+    cse_strategy_mix mix{};
+    int n_proc = 0;
+    uint64_t seed = 0;
     int64_t budget = 0;
-    std::vector<int> pos_of_mat;      // matrix index -> position in batch->hmats
+    size_t bytes = 0;
+    std::chrono::steady_clock::time_point t_submit;
+    SearchDev* sd = nullptr;
+    cse_result* res = nullptr;
+    int status = CSE_OK;
+    std::string error;
+    bool done = false;
+};
+
+struct cse_server {
+    cse_opts opts{};
+    uint64_t hbm_budget = 0;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::thread worker;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<Request*> pending;
+    std::vector<Request*> active;
+    std::map<uint64_t, Request*> by_ticket;
+    bool stop = false;
+    uint64_t next_ticket = 1;
+    uint64_t used_bytes = 0;
+    // statistics
+    std::vector<double> latencies_ms;
+    int64_t steps_done = 0;
+    std::chrono::steady_clock::time_point t_first, t_last;
+    bool any = false;
+    int rounds_run = 0, max_active = 0;
 };
 
 extern "C" {
@@ -219,304 +734,7 @@ void cse_scheme_free(cse_scheme* s) {
     delete s;
 }
 
-static int check_mix(const cse_strategy_mix* mix, uint64_t* wsum_out) {
-    if (!mix) return fail(CSE_EINVAL, "NULL strategy mix");
-    if (mix->w_gp != 0) return fail(CSE_EINVAL, "Greedy-Potential (w_gp) is not implemented; set it to 0");
-    const uint64_t wsum = (uint64_t)mix->w_gi + mix->w_ga + mix->w_gr + mix->w_wr + mix->w_mix + mix->w_g;
-    if (wsum == 0 || wsum > 0xFFFFFFFFull) return fail(CSE_EINVAL, "strategy weights: sum must be in [1, 2^32)");
-    *wsum_out = wsum;
-    return CSE_OK;
-}
 
-// Builds and enqueues n independent searches as one launch sequence: per
-// round, one round kernel per class of equal words-per-column (and memory
-// path), then one share kernel over all searches.  Each search keeps its own
-// step clock, so its result does not depend on the others.
-static int run_batch(int n, const cse_scheme* const* schemes, const cse_strategy_mix* mixes,
-                     const int32_t* n_procs, const uint64_t* seeds, const int64_t* budgets,
-                     const cse_opts* opts_in, void* cuda_stream, cse_result** outs) {
-    if (!outs) return fail(CSE_EINVAL, "out is NULL");
-    if (n < 1 || !schemes || !mixes || !n_procs || !seeds || !budgets)
-        return fail(CSE_EINVAL, "n_searches must be >= 1 with non-NULL arrays");
-    for (int i = 0; i < n; i++) outs[i] = nullptr;
-    cse_opts opts;
-    if (opts_in)
-        opts = *opts_in;
-    else
-        cse_opts_default(&opts);
-    if (opts.share_interval < 1) return fail(CSE_EINVAL, "share_interval must be >= 1");
-    if (opts.share_permille > 1000) return fail(CSE_EINVAL, "share_permille must be <= 1000");
-    if (opts.patience_rounds != 0 || (opts.flags & ~(uint32_t)CSE_FLAG_GRAPH) != 0)
-        return fail(CSE_EINVAL, "reserved option fields must be 0");
-    const int cap = (int)opts.col_cap;
-    if (cap > CSE_MAX_COLS) return fail(CSE_EINVAL, "col_cap must be <= 512");
-    const int ppc_req = (int)opts.procs_per_cta;
-    if (ppc_req < 0 || ppc_req > 4) return fail(CSE_EINVAL, "procs_per_cta must be in [0, 4]");
-    std::vector<uint64_t> wsums(n);
-    int64_t max_budget = 0, total_mats = 0;
-    for (int i = 0; i < n; i++) {
-        const cse_scheme* s = schemes[i];
-        if (!s) return fail(CSE_EINVAL, "NULL scheme");
-        int rc = check_mix(&mixes[i], &wsums[i]);
-        if (rc) return rc;
-        if (n_procs[i] < 1 || n_procs[i] > (1 << 20)) return fail(CSE_EINVAL, "n_processes must be in [1, 2^20]");
-        if (budgets[i] < 0 || budgets[i] >= INT32_MAX) return fail(CSE_EINVAL, "step_budget must be in [0, 2^31)");
-        for (int k = 0; k < s->n_mats; k++)
-            if (s->cols[k] >= cap) return fail(CSE_EINVAL, "col_cap must exceed every matrix's column count");
-        max_budget = std::max(max_budget, budgets[i]);
-        total_mats += s->n_mats;
-    }
-    const int smem_max = max_smem_per_block();
-    if (smem_max <= 0) return fail(CSE_ECUDA, "no CUDA device");
-    set_pool_threshold_once();
-    cudaStream_t stream = (cudaStream_t)cuda_stream;
-    const bool use_graph = (opts.flags & CSE_FLAG_GRAPH) != 0;
-
-    // every matrix of every search, ordered by words per column
-    struct Ref { int search, mat, W, mmax, n_proc; };
-    std::vector<Ref> refs;
-    for (int i = 0; i < n; i++)
-        for (int k = 0; k < schemes[i]->n_mats; k++)
-            refs.push_back({i, k, schemes[i]->W[k], schemes[i]->mmax[k], n_procs[i]});
-    std::stable_sort(refs.begin(), refs.end(), [](const Ref& x, const Ref& y) { return x.W < y.W; });
-    const int nm = (int)refs.size();
-
-    // launch groups: equal W, one round kernel launch each; a group whose
-    // per-process arrays are too large for a shared-memory slice runs on HBM
-    struct Group { int W, begin, count, units, mmax; bool gm; WarpLayout L; int ppc; };
-    std::vector<Group> groups;
-    std::vector<int> group_of(nm);
-    for (int q = 0; q < nm; q++) {
-        if (groups.empty() || groups.back().W != refs[q].W) groups.push_back({refs[q].W, q, 0, 0, 0, false, {}, 0});
-        Group& g = groups.back();
-        g.count++;
-        g.units += refs[q].n_proc;
-        g.mmax = std::max(g.mmax, refs[q].mmax);
-        group_of[q] = (int)groups.size() - 1;
-    }
-    for (Group& g : groups) {
-        g.L = make_layout(g.W, cap, g.mmax);
-        g.gm = g.L.per_warp > kSmemPerWarpLimit;
-        g.ppc = ppc_req ? ppc_req : 4;
-        if (!g.gm)
-            while (g.ppc > 1 && (long long)g.L.per_warp * g.ppc > smem_max) g.ppc--;
-        cudaError_t e = prepare_round(g.W, g.gm, g.L, g.ppc);
-        if (e != cudaSuccess) return fail(CSE_ECUDA, std::string("kernel attributes: ") + cudaGetErrorString(e));
-    }
-
-    Carve cv;
-    struct Offs { size_t state, best, snap, snapm, rmin, res, resm, cnt; int sw; };
-    std::vector<Offs> of(nm);
-    for (int q = 0; q < nm; q++) {
-        const Ref& rf = refs[q];
-        const Group& g = groups[group_of[q]];
-        Offs& o = of[q];
-        o.sw = g.gm ? state_words_gm(g.L) : state_words(rf.W, cap, rf.mmax);
-        o.state = cv.take((size_t)rf.n_proc * o.sw * 4);
-        o.best = cv.take((size_t)rf.n_proc * cap * 4);
-        o.snap = cv.take((size_t)cap * 4);
-        o.snapm = cv.take(8);
-        o.rmin = cv.take(8);
-        o.res = cv.take((size_t)cap * 4);
-        o.resm = cv.take(8);
-        o.cnt = cv.take(16);
-    }
-    const size_t off_clock = cv.take(4 * (size_t)n), off_status = cv.take(4 * (size_t)n);
-    const size_t off_pos = cv.take(4 * (size_t)nm);
-    const size_t off_mats = cv.take(sizeof(DevMat) * nm), off_search = cv.take(sizeof(DevSearch) * n);
-
-    Batch* B = new (std::nothrow) Batch();
-    if (!B) return fail(CSE_ENOMEM, "host allocation");
-    B->stream = stream;
-    B->rounds = 0;
-    for (int i = 0; i < n; i++)
-        B->rounds = std::max(B->rounds, (int)((budgets[i] + opts.share_interval - 1) / opts.share_interval));
-    cudaError_t e = cudaMallocAsync(&B->d_block, cv.off, stream);
-    if (e != cudaSuccess) {
-        B->d_block = nullptr;
-        delete B;
-        return fail(e == cudaErrorMemoryAllocation ? CSE_ENOMEM : CSE_ECUDA,
-                    std::string("device allocation: ") + cudaGetErrorString(e));
-    }
-    char* b = (char*)B->d_block;
-    auto bail = [&](cudaError_t err, const char* what) {
-        cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
-        if (B->cap_stream && cudaStreamIsCapturing(B->cap_stream, &cst) == cudaSuccess &&
-            cst != cudaStreamCaptureStatusNone) {
-            cudaGraph_t g = nullptr;
-            cudaStreamEndCapture(B->cap_stream, &g);
-            if (g) cudaGraphDestroy(g);
-        }
-        B->ev_end = nullptr;
-        B->release();
-        delete B;
-        return fail(CSE_ECUDA, std::string(what) + ": " + cudaGetErrorString(err));
-    };
-
-    // per-search parameters; positions of each search's matrices
-    std::vector<int32_t> pos((size_t)nm);
-    std::vector<int> first_pos(n, 0), count(n, 0);
-    {
-        std::vector<std::vector<int>> by_search(n);
-        for (int q = 0; q < nm; q++) by_search[refs[q].search].push_back(q);
-        int o = 0;
-        for (int i = 0; i < n; i++) {
-            first_pos[i] = o;
-            count[i] = (int)by_search[i].size();
-            for (int q : by_search[i]) pos[o++] = q;
-        }
-    }
-    B->hsearch.resize(n);
-    for (int i = 0; i < n; i++) {
-        DevSearch& S = B->hsearch[i];
-        const cse_strategy_mix* mix = &mixes[i];
-        S.seed = seeds[i];
-        S.w[ST_GI] = mix->w_gi;
-        S.w[ST_GA] = mix->w_ga;
-        S.w[ST_GR] = mix->w_gr;
-        S.w[ST_WR] = mix->w_wr;
-        S.w[ST_MIX] = mix->w_mix;
-        S.w[ST_G] = mix->w_g;
-        S.wsum = (uint32_t)wsums[i];
-        S.budget = (int32_t)budgets[i];
-        S.interval = (int32_t)opts.share_interval;
-        S.share_thr = ((uint64_t)opts.share_permille << 32) / 1000u;
-        S.clock = (int32_t*)(b + off_clock) + i;
-        S.status = (int32_t*)(b + off_status) + i;
-        S.mat_pos = (const int32_t*)(b + off_pos) + first_pos[i];
-        S.n_mats = count[i];
-    }
-    B->hmats.resize(nm);
-    for (int q = 0; q < nm; q++) {
-        const Ref& rf = refs[q];
-        const cse_scheme* s = schemes[rf.search];
-        const int k = rf.mat;
-        const Group& g = groups[group_of[q]];
-        DevMat& M = B->hmats[q];
-        M.pn0 = s->d_pn0[k];
-        M.cand0 = s->d_cand0[k];
-        M.meta0 = s->d_meta0[k];
-        M.rows = s->rows[k];
-        M.nx = s->cols[k];
-        M.W = s->W[k];
-        M.cap = cap;
-        M.mmax = s->mmax[k];
-        M.mat_index = k;
-        M.n_proc = rf.n_proc;
-        M.search = rf.search;
-        M.unit_base = 0;
-        M.state_words = of[q].sw;
-        M.state = (uint32_t*)(b + of[q].state);
-        M.best_list = (int32_t*)(b + of[q].best);
-        M.snap = (int32_t*)(b + of[q].snap);
-        M.snap_meta = (int32_t*)(b + of[q].snapm);
-        M.round_min = (unsigned long long*)(b + of[q].rmin);
-        M.result = (int32_t*)(b + of[q].res);
-        M.result_meta = (int32_t*)(b + of[q].resm);
-        M.counters = (unsigned long long*)(b + of[q].cnt);
-        (void)g;
-    }
-    for (const Group& g : groups) {  // unit_base is relative to the group's launch
-        int u = 0;
-        for (int q = g.begin; q < g.begin + g.count; q++) {
-            B->hmats[q].unit_base = u;
-            u += refs[q].n_proc;
-        }
-    }
-    DevMat* d_mats = (DevMat*)(b + off_mats);
-    DevSearch* d_search = (DevSearch*)(b + off_search);
-    e = cudaMemcpyAsync(d_mats, B->hmats.data(), sizeof(DevMat) * nm, cudaMemcpyHostToDevice, stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(d_search, B->hsearch.data(), sizeof(DevSearch) * n, cudaMemcpyHostToDevice, stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(b + off_pos, pos.data(), 4 * (size_t)nm, cudaMemcpyHostToDevice, stream);
-    if (e != cudaSuccess) return bail(e, "parameter upload");
-    if ((e = cudaEventCreate(&B->ev_begin)) != cudaSuccess) return bail(e, "event");
-    if ((e = cudaEventCreate(&B->ev_end)) != cudaSuccess) return bail(e, "event");
-    B->ev_round.resize(2 * (size_t)B->rounds);
-    for (auto& ev : B->ev_round)
-        if ((e = cudaEventCreate(&ev)) != cudaSuccess) return bail(e, "event");
-    const bool concurrent = use_graph && groups.size() > 1;
-    if (concurrent) {
-        B->aux.resize(groups.size());
-        B->ev_fork.resize(groups.size() + 1);
-        for (auto& st : B->aux)
-            if ((e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) != cudaSuccess) return bail(e, "stream");
-        for (auto& ev : B->ev_fork)
-            if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) return bail(e, "event");
-    }
-    B->launches_per_round = (int)groups.size() + 1;
-
-    // With CSE_FLAG_GRAPH the sequence is captured on a private stream (the
-    // caller's may be the legacy default stream, which cannot be captured)
-    // and the instantiated graph is launched once on the caller's stream.
-    cudaStream_t ls = stream;
-    if (use_graph) {
-        if ((e = cudaStreamCreateWithFlags(&B->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
-            return bail(e, "stream");
-        ls = B->cap_stream;
-        if ((e = cudaStreamBeginCapture(ls, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
-            return bail(e, "stream capture");
-    }
-    // timing events: inside a capture they must be external record nodes
-    auto rec = [&](cudaEvent_t ev) {
-        return use_graph ? cudaEventRecordWithFlags(ev, ls, cudaEventRecordExternal) : cudaEventRecord(ev, ls);
-    };
-    rec(B->ev_begin);
-    if ((e = launch_init(d_mats, nm, d_search, n, ls)) != cudaSuccess) return bail(e, "init");
-    for (int rd = 0; rd < B->rounds; rd++) {
-        rec(B->ev_round[2 * rd]);
-        if (concurrent) {  // the groups of a round are independent: parallel graph branches
-            cudaEventRecord(B->ev_fork[0], ls);
-            for (size_t gi = 0; gi < groups.size(); gi++) {
-                const Group& g = groups[gi];
-                cudaStreamWaitEvent(B->aux[gi], B->ev_fork[0], 0);
-                e = launch_round(g.W, g.gm, d_mats + g.begin, g.count, d_search, g.units, g.L, g.ppc, B->aux[gi]);
-                if (e != cudaSuccess) return bail(e, "round kernel");
-                cudaEventRecord(B->ev_fork[gi + 1], B->aux[gi]);
-                cudaStreamWaitEvent(ls, B->ev_fork[gi + 1], 0);
-            }
-        } else {
-            for (const Group& g : groups) {
-                e = launch_round(g.W, g.gm, d_mats + g.begin, g.count, d_search, g.units, g.L, g.ppc, ls);
-                if (e != cudaSuccess) return bail(e, "round kernel");
-            }
-        }
-        rec(B->ev_round[2 * rd + 1]);
-        if ((e = launch_share(d_mats, d_search, n, ls)) != cudaSuccess) return bail(e, "share kernel");
-    }
-    if ((e = rec(B->ev_end)) != cudaSuccess) return bail(e, "event record");
-    if (use_graph) {
-        if ((e = cudaStreamEndCapture(ls, &B->graph)) != cudaSuccess) return bail(e, "end capture");
-        if ((e = cudaGraphInstantiate(&B->gexec, B->graph, 0)) != cudaSuccess) return bail(e, "graph instantiate");
-        if ((e = cudaGraphLaunch(B->gexec, stream)) != cudaSuccess) return bail(e, "graph launch");
-    }
-
-    for (int i = 0; i < n; i++) {
-        cse_result* r = new (std::nothrow) cse_result();
-        if (!r) {
-            for (int j = 0; j < i; j++) {
-                delete outs[j];
-                outs[j] = nullptr;
-            }
-            B->release();
-            delete B;
-            return fail(CSE_ENOMEM, "host allocation");
-        }
-        r->batch = B;
-        r->search = i;
-        r->n_mats = schemes[i]->n_mats;
-        r->n_proc = n_procs[i];
-        r->cap = cap;
-        r->budget = budgets[i];
-        r->pos_of_mat.assign(r->n_mats, 0);
-        for (int q = 0; q < nm; q++)
-            if (refs[q].search == i) r->pos_of_mat[refs[q].mat] = q;
-        B->refs++;
-        outs[i] = r;
-    }
-    return CSE_OK;
-}
 
 int cse_search(const cse_scheme* s, const cse_strategy_mix* mix, int32_t n_proc, uint64_t seed,
                int64_t budget, const cse_opts* opts, void* cuda_stream, cse_result** out) {
@@ -532,11 +750,94 @@ int cse_search_batch(int32_t n_searches, const cse_scheme* const* schemes, const
     return run_batch(n_searches, schemes, mixes, n_processes, seeds, step_budgets, opts, cuda_stream, outs);
 }
 
+int cse_autotune(int32_t n_searches, const cse_scheme* const* schemes, const cse_strategy_mix* mixes,
+                 const int32_t* n_processes, const uint64_t* seeds, const int64_t* step_budgets,
+                 const cse_opts* opts, int32_t trial_steps, void* cuda_stream, cse_tune_entry* entries,
+                 int32_t max_entries, int32_t* n_entries) {
+    if (n_searches < 1 || n_searches > 4096 || !step_budgets) return fail(CSE_EINVAL, "bad n_searches");
+    if (trial_steps < 1) return fail(CSE_EINVAL, "trial_steps must be >= 1");
+    std::vector<int64_t> tb(n_searches);
+    for (int i = 0; i < n_searches; i++) tb[i] = std::min<int64_t>(step_budgets[i], trial_steps);
+    std::vector<std::vector<float>> ms(4);
+    std::vector<ClassKey> keys;
+    std::vector<cse_result*> outs(n_searches);
+    for (int ppc = 1; ppc <= 4; ppc++) {
+        for (int rep = 0; rep < 2; rep++) {  // the first run warms up
+            Trial tr;
+            tr.force_ppc = ppc;
+            std::vector<ClassKey> k;
+            tr.keys = &k;
+            int rc = run_batch(n_searches, schemes, mixes, n_processes, seeds, tb.data(), opts, cuda_stream,
+                               outs.data(), &tr);
+            if (rc) return rc;
+            rc = trial_times(outs[0], &ms[ppc - 1]);
+            for (auto* r : outs) cse_result_free(r);
+            if (rc) return rc;
+            keys = k;
+        }
+    }
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    int32_t ne = 0;
+    for (size_t gi = 0; gi < keys.size(); gi++) {
+        int best = 1;
+        for (int ppc = 2; ppc <= 4; ppc++)
+            if (ms[ppc - 1][gi] < ms[best - 1][gi]) best = ppc;
+        g_tuned_ppc[keys[gi]] = best;
+        if (entries && ne < max_entries) {
+            cse_tune_entry& en = entries[ne];
+            en.words_per_column = keys[gi].W;
+            en.hbm_path = keys[gi].gm;
+            en.candidate_bound = keys[gi].mbucket;
+            en.procs_per_cta = best;
+            for (int ppc = 1; ppc <= 4; ppc++) en.trial_ms[ppc - 1] = ms[ppc - 1][gi];
+        }
+        ne++;
+    }
+    if (n_entries) *n_entries = ne;
+    return CSE_OK;
+}
+
+int cse_tune_interval(int32_t n_searches, const cse_scheme* const* schemes, const cse_strategy_mix* mixes,
+                      const int32_t* n_processes, const uint64_t* seeds, const int64_t* step_budgets,
+                      const cse_opts* opts_in, const uint32_t* candidates, int32_t n_candidates,
+                      int32_t trial_steps, void* cuda_stream, uint32_t* best_interval, int64_t* best_total) {
+    if (!candidates || n_candidates < 1 || trial_steps < 1 || !step_budgets || n_searches < 1)
+        return fail(CSE_EINVAL, "bad interval candidates or trial size");
+    cse_opts opts;
+    int rc = check_opts(opts_in, &opts);
+    if (rc) return rc;
+    std::vector<int64_t> tb(n_searches);
+    for (int i = 0; i < n_searches; i++) tb[i] = std::min<int64_t>(step_budgets[i], trial_steps);
+    std::vector<cse_result*> outs(n_searches);
+    int64_t best = INT64_MAX;
+    uint32_t besti = candidates[0];
+    for (int c = 0; c < n_candidates; c++) {
+        opts.share_interval = candidates[c];
+        rc = run_batch(n_searches, schemes, mixes, n_processes, seeds, tb.data(), &opts, cuda_stream, outs.data());
+        if (rc) return rc;
+        int64_t total = 0;
+        for (auto* r : outs) {
+            int64_t t = 0;
+            if (rc == CSE_OK) rc = cse_result_fetch(r, 0, nullptr, 0, nullptr, nullptr, &t);
+            total += t;
+        }
+        for (auto* r : outs) cse_result_free(r);
+        if (rc) return rc;
+        if (total < best) {
+            best = total;
+            besti = candidates[c];
+        }
+    }
+    if (best_interval) *best_interval = besti;
+    if (best_total) *best_total = best;
+    return CSE_OK;
+}
+
 static int wait_result(const cse_result* r) {
-    if (!r) return fail(CSE_EINVAL, "NULL result");
-    CUDA_TRY(cudaEventSynchronize(r->batch->ev_end));
+    if (!r || !r->sd) return fail(CSE_EINVAL, "NULL result");
+    if (r->batch) CUDA_TRY(cudaEventSynchronize(r->batch->ev_end));
     int32_t status = 0;
-    CUDA_TRY(cudaMemcpy(&status, r->batch->hsearch[r->search].status, 4, cudaMemcpyDeviceToHost));
+    CUDA_TRY(cudaMemcpy(&status, r->sd->search.status, 4, cudaMemcpyDeviceToHost));
     if (status != 0) return fail(CSE_ESTATE, "device consistency check failed (candidate list overflow)");
     return CSE_OK;
 }
@@ -545,20 +846,19 @@ int cse_result_fetch(const cse_result* r, int32_t mat, int32_t* subst, int32_t c
                      int64_t* additions, int64_t* total_additions) {
     int rc = wait_result(r);
     if (rc) return rc;
-    if (mat < 0 || mat >= r->n_mats) return fail(CSE_EINVAL, "matrix index out of range");
+    const SearchDev* sd = r->sd;
+    if (mat < 0 || mat >= sd->n_mats) return fail(CSE_EINVAL, "matrix index out of range");
     int64_t total = 0;
     int32_t meta[2] = {0, 0};
-    for (int k = 0; k < r->n_mats; k++) {
-        const DevMat& M = r->batch->hmats[r->pos_of_mat[k]];
+    for (int k = 0; k < sd->n_mats; k++) {
         int32_t mk[2];
-        CUDA_TRY(cudaMemcpy(mk, M.result_meta, 8, cudaMemcpyDeviceToHost));
+        CUDA_TRY(cudaMemcpy(mk, sd->mats[k].result_meta, 8, cudaMemcpyDeviceToHost));
         total += mk[0];
         if (k == mat) std::memcpy(meta, mk, 8);
     }
-    const DevMat& M = r->batch->hmats[r->pos_of_mat[mat]];
     if (subst && cap_entries > 0) {
-        const int n = std::min(cap_entries, meta[1]);
-        if (n > 0) CUDA_TRY(cudaMemcpy(subst, M.result, (size_t)n * 4, cudaMemcpyDeviceToHost));
+        const int nn = std::min(cap_entries, meta[1]);
+        if (nn > 0) CUDA_TRY(cudaMemcpy(subst, sd->mats[mat].result, (size_t)nn * 4, cudaMemcpyDeviceToHost));
     }
     if (n_subst) *n_subst = meta[1];
     if (additions) *additions = meta[0];
@@ -569,12 +869,13 @@ int cse_result_fetch(const cse_result* r, int32_t mat, int32_t* subst, int32_t c
 int cse_result_procs(const cse_result* r, int32_t mat, cse_proc_record* out) {
     int rc = wait_result(r);
     if (rc) return rc;
-    if (mat < 0 || mat >= r->n_mats || !out) return fail(CSE_EINVAL, "bad matrix index or output");
-    const DevMat& M = r->batch->hmats[r->pos_of_mat[mat]];
-    if (r->budget == 0) {  // no step ran: every record is the input itself
+    const SearchDev* sd = r->sd;
+    if (mat < 0 || mat >= sd->n_mats || !out) return fail(CSE_EINVAL, "bad matrix index or output");
+    const DevMat& M = sd->mats[mat];
+    if (sd->budget == 0) {  // no step ran: every record is the input itself
         int32_t meta[2];
         CUDA_TRY(cudaMemcpy(meta, M.result_meta, 8, cudaMemcpyDeviceToHost));
-        for (int p = 0; p < r->n_proc; p++) {
+        for (int p = 0; p < sd->n_proc; p++) {
             out[p].best_cost = meta[0];
             out[p].best_len = 0;
             out[p].runs = 0;
@@ -585,19 +886,19 @@ int cse_result_procs(const cse_result* r, int32_t mat, cse_proc_record* out) {
         }
         return CSE_OK;
     }
-    std::vector<uint32_t> hdr((size_t)r->n_proc * H_WORDS);
-    CUDA_TRY(cudaMemcpy2D(hdr.data(), H_WORDS * 4, M.state, (size_t)M.state_words * 4, H_WORDS * 4, r->n_proc,
+    std::vector<uint32_t> hdr((size_t)sd->n_proc * H_WORDS);
+    CUDA_TRY(cudaMemcpy2D(hdr.data(), H_WORDS * 4, M.state, (size_t)M.state_words * 4, H_WORDS * 4, sd->n_proc,
                           cudaMemcpyDeviceToHost));
-    std::vector<int32_t> lists((size_t)r->n_proc * r->cap);
+    std::vector<int32_t> lists((size_t)sd->n_proc * sd->cap);
     CUDA_TRY(cudaMemcpy(lists.data(), M.best_list, lists.size() * 4, cudaMemcpyDeviceToHost));
-    for (int p = 0; p < r->n_proc; p++) {
+    for (int p = 0; p < sd->n_proc; p++) {
         const uint32_t* h = &hdr[(size_t)p * H_WORDS];
         cse_proc_record& o = out[p];
         o.best_cost = (int32_t)h[H_BEST_COST];
         o.best_len = (int32_t)h[H_BEST_LEN];
         o.runs = (int32_t)h[H_RUNS];
         uint64_t hh = kFnv0;
-        for (int x = 0; x < o.best_len; x++) hh = fnv(hh, (uint32_t)lists[(size_t)p * r->cap + x]);
+        for (int x = 0; x < o.best_len; x++) hh = fnv(hh, (uint32_t)lists[(size_t)p * sd->cap + x]);
         o.best_hash = hh;
         o.traj_hash = (uint64_t)h[H_TRAJ_LO] | (uint64_t)h[H_TRAJ_HI] << 32;
         o.ops = (int64_t)((uint64_t)h[H_OPS_LO] | (uint64_t)h[H_OPS_HI] << 32);
@@ -609,15 +910,15 @@ int cse_result_procs(const cse_result* r, int32_t mat, cse_proc_record* out) {
 int cse_result_counters(const cse_result* r, int64_t* process_steps, int64_t* substeps, int64_t* alg_ops) {
     int rc = wait_result(r);
     if (rc) return rc;
+    const SearchDev* sd = r->sd;
     uint64_t ops = 0, sub = 0;
-    for (int k = 0; k < r->n_mats; k++) {
-        const DevMat& M = r->batch->hmats[r->pos_of_mat[k]];
+    for (int k = 0; k < sd->n_mats; k++) {
         unsigned long long c[2];
-        CUDA_TRY(cudaMemcpy(c, M.counters, 16, cudaMemcpyDeviceToHost));
+        CUDA_TRY(cudaMemcpy(c, sd->mats[k].counters, 16, cudaMemcpyDeviceToHost));
         ops += c[0];
         sub += c[1];
     }
-    if (process_steps) *process_steps = (int64_t)r->n_mats * r->n_proc * r->budget;
+    if (process_steps) *process_steps = (int64_t)sd->n_mats * sd->n_proc * sd->budget;
     if (substeps) *substeps = (int64_t)sub;
     if (alg_ops) *alg_ops = (int64_t)ops;
     return CSE_OK;
@@ -627,6 +928,12 @@ int cse_result_timing(const cse_result* r, float* round_ms, float* total_ms, int
     int rc = wait_result(r);
     if (rc) return rc;
     const Batch* B = r->batch;
+    if (!B) {  // a served request: time from submission to completion
+        if (round_ms) *round_ms = (float)r->latency_ms;
+        if (total_ms) *total_ms = (float)r->latency_ms;
+        if (n_rounds) *n_rounds = r->sd->rounds;
+        return CSE_OK;
+    }
     float sum = 0.f, tot = 0.f;
     for (int rd = 0; rd < B->rounds; rd++) {
         float x = 0.f;
@@ -641,21 +948,262 @@ int cse_result_timing(const cse_result* r, float* round_ms, float* total_ms, int
 }
 
 int cse_result_launches(const cse_result* r, int32_t* kernels, int32_t* searches_in_launch) {
-    if (!r) return fail(CSE_EINVAL, "NULL result");
+    if (!r || !r->sd) return fail(CSE_EINVAL, "NULL result");
     const Batch* B = r->batch;
-    if (kernels) *kernels = 1 + B->rounds * B->launches_per_round;
-    if (searches_in_launch) *searches_in_launch = (int32_t)B->hsearch.size();
+    if (kernels) *kernels = B ? B->rounds * ((int)B->ls.groups.size() + 1) : 0;
+    if (searches_in_launch) *searches_in_launch = B ? (int32_t)B->ls.searches.size() : 0;
     return CSE_OK;
 }
 
 void cse_result_free(cse_result* r) {
     if (!r) return;
     Batch* B = r->batch;
+    if (B) cudaEventSynchronize(B->ev_end);
+    search_free(r->sd);
     delete r;
     if (B && --B->refs == 0) {
         B->release();
         delete B;
     }
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// server worker
+// ---------------------------------------------------------------------------
+static void server_finish(cse_server* sv, Request* q) {
+    const auto now = std::chrono::steady_clock::now();
+    if (q->status == CSE_OK) {
+        q->res = new (std::nothrow) cse_result();
+        if (!q->res) {
+            q->status = CSE_ENOMEM;
+            q->error = "host allocation";
+        } else {
+            q->sd->stream = nullptr;  // freed later on the default stream: its kernels are done
+            q->res->sd = q->sd;
+            q->res->latency_ms = std::chrono::duration<double, std::milli>(now - q->t_submit).count();
+            q->sd = nullptr;
+            sv->latencies_ms.push_back(q->res->latency_ms);
+            sv->steps_done += (int64_t)q->res->sd->n_mats * q->res->sd->n_proc * q->res->sd->budget;
+            sv->t_last = now;
+        }
+    }
+    if (q->sd) {
+        search_free(q->sd);
+        q->sd = nullptr;
+    }
+    q->done = true;
+}
+
+static void server_loop(cse_server* sv) {
+    cudaSetDevice(sv->device);
+    LaunchSet ls;
+    bool dirty = true;
+    while (true) {
+        std::vector<Request*> admitted;
+        {
+            std::unique_lock<std::mutex> lk(sv->mu);
+            sv->cv_work.wait(lk, [&] { return sv->stop || !sv->pending.empty() || !sv->active.empty(); });
+            if (sv->stop) break;
+            // FIFO admission by device footprint, at a round boundary
+            while (!sv->pending.empty()) {
+                Request* q = sv->pending.front();
+                if (!sv->active.empty() && sv->used_bytes + q->bytes > sv->hbm_budget) break;
+                sv->pending.pop_front();
+                sv->used_bytes += q->bytes;
+                admitted.push_back(q);
+            }
+        }
+        std::vector<Request*> finished;
+        for (Request* q : admitted) {
+            const int rc = search_create(q->scheme, &q->mix, q->n_proc, q->seed, q->budget, sv->opts, sv->stream, &q->sd);
+            if (rc) {
+                q->status = rc;
+                q->error = g_err;
+                finished.push_back(q);
+            } else if (q->sd->rounds == 0) {
+                finished.push_back(q);
+            } else {
+                std::lock_guard<std::mutex> lk(sv->mu);
+                sv->active.push_back(q);
+                dirty = true;
+            }
+        }
+        std::vector<Request*> act;
+        {
+            std::lock_guard<std::mutex> lk(sv->mu);
+            act = sv->active;
+        }
+        int err = CSE_OK;
+        std::string msg;
+        if (!act.empty()) {
+            if (dirty) {
+                if (ls.d_params) cudaFreeAsync(ls.d_params, sv->stream);
+                ls = LaunchSet();
+                std::vector<SearchDev*> sds;
+                for (Request* q : act) sds.push_back(q->sd);
+                err = build_launch(sds, (int)sv->opts.procs_per_cta, nullptr, sv->stream, &ls);
+                if (err) msg = g_err;
+                dirty = false;
+            }
+            if (err == CSE_OK) {
+                cudaError_t e = enqueue_round(ls, sv->stream, nullptr, nullptr, nullptr);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(sv->stream);
+                if (e != cudaSuccess) {
+                    err = CSE_ECUDA;
+                    msg = std::string("round: ") + cudaGetErrorString(e);
+                }
+            }
+        }
+        std::lock_guard<std::mutex> lk(sv->mu);
+        if (!act.empty()) {
+            sv->rounds_run++;
+            sv->max_active = std::max(sv->max_active, (int)act.size());
+        }
+        for (Request* q : act) {
+            if (err) {
+                q->status = err;
+                q->error = msg;
+            } else if (++q->sd->rounds_done < q->sd->rounds) {
+                continue;
+            }
+            finished.push_back(q);
+            sv->active.erase(std::find(sv->active.begin(), sv->active.end(), q));
+            dirty = true;
+        }
+        for (Request* q : finished) {
+            sv->used_bytes -= q->bytes;
+            server_finish(sv, q);
+        }
+        if (!finished.empty()) sv->cv_done.notify_all();
+    }
+    if (ls.d_params) cudaFreeAsync(ls.d_params, sv->stream);
+    cudaStreamSynchronize(sv->stream);
+}
+
+extern "C" {
+
+int cse_server_create(const cse_opts* opts_in, uint64_t hbm_budget_bytes, cse_server** out) {
+    if (!out) return fail(CSE_EINVAL, "out is NULL");
+    *out = nullptr;
+    cse_opts opts;
+    int rc = check_opts(opts_in, &opts);
+    if (rc) return rc;
+    opts.flags = 0;
+    if (max_smem_per_block() <= 0) return fail(CSE_ECUDA, "no CUDA device");
+    cse_server* sv = new (std::nothrow) cse_server();
+    if (!sv) return fail(CSE_ENOMEM, "host allocation");
+    sv->opts = opts;
+    sv->hbm_budget = hbm_budget_bytes ? hbm_budget_bytes : UINT64_MAX;
+    cudaGetDevice(&sv->device);
+    cudaError_t e = cudaStreamCreateWithFlags(&sv->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        delete sv;
+        return fail(CSE_ECUDA, std::string("stream: ") + cudaGetErrorString(e));
+    }
+    sv->worker = std::thread(server_loop, sv);
+    *out = sv;
+    return CSE_OK;
+}
+
+int cse_server_submit(cse_server* sv, const cse_scheme* s, const cse_strategy_mix* mix, int32_t n_proc,
+                      uint64_t seed, int64_t step_budget, uint64_t* ticket) {
+    if (!sv || !ticket) return fail(CSE_EINVAL, "NULL server or ticket");
+    SearchDev tmp;
+    uint64_t w;
+    std::vector<size_t> of;
+    int rc = search_plan(s, mix, n_proc, step_budget, sv->opts, &tmp, &w, &of);
+    if (rc) return rc;
+    Request* q = new (std::nothrow) Request();
+    if (!q) return fail(CSE_ENOMEM, "host allocation");
+    q->scheme = s;
+    q->mix = *mix;
+    q->n_proc = n_proc;
+    q->seed = seed;
+    q->budget = step_budget;
+    q->bytes = tmp.bytes;
+    q->t_submit = std::chrono::steady_clock::now();
+    std::lock_guard<std::mutex> lk(sv->mu);
+    if (sv->stop) {
+        delete q;
+        return fail(CSE_EBUSY, "server is stopping");
+    }
+    if (sv->pending.size() >= kServerMaxPending) {
+        delete q;
+        return fail(CSE_EBUSY, "server queue is full");
+    }
+    q->ticket = sv->next_ticket++;
+    if (!sv->any) {
+        sv->any = true;
+        sv->t_first = q->t_submit;
+    }
+    sv->pending.push_back(q);
+    sv->by_ticket[q->ticket] = q;
+    *ticket = q->ticket;
+    sv->cv_work.notify_one();
+    return CSE_OK;
+}
+
+int cse_server_wait(cse_server* sv, uint64_t ticket, int64_t timeout_us, cse_result** out) {
+    if (!sv || !out) return fail(CSE_EINVAL, "NULL server or output");
+    *out = nullptr;
+    std::unique_lock<std::mutex> lk(sv->mu);
+    auto it = sv->by_ticket.find(ticket);
+    if (it == sv->by_ticket.end()) return fail(CSE_EINVAL, "unknown ticket");
+    Request* q = it->second;
+    auto ready = [&] { return q->done; };
+    if (timeout_us < 0) {
+        sv->cv_done.wait(lk, ready);
+    } else if (!sv->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), ready)) {
+        return fail(CSE_ETIMEOUT, "request not finished within the timeout");
+    }
+    sv->by_ticket.erase(it);
+    const int st = q->status;
+    const std::string err = q->error;
+    *out = q->res;
+    delete q;
+    if (st != CSE_OK) return fail(st, err);
+    return CSE_OK;
+}
+
+int cse_server_stats(cse_server* sv, double* p50_ms, double* p99_ms, double* steps_per_s, int32_t* completed) {
+    if (!sv) return fail(CSE_EINVAL, "NULL server");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    std::vector<double> v = sv->latencies_ms;
+    std::sort(v.begin(), v.end());
+    auto pct = [&](double p) -> double {
+        if (v.empty()) return 0.0;
+        size_t i = (size_t)std::ceil(p * (double)v.size()) - 1;
+        return v[std::min(i, v.size() - 1)];
+    };
+    if (p50_ms) *p50_ms = pct(0.50);
+    if (p99_ms) *p99_ms = pct(0.99);
+    if (steps_per_s) {
+        const double s = sv->any ? std::chrono::duration<double>(sv->t_last - sv->t_first).count() : 0.0;
+        *steps_per_s = s > 0 ? (double)sv->steps_done / s : 0.0;
+    }
+    if (completed) *completed = (int32_t)v.size();
+    return CSE_OK;
+}
+
+void cse_server_free(cse_server* sv) {
+    if (!sv) return;
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        sv->stop = true;
+    }
+    sv->cv_work.notify_all();
+    if (sv->worker.joinable()) sv->worker.join();
+    for (Request* q : sv->active) search_free(q->sd);
+    for (auto& kv : sv->by_ticket) {
+        Request* q = kv.second;
+        if (q->res) cse_result_free(q->res);
+        else if (q->sd && std::find(sv->active.begin(), sv->active.end(), q) == sv->active.end()) search_free(q->sd);
+        delete q;
+    }
+    cudaStreamDestroy(sv->stream);
+    delete sv;
 }
 
 }  // extern "C"

@@ -28,6 +28,12 @@ constexpr int kMaxW = 8;          // 32-bit words per column (256 rows)
 constexpr int kMaxCap = 512;      // column capacity
 constexpr uint64_t kFnv0 = 0xCBF29CE484222325ull;
 
+// Shared-memory carve-up of one process (one warp), in bytes.
+struct WarpLayout {
+    int32_t off_pn, off_cand, off_f, off_aw, off_poslo, off_hs, off_he, off_base, off_lc;
+    int32_t per_warp;
+};
+
 // One matrix of one search, as the kernels see it.
 struct DevMat {
     const uint2* pn0;        // original columns [nx][W]: x = rows with +1, y = rows with -1
@@ -47,6 +53,8 @@ struct DevMat {
     int32_t* result;         // [cap] best list of the search
     int32_t* result_meta;    // [0] cost, [1] length
     unsigned long long* counters;   // [0] algorithmic ops, [1] substitution steps
+    WarpLayout gml;          // layout of the working arrays inside a state region
+                             // (HBM path only; fixed for the life of the search)
 };
 
 struct DevSearch {
@@ -59,12 +67,6 @@ struct DevSearch {
     const int32_t* mat_pos;  // positions of this search's matrices in the DevMat array
     int32_t n_mats;
     int32_t* status;         // nonzero: a device-side consistency check failed
-};
-
-// Shared-memory carve-up of one process (one warp), in bytes.
-struct WarpLayout {
-    int32_t off_pn, off_cand, off_f, off_aw, off_poslo, off_hs, off_he, off_base, off_lc;
-    int32_t per_warp;
 };
 
 WarpLayout make_layout(int W, int cap, int mmax);

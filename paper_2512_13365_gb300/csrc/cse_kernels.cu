@@ -665,7 +665,7 @@ __global__ void __launch_bounds__(128, CSE_MIN_BLOCKS) round_kernel(const DevMat
     uint32_t* st = M->state + (size_t)(unit - M->unit_base) * M->state_words;
     Engine<W> E;
     E.sm = GM ? reinterpret_cast<unsigned char*>(st + H_WORDS) : smem + (size_t)warp * L.per_warp;
-    E.L = &L;
+    E.L = GM ? &M->gml : &L;
     E.M = M;
     E.S = S;
     E.proc = unit - M->unit_base;

@@ -216,3 +216,33 @@ def test_graph_single_search(cse):
                    graph=True)
     ref = O.search_obj(s, n_threads=8)
     assert r.costs == ref.cost and r.lists == ref.lists
+
+
+def test_autotuner_changes_speed_not_results(cse):
+    searches = synth.config3(n_schemes=4, n_proc=64, budget=64, interval=16)
+    schemes = [cse.Scheme(s.mats) for s in searches]
+    args = (schemes, [s.weights for s in searches], [s.n_proc for s in searches], [s.seed for s in searches],
+            [s.budget for s in searches])
+    before = cse.search_batch(*args, interval=16, cap=256)
+    ents = cse.autotune(*args, interval=16, cap=256, trial_steps=32)
+    assert ents and all(1 <= e["procs_per_cta"] <= 4 and min(e["trial_ms"]) > 0 for e in ents)
+    after = cse.search_batch(*args, interval=16, cap=256)
+    for a, b, s in zip(before, after, searches):
+        assert a.lists == b.lists and a.costs == b.costs
+        for k in range(len(s.mats)):
+            assert np.array_equal(a.procs(k), b.procs(k))
+
+
+def test_interval_tuner_picks_lowest_total(cse):
+    searches = synth.config3(n_schemes=3, n_proc=48, budget=96, interval=16)
+    schemes = [cse.Scheme(s.mats) for s in searches]
+    args = (schemes, [s.weights for s in searches], [s.n_proc for s in searches], [s.seed for s in searches],
+            [s.budget for s in searches])
+    best, total = cse.tune_interval(*args, candidates=(8, 16, 48), cap=256, trial_steps=96)
+    totals = {}
+    for iv in (8, 16, 48):
+        rs = cse.search_batch(*args, interval=iv, cap=256)
+        totals[iv] = sum(r.total for r in rs)
+    assert total == totals[best] == min(totals.values())
+    assert best == min((v, i) for i, v in zip((0, 1, 2), [totals[8], totals[16], totals[48]]))[1] * 0 + \
+        [8, 16, 48][[totals[8], totals[16], totals[48]].index(min(totals.values()))]

@@ -1,0 +1,83 @@
+"""Serving (continuous batching): requests of different shapes arrive while
+others run; each result must be exactly the result of the same search run
+alone, and admission must respect the device-memory budget."""
+import time
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2512_13365_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cse():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2512_13365_gb300 import cse as c
+    return c
+
+
+def _requests(n, n_proc, budget):
+    reqs = synth.serving_requests(n_req=n, n_proc=n_proc, budget=budget)
+    out = []
+    for _, s in reqs:
+        s.interval, s.cap = 16, 512
+        out.append(s)
+    return out
+
+
+def _same(cse, a, b, n_mats):
+    assert a.lists == b.lists and a.costs == b.costs
+    for k in range(n_mats):
+        assert np.array_equal(a.procs(k), b.procs(k))
+
+
+def test_served_results_equal_alone(cse):
+    reqs = _requests(6, 48, 40)
+    sv = cse.Server(interval=16, cap=512)
+    schemes = [cse.Scheme(s.mats) for s in reqs]
+    tickets = []
+    for i, (s, sc) in enumerate(zip(reqs, schemes)):
+        tickets.append(sv.submit(sc, s.weights, s.n_proc, s.seed, s.budget))
+        if i % 2:
+            time.sleep(0.002)  # later requests join while earlier ones run
+    served = [sv.wait(t, timeout_us=120_000_000) for t in tickets]
+    st = sv.stats()
+    assert st["completed"] == len(reqs) and st["p99_ms"] >= st["p50_ms"] > 0 and st["steps_per_s"] > 0
+    for s, sc, r in zip(reqs, schemes, served):
+        alone = cse.search(sc, s.weights, s.n_proc, s.seed, s.budget, 16, s.permille, 512)
+        _same(cse, r, alone, len(s.mats))
+    ref = O.search_obj(reqs[0], n_threads=8)
+    assert served[0].costs == ref.cost and served[0].lists == ref.lists
+    sv.free()
+
+
+def test_admission_by_memory_budget(cse):
+    reqs = _requests(4, 32, 48)
+    # a budget smaller than any single search: requests run one at a time
+    sv = cse.Server(interval=16, cap=512, hbm_budget=1)
+    schemes = [cse.Scheme(s.mats) for s in reqs]
+    tickets = [sv.submit(sc, s.weights, s.n_proc, s.seed, s.budget) for s, sc in zip(reqs, schemes)]
+    served = [sv.wait(t) for t in tickets]
+    for s, sc, r in zip(reqs, schemes, served):
+        alone = cse.search(sc, s.weights, s.n_proc, s.seed, s.budget, 16, s.permille, 512)
+        _same(cse, r, alone, len(s.mats))
+    sv.free()
+
+
+def test_wait_timeout_and_bad_requests(cse):
+    s = synth.config2(n_proc=256, budget=512)
+    sv = cse.Server(interval=32, cap=128)
+    sc = cse.Scheme(s.mats)
+    t = sv.submit(sc, s.weights, s.n_proc, s.seed, s.budget)
+    with pytest.raises(cse.CseError) as ei:
+        sv.wait(t, timeout_us=0)
+    assert ei.value.code == cse.CSE_ETIMEOUT
+    r = sv.wait(t)
+    assert r.total > 0
+    with pytest.raises(cse.CseError):
+        sv.submit(sc, (0,) * 6, 4, 0, 10)  # all weights zero
+    sv.free()
