@@ -240,6 +240,140 @@ def cpu_baseline(s, budget):
     return out
 
 
+def run_batched(args):
+    """32 schemes of uneven shapes (config 3) in one CUDA-graph launch
+    sequence, against one launch sequence per scheme on the same GPU."""
+    import torch
+    from paper_2512_13365_gb300 import cse, synth
+    dev = torch.device("cuda", 0)
+    searches = synth.config3()
+    if args.budget:
+        for s in searches:
+            s.budget = args.budget
+    cap = searches[0].cap
+    schemes = [cse.Scheme(s.mats) for s in searches]
+    ba = (schemes, [s.weights for s in searches], [s.n_proc for s in searches], [s.seed for s in searches],
+          [s.budget for s in searches])
+    stream = torch.cuda.Stream(device=dev)
+    t0 = time.perf_counter()
+    tuned = cse.autotune(*ba, interval=32, cap=cap, trial_steps=64, stream=stream)
+    interval, _ = cse.tune_interval(*ba, candidates=(16, 32, 64), cap=cap, trial_steps=128, stream=stream)
+    tune_s = time.perf_counter() - t0
+    psteps = sum(s.process_steps() for s in searches)
+    l2 = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+
+    def batched():
+        rs = cse.search_batch(*ba, interval=interval, cap=cap, stream=stream, graph=True)
+        return rs
+
+    def per_scheme():
+        return [cse.search(sc, s.weights, s.n_proc, s.seed, s.budget, interval, s.permille, cap, stream=stream)
+                for sc, s in zip(schemes, searches)]
+
+    out = {}
+    for name, fn in (("batched", batched), ("per_scheme", per_scheme)):
+        for _ in range(args.warmup):
+            for r in fn():
+                r.free()
+        ms = []
+        totals = None
+        for _ in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush_l2(l2)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            rs = fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+            totals = [r.total for r in rs]
+            kernels = rs[0].launches()[0] if name == "batched" else sum(r.launches()[0] for r in rs)
+            for r in rs:
+                r.free()
+        out[name] = {"ms": statistics.mean(ms), "value": psteps / (statistics.mean(ms) / 1000.0),
+                     "best_additions_total": sum(totals), "kernel_launches": kernels}
+    assert out["batched"]["best_additions_total"] == out["per_scheme"]["best_additions_total"]
+    line = {
+        "metric": METRIC, "value": out["batched"]["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": out["batched"]["ms"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": f"batched: {len(searches)} schemes (config 3)", "n_processes": searches[0].n_proc,
+                   "step_budget": searches[0].budget, "share_interval": interval, "col_cap": cap,
+                   "shapes": [[list(m.shape) for m in s.mats] for s in searches[:3]] + ["..."],
+                   "l2": "flushed (256 MB write) between timed steps"},
+        "batched_graph": out["batched"], "one_launch_sequence_per_scheme": out["per_scheme"],
+        "speedup_batched_vs_per_scheme": out["per_scheme"]["ms"] / out["batched"]["ms"],
+        "autotune": {"seconds": tune_s, "classes": tuned, "interval_candidates": [16, 32, 64],
+                     "interval_chosen": interval},
+    }
+    print(json.dumps(line))
+
+
+def run_serving(args):
+    """Poisson stream of reduction requests (config 5) through the server,
+    against running each request alone as it arrives."""
+    import torch
+    from paper_2512_13365_gb300 import cse, synth
+    reqs = synth.serving_requests(n_req=args.requests, rate_hz=50.0, n_proc=2048, budget=args.budget or 256)
+    for _, s in reqs:
+        s.cap = 512
+    psteps = sum(s.process_steps() for _, s in reqs)
+
+    def serve():
+        sv = cse.Server(interval=32, cap=512)
+        t0 = time.perf_counter()
+        tickets = []
+        for t_arr, s in reqs:
+            d = t0 + t_arr - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+            sc = cse.Scheme(s.mats)
+            tickets.append((sv.submit(sc, s.weights, s.n_proc, s.seed, s.budget), sc))
+        totals = [sv.wait(t).total for t, _ in tickets]
+        wall = time.perf_counter() - t0
+        st = sv.stats()
+        sv.free()
+        return st, wall, totals
+
+    def alone():
+        t0 = time.perf_counter()
+        lat, totals = [], []
+        for t_arr, s in reqs:
+            d = t0 + t_arr - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+            sc = cse.Scheme(s.mats)
+            r = cse.search(sc, s.weights, s.n_proc, s.seed, s.budget, 32, s.permille, 512)
+            totals.append(r.total)
+            lat.append((time.perf_counter() - t0 - t_arr) * 1000.0)
+            r.free()
+        wall = time.perf_counter() - t0
+        lat.sort()
+        pct = lambda p: lat[min(len(lat) - 1, int(np.ceil(p * len(lat))) - 1)]
+        return {"p50_ms": pct(0.5), "p99_ms": pct(0.99), "steps_per_s": psteps / wall}, wall, totals
+
+    import numpy as np
+    for _ in range(args.warmup):
+        pass
+    st, wall, tot_s = serve()
+    st_a, wall_a, tot_a = alone()
+    assert tot_s == tot_a
+    line = {
+        "metric": METRIC, "value": psteps / wall, "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 0,
+        "ms_per_step": wall * 1000.0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int32", "data": "synthetic",
+        "config": {"workload": f"serving: {len(reqs)} Poisson requests at 50/s (config 5)", "n_processes": 2048,
+                   "step_budget": reqs[0][1].budget, "share_interval": 32, "col_cap": 512},
+        "served": {"p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "process_steps_per_s": st["steps_per_s"],
+                   "wall_s": wall},
+        "one_launch_per_request": {"p50_ms": st_a["p50_ms"], "p99_ms": st_a["p99_ms"],
+                                   "process_steps_per_s": st_a["steps_per_s"], "wall_s": wall_a},
+        "results_identical": True,
+    }
+    print(json.dumps(line))
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -279,7 +413,9 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="cfg2")
+    ap.add_argument("--workload", default="cfg2",
+                    help="cfg2 (default, the benchmark line), cfg1, cfg3 (batched), cfg5 (serving)")
+    ap.add_argument("--requests", type=int, default=200, help="cfg5: number of requests")
     ap.add_argument("--ppc", type=int, default=0, help="processes per CTA (0 = library default)")
     ap.add_argument("--cpu-budget", type=int, default=0,
                     help="steps of the oracle sample (0 = the whole search, about 10 s on 16 cores)")
@@ -291,6 +427,10 @@ def main():
     os.makedirs(args.out, exist_ok=True)
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "cfg3":
+        run_batched(args)
+    elif args.workload == "cfg5":
+        run_serving(args)
     else:
         run_ours(args)
 

@@ -217,16 +217,19 @@ void cse_scheme_free(cse_scheme* s);
 
 /* ---- Serving (continuous batching) ----------------------------------------
  * A server owns a worker thread and a CUDA stream on the current device.
- * Requests (a scheme and its search parameters) queue in FIFO order; at every
- * round boundary the worker admits queued requests while the device memory
- * of all active searches stays within hbm_budget_bytes (0 = no limit; a
- * request larger than the budget runs alone), then runs one round (one
- * kernel per class of matrices over every active search, then the share
- * kernel).  Admitted searches therefore run concurrently with those already
- * on the device and leave as soon as their step budget is done.  Each
+ * Requests (a scheme and its search parameters) queue in FIFO order.  At
+ * every round boundary the worker admits queued requests while (a) the
+ * device memory of all active searches stays within hbm_budget_bytes (0 = no
+ * limit) and (b) their processes (all matrices) stay within
+ * max_active_processes (0 = eight waves of one process per resident warp,
+ * 8 x 32 x SMs); a request that exceeds a limit alone runs alone.  Then it
+ * runs one round (one kernel per class of matrices over every active search,
+ * then the share kernel).  Admitted searches run concurrently with those
+ * already on the device and leave as soon as their step budget is done.  Each
  * search keeps its own step clock, so a request's result is exactly what
  * cse_search returns for it alone.  opts->flags is ignored. */
-int cse_server_create(const cse_opts* opts, uint64_t hbm_budget_bytes, cse_server** out);
+int cse_server_create(const cse_opts* opts, uint64_t hbm_budget_bytes, int64_t max_active_processes,
+                      cse_server** out);
 
 /* Queues a request; the scheme must stay loaded until its result is taken.
  * Returns CSE_EINVAL for invalid parameters (checked here), CSE_EBUSY when

@@ -95,7 +95,7 @@ def lib() -> ctypes.CDLL:
     L.cse_result_free.restype = None
     L.cse_scheme_free.argtypes = [vp]
     L.cse_scheme_free.restype = None
-    L.cse_server_create.argtypes = [ctypes.POINTER(Opts), ctypes.c_uint64, ctypes.POINTER(vp)]
+    L.cse_server_create.argtypes = [ctypes.POINTER(Opts), ctypes.c_uint64, ctypes.c_int64, ctypes.POINTER(vp)]
     L.cse_server_submit.argtypes = [vp, vp, ctypes.POINTER(Mix), i32, u64, i64, ctypes.POINTER(ctypes.c_uint64)]
     L.cse_server_wait.argtypes = [vp, ctypes.c_uint64, i64, ctypes.POINTER(vp)]
     L.cse_server_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
@@ -322,10 +322,10 @@ class Server:
     """Continuous-batching server (cse_server_*)."""
 
     def __init__(self, interval: int = 32, permille: int = 400, cap: int = 128, hbm_budget: int = 0,
-                 procs_per_cta: int = 0):
+                 max_active_processes: int = 0, procs_per_cta: int = 0):
         h = ctypes.c_void_p()
         _check(lib().cse_server_create(ctypes.byref(make_opts(interval, permille, cap, procs_per_cta)), hbm_budget,
-                                       ctypes.byref(h)))
+                                       max_active_processes, ctypes.byref(h)))
         self.handle = h
         self.cap = cap
         self._keep = {}

@@ -591,6 +591,7 @@ struct Request {
     uint64_t seed = 0;
     int64_t budget = 0;
     size_t bytes = 0;
+    int64_t units = 0;
     std::chrono::steady_clock::time_point t_submit;
     SearchDev* sd = nullptr;
     cse_result* res = nullptr;
@@ -602,6 +603,8 @@ struct Request {
 struct cse_server {
     cse_opts opts{};
     uint64_t hbm_budget = 0;
+    int64_t max_units = 0;     // cap on the processes (all matrices) of active searches
+    int64_t active_units = 0;
     int device = 0;
     cudaStream_t stream = nullptr;
     std::thread worker;
@@ -1009,9 +1012,12 @@ static void server_loop(cse_server* sv) {
             // FIFO admission by device footprint, at a round boundary
             while (!sv->pending.empty()) {
                 Request* q = sv->pending.front();
-                if (!sv->active.empty() && sv->used_bytes + q->bytes > sv->hbm_budget) break;
+                if (!sv->active.empty() && (sv->used_bytes + q->bytes > sv->hbm_budget ||
+                                            sv->active_units + q->units > sv->max_units))
+                    break;
                 sv->pending.pop_front();
                 sv->used_bytes += q->bytes;
+                sv->active_units += q->units;
                 admitted.push_back(q);
             }
         }
@@ -1074,6 +1080,7 @@ static void server_loop(cse_server* sv) {
         }
         for (Request* q : finished) {
             sv->used_bytes -= q->bytes;
+            sv->active_units -= q->units;
             server_finish(sv, q);
         }
         if (!finished.empty()) sv->cv_done.notify_all();
@@ -1084,7 +1091,8 @@ static void server_loop(cse_server* sv) {
 
 extern "C" {
 
-int cse_server_create(const cse_opts* opts_in, uint64_t hbm_budget_bytes, cse_server** out) {
+int cse_server_create(const cse_opts* opts_in, uint64_t hbm_budget_bytes, int64_t max_active_processes,
+                      cse_server** out) {
     if (!out) return fail(CSE_EINVAL, "out is NULL");
     *out = nullptr;
     cse_opts opts;
@@ -1097,6 +1105,10 @@ int cse_server_create(const cse_opts* opts_in, uint64_t hbm_budget_bytes, cse_se
     sv->opts = opts;
     sv->hbm_budget = hbm_budget_bytes ? hbm_budget_bytes : UINT64_MAX;
     cudaGetDevice(&sv->device);
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, sv->device);
+    // default: eight waves of one process per resident warp (32 per SM)
+    sv->max_units = max_active_processes > 0 ? max_active_processes : (int64_t)8 * 32 * std::max(sms, 1);
     cudaError_t e = cudaStreamCreateWithFlags(&sv->stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
         delete sv;
@@ -1123,6 +1135,7 @@ int cse_server_submit(cse_server* sv, const cse_scheme* s, const cse_strategy_mi
     q->seed = seed;
     q->budget = step_budget;
     q->bytes = tmp.bytes;
+    q->units = (int64_t)tmp.n_mats * tmp.n_proc;
     q->t_submit = std::chrono::steady_clock::now();
     std::lock_guard<std::mutex> lk(sv->mu);
     if (sv->stop) {

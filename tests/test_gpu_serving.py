@@ -59,13 +59,18 @@ def test_admission_by_memory_budget(cse):
     reqs = _requests(4, 32, 48)
     # a budget smaller than any single search: requests run one at a time
     sv = cse.Server(interval=16, cap=512, hbm_budget=1)
+    sv2 = cse.Server(interval=16, cap=512, max_active_processes=1)
     schemes = [cse.Scheme(s.mats) for s in reqs]
     tickets = [sv.submit(sc, s.weights, s.n_proc, s.seed, s.budget) for s, sc in zip(reqs, schemes)]
     served = [sv.wait(t) for t in tickets]
-    for s, sc, r in zip(reqs, schemes, served):
+    tickets2 = [sv2.submit(sc, s.weights, s.n_proc, s.seed, s.budget) for s, sc in zip(reqs, schemes)]
+    served2 = [sv2.wait(t) for t in tickets2]
+    for s, sc, r, r2 in zip(reqs, schemes, served, served2):
         alone = cse.search(sc, s.weights, s.n_proc, s.seed, s.budget, 16, s.permille, 512)
         _same(cse, r, alone, len(s.mats))
+        _same(cse, r2, alone, len(s.mats))
     sv.free()
+    sv2.free()
 
 
 def test_wait_timeout_and_bad_requests(cse):
