@@ -252,6 +252,35 @@ int cse_server_stats(cse_server* s, double* p50_ms, double* p99_ms, double* step
  * server.  No other call on it may be in progress. */
 void cse_server_free(cse_server* s);
 
+/* ---- A search that allocates no device memory ------------------------------
+ * The paper has no counterpart: this is an integration aid.  Some callers may
+ * not allocate device memory when they run a search -- a host that has handed
+ * the whole device to another framework's memory pool, a latency-critical
+ * loop where an allocation can stall on device-wide synchronisation, a plugin
+ * that only receives device pointers.  cse_search_static runs the same search
+ * as cse_search with every byte of scratch (process states, best lists,
+ * sharing snapshots, launch parameters) taken from one file-scope device
+ * array of CSE_STATIC_SCRATCH_BYTES that every GPU loading this library keeps
+ * until the process exits; it calls no allocation routine.
+ *   - The scheme must already be loaded (cse_scheme_load allocates; do that
+ *     during set-up).
+ *   - d_lists: device buffer of n_mats * col_cap int32; matrix k's best list
+ *     (packed entries) is written at d_lists + k * col_cap.
+ *   - d_meta: device buffer of n_mats * 2 int32; (Cost, length) of matrix k
+ *     at d_meta + 2k.  The values equal cse_result_fetch's for cse_search.
+ *   - A search needing more scratch than CSE_STATIC_SCRATCH_BYTES is refused
+ *     with CSE_ENOMEM before anything runs (the message gives the size).
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - The call enqueues on cuda_stream and waits for the search to finish.
+ *   - All calls share the one array and each re-initialises what it reads;
+ *     calls that overlap on the GPU (for example from two host threads) race
+ *     and corrupt each other. */
+#define CSE_STATIC_SCRATCH_BYTES (32u << 20)
+int cse_search_static(const cse_scheme* s, const cse_strategy_mix* mix, int32_t n_processes, uint64_t seed,
+                      int64_t step_budget, const cse_opts* opts, void* cuda_stream, int32_t* d_lists,
+                      int32_t* d_meta);
+
 /* Message of the last error on the calling thread ("" if none). */
 const char* cse_last_error(void);
 

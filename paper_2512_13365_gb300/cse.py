@@ -56,7 +56,8 @@ _lib = None
 EXPORTS = ["cse_opts_default", "cse_scheme_load", "cse_scheme_load_uvw", "cse_scheme_shape", "cse_search",
            "cse_search_batch", "cse_autotune", "cse_tune_interval", "cse_result_fetch", "cse_result_procs", "cse_result_counters", "cse_result_timing",
            "cse_result_launches", "cse_result_free", "cse_scheme_free", "cse_last_error",
-           "cse_server_create", "cse_server_submit", "cse_server_wait", "cse_server_stats", "cse_server_free"]
+           "cse_server_create", "cse_server_submit", "cse_server_wait", "cse_server_stats", "cse_server_free",
+           "cse_search_static"]
 
 FLAG_GRAPH = 1
 
@@ -100,6 +101,7 @@ def lib() -> ctypes.CDLL:
     L.cse_server_wait.argtypes = [vp, ctypes.c_uint64, i64, ctypes.POINTER(vp)]
     L.cse_server_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                    ctypes.POINTER(ctypes.c_double), pi32]
+    L.cse_search_static.argtypes = [vp, ctypes.POINTER(Mix), i32, u64, i64, ctypes.POINTER(Opts), vp, vp, vp]
     L.cse_server_free.argtypes = [vp]
     L.cse_server_free.restype = None
     for n in EXPORTS:

@@ -92,15 +92,7 @@ struct Trial {
 
 }  // namespace
 
-struct cse_scheme {
-    int n_mats = 0;
-    int rows[CSE_MAX_MATS], cols[CSE_MAX_MATS], W[CSE_MAX_MATS], mmax[CSE_MAX_MATS];
-    int8_t* d_raw[CSE_MAX_MATS];
-    uint2* d_pn0[CSE_MAX_MATS];
-    uint32_t* d_cand0[CSE_MAX_MATS];
-    int32_t* d_meta0[CSE_MAX_MATS];
-    void* d_block = nullptr;
-};
+int cse::set_error(int code, const std::string& msg) { return fail(code, msg); }
 
 // ---------------------------------------------------------------------------
 // One search on the device: its own allocation (process states, best lists,

@@ -3,7 +3,22 @@
 #pragma once
 
 #include <cstdint>
+#include <string>
 #include <cuda_runtime.h>
+
+#include "cse.h"
+
+// A loaded scheme: per matrix the raw rows, the packed columns, the initial
+// candidate list and (A_naive, initial candidate count), all on the device.
+struct cse_scheme {
+    int n_mats = 0;
+    int rows[CSE_MAX_MATS], cols[CSE_MAX_MATS], W[CSE_MAX_MATS], mmax[CSE_MAX_MATS];
+    int8_t* d_raw[CSE_MAX_MATS];
+    uint2* d_pn0[CSE_MAX_MATS];
+    uint32_t* d_cand0[CSE_MAX_MATS];
+    int32_t* d_meta0[CSE_MAX_MATS];
+    void* d_block = nullptr;
+};
 
 namespace cse {
 
@@ -91,5 +106,8 @@ cudaError_t launch_share(const DevMat* mats, const DevSearch* searches, int n_se
 // Sets the launch attributes of a round kernel (call outside stream capture).
 cudaError_t prepare_round(int W, bool gm, const WarpLayout& L, int procs_per_cta);
 int max_smem_per_block();
+
+// Records the calling thread's error message (cse_last_error) and returns code.
+int set_error(int code, const std::string& msg);
 
 }  // namespace cse
