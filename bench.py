@@ -27,13 +27,19 @@ SM_COUNT_NOMINAL = 152
 LANES_PER_SM = 128  # 4 schedulers x 32 lanes: one warp instruction per scheduler per clock
 
 
-def workload(name: str):
+def workload(name: str, procs: int = 0):
     from paper_2512_13365_gb300 import synth
     if name == "cfg1":
-        return synth.config1()
-    if name == "cfg2":
-        return synth.config2()
-    raise SystemExit(f"unknown workload {name}")
+        s = synth.config1()
+    elif name == "cfg2":
+        s = synth.config2()
+    elif name == "cfg4":
+        s = synth.config4()
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    if procs:
+        s.n_proc = procs
+    return s
 
 
 def dist_env():
@@ -108,7 +114,7 @@ def run_ours(args):
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    s = workload(args.workload)
+    s = workload(args.workload, args.procs)
     if args.budget:
         s.budget = args.budget
     s.seed = s.seed + rank  # weak scaling: each rank searches its own seed, no data-path collective
@@ -206,7 +212,7 @@ def run_ours(args):
                 "ms_per_step": statistics.mean(e2e_ms) if e2e_ms else None},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "Tops/s",
                      "frac": achieved / peak_ops, "traffic": None,
-                     "kernel": "round_kernel<1>", "alg_ops_per_launch": ops_per_launch,
+                     "kernel": "round_kernel (all classes of the round)", "alg_ops_per_launch": ops_per_launch,
                      "avg_launch_ms": avg_round_ms,
                      "peak_source": f"{props.multi_processor_count} SMs x {LANES_PER_SM} lanes x {sm_mhz:.0f} MHz"},
         "clocks": clk,
@@ -416,6 +422,7 @@ def main():
     ap.add_argument("--workload", default="cfg2",
                     help="cfg2 (default, the benchmark line), cfg1, cfg3 (batched), cfg5 (serving)")
     ap.add_argument("--requests", type=int, default=200, help="cfg5: number of requests")
+    ap.add_argument("--procs", type=int, default=0, help="override the process count (reduced-scale runs)")
     ap.add_argument("--ppc", type=int, default=0, help="processes per CTA (0 = library default)")
     ap.add_argument("--cpu-budget", type=int, default=0,
                     help="steps of the oracle sample (0 = the whole search, about 10 s on 16 cores)")

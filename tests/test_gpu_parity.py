@@ -246,3 +246,20 @@ def test_interval_tuner_picks_lowest_total(cse):
     assert total == totals[best] == min(totals.values())
     assert best == min((v, i) for i, v in zip((0, 1, 2), [totals[8], totals[16], totals[48]]))[1] * 0 + \
         [8, 16, 48][[totals[8], totals[16], totals[48]].index(min(totals.values()))]
+
+
+def test_large_search_full_process_count_sampled(cse):
+    """(6,6,6:153)-shaped search at its full 65536 processes per matrix, up to
+    the first sharing boundary (32 steps): no snapshot exists yet, so every
+    process is independent and the oracle can replay a sample of them exactly."""
+    s = synth.config4(budget=32)
+    r = cse.search_obj(s)
+    sample = [0, 1, 777, 4095, 31337, 65535]
+    ref = O.search_obj(s, n_threads=8, subset=sample)
+    for k in range(3):
+        got, exp = r.procs(k)[sample], ref.digests[k][sample]
+        for f in FIELDS:
+            assert np.array_equal(got[f], exp[f]), (k, f)
+    # the published result is the best over all processes: never worse than the sample
+    assert all(c <= int(ref.digests[k][sample]["best_cost"].min()) for k, c in enumerate(r.costs))
+    r.free()
