@@ -99,6 +99,19 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def measured_traffic():
+    """DRAM bytes per launch of the round kernel from the last ncu capture,
+    if that capture was taken of the current kernel source; else None."""
+    import hashlib
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "round_kernel_traffic.json")))
+        src = open(os.path.join(ROOT, "paper_2512_13365_gb300", "csrc", "cse_kernels.cu"), "rb").read()
+    except (OSError, ValueError):
+        return None
+    sha = hashlib.sha256(src).hexdigest()[:16]
+    return rec.get("dram_bytes_per_launch") if rec.get("kernel_source_sha256_prefix") == sha else None
+
+
 def flush_l2(buf):
     buf.zero_()
 
@@ -195,7 +208,7 @@ def run_ours(args):
     avg_round_ms = statistics.mean(round_ms) / n_rounds
     ops_per_launch = ops_total / n_rounds
     achieved = ops_per_launch / (avg_round_ms / 1000.0) / 1e12
-    launches_per_search = 1 + n_rounds * 2
+    launches_per_search = n_rounds * 2  # per round: the step engine and the share kernel
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -211,7 +224,8 @@ def run_ours(args):
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": statistics.mean(e2e_ms) if e2e_ms else None},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "Tops/s",
-                     "frac": achieved / peak_ops, "traffic": None,
+                     "frac": achieved / peak_ops, "traffic": measured_traffic(),
+                     "traffic_unit": "bytes per launch (dram read + write, last ncu capture of this kernel source)",
                      "kernel": "round_kernel (all classes of the round)", "alg_ops_per_launch": ops_per_launch,
                      "avg_launch_ms": avg_round_ms,
                      "peak_source": f"{props.multi_processor_count} SMs x {LANES_PER_SM} lanes x {sm_mhz:.0f} MHz"},

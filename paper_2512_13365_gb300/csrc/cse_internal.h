@@ -96,8 +96,6 @@ constexpr int kSmemPerWarpLimit = 24 * 1024;
 // launch error, if any.
 cudaError_t launch_ingest(const int8_t* raw, int rows, int nx, int W, uint2* pn0, uint32_t* cand0,
                           int32_t* meta0, int mmax, cudaStream_t stream);
-cudaError_t launch_init(const DevMat* mats, int n_mats, const DevSearch* searches, int n_searches,
-                        cudaStream_t stream);
 cudaError_t launch_round(int W, bool gm, const DevMat* mats, int n_mats, const DevSearch* searches,
                          int total_units, const WarpLayout& L, int procs_per_cta,
                          cudaStream_t stream);

@@ -798,25 +798,6 @@ __global__ void share_kernel(const DevMat* __restrict__ mats, const DevSearch* _
     if (threadIdx.x == 0) *S->clock = t1;
 }
 
-__global__ void init_kernel(const DevMat* __restrict__ mats, int n_mats,
-                            const DevSearch* __restrict__ searches, int n_searches) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    if (x < n_mats) {
-        const DevMat* M = &mats[x];
-        *M->round_min = ~0ull;
-        M->snap_meta[0] = INT_MAX;
-        M->snap_meta[1] = 0;
-        M->result_meta[0] = M->meta0[0];
-        M->result_meta[1] = 0;
-        M->counters[0] = 0;
-        M->counters[1] = 0;
-    }
-    if (x < n_searches) {
-        *searches[x].clock = 0;
-        *searches[x].status = 0;
-    }
-}
-
 // ---------------------------------------------------------------------------
 // host-side launchers
 // ---------------------------------------------------------------------------
@@ -857,13 +838,6 @@ int state_words_gm(const WarpLayout& L) { return H_WORDS + ((L.per_warp / 4 + 3)
 cudaError_t launch_ingest(const int8_t* raw, int rows, int nx, int W, uint2* pn0, uint32_t* cand0,
                           int32_t* meta0, int mmax, cudaStream_t stream) {
     ingest_kernel<<<1, 32, 0, stream>>>(raw, rows, nx, W, pn0, cand0, meta0, mmax);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_init(const DevMat* mats, int n_mats, const DevSearch* searches, int n_searches,
-                        cudaStream_t stream) {
-    const int n = n_mats > n_searches ? n_mats : n_searches;
-    init_kernel<<<(n + 127) / 128, 128, 0, stream>>>(mats, n_mats, searches, n_searches);
     return cudaGetLastError();
 }
 
