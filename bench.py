@@ -99,6 +99,24 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(x: float, device) -> float:
+    """The largest value of x over all ranks (the slowest rank's time); x on
+    a single process."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: int, world: int, max_ms: float) -> float:
+    """Weak scaling: every rank runs its own search of the same size, so the
+    job processes world * units in the slowest rank's time."""
+    return units_per_rank * world / (max_ms / 1000.0)
+
+
 def measured_traffic():
     """DRAM bytes per launch of the round kernel from the last ncu capture,
     if that capture was taken of the current kernel source; else None."""
@@ -175,13 +193,9 @@ def run_ours(args):
     costs = results[-1].costs
     for r in results:
         r.free()
-    ms = statistics.mean(step_ms)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(statistics.mean(step_ms), dev)
     psteps = s.process_steps()
-    value = psteps * world / (ms / 1000.0)
+    value = whole_job_rate(psteps, world, ms)
 
     # end to end through the public API: host buffers in, results to the host
     e2e_ms = []
@@ -309,11 +323,31 @@ def run_batched(args):
             ms.append(a.elapsed_time(b))
             totals = [r.total for r in rs]
             kernels = rs[0].launches()[0] if name == "batched" else sum(r.launches()[0] for r in rs)
+            if name == "batched":
+                round_ms, _, n_rounds = rs[0].timing()
+                ops_total = sum(r.counters()[2] for r in rs)
             for r in rs:
                 r.free()
         out[name] = {"ms": statistics.mean(ms), "value": psteps / (statistics.mean(ms) / 1000.0),
                      "best_additions_total": sum(totals), "kernel_launches": kernels}
     assert out["batched"]["best_additions_total"] == out["per_scheme"]["best_additions_total"]
+    pk = peaks()
+    props = torch.cuda.get_device_properties(dev)
+    sm_mhz = float(pk.get("sm_max_mhz", 2070.0))
+    peak_ops = props.multi_processor_count * LANES_PER_SM * sm_mhz * 1e6 / 1e12
+    achieved = ops_total / (round_ms / 1000.0) / 1e12
+    # the oracle on the same batch, all schemes and processes, first cpu_budget steps
+    from oracle import oracle as O
+    import copy
+    cores = len(os.sched_getaffinity(0))
+    cb = args.cpu_budget or 64
+    t0 = time.perf_counter()
+    for s in searches:
+        smp = copy.copy(s)
+        smp.budget = min(cb, s.budget)
+        O.search_obj(smp, n_threads=cores, digests=False)
+    cpu_s = time.perf_counter() - t0
+    cpu_steps = sum(len(s.mats) * s.n_proc * min(cb, s.budget) for s in searches)
     line = {
         "metric": METRIC, "value": out["batched"]["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": out["batched"]["ms"], "higher_is_better": True, "scaling": "weak",
@@ -326,6 +360,14 @@ def run_batched(args):
         "speedup_batched_vs_per_scheme": out["per_scheme"]["ms"] / out["batched"]["ms"],
         "autotune": {"seconds": tune_s, "classes": tuned, "interval_candidates": [16, 32, 64],
                      "interval_chosen": interval},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "Tops/s",
+                     "frac": achieved / peak_ops, "traffic": None,
+                     "kernel": "round kernels of the batched graph (all classes)",
+                     "alg_ops_per_launch": ops_total / n_rounds, "avg_launch_ms": round_ms / n_rounds},
+        "cpu_baseline": {"value": cpu_steps / cpu_s, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"all {len(searches)} schemes x 3 matrices x {searches[0].n_proc} processes, "
+                                   f"first {cb} steps ({cpu_steps} process-steps, {cpu_s:.1f} s)"},
+        "gpu_launches": out["batched"]["kernel_launches"] * args.steps,
     }
     print(json.dumps(line))
 
