@@ -75,6 +75,8 @@ typedef struct {
 #define CSE_FLAG_GRAPH 1u  /* capture the whole launch sequence in one CUDA graph
                               and launch it once; the round kernels of different
                               matrix classes become parallel graph branches */
+#define CSE_FLAG_TRACE 2u  /* record each process's trajectory hash (see
+                              cse_proc_record); costs a few per cent */
 
 /* Search options.  Fields that change results: share_interval,
  * share_permille, col_cap.  The rest only change how the work is launched. */
@@ -182,7 +184,9 @@ typedef struct {
     uint64_t best_hash; /* FNV-1a over the 32-bit entries of the best list   */
     uint64_t traj_hash; /* FNV-1a over the trajectory: (t, 0xA0000000 |
                            strategy << 12 | replayed) at each run start and
-                           (t, entry) at each substitution step              */
+                           (t, entry) at each substitution step; recorded
+                           only with CSE_FLAG_TRACE, else the FNV offset
+                           basis 0xCBF29CE484222325                          */
     int64_t ops;        /* algorithmic integer operations (see the counters
                            of cse_result_counters)                           */
     int64_t substeps;   /* steps that made a substitution                    */
@@ -227,7 +231,8 @@ void cse_scheme_free(cse_scheme* s);
  * then the share kernel).  Admitted searches run concurrently with those
  * already on the device and leave as soon as their step budget is done.  Each
  * search keeps its own step clock, so a request's result is exactly what
- * cse_search returns for it alone.  opts->flags is ignored. */
+ * cse_search returns for it alone.  Of opts->flags only CSE_FLAG_TRACE is
+ * used. */
 int cse_server_create(const cse_opts* opts, uint64_t hbm_budget_bytes, int64_t max_active_processes,
                       cse_server** out);
 

@@ -190,7 +190,7 @@ static int check_opts(const cse_opts* opts_in, cse_opts* opts) {
         cse_opts_default(opts);
     if (opts->share_interval < 1) return fail(CSE_EINVAL, "share_interval must be >= 1");
     if (opts->share_permille > 1000) return fail(CSE_EINVAL, "share_permille must be <= 1000");
-    if (opts->patience_rounds != 0 || (opts->flags & ~(uint32_t)CSE_FLAG_GRAPH) != 0)
+    if (opts->patience_rounds != 0 || (opts->flags & ~(uint32_t)(CSE_FLAG_GRAPH | CSE_FLAG_TRACE)) != 0)
         return fail(CSE_EINVAL, "reserved option fields must be 0");
     if (opts->col_cap > CSE_MAX_COLS) return fail(CSE_EINVAL, "col_cap must be <= 512");
     if (opts->procs_per_cta > 4) return fail(CSE_EINVAL, "procs_per_cta must be in [0, 4]");
@@ -279,6 +279,7 @@ static int search_create(const cse_scheme* s, const cse_strategy_mix* mix, int n
     S.clock = (int32_t*)(b + of[8 * s->n_mats]);
     S.status = (int32_t*)(b + of[8 * s->n_mats + 1]);
     S.n_mats = s->n_mats;
+    S.trace = (opts.flags & CSE_FLAG_TRACE) ? 1 : 0;
     static const int32_t snap_init[2] = {INT_MAX, 0};
     for (int k = 0; k < s->n_mats; k++) {
         DevMat& M = sd->mats[k];
@@ -1090,7 +1091,7 @@ int cse_server_create(const cse_opts* opts_in, uint64_t hbm_budget_bytes, int64_
     cse_opts opts;
     int rc = check_opts(opts_in, &opts);
     if (rc) return rc;
-    opts.flags = 0;
+    opts.flags &= CSE_FLAG_TRACE;
     if (max_smem_per_block() <= 0) return fail(CSE_ECUDA, "no CUDA device");
     cse_server* sv = new (std::nothrow) cse_server();
     if (!sv) return fail(CSE_ENOMEM, "host allocation");

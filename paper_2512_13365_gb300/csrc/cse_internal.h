@@ -45,7 +45,7 @@ constexpr uint64_t kFnv0 = 0xCBF29CE484222325ull;
 
 // Shared-memory carve-up of one process (one warp), in bytes.
 struct WarpLayout {
-    int32_t off_pn, off_cand, off_f, off_aw, off_poslo, off_hs, off_he, off_base, off_lc;
+    int32_t off_cold, off_pn, off_cand, off_f, off_aw, off_poslo, off_hs, off_he, off_base, off_lc;
     int32_t per_warp;
 };
 
@@ -82,6 +82,7 @@ struct DevSearch {
     const int32_t* mat_pos;  // positions of this search's matrices in the DevMat array
     int32_t n_mats;
     int32_t* status;         // nonzero: a device-side consistency check failed
+    int32_t trace;           // record the trajectory hash (CSE_FLAG_TRACE)
 };
 
 WarpLayout make_layout(int W, int cap, int mmax);

@@ -155,6 +155,18 @@ __device__ __noinline__ uint4 philox_call(uint32_t c0, uint32_t c1, uint32_t c2,
     return make_uint4(c0, c1, c2, c3);
 }
 
+// Per-process values touched a few times per step at most.  They live in
+// the warp's shared memory (written by lane 0) rather than in 32 register
+// copies: the step engine is register-bound.
+struct Cold {
+    unsigned long long traj;   // trajectory hash (CSE_FLAG_TRACE)
+    int runs, substeps, best_cost, best_len, trace;
+    // algorithmic-op tallies of the round: substitutions, pair counts that
+    // can change, candidates scanned by g/ga/wr/gr; Greedy-Intersections
+    // terms, Philox blocks and scored candidates
+    unsigned t_sub, t_pairs, t_scan, t_gi_terms, t_gi_blocks, t_gi_cands;
+};
+
 template <int W>
 struct Engine {
     unsigned char* sm;   // this warp's shared memory
@@ -165,10 +177,7 @@ struct Engine {
     int proc, lane, cap, mmax;
     uint32_t lt;
     // warp-uniform state
-    int ncols, nf, m, cost, strat, a, b, ended, runs, substeps, best_cost, best_len;
-    uint64_t traj;
-    long long ops;       // warp-uniform part of the op count
-    long long ops_lane;  // per-lane part (gi scoring), reduced at the end
+    int ncols, nf, m, cost, strat, a, b, ended;
     int overflow;
 
     __device__ __forceinline__ uint2* pn() const { return reinterpret_cast<uint2*>(sm + L->off_pn); }
@@ -180,6 +189,7 @@ struct Engine {
     __device__ __forceinline__ uint16_t* he() const { return reinterpret_cast<uint16_t*>(sm + L->off_he); }
     __device__ __forceinline__ uint16_t* vbase() const { return reinterpret_cast<uint16_t*>(sm + L->off_base); }
     __device__ __forceinline__ uint16_t* lc() const { return reinterpret_cast<uint16_t*>(sm + L->off_lc); }
+    __device__ __forceinline__ Cold* cold() const { return reinterpret_cast<Cold*>(sm + L->off_cold); }
 
     __device__ __forceinline__ uint32_t c2(uint32_t purpose, uint32_t extra_hi) const {
         return ((uint32_t)M->mat_index & 0xFFu) << 24 | (purpose & 0xFu) << 20 | (extra_hi & 0xFFFFFu);
@@ -300,20 +310,29 @@ struct Engine {
         ncols++;
         cost -= c - 1;
         m = newm;
-        ops += 10LL * M->W + 5LL * M->W * (nij + nu);
+        if (lane == 0) {
+            Cold* cd = cold();
+            cd->t_sub++;
+            cd->t_pairs += (unsigned)(nij + nu);
+        }
         __syncwarp();
     }
 
     // Closes the current run into the process's best record (strictly lower
     // cost replaces).
     __device__ void fold() {
-        if (cost < best_cost) {
+        Cold* cd = cold();
+        if (cost < cd->best_cost) {
             int32_t* dst = M->best_list + (size_t)proc * cap;
             const int32_t* f = F();
             for (int x = lane; x < nf; x += 32) dst[x] = f[x];
-            best_cost = cost;
-            best_len = nf;
+            __syncwarp();
+            if (lane == 0) {
+                cd->best_cost = cost;
+                cd->best_len = nf;
+            }
         }
+        __syncwarp();
     }
 
     // Run start at step t (Section 3.5.1-3.5.2): strategy, alpha, beta, fresh
@@ -321,7 +340,7 @@ struct Engine {
     // replay (Section 3.5.2); the caller replays them.
     __device__ int start_run(int t) {
         if (t > 0) fold();
-        runs++;
+        if (lane == 0) cold()->runs++;
         const uint4 R = draw(t, PU_RUN);
         if (proc == 0 && t == 0) {
             strat = ST_G;
@@ -355,7 +374,10 @@ struct Engine {
             if (K >= 1) k = 1 + (int)scale32(draw(t, PU_SHAREK).x, (uint32_t)K);
         }
         ended = 0;
-        traj = fnv(fnv(traj, (uint32_t)t), 0xA0000000u | (uint32_t)strat << 12 | (uint32_t)k);
+        if (lane == 0) {
+            Cold* cd = cold();
+            if (cd->trace) cd->traj = fnv(fnv(cd->traj, (uint32_t)t), 0xA0000000u | (uint32_t)strat << 12 | (uint32_t)k);
+        }
         __syncwarp();
         return k;
     }
@@ -499,6 +521,7 @@ struct Engine {
         const uint32_t c2g = c2(PU_GI, 0);
         long long best_s = LLONG_MIN;
         int best_q = -1;
+        unsigned gi_terms = 0, gi_blocks = 0;
         for (int base = 0; base < m; base += 32) {
             const int p = base + lane;
             if (p < m) {
@@ -572,7 +595,8 @@ struct Engine {
                     best_s = sc;
                     best_q = p;
                 }
-                ops_lane += 3LL * nint + 8 + 40LL * nb;
+                gi_terms += nint;
+                gi_blocks += nb;
             }
         }
 #pragma unroll
@@ -583,6 +607,14 @@ struct Engine {
                 best_s = s2;
                 best_q = q2;
             }
+        }
+        gi_terms = __reduce_add_sync(FULL_MASK, gi_terms);
+        gi_blocks = __reduce_add_sync(FULL_MASK, gi_blocks);
+        if (lane == 0) {
+            Cold* cd = cold();
+            cd->t_gi_terms += gi_terms;
+            cd->t_gi_blocks += gi_blocks;
+            cd->t_gi_cands += (unsigned)m;
         }
         return best_q;
     }
@@ -597,7 +629,7 @@ struct Engine {
         }
         if (s == ST_GR) s = d.y < 0xC0000000u ? ST_GA : ST_WR;
         if (s == ST_GI) return sel_gi(t);
-        ops += 2LL * m;
+        if (lane == 0) cold()->t_scan += (unsigned)m;
         if (s == ST_GA) return sel_ga(d.z);
         if (s == ST_WR) return sel_wr(d.w);
         return sel_g();
@@ -631,8 +663,11 @@ struct Engine {
             subst(i, j, neg);
             if (e >= replay) break;
         }
-        substeps++;
-        traj = fnv(fnv(traj, (uint32_t)t), (uint32_t)F()[nf - 1]);
+        if (lane == 0) {
+            Cold* cd = cold();
+            cd->substeps++;
+            if (cd->trace) cd->traj = fnv(fnv(cd->traj, (uint32_t)t), (uint32_t)F()[nf - 1]);
+        }
         if (m == 0 || ncols >= cap) ended = 1;
     }
 };
@@ -673,9 +708,9 @@ __global__ void __launch_bounds__(128, CSE_MIN_BLOCKS) round_kernel(const DevMat
     E.cap = M->cap;
     E.mmax = M->mmax;
     E.lt = lanemask_lt();
-    E.ops_lane = 0;
     E.overflow = 0;
-
+    Cold* cd = E.cold();
+    long long ops;
     if (t0 == 0) {
         E.ncols = M->nx;
         E.nf = 0;
@@ -685,12 +720,14 @@ __global__ void __launch_bounds__(128, CSE_MIN_BLOCKS) round_kernel(const DevMat
         E.a = 0;
         E.b = 0;
         E.ended = 1;
-        E.runs = 0;
-        E.substeps = 0;
-        E.best_cost = M->meta0[0];
-        E.best_len = 0;
-        E.traj = kFnv0;
-        E.ops = 0;
+        ops = 0;
+        if (lane == 0) {
+            cd->runs = 0;
+            cd->substeps = 0;
+            cd->best_cost = M->meta0[0];
+            cd->best_len = 0;
+            cd->traj = kFnv0;
+        }
     } else {
         E.ncols = (int)st[H_NCOLS];
         E.nf = (int)st[H_NF];
@@ -700,12 +737,19 @@ __global__ void __launch_bounds__(128, CSE_MIN_BLOCKS) round_kernel(const DevMat
         E.a = (int)st[H_A];
         E.b = (int)st[H_B];
         E.ended = (int)st[H_ENDED];
-        E.runs = (int)st[H_RUNS];
-        E.substeps = (int)st[H_SUBSTEPS];
-        E.best_cost = (int)st[H_BEST_COST];
-        E.best_len = (int)st[H_BEST_LEN];
-        E.traj = (uint64_t)st[H_TRAJ_LO] | (uint64_t)st[H_TRAJ_HI] << 32;
-        E.ops = (long long)((uint64_t)st[H_OPS_LO] | (uint64_t)st[H_OPS_HI] << 32);
+        ops = (long long)((uint64_t)st[H_OPS_LO] | (uint64_t)st[H_OPS_HI] << 32);
+        if (lane == 0) {
+            cd->runs = (int)st[H_RUNS];
+            cd->substeps = (int)st[H_SUBSTEPS];
+            cd->best_cost = (int)st[H_BEST_COST];
+            cd->best_len = (int)st[H_BEST_LEN];
+            cd->traj = (uint64_t)st[H_TRAJ_LO] | (uint64_t)st[H_TRAJ_HI] << 32;
+        }
+    }
+    if (lane == 0) {
+        cd->trace = S->trace;
+        cd->t_sub = cd->t_pairs = cd->t_scan = 0;
+        cd->t_gi_terms = cd->t_gi_blocks = cd->t_gi_cands = 0;
     }
     if (t0 > 0 && !GM) {
         const uint2* spn = reinterpret_cast<const uint2*>(st + H_WORDS);
@@ -718,18 +762,22 @@ __global__ void __launch_bounds__(128, CSE_MIN_BLOCKS) round_kernel(const DevMat
         int32_t* F = E.F();
         for (int x = lane; x < E.nf; x += 32) F[x] = sf[x];
     }
-    const long long ops_before = E.ops;
-    const int sub_before = E.substeps;
     __syncwarp();
+    const int sub_before = cd->substeps;
 
     for (int t = t0; t < t1; t++) E.step(t);
     E.fold();
 
-    E.ops += warp_sum64(E.ops_lane);
     if (lane == 0) {
-        atomicMin(M->round_min, (unsigned long long)(uint32_t)E.best_cost << 32 | (uint32_t)E.proc);
-        atomicAdd(&M->counters[0], (unsigned long long)(E.ops - ops_before));
-        atomicAdd(&M->counters[1], (unsigned long long)(E.substeps - sub_before));
+        // algorithmic ops of the round: 10 W per rewrite, 5 W per pair count
+        // that can change, 2 per candidate scanned, and per gi candidate 3 per
+        // intersecting term + 8 + 40 per Philox block
+        const long long dops = 10LL * M->W * cd->t_sub + 5LL * M->W * cd->t_pairs + 2LL * cd->t_scan +
+                               3LL * cd->t_gi_terms + 40LL * cd->t_gi_blocks + 8LL * cd->t_gi_cands;
+        ops += dops;
+        atomicMin(M->round_min, (unsigned long long)(uint32_t)cd->best_cost << 32 | (uint32_t)E.proc);
+        atomicAdd(&M->counters[0], (unsigned long long)dops);
+        atomicAdd(&M->counters[1], (unsigned long long)(cd->substeps - sub_before));
         if (E.overflow) atomicExch(S->status, 1);
         st[H_NCOLS] = (uint32_t)E.ncols;
         st[H_NF] = (uint32_t)E.nf;
@@ -739,14 +787,14 @@ __global__ void __launch_bounds__(128, CSE_MIN_BLOCKS) round_kernel(const DevMat
         st[H_A] = (uint32_t)E.a;
         st[H_B] = (uint32_t)E.b;
         st[H_ENDED] = (uint32_t)E.ended;
-        st[H_RUNS] = (uint32_t)E.runs;
-        st[H_SUBSTEPS] = (uint32_t)E.substeps;
-        st[H_BEST_COST] = (uint32_t)E.best_cost;
-        st[H_BEST_LEN] = (uint32_t)E.best_len;
-        st[H_TRAJ_LO] = (uint32_t)E.traj;
-        st[H_TRAJ_HI] = (uint32_t)(E.traj >> 32);
-        st[H_OPS_LO] = (uint32_t)(uint64_t)E.ops;
-        st[H_OPS_HI] = (uint32_t)((uint64_t)E.ops >> 32);
+        st[H_RUNS] = (uint32_t)cd->runs;
+        st[H_SUBSTEPS] = (uint32_t)cd->substeps;
+        st[H_BEST_COST] = (uint32_t)cd->best_cost;
+        st[H_BEST_LEN] = (uint32_t)cd->best_len;
+        st[H_TRAJ_LO] = (uint32_t)cd->traj;
+        st[H_TRAJ_HI] = (uint32_t)(cd->traj >> 32);
+        st[H_OPS_LO] = (uint32_t)(uint64_t)ops;
+        st[H_OPS_HI] = (uint32_t)((uint64_t)ops >> 32);
     }
     if (!GM && t1 < S->budget) {  // the state is needed by the next round
         uint2* spn = reinterpret_cast<uint2*>(st + H_WORDS);
@@ -806,6 +854,8 @@ static int align16(int x) { return (x + 15) & ~15; }
 WarpLayout make_layout(int W, int cap, int mmax) {
     WarpLayout L;
     int o = 0;
+    L.off_cold = o;
+    o = align16(o + (int)sizeof(Cold));
     L.off_pn = o;
     o = align16(o + cap * W * 8);
     L.off_cand = o;

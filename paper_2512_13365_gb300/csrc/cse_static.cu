@@ -73,7 +73,7 @@ extern "C" int cse_search_static(const cse_scheme* s, const cse_strategy_mix* mi
     else
         cse_opts_default(&opts);
     if (opts.share_interval < 1 || opts.share_permille > 1000 || opts.patience_rounds != 0 ||
-        (opts.flags & ~(uint32_t)CSE_FLAG_GRAPH) != 0 || opts.col_cap > CSE_MAX_COLS || opts.procs_per_cta > 4)
+        (opts.flags & ~(uint32_t)(CSE_FLAG_GRAPH | CSE_FLAG_TRACE)) != 0 || opts.col_cap > CSE_MAX_COLS || opts.procs_per_cta > 4)
         return set_error(CSE_EINVAL, "invalid options");
     if (mix->w_gp != 0) return set_error(CSE_EINVAL, "Greedy-Potential (w_gp) is not implemented; set it to 0");
     const uint64_t wsum = (uint64_t)mix->w_gi + mix->w_ga + mix->w_gr + mix->w_wr + mix->w_mix + mix->w_g;
@@ -138,6 +138,7 @@ extern "C" int cse_search_static(const cse_scheme* s, const cse_strategy_mix* mi
     S.status = (int32_t*)(b + o_status);
     S.mat_pos = (const int32_t*)(b + o_pos);
     S.n_mats = nm;
+    S.trace = (opts.flags & CSE_FLAG_TRACE) ? 1 : 0;
     struct Group { int W, begin, count, units, mmax; bool gm; WarpLayout L; int ppc; };
     std::vector<Group> groups;
     std::vector<DevMat> dm(nm);

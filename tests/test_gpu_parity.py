@@ -24,7 +24,7 @@ def cse():
 
 
 def assert_parity(cse, s, ref=None, procs_per_cta=0, check_procs=True):
-    r = cse.search_obj(s, procs_per_cta=procs_per_cta)
+    r = cse.search_obj(s, procs_per_cta=procs_per_cta, trace=True)
     if ref is None:
         ref = O.search_obj(s, n_threads=8)
     assert r.costs == ref.cost
@@ -114,9 +114,9 @@ def test_single_row_and_single_process(cse):
 
 def test_seeds_differ(cse):
     s = synth.config2(n_proc=32, budget=64)
-    a = cse.search_obj(s)
+    a = cse.search_obj(s, trace=True)
     s.seed = 1
-    b = cse.search_obj(s)
+    b = cse.search_obj(s, trace=True)
     assert not np.array_equal(a.procs(0)["traj_hash"], b.procs(0)["traj_hash"])
 
 
@@ -188,11 +188,11 @@ def test_batch_equals_each_search_alone(cse, graph):
     searches[1].n_proc, searches[2].budget, searches[3].seed = 23, 33, 99
     searches.append(synth.config2(n_proc=30, budget=50))
     searches[-1].interval, searches[-1].cap = 16, 256
-    batch = cse.search_batch_obj(searches, graph=graph)
+    batch = cse.search_batch_obj(searches, graph=graph, trace=True)
     kernels, shared = batch[0].launches()
     assert shared == len(searches) and kernels >= 1 + 5  # init + rounds x (groups + share)
     for s, rb in zip(searches, batch):
-        alone = cse.search_obj(s)
+        alone = cse.search_obj(s, trace=True)
         pb, lb, cb = _records(cse, rb, len(s.mats))
         pa, la, ca = _records(cse, alone, len(s.mats))
         assert lb == la and cb == ca
@@ -223,10 +223,10 @@ def test_autotuner_changes_speed_not_results(cse):
     schemes = [cse.Scheme(s.mats) for s in searches]
     args = (schemes, [s.weights for s in searches], [s.n_proc for s in searches], [s.seed for s in searches],
             [s.budget for s in searches])
-    before = cse.search_batch(*args, interval=16, cap=256)
+    before = cse.search_batch(*args, interval=16, cap=256, trace=True)
     ents = cse.autotune(*args, interval=16, cap=256, trial_steps=32)
     assert ents and all(1 <= e["procs_per_cta"] <= 4 and min(e["trial_ms"]) > 0 for e in ents)
-    after = cse.search_batch(*args, interval=16, cap=256)
+    after = cse.search_batch(*args, interval=16, cap=256, trace=True)
     for a, b, s in zip(before, after, searches):
         assert a.lists == b.lists and a.costs == b.costs
         for k in range(len(s.mats)):
@@ -244,8 +244,7 @@ def test_interval_tuner_picks_lowest_total(cse):
         rs = cse.search_batch(*args, interval=iv, cap=256)
         totals[iv] = sum(r.total for r in rs)
     assert total == totals[best] == min(totals.values())
-    assert best == min((v, i) for i, v in zip((0, 1, 2), [totals[8], totals[16], totals[48]]))[1] * 0 + \
-        [8, 16, 48][[totals[8], totals[16], totals[48]].index(min(totals.values()))]
+    assert best == [8, 16, 48][[totals[8], totals[16], totals[48]].index(min(totals.values()))]
 
 
 def test_large_search_full_process_count_sampled(cse):
@@ -253,7 +252,7 @@ def test_large_search_full_process_count_sampled(cse):
     the first sharing boundary (32 steps): no snapshot exists yet, so every
     process is independent and the oracle can replay a sample of them exactly."""
     s = synth.config4(budget=32)
-    r = cse.search_obj(s)
+    r = cse.search_obj(s, trace=True)
     sample = [0, 1, 777, 4095, 31337, 65535]
     ref = O.search_obj(s, n_threads=8, subset=sample)
     for k in range(3):
@@ -263,3 +262,15 @@ def test_large_search_full_process_count_sampled(cse):
     # the published result is the best over all processes: never worse than the sample
     assert all(c <= int(ref.digests[k][sample]["best_cost"].min()) for k, c in enumerate(r.costs))
     r.free()
+
+
+def test_trace_flag_only_changes_the_trajectory_record(cse):
+    s = synth.config2(n_proc=64, budget=80)
+    plain = cse.search_obj(s)
+    traced = cse.search_obj(s, trace=True)
+    assert plain.lists == traced.lists and plain.costs == traced.costs
+    for k in range(3):
+        a, b = plain.procs(k), traced.procs(k)
+        assert (a["traj_hash"] == 0xCBF29CE484222325).all()
+        for f in ("best_cost", "best_len", "runs", "best_hash", "ops", "substeps"):
+            assert np.array_equal(a[f], b[f])

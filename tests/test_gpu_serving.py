@@ -37,7 +37,7 @@ def _same(cse, a, b, n_mats):
 
 def test_served_results_equal_alone(cse):
     reqs = _requests(6, 48, 40)
-    sv = cse.Server(interval=16, cap=512)
+    sv = cse.Server(interval=16, cap=512, trace=True)
     schemes = [cse.Scheme(s.mats) for s in reqs]
     tickets = []
     for i, (s, sc) in enumerate(zip(reqs, schemes)):
@@ -48,7 +48,7 @@ def test_served_results_equal_alone(cse):
     st = sv.stats()
     assert st["completed"] == len(reqs) and st["p99_ms"] >= st["p50_ms"] > 0 and st["steps_per_s"] > 0
     for s, sc, r in zip(reqs, schemes, served):
-        alone = cse.search(sc, s.weights, s.n_proc, s.seed, s.budget, 16, s.permille, 512)
+        alone = cse.search(sc, s.weights, s.n_proc, s.seed, s.budget, 16, s.permille, 512, trace=True)
         _same(cse, r, alone, len(s.mats))
     ref = O.search_obj(reqs[0], n_threads=8)
     assert served[0].costs == ref.cost and served[0].lists == ref.lists
