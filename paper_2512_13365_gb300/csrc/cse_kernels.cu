@@ -160,7 +160,9 @@ __device__ __noinline__ uint4 philox_call(uint32_t c0, uint32_t c1, uint32_t c2,
 // copies: the step engine is register-bound.
 struct Cold {
     unsigned long long traj;   // trajectory hash (CSE_FLAG_TRACE)
-    int runs, substeps, best_cost, best_len, trace;
+    unsigned long long ops;    // algorithmic-op total before this round
+    int runs, substeps, best_cost, best_len, trace, overflow, sub_before;
+    int strat, a, b;           // the current run's strategy, alpha, beta
     // algorithmic-op tallies of the round: substitutions, pair counts that
     // can change, candidates scanned by g/ga/wr/gr; Greedy-Intersections
     // terms, Philox blocks and scored candidates
@@ -175,10 +177,8 @@ struct Engine {
     const DevMat* M;
     const DevSearch* S;
     int proc, lane, cap, mmax;
-    uint32_t lt;
     // warp-uniform state
-    int ncols, nf, m, cost, strat, a, b, ended;
-    int overflow;
+    int ncols, nf, m, cost, ended;
 
     __device__ __forceinline__ uint2* pn() const { return reinterpret_cast<uint2*>(sm + L->off_pn); }
     __device__ __forceinline__ uint32_t* cand() const { return reinterpret_cast<uint32_t*>(sm + L->off_cand); }
@@ -217,6 +217,7 @@ struct Engine {
     // Substitution of (x_i + s x_j), i < j, by the fresh x_k, k = ncols
     // (Section 3.2.1, Algorithm 1), with the candidate list update.
     __device__ void subst(int i, int j, int neg) {
+        const uint32_t lt = lanemask_lt();
         uint2* P = pn();
         uint32_t* C = cand();
         const int k = ncols;
@@ -302,7 +303,7 @@ struct Engine {
             newm += __popc(bp) + __popc(bm);
         }
         if (newm > mmax) {
-            overflow = 1;
+            if (lane == 0) cold()->overflow = 1;
             newm = mmax;
         }
         if (lane == 0) F()[nf] = (int32_t)((uint32_t)i | (uint32_t)j << 10 | (uint32_t)neg << 20);
@@ -342,12 +343,10 @@ struct Engine {
         if (t > 0) fold();
         if (lane == 0) cold()->runs++;
         const uint4 R = draw(t, PU_RUN);
-        if (proc == 0 && t == 0) {
-            strat = ST_G;
-        } else {
+        int strat = ST_G;
+        if (!(proc == 0 && t == 0)) {
             const uint32_t x = scale32(R.x, S->wsum);
             uint32_t acc = 0;
-            strat = ST_G;
             for (int s = 0; s < ST_N; s++) {
                 acc += S->w[s];
                 if (x < acc) {
@@ -356,8 +355,12 @@ struct Engine {
                 }
             }
         }
-        a = (int)scale32(R.y, 32769u);
-        b = 32768 + (int)scale32(R.z, 32769u);
+        if (lane == 0) {
+            Cold* cd = cold();
+            cd->strat = strat;
+            cd->a = (int)scale32(R.y, 32769u);
+            cd->b = 32768 + (int)scale32(R.z, 32769u);
+        }
         const int nx = M->nx;
         uint2* P = pn();
         uint32_t* C = cand();
@@ -376,7 +379,7 @@ struct Engine {
         ended = 0;
         if (lane == 0) {
             Cold* cd = cold();
-            if (cd->trace) cd->traj = fnv(fnv(cd->traj, (uint32_t)t), 0xA0000000u | (uint32_t)strat << 12 | (uint32_t)k);
+            if (cd->trace) cd->traj = fnv(fnv(cd->traj, (uint32_t)t), 0xA0000000u | (uint32_t)cd->strat << 12 | (uint32_t)k);
         }
         __syncwarp();
         return k;
@@ -396,6 +399,7 @@ struct Engine {
 
     // Greedy-Alternative: uniform among the max-c ties, (u * n_ties) >> 32-th in order.
     __device__ int sel_ga(uint32_t u) const {
+        const uint32_t lt = lanemask_lt();
         const uint32_t* C = cand();
         int lmax = 0, lcnt = 0;
         for (int q = lane; q < m; q += 32) {
@@ -453,6 +457,7 @@ struct Engine {
     // Philox bit at its position in A_v, so each lane scores its candidate with
     // two straight loops over byte arrays.
     __device__ int sel_gi(int t) {
+        const uint32_t lt = lanemask_lt();
         const uint32_t* C = cand();
         uint16_t* HS = hs();
         uint16_t* HE = he();
@@ -519,6 +524,7 @@ struct Engine {
         // scoring: one candidate p per lane
         const uint32_t k0 = (uint32_t)S->seed, k1 = (uint32_t)(S->seed >> 32);
         const uint32_t c2g = c2(PU_GI, 0);
+        const long long a = cold()->a, b = cold()->b;
         long long best_s = LLONG_MIN;
         int best_q = -1;
         unsigned gi_terms = 0, gi_blocks = 0;
@@ -590,7 +596,7 @@ struct Engine {
                 }
                 const int D = T - wp - inter;
                 const long long sc = ((long long)wp << 32) +
-                                     (long long)a * (((long long)D << 16) + (long long)b * (long long)X);
+                                     a * (((long long)D << 16) + b * (long long)X);
                 if (sc > best_s) {
                     best_s = sc;
                     best_q = p;
@@ -620,7 +626,7 @@ struct Engine {
     }
 
     __device__ int choose(int t) {
-        int s = strat;
+        int s = cold()->strat;
         uint4 d = make_uint4(0, 0, 0, 0);
         if (s != ST_G && s != ST_GI) d = draw(t, PU_STEP);
         if (s == ST_MIX) {
@@ -707,21 +713,18 @@ __global__ void __launch_bounds__(128, CSE_MIN_BLOCKS) round_kernel(const DevMat
     E.lane = lane;
     E.cap = M->cap;
     E.mmax = M->mmax;
-    E.lt = lanemask_lt();
-    E.overflow = 0;
     Cold* cd = E.cold();
-    long long ops;
     if (t0 == 0) {
         E.ncols = M->nx;
         E.nf = 0;
         E.m = 0;
         E.cost = M->meta0[0];
-        E.strat = ST_G;
-        E.a = 0;
-        E.b = 0;
         E.ended = 1;
-        ops = 0;
         if (lane == 0) {
+            cd->ops = 0;
+            cd->strat = ST_G;
+            cd->a = 0;
+            cd->b = 0;
             cd->runs = 0;
             cd->substeps = 0;
             cd->best_cost = M->meta0[0];
@@ -733,12 +736,12 @@ __global__ void __launch_bounds__(128, CSE_MIN_BLOCKS) round_kernel(const DevMat
         E.nf = (int)st[H_NF];
         E.m = (int)st[H_M];
         E.cost = (int)st[H_COST];
-        E.strat = (int)st[H_STRAT];
-        E.a = (int)st[H_A];
-        E.b = (int)st[H_B];
         E.ended = (int)st[H_ENDED];
-        ops = (long long)((uint64_t)st[H_OPS_LO] | (uint64_t)st[H_OPS_HI] << 32);
         if (lane == 0) {
+            cd->ops = (uint64_t)st[H_OPS_LO] | (uint64_t)st[H_OPS_HI] << 32;
+            cd->strat = (int)st[H_STRAT];
+            cd->a = (int)st[H_A];
+            cd->b = (int)st[H_B];
             cd->runs = (int)st[H_RUNS];
             cd->substeps = (int)st[H_SUBSTEPS];
             cd->best_cost = (int)st[H_BEST_COST];
@@ -748,6 +751,7 @@ __global__ void __launch_bounds__(128, CSE_MIN_BLOCKS) round_kernel(const DevMat
     }
     if (lane == 0) {
         cd->trace = S->trace;
+        cd->overflow = 0;
         cd->t_sub = cd->t_pairs = cd->t_scan = 0;
         cd->t_gi_terms = cd->t_gi_blocks = cd->t_gi_cands = 0;
     }
@@ -762,8 +766,8 @@ __global__ void __launch_bounds__(128, CSE_MIN_BLOCKS) round_kernel(const DevMat
         int32_t* F = E.F();
         for (int x = lane; x < E.nf; x += 32) F[x] = sf[x];
     }
+    if (lane == 0) cd->sub_before = cd->substeps;
     __syncwarp();
-    const int sub_before = cd->substeps;
 
     for (int t = t0; t < t1; t++) E.step(t);
     E.fold();
@@ -774,18 +778,19 @@ __global__ void __launch_bounds__(128, CSE_MIN_BLOCKS) round_kernel(const DevMat
         // intersecting term + 8 + 40 per Philox block
         const long long dops = 10LL * M->W * cd->t_sub + 5LL * M->W * cd->t_pairs + 2LL * cd->t_scan +
                                3LL * cd->t_gi_terms + 40LL * cd->t_gi_blocks + 8LL * cd->t_gi_cands;
-        ops += dops;
+        const unsigned long long ops = cd->ops + (unsigned long long)dops;
+        uint32_t* st = M->state + (size_t)E.proc * M->state_words;
         atomicMin(M->round_min, (unsigned long long)(uint32_t)cd->best_cost << 32 | (uint32_t)E.proc);
         atomicAdd(&M->counters[0], (unsigned long long)dops);
-        atomicAdd(&M->counters[1], (unsigned long long)(cd->substeps - sub_before));
-        if (E.overflow) atomicExch(S->status, 1);
+        atomicAdd(&M->counters[1], (unsigned long long)(cd->substeps - cd->sub_before));
+        if (cd->overflow) atomicExch(S->status, 1);
         st[H_NCOLS] = (uint32_t)E.ncols;
         st[H_NF] = (uint32_t)E.nf;
         st[H_M] = (uint32_t)E.m;
         st[H_COST] = (uint32_t)E.cost;
-        st[H_STRAT] = (uint32_t)E.strat;
-        st[H_A] = (uint32_t)E.a;
-        st[H_B] = (uint32_t)E.b;
+        st[H_STRAT] = (uint32_t)cd->strat;
+        st[H_A] = (uint32_t)cd->a;
+        st[H_B] = (uint32_t)cd->b;
         st[H_ENDED] = (uint32_t)E.ended;
         st[H_RUNS] = (uint32_t)cd->runs;
         st[H_SUBSTEPS] = (uint32_t)cd->substeps;
@@ -793,8 +798,8 @@ __global__ void __launch_bounds__(128, CSE_MIN_BLOCKS) round_kernel(const DevMat
         st[H_BEST_LEN] = (uint32_t)cd->best_len;
         st[H_TRAJ_LO] = (uint32_t)cd->traj;
         st[H_TRAJ_HI] = (uint32_t)(cd->traj >> 32);
-        st[H_OPS_LO] = (uint32_t)(uint64_t)ops;
-        st[H_OPS_HI] = (uint32_t)((uint64_t)ops >> 32);
+        st[H_OPS_LO] = (uint32_t)ops;
+        st[H_OPS_HI] = (uint32_t)(ops >> 32);
     }
     if (!GM && t1 < S->budget) {  // the state is needed by the next round
         uint2* spn = reinterpret_cast<uint2*>(st + H_WORDS);
