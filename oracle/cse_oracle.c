@@ -29,6 +29,11 @@
  *   R6 gr: ga when u < 3 * 2^30 (p = 0.75), else wr, separate draws.
  *   R7 mix: per step, (u * 15) >> 32 in [0,8) gi, [8,12) ga, [12,14) gr,
  *      [14,15) wr (weights 8/4/2/1 of Section 3.4.3).
+ *   R7b gp (Greedy-Potential, Section 2.2 and the weights of Section 3.5.1):
+ *      the potential N_p of a candidate is the number of signed pairs that
+ *      occur at least twice after a trial substitution of p -- only pairs with
+ *      the fresh variable can be new; score (c_p - 1) 2^16 + a N_p with the
+ *      run's alpha = a / 2^16 (R8); argmax, lowest key on ties.
  *   R8 alpha = a / 2^16 with a = (u * 32769) >> 32 in [0, 32768];
  *      beta = b / 2^16 with b = 32768 + ((u * 32769) >> 32) in [32768, 65536];
  *      both drawn at the start of every run.  gi score
@@ -51,7 +56,7 @@
  *   R11 run start: close the old run into the process best (strictly lower
  *      cost replaces); strategy = g for process 0's first run, else drawn
  *      from the weights (u * sum) >> 32 against cumulative weights in the
- *      order gi, ga, gr, wr, mix, g; if a snapshot exists and
+ *      order gi, ga, gr, wr, mix, g, gp; if a snapshot exists and
  *      u < floor(permille * 2^32 / 1000), L = snapshot length, K = floor(3L/4),
  *      and if K >= 1 the first k = 1 + ((u' * K) >> 32) substitutions of the
  *      snapshot are replayed (Section 3.5.2).  Replays are not steps.
@@ -379,6 +384,63 @@ int32_t oracle_gi_scores_coins(const uint32_t* keys, const int32_t* counts, int3
     return sel_gi(keys, counts, m, a, b, &cs, score, NULL);
 }
 
+/* Greedy-Potential: a trial substitution of every candidate on a copy of
+ * the expressions, then a recount of the pairs that contain the fresh
+ * variable x_k (the only pairs whose count can grow). */
+static int32_t gp_potential(const int8_t* coef, int32_t rows, int32_t ncols, int32_t stride, uint32_t key,
+                            int8_t* trial, uint32_t* scratch, int32_t* live_out) {
+    memcpy(trial, coef, (size_t)rows * (size_t)stride);
+    const int32_t k = ncols;
+    substitute(trial, rows, stride, k, (int32_t)KEY_I(key), (int32_t)KEY_J(key), (int32_t)KEY_NEG(key));
+    int64_t n = 0;
+    for (int32_t r = 0; r < rows; r++) {
+        const int8_t* row = trial + (int64_t)r * stride;
+        if (!row[k]) continue;
+        for (int32_t u = 0; u < k; u++)
+            if (row[u]) scratch[n++] = KEY(u, k, row[u] * row[k] < 0);
+    }
+    qsort(scratch, (size_t)n, sizeof(uint32_t), cmp_u32);
+    int32_t pot = 0;
+    for (int64_t a = 0; a < n;) {
+        int64_t b = a;
+        while (b < n && scratch[b] == scratch[a]) b++;
+        pot += (b - a) >= 2;
+        a = b;
+    }
+    if (live_out) {
+        int32_t live = 0;
+        for (int32_t u = 0; u < k; u++) {
+            int32_t any = 0;
+            for (int32_t r = 0; r < rows && !any; r++) any = trial[(int64_t)r * stride + u] != 0;
+            live += any;
+        }
+        *live_out = live;
+    }
+    return pot;
+}
+
+int32_t oracle_gp_potentials(const int8_t* mat, int32_t rows, int32_t cols, int32_t* pot, int32_t max_out) {
+    const int32_t stride = cols + 1;
+    int8_t* coef = (int8_t*)calloc((size_t)rows * (size_t)stride, 1);
+    int8_t* trial = (int8_t*)calloc((size_t)rows * (size_t)stride, 1);
+    for (int32_t r = 0; r < rows; r++)
+        for (int32_t v = 0; v < cols; v++) coef[(int64_t)r * stride + v] = mat[(int64_t)r * cols + v];
+    int64_t occ = max_pair_occurrences(mat, rows, cols, cols);
+    uint32_t* scratch = (uint32_t*)malloc((size_t)(occ + (int64_t)rows * stride + 1) * 4);
+    uint32_t* keys = (uint32_t*)malloc((size_t)(occ + 1) * 4);
+    int32_t* cnt = (int32_t*)malloc((size_t)(occ + 1) * 4);
+    int32_t nz[1024];
+    int32_t m = count_pairs(coef, rows, cols, stride, 2, scratch, nz, keys, cnt, (int32_t)occ + 1);
+    for (int32_t p = 0; p < m && p < max_out; p++)
+        pot[p] = gp_potential(coef, rows, cols, stride, keys[p], trial, scratch, NULL);
+    free(coef);
+    free(trial);
+    free(scratch);
+    free(keys);
+    free(cnt);
+    return m;
+}
+
 /* ------------------------------------------------------------------ */
 /* Brute force over Algorithm 1 sequences (tiny matrices, test pin)     */
 /* ------------------------------------------------------------------ */
@@ -510,6 +572,7 @@ typedef struct {
 typedef struct {
     uint32_t* scratch;
     int32_t* nz;
+    int8_t* trial;  /* Greedy-Potential trial copy of the expressions */
 } work_t;
 
 static int64_t run_cost(const search_t* S, const mat_t* M, const proc_t* P) {
@@ -616,10 +679,10 @@ static void start_run(const search_t* S, int32_t mi, int32_t pi, int64_t t, work
     P->traj = fnv(P->traj, 0xA0000000u | (uint32_t)P->strategy << 12 | (uint32_t)k);
 }
 
-static int32_t choose(const search_t* S, int32_t mi, int32_t pi, int64_t t, proc_t* P) {
+static int32_t choose(const search_t* S, int32_t mi, int32_t pi, int64_t t, proc_t* P, work_t* wk) {
     int32_t strat = P->strategy;
     uint32_t d[4] = {0, 0, 0, 0};
-    if (strat != OR_G && strat != OR_GI) draw4(S->seed, pi, t, mi, PU_STEP, 0, 0, d);
+    if (strat != OR_G && strat != OR_GI && strat != OR_GP) draw4(S->seed, pi, t, mi, PU_STEP, 0, 0, d);
     if (strat == OR_MIX) {
         uint32_t r = scale(d[0], 15);
         strat = r < 8 ? OR_GI : r < 12 ? OR_GA : r < 14 ? OR_GR : OR_WR;
@@ -643,6 +706,23 @@ static int32_t choose(const search_t* S, int32_t mi, int32_t pi, int64_t t, proc
             P->ops += ops;
             return sel;
         }
+        case OR_GP: {
+            const mat_t* M = &S->mats[mi];
+            int32_t best = -1;
+            int64_t best_s = 0;
+            for (int32_t p = 0; p < P->m; p++) {
+                int32_t live = 0;
+                int32_t pot = gp_potential(P->coef, M->rows, P->ncols, S->cap, P->keys[p], wk->trial, wk->scratch,
+                                           &live);
+                int64_t sc = ((int64_t)(P->cnt[p] - 1) << 16) + (int64_t)P->a * pot;
+                if (best < 0 || sc > best_s) {
+                    best = p;
+                    best_s = sc;
+                }
+                P->ops += 5 * (int64_t)M->w32 * live + 8;
+            }
+            return best;
+        }
         default: return -1;
     }
 }
@@ -655,7 +735,7 @@ static void step(const search_t* S, int32_t mi, int32_t pi, int64_t t, work_t* w
         P->ended = 1;
         return;
     }
-    int32_t sel = choose(S, mi, pi, t, P);
+    int32_t sel = choose(S, mi, pi, t, P, wk);
     uint32_t key = P->keys[sel];
     do_subst(S, M, P, wk, key);
     P->substeps++;
@@ -696,7 +776,7 @@ static int valid_matrix(const int8_t* m, int32_t rows, int32_t cols) {
 }
 
 int oracle_search(int32_t n_mats, const int8_t* const* mats, const int32_t* rows,
-                  const int32_t* cols, const uint32_t* weights6, int32_t n_proc, uint64_t seed,
+                  const int32_t* cols, const uint32_t* weights7, int32_t n_proc, uint64_t seed,
                   int64_t budget, int32_t interval, int32_t permille, int32_t cap,
                   int32_t n_threads, const int32_t* proc_subset, int32_t n_subset,
                   int64_t* out_cost, int32_t* out_len, int32_t* out_list, oracle_digest* dig) {
@@ -712,8 +792,8 @@ int oracle_search(int32_t n_mats, const int8_t* const* mats, const int32_t* rows
     S.cap = cap;
     S.seed = seed;
     for (int32_t s = 0; s < OR_NSTRAT; s++) {
-        S.w[s] = weights6[s];
-        S.wsum += weights6[s];
+        S.w[s] = weights7[s];
+        S.wsum += weights7[s];
     }
     if (S.wsum == 0 || S.wsum > 0xFFFFFFFFull) return -1;
     for (int32_t mi = 0; mi < n_mats; mi++)
@@ -736,7 +816,7 @@ int oracle_search(int32_t n_mats, const int8_t* const* mats, const int32_t* rows
 
     S.mats = (mat_t*)calloc((size_t)n_mats, sizeof(mat_t));
     int64_t max_occ_all = 0;
-    int32_t max_cols = 0;
+    int32_t max_cols = 0, max_rows = 0;
     for (int32_t mi = 0; mi < n_mats; mi++) {
         mat_t* M = &S.mats[mi];
         M->orig = mats[mi];
@@ -747,6 +827,7 @@ int oracle_search(int32_t n_mats, const int8_t* const* mats, const int32_t* rows
         M->max_occ = max_pair_occurrences(mats[mi], rows[mi], cols[mi], cols[mi]);
         if (M->max_occ > max_occ_all) max_occ_all = M->max_occ;
         if (cols[mi] > max_cols) max_cols = cols[mi];
+        if (rows[mi] > max_rows) max_rows = rows[mi];
         M->snap_cost = INT64_MAX;
         M->snap = (int32_t*)calloc((size_t)cap, sizeof(int32_t));
         M->procs = (proc_t*)calloc((size_t)n_proc, sizeof(proc_t));
@@ -769,8 +850,9 @@ int oracle_search(int32_t n_mats, const int8_t* const* mats, const int32_t* rows
     pthread_t* th = (pthread_t*)calloc((size_t)n_threads, sizeof(pthread_t));
     for (int32_t k = 0; k < n_threads; k++) {
         jobs[k].S = &S;
-        jobs[k].wk.scratch = (uint32_t*)malloc((size_t)(max_occ_all + 1) * sizeof(uint32_t));
+        jobs[k].wk.scratch = (uint32_t*)malloc((size_t)(max_occ_all + (int64_t)max_rows * cap + 1) * sizeof(uint32_t));
         jobs[k].wk.nz = (int32_t*)malloc((size_t)(cap + 1) * sizeof(int32_t));
+        jobs[k].wk.trial = (int8_t*)malloc((size_t)max_rows * (size_t)cap);
         jobs[k].u0 = units * k / n_threads;
         jobs[k].u1 = units * (k + 1) / n_threads;
     }
@@ -840,6 +922,7 @@ int oracle_search(int32_t n_mats, const int8_t* const* mats, const int32_t* rows
     for (int32_t k = 0; k < n_threads; k++) {
         free(jobs[k].wk.scratch);
         free(jobs[k].wk.nz);
+        free(jobs[k].wk.trial);
     }
     free(jobs);
     free(th);

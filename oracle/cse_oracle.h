@@ -22,7 +22,7 @@ extern "C" {
 #endif
 
 /* Strategy indices (Section 3.4); weights are given in this order. */
-enum { OR_GI = 0, OR_GA = 1, OR_GR = 2, OR_WR = 3, OR_MIX = 4, OR_G = 5, OR_NSTRAT = 6 };
+enum { OR_GI = 0, OR_GA = 1, OR_GR = 2, OR_WR = 3, OR_MIX = 4, OR_G = 5, OR_GP = 6, OR_NSTRAT = 7 };
 
 /* Per-process summary used by the parity tests. */
 typedef struct {
@@ -66,18 +66,24 @@ int32_t oracle_select_basic(int32_t kind, const int32_t* counts, int32_t m, cons
 int32_t oracle_gi_scores_coins(const uint32_t* keys, const int32_t* counts, int32_t m,
                                uint32_t a, uint32_t b, const uint8_t* coin_bits, int64_t* score);
 
+/* Greedy-Potential potential of every candidate (c >= 2, canonical order) of
+ * a matrix: N_p = number of signed pairs that occur at least twice after a
+ * trial substitution of p, all of which contain the fresh variable.  Writes
+ * up to max_out values; returns the number of candidates. */
+int32_t oracle_gp_potentials(const int8_t* mat, int32_t rows, int32_t cols, int32_t* pot, int32_t max_out);
+
 /* Exhaustive minimum of Cost over all sequences of Algorithm 1 on a tiny
  * matrix (rows * cols small).  Returns the optimum, or -1 on overflow. */
 int64_t oracle_bruteforce(const int8_t* mat, int32_t rows, int32_t cols, int32_t cap);
 
 /* The full search (Sections 3.3-3.5, Algorithm 1) over n_mats expression sets.
- * weights6: gi, ga, gr, wr, mix, g.  Outputs per matrix: best cost, length,
+ * weights7: gi, ga, gr, wr, mix, g, gp.  Outputs per matrix: best cost, length,
  * list (cap entries per matrix).  dig: n_mats * n_proc digests or NULL.
  * proc_subset: if non-NULL, only these processes are simulated (exact only
  * while no snapshot is published, i.e. budget <= interval).
  * Returns 0, or a negative error code for invalid arguments. */
 int oracle_search(int32_t n_mats, const int8_t* const* mats, const int32_t* rows,
-                  const int32_t* cols, const uint32_t* weights6, int32_t n_proc, uint64_t seed,
+                  const int32_t* cols, const uint32_t* weights7, int32_t n_proc, uint64_t seed,
                   int64_t budget, int32_t interval, int32_t permille, int32_t cap,
                   int32_t n_threads, const int32_t* proc_subset, int32_t n_subset,
                   int64_t* out_cost, int32_t* out_len, int32_t* out_list, oracle_digest* dig);

@@ -20,7 +20,8 @@ _LIB = os.path.join(_HERE, "_build", "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-G, GI, GA, GR, WR, MIX = 5, 0, 1, 2, 3, 4
+G, GI, GA, GR, WR, MIX, GP = 5, 0, 1, 2, 3, 4, 6
+N_STRATEGIES = 7
 
 
 class Digest(ctypes.Structure):
@@ -68,6 +69,8 @@ def lib():
         L.oracle_gi_scores_coins.argtypes = [u32p, i32p, ctypes.c_int32, ctypes.c_uint32, ctypes.c_uint32,
                                              ctypes.POINTER(ctypes.c_uint8), i64p]
         L.oracle_gi_scores_coins.restype = ctypes.c_int32
+        L.oracle_gp_potentials.argtypes = [i8p, ctypes.c_int32, ctypes.c_int32, i32p, ctypes.c_int32]
+        L.oracle_gp_potentials.restype = ctypes.c_int32
         L.oracle_bruteforce.argtypes = [i8p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]
         L.oracle_bruteforce.restype = ctypes.c_int64
         L.oracle_search.argtypes = [ctypes.c_int32, ctypes.POINTER(i8p), i32p, i32p, u32p, ctypes.c_int32,
@@ -152,6 +155,15 @@ def gi_scores(keys: Sequence[int], counts: Sequence[int], a: int, b: int, coins:
     return int(best), [int(x) for x in sc]
 
 
+def gp_potentials(mat: np.ndarray) -> List[int]:
+    """Greedy-Potential potential of every candidate (c >= 2) in canonical order."""
+    m = np.ascontiguousarray(mat, dtype=np.int8)
+    cap = m.shape[0] * m.shape[1] * m.shape[1] + 1
+    pot = np.zeros(cap, dtype=np.int32)
+    n = lib().oracle_gp_potentials(_p(m, ctypes.c_int8), m.shape[0], m.shape[1], _p(pot, ctypes.c_int32), cap)
+    return [int(x) for x in pot[:n]]
+
+
 def bruteforce(mat: np.ndarray, cap: Optional[int] = None) -> int:
     m = np.ascontiguousarray(mat, dtype=np.int8)
     if cap is None:
@@ -179,7 +191,10 @@ def search(mats: Sequence[np.ndarray], weights, n_proc: int, seed: int, budget: 
     ptrs = (ctypes.POINTER(ctypes.c_int8) * n)(*[_p(m, ctypes.c_int8) for m in ms])
     rows = np.array([m.shape[0] for m in ms], dtype=np.int32)
     cols = np.array([m.shape[1] for m in ms], dtype=np.int32)
-    w = np.array(list(weights), dtype=np.uint32)
+    w = np.zeros(N_STRATEGIES, dtype=np.uint32)   # gi, ga, gr, wr, mix, g, gp; missing trailing weights are 0
+    if len(weights) > N_STRATEGIES:
+        raise ValueError("at most 7 strategy weights")
+    w[:len(weights)] = list(weights)
     cost = np.zeros(n, dtype=np.int64)
     length = np.zeros(n, dtype=np.int32)
     lists = np.zeros((n, cap), dtype=np.int32)

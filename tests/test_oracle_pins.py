@@ -414,3 +414,90 @@ def test_gi_score_structure(seed):
                     if q != p and ({ip, jp} & set(O.unkey(keys[q])[:2])))
         d = T - (counts[p] - 1) - inter
         assert s0[p] == ((counts[p] - 1) << 32) + a * (d << 16)
+
+
+# ---------------------------------------------------------------- Greedy-Potential
+def _gp_fixture():
+    mat, gp, picks = [], [], {}
+    sec = None
+    for ln in _lines("gp_example.txt"):
+        f = ln.split()
+        if f[0] == "matrix":
+            sec = "matrix"
+        elif f[0] == "gp":
+            gp.append(tuple(int(x) for x in f[1:]))
+        elif f[0].startswith("pick_"):
+            picks[f[0]] = tuple(int(x) for x in f[1:])
+        elif sec == "matrix":
+            mat.append([int(x) for x in f])
+    return np.array(mat, np.int8), gp, picks
+
+
+def _gp_pick(counts, pots, a):
+    """argmax of (c - 1) 2^16 + a N, first in canonical order on ties."""
+    sc = [((c - 1) << 16) + a * n for c, n in zip(counts, pots)]
+    return sc.index(max(sc))
+
+
+def test_gp_hand_derived_potentials():
+    mat, gp, picks = _gp_fixture()
+    cand = O.pairs(mat)
+    assert [(*O.unkey(k), c) for k, c in cand] == [g[:4] for g in gp]
+    assert O.gp_potentials(mat) == [g[4] for g in gp]
+    counts = [c for _, c in cand]
+    pots = [g[4] for g in gp]
+    assert O.unkey(cand[_gp_pick(counts, pots, 1)][0]) == picks["pick_positive"]
+    assert O.unkey(cand[_gp_pick(counts, pots, 32768)][0]) == picks["pick_positive"]
+    assert O.unkey(cand[_gp_pick(counts, pots, 0)][0]) == picks["pick_zero"]
+
+
+def _numpy_potential(mat, i, j, s):
+    """Trial substitution and a from-scratch count of every signed pair of the
+    new rows (all columns, not only the fresh one): the pairs that reach a
+    count of 2 and did not have it before."""
+    cur, _ = expand(mat, [O.entry(i, j, s)])
+
+    def counts(m):
+        c = {}
+        for r in m:
+            idx = np.nonzero(r)[0]
+            for a, b in itertools.combinations(idx, 2):
+                kk = (a, b, int(r[a] * r[b]))
+                c[kk] = c.get(kk, 0) + 1
+        return c
+
+    before, after = counts(mat.astype(np.int64)), counts(cur)
+    return sum(1 for kk, c in after.items() if c >= 2 and before.get(kk, 0) < 2)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_gp_potential_counts_only_new_possibilities(seed):
+    """No pair of old variables can gain occurrences, so the new possibilities
+    are exactly the repeated pairs that contain the fresh variable."""
+    mat = synth.random_matrix(700 + seed, 16, 8, 2, 5, n_planted=5)
+    cand = O.pairs(mat)
+    pots = O.gp_potentials(mat)
+    assert len(pots) == len(cand) > 0
+    for (k, _), n in zip(cand, pots):
+        assert n == _numpy_potential(mat, *O.unkey(k))
+
+
+def test_gp_search_reaches_optimum_on_the_paper_example():
+    """Process 0 runs Greedy first; every other process runs Greedy-Potential
+    (weights gp only), whose first pick on this matrix is x1 - x3 for any
+    alpha > 0; both routes reach the exhaustive optimum 6."""
+    mat, *_ = _example()
+    r = O.search([mat], (0, 0, 0, 0, 0, 0, 1), 8, 3, 4, 64, 0, 16)
+    assert r.cost == [6]
+    assert (r.digests[0]["best_cost"] == 6).all()
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_gp_lists_are_valid_programs(seed):
+    mats = [synth.random_matrix(900 + seed, 14, 9, 2, 5, n_planted=4)]
+    r = O.search(mats, (0, 0, 0, 0, 0, 0, 1), 16, seed, 48, 8, 400, 48)
+    m, lst, cost = mats[0], r.lists[0], r.cost[0]
+    cur, back = expand(m, lst)
+    assert np.array_equal(back, m.astype(np.int64))
+    assert cost_of(cur, len(lst)) == cost
+    assert cost >= O.bruteforce(m) if m.size <= 30 else cost <= O.naive(m)
