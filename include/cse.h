@@ -65,8 +65,11 @@ typedef struct cse_server cse_server;
 /* Integer strategy weights (Section 3.5.1): the paper's gi 8, ga 4, gr 2,
  * wr 1, mix 0.1, gp 0.01 become 800, 400, 200, 100, 10 and 1 here.  w_g is
  * Greedy (the paper gives it weight 0 apart from process 0's first run).
- * Greedy-Potential is not implemented: w_gp must be 0.  At least one weight
- * must be nonzero; the sum must fit in 32 bits. */
+ * w_gp is Greedy-Potential (Section 2.2): every candidate is scored by a trial
+ * substitution, (c - 1) 2^16 + a N with N the number of pairs that then occur
+ * at least twice and a the run's alpha in units of 2^-16.  A run draws its
+ * strategy from the weights in the order gi, ga, gr, wr, mix, g, gp.  At least
+ * one weight must be nonzero; the sum must fit in 32 bits. */
 typedef struct {
     uint32_t w_gi, w_ga, w_gr, w_wr, w_mix, w_g, w_gp;
 } cse_strategy_mix;

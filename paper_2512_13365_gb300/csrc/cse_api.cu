@@ -176,8 +176,7 @@ static void search_free(SearchDev* sd) {
 
 static int check_mix(const cse_strategy_mix* mix, uint64_t* wsum_out) {
     if (!mix) return fail(CSE_EINVAL, "NULL strategy mix");
-    if (mix->w_gp != 0) return fail(CSE_EINVAL, "Greedy-Potential (w_gp) is not implemented; set it to 0");
-    const uint64_t wsum = (uint64_t)mix->w_gi + mix->w_ga + mix->w_gr + mix->w_wr + mix->w_mix + mix->w_g;
+    const uint64_t wsum = (uint64_t)mix->w_gi + mix->w_ga + mix->w_gr + mix->w_wr + mix->w_mix + mix->w_g + mix->w_gp;
     if (wsum == 0 || wsum > 0xFFFFFFFFull) return fail(CSE_EINVAL, "strategy weights: sum must be in [1, 2^32)");
     *wsum_out = wsum;
     return CSE_OK;
@@ -272,6 +271,7 @@ static int search_create(const cse_scheme* s, const cse_strategy_mix* mix, int n
     S.w[ST_WR] = mix->w_wr;
     S.w[ST_MIX] = mix->w_mix;
     S.w[ST_G] = mix->w_g;
+    S.w[ST_GP] = mix->w_gp;
     S.wsum = (uint32_t)wsum;
     S.budget = (int32_t)budget;
     S.interval = (int32_t)opts.share_interval;

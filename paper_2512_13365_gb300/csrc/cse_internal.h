@@ -23,7 +23,7 @@ struct cse_scheme {
 namespace cse {
 
 // Strategy indices, in the order of the weights of cse_strategy_mix.
-enum Strategy : int { ST_GI = 0, ST_GA = 1, ST_GR = 2, ST_WR = 3, ST_MIX = 4, ST_G = 5, ST_N = 6 };
+enum Strategy : int { ST_GI = 0, ST_GA = 1, ST_GR = 2, ST_WR = 3, ST_MIX = 4, ST_G = 5, ST_GP = 6, ST_N = 7 };
 
 // Purposes of the Philox draws (third counter word, bits 20..23).
 //   RUN    at a run start: lane 0 strategy, 1 alpha, 2 beta, 3 share coin

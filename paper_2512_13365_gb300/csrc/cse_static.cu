@@ -75,8 +75,7 @@ extern "C" int cse_search_static(const cse_scheme* s, const cse_strategy_mix* mi
     if (opts.share_interval < 1 || opts.share_permille > 1000 || opts.patience_rounds != 0 ||
         (opts.flags & ~(uint32_t)(CSE_FLAG_GRAPH | CSE_FLAG_TRACE)) != 0 || opts.col_cap > CSE_MAX_COLS || opts.procs_per_cta > 4)
         return set_error(CSE_EINVAL, "invalid options");
-    if (mix->w_gp != 0) return set_error(CSE_EINVAL, "Greedy-Potential (w_gp) is not implemented; set it to 0");
-    const uint64_t wsum = (uint64_t)mix->w_gi + mix->w_ga + mix->w_gr + mix->w_wr + mix->w_mix + mix->w_g;
+    const uint64_t wsum = (uint64_t)mix->w_gi + mix->w_ga + mix->w_gr + mix->w_wr + mix->w_mix + mix->w_g + mix->w_gp;
     if (wsum == 0 || wsum > 0xFFFFFFFFull) return set_error(CSE_EINVAL, "strategy weights: sum must be in [1, 2^32)");
     if (n_proc < 1 || n_proc > (1 << 20)) return set_error(CSE_EINVAL, "n_processes must be in [1, 2^20]");
     if (budget < 0 || budget >= INT32_MAX) return set_error(CSE_EINVAL, "step_budget must be in [0, 2^31)");
@@ -130,6 +129,7 @@ extern "C" int cse_search_static(const cse_scheme* s, const cse_strategy_mix* mi
     S.w[ST_WR] = mix->w_wr;
     S.w[ST_MIX] = mix->w_mix;
     S.w[ST_G] = mix->w_g;
+    S.w[ST_GP] = mix->w_gp;
     S.wsum = (uint32_t)wsum;
     S.budget = (int32_t)budget;
     S.interval = (int32_t)opts.share_interval;

@@ -127,7 +127,7 @@ class Search:
 
     name: str
     mats: List[np.ndarray]
-    weights: Tuple[int, int, int, int, int, int]  # gi, ga, gr, wr, mix, g (x100 of the paper's)
+    weights: Tuple[int, ...]  # gi, ga, gr, wr, mix, g[, gp] (x100 of the paper's); missing gp = 0
     n_proc: int
     seed: int
     budget: int
@@ -139,9 +139,12 @@ class Search:
         return len(self.mats) * self.n_proc * self.budget
 
 
-# Strategy weights of Section 3.5.1 (x100, Greedy-Potential excluded).
-PAPER_WEIGHTS = (800, 400, 200, 100, 10, 0)
+# The default strategy weights of Section 3.5.1 (x100): gi 8, ga 4, gr 2,
+# wr 1, mix 0.1, gp 0.01; and the same without Greedy-Potential.
+PAPER_WEIGHTS = (800, 400, 200, 100, 10, 0, 1)
+PAPER_WEIGHTS_NO_GP = (800, 400, 200, 100, 10, 0)
 GI_ONLY = (1, 0, 0, 0, 0, 0)
+GP_ONLY = (0, 0, 0, 0, 0, 0, 1)
 
 
 def config1(n_proc: int = 64, budget: int = 200) -> Search:

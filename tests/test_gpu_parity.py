@@ -63,7 +63,8 @@ def test_word_widths(cse, rows):
 
 
 @pytest.mark.parametrize("weights", [synth.GI_ONLY, (0, 1, 0, 0, 0, 0), (0, 0, 1, 0, 0, 0), (0, 0, 0, 1, 0, 0),
-                                     (0, 0, 0, 0, 1, 0), (0, 0, 0, 0, 0, 1), synth.PAPER_WEIGHTS])
+                                     (0, 0, 0, 0, 1, 0), (0, 0, 0, 0, 0, 1), synth.GP_ONLY, synth.PAPER_WEIGHTS,
+                                     synth.PAPER_WEIGHTS_NO_GP])
 def test_each_strategy(cse, weights):
     s = synth.config2(n_proc=64, budget=96)
     s.weights = weights
@@ -126,7 +127,7 @@ def test_invalid_search_arguments(cse):
     with pytest.raises(cse.CseError):
         cse.search(sc, (0,) * 6, 4, 0, 10)                    # all weights zero
     with pytest.raises(cse.CseError):
-        cse.search(sc, (1, 0, 0, 0, 0, 0, 1), 4, 0, 10)       # Greedy-Potential
+        cse.search(sc, (0xFFFFFFFF, 0, 0, 0, 0, 0, 1), 4, 0, 10)  # weight sum above 32 bits
     with pytest.raises(cse.CseError):
         cse.search(sc, synth.GI_ONLY, 4, 0, 10, cap=7)         # cap <= cols
     with pytest.raises(cse.CseError):
@@ -165,6 +166,21 @@ def test_large_matrices_run_from_hbm(cse):
     the HBM state region.  Reduced process count and budget."""
     s = synth.config4(n_proc=24, budget=48)
     s.interval = 16
+    assert_parity(cse, s)
+
+
+@pytest.mark.parametrize("rows", [20, 64, 130, 256])
+def test_greedy_potential_word_widths(cse, rows):
+    # trial columns of W = 1, 2, 5 and 8 words; Greedy-Potential in every run
+    mats = [synth.random_matrix(rows + 5, rows, 10, 2, 5, n_planted=6),
+            synth.random_matrix(rows + 6, 14, min(rows, 40), 2, 5, n_planted=3)]
+    s = synth.Search(f"gp{rows}", mats, synth.GP_ONLY, 21, 4, 40, 16, 400, 96)
+    assert_parity(cse, s)
+
+
+def test_greedy_potential_from_hbm(cse):
+    s = synth.config4(n_proc=6, budget=12)
+    s.weights, s.interval = (0, 0, 0, 0, 0, 1, 3), 8
     assert_parity(cse, s)
 
 
