@@ -67,6 +67,17 @@
  *      that snapshot.
  *   R13 end of budget: every process folds its current run; the result per
  *      matrix is the lowest (best cost, process).
+ *   R14 iteration mode (Sections 3.5.2 and 4: the paper's own schedule).
+ *      Iteration tau: every process performs one whole run, from its start
+ *      (strategy, alpha, beta, share coin and prefix replay as in R11) until
+ *      it ends; its steps carry the clock values t = tau * cap, tau * cap + 1,
+ *      ... (a run has fewer than cap steps, so every draw keeps its own
+ *      counter).  After the iteration every process folds, and the snapshot
+ *      takes the lowest (best cost, process) if strictly lower.  The search
+ *      stops after max_iterations iterations, or earlier when the sum over
+ *      the matrices of the best cost has not decreased for `patience`
+ *      consecutive iterations (the paper: unchanged for 10; patience 0 never
+ *      stops early).  The first iteration always counts as an improvement.
  */
 #include "cse_oracle.h"
 
@@ -748,6 +759,8 @@ typedef struct {
     const search_t* S;
     int64_t t0, t1;
     int64_t u0, u1; /* unit range: unit = mi * n_sub + subset index */
+    int32_t whole_run; /* iteration mode: one whole run per process, from step t0 */
+    int64_t steps;     /* steps executed by this job (iteration mode) */
     work_t wk;
 } job_t;
 
@@ -757,7 +770,17 @@ static void* run_job(void* arg) {
     for (int64_t u = J->u0; u < J->u1; u++) {
         int32_t mi = (int32_t)(u / S->n_sub);
         int32_t pi = S->subset[u % S->n_sub];
-        for (int64_t t = J->t0; t < J->t1; t++) step(S, mi, pi, t, &J->wk);
+        if (J->whole_run) {
+            /* one iteration of Section 3.5.2: the run goes on until it ends */
+            int64_t t = J->t0;
+            do {
+                step(S, mi, pi, t, &J->wk);
+                t++;
+            } while (!S->mats[mi].procs[pi].ended);
+            J->steps += t - J->t0;
+        } else {
+            for (int64_t t = J->t0; t < J->t1; t++) step(S, mi, pi, t, &J->wk);
+        }
     }
     return NULL;
 }
@@ -775,14 +798,20 @@ static int valid_matrix(const int8_t* m, int32_t rows, int32_t cols) {
     return 1;
 }
 
-int oracle_search(int32_t n_mats, const int8_t* const* mats, const int32_t* rows,
-                  const int32_t* cols, const uint32_t* weights7, int32_t n_proc, uint64_t seed,
-                  int64_t budget, int32_t interval, int32_t permille, int32_t cap,
-                  int32_t n_threads, const int32_t* proc_subset, int32_t n_subset,
-                  int64_t* out_cost, int32_t* out_len, int32_t* out_list, oracle_digest* dig) {
-    if (n_mats < 1 || n_mats > 256 || n_proc < 1 || budget < 0 || interval < 1 ||
+/* The search in either mode.  interval >= 1: the step clock (R10-R13),
+ * budget = steps.  interval == 0: iteration mode (R14), budget = maximum
+ * iterations, patience as stated there.  stats (may be NULL): [0] rounds
+ * run (steps rounded up to intervals, or iterations), [1] process-steps. */
+static int search_impl(int32_t n_mats, const int8_t* const* mats, const int32_t* rows,
+                       const int32_t* cols, const uint32_t* weights7, int32_t n_proc, uint64_t seed,
+                       int64_t budget, int32_t interval, int32_t patience, int32_t permille, int32_t cap,
+                       int32_t n_threads, const int32_t* proc_subset, int32_t n_subset,
+                       int64_t* out_cost, int32_t* out_len, int32_t* out_list, oracle_digest* dig,
+                       int64_t* stats) {
+    if (n_mats < 1 || n_mats > 256 || n_proc < 1 || budget < 0 || interval < 0 || patience < 0 ||
         permille < 0 || permille > 1000 || cap < 2 || cap > 1024)
         return -1;
+    if (interval == 0 && (proc_subset || budget > INT32_MAX / cap)) return -1;
     search_t S;
     memset(&S, 0, sizeof S);
     S.n_mats = n_mats;
@@ -857,11 +886,17 @@ int oracle_search(int32_t n_mats, const int8_t* const* mats, const int32_t* rows
         jobs[k].u1 = units * (k + 1) / n_threads;
     }
 
-    for (int64_t t0 = 0; t0 < budget; t0 += interval) {
-        int64_t t1 = t0 + interval < budget ? t0 + interval : budget;
+    int64_t rounds = 0, psteps = 0;
+    int64_t best_total = INT64_MAX;
+    int32_t stale = 0;
+    const int64_t n_rounds = interval > 0 ? (budget + interval - 1) / interval : budget;
+    for (int64_t rd = 0; rd < n_rounds; rd++) {
+        int64_t t0 = interval > 0 ? rd * interval : rd * cap;
+        int64_t t1 = interval > 0 ? (t0 + interval < budget ? t0 + interval : budget) : t0;
         for (int32_t k = 0; k < n_threads; k++) {
             jobs[k].t0 = t0;
             jobs[k].t1 = t1;
+            jobs[k].whole_run = interval == 0;
         }
         if (n_threads == 1) {
             run_job(&jobs[0]);
@@ -869,7 +904,10 @@ int oracle_search(int32_t n_mats, const int8_t* const* mats, const int32_t* rows
             for (int32_t k = 0; k < n_threads; k++) pthread_create(&th[k], NULL, run_job, &jobs[k]);
             for (int32_t k = 0; k < n_threads; k++) pthread_join(th[k], NULL);
         }
+        rounds++;
+        if (interval > 0) psteps += (t1 - t0) * n_mats * S.n_sub;
         /* sharing boundary (or end of budget): fold, then publish */
+        int64_t total = 0;
         for (int32_t mi = 0; mi < n_mats; mi++) {
             mat_t* M = &S.mats[mi];
             int32_t win = -1;
@@ -881,12 +919,30 @@ int oracle_search(int32_t n_mats, const int8_t* const* mats, const int32_t* rows
                 if (!M->procs[p].coef) continue;
                 if (win < 0 || M->procs[p].best_cost < M->procs[win].best_cost) win = p;
             }
-            if (t1 % interval == 0 && win >= 0 && M->procs[win].best_cost < M->snap_cost) {
+            int boundary = interval > 0 ? (t1 % interval == 0) : 1;
+            if (boundary && win >= 0 && M->procs[win].best_cost < M->snap_cost) {
                 M->snap_cost = M->procs[win].best_cost;
                 M->snap_len = M->procs[win].best_len;
                 memcpy(M->snap, M->procs[win].best, (size_t)M->snap_len * sizeof(int32_t));
             }
+            if (win >= 0) total += M->procs[win].best_cost;
         }
+        if (interval == 0) {
+            /* R14: convergence when the scheme's best total has not improved
+             * for `patience` consecutive iterations */
+            if (total < best_total) {
+                best_total = total;
+                stale = 0;
+            } else {
+                stale++;
+            }
+            if (patience > 0 && stale >= patience) break;
+        }
+    }
+    for (int32_t k = 0; k < n_threads; k++) psteps += jobs[k].steps;
+    if (stats) {
+        stats[0] = rounds;
+        stats[1] = psteps;
     }
     /* budget == 0: results are the inputs */
 
@@ -942,4 +998,23 @@ int oracle_search(int32_t n_mats, const int8_t* const* mats, const int32_t* rows
     free(S.mats);
     free(all);
     return 0;
+}
+
+int oracle_search(int32_t n_mats, const int8_t* const* mats, const int32_t* rows,
+                  const int32_t* cols, const uint32_t* weights7, int32_t n_proc, uint64_t seed,
+                  int64_t budget, int32_t interval, int32_t permille, int32_t cap,
+                  int32_t n_threads, const int32_t* proc_subset, int32_t n_subset,
+                  int64_t* out_cost, int32_t* out_len, int32_t* out_list, oracle_digest* dig) {
+    if (interval < 1) return -1;
+    return search_impl(n_mats, mats, rows, cols, weights7, n_proc, seed, budget, interval, 0, permille, cap,
+                       n_threads, proc_subset, n_subset, out_cost, out_len, out_list, dig, NULL);
+}
+
+int oracle_search_iterations(int32_t n_mats, const int8_t* const* mats, const int32_t* rows,
+                             const int32_t* cols, const uint32_t* weights7, int32_t n_proc, uint64_t seed,
+                             int64_t max_iterations, int32_t patience, int32_t permille, int32_t cap,
+                             int32_t n_threads, int64_t* out_cost, int32_t* out_len, int32_t* out_list,
+                             oracle_digest* dig, int64_t* stats) {
+    return search_impl(n_mats, mats, rows, cols, weights7, n_proc, seed, max_iterations, 0, patience, permille,
+                       cap, n_threads, NULL, 0, out_cost, out_len, out_list, dig, stats);
 }

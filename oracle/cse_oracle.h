@@ -88,6 +88,17 @@ int oracle_search(int32_t n_mats, const int8_t* const* mats, const int32_t* rows
                   int32_t n_threads, const int32_t* proc_subset, int32_t n_subset,
                   int64_t* out_cost, int32_t* out_len, int32_t* out_list, oracle_digest* dig);
 
+/* The search in iteration mode (Sections 3.5.2 and 4; R14 in cse_oracle.c):
+ * every process performs one whole run per iteration, sharing happens between
+ * iterations, and the search ends after max_iterations iterations or when the
+ * total best cost has not improved for `patience` consecutive iterations
+ * (0: never early).  stats (or NULL): [0] iterations run, [1] process-steps. */
+int oracle_search_iterations(int32_t n_mats, const int8_t* const* mats, const int32_t* rows,
+                             const int32_t* cols, const uint32_t* weights7, int32_t n_proc, uint64_t seed,
+                             int64_t max_iterations, int32_t patience, int32_t permille, int32_t cap,
+                             int32_t n_threads, int64_t* out_cost, int32_t* out_len, int32_t* out_list,
+                             oracle_digest* dig, int64_t* stats);
+
 #ifdef __cplusplus
 }
 #endif

@@ -78,6 +78,11 @@ def lib():
                                     ctypes.c_int32, ctypes.c_int32, i32p, ctypes.c_int32, i64p, i32p, i32p,
                                     ctypes.POINTER(Digest)]
         L.oracle_search.restype = ctypes.c_int
+        L.oracle_search_iterations.argtypes = [ctypes.c_int32, ctypes.POINTER(i8p), i32p, i32p, u32p, ctypes.c_int32,
+                                               ctypes.c_uint64, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                               ctypes.c_int32, ctypes.c_int32, i64p, i32p, i32p,
+                                               ctypes.POINTER(Digest), i64p]
+        L.oracle_search_iterations.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -209,6 +214,38 @@ def search(mats: Sequence[np.ndarray], weights, n_proc: int, seed: int, budget: 
         raise ValueError(f"oracle_search rejected its arguments (rc={rc})")
     return SearchResult([int(x) for x in cost], [int(x) for x in length],
                         [[int(e) for e in lists[k, :length[k]]] for k in range(n)], dig)
+
+
+def search_iterations(mats: Sequence[np.ndarray], weights, n_proc: int, seed: int, max_iterations: int,
+                      patience: int, permille: int, cap: int, n_threads: int = 1,
+                      digests: bool = True) -> SearchResult:
+    """Iteration mode (the paper's schedule): one whole run per process per
+    iteration, sharing between iterations, stop on patience.  The result's
+    `iterations` and `process_steps` say how long it ran."""
+    ms = [np.ascontiguousarray(m, dtype=np.int8) for m in mats]
+    n = len(ms)
+    ptrs = (ctypes.POINTER(ctypes.c_int8) * n)(*[_p(m, ctypes.c_int8) for m in ms])
+    rows = np.array([m.shape[0] for m in ms], dtype=np.int32)
+    cols = np.array([m.shape[1] for m in ms], dtype=np.int32)
+    w = np.zeros(N_STRATEGIES, dtype=np.uint32)
+    w[:len(weights)] = list(weights)
+    cost = np.zeros(n, dtype=np.int64)
+    length = np.zeros(n, dtype=np.int32)
+    lists = np.zeros((n, cap), dtype=np.int32)
+    dig = np.zeros((n, n_proc), dtype=DIGEST_DTYPE) if digests else None
+    stats = np.zeros(2, dtype=np.int64)
+    rc = lib().oracle_search_iterations(n, ptrs, _p(rows, ctypes.c_int32), _p(cols, ctypes.c_int32),
+                                        _p(w, ctypes.c_uint32), n_proc, seed, max_iterations, patience, permille,
+                                        cap, n_threads, _p(cost, ctypes.c_int64), _p(length, ctypes.c_int32),
+                                        _p(lists, ctypes.c_int32),
+                                        None if dig is None else dig.ctypes.data_as(ctypes.POINTER(Digest)),
+                                        _p(stats, ctypes.c_int64))
+    if rc != 0:
+        raise ValueError(f"oracle_search_iterations rejected its arguments (rc={rc})")
+    r = SearchResult([int(x) for x in cost], [int(x) for x in length],
+                     [[int(e) for e in lists[k, :length[k]]] for k in range(n)], dig)
+    r.iterations, r.process_steps = int(stats[0]), int(stats[1])
+    return r
 
 
 def search_obj(s, **kw) -> SearchResult:

@@ -501,3 +501,45 @@ def test_gp_lists_are_valid_programs(seed):
     assert np.array_equal(back, m.astype(np.int64))
     assert cost_of(cur, len(lst)) == cost
     assert cost >= O.bruteforce(m) if m.size <= 30 else cost <= O.naive(m)
+
+
+# ---------------------------------------------------------------- iteration mode
+def test_iteration_mode_closed_forms_on_the_example():
+    """Greedy alone on the worked example: every run takes (x1 - x2), then
+    (x3 - x4), and ends after 2 steps at Cost 6.  Without sharing each
+    iteration costs 2 steps per process; the first iteration improves the
+    total and the next `patience` do not, so the search stops after
+    patience + 1 iterations.  With sharing at 100%, K = floor(3 * 2 / 4) = 1
+    and every later run replays (x1 - x2) and needs a single step."""
+    mat, *_ = _example()
+    P, pat = 5, 4
+    r = O.search_iterations([mat], (0, 0, 0, 0, 0, 1), P, 0, 100, pat, 0, 16)
+    assert r.cost == [6] and r.iterations == pat + 1
+    assert r.process_steps == 2 * P * (pat + 1)
+    assert (r.digests[0]["runs"] == pat + 1).all() and (r.digests[0]["substeps"] == 2 * (pat + 1)).all()
+    r = O.search_iterations([mat], (0, 0, 0, 0, 0, 1), P, 0, 100, pat, 1000, 16)
+    assert r.iterations == pat + 1 and r.process_steps == P * (2 + pat)
+    assert (r.digests[0]["substeps"] == 2 + pat).all()
+    # patience 0: exactly the maximum number of iterations
+    r = O.search_iterations([mat], (0, 0, 0, 0, 0, 1), P, 0, 7, 0, 0, 16)
+    assert r.iterations == 7 and r.process_steps == 2 * P * 7
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_iteration_mode_stopping_rule(seed):
+    """Stopped by patience p after I iterations: the last p iterations did not
+    improve and iteration I - p did.  So a run capped at I - p iterations has
+    the same costs (the lists may differ: a lower-numbered process can tie the
+    best later), and one capped at I - p - 1 a strictly larger total."""
+    mats = [synth.random_matrix(600 + seed, 16, 8, 2, 5, n_planted=5),
+            synth.random_matrix(650 + seed, 8, 14, 2, 5, n_planted=3)]
+    p = 3
+    a = O.search_iterations(mats, synth.PAPER_WEIGHTS, 24, seed, 200, p, 400, 48)
+    assert p < a.iterations < 200
+    b = O.search_iterations(mats, synth.PAPER_WEIGHTS, 24, seed, a.iterations - p, 0, 400, 48)
+    assert b.cost == a.cost
+    c = O.search_iterations(mats, synth.PAPER_WEIGHTS, 24, seed, a.iterations - p - 1, 0, 400, 48)
+    assert sum(c.cost) > sum(a.cost)
+    for k, m in enumerate(mats):
+        cur, back = expand(m, a.lists[k])
+        assert np.array_equal(back, m.astype(np.int64)) and cost_of(cur, len(a.lists[k])) == a.cost[k]
