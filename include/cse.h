@@ -82,13 +82,28 @@ typedef struct {
                               cse_proc_record); costs a few per cent */
 
 /* Search options.  Fields that change results: share_interval,
- * share_permille, col_cap.  The rest only change how the work is launched. */
+ * share_permille, col_cap, patience_rounds.  The rest only change how the
+ * work is launched.
+ *
+ * share_interval >= 1 selects the step clock: every process makes one step
+ * per global step, and sharing happens every share_interval steps.
+ * share_interval = 0 selects iteration mode, the paper's own schedule
+ * (Sections 3.5.2 and 4): in each iteration every process performs one whole
+ * run, from its start until no pair repeats (or the columns are used up);
+ * sharing happens between iterations; step_budget is then the maximum number
+ * of iterations, and the search stops earlier once the sum over the matrices
+ * of the best Cost has not decreased for patience_rounds consecutive
+ * iterations (the paper: 10; 0 = never early).  The draws of the steps of
+ * iteration i use the step numbers i * col_cap, i * col_cap + 1, ... */
 typedef struct {
-    uint32_t share_interval;  /* steps between sharing boundaries, >= 1      */
+    uint32_t share_interval;  /* steps between sharing boundaries; 0 =
+                                 iteration mode                               */
     uint32_t share_permille;  /* share probability at a run start, 0..1000
                                  (paper default 40%: 400)                     */
     uint32_t col_cap;         /* column capacity, cols < col_cap <= 512       */
-    uint32_t patience_rounds; /* reserved, must be 0                         */
+    uint32_t patience_rounds; /* iteration mode: iterations without
+                                 improvement that end the search; must be 0
+                                 with the step clock                          */
     uint64_t max_spin;        /* reserved for bounded device waits (unused)  */
     uint32_t procs_per_cta;   /* processes (warps) per CTA; 0 = automatic    */
     uint32_t flags;           /* CSE_FLAG_* bits; other bits must be 0       */
@@ -109,7 +124,9 @@ int cse_scheme_load(const int8_t* const* mats, const int32_t* rows, const int32_
 /* Loads a scheme (m,n,p:r) from its coefficient tensors (Section 3.1):
  * U is r x (m*n), V is r x (n*p), W is r x (m*p), each row-major with the
  * matrix entries in row-major order.  The three sets are E_U = U, E_V = V and
- * E_W = W^T (Section 3.2).  The Brent equations are not checked. */
+ * E_W = W^T (Section 3.2).  The Brent equations are not checked here (see
+ * cse_brent_check): the synthetic stand-ins of real schemes do not satisfy
+ * them, and the elimination does not need them. */
 int cse_scheme_load_uvw(int32_t m, int32_t n, int32_t p, int32_t r, const int8_t* U,
                         const int8_t* V, const int8_t* W, cse_scheme** out);
 
@@ -121,7 +138,12 @@ int cse_scheme_shape(const cse_scheme* s, int32_t mat, int32_t* rows, int32_t* c
  * opts->share_interval steps (Section 3.5.2).  The work is enqueued on
  * cuda_stream (a cudaStream_t, or NULL for the legacy default stream) and the
  * call returns without waiting; *out owns the device state and results.
- * n_processes <= 2^20, 0 <= step_budget < 2^31. */
+ * n_processes <= 2^20, 0 <= step_budget < 2^31.  In iteration mode
+ * (share_interval = 0) the call returns only when the search has finished:
+ * the host reads the convergence state every 4 iterations, so the length of
+ * the launch sequence depends on the data; step_budget (the maximum number
+ * of iterations) times col_cap must stay below 2^31.  CSE_FLAG_GRAPH is
+ * rejected in that mode. */
 int cse_search(const cse_scheme* s, const cse_strategy_mix* mix, int32_t n_processes,
                uint64_t seed, int64_t step_budget, const cse_opts* opts, void* cuda_stream,
                cse_result** out);
@@ -199,7 +221,8 @@ typedef struct {
 int cse_result_procs(const cse_result* r, int32_t mat, cse_proc_record* out);
 
 /* Waits for the search and reports, summed over all matrices and processes:
- * *process_steps = n_mats * n_processes * step_budget, *substeps = steps
+ * *process_steps = n_mats * n_processes * step_budget with the step clock,
+ * the steps the runs actually made in iteration mode, *substeps = steps
  * that made a substitution, *alg_ops = algorithmic integer operations.
  * An algorithmic op count is defined per step from the method's quantities:
  * 10 W for a rewrite plus 5 W per pair count that can change (candidates
@@ -214,6 +237,11 @@ int cse_result_counters(const cse_result* r, int64_t* process_steps, int64_t* su
  * recorded around the round kernels on the search's stream: *round_ms sums
  * the step-engine launches, *total_ms spans the whole search. */
 int cse_result_timing(const cse_result* r, float* round_ms, float* total_ms, int32_t* n_rounds);
+
+/* Iteration mode only (share_interval = 0): waits for the search and reports
+ * the iterations it ran, whether it stopped by the patience rule before its
+ * maximum, and the final sum over the matrices of the best Cost. */
+int cse_result_iterations(const cse_result* r, int32_t* iterations, int32_t* converged, int64_t* best_total);
 
 /* Kernel launches of the search's launch sequence (shared by all searches of
  * a batch) and the number of searches that shared it. */
@@ -235,7 +263,7 @@ void cse_scheme_free(cse_scheme* s);
  * already on the device and leave as soon as their step budget is done.  Each
  * search keeps its own step clock, so a request's result is exactly what
  * cse_search returns for it alone.  Of opts->flags only CSE_FLAG_TRACE is
- * used. */
+ * used.  The server runs the step clock: share_interval = 0 is rejected. */
 int cse_server_create(const cse_opts* opts, uint64_t hbm_budget_bytes, int64_t max_active_processes,
                       cse_server** out);
 

@@ -55,7 +55,7 @@ _lib = None
 # every symbol include/cse.h declares
 EXPORTS = ["cse_opts_default", "cse_scheme_load", "cse_scheme_load_uvw", "cse_scheme_shape", "cse_search",
            "cse_search_batch", "cse_autotune", "cse_tune_interval", "cse_result_fetch", "cse_result_procs", "cse_result_counters", "cse_result_timing",
-           "cse_result_launches", "cse_result_free", "cse_scheme_free", "cse_last_error",
+           "cse_result_iterations", "cse_result_launches", "cse_result_free", "cse_scheme_free", "cse_last_error",
            "cse_server_create", "cse_server_submit", "cse_server_wait", "cse_server_stats", "cse_server_free",
            "cse_search_static"]
 
@@ -85,6 +85,7 @@ def lib() -> ctypes.CDLL:
     L.cse_search_batch.argtypes = [i32, ctypes.POINTER(vp), ctypes.POINTER(Mix), pi32, ctypes.POINTER(u64), pi64,
                                    ctypes.POINTER(Opts), vp, ctypes.POINTER(vp)]
     L.cse_result_launches.argtypes = [vp, pi32, pi32]
+    L.cse_result_iterations.argtypes = [vp, pi32, pi32, pi64]
     batch_args = [i32, ctypes.POINTER(vp), ctypes.POINTER(Mix), pi32, ctypes.POINTER(u64), pi64, ctypes.POINTER(Opts)]
     L.cse_autotune.argtypes = batch_args + [i32, vp, ctypes.POINTER(TuneEntry), i32, pi32]
     L.cse_tune_interval.argtypes = batch_args + [ctypes.POINTER(ctypes.c_uint32), i32, i32, vp,
@@ -210,6 +211,12 @@ class Result:
         _check(lib().cse_result_timing(self.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(n)))
         return a.value, b.value, n.value
 
+    def iterations(self) -> Tuple[int, bool, int]:
+        """Iteration mode: (iterations run, stopped by the patience rule, final best total)."""
+        it, cv, tot = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+        _check(lib().cse_result_iterations(self.handle, ctypes.byref(it), ctypes.byref(cv), ctypes.byref(tot)))
+        return it.value, bool(cv.value), tot.value
+
     def launches(self) -> Tuple[int, int]:
         """(kernel launches of the launch sequence, searches that shared it)."""
         k, n = ctypes.c_int32(), ctypes.c_int32()
@@ -234,20 +241,23 @@ def make_mix(weights) -> Mix:
 
 
 def make_opts(interval: int = 32, permille: int = 400, cap: int = 128, procs_per_cta: int = 0,
-              graph: bool = False, trace: bool = False) -> Opts:
+              graph: bool = False, trace: bool = False, patience: int = 0) -> Opts:
+    """interval 0 selects iteration mode (budget = maximum iterations, stop
+    after `patience` iterations without improvement)."""
     o = Opts()
     lib().cse_opts_default(ctypes.byref(o))
     o.share_interval, o.share_permille, o.col_cap, o.procs_per_cta = interval, permille, cap, procs_per_cta
+    o.patience_rounds = patience
     o.flags = (FLAG_GRAPH if graph else 0) | (FLAG_TRACE if trace else 0)
     return o
 
 
 def search(scheme: Scheme, weights, n_proc: int, seed: int, budget: int, interval: int = 32,
            permille: int = 400, cap: int = 128, stream=None, procs_per_cta: int = 0, graph: bool = False,
-           trace: bool = False) -> Result:
+           trace: bool = False, patience: int = 0) -> Result:
     """cse_search: enqueue the search and return its Result handle."""
     mix = make_mix(weights)
-    opts = make_opts(interval, permille, cap, procs_per_cta, graph, trace)
+    opts = make_opts(interval, permille, cap, procs_per_cta, graph, trace, patience)
     h = ctypes.c_void_p()
     _check(lib().cse_search(scheme.handle, ctypes.byref(mix), n_proc, seed, budget, ctypes.byref(opts),
                             _stream_ptr(stream), ctypes.byref(h)))
@@ -264,7 +274,8 @@ def search_obj(s, scheme: Optional[Scheme] = None, **kw) -> Result:
 
 def search_batch(schemes: Sequence[Scheme], weights: Sequence, n_procs: Sequence[int], seeds: Sequence[int],
                  budgets: Sequence[int], interval: int = 32, permille: int = 400, cap: int = 128, stream=None,
-                 procs_per_cta: int = 0, graph: bool = True, trace: bool = False) -> List[Result]:
+                 procs_per_cta: int = 0, graph: bool = True, trace: bool = False,
+                 patience: int = 0) -> List[Result]:
     """cse_search_batch: independent searches in one launch sequence."""
     n = len(schemes)
     hs = (ctypes.c_void_p * n)(*[s.handle for s in schemes])
@@ -272,7 +283,7 @@ def search_batch(schemes: Sequence[Scheme], weights: Sequence, n_procs: Sequence
     np_ = (ctypes.c_int32 * n)(*n_procs)
     sd = (ctypes.c_uint64 * n)(*seeds)
     bd = (ctypes.c_int64 * n)(*budgets)
-    opts = make_opts(interval, permille, cap, procs_per_cta, graph, trace)
+    opts = make_opts(interval, permille, cap, procs_per_cta, graph, trace, patience)
     outs = (ctypes.c_void_p * n)()
     _check(lib().cse_search_batch(n, hs, mixes, np_, sd, bd, ctypes.byref(opts), _stream_ptr(stream), outs))
     res = []

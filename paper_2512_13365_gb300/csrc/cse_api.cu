@@ -49,6 +49,9 @@ struct Carve {
 
 uint64_t fnv(uint64_t h, uint32_t w) { return (h ^ w) * 0x100000001B3ull; }
 
+// Iteration mode: rounds enqueued between two reads of the convergence state.
+constexpr int kIterationChunk = 4;
+
 void set_pool_threshold_once() {
     static bool done = false;
     if (done) return;
@@ -187,10 +190,14 @@ static int check_opts(const cse_opts* opts_in, cse_opts* opts) {
         *opts = *opts_in;
     else
         cse_opts_default(opts);
-    if (opts->share_interval < 1) return fail(CSE_EINVAL, "share_interval must be >= 1");
     if (opts->share_permille > 1000) return fail(CSE_EINVAL, "share_permille must be <= 1000");
-    if (opts->patience_rounds != 0 || (opts->flags & ~(uint32_t)(CSE_FLAG_GRAPH | CSE_FLAG_TRACE)) != 0)
+    if ((opts->flags & ~(uint32_t)(CSE_FLAG_GRAPH | CSE_FLAG_TRACE)) != 0)
         return fail(CSE_EINVAL, "reserved option fields must be 0");
+    if (opts->share_interval != 0 && opts->patience_rounds != 0)
+        return fail(CSE_EINVAL, "patience_rounds applies to iteration mode (share_interval = 0) only");
+    if (opts->share_interval == 0 && (opts->flags & CSE_FLAG_GRAPH))
+        return fail(CSE_EINVAL, "iteration mode (share_interval = 0) cannot be captured in a graph: "
+                                "its length depends on convergence");
     if (opts->col_cap > CSE_MAX_COLS) return fail(CSE_EINVAL, "col_cap must be <= 512");
     if (opts->procs_per_cta > 4) return fail(CSE_EINVAL, "procs_per_cta must be in [0, 4]");
     return CSE_OK;
@@ -205,13 +212,16 @@ static int search_plan(const cse_scheme* s, const cse_strategy_mix* mix, int n_p
     if (n_proc < 1 || n_proc > (1 << 20)) return fail(CSE_EINVAL, "n_processes must be in [1, 2^20]");
     if (budget < 0 || budget >= INT32_MAX) return fail(CSE_EINVAL, "step_budget must be in [0, 2^31)");
     const int cap = (int)opts.col_cap;
+    if (opts.share_interval == 0 && cap > 0 && budget > INT32_MAX / cap - 1)
+        return fail(CSE_EINVAL, "iteration mode: max iterations x col_cap must stay below 2^31");
     for (int k = 0; k < s->n_mats; k++)
         if (s->cols[k] >= cap) return fail(CSE_EINVAL, "col_cap must exceed every matrix's column count");
     sd->n_mats = s->n_mats;
     sd->n_proc = n_proc;
     sd->cap = cap;
     sd->budget = budget;
-    sd->rounds = (int)((budget + opts.share_interval - 1) / opts.share_interval);
+    sd->rounds = opts.share_interval ? (int)((budget + opts.share_interval - 1) / opts.share_interval)
+                                     : (int)budget;  // iteration mode: at most `budget` iterations
     sd->mats.assign(s->n_mats, DevMat{});
     sd->gm.assign(s->n_mats, 0);
     Carve cv;
@@ -232,10 +242,11 @@ static int search_plan(const cse_scheme* s, const cse_strategy_mix* mix, int n_p
         offs->push_back(cv.take(8));                                    // round minimum
         offs->push_back(cv.take((size_t)cap * 4));                      // result
         offs->push_back(cv.take(8));                                    // result meta
-        offs->push_back(cv.take(16));                                   // counters
+        offs->push_back(cv.take(32));                                   // counters
     }
-    offs->push_back(cv.take(4));  // clock
-    offs->push_back(cv.take(4));  // status
+    offs->push_back(cv.take(4));   // clock
+    offs->push_back(cv.take(4));   // status
+    offs->push_back(cv.take(16));  // convergence state (iteration mode)
     sd->bytes = cv.off;
     return CSE_OK;
 }
@@ -275,9 +286,11 @@ static int search_create(const cse_scheme* s, const cse_strategy_mix* mix, int n
     S.wsum = (uint32_t)wsum;
     S.budget = (int32_t)budget;
     S.interval = (int32_t)opts.share_interval;
+    S.patience = (int32_t)opts.patience_rounds;
     S.share_thr = ((uint64_t)opts.share_permille << 32) / 1000u;
     S.clock = (int32_t*)(b + of[8 * s->n_mats]);
     S.status = (int32_t*)(b + of[8 * s->n_mats + 1]);
+    S.conv = (int32_t*)(b + of[8 * s->n_mats + 2]);
     S.n_mats = s->n_mats;
     S.trace = (opts.flags & CSE_FLAG_TRACE) ? 1 : 0;
     static const int32_t snap_init[2] = {INT_MAX, 0};
@@ -307,8 +320,10 @@ static int search_create(const cse_scheme* s, const cse_strategy_mix* mix, int n
         if (e == cudaSuccess) e = cudaMemcpyAsync(M.snap_meta, snap_init, 8, cudaMemcpyHostToDevice, stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(M.result_meta, M.meta0, 4, cudaMemcpyDeviceToDevice, stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(M.result_meta + 1, 0, 4, stream);
-        if (e == cudaSuccess) e = cudaMemsetAsync(M.counters, 0, 16, stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(M.counters, 0, 32, stream);
     }
+    static const int32_t conv_init[4] = {0, 0, INT_MAX, 0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(S.conv, conv_init, 16, cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(S.clock, 0, 4, stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(S.status, 0, 4, stream);
     if (e != cudaSuccess) {
@@ -439,6 +454,8 @@ static int run_batch(int n, const cse_scheme* const* schemes, const cse_strategy
     cse_opts opts;
     int rc = check_opts(opts_in, &opts);
     if (rc) return rc;
+    const bool iter_mode = opts.share_interval == 0;
+    if (iter_mode && trial) return fail(CSE_EINVAL, "launch tuning runs in step-clock mode (share_interval >= 1)");
     for (int i = 0; i < n; i++) {  // validate everything before allocating
         SearchDev tmp;
         uint64_t w;
@@ -503,7 +520,7 @@ static int run_batch(int n, const cse_scheme* const* schemes, const cse_strategy
     const size_t ng = B->ls.groups.size();
     if ((e = cudaEventCreate(&B->ev_begin)) != cudaSuccess) return bail(e, "event");
     if ((e = cudaEventCreate(&B->ev_end)) != cudaSuccess) return bail(e, "event");
-    B->ev_round.resize(2 * (size_t)B->rounds);
+    B->ev_round.resize(iter_mode ? 0 : 2 * (size_t)B->rounds);  // iteration mode: created per round
     for (auto& ev : B->ev_round)
         if ((e = cudaEventCreate(&ev)) != cudaSuccess) return bail(e, "event");
     if (trial) {
@@ -536,12 +553,43 @@ static int run_batch(int n, const cse_scheme* const* schemes, const cse_strategy
         return use_graph ? cudaEventRecordWithFlags(ev, ls, cudaEventRecordExternal) : cudaEventRecord(ev, ls);
     };
     rec(B->ev_begin);
-    for (int rd = 0; rd < B->rounds; rd++) {
-        rec(B->ev_round[2 * rd]);
-        e = enqueue_round(B->ls, ls, concurrent ? &B->aux : nullptr, concurrent ? &B->ev_fork : nullptr,
-                          trial ? &B->ev_group[2 * ng * rd] : nullptr);
-        if (e != cudaSuccess) return bail(e, "round launch");
-        rec(B->ev_round[2 * rd + 1]);
+    if (iter_mode) {
+        // Iteration mode (Section 3.5.2, stopping rule of Section 4): rounds
+        // are enqueued in chunks; between chunks the host reads every
+        // search's convergence state and stops once all have finished.
+        // Rounds of a finished search return at once on the device.
+        std::vector<int32_t> conv(4 * (size_t)n, 0);
+        int rd = 0;
+        while (rd < B->rounds) {
+            const int end = std::min(B->rounds, rd + kIterationChunk);
+            for (; rd < end; rd++) {
+                cudaEvent_t a = nullptr, z = nullptr;
+                if ((e = cudaEventCreate(&a)) != cudaSuccess) return bail(e, "event");
+                B->ev_round.push_back(a);
+                if ((e = cudaEventCreate(&z)) != cudaSuccess) return bail(e, "event");
+                B->ev_round.push_back(z);
+                rec(a);
+                e = enqueue_round(B->ls, ls, nullptr, nullptr, nullptr);
+                if (e != cudaSuccess) return bail(e, "round launch");
+                rec(z);
+            }
+            for (int i = 0; i < n && e == cudaSuccess; i++)
+                e = cudaMemcpyAsync(&conv[4 * (size_t)i], sds[i]->search.conv, 16, cudaMemcpyDeviceToHost, ls);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(ls);
+            if (e != cudaSuccess) return bail(e, "convergence read");
+            bool all = true;
+            for (int i = 0; i < n; i++) all = all && (conv[4 * (size_t)i + 1] != 0 || conv[4 * (size_t)i + 3] >= sds[i]->budget);
+            if (all) break;
+        }
+        B->rounds = rd;
+    } else {
+        for (int rd = 0; rd < B->rounds; rd++) {
+            rec(B->ev_round[2 * rd]);
+            e = enqueue_round(B->ls, ls, concurrent ? &B->aux : nullptr, concurrent ? &B->ev_fork : nullptr,
+                              trial ? &B->ev_group[2 * ng * rd] : nullptr);
+            if (e != cudaSuccess) return bail(e, "round launch");
+            rec(B->ev_round[2 * rd + 1]);
+        }
     }
     if ((e = rec(B->ev_end)) != cudaSuccess) return bail(e, "event record");
     if (use_graph) {
@@ -799,6 +847,8 @@ int cse_tune_interval(int32_t n_searches, const cse_scheme* const* schemes, cons
                       int32_t trial_steps, void* cuda_stream, uint32_t* best_interval, int64_t* best_total) {
     if (!candidates || n_candidates < 1 || trial_steps < 1 || !step_budgets || n_searches < 1)
         return fail(CSE_EINVAL, "bad interval candidates or trial size");
+    for (int c = 0; c < n_candidates; c++)
+        if (candidates[c] < 1) return fail(CSE_EINVAL, "interval candidates must be >= 1");
     cse_opts opts;
     int rc = check_opts(opts_in, &opts);
     if (rc) return rc;
@@ -907,14 +957,16 @@ int cse_result_counters(const cse_result* r, int64_t* process_steps, int64_t* su
     int rc = wait_result(r);
     if (rc) return rc;
     const SearchDev* sd = r->sd;
-    uint64_t ops = 0, sub = 0;
+    uint64_t ops = 0, sub = 0, steps = 0;
     for (int k = 0; k < sd->n_mats; k++) {
-        unsigned long long c[2];
-        CUDA_TRY(cudaMemcpy(c, sd->mats[k].counters, 16, cudaMemcpyDeviceToHost));
+        unsigned long long c[3];
+        CUDA_TRY(cudaMemcpy(c, sd->mats[k].counters, 24, cudaMemcpyDeviceToHost));
         ops += c[0];
         sub += c[1];
+        steps += c[2];
     }
-    if (process_steps) *process_steps = (int64_t)sd->n_mats * sd->n_proc * sd->budget;
+    if (process_steps)  // iteration mode: counted on the device (runs differ in length)
+        *process_steps = sd->search.interval == 0 ? (int64_t)steps : (int64_t)sd->n_mats * sd->n_proc * sd->budget;
     if (substeps) *substeps = (int64_t)sub;
     if (alg_ops) *alg_ops = (int64_t)ops;
     return CSE_OK;
@@ -940,6 +992,19 @@ int cse_result_timing(const cse_result* r, float* round_ms, float* total_ms, int
     if (round_ms) *round_ms = sum;
     if (total_ms) *total_ms = tot;
     if (n_rounds) *n_rounds = B->rounds;
+    return CSE_OK;
+}
+
+int cse_result_iterations(const cse_result* r, int32_t* iterations, int32_t* converged, int64_t* best_total) {
+    int rc = wait_result(r);
+    if (rc) return rc;
+    const SearchDev* sd = r->sd;
+    if (sd->search.interval != 0) return fail(CSE_EINVAL, "not an iteration-mode search (share_interval = 0)");
+    int32_t conv[4];
+    CUDA_TRY(cudaMemcpy(conv, sd->search.conv, 16, cudaMemcpyDeviceToHost));
+    if (iterations) *iterations = conv[3];
+    if (converged) *converged = conv[1] != 0 && conv[3] < sd->budget ? 1 : 0;
+    if (best_total) *best_total = conv[2] == INT_MAX ? -1 : conv[2];
     return CSE_OK;
 }
 
@@ -1092,6 +1157,8 @@ int cse_server_create(const cse_opts* opts_in, uint64_t hbm_budget_bytes, int64_
     int rc = check_opts(opts_in, &opts);
     if (rc) return rc;
     opts.flags &= CSE_FLAG_TRACE;
+    if (opts.share_interval == 0)
+        return fail(CSE_EINVAL, "the server admits requests at round boundaries of the step clock: share_interval >= 1");
     if (max_smem_per_block() <= 0) return fail(CSE_ECUDA, "no CUDA device");
     cse_server* sv = new (std::nothrow) cse_server();
     if (!sv) return fail(CSE_ENOMEM, "host allocation");

@@ -67,7 +67,8 @@ struct DevMat {
     unsigned long long* round_min;  // (best cost << 32 | process), min over the round
     int32_t* result;         // [cap] best list of the search
     int32_t* result_meta;    // [0] cost, [1] length
-    unsigned long long* counters;   // [0] algorithmic ops, [1] substitution steps
+    unsigned long long* counters;   // [0] algorithmic ops, [1] substitution steps,
+                                    // [2] process-steps (iteration mode)
     WarpLayout gml;          // layout of the working arrays inside a state region
                              // (HBM path only; fixed for the life of the search)
 };
@@ -76,9 +77,15 @@ struct DevSearch {
     uint64_t seed;
     uint32_t w[ST_N];
     uint32_t wsum;
-    int32_t budget, interval;
+    int32_t budget, interval;  // interval 0: iteration mode, budget = max iterations
+    int32_t patience;        // iteration mode: stop after this many iterations
+                             // without improvement of the total (0: never)
     uint64_t share_thr;      // draw < share_thr => copy a prefix of the snapshot
-    int32_t* clock;          // first step of the next round
+    int32_t* clock;          // first step of the next round (iteration mode: the
+                             // next iteration)
+    int32_t* conv;           // iteration mode: [0] iterations without
+                             // improvement, [1] converged, [2] best total,
+                             // [3] iterations run
     const int32_t* mat_pos;  // positions of this search's matrices in the DevMat array
     int32_t n_mats;
     int32_t* status;         // nonzero: a device-side consistency check failed

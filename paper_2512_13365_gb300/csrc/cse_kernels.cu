@@ -776,9 +776,14 @@ __global__ void __launch_bounds__(128, CSE_MIN_BLOCKS) round_kernel(const DevMat
     while (mi + 1 < n_mats && mats[mi + 1].unit_base <= unit) mi++;
     const DevMat* M = &mats[mi];
     const DevSearch* S = &searches[M->search];
-    const int t0 = *S->clock;
-    if (t0 >= S->budget) return;
-    const int t1 = min(t0 + S->interval, S->budget);
+    // step clock: this round runs steps [t0, t1).  Iteration mode: one whole
+    // run per process, from step t0 = iteration * cap until the run ends.
+    const bool iter_mode = S->interval == 0;
+    const int clk = *S->clock;
+    if (clk >= S->budget || (iter_mode && S->conv[1])) return;
+    const int t0 = iter_mode ? clk * M->cap : clk;
+    const int t1 = iter_mode ? t0 : min(t0 + S->interval, S->budget);
+    const bool more = iter_mode ? clk + 1 < S->budget : t1 < S->budget;
 
     uint32_t* st = M->state + (size_t)(unit - M->unit_base) * M->state_words;
     Engine<W> E;
@@ -847,7 +852,19 @@ __global__ void __launch_bounds__(128, CSE_MIN_BLOCKS) round_kernel(const DevMat
     if (lane == 0) cd->sub_before = cd->substeps;
     __syncwarp();
 
-    for (int t = t0; t < t1; t++) E.step(t);
+    int steps_run = t1 - t0;
+    if (iter_mode) {
+        // a run makes at most cap - nx substitutions plus the step that ends
+        // it, so t stays below the next iteration's first step
+        int t = t0;
+        do {
+            E.step(t);
+            t++;
+        } while (!E.ended);
+        steps_run = t - t0;
+    } else {
+        for (int t = t0; t < t1; t++) E.step(t);
+    }
     E.fold();
 
     if (lane == 0) {
@@ -862,6 +879,7 @@ __global__ void __launch_bounds__(128, CSE_MIN_BLOCKS) round_kernel(const DevMat
         atomicMin(M->round_min, (unsigned long long)(uint32_t)cd->best_cost << 32 | (uint32_t)E.proc);
         atomicAdd(&M->counters[0], (unsigned long long)dops);
         atomicAdd(&M->counters[1], (unsigned long long)(cd->substeps - cd->sub_before));
+        if (iter_mode) atomicAdd(&M->counters[2], (unsigned long long)steps_run);
         if (cd->overflow) atomicExch(S->status, 1);
         st[H_NCOLS] = (uint32_t)E.ncols;
         st[H_NF] = (uint32_t)E.nf;
@@ -880,7 +898,7 @@ __global__ void __launch_bounds__(128, CSE_MIN_BLOCKS) round_kernel(const DevMat
         st[H_OPS_LO] = (uint32_t)ops;
         st[H_OPS_HI] = (uint32_t)(ops >> 32);
     }
-    if (!GM && t1 < S->budget) {  // the state is needed by the next round
+    if (!GM && more) {  // the state is needed by the next round
         uint2* spn = reinterpret_cast<uint2*>(st + H_WORDS);
         const uint2* P = E.pn();
         for (int x = lane; x < E.ncols * W; x += 32) spn[x] = P[x];
@@ -894,21 +912,28 @@ __global__ void __launch_bounds__(128, CSE_MIN_BLOCKS) round_kernel(const DevMat
 }
 
 // Sharing boundary (Section 3.5.2) and result publication.  One CTA per
-// search, one warp per matrix.
+// search, one warp per matrix.  In iteration mode every round is a boundary,
+// followed by the convergence test on the sum of the matrices' best costs
+// (Section 4: unchanged for `patience` iterations ends the search).
 __global__ void share_kernel(const DevMat* __restrict__ mats, const DevSearch* __restrict__ searches) {
     const DevSearch* S = &searches[blockIdx.x];
-    const int t0 = *S->clock;
-    if (t0 >= S->budget) return;
-    const int t1 = min(t0 + S->interval, S->budget);
+    const bool iter_mode = S->interval == 0;
+    const int c0 = *S->clock;
+    if (c0 >= S->budget || (iter_mode && S->conv[1])) return;
+    const int c1 = iter_mode ? c0 + 1 : min(c0 + S->interval, S->budget);
+    const bool boundary = iter_mode || c1 % S->interval == 0;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    __shared__ int s_total, s_final;
+    if (threadIdx.x == 0) s_total = 0;
+    __syncthreads();
     for (int k = warp; k < S->n_mats; k += nw) {
         const DevMat* M = &mats[S->mat_pos[k]];
         const unsigned long long key = *M->round_min;
-        if (key == ~0ull) continue;  // no process reported (cannot happen when t0 < budget)
+        if (key == ~0ull) continue;  // no process reported (cannot happen while the search runs)
         const int cost = (int)(key >> 32), win = (int)(key & 0xFFFFFFFFu);
-        const int len = (int)M->state[(size_t)win * M->state_words + H_BEST_LEN];
-        const int32_t* src = M->best_list + (size_t)win * M->cap;
-        if (t1 % S->interval == 0 && cost < M->snap_meta[0]) {
+        if (boundary && cost < M->snap_meta[0]) {
+            const int len = (int)M->state[(size_t)win * M->state_words + H_BEST_LEN];
+            const int32_t* src = M->best_list + (size_t)win * M->cap;
             for (int x = lane; x < len; x += 32) M->snap[x] = src[x];
             __syncwarp();
             if (lane == 0) {
@@ -916,7 +941,34 @@ __global__ void share_kernel(const DevMat* __restrict__ mats, const DevSearch* _
                 M->snap_meta[1] = len;
             }
         }
-        if (t1 == S->budget) {
+        if (lane == 0) atomicAdd(&s_total, cost);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        bool fin = c1 == S->budget;
+        if (iter_mode) {
+            int32_t* cv = S->conv;
+            if (s_total < cv[2]) {
+                cv[2] = s_total;
+                cv[0] = 0;
+            } else {
+                cv[0]++;
+            }
+            if (S->patience > 0 && cv[0] >= S->patience) fin = true;
+            cv[3] = c1;
+            if (fin) cv[1] = 1;
+        }
+        s_final = fin ? 1 : 0;
+    }
+    __syncthreads();
+    for (int k = warp; k < S->n_mats; k += nw) {
+        const DevMat* M = &mats[S->mat_pos[k]];
+        const unsigned long long key = *M->round_min;
+        if (key == ~0ull) continue;
+        if (s_final) {
+            const int cost = (int)(key >> 32), win = (int)(key & 0xFFFFFFFFu);
+            const int len = (int)M->state[(size_t)win * M->state_words + H_BEST_LEN];
+            const int32_t* src = M->best_list + (size_t)win * M->cap;
             for (int x = lane; x < len; x += 32) M->result[x] = src[x];
             if (lane == 0) {
                 M->result_meta[0] = cost;
@@ -927,7 +979,7 @@ __global__ void share_kernel(const DevMat* __restrict__ mats, const DevSearch* _
         if (lane == 0) *M->round_min = ~0ull;
     }
     __syncthreads();
-    if (threadIdx.x == 0) *S->clock = t1;
+    if (threadIdx.x == 0) *S->clock = c1;
 }
 
 // ---------------------------------------------------------------------------

@@ -74,7 +74,8 @@ extern "C" int cse_search_static(const cse_scheme* s, const cse_strategy_mix* mi
         cse_opts_default(&opts);
     if (opts.share_interval < 1 || opts.share_permille > 1000 || opts.patience_rounds != 0 ||
         (opts.flags & ~(uint32_t)(CSE_FLAG_GRAPH | CSE_FLAG_TRACE)) != 0 || opts.col_cap > CSE_MAX_COLS || opts.procs_per_cta > 4)
-        return set_error(CSE_EINVAL, "invalid options");
+        return set_error(CSE_EINVAL, "invalid options (this entry point runs the step clock only: share_interval >= 1, "
+                                     "patience_rounds 0)");
     const uint64_t wsum = (uint64_t)mix->w_gi + mix->w_ga + mix->w_gr + mix->w_wr + mix->w_mix + mix->w_g + mix->w_gp;
     if (wsum == 0 || wsum > 0xFFFFFFFFull) return set_error(CSE_EINVAL, "strategy weights: sum must be in [1, 2^32)");
     if (n_proc < 1 || n_proc > (1 << 20)) return set_error(CSE_EINVAL, "n_processes must be in [1, 2^20]");
@@ -100,7 +101,7 @@ extern "C" int cse_search_static(const cse_scheme* s, const cse_strategy_mix* mi
         o_snap[k] = take(off, (size_t)cap * 4);
         o_snapm[k] = take(off, 8);
         o_rmin[k] = take(off, 8);
-        o_cnt[k] = take(off, 16);
+        o_cnt[k] = take(off, 32);
     }
     const size_t o_clock = take(off, 4), o_status = take(off, 4);
     const size_t o_mats = take(off, sizeof(DevMat) * nm), o_search = take(off, sizeof(DevSearch));
@@ -196,7 +197,7 @@ extern "C" int cse_search_static(const cse_scheme* s, const cse_strategy_mix* mi
         if (e == cudaSuccess) e = cudaMemcpyAsync(b + o_snapm[k], snap_init, 8, cudaMemcpyHostToDevice, stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(d_meta + 2 * k, s->d_meta0[k], 4, cudaMemcpyDeviceToDevice, stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(d_meta + 2 * k + 1, 0, 4, stream);
-        if (e == cudaSuccess) e = cudaMemsetAsync(b + o_cnt[k], 0, 16, stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(b + o_cnt[k], 0, 32, stream);
     }
     if (e == cudaSuccess) e = cudaMemsetAsync(b + o_clock, 0, 4, stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(b + o_status, 0, 4, stream);

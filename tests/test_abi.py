@@ -75,3 +75,27 @@ def test_opts_default(L):
     o = cse.Opts()
     L.cse_opts_default(ctypes.byref(o))
     assert (o.share_interval, o.share_permille, o.col_cap, o.flags) == (32, 400, 128, 0)
+
+
+@pytest.mark.parametrize("interval,patience,graph,msg", [
+    (32, 3, False, b"patience_rounds applies to iteration mode"),
+    (0, 10, True, b"cannot be captured in a graph"),
+])
+def test_iteration_mode_option_checks_without_device(L, interval, patience, graph, msg):
+    dummy = ctypes.c_void_p(1)   # never dereferenced: the options are checked first
+    schemes = (ctypes.c_void_p * 1)(dummy)
+    mixes = (cse.Mix * 1)(cse.make_mix((1, 0, 0, 0, 0, 0)))
+    n_proc = (ctypes.c_int32 * 1)(4)
+    seeds = (ctypes.c_uint64 * 1)(0)
+    budgets = (ctypes.c_int64 * 1)(10)
+    opts = cse.make_opts(interval=interval, graph=graph, patience=patience)
+    outs = (ctypes.c_void_p * 1)()
+    rc = L.cse_search_batch(1, schemes, mixes, n_proc, seeds, budgets, ctypes.byref(opts), None, outs)
+    assert rc == cse.CSE_EINVAL and msg in L.cse_last_error()
+
+
+def test_server_rejects_iteration_mode_without_device(L):
+    opts = cse.make_opts(interval=0, patience=10)
+    h = ctypes.c_void_p()
+    assert L.cse_server_create(ctypes.byref(opts), 0, 0, ctypes.byref(h)) == cse.CSE_EINVAL
+    assert b"share_interval >= 1" in L.cse_last_error()

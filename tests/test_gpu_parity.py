@@ -133,7 +133,9 @@ def test_invalid_search_arguments(cse):
     with pytest.raises(cse.CseError):
         cse.search(sc, synth.GI_ONLY, 0, 0, 10)                # no processes
     with pytest.raises(cse.CseError):
-        cse.search(sc, synth.GI_ONLY, 4, 0, 10, interval=0)
+        cse.search(sc, synth.GI_ONLY, 4, 0, 10, interval=32, patience=3)   # patience needs iteration mode
+    with pytest.raises(cse.CseError):
+        cse.search(sc, synth.GI_ONLY, 4, 0, 10, interval=0, graph=True)    # iteration mode has no graph
 
 
 def test_config2_full_size(cse):
@@ -290,3 +292,71 @@ def test_trace_flag_only_changes_the_trajectory_record(cse):
         assert (a["traj_hash"] == 0xCBF29CE484222325).all()
         for f in ("best_cost", "best_len", "runs", "best_hash", "ops", "substeps"):
             assert np.array_equal(a[f], b[f])
+
+
+# ---------------------------------------------------------------- iteration mode
+def assert_parity_iterations(cse, s, patience, ref=None, r=None):
+    """Iteration mode (share_interval = 0): s.budget is the maximum number of
+    iterations."""
+    if r is None:
+        r = cse.search_obj(s, patience=patience, trace=True)
+    if ref is None:
+        ref = O.search_iterations(s.mats, s.weights, s.n_proc, s.seed, s.budget, patience, s.permille, s.cap,
+                                  n_threads=8)
+    assert r.costs == ref.cost
+    assert r.lists == ref.lists
+    for k in range(len(s.mats)):
+        got, exp = r.procs(k), ref.digests[k]
+        for f in FIELDS:
+            bad = np.nonzero(got[f] != exp[f])[0]
+            assert bad.size == 0, f"matrix {k} field {f}: {bad.size} processes differ, first {bad[:5]}"
+    steps, sub, ops = r.counters()
+    assert steps == ref.process_steps
+    assert sub == int(sum(ref.digests[k]["substeps"].sum() for k in range(len(s.mats))))
+    assert ops == int(sum(ref.digests[k]["ops"].sum() for k in range(len(s.mats))))
+    it, conv, total = r.iterations()
+    assert it == ref.iterations and total == sum(ref.cost)
+    assert conv == (ref.iterations < s.budget)
+    r.free()
+    return ref
+
+
+def test_iteration_mode_paper_example(cse):
+    mat = np.array([[1, 1, -1, 1], [1, -1, 0, -1], [1, -1, -1, 1]], np.int8)
+    for permille in (0, 1000):
+        s = synth.Search("example", [mat], (0, 0, 0, 0, 0, 1), 5, 0, 100, 0, permille, 16)
+        ref = assert_parity_iterations(cse, s, 4)
+        assert ref.iterations == 5 and ref.cost == [6]
+
+
+@pytest.mark.parametrize("patience,max_it", [(4, 60), (0, 9), (10, 200)])
+def test_iteration_mode_config2_reduced(cse, patience, max_it):
+    s = synth.config2(n_proc=128, budget=max_it)
+    s.interval = 0
+    assert_parity_iterations(cse, s, patience)
+
+
+@pytest.mark.parametrize("rows", [20, 100, 256])
+def test_iteration_mode_word_widths(cse, rows):
+    mats = [synth.random_matrix(rows + 11, rows, 10, 2, 5, n_planted=6),
+            synth.random_matrix(rows + 12, 12, min(rows, 40), 2, 5, n_planted=3)]
+    s = synth.Search(f"it{rows}", mats, synth.PAPER_WEIGHTS, 33, 8, 30, 0, 400, 96)
+    assert_parity_iterations(cse, s, 3)
+
+
+def test_iteration_mode_from_hbm(cse):
+    s = synth.config4(n_proc=4, budget=2)
+    s.interval = 0
+    assert_parity_iterations(cse, s, 0)
+
+
+def test_iteration_mode_batch_equals_alone(cse):
+    ss = [synth.config2(n_proc=64, budget=40), synth.config1(n_proc=40, budget=40)]
+    for k, s in enumerate(ss):
+        s.interval, s.seed, s.cap = 0, 3 + k, 128
+    scs = [cse.Scheme(s.mats) for s in ss]
+    rs = cse.search_batch(scs, [s.weights for s in ss], [s.n_proc for s in ss], [s.seed for s in ss],
+                          [s.budget for s in ss], interval=0, permille=400, cap=128, graph=False, trace=True,
+                          patience=5)
+    for s, r in zip(ss, rs):
+        assert_parity_iterations(cse, s, 5, r=r)
