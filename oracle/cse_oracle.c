@@ -452,6 +452,30 @@ int32_t oracle_gp_potentials(const int8_t* mat, int32_t rows, int32_t cols, int3
     return m;
 }
 
+/* Brent equations (Section 3.1): for every entry a_ij of A, b_jk of B and
+ * c_ik of C, sum over the r products of u_ij v_j'k w_i'k' must be 1 exactly
+ * when j = j', i = i' and k = k', and 0 otherwise.  U, V, W are r x (m n),
+ * r x (n p), r x (m p), entries in row-major order.  Returns the number of
+ * (a, b, c) index triples whose sum is wrong. */
+int64_t oracle_brent_violations(int32_t m, int32_t n, int32_t p, int32_t r, const int8_t* U, const int8_t* V,
+                                const int8_t* W) {
+    int64_t bad = 0;
+    for (int32_t i = 0; i < m; i++)
+        for (int32_t j = 0; j < n; j++)
+            for (int32_t j2 = 0; j2 < n; j2++)
+                for (int32_t k = 0; k < p; k++)
+                    for (int32_t i2 = 0; i2 < m; i2++)
+                        for (int32_t k2 = 0; k2 < p; k2++) {
+                            int64_t sum = 0;
+                            for (int32_t l = 0; l < r; l++)
+                                sum += (int64_t)U[(int64_t)l * m * n + i * n + j] *
+                                       V[(int64_t)l * n * p + j2 * p + k] * W[(int64_t)l * m * p + i2 * p + k2];
+                            int64_t want = (j == j2 && i == i2 && k == k2) ? 1 : 0;
+                            bad += sum != want;
+                        }
+    return bad;
+}
+
 /* ------------------------------------------------------------------ */
 /* Brute force over Algorithm 1 sequences (tiny matrices, test pin)     */
 /* ------------------------------------------------------------------ */

@@ -72,6 +72,13 @@ int32_t oracle_gi_scores_coins(const uint32_t* keys, const int32_t* counts, int3
  * up to max_out values; returns the number of candidates. */
 int32_t oracle_gp_potentials(const int8_t* mat, int32_t rows, int32_t cols, int32_t* pot, int32_t max_out);
 
+/* Brent equations of a scheme (m,n,p:r) (Section 3.1): U is r x (m n), V is
+ * r x (n p), W is r x (m p), row-major, matrix entries in row-major order.
+ * Returns the number of index triples (a_ij, b_j'k, c_i'k') whose sum over the
+ * products differs from [j = j'][i = i'][k = k']; 0 for a valid scheme. */
+int64_t oracle_brent_violations(int32_t m, int32_t n, int32_t p, int32_t r, const int8_t* U, const int8_t* V,
+                                const int8_t* W);
+
 /* Exhaustive minimum of Cost over all sequences of Algorithm 1 on a tiny
  * matrix (rows * cols small).  Returns the optimum, or -1 on overflow. */
 int64_t oracle_bruteforce(const int8_t* mat, int32_t rows, int32_t cols, int32_t cap);

@@ -71,6 +71,8 @@ def lib():
         L.oracle_gi_scores_coins.restype = ctypes.c_int32
         L.oracle_gp_potentials.argtypes = [i8p, ctypes.c_int32, ctypes.c_int32, i32p, ctypes.c_int32]
         L.oracle_gp_potentials.restype = ctypes.c_int32
+        L.oracle_brent_violations.argtypes = [ctypes.c_int32] * 4 + [i8p, i8p, i8p]
+        L.oracle_brent_violations.restype = ctypes.c_int64
         L.oracle_bruteforce.argtypes = [i8p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]
         L.oracle_bruteforce.restype = ctypes.c_int64
         L.oracle_search.argtypes = [ctypes.c_int32, ctypes.POINTER(i8p), i32p, i32p, u32p, ctypes.c_int32,
@@ -167,6 +169,15 @@ def gp_potentials(mat: np.ndarray) -> List[int]:
     pot = np.zeros(cap, dtype=np.int32)
     n = lib().oracle_gp_potentials(_p(m, ctypes.c_int8), m.shape[0], m.shape[1], _p(pot, ctypes.c_int32), cap)
     return [int(x) for x in pot[:n]]
+
+
+def brent_violations(m: int, n: int, p: int, U: np.ndarray, V: np.ndarray, W: np.ndarray) -> int:
+    """Number of violated Brent equations of the scheme (m,n,p:r)."""
+    U, V, W = (np.ascontiguousarray(x, dtype=np.int8) for x in (U, V, W))
+    r = U.shape[0]
+    assert U.shape == (r, m * n) and V.shape == (r, n * p) and W.shape == (r, m * p)
+    return int(lib().oracle_brent_violations(m, n, p, r, _p(U, ctypes.c_int8), _p(V, ctypes.c_int8),
+                                             _p(W, ctypes.c_int8)))
 
 
 def bruteforce(mat: np.ndarray, cap: Optional[int] = None) -> int:

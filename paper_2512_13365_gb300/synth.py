@@ -274,6 +274,20 @@ def strassen_uvw() -> Tuple[np.ndarray, np.ndarray, np.ndarray]:
     return U, V, W
 
 
+def standard_uvw(m: int, n: int, p: int) -> Tuple[np.ndarray, np.ndarray, np.ndarray]:
+    """The schoolbook scheme (m,n,p:mnp): one product a_ij b_jk per (i, j, k),
+    added into c_ik.  Rows of U, V, W in the layout of strassen_uvw."""
+    r = m * n * p
+    U = np.zeros((r, m * n), np.int8)
+    V = np.zeros((r, n * p), np.int8)
+    W = np.zeros((r, m * p), np.int8)
+    for l, (i, j, k) in enumerate((i, j, k) for i in range(m) for j in range(n) for k in range(p)):
+        U[l, i * n + j] = 1
+        V[l, j * p + k] = 1
+        W[l, i * p + k] = 1
+    return U, V, W
+
+
 def scheme_sides(U: np.ndarray, V: np.ndarray, W: np.ndarray) -> List[np.ndarray]:
     """E_U = U (r x mn), E_V = V (r x np), E_W = W^T (mp x r) (Section 3.2)."""
     return [np.ascontiguousarray(U, dtype=np.int8), np.ascontiguousarray(V, dtype=np.int8),

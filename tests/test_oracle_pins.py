@@ -543,3 +543,38 @@ def test_iteration_mode_stopping_rule(seed):
     for k, m in enumerate(mats):
         cur, back = expand(m, a.lists[k])
         assert np.array_equal(back, m.astype(np.int64)) and cost_of(cur, len(a.lists[k])) == a.cost[k]
+
+
+# ---------------------------------------------------------------- Brent equations
+@pytest.mark.parametrize("shape", [(2, 2, 2), (2, 3, 4), (3, 3, 3), (1, 5, 2)])
+def test_brent_standard_algorithm_is_valid(shape):
+    U, V, W = synth.standard_uvw(*shape)
+    assert O.brent_violations(*shape, U, V, W) == 0
+
+
+def test_brent_strassen_and_single_flips():
+    """Strassen satisfies the Brent equations (Section 3.1).  Flipping one
+    nonzero u_a of product l changes every sum that product l enters with
+    that a, by 2 v_b w_c: exactly nnz(V[l]) * nnz(W[l]) equations break."""
+    U, V, W = synth.strassen_uvw()
+    assert O.brent_violations(2, 2, 2, U, V, W) == 0
+    for l in range(7):
+        for a in np.nonzero(U[l])[0]:
+            U2 = U.copy()
+            U2[l, a] = -U2[l, a]
+            assert O.brent_violations(2, 2, 2, U2, V, W) == np.count_nonzero(V[l]) * np.count_nonzero(W[l])
+    # a dropped product breaks the equations of its own (a, b, c) support
+    assert O.brent_violations(2, 2, 2, U[1:], V[1:], W[1:]) == \
+        np.count_nonzero(U[0]) * np.count_nonzero(V[0]) * np.count_nonzero(W[0])
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_brent_counts_match_numpy_tensor(seed):
+    rng = np.random.default_rng(seed)
+    m, n, p, r = 2, 3, 2, 9
+    U, V, W = (rng.integers(-1, 2, (r, k)).astype(np.int8) for k in (m * n, n * p, m * p))
+    T = np.einsum("la,lb,lc->abc", U.astype(int), V.astype(int), W.astype(int))
+    ref = np.zeros_like(T)
+    for i, j, k in itertools.product(range(m), range(n), range(p)):
+        ref[i * n + j, j * p + k, i * p + k] = 1
+    assert O.brent_violations(m, n, p, U, V, W) == int(np.count_nonzero(T != ref))
