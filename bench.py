@@ -436,6 +436,100 @@ def run_serving(args):
     print(json.dumps(line))
 
 
+def run_iterations(args):
+    """The paper's own schedule (iteration mode, share_interval = 0) on the
+    (3,3,3:23)-shaped workload: 4096 processes per matrix, one whole run per
+    process per iteration, sharing between iterations, stop when the best
+    total has not improved for 10 iterations (Section 4).  The search length
+    depends on convergence, so `value` counts the steps the runs made."""
+    import torch
+    from paper_2512_13365_gb300 import cse
+    from oracle import oracle as O
+    dev = torch.device("cuda", 0)
+    s = workload("cfg2", args.procs)
+    s.interval, s.budget = 0, args.budget or 1000
+    patience = 10
+    stream = torch.cuda.Stream(device=dev)
+    scheme = cse.Scheme(s.mats)
+    l2 = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+
+    def one():
+        return cse.search(scheme, s.weights, s.n_proc, s.seed, s.budget, 0, s.permille, s.cap, stream=stream,
+                          patience=patience)
+
+    for _ in range(args.warmup):
+        one().free()
+    torch.cuda.synchronize()
+    clocks = Clocks(os.path.join(args.out, "clocks_iter.csv"), 0)
+    ms, rec = [], None
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush_l2(l2)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        r = one()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+        steps, sub, ops = r.counters()
+        round_ms, _, n_rounds = r.timing()
+        it, conv, total = r.iterations()
+        rec = (steps, ops, round_ms, n_rounds, it, conv, total, r.costs, r.launches()[0])
+        r.free()
+    clk = clocks.stop()
+    steps, ops, round_ms, n_rounds, it, conv, total, costs, kernels = rec
+    t = statistics.mean(ms)
+    # end to end: load from host buffers, search to convergence, fetch every list
+    e2e_ms, d2h = [], 0
+    for _ in range(0 if args.no_e2e else 2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sc = cse.Scheme(s.mats)
+        r = cse.search(sc, s.weights, s.n_proc, s.seed, s.budget, 0, s.permille, s.cap, stream=stream,
+                       patience=patience)
+        lists = [r.fetch(k) for k in range(len(s.mats))]
+        e2e_ms.append((time.perf_counter() - t0) * 1000.0)
+        d2h = sum(4 * len(l) + 16 for l, _, _ in lists)
+        r.free()
+        sc.free()
+    pk = peaks()
+    props = torch.cuda.get_device_properties(dev)
+    sm_mhz = float(pk.get("sm_max_mhz", 2070.0))
+    peak_ops = props.multi_processor_count * LANES_PER_SM * sm_mhz * 1e6 / 1e12
+    achieved = ops / (round_ms / 1000.0) / 1e12
+    line = {
+        "metric": METRIC, "value": steps / (t / 1000.0), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": f"{s.name}, iteration mode (patience {patience})",
+                   "matrices": [list(m.shape) for m in s.mats], "n_processes": s.n_proc,
+                   "max_iterations": s.budget, "share_permille": s.permille, "col_cap": s.cap,
+                   "strategy_weights_gi_ga_gr_wr_mix_g_gp": list(s.weights),
+                   "l2": "flushed (256 MB write) between timed steps"},
+        "iterations": it, "converged": conv, "process_steps_per_search": steps,
+        "best_additions": total, "best_additions_per_matrix": costs,
+        "e2e": {"value": steps / (statistics.mean(e2e_ms) / 1000.0) if e2e_ms else None, "unit": UNIT,
+                "h2d_bytes_per_step": sum(m.nbytes for m in s.mats), "d2h_bytes_per_step": d2h,
+                "ms_per_step": statistics.mean(e2e_ms) if e2e_ms else None},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "Tops/s",
+                     "frac": achieved / peak_ops, "traffic": None, "kernel": "round_kernel (whole runs)",
+                     "alg_ops_per_launch": ops / n_rounds, "avg_launch_ms": round_ms / n_rounds},
+        "clocks": clk, "gpu_launches": kernels * args.steps,
+    }
+    if not args.no_cpu_baseline:
+        cores = len(os.sched_getaffinity(0))
+        t0 = time.perf_counter()
+        ref = O.search_iterations(s.mats, s.weights, s.n_proc, s.seed, s.budget, patience, s.permille, s.cap,
+                                  n_threads=cores, digests=False)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": ref.process_steps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": f"the whole search ({ref.iterations} iterations, "
+                                          f"{ref.process_steps} process-steps, {dt:.1f} s)",
+                                "best_additions": sum(ref.cost)}
+    print(json.dumps(line))
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -476,7 +570,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="cfg2",
-                    help="cfg2 (default, the benchmark line), cfg1, cfg3 (batched), cfg5 (serving)")
+                    help="cfg2 (default, the benchmark line), cfg1, cfg4, cfg3 (batched), cfg5 (serving), "
+                         "cfg2-iter (iteration mode)")
     ap.add_argument("--requests", type=int, default=200, help="cfg5: number of requests")
     ap.add_argument("--procs", type=int, default=0, help="override the process count (reduced-scale runs)")
     ap.add_argument("--ppc", type=int, default=0, help="processes per CTA (0 = library default)")
@@ -494,6 +589,8 @@ def main():
         run_batched(args)
     elif args.workload == "cfg5":
         run_serving(args)
+    elif args.workload == "cfg2-iter":
+        run_iterations(args)
     else:
         run_ours(args)
 

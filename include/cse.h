@@ -130,6 +130,16 @@ int cse_scheme_load(const int8_t* const* mats, const int32_t* rows, const int32_
 int cse_scheme_load_uvw(int32_t m, int32_t n, int32_t p, int32_t r, const int8_t* U,
                         const int8_t* V, const int8_t* W, cse_scheme** out);
 
+/* Checks the Brent equations of a scheme (m,n,p:r) (Section 3.1) on the
+ * device: for every entry a_ij, b_j'k, c_i'k' the sum over the r products of
+ * u_ij v_j'k w_i'k' must be 1 when j = j', i = i', k = k' and 0 otherwise.
+ * U, V, W are host arrays in the layout of cse_scheme_load_uvw (any int8
+ * values).  *violations = the number of index triples whose sum is wrong (0
+ * for a valid scheme).  m n, n p, m p <= 4096, r <= 65536.  Synchronous; it
+ * allocates and frees its own device buffers. */
+int cse_brent_check(int32_t m, int32_t n, int32_t p, int32_t r, const int8_t* U, const int8_t* V,
+                    const int8_t* W, int64_t* violations);
+
 /* Shape of a loaded matrix. */
 int cse_scheme_shape(const cse_scheme* s, int32_t mat, int32_t* rows, int32_t* cols);
 
@@ -242,6 +252,15 @@ int cse_result_timing(const cse_result* r, float* round_ms, float* total_ms, int
  * the iterations it ran, whether it stopped by the patience rule before its
  * maximum, and the final sum over the matrices of the best Cost. */
 int cse_result_iterations(const cse_result* r, int32_t* iterations, int32_t* converged, int64_t* best_total);
+
+/* Component-wise (hybrid) minimum over several results of the same scheme
+ * (Section 5, component-wise analysis: the best U, V and W parts may come
+ * from different runs).  Waits for every result; best_result[k] (n_mats
+ * entries) = the index of the result with the lowest Cost for matrix k, the
+ * first one on ties; *total_additions = the sum of those Costs.  The results
+ * must have the same number and shapes of matrices. */
+int cse_result_hybrid(const cse_result* const* results, int32_t n_results, int32_t* best_result,
+                      int64_t* total_additions);
 
 /* Kernel launches of the search's launch sequence (shared by all searches of
  * a batch) and the number of searches that shared it. */

@@ -55,7 +55,8 @@ _lib = None
 # every symbol include/cse.h declares
 EXPORTS = ["cse_opts_default", "cse_scheme_load", "cse_scheme_load_uvw", "cse_scheme_shape", "cse_search",
            "cse_search_batch", "cse_autotune", "cse_tune_interval", "cse_result_fetch", "cse_result_procs", "cse_result_counters", "cse_result_timing",
-           "cse_result_iterations", "cse_result_launches", "cse_result_free", "cse_scheme_free", "cse_last_error",
+           "cse_result_iterations", "cse_result_hybrid", "cse_brent_check", "cse_result_launches",
+           "cse_result_free", "cse_scheme_free", "cse_last_error",
            "cse_server_create", "cse_server_submit", "cse_server_wait", "cse_server_stats", "cse_server_free",
            "cse_search_static"]
 
@@ -86,6 +87,8 @@ def lib() -> ctypes.CDLL:
                                    ctypes.POINTER(Opts), vp, ctypes.POINTER(vp)]
     L.cse_result_launches.argtypes = [vp, pi32, pi32]
     L.cse_result_iterations.argtypes = [vp, pi32, pi32, pi64]
+    L.cse_result_hybrid.argtypes = [ctypes.POINTER(vp), i32, pi32, pi64]
+    L.cse_brent_check.argtypes = [i32, i32, i32, i32, vp, vp, vp, pi64]
     batch_args = [i32, ctypes.POINTER(vp), ctypes.POINTER(Mix), pi32, ctypes.POINTER(u64), pi64, ctypes.POINTER(Opts)]
     L.cse_autotune.argtypes = batch_args + [i32, vp, ctypes.POINTER(TuneEntry), i32, pi32]
     L.cse_tune_interval.argtypes = batch_args + [ctypes.POINTER(ctypes.c_uint32), i32, i32, vp,
@@ -233,6 +236,29 @@ class Result:
             self.free()
         except Exception:
             pass
+
+
+def hybrid(results: Sequence["Result"]) -> Tuple[List[int], int]:
+    """cse_result_hybrid: per matrix, the index of the result with the lowest
+    Cost (first on ties), and the total of those Costs."""
+    n = len(results)
+    hs = (ctypes.c_void_p * n)(*[r.handle.value for r in results])
+    nm = results[0].n_mats
+    best = (ctypes.c_int32 * nm)()
+    tot = ctypes.c_int64()
+    _check(lib().cse_result_hybrid(hs, n, best, ctypes.byref(tot)))
+    return list(best), tot.value
+
+
+def brent_check(m: int, n: int, p: int, U: np.ndarray, V: np.ndarray, W: np.ndarray) -> int:
+    """cse_brent_check: the number of violated Brent equations (0 = valid scheme)."""
+    U, V, W = (np.ascontiguousarray(x, dtype=np.int8) for x in (U, V, W))
+    r = U.shape[0]
+    if U.shape != (r, m * n) or V.shape != (r, n * p) or W.shape != (r, m * p):
+        raise ValueError("U, V, W must be r x mn, r x np, r x mp")
+    out = ctypes.c_int64()
+    _check(lib().cse_brent_check(m, n, p, r, U.ctypes.data, V.ctypes.data, W.ctypes.data, ctypes.byref(out)))
+    return out.value
 
 
 def make_mix(weights) -> Mix:

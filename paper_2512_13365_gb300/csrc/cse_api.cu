@@ -765,6 +765,32 @@ int cse_scheme_load_uvw(int32_t m, int32_t n, int32_t p, int32_t r, const int8_t
     return cse_scheme_load(mats, rows, cols, 3, out);
 }
 
+int cse_brent_check(int32_t m, int32_t n, int32_t p, int32_t r, const int8_t* U, const int8_t* V, const int8_t* W,
+                    int64_t* violations) {
+    if (m < 1 || n < 1 || p < 1 || r < 1 || !U || !V || !W || !violations)
+        return fail(CSE_EINVAL, "bad scheme dimensions or NULL argument");
+    if ((int64_t)m * n > 4096 || (int64_t)n * p > 4096 || (int64_t)m * p > 4096 || r > 65536)
+        return fail(CSE_EINVAL, "scheme too large for the Brent check (m n, n p, m p <= 4096, r <= 65536)");
+    const size_t su = (size_t)r * m * n, sv = (size_t)r * n * p, sw = (size_t)r * m * p;
+    char* d = nullptr;
+    CUDA_TRY(cudaMalloc(&d, su + sv + sw + 16));
+    int8_t* dU = (int8_t*)d + 16;
+    int8_t* dV = dU + su;
+    int8_t* dW = dV + sv;
+    unsigned long long* dbad = (unsigned long long*)d;
+    unsigned long long bad = 0;
+    cudaError_t e = cudaMemset(dbad, 0, 8);
+    if (e == cudaSuccess) e = cudaMemcpy(dU, U, su, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dV, V, sv, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dW, W, sw, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = launch_brent(dU, dV, dW, m, n, p, r, dbad, nullptr);
+    if (e == cudaSuccess) e = cudaMemcpy(&bad, dbad, 8, cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return fail(CSE_ECUDA, std::string("Brent check: ") + cudaGetErrorString(e));
+    *violations = (int64_t)bad;
+    return CSE_OK;
+}
+
 int cse_scheme_shape(const cse_scheme* s, int32_t mat, int32_t* rows, int32_t* cols) {
     if (!s || mat < 0 || mat >= s->n_mats) return fail(CSE_EINVAL, "bad scheme or matrix index");
     if (rows) *rows = s->rows[mat];
@@ -1005,6 +1031,37 @@ int cse_result_iterations(const cse_result* r, int32_t* iterations, int32_t* con
     if (iterations) *iterations = conv[3];
     if (converged) *converged = conv[1] != 0 && conv[3] < sd->budget ? 1 : 0;
     if (best_total) *best_total = conv[2] == INT_MAX ? -1 : conv[2];
+    return CSE_OK;
+}
+
+int cse_result_hybrid(const cse_result* const* results, int32_t n_results, int32_t* best_result,
+                      int64_t* total_additions) {
+    if (!results || n_results < 1 || !best_result) return fail(CSE_EINVAL, "no results or NULL output");
+    const SearchDev* s0 = results[0] ? results[0]->sd : nullptr;
+    if (!s0) return fail(CSE_EINVAL, "NULL result");
+    for (int i = 1; i < n_results; i++) {
+        const SearchDev* si = results[i] ? results[i]->sd : nullptr;
+        if (!si || si->n_mats != s0->n_mats) return fail(CSE_EINVAL, "results of different schemes");
+        for (int k = 0; k < s0->n_mats; k++)
+            if (si->rows[k] != s0->rows[k] || si->cols[k] != s0->cols[k])
+                return fail(CSE_EINVAL, "results of different schemes");
+    }
+    std::vector<int64_t> best(s0->n_mats, INT64_MAX);
+    for (int i = 0; i < n_results; i++) {
+        int rc = wait_result(results[i]);
+        if (rc) return rc;
+        for (int k = 0; k < s0->n_mats; k++) {
+            int32_t meta[2];
+            CUDA_TRY(cudaMemcpy(meta, results[i]->sd->mats[k].result_meta, 8, cudaMemcpyDeviceToHost));
+            if (meta[0] < best[k]) {  // strictly lower: the first result wins ties
+                best[k] = meta[0];
+                best_result[k] = i;
+            }
+        }
+    }
+    int64_t t = 0;
+    for (int64_t b : best) t += b;
+    if (total_additions) *total_additions = t;
     return CSE_OK;
 }
 

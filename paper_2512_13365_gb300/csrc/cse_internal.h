@@ -109,6 +109,8 @@ cudaError_t launch_round(int W, bool gm, const DevMat* mats, int n_mats, const D
                          cudaStream_t stream);
 cudaError_t launch_share(const DevMat* mats, const DevSearch* searches, int n_searches,
                          cudaStream_t stream);
+cudaError_t launch_brent(const int8_t* U, const int8_t* V, const int8_t* W, int m, int n, int p, int r,
+                         unsigned long long* bad, cudaStream_t stream);
 // Sets the launch attributes of a round kernel (call outside stream capture).
 cudaError_t prepare_round(int W, bool gm, const WarpLayout& L, int procs_per_cta);
 int max_smem_per_block();

@@ -19,6 +19,7 @@
 // extra_lo); all lanes of a warp evaluate the same draw, so no shuffles are
 // needed to share it.
 
+#include <algorithm>
 #include <climits>
 #include <cstdint>
 
@@ -982,6 +983,32 @@ __global__ void share_kernel(const DevMat* __restrict__ mats, const DevSearch* _
     if (threadIdx.x == 0) *S->clock = c1;
 }
 
+// Brent equations (Section 3.1) of a scheme (m,n,p:r): one thread per index
+// triple (a_ij, b_j'k, c_i'k'), grid-stride; counts the triples whose sum
+// over the r products differs from [j = j'][i = i'][k = k'].  Consecutive
+// threads take consecutive c, so the W reads coalesce and U, V broadcast.
+__global__ void brent_kernel(const int8_t* __restrict__ U, const int8_t* __restrict__ V,
+                             const int8_t* __restrict__ W, int m, int n, int p, int r, long long total,
+                             unsigned long long* __restrict__ bad) {
+    const int mn = m * n, np = n * p, mp = m * p;
+    unsigned long long cnt = 0;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(t % mp);
+        const long long ab = t / mp;
+        const int b = (int)(ab % np), a = (int)(ab / np);
+        int sum = 0;
+        for (int l = 0; l < r; l++)
+            sum += (int)U[(size_t)l * mn + a] * (int)V[(size_t)l * np + b] * (int)W[(size_t)l * mp + c];
+        const int i = a / n, j = a % n, j2 = b / p, k = b % p, i2 = c / p, k2 = c % p;
+        const int want = (j == j2 && i == i2 && k == k2) ? 1 : 0;
+        cnt += sum != want;
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) cnt += __shfl_xor_sync(FULL_MASK, cnt, o);
+    if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(bad, cnt);
+}
+
 // ---------------------------------------------------------------------------
 // host-side launchers
 // ---------------------------------------------------------------------------
@@ -1070,6 +1097,18 @@ cudaError_t prepare_round(int W, bool gm, const WarpLayout& L, int ppc) {
 cudaError_t launch_share(const DevMat* mats, const DevSearch* searches, int n_searches,
                          cudaStream_t stream) {
     share_kernel<<<n_searches, 128, 0, stream>>>(mats, searches);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_brent(const int8_t* U, const int8_t* V, const int8_t* W, int m, int n, int p, int r,
+                         unsigned long long* bad, cudaStream_t stream) {
+    const long long total = (long long)m * n * n * p * m * p;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long want = (total + 255) / 256;
+    const int grid = (int)std::max(1LL, std::min(want, (long long)std::max(sms, 1) * 8));
+    brent_kernel<<<grid, 256, 0, stream>>>(U, V, W, m, n, p, r, total, bad);
     return cudaGetLastError();
 }
 

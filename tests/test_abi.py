@@ -99,3 +99,15 @@ def test_server_rejects_iteration_mode_without_device(L):
     h = ctypes.c_void_p()
     assert L.cse_server_create(ctypes.byref(opts), 0, 0, ctypes.byref(h)) == cse.CSE_EINVAL
     assert b"share_interval >= 1" in L.cse_last_error()
+
+
+def test_brent_and_hybrid_argument_checks_without_device(L):
+    out = ctypes.c_int64()
+    a = np.ones(4, np.int8)
+    assert L.cse_brent_check(0, 2, 2, 1, a.ctypes.data, a.ctypes.data, a.ctypes.data, ctypes.byref(out)) == \
+        cse.CSE_EINVAL
+    assert L.cse_brent_check(2, 2, 2, 1, None, a.ctypes.data, a.ctypes.data, ctypes.byref(out)) == cse.CSE_EINVAL
+    assert L.cse_brent_check(100, 100, 2, 1, a.ctypes.data, a.ctypes.data, a.ctypes.data, ctypes.byref(out)) == \
+        cse.CSE_EINVAL
+    best = (ctypes.c_int32 * 3)()
+    assert L.cse_result_hybrid(None, 2, best, None) == cse.CSE_EINVAL
