@@ -331,6 +331,35 @@ def run_batched(args):
         out[name] = {"ms": statistics.mean(ms), "value": psteps / (statistics.mean(ms) / 1000.0),
                      "best_additions_total": sum(totals), "kernel_launches": kernels}
     assert out["batched"]["best_additions_total"] == out["per_scheme"]["best_additions_total"]
+
+    # best additions at a fixed wall-clock budget: the per-scheme launches get
+    # the step budget B; the batched graph gets as many steps (a multiple of
+    # the sharing interval) as fit in the same device time
+    B = searches[0].budget
+    wall = out["per_scheme"]["ms"]
+    B2 = max(B, int(B * wall / out["batched"]["ms"]) // interval * interval)
+    fixed = None
+    while B2 >= B:
+        ba2 = ba[:4] + ([B2] * len(searches),)
+        with torch.cuda.stream(stream):
+            flush_l2(l2)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        rs = cse.search_batch(*ba2, interval=interval, cap=cap, stream=stream, graph=True)
+        b.record(stream)
+        torch.cuda.synchronize()
+        t2 = a.elapsed_time(b)
+        tot2 = sum(r.total for r in rs)
+        for r in rs:
+            r.free()
+        if t2 <= wall or B2 == B:
+            fixed = {"device_ms_budget": wall,
+                     "one_launch_sequence_per_scheme": {"step_budget": B,
+                                                        "best_additions_total": out["per_scheme"]["best_additions_total"]},
+                     "batched_graph": {"step_budget": B2, "ms": t2, "best_additions_total": tot2}}
+            break
+        B2 -= interval
     pk = peaks()
     props = torch.cuda.get_device_properties(dev)
     sm_mhz = float(pk.get("sm_max_mhz", 2070.0))
@@ -358,6 +387,7 @@ def run_batched(args):
                    "l2": "flushed (256 MB write) between timed steps"},
         "batched_graph": out["batched"], "one_launch_sequence_per_scheme": out["per_scheme"],
         "speedup_batched_vs_per_scheme": out["per_scheme"]["ms"] / out["batched"]["ms"],
+        "fixed_wall_clock": fixed,
         "autotune": {"seconds": tune_s, "classes": tuned, "interval_candidates": [16, 32, 64],
                      "interval_chosen": interval},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "Tops/s",
