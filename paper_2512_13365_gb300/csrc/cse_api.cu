@@ -233,8 +233,8 @@ static int search_plan(const cse_scheme* s, const cse_strategy_mix* mix, int n_p
         const bool gm = own.per_warp > kSmemPerWarpLimit;
         sd->gm[k] = gm;
         DevMat& M = sd->mats[k];
-        M.gml = own;
-        M.state_words = gm ? state_words_gm(own) : state_words(s->W[k], cap, s->mmax[k]);
+        M.gml = gm ? make_layout(s->W[k], cap, s->mmax[k], true) : own;
+        M.state_words = gm ? state_words_gm(M.gml) : state_words(s->W[k], cap, s->mmax[k]);
         offs->push_back(cv.take((size_t)n_proc * M.state_words * 4));   // state
         offs->push_back(cv.take((size_t)n_proc * cap * 4));             // best lists
         offs->push_back(cv.take((size_t)cap * 4));                      // snapshot

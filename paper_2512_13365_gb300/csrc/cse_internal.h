@@ -46,6 +46,7 @@ constexpr uint64_t kFnv0 = 0xCBF29CE484222325ull;
 // Shared-memory carve-up of one process (one warp), in bytes.
 struct WarpLayout {
     int32_t off_cold, off_pn, off_cand, off_f, off_aw, off_poslo, off_hs, off_he, off_base, off_lc;
+    int32_t off_pb, off_g, off_pln;  // HBM path: Greedy-Intersections bit-planes
     int32_t per_warp;
 };
 
@@ -92,7 +93,8 @@ struct DevSearch {
     int32_t trace;           // record the trajectory hash (CSE_FLAG_TRACE)
 };
 
-WarpLayout make_layout(int W, int cap, int mmax);
+// planes: the HBM-path layout (weight bit-planes instead of weight bytes).
+WarpLayout make_layout(int W, int cap, int mmax, bool planes = false);
 int state_words(int W, int cap, int mmax);
 int state_words_gm(const WarpLayout& L);
 

@@ -244,7 +244,7 @@ struct Cold {
     unsigned t_sub, t_pairs, t_scan, t_gi_terms, t_gi_blocks, t_gi_cands;
 };
 
-template <int W>
+template <int W, bool GM>
 struct Engine {
     unsigned char* sm;   // this warp's shared memory
     const WarpLayout* L;
@@ -264,6 +264,12 @@ struct Engine {
     __device__ __forceinline__ uint16_t* he() const { return reinterpret_cast<uint16_t*>(sm + L->off_he); }
     __device__ __forceinline__ uint16_t* vbase() const { return reinterpret_cast<uint16_t*>(sm + L->off_base); }
     __device__ __forceinline__ uint16_t* lc() const { return reinterpret_cast<uint16_t*>(sm + L->off_lc); }
+    // HBM path only: per-variable plane base and weight sum, and the planes
+    __device__ __forceinline__ uint16_t* pbase() const { return reinterpret_cast<uint16_t*>(sm + L->off_pb); }
+    __device__ __forceinline__ uint32_t* gsum() const { return reinterpret_cast<uint32_t*>(sm + L->off_g); }
+    __device__ __forceinline__ unsigned long long* planes() const {
+        return reinterpret_cast<unsigned long long*>(sm + L->off_pln);
+    }
     __device__ __forceinline__ Cold* cold() const { return reinterpret_cast<Cold*>(sm + L->off_cold); }
 
     __device__ __forceinline__ uint32_t c2(uint32_t purpose, uint32_t extra_hi) const {
@@ -700,6 +706,181 @@ struct Engine {
         return best_q;
     }
 
+    // Greedy-Intersections for large matrices (HBM path): the same exact
+    // integer score as sel_gi, with the coin-weighted sums taken over
+    // bit-planes instead of byte loops.  For every variable v and every 64
+    // positions of A_v, plane k is the 64-bit mask of the positions whose
+    // weight has bit k set; then sum coin(x) w(x) over a block is
+    // sum_k 2^k popc(plane_k & coins), and the plain sums are G[v].  The lists
+    // of these matrices hold hundreds of candidates, so this replaces
+    // O(|A_i| + |A_j|) byte steps per candidate by O(B (|A_i| + |A_j|) / 64)
+    // popcounts, B = bits of the largest weight.
+    __device__ int sel_gi_planes(int t) {
+        const uint32_t lt = lanemask_lt();
+        const uint32_t* C = cand();
+        uint16_t* HS = hs();
+        uint16_t* HE = he();
+        uint16_t* VB = vbase();
+        uint16_t* LC = lc();
+        uint16_t* PB = pbase();
+        uint32_t* G = gsum();
+        uint16_t* PL = poslo();
+        unsigned long long* PLN = planes();
+        int part = 0, wmax = 1;
+        for (int v = lane; v < ncols; v += 32) {
+            HS[v] = 0;
+            HE[v] = 0;
+            LC[v] = 0;
+            G[v] = 0;
+        }
+        __syncwarp();
+        for (int base = 0; base < m; base += 32) {
+            const int q = base + lane;
+            const bool valid = q < m;
+            const uint32_t act = __ballot_sync(FULL_MASK, valid);
+            if (valid) {
+                const uint32_t e = C[q];
+                const int hi = key_hi(e), lo = key_lo(e);
+                part += cand_c(e) - 1;
+                wmax = max(wmax, cand_c(e) - 1);
+                if (q == 0 || key_hi(C[q - 1]) != hi) HS[hi] = (uint16_t)q;
+                if (q == m - 1 || key_hi(C[q + 1]) != hi) HE[hi] = (uint16_t)(q + 1);
+                const uint32_t peers = __match_any_sync(act, lo);
+                if ((peers & lt) == 0) LC[lo] = (uint16_t)(LC[lo] + __popc(peers));
+            }
+            __syncwarp();
+        }
+        const int T = __reduce_add_sync(FULL_MASK, part);
+        const int B = 32 - __clz((int)__reduce_max_sync(FULL_MASK, (uint32_t)wmax));
+        // positions (low 16 bits) and 64-position blocks (high 16 bits) of A_v
+        uint32_t run = 0;
+        for (int base = 0; base < ncols; base += 32) {
+            const int v = base + lane;
+            const int deg = v < ncols ? (HE[v] - HS[v]) + LC[v] : 0;
+            const uint32_t packed = (uint32_t)deg | (uint32_t)((deg + 63) >> 6) << 16;
+            const uint32_t incl = (uint32_t)warp_incl_scan((int)packed, lane);
+            if (v < ncols) {
+                const uint32_t ex = run + incl - packed;
+                VB[v] = (uint16_t)(ex & 0xFFFFu);
+                PB[v] = (uint16_t)(ex >> 16);
+                LC[v] = 0;
+            }
+            run += (uint32_t)__shfl_sync(FULL_MASK, (int)incl, 31);
+        }
+        const int nplanes = (int)(run >> 16) * B;
+        for (int x = lane; x < nplanes; x += 32) PLN[x] = 0ull;
+        __syncwarp();
+        for (int base = 0; base < m; base += 32) {
+            const int q = base + lane;
+            const bool valid = q < m;
+            const uint32_t act = __ballot_sync(FULL_MASK, valid);
+            uint32_t peers = 0;
+            int lo = 0;
+            if (valid) {
+                const uint32_t e = C[q];
+                const int hi = key_hi(e);
+                lo = key_lo(e);
+                const uint32_t w = (uint32_t)(cand_c(e) - 1);
+                peers = __match_any_sync(act, lo);
+                const int xh = q - HS[hi];
+                const int xl = (HE[lo] - HS[lo]) + LC[lo] + __popc(peers & lt);
+                PL[q] = (uint16_t)(VB[lo] + xl);
+                unsigned long long* ph = PLN + (size_t)(PB[hi] + (xh >> 6)) * B;
+                unsigned long long* pl = PLN + (size_t)(PB[lo] + (xl >> 6)) * B;
+                for (int k = 0; k < B; k++)
+                    if ((w >> k) & 1u) {
+                        atomicOr(ph + k, 1ull << (xh & 63));
+                        atomicOr(pl + k, 1ull << (xl & 63));
+                    }
+                atomicAdd(G + hi, w);
+                atomicAdd(G + lo, w);
+            }
+            __syncwarp();
+            if (valid && (peers & lt) == 0) LC[lo] = (uint16_t)(LC[lo] + __popc(peers));
+            __syncwarp();
+        }
+        __threadfence_block();
+        __syncwarp();
+        // scoring: one candidate p per lane
+        const uint32_t k0 = (uint32_t)S->seed, k1 = (uint32_t)(S->seed >> 32);
+        const uint32_t c2g = c2(PU_GI, 0);
+        const long long a = cold()->a, b = cold()->b;
+        long long best_s = LLONG_MIN;
+        int best_q = -1;
+        unsigned gi_terms = 0, gi_blocks = 0;
+        for (int base = 0; base < m; base += 32) {
+            const int p = base + lane;
+            if (p < m) {
+                const uint32_t e = C[p];
+                const int i = key_lo(e), j = key_hi(e), wp = cand_c(e) - 1;
+                const uint32_t key = e & 0x1FFFFFu;
+                const int n0 = (HE[i] - HS[i]) + LC[i];
+                const int n1 = (HE[j] - HS[j]) + LC[j];
+                const int lp0 = PL[p] - VB[i];  // p's place in A_i
+                const int lp1 = p - HS[j];      // p's place in A_j
+                int sib = -1;                   // the sign twin (i, j, -s), if a candidate
+                if (!(e & 1u)) {
+                    if (p + 1 < m && (C[p + 1] & 0x1FFFFFu) == (key | 1u)) sib = p + 1;
+                } else {
+                    if (p >= 1 && (C[p - 1] & 0x1FFFFFu) == (key & ~1u)) sib = p - 1;
+                }
+                const int ls1 = sib - HS[j];
+                const int wsib = sib >= 0 ? cand_c(C[sib]) - 1 : 0;
+                const int nint = (n0 - 1) + (n1 - 1 - (sib >= 0 ? 1 : 0));
+                long long X = 0;
+                int inter = 0, nb = 0;
+                if (nint > 0) {
+                    const int nb0 = (n0 + 63) >> 6, nb1 = (n1 + 63) >> 6;
+                    nb = nb0 > nb1 ? nb0 : nb1;
+                    const unsigned long long* P0 = PLN + (size_t)PB[i] * B;
+                    const unsigned long long* P1 = PLN + (size_t)PB[j] * B;
+                    for (int blk = 0; blk < nb; blk++) {
+                        uint32_t r0 = (uint32_t)proc, r1 = (uint32_t)t, r2 = c2g | (uint32_t)blk, r3 = key;
+                        philox(r0, r1, r2, r3, k0, k1);
+                        const unsigned long long R0 = (unsigned long long)r1 << 32 | r0;
+                        const unsigned long long R1 = (unsigned long long)r3 << 32 | r2;
+                        if (blk < nb0) {
+                            for (int k = 0; k < B; k++) X += (long long)__popcll(P0[blk * B + k] & R0) << k;
+                            if ((lp0 >> 6) == blk && ((R0 >> (lp0 & 63)) & 1ull)) X -= wp;
+                        }
+                        if (blk < nb1) {
+                            for (int k = 0; k < B; k++) X += (long long)__popcll(P1[blk * B + k] & R1) << k;
+                            if ((lp1 >> 6) == blk && ((R1 >> (lp1 & 63)) & 1ull)) X -= wp;
+                            if (sib >= 0 && (ls1 >> 6) == blk && ((R1 >> (ls1 & 63)) & 1ull)) X -= wsib;
+                        }
+                    }
+                    inter = (int)G[i] + (int)G[j] - 2 * wp - wsib;
+                }
+                const int D = T - wp - inter;
+                const long long sc = ((long long)wp << 32) + a * (((long long)D << 16) + b * X);
+                if (sc > best_s) {
+                    best_s = sc;
+                    best_q = p;
+                }
+                gi_terms += nint;
+                gi_blocks += nb;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            const long long s2 = __shfl_xor_sync(FULL_MASK, best_s, o);
+            const int q2 = __shfl_xor_sync(FULL_MASK, best_q, o);
+            if (s2 > best_s || (s2 == best_s && (unsigned)q2 < (unsigned)best_q)) {
+                best_s = s2;
+                best_q = q2;
+            }
+        }
+        gi_terms = __reduce_add_sync(FULL_MASK, gi_terms);
+        gi_blocks = __reduce_add_sync(FULL_MASK, gi_blocks);
+        if (lane == 0) {
+            Cold* cd = cold();
+            cd->t_gi_terms += gi_terms;
+            cd->t_gi_blocks += gi_blocks;
+            cd->t_gi_cands += (unsigned)m;
+        }
+        return best_q;
+    }
+
     __device__ int sel_gp() { return gp_select<W>(pn(), cand(), ncols, m, (uint32_t)cold()->a, lane, &cold()->t_gp); }
 
     __device__ int choose(int t) {
@@ -711,7 +892,12 @@ struct Engine {
             s = r < 8 ? ST_GI : r < 12 ? ST_GA : r < 14 ? ST_GR : ST_WR;
         }
         if (s == ST_GR) s = d.y < 0xC0000000u ? ST_GA : ST_WR;
-        if (s == ST_GI) return sel_gi(t);
+        if (s == ST_GI) {
+            if constexpr (GM)
+                return sel_gi_planes(t);
+            else
+                return sel_gi(t);
+        }
         if (s == ST_GP) return sel_gp();
         if (lane == 0) cold()->t_scan += (unsigned)m;
         if (s == ST_GA) return sel_ga(d.z);
@@ -779,15 +965,12 @@ __global__ void __launch_bounds__(128, CSE_MIN_BLOCKS) round_kernel(const DevMat
     const DevSearch* S = &searches[M->search];
     // step clock: this round runs steps [t0, t1).  Iteration mode: one whole
     // run per process, from step t0 = iteration * cap until the run ends.
-    const bool iter_mode = S->interval == 0;
     const int clk = *S->clock;
-    if (clk >= S->budget || (iter_mode && S->conv[1])) return;
-    const int t0 = iter_mode ? clk * M->cap : clk;
-    const int t1 = iter_mode ? t0 : min(t0 + S->interval, S->budget);
-    const bool more = iter_mode ? clk + 1 < S->budget : t1 < S->budget;
+    if (clk >= S->budget || (S->interval == 0 && S->conv[1])) return;
+    const int t0 = S->interval == 0 ? clk * M->cap : clk;
 
     uint32_t* st = M->state + (size_t)(unit - M->unit_base) * M->state_words;
-    Engine<W> E;
+    Engine<W, GM> E;
     E.sm = GM ? reinterpret_cast<unsigned char*>(st + H_WORDS) : smem + (size_t)warp * L.per_warp;
     E.L = GM ? &M->gml : &L;
     E.M = M;
@@ -853,20 +1036,21 @@ __global__ void __launch_bounds__(128, CSE_MIN_BLOCKS) round_kernel(const DevMat
     if (lane == 0) cd->sub_before = cd->substeps;
     __syncwarp();
 
-    int steps_run = t1 - t0;
-    if (iter_mode) {
-        // a run makes at most cap - nx substitutions plus the step that ends
-        // it, so t stays below the next iteration's first step
-        int t = t0;
-        do {
-            E.step(t);
-            t++;
-        } while (!E.ended);
-        steps_run = t - t0;
-    } else {
-        for (int t = t0; t < t1; t++) E.step(t);
+    // Iteration mode: the run goes on until it ends; it makes at most
+    // cap - nx substitutions plus the step that ends it, so it ends before
+    // t0 + cap, the next iteration's first step (the bound is never reached).
+    // One call site of step() keeps a single copy of the engine in the code.
+    const bool iter = S->interval == 0;
+    const int t1 = iter ? t0 + M->cap : min(t0 + S->interval, S->budget);
+    int t = t0;
+    while (t < t1) {
+        E.step(t);
+        t++;
+        if (iter && E.ended) break;
     }
     E.fold();
+    // the state is needed by the next round
+    const bool more = S->interval == 0 ? t0 / M->cap + 1 < S->budget : t < S->budget;
 
     if (lane == 0) {
         // algorithmic ops of the round: 10 W per rewrite, 5 W per pair count
@@ -880,7 +1064,7 @@ __global__ void __launch_bounds__(128, CSE_MIN_BLOCKS) round_kernel(const DevMat
         atomicMin(M->round_min, (unsigned long long)(uint32_t)cd->best_cost << 32 | (uint32_t)E.proc);
         atomicAdd(&M->counters[0], (unsigned long long)dops);
         atomicAdd(&M->counters[1], (unsigned long long)(cd->substeps - cd->sub_before));
-        if (iter_mode) atomicAdd(&M->counters[2], (unsigned long long)steps_run);
+        if (S->interval == 0) atomicAdd(&M->counters[2], (unsigned long long)(t - t0));
         if (cd->overflow) atomicExch(S->status, 1);
         st[H_NCOLS] = (uint32_t)E.ncols;
         st[H_NF] = (uint32_t)E.nf;
@@ -899,7 +1083,7 @@ __global__ void __launch_bounds__(128, CSE_MIN_BLOCKS) round_kernel(const DevMat
         st[H_OPS_LO] = (uint32_t)ops;
         st[H_OPS_HI] = (uint32_t)(ops >> 32);
     }
-    if (!GM && more) {  // the state is needed by the next round
+    if (!GM && more) {
         uint2* spn = reinterpret_cast<uint2*>(st + H_WORDS);
         const uint2* P = E.pn();
         for (int x = lane; x < E.ncols * W; x += 32) spn[x] = P[x];
@@ -1014,8 +1198,8 @@ __global__ void brent_kernel(const int8_t* __restrict__ U, const int8_t* __restr
 // ---------------------------------------------------------------------------
 static int align16(int x) { return (x + 15) & ~15; }
 
-WarpLayout make_layout(int W, int cap, int mmax) {
-    WarpLayout L;
+WarpLayout make_layout(int W, int cap, int mmax, bool planes) {
+    WarpLayout L{};
     int o = 0;
     L.off_cold = o;
     o = align16(o + (int)sizeof(Cold));
@@ -1026,7 +1210,7 @@ WarpLayout make_layout(int W, int cap, int mmax) {
     L.off_f = o;
     o = align16(o + cap * 4);
     L.off_aw = o;
-    o = align16(o + 2 * mmax);
+    o = align16(o + (planes ? 0 : 2 * mmax));
     L.off_poslo = o;
     o = align16(o + mmax * 2);
     L.off_hs = o;
@@ -1037,6 +1221,17 @@ WarpLayout make_layout(int W, int cap, int mmax) {
     o = align16(o + cap * 2);
     L.off_lc = o;
     o = align16(o + cap * 2);
+    if (planes) {
+        // sum over v of ceil(|A_v| / 64) <= (2 mmax + 63 cap) / 64; 8 planes
+        // cover any weight c - 1 <= 255
+        const int max_blocks = (2 * mmax + 63 * cap) / 64 + 1;
+        L.off_pb = o;
+        o = align16(o + cap * 2);
+        L.off_g = o;
+        o = align16(o + cap * 4);
+        L.off_pln = o;
+        o = align16(o + max_blocks * 8 * 8);
+    }
     L.per_warp = o;
     return L;
 }

@@ -94,8 +94,8 @@ extern "C" int cse_search_static(const cse_scheme* s, const cse_strategy_mix* mi
     for (int k = 0; k < nm; k++) {
         const WarpLayout own = make_layout(s->W[k], cap, s->mmax[k]);
         gm[k] = own.per_warp > kSmemPerWarpLimit;
-        mats[k].gml = own;
-        mats[k].state_words = gm[k] ? state_words_gm(own) : state_words(s->W[k], cap, s->mmax[k]);
+        mats[k].gml = gm[k] ? make_layout(s->W[k], cap, s->mmax[k], true) : own;
+        mats[k].state_words = gm[k] ? state_words_gm(mats[k].gml) : state_words(s->W[k], cap, s->mmax[k]);
         o_state[k] = take(off, (size_t)n_proc * mats[k].state_words * 4);
         o_best[k] = take(off, (size_t)n_proc * cap * 4);
         o_snap[k] = take(off, (size_t)cap * 4);
