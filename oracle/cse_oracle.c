@@ -47,6 +47,12 @@
  *      GI, extra_hi = x >> 6 (bit x & 63), extra_lo = key(p).  Positions
  *      count every member of A_v, p and its sign twin included, so each
  *      intersecting q gets its own bit.  Coin 1: q survives with weight beta.
+ *   R9b shared coins (option ORACLE_GI_SHARED_COINS; the paper gives only the
+ *      marginals): every candidate q gets one coin per step, the same for
+ *      every p that intersects it: bit q & 31 of word (q >> 5) & 3 of the draw
+ *      with purpose GIS (4), extra_hi = q >> 7, extra_lo = 0.  The score is
+ *      the same sum over intersecting q; the op count per step is 40 per
+ *      128 candidates + 18 per candidate + 2 per column.
  *   R10 the step clock: every process performs one step per t.  A step
  *      first (re)starts the run if t == 0 or the previous run ended, then
  *      makes one substitution if a pair with c > 1 exists and a free column
@@ -94,7 +100,7 @@
 #define ENT_J(e) ((int32_t)(((uint32_t)(e) >> 10) & 0x3FFu))
 #define ENT_NEG(e) ((int32_t)(((uint32_t)(e) >> 20) & 1u))
 
-enum { PU_RUN = 0, PU_SHAREK = 1, PU_STEP = 2, PU_GI = 3 };
+enum { PU_RUN = 0, PU_SHAREK = 1, PU_STEP = 2, PU_GI = 3, PU_GIS = 4 };
 
 /* ------------------------------------------------------------------ */
 /* Philox4x32-10, from the definition in Salmon et al., SC'11:          */
@@ -321,10 +327,17 @@ typedef struct {
     /* explicit mode */
     const uint8_t* bits;
     int32_t m;
+    /* shared mode (R9b): one coin per candidate q per step, seen by every p */
+    int32_t shared, ncols;
 } coin_src;
 
 static int coin_at(coin_src* cs, int32_t p, int32_t q, int32_t slot, int32_t rho) {
     if (cs->bits) return cs->bits[(int64_t)p * cs->m + q] != 0;
+    if (cs->shared) {
+        uint32_t o[4];
+        draw4(cs->seed, cs->proc, cs->t, cs->mat, PU_GIS, (uint32_t)q >> 7, 0, o);
+        return (int)((o[(q >> 5) & 3] >> (q & 31)) & 1u);
+    }
     int32_t blk = rho >> 6;
     if (cs->block_p != p || cs->block_idx != blk) {
         draw4(cs->seed, cs->proc, cs->t, cs->mat, PU_GI, (uint32_t)blk, cs->keys[p], cs->block);
@@ -381,6 +394,9 @@ static int32_t sel_gi(const uint32_t* keys, const int32_t* cnt, int32_t m, uint3
         int32_t b0 = (pos0 + 63) >> 6, b1 = (pos1 + 63) >> 6;
         ops += 3 * (int64_t)n_inter + 8 + (n_inter ? 40 * (int64_t)(b0 > b1 ? b0 : b1) : 0);
     }
+    /* shared coins: 40 per Philox block of 128 candidates, 18 per candidate
+     * (its two per-variable sums and its score), 2 per column */
+    if (cs->shared) ops = 40 * (int64_t)((m + 127) / 128) + 18 * (int64_t)m + 2 * (int64_t)cs->ncols;
     if (ops_out) *ops_out = ops;
     return best;
 }
@@ -596,6 +612,7 @@ typedef struct {
 
 typedef struct {
     int32_t n_mats, n_proc, interval, permille, cap;
+    int32_t gi_shared;  /* R9b */
     uint64_t seed;
     uint32_t w[OR_NSTRAT];
     uint64_t wsum;
@@ -736,6 +753,8 @@ static int32_t choose(const search_t* S, int32_t mi, int32_t pi, int64_t t, proc
             cs.t = t;
             cs.keys = P->keys;
             cs.block_p = -1;
+            cs.shared = S->gi_shared;
+            cs.ncols = P->ncols;
             int64_t ops = 0;
             int32_t sel = sel_gi(P->keys, P->cnt, P->m, (uint32_t)P->a, (uint32_t)P->b, &cs, NULL, &ops);
             P->ops += ops;
@@ -829,9 +848,10 @@ static int valid_matrix(const int8_t* m, int32_t rows, int32_t cols) {
 static int search_impl(int32_t n_mats, const int8_t* const* mats, const int32_t* rows,
                        const int32_t* cols, const uint32_t* weights7, int32_t n_proc, uint64_t seed,
                        int64_t budget, int32_t interval, int32_t patience, int32_t permille, int32_t cap,
-                       int32_t n_threads, const int32_t* proc_subset, int32_t n_subset,
+                       uint32_t flags, int32_t n_threads, const int32_t* proc_subset, int32_t n_subset,
                        int64_t* out_cost, int32_t* out_len, int32_t* out_list, oracle_digest* dig,
                        int64_t* stats) {
+    if (flags & ~(uint32_t)ORACLE_GI_SHARED_COINS) return -1;
     if (n_mats < 1 || n_mats > 256 || n_proc < 1 || budget < 0 || interval < 0 || patience < 0 ||
         permille < 0 || permille > 1000 || cap < 2 || cap > 1024)
         return -1;
@@ -844,6 +864,7 @@ static int search_impl(int32_t n_mats, const int8_t* const* mats, const int32_t*
     S.permille = permille;
     S.cap = cap;
     S.seed = seed;
+    S.gi_shared = (flags & ORACLE_GI_SHARED_COINS) != 0;
     for (int32_t s = 0; s < OR_NSTRAT; s++) {
         S.w[s] = weights7[s];
         S.wsum += weights7[s];
@@ -1030,15 +1051,25 @@ int oracle_search(int32_t n_mats, const int8_t* const* mats, const int32_t* rows
                   int32_t n_threads, const int32_t* proc_subset, int32_t n_subset,
                   int64_t* out_cost, int32_t* out_len, int32_t* out_list, oracle_digest* dig) {
     if (interval < 1) return -1;
-    return search_impl(n_mats, mats, rows, cols, weights7, n_proc, seed, budget, interval, 0, permille, cap,
+    return search_impl(n_mats, mats, rows, cols, weights7, n_proc, seed, budget, interval, 0, permille, cap, 0,
                        n_threads, proc_subset, n_subset, out_cost, out_len, out_list, dig, NULL);
+}
+
+int oracle_search_flags(int32_t n_mats, const int8_t* const* mats, const int32_t* rows,
+                        const int32_t* cols, const uint32_t* weights7, int32_t n_proc, uint64_t seed,
+                        int64_t budget, int32_t interval, int32_t permille, int32_t cap, uint32_t flags,
+                        int32_t n_threads, const int32_t* proc_subset, int32_t n_subset,
+                        int64_t* out_cost, int32_t* out_len, int32_t* out_list, oracle_digest* dig) {
+    if (interval < 1) return -1;
+    return search_impl(n_mats, mats, rows, cols, weights7, n_proc, seed, budget, interval, 0, permille, cap,
+                       flags, n_threads, proc_subset, n_subset, out_cost, out_len, out_list, dig, NULL);
 }
 
 int oracle_search_iterations(int32_t n_mats, const int8_t* const* mats, const int32_t* rows,
                              const int32_t* cols, const uint32_t* weights7, int32_t n_proc, uint64_t seed,
                              int64_t max_iterations, int32_t patience, int32_t permille, int32_t cap,
-                             int32_t n_threads, int64_t* out_cost, int32_t* out_len, int32_t* out_list,
-                             oracle_digest* dig, int64_t* stats) {
+                             uint32_t flags, int32_t n_threads, int64_t* out_cost, int32_t* out_len,
+                             int32_t* out_list, oracle_digest* dig, int64_t* stats) {
     return search_impl(n_mats, mats, rows, cols, weights7, n_proc, seed, max_iterations, 0, patience, permille,
-                       cap, n_threads, NULL, 0, out_cost, out_len, out_list, dig, stats);
+                       cap, flags, n_threads, NULL, 0, out_cost, out_len, out_list, dig, stats);
 }

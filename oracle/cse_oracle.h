@@ -21,6 +21,10 @@
 extern "C" {
 #endif
 
+/* Search flag: Greedy-Intersections with one coin per candidate per step,
+ * shared by every candidate it intersects (R9b in cse_oracle.c). */
+#define ORACLE_GI_SHARED_COINS 1u
+
 /* Strategy indices (Section 3.4); weights are given in this order. */
 enum { OR_GI = 0, OR_GA = 1, OR_GR = 2, OR_WR = 3, OR_MIX = 4, OR_G = 5, OR_GP = 6, OR_NSTRAT = 7 };
 
@@ -103,8 +107,15 @@ int oracle_search(int32_t n_mats, const int8_t* const* mats, const int32_t* rows
 int oracle_search_iterations(int32_t n_mats, const int8_t* const* mats, const int32_t* rows,
                              const int32_t* cols, const uint32_t* weights7, int32_t n_proc, uint64_t seed,
                              int64_t max_iterations, int32_t patience, int32_t permille, int32_t cap,
-                             int32_t n_threads, int64_t* out_cost, int32_t* out_len, int32_t* out_list,
-                             oracle_digest* dig, int64_t* stats);
+                             uint32_t flags, int32_t n_threads, int64_t* out_cost, int32_t* out_len,
+                             int32_t* out_list, oracle_digest* dig, int64_t* stats);
+
+/* oracle_search with search flags (ORACLE_GI_SHARED_COINS). */
+int oracle_search_flags(int32_t n_mats, const int8_t* const* mats, const int32_t* rows,
+                        const int32_t* cols, const uint32_t* weights7, int32_t n_proc, uint64_t seed,
+                        int64_t budget, int32_t interval, int32_t permille, int32_t cap, uint32_t flags,
+                        int32_t n_threads, const int32_t* proc_subset, int32_t n_subset,
+                        int64_t* out_cost, int32_t* out_len, int32_t* out_list, oracle_digest* dig);
 
 #ifdef __cplusplus
 }

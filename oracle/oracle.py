@@ -22,6 +22,7 @@ _lib = None
 
 G, GI, GA, GR, WR, MIX, GP = 5, 0, 1, 2, 3, 4, 6
 N_STRATEGIES = 7
+GI_SHARED_COINS = 1  # search flag: one Greedy-Intersections coin per candidate per step
 
 
 class Digest(ctypes.Structure):
@@ -82,8 +83,13 @@ def lib():
         L.oracle_search.restype = ctypes.c_int
         L.oracle_search_iterations.argtypes = [ctypes.c_int32, ctypes.POINTER(i8p), i32p, i32p, u32p, ctypes.c_int32,
                                                ctypes.c_uint64, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
-                                               ctypes.c_int32, ctypes.c_int32, i64p, i32p, i32p,
+                                               ctypes.c_int32, ctypes.c_uint32, ctypes.c_int32, i64p, i32p, i32p,
                                                ctypes.POINTER(Digest), i64p]
+        L.oracle_search_flags.argtypes = [ctypes.c_int32, ctypes.POINTER(i8p), i32p, i32p, u32p, ctypes.c_int32,
+                                          ctypes.c_uint64, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                          ctypes.c_int32, ctypes.c_uint32, ctypes.c_int32, i32p, ctypes.c_int32,
+                                          i64p, i32p, i32p, ctypes.POINTER(Digest)]
+        L.oracle_search_flags.restype = ctypes.c_int
         L.oracle_search_iterations.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -201,7 +207,7 @@ class SearchResult:
 
 def search(mats: Sequence[np.ndarray], weights, n_proc: int, seed: int, budget: int, interval: int,
            permille: int, cap: int, n_threads: int = 1, subset: Optional[Sequence[int]] = None,
-           digests: bool = True) -> SearchResult:
+           digests: bool = True, flags: int = 0) -> SearchResult:
     ms = [np.ascontiguousarray(m, dtype=np.int8) for m in mats]
     n = len(ms)
     ptrs = (ctypes.POINTER(ctypes.c_int8) * n)(*[_p(m, ctypes.c_int8) for m in ms])
@@ -216,8 +222,8 @@ def search(mats: Sequence[np.ndarray], weights, n_proc: int, seed: int, budget: 
     lists = np.zeros((n, cap), dtype=np.int32)
     dig = np.zeros((n, n_proc), dtype=DIGEST_DTYPE) if digests else None
     sub = None if subset is None else np.ascontiguousarray(np.array(subset, dtype=np.int32))
-    rc = lib().oracle_search(n, ptrs, _p(rows, ctypes.c_int32), _p(cols, ctypes.c_int32),
-                             _p(w, ctypes.c_uint32), n_proc, seed, budget, interval, permille, cap, n_threads,
+    rc = lib().oracle_search_flags(n, ptrs, _p(rows, ctypes.c_int32), _p(cols, ctypes.c_int32),
+                             _p(w, ctypes.c_uint32), n_proc, seed, budget, interval, permille, cap, flags, n_threads,
                              None if sub is None else _p(sub, ctypes.c_int32), 0 if sub is None else len(sub),
                              _p(cost, ctypes.c_int64), _p(length, ctypes.c_int32), _p(lists, ctypes.c_int32),
                              None if dig is None else dig.ctypes.data_as(ctypes.POINTER(Digest)))
@@ -229,7 +235,7 @@ def search(mats: Sequence[np.ndarray], weights, n_proc: int, seed: int, budget: 
 
 def search_iterations(mats: Sequence[np.ndarray], weights, n_proc: int, seed: int, max_iterations: int,
                       patience: int, permille: int, cap: int, n_threads: int = 1,
-                      digests: bool = True) -> SearchResult:
+                      digests: bool = True, flags: int = 0) -> SearchResult:
     """Iteration mode (the paper's schedule): one whole run per process per
     iteration, sharing between iterations, stop on patience.  The result's
     `iterations` and `process_steps` say how long it ran."""
@@ -247,7 +253,7 @@ def search_iterations(mats: Sequence[np.ndarray], weights, n_proc: int, seed: in
     stats = np.zeros(2, dtype=np.int64)
     rc = lib().oracle_search_iterations(n, ptrs, _p(rows, ctypes.c_int32), _p(cols, ctypes.c_int32),
                                         _p(w, ctypes.c_uint32), n_proc, seed, max_iterations, patience, permille,
-                                        cap, n_threads, _p(cost, ctypes.c_int64), _p(length, ctypes.c_int32),
+                                        cap, flags, n_threads, _p(cost, ctypes.c_int64), _p(length, ctypes.c_int32),
                                         _p(lists, ctypes.c_int32),
                                         None if dig is None else dig.ctypes.data_as(ctypes.POINTER(Digest)),
                                         _p(stats, ctypes.c_int64))

@@ -578,3 +578,71 @@ def test_brent_counts_match_numpy_tensor(seed):
     for i, j, k in itertools.product(range(m), range(n), range(p)):
         ref[i * n + j, j * p + k, i * p + k] = 1
     assert O.brent_violations(m, n, p, U, V, W) == int(np.count_nonzero(T != ref))
+
+
+# ---------------------------------------------------------------- shared gi coins
+def _fnv(words):
+    h = 0xCBF29CE484222325
+    for w in words:
+        h = ((h ^ (w & 0xFFFFFFFF)) * 0x100000001B3) & 0xFFFFFFFFFFFFFFFF
+    return h
+
+
+def _draw4(seed, proc, t, mat, purpose, extra_hi=0, extra_lo=0):
+    return O.philox([proc, t, (mat & 0xFF) << 24 | (purpose & 0xF) << 20 | (extra_hi & 0xFFFFF), extra_lo],
+                    [seed & 0xFFFFFFFF, seed >> 32])
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_shared_coin_first_pick_from_the_stated_draws(seed):
+    """Greedy-Intersections with shared coins, rebuilt from Philox (pinned by
+    its known answers) and the readings: the run draw gives alpha and beta,
+    each candidate q gets the coin at bit q & 31 of word (q >> 5) & 3 of the
+    purpose-4 draw for block q >> 7, and the first substitution of process 1
+    is the argmax of the scores with those coins (identical for every p)."""
+    mat = synth.random_matrix(800 + seed, 60, 14, 3, 7, n_planted=12)   # m ~ 180: two 128-blocks
+    keys, counts = zip(*O.pairs(mat))
+    m = len(keys)
+    run = _draw4(seed, 1, 0, 0, 0)
+    a = (run[1] * 32769) >> 32
+    b = 32768 + ((run[2] * 32769) >> 32)
+    coins = np.array([(_draw4(seed, 1, 0, 0, 4, q >> 7)[(q >> 5) & 3] >> (q & 31)) & 1 for q in range(m)], np.uint8)
+    best, _ = O.gi_scores(keys, counts, a, b, np.tile(coins, (m, 1)))
+    i, j, s = O.unkey(keys[best])
+    r = O.search([mat], synth.GI_ONLY, 2, seed, 1, 8, 0, 32, flags=O.GI_SHARED_COINS)
+    assert r.digests[0]["best_hash"][1] == _fnv([O.entry(i, j, s)])
+    assert r.digests[0]["best_len"][1] == 1
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_shared_coin_scores_from_per_variable_sums(seed):
+    """With one coin per candidate, X_p = X_i + X_j - 2 coin_p w_p - coin_t w_t
+    (t the sign twin) where X_v sums coin_q w_q over the candidates holding
+    x_v; the same holds for the plain sums.  Checked against the direct
+    O(m^2) scores."""
+    mat = synth.random_matrix(900 + seed, 24, 10, 2, 5, n_planted=7)
+    keys, counts = zip(*O.pairs(mat))
+    m = len(keys)
+    rng = np.random.default_rng(seed)
+    coins = rng.integers(0, 2, m).astype(np.int64)
+    a, b = 20000, 40000
+    _, sc = O.gi_scores(keys, counts, a, b, np.tile(coins.astype(np.uint8), (m, 1)))
+    w = np.array(counts, np.int64) - 1
+    ij = [O.unkey(k)[:2] for k in keys]
+    nv = 1 + max(max(x) for x in ij)
+    G = np.zeros(nv, np.int64)
+    X = np.zeros(nv, np.int64)
+    for (i, j), wq, cq in zip(ij, w, coins):
+        G[i] += wq
+        G[j] += wq
+        X[i] += cq * wq
+        X[j] += cq * wq
+    T = int(w.sum())
+    for p, (i, j) in enumerate(ij):
+        tw = [q for q in range(m) if q != p and ij[q] == (i, j)]
+        wt = int(w[tw[0]]) if tw else 0
+        ct = int(coins[tw[0]]) if tw else 0
+        inter = G[i] + G[j] - 2 * w[p] - wt
+        x = X[i] + X[j] - 2 * coins[p] * w[p] - ct * wt
+        d = T - w[p] - inter
+        assert sc[p] == (int(w[p]) << 32) + a * ((int(d) << 16) + b * int(x))
