@@ -80,10 +80,17 @@ typedef struct {
                               matrix classes become parallel graph branches */
 #define CSE_FLAG_TRACE 2u  /* record each process's trajectory hash (see
                               cse_proc_record); costs a few per cent */
+#define CSE_FLAG_GI_SHARED_COINS 4u  /* changes results: Greedy-Intersections
+                              draws one coin per candidate per step, seen by
+                              every candidate it intersects, instead of one
+                              coin per (scored, intersecting) pair; the paper
+                              (Section 3.4.2) fixes only each coin's 1/2
+                              marginal.  Scoring then costs O(m + columns) per
+                              step through per-variable sums. */
 
 /* Search options.  Fields that change results: share_interval,
- * share_permille, col_cap, patience_rounds.  The rest only change how the
- * work is launched.
+ * share_permille, col_cap, patience_rounds and the flag
+ * CSE_FLAG_GI_SHARED_COINS.  The rest only change how the work is launched.
  *
  * share_interval >= 1 selects the step clock: every process makes one step
  * per global step, and sharing happens every share_interval steps.

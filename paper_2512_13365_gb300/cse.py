@@ -62,6 +62,7 @@ EXPORTS = ["cse_opts_default", "cse_scheme_load", "cse_scheme_load_uvw", "cse_sc
 
 FLAG_GRAPH = 1
 FLAG_TRACE = 2
+FLAG_GI_SHARED_COINS = 4
 
 
 def lib() -> ctypes.CDLL:
@@ -267,23 +268,23 @@ def make_mix(weights) -> Mix:
 
 
 def make_opts(interval: int = 32, permille: int = 400, cap: int = 128, procs_per_cta: int = 0,
-              graph: bool = False, trace: bool = False, patience: int = 0) -> Opts:
+              graph: bool = False, trace: bool = False, patience: int = 0, gi_shared: bool = False) -> Opts:
     """interval 0 selects iteration mode (budget = maximum iterations, stop
     after `patience` iterations without improvement)."""
     o = Opts()
     lib().cse_opts_default(ctypes.byref(o))
     o.share_interval, o.share_permille, o.col_cap, o.procs_per_cta = interval, permille, cap, procs_per_cta
     o.patience_rounds = patience
-    o.flags = (FLAG_GRAPH if graph else 0) | (FLAG_TRACE if trace else 0)
+    o.flags = (FLAG_GRAPH if graph else 0) | (FLAG_TRACE if trace else 0) | (FLAG_GI_SHARED_COINS if gi_shared else 0)
     return o
 
 
 def search(scheme: Scheme, weights, n_proc: int, seed: int, budget: int, interval: int = 32,
            permille: int = 400, cap: int = 128, stream=None, procs_per_cta: int = 0, graph: bool = False,
-           trace: bool = False, patience: int = 0) -> Result:
+           trace: bool = False, patience: int = 0, gi_shared: bool = False) -> Result:
     """cse_search: enqueue the search and return its Result handle."""
     mix = make_mix(weights)
-    opts = make_opts(interval, permille, cap, procs_per_cta, graph, trace, patience)
+    opts = make_opts(interval, permille, cap, procs_per_cta, graph, trace, patience, gi_shared)
     h = ctypes.c_void_p()
     _check(lib().cse_search(scheme.handle, ctypes.byref(mix), n_proc, seed, budget, ctypes.byref(opts),
                             _stream_ptr(stream), ctypes.byref(h)))
@@ -301,7 +302,7 @@ def search_obj(s, scheme: Optional[Scheme] = None, **kw) -> Result:
 def search_batch(schemes: Sequence[Scheme], weights: Sequence, n_procs: Sequence[int], seeds: Sequence[int],
                  budgets: Sequence[int], interval: int = 32, permille: int = 400, cap: int = 128, stream=None,
                  procs_per_cta: int = 0, graph: bool = True, trace: bool = False,
-                 patience: int = 0) -> List[Result]:
+                 patience: int = 0, gi_shared: bool = False) -> List[Result]:
     """cse_search_batch: independent searches in one launch sequence."""
     n = len(schemes)
     hs = (ctypes.c_void_p * n)(*[s.handle for s in schemes])
@@ -309,7 +310,7 @@ def search_batch(schemes: Sequence[Scheme], weights: Sequence, n_procs: Sequence
     np_ = (ctypes.c_int32 * n)(*n_procs)
     sd = (ctypes.c_uint64 * n)(*seeds)
     bd = (ctypes.c_int64 * n)(*budgets)
-    opts = make_opts(interval, permille, cap, procs_per_cta, graph, trace, patience)
+    opts = make_opts(interval, permille, cap, procs_per_cta, graph, trace, patience, gi_shared)
     outs = (ctypes.c_void_p * n)()
     _check(lib().cse_search_batch(n, hs, mixes, np_, sd, bd, ctypes.byref(opts), _stream_ptr(stream), outs))
     res = []
@@ -363,9 +364,11 @@ class Server:
     """Continuous-batching server (cse_server_*)."""
 
     def __init__(self, interval: int = 32, permille: int = 400, cap: int = 128, hbm_budget: int = 0,
-                 max_active_processes: int = 0, procs_per_cta: int = 0, trace: bool = False):
+                 max_active_processes: int = 0, procs_per_cta: int = 0, trace: bool = False,
+                 gi_shared: bool = False):
         h = ctypes.c_void_p()
-        _check(lib().cse_server_create(ctypes.byref(make_opts(interval, permille, cap, procs_per_cta, trace=trace)),
+        opts = make_opts(interval, permille, cap, procs_per_cta, trace=trace, gi_shared=gi_shared)
+        _check(lib().cse_server_create(ctypes.byref(opts),
                                        hbm_budget,
                                        max_active_processes, ctypes.byref(h)))
         self.handle = h

@@ -132,6 +132,7 @@ struct LaunchSet {
     void* d_params = nullptr;
     DevMat* d_mats = nullptr;
     DevSearch* d_searches = nullptr;
+    bool gs = false;  // the searches use shared Greedy-Intersections coins
 };
 
 // One static launch (cse_search / cse_search_batch): events, the parameter
@@ -191,7 +192,7 @@ static int check_opts(const cse_opts* opts_in, cse_opts* opts) {
     else
         cse_opts_default(opts);
     if (opts->share_permille > 1000) return fail(CSE_EINVAL, "share_permille must be <= 1000");
-    if ((opts->flags & ~(uint32_t)(CSE_FLAG_GRAPH | CSE_FLAG_TRACE)) != 0)
+    if ((opts->flags & ~(uint32_t)(CSE_FLAG_GRAPH | CSE_FLAG_TRACE | CSE_FLAG_GI_SHARED_COINS)) != 0)
         return fail(CSE_EINVAL, "reserved option fields must be 0");
     if (opts->share_interval != 0 && opts->patience_rounds != 0)
         return fail(CSE_EINVAL, "patience_rounds applies to iteration mode (share_interval = 0) only");
@@ -293,6 +294,7 @@ static int search_create(const cse_scheme* s, const cse_strategy_mix* mix, int n
     S.conv = (int32_t*)(b + of[8 * s->n_mats + 2]);
     S.n_mats = s->n_mats;
     S.trace = (opts.flags & CSE_FLAG_TRACE) ? 1 : 0;
+    S.gi_shared = (opts.flags & CSE_FLAG_GI_SHARED_COINS) ? 1 : 0;
     static const int32_t snap_init[2] = {INT_MAX, 0};
     for (int k = 0; k < s->n_mats; k++) {
         DevMat& M = sd->mats[k];
@@ -348,6 +350,9 @@ static int build_launch(const std::vector<SearchDev*>& act, int ppc_req, const T
         return x.W != y.W ? x.W < y.W : x.gm < y.gm;
     });
     const int nm = (int)refs.size(), n = (int)act.size();
+    ls->gs = n > 0 && act[0]->search.gi_shared != 0;
+    for (int i = 1; i < n; i++)
+        if ((act[i]->search.gi_shared != 0) != ls->gs) return fail(CSE_EINVAL, "searches of one launch differ in coin mode");
     ls->mats.resize(nm);
     ls->groups.clear();
     for (int q = 0; q < nm; q++) {
@@ -377,7 +382,7 @@ static int build_launch(const std::vector<SearchDev*>& act, int ppc_req, const T
         if (!g.gm)
             while (g.ppc > 1 && (long long)g.L.per_warp * g.ppc > smem_max) g.ppc--;
         if (!g.gm && g.L.per_warp > smem_max) return fail(CSE_ENOMEM, "process slice exceeds shared memory");
-        cudaError_t e = prepare_round(g.W, g.gm, g.L, g.ppc);
+        cudaError_t e = prepare_round(g.W, g.gm, ls->gs, g.L, g.ppc);
         if (e != cudaSuccess) return fail(CSE_ECUDA, std::string("kernel attributes: ") + cudaGetErrorString(e));
         if (trial && trial->keys) trial->keys->push_back(g.key);
     }
@@ -423,7 +428,8 @@ static cudaError_t enqueue_round(const LaunchSet& ls, cudaStream_t st, const std
         for (size_t gi = 0; gi < ng; gi++) {
             const auto& g = ls.groups[gi];
             cudaStreamWaitEvent((*aux)[gi], (*fork)[0], 0);
-            e = launch_round(g.W, g.gm, ls.d_mats + g.begin, g.count, ls.d_searches, g.units, g.L, g.ppc, (*aux)[gi]);
+            e = launch_round(g.W, g.gm, ls.gs, ls.d_mats + g.begin, g.count, ls.d_searches, g.units, g.L, g.ppc,
+                             (*aux)[gi]);
             if (e != cudaSuccess) return e;
             cudaEventRecord((*fork)[gi + 1], (*aux)[gi]);
             cudaStreamWaitEvent(st, (*fork)[gi + 1], 0);
@@ -432,7 +438,7 @@ static cudaError_t enqueue_round(const LaunchSet& ls, cudaStream_t st, const std
         for (size_t gi = 0; gi < ng; gi++) {
             const auto& g = ls.groups[gi];
             if (group_ev) cudaEventRecord(group_ev[2 * gi], st);
-            e = launch_round(g.W, g.gm, ls.d_mats + g.begin, g.count, ls.d_searches, g.units, g.L, g.ppc, st);
+            e = launch_round(g.W, g.gm, ls.gs, ls.d_mats + g.begin, g.count, ls.d_searches, g.units, g.L, g.ppc, st);
             if (e != cudaSuccess) return e;
             if (group_ev) cudaEventRecord(group_ev[2 * gi + 1], st);
         }
@@ -1213,7 +1219,7 @@ int cse_server_create(const cse_opts* opts_in, uint64_t hbm_budget_bytes, int64_
     cse_opts opts;
     int rc = check_opts(opts_in, &opts);
     if (rc) return rc;
-    opts.flags &= CSE_FLAG_TRACE;
+    opts.flags &= CSE_FLAG_TRACE | CSE_FLAG_GI_SHARED_COINS;
     if (opts.share_interval == 0)
         return fail(CSE_EINVAL, "the server admits requests at round boundaries of the step clock: share_interval >= 1");
     if (max_smem_per_block() <= 0) return fail(CSE_ECUDA, "no CUDA device");

@@ -30,7 +30,7 @@ enum Strategy : int { ST_GI = 0, ST_GA = 1, ST_GR = 2, ST_WR = 3, ST_MIX = 4, ST
 //   SHAREK prefix length of a shared start (lane 0)
 //   STEP   per step, when the strategy draws: lane 0 mix, 1 gr, 2 ga, 3 wr
 //   GI     Greedy-Intersections coins of one candidate (extra_lo = its key)
-enum Purpose : uint32_t { PU_RUN = 0, PU_SHAREK = 1, PU_STEP = 2, PU_GI = 3 };
+enum Purpose : uint32_t { PU_RUN = 0, PU_SHAREK = 1, PU_STEP = 2, PU_GI = 3, PU_GIS = 4 };
 
 // Per-process state header, in 32-bit words at the start of the process's
 // state region in global memory.
@@ -91,6 +91,7 @@ struct DevSearch {
     int32_t n_mats;
     int32_t* status;         // nonzero: a device-side consistency check failed
     int32_t trace;           // record the trajectory hash (CSE_FLAG_TRACE)
+    int32_t gi_shared;       // Greedy-Intersections with shared coins (CSE_FLAG_GI_SHARED_COINS)
 };
 
 // planes: the HBM-path layout (weight bit-planes instead of weight bytes).
@@ -106,15 +107,19 @@ constexpr int kSmemPerWarpLimit = 24 * 1024;
 // launch error, if any.
 cudaError_t launch_ingest(const int8_t* raw, int rows, int nx, int W, uint2* pn0, uint32_t* cand0,
                           int32_t* meta0, int mmax, cudaStream_t stream);
-cudaError_t launch_round(int W, bool gm, const DevMat* mats, int n_mats, const DevSearch* searches,
+// gs: the engine variant with shared Greedy-Intersections coins.
+cudaError_t launch_round(int W, bool gm, bool gs, const DevMat* mats, int n_mats, const DevSearch* searches,
                          int total_units, const WarpLayout& L, int procs_per_cta,
                          cudaStream_t stream);
+cudaError_t launch_round_gs(int W, bool gm, const DevMat* mats, int n_mats, const DevSearch* searches,
+                            int total_units, const WarpLayout& L, int procs_per_cta, cudaStream_t stream,
+                            bool prepare_only);
 cudaError_t launch_share(const DevMat* mats, const DevSearch* searches, int n_searches,
                          cudaStream_t stream);
 cudaError_t launch_brent(const int8_t* U, const int8_t* V, const int8_t* W, int m, int n, int p, int r,
                          unsigned long long* bad, cudaStream_t stream);
 // Sets the launch attributes of a round kernel (call outside stream capture).
-cudaError_t prepare_round(int W, bool gm, const WarpLayout& L, int procs_per_cta);
+cudaError_t prepare_round(int W, bool gm, bool gs, const WarpLayout& L, int procs_per_cta);
 int max_smem_per_block();
 
 // Records the calling thread's error message (cse_last_error) and returns code.

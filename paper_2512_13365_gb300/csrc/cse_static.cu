@@ -73,7 +73,7 @@ extern "C" int cse_search_static(const cse_scheme* s, const cse_strategy_mix* mi
     else
         cse_opts_default(&opts);
     if (opts.share_interval < 1 || opts.share_permille > 1000 || opts.patience_rounds != 0 ||
-        (opts.flags & ~(uint32_t)(CSE_FLAG_GRAPH | CSE_FLAG_TRACE)) != 0 || opts.col_cap > CSE_MAX_COLS || opts.procs_per_cta > 4)
+        (opts.flags & ~(uint32_t)(CSE_FLAG_GRAPH | CSE_FLAG_TRACE | CSE_FLAG_GI_SHARED_COINS)) != 0 || opts.col_cap > CSE_MAX_COLS || opts.procs_per_cta > 4)
         return set_error(CSE_EINVAL, "invalid options (this entry point runs the step clock only: share_interval >= 1, "
                                      "patience_rounds 0)");
     const uint64_t wsum = (uint64_t)mix->w_gi + mix->w_ga + mix->w_gr + mix->w_wr + mix->w_mix + mix->w_g + mix->w_gp;
@@ -140,6 +140,7 @@ extern "C" int cse_search_static(const cse_scheme* s, const cse_strategy_mix* mi
     S.mat_pos = (const int32_t*)(b + o_pos);
     S.n_mats = nm;
     S.trace = (opts.flags & CSE_FLAG_TRACE) ? 1 : 0;
+    S.gi_shared = (opts.flags & CSE_FLAG_GI_SHARED_COINS) ? 1 : 0;
     struct Group { int W, begin, count, units, mmax; bool gm; WarpLayout L; int ppc; };
     std::vector<Group> groups;
     std::vector<DevMat> dm(nm);
@@ -181,7 +182,7 @@ extern "C" int cse_search_static(const cse_scheme* s, const cse_strategy_mix* mi
         g.ppc = opts.procs_per_cta ? (int)opts.procs_per_cta : 2;
         if (!g.gm)
             while (g.ppc > 1 && (long long)g.L.per_warp * g.ppc > smem_max) g.ppc--;
-        cudaError_t e = prepare_round(g.W, g.gm, g.L, g.ppc);
+        cudaError_t e = prepare_round(g.W, g.gm, S.gi_shared != 0, g.L, g.ppc);
         if (e != cudaSuccess) return set_error(CSE_ECUDA, std::string("kernel attributes: ") + cudaGetErrorString(e));
     }
 
@@ -207,7 +208,8 @@ extern "C" int cse_search_static(const cse_scheme* s, const cse_strategy_mix* mi
     const int rounds = (int)((budget + opts.share_interval - 1) / opts.share_interval);
     for (int rd = 0; rd < rounds && e == cudaSuccess; rd++) {
         for (const Group& g : groups) {
-            e = launch_round(g.W, g.gm, d_mats + g.begin, g.count, d_search, g.units, g.L, g.ppc, stream);
+            e = launch_round(g.W, g.gm, S.gi_shared != 0, d_mats + g.begin, g.count, d_search, g.units, g.L, g.ppc,
+                             stream);
             if (e != cudaSuccess) break;
         }
         if (e == cudaSuccess) e = launch_share(d_mats, d_search, 1, stream);

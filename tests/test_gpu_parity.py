@@ -23,10 +23,10 @@ def cse():
     return c
 
 
-def assert_parity(cse, s, ref=None, procs_per_cta=0, check_procs=True):
-    r = cse.search_obj(s, procs_per_cta=procs_per_cta, trace=True)
+def assert_parity(cse, s, ref=None, procs_per_cta=0, check_procs=True, gi_shared=False):
+    r = cse.search_obj(s, procs_per_cta=procs_per_cta, trace=True, gi_shared=gi_shared)
     if ref is None:
-        ref = O.search_obj(s, n_threads=8)
+        ref = O.search_obj(s, n_threads=8, flags=O.GI_SHARED_COINS if gi_shared else 0)
     assert r.costs == ref.cost
     assert r.lists == ref.lists
     if check_procs:
@@ -295,14 +295,14 @@ def test_trace_flag_only_changes_the_trajectory_record(cse):
 
 
 # ---------------------------------------------------------------- iteration mode
-def assert_parity_iterations(cse, s, patience, ref=None, r=None):
+def assert_parity_iterations(cse, s, patience, ref=None, r=None, gi_shared=False):
     """Iteration mode (share_interval = 0): s.budget is the maximum number of
     iterations."""
     if r is None:
-        r = cse.search_obj(s, patience=patience, trace=True)
+        r = cse.search_obj(s, patience=patience, trace=True, gi_shared=gi_shared)
     if ref is None:
         ref = O.search_iterations(s.mats, s.weights, s.n_proc, s.seed, s.budget, patience, s.permille, s.cap,
-                                  n_threads=8)
+                                  n_threads=8, flags=O.GI_SHARED_COINS if gi_shared else 0)
     assert r.costs == ref.cost
     assert r.lists == ref.lists
     for k in range(len(s.mats)):
@@ -360,3 +360,40 @@ def test_iteration_mode_batch_equals_alone(cse):
                           patience=5)
     for s, r in zip(ss, rs):
         assert_parity_iterations(cse, s, 5, r=r)
+
+
+# ---------------------------------------------------------------- shared gi coins
+@pytest.mark.parametrize("weights", [synth.GI_ONLY, synth.PAPER_WEIGHTS, (0, 0, 0, 0, 1, 0)])
+def test_shared_coins_config2_reduced(cse, weights):
+    s = synth.config2(n_proc=160, budget=120)
+    s.weights = weights
+    assert_parity(cse, s, gi_shared=True)
+
+
+@pytest.mark.parametrize("rows", [20, 64, 130, 256])
+def test_shared_coins_word_widths(cse, rows):
+    # m up to several hundred candidates: several 128-candidate coin blocks
+    mats = [synth.random_matrix(rows + 21, rows, 12, 3, 7, n_planted=10),
+            synth.random_matrix(rows + 22, 16, min(rows, 48), 3, 7, n_planted=5)]
+    s = synth.Search(f"gs{rows}", mats, synth.GI_ONLY, 29, 6, 48, 16, 400, 128)
+    assert_parity(cse, s, gi_shared=True)
+
+
+def test_shared_coins_from_hbm(cse):
+    s = synth.config4(n_proc=16, budget=24)
+    s.interval = 8
+    assert_parity(cse, s, gi_shared=True)
+
+
+def test_shared_coins_iteration_mode(cse):
+    s = synth.config2(n_proc=96, budget=40)
+    s.interval = 0
+    assert_parity_iterations(cse, s, 4, gi_shared=True)
+
+
+def test_shared_coins_change_results(cse):
+    s = synth.config2(n_proc=64, budget=64)
+    s.weights = synth.GI_ONLY
+    a = cse.search_obj(s, trace=True)
+    b = cse.search_obj(s, trace=True, gi_shared=True)
+    assert not np.array_equal(a.procs(0)["traj_hash"], b.procs(0)["traj_hash"])
