@@ -117,16 +117,24 @@ def whole_job_rate(units_per_rank: int, world: int, max_ms: float) -> float:
     return units_per_rank * world / (max_ms / 1000.0)
 
 
+def kernel_source_sha() -> str:
+    """sha256 prefix of the round kernel's sources (the engine and its unit)."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("cse_engine.cuh", "cse_kernels.cu"):
+        with open(os.path.join(ROOT, "paper_2512_13365_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def measured_traffic():
     """DRAM bytes per launch of the round kernel from the last ncu capture,
     if that capture was taken of the current kernel source; else None."""
-    import hashlib
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", "round_kernel_traffic.json")))
-        src = open(os.path.join(ROOT, "paper_2512_13365_gb300", "csrc", "cse_kernels.cu"), "rb").read()
+        sha = kernel_source_sha()
     except (OSError, ValueError):
         return None
-    sha = hashlib.sha256(src).hexdigest()[:16]
     return rec.get("dram_bytes_per_launch") if rec.get("kernel_source_sha256_prefix") == sha else None
 
 
@@ -155,7 +163,7 @@ def run_ours(args):
 
     def one():
         return cse.search(scheme, s.weights, s.n_proc, s.seed, s.budget, s.interval, s.permille, s.cap,
-                          stream=stream, procs_per_cta=args.ppc)
+                          stream=stream, procs_per_cta=args.ppc, gi_shared=args.gi_shared)
 
     for _ in range(args.warmup):
         r = one()
@@ -206,7 +214,7 @@ def run_ours(args):
         t0 = time.perf_counter()
         sc = cse.Scheme(s.mats)
         r = cse.search(sc, s.weights, s.n_proc, s.seed, s.budget, s.interval, s.permille, s.cap, stream=stream,
-                       procs_per_cta=args.ppc)
+                       procs_per_cta=args.ppc, gi_shared=args.gi_shared)
         lists = [r.fetch(k) for k in range(len(s.mats))]
         e2e_ms.append((time.perf_counter() - t0) * 1000.0)
         d2h = sum(4 * len(l) + 16 for l, _, _ in lists)
@@ -228,7 +236,8 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": s.name, "matrices": [list(m.shape) for m in s.mats], "n_processes": s.n_proc,
+        "config": {"workload": s.name + (" (shared gi coins)" if args.gi_shared else ""),
+                   "matrices": [list(m.shape) for m in s.mats], "n_processes": s.n_proc,
                    "step_budget": s.budget, "share_interval": s.interval, "share_permille": s.permille,
                    "col_cap": s.cap, "strategy_weights_gi_ga_gr_wr_mix_g": list(s.weights),
                    "process_steps_per_step": psteps, "l2": "flushed (256 MB write) between timed steps",
@@ -247,7 +256,7 @@ def run_ours(args):
         "gpu_launches": launches_per_search * args.steps,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(s, args.cpu_budget or s.budget)
+        line["cpu_baseline"] = cpu_baseline(s, args.cpu_budget or s.budget, args.gi_shared)
     if world > 1:
         torch.distributed.barrier()
         torch.distributed.destroy_process_group()
@@ -255,7 +264,7 @@ def run_ours(args):
         print(json.dumps(line))
 
 
-def cpu_baseline(s, budget):
+def cpu_baseline(s, budget, gi_shared=False):
     """The oracle, as it stands, on a bounded sample of the same workload:
     all processes, the first `budget` steps, on every host core."""
     from oracle import oracle as O
@@ -264,7 +273,7 @@ def cpu_baseline(s, budget):
     smp = copy.copy(s)
     smp.budget = budget
     t0 = time.perf_counter()
-    ref = O.search_obj(smp, n_threads=cores, digests=False)
+    ref = O.search_obj(smp, n_threads=cores, digests=False, flags=O.GI_SHARED_COINS if gi_shared else 0)
     dt = time.perf_counter() - t0
     out = {"value": smp.process_steps() / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
            "sample": f"{s.name}: all {s.n_proc} processes x {len(s.mats)} matrices, first {budget} of "
@@ -610,6 +619,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--budget", type=int, default=0, help="override the step budget (profiling runs)")
+    ap.add_argument("--gi-shared", action="store_true",
+                    help="Greedy-Intersections with shared coins (an option that changes results)")
     ap.add_argument("--out", default=os.path.join(ROOT, "gpurun_out"))
     args = ap.parse_args()
     os.makedirs(args.out, exist_ok=True)
