@@ -132,6 +132,7 @@ struct LaunchSet {
     void* d_params = nullptr;
     DevMat* d_mats = nullptr;
     DevSearch* d_searches = nullptr;
+    int* d_work = nullptr;  // one work counter per group (round kernel launch)
     bool gs = false;  // the searches use shared Greedy-Intersections coins
 };
 
@@ -395,6 +396,7 @@ static int build_launch(const std::vector<SearchDev*>& act, int ppc_req, const T
     for (int q = 0; q < nm; q++) ls->pos[fill[refs[q].search]++] = q;
     Carve cv;
     const size_t om = cv.take(sizeof(DevMat) * nm), os = cv.take(sizeof(DevSearch) * n), op = cv.take(4 * (size_t)nm);
+    const size_t ow = cv.take(4 * ls->groups.size());
     cudaError_t e = cudaMallocAsync(&ls->d_params, cv.off, stream);
     if (e != cudaSuccess) {
         ls->d_params = nullptr;
@@ -403,6 +405,7 @@ static int build_launch(const std::vector<SearchDev*>& act, int ppc_req, const T
     char* b = (char*)ls->d_params;
     ls->d_mats = (DevMat*)(b + om);
     ls->d_searches = (DevSearch*)(b + os);
+    ls->d_work = (int*)(b + ow);
     ls->searches.resize(n);
     for (int i = 0; i < n; i++) {
         ls->searches[i] = act[i]->search;
@@ -413,6 +416,7 @@ static int build_launch(const std::vector<SearchDev*>& act, int ppc_req, const T
         e = cudaMemcpyAsync(ls->d_searches, ls->searches.data(), sizeof(DevSearch) * n, cudaMemcpyHostToDevice,
                             stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(b + op, ls->pos.data(), 4 * (size_t)nm, cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ls->d_work, 0, 4 * ls->groups.size(), stream);
     if (e != cudaSuccess) return fail(CSE_ECUDA, std::string("parameter upload: ") + cudaGetErrorString(e));
     return CSE_OK;
 }
@@ -428,8 +432,8 @@ static cudaError_t enqueue_round(const LaunchSet& ls, cudaStream_t st, const std
         for (size_t gi = 0; gi < ng; gi++) {
             const auto& g = ls.groups[gi];
             cudaStreamWaitEvent((*aux)[gi], (*fork)[0], 0);
-            e = launch_round(g.W, g.gm, ls.gs, ls.d_mats + g.begin, g.count, ls.d_searches, g.units, g.L, g.ppc,
-                             (*aux)[gi]);
+            e = launch_round(g.W, g.gm, ls.gs, ls.d_mats + g.begin, g.count, ls.d_searches, g.units,
+                             ls.d_work + gi, g.L, g.ppc, (*aux)[gi]);
             if (e != cudaSuccess) return e;
             cudaEventRecord((*fork)[gi + 1], (*aux)[gi]);
             cudaStreamWaitEvent(st, (*fork)[gi + 1], 0);
@@ -438,12 +442,13 @@ static cudaError_t enqueue_round(const LaunchSet& ls, cudaStream_t st, const std
         for (size_t gi = 0; gi < ng; gi++) {
             const auto& g = ls.groups[gi];
             if (group_ev) cudaEventRecord(group_ev[2 * gi], st);
-            e = launch_round(g.W, g.gm, ls.gs, ls.d_mats + g.begin, g.count, ls.d_searches, g.units, g.L, g.ppc, st);
+            e = launch_round(g.W, g.gm, ls.gs, ls.d_mats + g.begin, g.count, ls.d_searches, g.units,
+                             ls.d_work + gi, g.L, g.ppc, st);
             if (e != cudaSuccess) return e;
             if (group_ev) cudaEventRecord(group_ev[2 * gi + 1], st);
         }
     }
-    return launch_share(ls.d_mats, ls.d_searches, (int)ls.searches.size(), st);
+    return launch_share(ls.d_mats, ls.d_searches, (int)ls.searches.size(), ls.d_work, (int)ng, st);
 }
 
 // Builds and enqueues n independent searches as one static launch sequence.

@@ -1007,13 +1007,9 @@ struct Engine {
 // an SM between enough warps): the arrays stay in the state region itself and
 // the engine works on them through the L1/L2 caches.
 template <int W, bool GM, bool GS>
-__global__ void __launch_bounds__(128, CSE_MIN_BLOCKS) round_kernel(const DevMat* __restrict__ mats, int n_mats,
-                                                       const DevSearch* __restrict__ searches,
-                                                       int total_units, const __grid_constant__ WarpLayout L) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int unit = blockIdx.x * (blockDim.x >> 5) + warp;
-    if (unit >= total_units) return;
+__device__ __forceinline__ void run_unit(const DevMat* __restrict__ mats, int n_mats,
+                                         const DevSearch* __restrict__ searches, const WarpLayout& L,
+                                         unsigned char* smem, int warp, int lane, int unit) {
     int mi = 0;
     while (mi + 1 < n_mats && mats[mi + 1].unit_base <= unit) mi++;
     const DevMat* M = &mats[mi];
@@ -1151,42 +1147,72 @@ __global__ void __launch_bounds__(128, CSE_MIN_BLOCKS) round_kernel(const DevMat
     }
 }
 
+// One launch = one round of every process of a class of matrices.  The grid
+// holds as many CTAs as fit on the GPU at once, and every warp takes the next
+// process from the launch's work counter until none is left: a warp whose
+// process finished early starts another at once instead of idling until its
+// CTA's last warp is done.  The share kernel resets the counter for the next
+// round.
+template <int W, bool GM, bool GS>
+__global__ void __launch_bounds__(128, CSE_MIN_BLOCKS) round_kernel(const DevMat* __restrict__ mats, int n_mats,
+                                                       const DevSearch* __restrict__ searches,
+                                                       int total_units, int* __restrict__ work,
+                                                       const __grid_constant__ WarpLayout L) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (;;) {
+        int unit = 0;
+        if (lane == 0) unit = atomicAdd(work, 1);
+        unit = __shfl_sync(FULL_MASK, unit, 0);
+        if (unit >= total_units) return;
+        run_unit<W, GM, GS>(mats, n_mats, searches, L, smem, warp, lane, unit);
+        __syncwarp();
+    }
+}
+
 
 // Launchers of the round kernels of one engine variant (GS: shared coins).
 template <int W, bool GM, bool GS>
 static cudaError_t launch_round_w(const DevMat* mats, int n_mats, const DevSearch* searches, int total_units,
-                                  const WarpLayout& L, int ppc, cudaStream_t stream, bool prepare_only) {
+                                  int* work, const WarpLayout& L, int ppc, cudaStream_t stream, bool prepare_only) {
     const size_t smem = GM ? 0 : (size_t)L.per_warp * ppc;
     if (prepare_only)
         return cudaFuncSetAttribute(round_kernel<W, GM, GS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)smem);
-    const int grid = (total_units + ppc - 1) / ppc;
-    round_kernel<W, GM, GS><<<grid, 32 * ppc, smem, stream>>>(mats, n_mats, searches, total_units, L);
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, round_kernel<W, GM, GS>, 32 * ppc, smem);
+    if (e != cudaSuccess) return e;
+    const long long need = (total_units + ppc - 1) / ppc;
+    const int grid = (int)std::max(1LL, std::min(need, (long long)std::max(sms, 1) * std::max(per_sm, 1)));
+    round_kernel<W, GM, GS><<<grid, 32 * ppc, smem, stream>>>(mats, n_mats, searches, total_units, work, L);
     return cudaGetLastError();
 }
 
 template <bool GM, bool GS>
 static cudaError_t launch_round_gm(int W, const DevMat* mats, int n_mats, const DevSearch* searches,
-                                   int total_units, const WarpLayout& L, int ppc, cudaStream_t stream, bool prep) {
+                                   int total_units, int* work, const WarpLayout& L, int ppc, cudaStream_t stream,
+                                   bool prep) {
     switch (W) {
-        case 1: return launch_round_w<1, GM, GS>(mats, n_mats, searches, total_units, L, ppc, stream, prep);
-        case 2: return launch_round_w<2, GM, GS>(mats, n_mats, searches, total_units, L, ppc, stream, prep);
-        case 3: return launch_round_w<3, GM, GS>(mats, n_mats, searches, total_units, L, ppc, stream, prep);
-        case 4: return launch_round_w<4, GM, GS>(mats, n_mats, searches, total_units, L, ppc, stream, prep);
-        case 5: return launch_round_w<5, GM, GS>(mats, n_mats, searches, total_units, L, ppc, stream, prep);
-        case 6: return launch_round_w<6, GM, GS>(mats, n_mats, searches, total_units, L, ppc, stream, prep);
-        case 7: return launch_round_w<7, GM, GS>(mats, n_mats, searches, total_units, L, ppc, stream, prep);
-        case 8: return launch_round_w<8, GM, GS>(mats, n_mats, searches, total_units, L, ppc, stream, prep);
+        case 1: return launch_round_w<1, GM, GS>(mats, n_mats, searches, total_units, work, L, ppc, stream, prep);
+        case 2: return launch_round_w<2, GM, GS>(mats, n_mats, searches, total_units, work, L, ppc, stream, prep);
+        case 3: return launch_round_w<3, GM, GS>(mats, n_mats, searches, total_units, work, L, ppc, stream, prep);
+        case 4: return launch_round_w<4, GM, GS>(mats, n_mats, searches, total_units, work, L, ppc, stream, prep);
+        case 5: return launch_round_w<5, GM, GS>(mats, n_mats, searches, total_units, work, L, ppc, stream, prep);
+        case 6: return launch_round_w<6, GM, GS>(mats, n_mats, searches, total_units, work, L, ppc, stream, prep);
+        case 7: return launch_round_w<7, GM, GS>(mats, n_mats, searches, total_units, work, L, ppc, stream, prep);
+        case 8: return launch_round_w<8, GM, GS>(mats, n_mats, searches, total_units, work, L, ppc, stream, prep);
         default: return cudaErrorInvalidValue;
     }
 }
 
 template <bool GS>
 static cudaError_t launch_round_variant(int W, bool gm, const DevMat* mats, int n_mats, const DevSearch* searches,
-                                        int total_units, const WarpLayout& L, int ppc, cudaStream_t stream,
-                                        bool prep) {
-    return gm ? launch_round_gm<true, GS>(W, mats, n_mats, searches, total_units, L, ppc, stream, prep)
-              : launch_round_gm<false, GS>(W, mats, n_mats, searches, total_units, L, ppc, stream, prep);
+                                        int total_units, int* work, const WarpLayout& L, int ppc,
+                                        cudaStream_t stream, bool prep) {
+    return gm ? launch_round_gm<true, GS>(W, mats, n_mats, searches, total_units, work, L, ppc, stream, prep)
+              : launch_round_gm<false, GS>(W, mats, n_mats, searches, total_units, work, L, ppc, stream, prep);
 }
 
 }  // namespace cse

@@ -108,13 +108,15 @@ constexpr int kSmemPerWarpLimit = 24 * 1024;
 cudaError_t launch_ingest(const int8_t* raw, int rows, int nx, int W, uint2* pn0, uint32_t* cand0,
                           int32_t* meta0, int mmax, cudaStream_t stream);
 // gs: the engine variant with shared Greedy-Intersections coins.
+// work: the launch's work counter (zero at launch; the share kernel resets it).
 cudaError_t launch_round(int W, bool gm, bool gs, const DevMat* mats, int n_mats, const DevSearch* searches,
-                         int total_units, const WarpLayout& L, int procs_per_cta,
+                         int total_units, int* work, const WarpLayout& L, int procs_per_cta,
                          cudaStream_t stream);
 cudaError_t launch_round_gs(int W, bool gm, const DevMat* mats, int n_mats, const DevSearch* searches,
-                            int total_units, const WarpLayout& L, int procs_per_cta, cudaStream_t stream,
+                            int total_units, int* work, const WarpLayout& L, int procs_per_cta, cudaStream_t stream,
                             bool prepare_only);
-cudaError_t launch_share(const DevMat* mats, const DevSearch* searches, int n_searches,
+// Also zeroes the n_work (<= 128) work counters of the round kernels.
+cudaError_t launch_share(const DevMat* mats, const DevSearch* searches, int n_searches, int* work, int n_work,
                          cudaStream_t stream);
 cudaError_t launch_brent(const int8_t* U, const int8_t* V, const int8_t* W, int m, int n, int p, int r,
                          unsigned long long* bad, cudaStream_t stream);

@@ -72,7 +72,10 @@ __global__ void ingest_kernel(const int8_t* __restrict__ raw, int rows, int nx, 
 // search, one warp per matrix.  In iteration mode every round is a boundary,
 // followed by the convergence test on the sum of the matrices' best costs
 // (Section 4: unchanged for `patience` iterations ends the search).
-__global__ void share_kernel(const DevMat* __restrict__ mats, const DevSearch* __restrict__ searches) {
+__global__ void share_kernel(const DevMat* __restrict__ mats, const DevSearch* __restrict__ searches,
+                             int* __restrict__ work, int n_work) {
+    // the round kernels' work counters, for the next round
+    if (blockIdx.x == 0 && (int)threadIdx.x < n_work) work[threadIdx.x] = 0;
     const DevSearch* S = &searches[blockIdx.x];
     const bool iter_mode = S->interval == 0;
     const int c0 = *S->clock;
@@ -222,19 +225,20 @@ cudaError_t launch_ingest(const int8_t* raw, int rows, int nx, int W, uint2* pn0
 }
 
 cudaError_t launch_round(int W, bool gm, bool gs, const DevMat* mats, int n_mats, const DevSearch* searches,
-                         int total_units, const WarpLayout& L, int ppc, cudaStream_t stream) {
-    return gs ? launch_round_gs(W, gm, mats, n_mats, searches, total_units, L, ppc, stream, false)
-              : launch_round_variant<false>(W, gm, mats, n_mats, searches, total_units, L, ppc, stream, false);
+                         int total_units, int* work, const WarpLayout& L, int ppc, cudaStream_t stream) {
+    return gs ? launch_round_gs(W, gm, mats, n_mats, searches, total_units, work, L, ppc, stream, false)
+              : launch_round_variant<false>(W, gm, mats, n_mats, searches, total_units, work, L, ppc, stream, false);
 }
 
 cudaError_t prepare_round(int W, bool gm, bool gs, const WarpLayout& L, int ppc) {
-    return gs ? launch_round_gs(W, gm, nullptr, 0, nullptr, 0, L, ppc, nullptr, true)
-              : launch_round_variant<false>(W, gm, nullptr, 0, nullptr, 0, L, ppc, nullptr, true);
+    return gs ? launch_round_gs(W, gm, nullptr, 0, nullptr, 0, nullptr, L, ppc, nullptr, true)
+              : launch_round_variant<false>(W, gm, nullptr, 0, nullptr, 0, nullptr, L, ppc, nullptr, true);
 }
 
-cudaError_t launch_share(const DevMat* mats, const DevSearch* searches, int n_searches,
+cudaError_t launch_share(const DevMat* mats, const DevSearch* searches, int n_searches, int* work, int n_work,
                          cudaStream_t stream) {
-    share_kernel<<<n_searches, 128, 0, stream>>>(mats, searches);
+    if (n_work > 128) return cudaErrorInvalidValue;
+    share_kernel<<<n_searches, 128, 0, stream>>>(mats, searches, work, n_work);
     return cudaGetLastError();
 }
 

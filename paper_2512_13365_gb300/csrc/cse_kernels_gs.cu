@@ -8,8 +8,10 @@
 namespace cse {
 
 cudaError_t launch_round_gs(int W, bool gm, const DevMat* mats, int n_mats, const DevSearch* searches,
-                            int total_units, const WarpLayout& L, int ppc, cudaStream_t stream, bool prepare_only) {
-    return launch_round_variant<true>(W, gm, mats, n_mats, searches, total_units, L, ppc, stream, prepare_only);
+                            int total_units, int* work, const WarpLayout& L, int ppc, cudaStream_t stream,
+                            bool prepare_only) {
+    return launch_round_variant<true>(W, gm, mats, n_mats, searches, total_units, work, L, ppc, stream,
+                                      prepare_only);
 }
 
 }  // namespace cse

@@ -106,6 +106,7 @@ extern "C" int cse_search_static(const cse_scheme* s, const cse_strategy_mix* mi
     const size_t o_clock = take(off, 4), o_status = take(off, 4);
     const size_t o_mats = take(off, sizeof(DevMat) * nm), o_search = take(off, sizeof(DevSearch));
     const size_t o_pos = take(off, 4 * (size_t)nm);
+    const size_t o_work = take(off, 4 * (size_t)nm);  // one round-kernel work counter per group (<= nm groups)
     if (off > (size_t)CSE_STATIC_SCRATCH_BYTES)
         return set_error(CSE_ENOMEM, "this search needs " + std::to_string(off) +
                                          " bytes of scratch; the static scratch holds " +
@@ -202,17 +203,20 @@ extern "C" int cse_search_static(const cse_scheme* s, const cse_strategy_mix* mi
     }
     if (e == cudaSuccess) e = cudaMemsetAsync(b + o_clock, 0, 4, stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(b + o_status, 0, 4, stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b + o_work, 0, 4 * (size_t)nm, stream);
     if (e != cudaSuccess) return set_error(CSE_ECUDA, std::string("scratch set-up: ") + cudaGetErrorString(e));
 
     // ---- the rounds
     const int rounds = (int)((budget + opts.share_interval - 1) / opts.share_interval);
     for (int rd = 0; rd < rounds && e == cudaSuccess; rd++) {
-        for (const Group& g : groups) {
-            e = launch_round(g.W, g.gm, S.gi_shared != 0, d_mats + g.begin, g.count, d_search, g.units, g.L, g.ppc,
-                             stream);
+        int* work = (int*)(b + o_work);
+        for (size_t gi = 0; gi < groups.size(); gi++) {
+            const Group& g = groups[gi];
+            e = launch_round(g.W, g.gm, S.gi_shared != 0, d_mats + g.begin, g.count, d_search, g.units, work + gi,
+                             g.L, g.ppc, stream);
             if (e != cudaSuccess) break;
         }
-        if (e == cudaSuccess) e = launch_share(d_mats, d_search, 1, stream);
+        if (e == cudaSuccess) e = launch_share(d_mats, d_search, 1, work, (int)groups.size(), stream);
     }
     if (e != cudaSuccess) return set_error(CSE_ECUDA, std::string("launch: ") + cudaGetErrorString(e));
 
