@@ -281,9 +281,12 @@ void cse_scheme_free(cse_scheme* s);
  * Requests (a scheme and its search parameters) queue in FIFO order.  At
  * every round boundary the worker admits queued requests while (a) the
  * device memory of all active searches stays within hbm_budget_bytes (0 = no
- * limit) and (b) their processes (all matrices) stay within
+ * limit), (b) their processes (all matrices) stay within
  * max_active_processes (0 = eight waves of one process per resident warp,
- * 8 x 32 x SMs); a request that exceeds a limit alone runs alone.  Then it
+ * 8 x 32 x SMs) and (c) the shared-memory footprint of their process pools
+ * (each process of a matrix on the shared-memory path holds one slice) stays
+ * within eight waves of the GPU's shared memory (8 x SMs x per-SM capacity);
+ * a request that exceeds a limit alone runs alone.  Then it
  * runs one round (one kernel per class of matrices over every active search,
  * then the share kernel).  Admitted searches run concurrently with those
  * already on the device and leave as soon as their step budget is done.  Each

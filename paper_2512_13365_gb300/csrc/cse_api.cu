@@ -644,6 +644,7 @@ struct Request {
     int64_t budget = 0;
     size_t bytes = 0;
     int64_t units = 0;
+    uint64_t smem = 0;  // shared-memory footprint of its process pools
     std::chrono::steady_clock::time_point t_submit;
     SearchDev* sd = nullptr;
     cse_result* res = nullptr;
@@ -657,6 +658,8 @@ struct cse_server {
     uint64_t hbm_budget = 0;
     int64_t max_units = 0;     // cap on the processes (all matrices) of active searches
     int64_t active_units = 0;
+    uint64_t smem_budget = 0;  // cap on the shared-memory footprint of active searches
+    uint64_t used_smem = 0;
     int device = 0;
     cudaStream_t stream = nullptr;
     std::thread worker;
@@ -1139,11 +1142,13 @@ static void server_loop(cse_server* sv) {
             while (!sv->pending.empty()) {
                 Request* q = sv->pending.front();
                 if (!sv->active.empty() && (sv->used_bytes + q->bytes > sv->hbm_budget ||
-                                            sv->active_units + q->units > sv->max_units))
+                                            sv->active_units + q->units > sv->max_units ||
+                                            sv->used_smem + q->smem > sv->smem_budget))
                     break;
                 sv->pending.pop_front();
                 sv->used_bytes += q->bytes;
                 sv->active_units += q->units;
+                sv->used_smem += q->smem;
                 admitted.push_back(q);
             }
         }
@@ -1207,6 +1212,7 @@ static void server_loop(cse_server* sv) {
         for (Request* q : finished) {
             sv->used_bytes -= q->bytes;
             sv->active_units -= q->units;
+            sv->used_smem -= q->smem;
             server_finish(sv, q);
         }
         if (!finished.empty()) sv->cv_done.notify_all();
@@ -1237,6 +1243,9 @@ int cse_server_create(const cse_opts* opts_in, uint64_t hbm_budget_bytes, int64_
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, sv->device);
     // default: eight waves of one process per resident warp (32 per SM)
     sv->max_units = max_active_processes > 0 ? max_active_processes : (int64_t)8 * 32 * std::max(sms, 1);
+    int smem_sm = 0;
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, sv->device);
+    sv->smem_budget = (uint64_t)8 * (uint64_t)std::max(sms, 1) * (uint64_t)std::max(smem_sm, 1);
     cudaError_t e = cudaStreamCreateWithFlags(&sv->stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
         delete sv;
@@ -1264,6 +1273,8 @@ int cse_server_submit(cse_server* sv, const cse_scheme* s, const cse_strategy_mi
     q->budget = step_budget;
     q->bytes = tmp.bytes;
     q->units = (int64_t)tmp.n_mats * tmp.n_proc;
+    for (int k = 0; k < tmp.n_mats; k++)  // a slice per process of every shared-memory matrix
+        if (!tmp.gm[k]) q->smem += (uint64_t)tmp.mats[k].gml.per_warp * (uint64_t)n_proc;
     q->t_submit = std::chrono::steady_clock::now();
     std::lock_guard<std::mutex> lk(sv->mu);
     if (sv->stop) {
