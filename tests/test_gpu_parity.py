@@ -397,3 +397,38 @@ def test_shared_coins_change_results(cse):
     a = cse.search_obj(s, trace=True)
     b = cse.search_obj(s, trace=True, gi_shared=True)
     assert not np.array_equal(a.procs(0)["traj_hash"], b.procs(0)["traj_hash"])
+
+
+# ---------------------------------------------------------------- limits
+def test_largest_process_count_sampled(cse):
+    """2^20 processes per matrix (the largest the ABI accepts) on the
+    (3,3,3:23) shape, 16 steps (before the first sharing boundary), sampled
+    processes replayed by the oracle."""
+    s = synth.config2(n_proc=1 << 20, budget=16)
+    r = cse.search_obj(s, trace=True)
+    sample = [0, 1, 2, 65535, 524287, 999999, (1 << 20) - 1]
+    ref = O.search_obj(s, n_threads=8, subset=sample)
+    for k in range(3):
+        got, exp = r.procs(k)[sample], ref.digests[k][sample]
+        for f in FIELDS:
+            assert np.array_equal(got[f], exp[f]), (k, f)
+    steps, _, _ = r.counters()
+    assert steps == 3 * (1 << 20) * 16
+    r.free()
+
+
+def test_largest_shapes(cse):
+    """Sixteen matrices (the most a scheme may hold), among them 256 rows
+    (8 words per column) and 511 columns with the 512-column cap, plus
+    single-row and single-column-pair matrices; sparse rows keep the oracle
+    fast."""
+    mats = [synth.random_matrix(3000, 256, 24, 2, 3, n_planted=6),
+            synth.random_matrix(3001, 12, 511, 2, 3, n_planted=4),
+            synth.random_matrix(3002, 1, 6, 2, 6),
+            np.array([[1, 1], [1, 1], [-1, -1]], np.int8)]
+    mats += [synth.random_matrix(3003 + k, 8 + 3 * k, 6 + k, 2, 4, n_planted=2) for k in range(12)]
+    s = synth.Search("limits", mats, synth.PAPER_WEIGHTS, 9, 4, 24, 8, 400, 512)
+    ref = assert_parity(cse, s)
+    assert len(ref.cost) == 16
+    # the 511-column matrix has room for one substitution only
+    assert ref.length[1] <= 1
