@@ -1176,9 +1176,15 @@ template <int W, bool GM, bool GS>
 static cudaError_t launch_round_w(const DevMat* mats, int n_mats, const DevSearch* searches, int total_units,
                                   int* work, const WarpLayout& L, int ppc, cudaStream_t stream, bool prepare_only) {
     const size_t smem = GM ? 0 : (size_t)L.per_warp * ppc;
-    if (prepare_only)
+    if (prepare_only) {
+        if (GM) {  // the HBM path uses no shared memory: give the SM's unified cache to L1
+            cudaError_t e = cudaFuncSetAttribute(round_kernel<W, GM, GS>,
+                                                 cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+            if (e != cudaSuccess) return e;
+        }
         return cudaFuncSetAttribute(round_kernel<W, GM, GS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)smem);
+    }
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
