@@ -273,6 +273,29 @@ int cse_result_hybrid(const cse_result* const* results, int32_t n_results, int32
  * a batch) and the number of searches that shared it. */
 int cse_result_launches(const cse_result* r, int32_t* kernels, int32_t* searches_in_launch);
 
+/* ---- Checkpoint / resume ------------------------------------------------
+ * The paper's tool keeps no checkpoints; these make long searches
+ * restartable.  Every draw is keyed by (seed, process, step), so a search of
+ * B1 + B2 steps that is checkpointed after B1 and resumed for B2 more gives
+ * exactly the results (and per-process records) of one search of B1 + B2
+ * steps.
+ *
+ * cse_checkpoint_size: bytes of the checkpoint of r (a header, then r's
+ * device state byte for byte).
+ * cse_checkpoint_save: waits for r and writes its checkpoint to host_buf
+ * (bytes >= the size).  With the step clock the step budget must be a
+ * multiple of share_interval (a sharing boundary); in iteration mode any
+ * finished search qualifies.
+ * cse_search_resume: starts a search from a checkpoint of a search of the
+ * scheme s (same matrix shapes) that runs more_steps further steps
+ * (iterations in iteration mode).  The strategy mix, seed, process count and
+ * the options that change results come from the checkpoint; of launch_opts
+ * (may be NULL) only procs_per_cta is used.  Like cse_search otherwise. */
+int cse_checkpoint_size(const cse_result* r, size_t* bytes);
+int cse_checkpoint_save(const cse_result* r, void* host_buf, size_t bytes);
+int cse_search_resume(const cse_scheme* s, const void* checkpoint, size_t bytes, int64_t more_steps,
+                      const cse_opts* launch_opts, void* cuda_stream, cse_result** out);
+
 void cse_result_free(cse_result* r);
 void cse_scheme_free(cse_scheme* s);
 

@@ -55,7 +55,8 @@ _lib = None
 # every symbol include/cse.h declares
 EXPORTS = ["cse_opts_default", "cse_scheme_load", "cse_scheme_load_uvw", "cse_scheme_shape", "cse_search",
            "cse_search_batch", "cse_autotune", "cse_tune_interval", "cse_result_fetch", "cse_result_procs", "cse_result_counters", "cse_result_timing",
-           "cse_result_iterations", "cse_result_hybrid", "cse_brent_check", "cse_result_launches",
+           "cse_result_iterations", "cse_result_hybrid", "cse_brent_check", "cse_checkpoint_size",
+           "cse_checkpoint_save", "cse_search_resume", "cse_result_launches",
            "cse_result_free", "cse_scheme_free", "cse_last_error",
            "cse_server_create", "cse_server_submit", "cse_server_wait", "cse_server_stats", "cse_server_free",
            "cse_search_static"]
@@ -90,6 +91,9 @@ def lib() -> ctypes.CDLL:
     L.cse_result_iterations.argtypes = [vp, pi32, pi32, pi64]
     L.cse_result_hybrid.argtypes = [ctypes.POINTER(vp), i32, pi32, pi64]
     L.cse_brent_check.argtypes = [i32, i32, i32, i32, vp, vp, vp, pi64]
+    L.cse_checkpoint_size.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
+    L.cse_checkpoint_save.argtypes = [vp, vp, ctypes.c_size_t]
+    L.cse_search_resume.argtypes = [vp, vp, ctypes.c_size_t, i64, ctypes.POINTER(Opts), vp, ctypes.POINTER(vp)]
     batch_args = [i32, ctypes.POINTER(vp), ctypes.POINTER(Mix), pi32, ctypes.POINTER(u64), pi64, ctypes.POINTER(Opts)]
     L.cse_autotune.argtypes = batch_args + [i32, vp, ctypes.POINTER(TuneEntry), i32, pi32]
     L.cse_tune_interval.argtypes = batch_args + [ctypes.POINTER(ctypes.c_uint32), i32, i32, vp,
@@ -221,6 +225,14 @@ class Result:
         _check(lib().cse_result_iterations(self.handle, ctypes.byref(it), ctypes.byref(cv), ctypes.byref(tot)))
         return it.value, bool(cv.value), tot.value
 
+    def checkpoint(self) -> bytes:
+        """cse_checkpoint_save: the finished search's checkpoint as bytes."""
+        n = ctypes.c_size_t()
+        _check(lib().cse_checkpoint_size(self.handle, ctypes.byref(n)))
+        buf = ctypes.create_string_buffer(n.value)
+        _check(lib().cse_checkpoint_save(self.handle, buf, n.value))
+        return buf.raw
+
     def launches(self) -> Tuple[int, int]:
         """(kernel launches of the launch sequence, searches that shared it)."""
         k, n = ctypes.c_int32(), ctypes.c_int32()
@@ -289,6 +301,21 @@ def search(scheme: Scheme, weights, n_proc: int, seed: int, budget: int, interva
     _check(lib().cse_search(scheme.handle, ctypes.byref(mix), n_proc, seed, budget, ctypes.byref(opts),
                             _stream_ptr(stream), ctypes.byref(h)))
     return Result(h, len(scheme.mats), n_proc, cap)
+
+
+def resume(scheme: Scheme, checkpoint: bytes, more_steps: int, stream=None, procs_per_cta: int = 0) -> Result:
+    """cse_search_resume: continue a checkpointed search for more_steps steps."""
+    import struct
+    cap, = struct.unpack_from("<I", checkpoint, 20)       # header fields (cse_api.cu): col_cap ...
+    n_proc, = struct.unpack_from("<i", checkpoint, 36)    # ... and the process count
+    opts = make_opts(procs_per_cta=procs_per_cta)
+    buf = ctypes.create_string_buffer(checkpoint, len(checkpoint))
+    h = ctypes.c_void_p()
+    _check(lib().cse_search_resume(scheme.handle, buf, len(checkpoint), more_steps, ctypes.byref(opts),
+                                   _stream_ptr(stream), ctypes.byref(h)))
+    r = Result(h, len(scheme.mats), n_proc, cap)
+    r._scheme = scheme
+    return r
 
 
 def search_obj(s, scheme: Optional[Scheme] = None, **kw) -> Result:

@@ -112,6 +112,30 @@ struct SearchDev {
     std::vector<char> gm;       // matrix k runs on its HBM state region
     DevSearch search{};
     int rows[CSE_MAX_MATS], cols[CSE_MAX_MATS];
+    // the parameters it was created with (checkpoints record them)
+    cse_strategy_mix mix{};
+    cse_opts opts{};
+    uint64_t seed = 0;
+};
+
+// A checkpoint: this header, then the search's device block byte for byte.
+struct CkptHeader {
+    uint64_t magic;
+    uint32_t version, interval, permille, cap, patience, flags;
+    int32_t n_mats, n_proc;
+    int32_t rows[CSE_MAX_MATS], cols[CSE_MAX_MATS];
+    uint64_t seed;
+    cse_strategy_mix mix;
+    int64_t done;     // steps (iterations in iteration mode) already run
+    uint64_t bytes;   // size of the device block that follows
+};
+constexpr uint64_t kCkptMagic = 0x3154504B43455343ull;  // "CSECKPT1" as little-endian bytes
+constexpr uint32_t kCkptVersion = 1;
+
+// Resume of one search from a checkpoint (run_batch).
+struct Resume {
+    const CkptHeader* hdr;
+    const void* block;
 };
 
 // Kernel parameters of one launch over a set of searches: matrices grouped
@@ -267,6 +291,9 @@ static int search_create(const cse_scheme* s, const cse_strategy_mix* mix, int n
         return rc;
     }
     sd->stream = stream;
+    sd->mix = *mix;
+    sd->opts = opts;
+    sd->seed = seed;
     set_pool_threshold_once();
     cudaError_t e = cudaMallocAsync(&sd->d_block, sd->bytes, stream);
     if (e != cudaSuccess) {
@@ -457,7 +484,7 @@ static cudaError_t enqueue_round(const LaunchSet& ls, cudaStream_t st, const std
 static int run_batch(int n, const cse_scheme* const* schemes, const cse_strategy_mix* mixes,
                      const int32_t* n_procs, const uint64_t* seeds, const int64_t* budgets,
                      const cse_opts* opts_in, void* cuda_stream, cse_result** outs,
-                     const Trial* trial = nullptr) {
+                     const Trial* trial = nullptr, const Resume* resume = nullptr) {
     if (!outs) return fail(CSE_EINVAL, "out is NULL");
     if (n < 1 || !schemes || !mixes || !n_procs || !seeds || !budgets)
         return fail(CSE_EINVAL, "n_searches must be >= 1 with non-NULL arrays");
@@ -487,6 +514,20 @@ static int run_batch(int n, const cse_scheme* const* schemes, const cse_strategy
             drop();
             return rc;
         }
+    }
+    if (resume) {  // one search: its device block comes from the checkpoint
+        SearchDev* sd = sds[0];
+        if (resume->hdr->bytes != sd->bytes) {
+            drop();
+            return fail(CSE_EINVAL, "checkpoint does not match this scheme and these options");
+        }
+        cudaError_t e = cudaMemcpyAsync(sd->d_block, resume->block, sd->bytes, cudaMemcpyHostToDevice, stream);
+        if (e != cudaSuccess) {
+            drop();
+            return fail(CSE_ECUDA, std::string("checkpoint upload: ") + cudaGetErrorString(e));
+        }
+        const int64_t more = sd->budget - resume->hdr->done;
+        sd->rounds = iter_mode ? (int)more : (int)((more + opts.share_interval - 1) / opts.share_interval);
     }
     Batch* B = new (std::nothrow) Batch();
     if (!B) {
@@ -826,6 +867,75 @@ int cse_search(const cse_scheme* s, const cse_strategy_mix* mix, int32_t n_proc,
     *out = nullptr;
     if (!s || !mix) return fail(CSE_EINVAL, "NULL scheme or strategy mix");
     return run_batch(1, &s, mix, &n_proc, &seed, &budget, opts, cuda_stream, out);
+}
+
+static int wait_result(const cse_result* r);
+
+int cse_checkpoint_size(const cse_result* r, size_t* bytes) {
+    if (!r || !r->sd || !bytes) return fail(CSE_EINVAL, "NULL result or output");
+    *bytes = sizeof(CkptHeader) + r->sd->bytes;
+    return CSE_OK;
+}
+
+int cse_checkpoint_save(const cse_result* r, void* host_buf, size_t bytes) {
+    if (!r || !r->sd || !host_buf) return fail(CSE_EINVAL, "NULL result or buffer");
+    const SearchDev* sd = r->sd;
+    if (bytes < sizeof(CkptHeader) + sd->bytes) return fail(CSE_EINVAL, "checkpoint buffer too small");
+    const uint32_t iv = sd->opts.share_interval;
+    if (iv != 0 && sd->budget % iv != 0)
+        return fail(CSE_EINVAL, "a checkpoint needs a step budget that is a multiple of share_interval");
+    int rc = wait_result(r);
+    if (rc) return rc;
+    CkptHeader h{};
+    h.magic = kCkptMagic;
+    h.version = kCkptVersion;
+    h.interval = iv;
+    h.permille = sd->opts.share_permille;
+    h.cap = sd->opts.col_cap;
+    h.patience = sd->opts.patience_rounds;
+    h.flags = sd->opts.flags & (CSE_FLAG_GI_SHARED_COINS | CSE_FLAG_TRACE);
+    h.n_mats = sd->n_mats;
+    h.n_proc = sd->n_proc;
+    for (int k = 0; k < sd->n_mats; k++) {
+        h.rows[k] = sd->rows[k];
+        h.cols[k] = sd->cols[k];
+    }
+    h.seed = sd->seed;
+    h.mix = sd->mix;
+    h.done = sd->budget;
+    h.bytes = sd->bytes;
+    std::memcpy(host_buf, &h, sizeof h);
+    CUDA_TRY(cudaMemcpy((char*)host_buf + sizeof h, sd->d_block, sd->bytes, cudaMemcpyDeviceToHost));
+    return CSE_OK;
+}
+
+int cse_search_resume(const cse_scheme* s, const void* ckpt, size_t bytes, int64_t more_steps,
+                      const cse_opts* launch_opts, void* cuda_stream, cse_result** out) {
+    if (!out) return fail(CSE_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!s || !ckpt || bytes < sizeof(CkptHeader)) return fail(CSE_EINVAL, "NULL scheme or short checkpoint");
+    CkptHeader h;
+    std::memcpy(&h, ckpt, sizeof h);
+    if (h.magic != kCkptMagic || h.version != kCkptVersion) return fail(CSE_EINVAL, "not a checkpoint of this library");
+    if (bytes < sizeof h + h.bytes) return fail(CSE_EINVAL, "truncated checkpoint");
+    if (more_steps < 0 || h.done < 0 || h.done + more_steps >= INT32_MAX) return fail(CSE_EINVAL, "bad step count");
+    if (h.n_mats != s->n_mats) return fail(CSE_EINVAL, "checkpoint of another scheme");
+    for (int k = 0; k < s->n_mats; k++)
+        if (h.rows[k] != s->rows[k] || h.cols[k] != s->cols[k]) return fail(CSE_EINVAL, "checkpoint of another scheme");
+    cse_opts opts;
+    cse_opts_default(&opts);
+    if (launch_opts) opts = *launch_opts;  // the launch fields (procs_per_cta) come from the caller
+    opts.share_interval = h.interval;
+    opts.share_permille = h.permille;
+    opts.col_cap = h.cap;
+    opts.patience_rounds = h.patience;
+    // the coin mode changes results and the trace flag the trajectory record:
+    // both are the checkpoint's
+    opts.flags = (opts.flags & ~(uint32_t)(CSE_FLAG_GI_SHARED_COINS | CSE_FLAG_GRAPH | CSE_FLAG_TRACE)) | h.flags;    const int64_t total = h.done + more_steps;
+    const int32_t n_proc = h.n_proc;
+    const uint64_t seed = h.seed;
+    Resume res{&h, (const char*)ckpt + sizeof h};
+    return run_batch(1, &s, &h.mix, &n_proc, &seed, &total, &opts, cuda_stream, out, nullptr, &res);
 }
 
 int cse_search_batch(int32_t n_searches, const cse_scheme* const* schemes, const cse_strategy_mix* mixes,

@@ -1100,8 +1100,6 @@ __device__ __forceinline__ void run_unit(const DevMat* __restrict__ mats, int n_
         if (iter && E.ended) break;
     }
     E.fold();
-    // the state is needed by the next round
-    const bool more = S->interval == 0 ? t0 / M->cap + 1 < S->budget : t < S->budget;
 
     if (lane == 0) {
         // algorithmic ops of the round: 10 W per rewrite, 5 W per pair count
@@ -1134,7 +1132,7 @@ __device__ __forceinline__ void run_unit(const DevMat* __restrict__ mats, int n_
         st[H_OPS_LO] = (uint32_t)ops;
         st[H_OPS_HI] = (uint32_t)(ops >> 32);
     }
-    if (!GM && more) {
+    if (!GM) {  // the next round, or a checkpoint, reads the state back
         uint2* spn = reinterpret_cast<uint2*>(st + H_WORDS);
         const uint2* P = E.pn();
         for (int x = lane; x < E.ncols * W; x += 32) spn[x] = P[x];

@@ -85,8 +85,9 @@ struct DevSearch {
     int32_t* clock;          // first step of the next round (iteration mode: the
                              // next iteration)
     int32_t* conv;           // iteration mode: [0] iterations without
-                             // improvement, [1] converged, [2] best total,
-                             // [3] iterations run
+                             // improvement, [1] converged (the patience rule
+                             // ended the search), [2] best total, [3]
+                             // iterations run
     const int32_t* mat_pos;  // positions of this search's matrices in the DevMat array
     int32_t n_mats;
     int32_t* status;         // nonzero: a device-side consistency check failed

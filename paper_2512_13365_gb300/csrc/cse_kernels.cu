@@ -114,9 +114,13 @@ __global__ void share_kernel(const DevMat* __restrict__ mats, const DevSearch* _
             } else {
                 cv[0]++;
             }
-            if (S->patience > 0 && cv[0] >= S->patience) fin = true;
+            // converged: set only by the patience rule, so that a search
+            // that merely used up its iterations can be resumed
+            if (S->patience > 0 && cv[0] >= S->patience) {
+                fin = true;
+                cv[1] = 1;
+            }
             cv[3] = c1;
-            if (fin) cv[1] = 1;
         }
         s_final = fin ? 1 : 0;
     }

@@ -111,3 +111,12 @@ def test_brent_and_hybrid_argument_checks_without_device(L):
         cse.CSE_EINVAL
     best = (ctypes.c_int32 * 3)()
     assert L.cse_result_hybrid(None, 2, best, None) == cse.CSE_EINVAL
+
+
+def test_resume_rejects_foreign_data_without_device(L):
+    bogus = ctypes.create_string_buffer(b"\0" * 4096, 4096)
+    h = ctypes.c_void_p()
+    dummy = ctypes.c_void_p(1)   # never dereferenced: the header is checked first
+    assert L.cse_search_resume(dummy, bogus, 4096, 10, None, None, ctypes.byref(h)) == cse.CSE_EINVAL
+    assert b"not a checkpoint" in L.cse_last_error()
+    assert L.cse_search_resume(dummy, bogus, 8, 10, None, None, ctypes.byref(h)) == cse.CSE_EINVAL
