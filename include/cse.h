@@ -50,7 +50,8 @@ enum {
     CSE_ECUDA = 3,    /* CUDA runtime error (including: no device)             */
     CSE_ETIMEOUT = 4, /* a bounded wait expired                                */
     CSE_EBUSY = 5,    /* server admission refused (no room), non-blocking      */
-    CSE_ESTATE = 6    /* internal consistency check failed on the device       */
+    CSE_ESTATE = 6,   /* internal consistency check failed on the device       */
+    CSE_ECANCELED = 7 /* the request was cancelled (cse_server_cancel)         */
 };
 
 /* Limits of this implementation. */
@@ -329,6 +330,12 @@ int cse_server_submit(cse_server* s, const cse_scheme* scheme, const cse_strateg
  * CSE_ETIMEOUT if it is not done, else hands over its result (free it with
  * cse_result_free; cse_result_timing reports the time from submission to
  * completion).  Each ticket can be taken once. */
+/* Cancels a request: a queued request leaves the queue at once; a running one
+ * leaves the device at the next round boundary (its memory is released
+ * there).  cse_server_wait on its ticket then returns CSE_ECANCELED.  Returns
+ * CSE_EINVAL for an unknown ticket or a request that has already finished. */
+int cse_server_cancel(cse_server* server, uint64_t ticket);
+
 int cse_server_wait(cse_server* s, uint64_t ticket, int64_t timeout_us, cse_result** out);
 
 /* Time-to-result percentiles (ms) over completed requests, process-steps

@@ -15,7 +15,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.environ.get("CSE_GB300_LIB") or os.path.join(_HERE, "_build", "libcse_gb300.so")
 
-CSE_OK, CSE_EINVAL, CSE_ENOMEM, CSE_ECUDA, CSE_ETIMEOUT, CSE_EBUSY, CSE_ESTATE = range(7)
+CSE_OK, CSE_EINVAL, CSE_ENOMEM, CSE_ECUDA, CSE_ETIMEOUT, CSE_EBUSY, CSE_ESTATE, CSE_ECANCELED = range(8)
 
 
 class CseError(RuntimeError):
@@ -58,7 +58,8 @@ EXPORTS = ["cse_opts_default", "cse_scheme_load", "cse_scheme_load_uvw", "cse_sc
            "cse_result_iterations", "cse_result_hybrid", "cse_brent_check", "cse_checkpoint_size",
            "cse_checkpoint_save", "cse_search_resume", "cse_result_launches",
            "cse_result_free", "cse_scheme_free", "cse_last_error",
-           "cse_server_create", "cse_server_submit", "cse_server_wait", "cse_server_stats", "cse_server_free",
+           "cse_server_create", "cse_server_submit", "cse_server_cancel", "cse_server_wait", "cse_server_stats",
+           "cse_server_free",
            "cse_search_static"]
 
 FLAG_GRAPH = 1
@@ -109,6 +110,7 @@ def lib() -> ctypes.CDLL:
     L.cse_server_create.argtypes = [ctypes.POINTER(Opts), ctypes.c_uint64, ctypes.c_int64, ctypes.POINTER(vp)]
     L.cse_server_submit.argtypes = [vp, vp, ctypes.POINTER(Mix), i32, u64, i64, ctypes.POINTER(ctypes.c_uint64)]
     L.cse_server_wait.argtypes = [vp, ctypes.c_uint64, i64, ctypes.POINTER(vp)]
+    L.cse_server_cancel.argtypes = [vp, ctypes.c_uint64]
     L.cse_server_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                    ctypes.POINTER(ctypes.c_double), pi32]
     L.cse_search_static.argtypes = [vp, ctypes.POINTER(Mix), i32, u64, i64, ctypes.POINTER(Opts), vp, vp, vp]
@@ -409,9 +411,17 @@ class Server:
         self._keep[t.value] = (scheme, n_proc)
         return t.value
 
+    def cancel(self, ticket: int) -> None:
+        """cse_server_cancel: wait() on the ticket then raises CSE_ECANCELED."""
+        _check(lib().cse_server_cancel(self.handle, ticket))
+
     def wait(self, ticket: int, timeout_us: int = -1) -> Result:
         h = ctypes.c_void_p()
-        _check(lib().cse_server_wait(self.handle, ticket, timeout_us, ctypes.byref(h)))
+        rc = lib().cse_server_wait(self.handle, ticket, timeout_us, ctypes.byref(h))
+        if rc != CSE_OK:
+            if rc != CSE_ETIMEOUT:  # the ticket is consumed: release its inputs
+                self._keep.pop(ticket, None)
+            _check(rc)
         scheme, n_proc = self._keep.pop(ticket)
         r = Result(h, len(scheme.mats), n_proc, self.cap)
         r._scheme = scheme

@@ -692,6 +692,7 @@ struct Request {
     int status = CSE_OK;
     std::string error;
     bool done = false;
+    bool cancel = false;  // leave at the next round boundary
 };
 
 struct cse_server {
@@ -1312,6 +1313,9 @@ static void server_loop(cse_server* sv) {
             if (err) {
                 q->status = err;
                 q->error = msg;
+            } else if (q->cancel) {
+                q->status = CSE_ECANCELED;
+                q->error = "cancelled";
             } else if (++q->sd->rounds_done < q->sd->rounds) {
                 continue;
             }
@@ -1404,6 +1408,27 @@ int cse_server_submit(cse_server* sv, const cse_scheme* s, const cse_strategy_mi
     sv->by_ticket[q->ticket] = q;
     *ticket = q->ticket;
     sv->cv_work.notify_one();
+    return CSE_OK;
+}
+
+int cse_server_cancel(cse_server* sv, uint64_t ticket) {
+    if (!sv) return fail(CSE_EINVAL, "NULL server");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    auto it = sv->by_ticket.find(ticket);
+    if (it == sv->by_ticket.end()) return fail(CSE_EINVAL, "unknown ticket");
+    Request* q = it->second;
+    if (q->done) return fail(CSE_EINVAL, "the request has already finished");
+    auto pos = std::find(sv->pending.begin(), sv->pending.end(), q);
+    if (pos != sv->pending.end()) {  // still queued: nothing on the device yet
+        sv->pending.erase(pos);
+        q->status = CSE_ECANCELED;
+        q->error = "cancelled";
+        q->done = true;
+        sv->cv_done.notify_all();
+    } else {
+        q->cancel = true;  // running: the worker retires it at the next round boundary
+        sv->cv_work.notify_one();
+    }
     return CSE_OK;
 }
 

@@ -86,3 +86,47 @@ def test_wait_timeout_and_bad_requests(cse):
     with pytest.raises(cse.CseError):
         sv.submit(sc, (0,) * 6, 4, 0, 10)  # all weights zero
     sv.free()
+
+
+def test_allocation_failure_is_reported_and_serving_goes_on(cse):
+    """A request whose device state cannot be allocated (about 750 GB: the
+    (6,6,6:153) shape with 2^20 processes per matrix) fails alone with
+    CSE_ENOMEM at admission; the requests around it are served as usual."""
+    small = _requests(2, 32, 32)
+    big = synth.config4(n_proc=1 << 20, budget=32)
+    sv = cse.Server(interval=16, cap=512)
+    sch = [cse.Scheme(s.mats) for s in small]
+    big_sc = cse.Scheme(big.mats)
+    t0 = sv.submit(sch[0], small[0].weights, small[0].n_proc, small[0].seed, small[0].budget)
+    tb = sv.submit(big_sc, big.weights, big.n_proc, big.seed, big.budget)
+    t1 = sv.submit(sch[1], small[1].weights, small[1].n_proc, small[1].seed, small[1].budget)
+    with pytest.raises(cse.CseError) as e:
+        sv.wait(tb)
+    assert e.value.code == cse.CSE_ENOMEM
+    for s, sc, t in zip(small, sch, (t0, t1)):
+        alone = cse.search(sc, s.weights, s.n_proc, s.seed, s.budget, 16, s.permille, 512)
+        _same(cse, sv.wait(t), alone, len(s.mats))
+    sv.free()
+
+
+def test_cancel_queued_and_running_requests(cse):
+    s = synth.config2(n_proc=4096, budget=8192)       # about 0.2 s: still running when cancelled
+    q = synth.config2(n_proc=64, budget=64)
+    sv = cse.Server(interval=32, cap=128, max_active_processes=3 * 4096)   # the others wait in the queue
+    sc, qc = cse.Scheme(s.mats), cse.Scheme(q.mats)
+    t_run = sv.submit(sc, s.weights, s.n_proc, s.seed, s.budget)
+    t_queued = sv.submit(qc, q.weights, q.n_proc, q.seed, q.budget)
+    t_after = sv.submit(qc, q.weights, q.n_proc, q.seed + 1, q.budget)
+    sv.cancel(t_queued)
+    time.sleep(0.02)
+    sv.cancel(t_run)
+    for t in (t_queued, t_run):
+        with pytest.raises(cse.CseError) as e:
+            sv.wait(t)
+        assert e.value.code == cse.CSE_ECANCELED
+    r = sv.wait(t_after)                                 # the rest is served as usual
+    alone = cse.search(qc, q.weights, q.n_proc, q.seed + 1, q.budget, 32, q.permille, 128)
+    _same(cse, r, alone, 3)
+    with pytest.raises(cse.CseError):
+        sv.cancel(t_after)                               # already finished (and collected)
+    sv.free()
