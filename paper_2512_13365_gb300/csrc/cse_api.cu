@@ -16,6 +16,8 @@
 #include <thread>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "cse.h"
 #include "cse_internal.h"
 
@@ -36,6 +38,15 @@ int fail(int code, const std::string& msg) {
         if (e_ != cudaSuccess)                                                         \
             return fail(CSE_ECUDA, std::string(#x) + ": " + cudaGetErrorString(e_)); \
     } while (0)
+
+// NVTX range over a host-side span (enqueueing a search, a served round, a
+// result fetch), for timeline tools; free when no tool is attached.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Bump allocator over one device block.
 struct Carve {
@@ -485,6 +496,7 @@ static int run_batch(int n, const cse_scheme* const* schemes, const cse_strategy
                      const int32_t* n_procs, const uint64_t* seeds, const int64_t* budgets,
                      const cse_opts* opts_in, void* cuda_stream, cse_result** outs,
                      const Trial* trial = nullptr, const Resume* resume = nullptr) {
+    NvtxRange nvtx(trial ? "cse_trial" : resume ? "cse_search_resume" : n > 1 ? "cse_search_batch" : "cse_search");
     if (!outs) return fail(CSE_EINVAL, "out is NULL");
     if (n < 1 || !schemes || !mixes || !n_procs || !seeds || !budgets)
         return fail(CSE_EINVAL, "n_searches must be >= 1 with non-NULL arrays");
@@ -735,6 +747,7 @@ void cse_opts_default(cse_opts* o) {
 
 int cse_scheme_load(const int8_t* const* mats, const int32_t* rows, const int32_t* cols,
                     int32_t n_mats, cse_scheme** out) {
+    NvtxRange nvtx("cse_scheme_load");
     if (!out) return fail(CSE_EINVAL, "out is NULL");
     *out = nullptr;
     if (!mats || !rows || !cols) return fail(CSE_EINVAL, "NULL input array");
@@ -879,6 +892,7 @@ int cse_checkpoint_size(const cse_result* r, size_t* bytes) {
 }
 
 int cse_checkpoint_save(const cse_result* r, void* host_buf, size_t bytes) {
+    NvtxRange nvtx("cse_checkpoint_save");
     if (!r || !r->sd || !host_buf) return fail(CSE_EINVAL, "NULL result or buffer");
     const SearchDev* sd = r->sd;
     if (bytes < sizeof(CkptHeader) + sd->bytes) return fail(CSE_EINVAL, "checkpoint buffer too small");
@@ -1041,6 +1055,7 @@ static int wait_result(const cse_result* r) {
 
 int cse_result_fetch(const cse_result* r, int32_t mat, int32_t* subst, int32_t cap_entries, int32_t* n_subst,
                      int64_t* additions, int64_t* total_additions) {
+    NvtxRange nvtx("cse_result_fetch");
     int rc = wait_result(r);
     if (rc) return rc;
     const SearchDev* sd = r->sd;
@@ -1296,6 +1311,7 @@ static void server_loop(cse_server* sv) {
                 dirty = false;
             }
             if (err == CSE_OK) {
+                NvtxRange nvtx("cse_server_round");
                 cudaError_t e = enqueue_round(ls, sv->stream, nullptr, nullptr, nullptr);
                 if (e == cudaSuccess) e = cudaStreamSynchronize(sv->stream);
                 if (e != cudaSuccess) {
