@@ -239,7 +239,7 @@ def run_ours(args):
         "config": {"workload": s.name + (" (shared gi coins)" if args.gi_shared else ""),
                    "matrices": [list(m.shape) for m in s.mats], "n_processes": s.n_proc,
                    "step_budget": s.budget, "share_interval": s.interval, "share_permille": s.permille,
-                   "col_cap": s.cap, "strategy_weights_gi_ga_gr_wr_mix_g": list(s.weights),
+                   "col_cap": s.cap, "strategy_weights_gi_ga_gr_wr_mix_g_gp": list(s.weights),
                    "process_steps_per_step": psteps, "l2": "flushed (256 MB write) between timed steps",
                    "parallelism": f"{world} independent searches (one per GPU)"},
         "best_additions": total, "best_additions_per_matrix": costs,
