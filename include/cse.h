@@ -233,10 +233,22 @@ typedef struct {
     int64_t ops;        /* algorithmic integer operations (see the counters
                            of cse_result_counters)                           */
     int64_t substeps;   /* steps that made a substitution                    */
+    int32_t best_strategy; /* strategy of the run that produced the best
+                              record, in the weight order gi 0, ga 1, gr 2,
+                              wr 3, mix 4, g 5, gp 6; -1 if no run improved
+                              on the input (per-strategy win counts)         */
+    int32_t pad;
 } cse_proc_record;
 
 /* Waits for the search and writes n_processes records of matrix mat. */
 int cse_result_procs(const cse_result* r, int32_t mat, cse_proc_record* out);
+
+/* The best-Cost curve of matrix mat: costs[r] = the lowest best record over
+ * all processes after round r (step clock: after min((r + 1) share_interval,
+ * step_budget) steps; iteration mode: after iteration r).  *n_points = the
+ * rounds run, at most 4096 (later rounds are not recorded); up to max_points
+ * are written. */
+int cse_result_curve(const cse_result* r, int32_t mat, int32_t* costs, int32_t max_points, int32_t* n_points);
 
 /* Waits for the search and reports, summed over all matrices and processes:
  * *process_steps = n_mats * n_processes * step_budget with the step clock,

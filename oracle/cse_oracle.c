@@ -594,6 +594,7 @@ typedef struct {
     int32_t m;
     int64_t best_cost;
     int32_t best_len;
+    int32_t best_strategy; /* strategy of the run that gave the best record, -1 = none */
     int32_t* best;
     int32_t runs;
     uint64_t traj;
@@ -679,6 +680,7 @@ static void fold(const search_t* S, const mat_t* M, proc_t* P) {
     if (c < P->best_cost) {
         P->best_cost = c;
         P->best_len = P->nf;
+        P->best_strategy = P->strategy;
         memcpy(P->best, P->run, (size_t)P->nf * sizeof(int32_t));
     }
 }
@@ -850,7 +852,7 @@ static int search_impl(int32_t n_mats, const int8_t* const* mats, const int32_t*
                        int64_t budget, int32_t interval, int32_t patience, int32_t permille, int32_t cap,
                        uint32_t flags, int32_t n_threads, const int32_t* proc_subset, int32_t n_subset,
                        int64_t* out_cost, int32_t* out_len, int32_t* out_list, oracle_digest* dig,
-                       int64_t* stats) {
+                       int64_t* stats, int32_t* curve, int32_t curve_cap) {
     if (flags & ~(uint32_t)ORACLE_GI_SHARED_COINS) return -1;
     if (n_mats < 1 || n_mats > 256 || n_proc < 1 || budget < 0 || interval < 0 || patience < 0 ||
         permille < 0 || permille > 1000 || cap < 2 || cap > 1024)
@@ -914,6 +916,7 @@ static int search_impl(int32_t n_mats, const int8_t* const* mats, const int32_t*
             P->cnt = (int32_t*)calloc((size_t)M->max_occ + 1, sizeof(int32_t));
             P->best_cost = M->naive;
             P->best_len = 0;
+            P->best_strategy = -1;
             P->traj = FNV0;
         }
     }
@@ -971,6 +974,8 @@ static int search_impl(int32_t n_mats, const int8_t* const* mats, const int32_t*
                 memcpy(M->snap, M->procs[win].best, (size_t)M->snap_len * sizeof(int32_t));
             }
             if (win >= 0) total += M->procs[win].best_cost;
+            /* the best-Cost curve: the lowest best record after each round */
+            if (curve && win >= 0 && rd < curve_cap) curve[(int64_t)mi * curve_cap + rd] = (int32_t)M->procs[win].best_cost;
         }
         if (interval == 0) {
             /* R14: convergence when the scheme's best total has not improved
@@ -1009,6 +1014,8 @@ static int search_impl(int32_t n_mats, const int8_t* const* mats, const int32_t*
                 d->traj_hash = P->traj;
                 d->ops = P->ops;
                 d->substeps = P->substeps;
+                d->best_strategy = P->best_strategy;
+                d->pad = 0;
             }
         }
         if (out_cost) out_cost[mi] = M->procs[win].best_cost;
@@ -1052,24 +1059,27 @@ int oracle_search(int32_t n_mats, const int8_t* const* mats, const int32_t* rows
                   int64_t* out_cost, int32_t* out_len, int32_t* out_list, oracle_digest* dig) {
     if (interval < 1) return -1;
     return search_impl(n_mats, mats, rows, cols, weights7, n_proc, seed, budget, interval, 0, permille, cap, 0,
-                       n_threads, proc_subset, n_subset, out_cost, out_len, out_list, dig, NULL);
+                       n_threads, proc_subset, n_subset, out_cost, out_len, out_list, dig, NULL, NULL, 0);
 }
 
 int oracle_search_flags(int32_t n_mats, const int8_t* const* mats, const int32_t* rows,
                         const int32_t* cols, const uint32_t* weights7, int32_t n_proc, uint64_t seed,
                         int64_t budget, int32_t interval, int32_t permille, int32_t cap, uint32_t flags,
                         int32_t n_threads, const int32_t* proc_subset, int32_t n_subset,
-                        int64_t* out_cost, int32_t* out_len, int32_t* out_list, oracle_digest* dig) {
+                        int64_t* out_cost, int32_t* out_len, int32_t* out_list, oracle_digest* dig,
+                        int32_t* curve, int32_t curve_cap) {
     if (interval < 1) return -1;
     return search_impl(n_mats, mats, rows, cols, weights7, n_proc, seed, budget, interval, 0, permille, cap,
-                       flags, n_threads, proc_subset, n_subset, out_cost, out_len, out_list, dig, NULL);
+                       flags, n_threads, proc_subset, n_subset, out_cost, out_len, out_list, dig, NULL, curve,
+                       curve_cap);
 }
 
 int oracle_search_iterations(int32_t n_mats, const int8_t* const* mats, const int32_t* rows,
                              const int32_t* cols, const uint32_t* weights7, int32_t n_proc, uint64_t seed,
                              int64_t max_iterations, int32_t patience, int32_t permille, int32_t cap,
                              uint32_t flags, int32_t n_threads, int64_t* out_cost, int32_t* out_len,
-                             int32_t* out_list, oracle_digest* dig, int64_t* stats) {
+                             int32_t* out_list, oracle_digest* dig, int64_t* stats, int32_t* curve,
+                             int32_t curve_cap) {
     return search_impl(n_mats, mats, rows, cols, weights7, n_proc, seed, max_iterations, 0, patience, permille,
-                       cap, flags, n_threads, NULL, 0, out_cost, out_len, out_list, dig, stats);
+                       cap, flags, n_threads, NULL, 0, out_cost, out_len, out_list, dig, stats, curve, curve_cap);
 }

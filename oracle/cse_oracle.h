@@ -37,6 +37,8 @@ typedef struct {
     uint64_t traj_hash;  /* FNV-1a over the trajectory events               */
     int64_t ops;         /* algorithmic integer-op count of the trajectory  */
     int64_t substeps;    /* steps that made a substitution                  */
+    int32_t best_strategy; /* strategy of the run of the best record (-1: none) */
+    int32_t pad;
 } oracle_digest;
 
 /* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11). */
@@ -108,14 +110,19 @@ int oracle_search_iterations(int32_t n_mats, const int8_t* const* mats, const in
                              const int32_t* cols, const uint32_t* weights7, int32_t n_proc, uint64_t seed,
                              int64_t max_iterations, int32_t patience, int32_t permille, int32_t cap,
                              uint32_t flags, int32_t n_threads, int64_t* out_cost, int32_t* out_len,
-                             int32_t* out_list, oracle_digest* dig, int64_t* stats);
+                             int32_t* out_list, oracle_digest* dig, int64_t* stats, int32_t* curve,
+                             int32_t curve_cap);
 
-/* oracle_search with search flags (ORACLE_GI_SHARED_COINS). */
+/* oracle_search with search flags (ORACLE_GI_SHARED_COINS) and, if curve is
+ * not NULL, the best-Cost curve: curve[mi * curve_cap + r] = the lowest best
+ * record of matrix mi after round r (r < curve_cap).  The same curve is an
+ * optional output of oracle_search_iterations (one round per iteration). */
 int oracle_search_flags(int32_t n_mats, const int8_t* const* mats, const int32_t* rows,
                         const int32_t* cols, const uint32_t* weights7, int32_t n_proc, uint64_t seed,
                         int64_t budget, int32_t interval, int32_t permille, int32_t cap, uint32_t flags,
                         int32_t n_threads, const int32_t* proc_subset, int32_t n_subset,
-                        int64_t* out_cost, int32_t* out_len, int32_t* out_list, oracle_digest* dig);
+                        int64_t* out_cost, int32_t* out_len, int32_t* out_list, oracle_digest* dig,
+                        int32_t* curve, int32_t curve_cap);
 
 #ifdef __cplusplus
 }

@@ -28,12 +28,13 @@ GI_SHARED_COINS = 1  # search flag: one Greedy-Intersections coin per candidate 
 class Digest(ctypes.Structure):
     _fields_ = [("best_cost", ctypes.c_int64), ("best_len", ctypes.c_int32), ("runs", ctypes.c_int32),
                 ("best_hash", ctypes.c_uint64), ("traj_hash", ctypes.c_uint64), ("ops", ctypes.c_int64),
-                ("substeps", ctypes.c_int64)]
+                ("substeps", ctypes.c_int64), ("best_strategy", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
 DIGEST_DTYPE = np.dtype([("best_cost", "<i8"), ("best_len", "<i4"), ("runs", "<i4"),
                          ("best_hash", "<u8"), ("traj_hash", "<u8"), ("ops", "<i8"),
-                         ("substeps", "<i8")])
+                         ("substeps", "<i8"), ("best_strategy", "<i4"), ("pad", "<i4")])
+CURVE_POINTS = 4096  # rounds recorded in the best-Cost curve
 assert DIGEST_DTYPE.itemsize == ctypes.sizeof(Digest)
 
 
@@ -84,11 +85,11 @@ def lib():
         L.oracle_search_iterations.argtypes = [ctypes.c_int32, ctypes.POINTER(i8p), i32p, i32p, u32p, ctypes.c_int32,
                                                ctypes.c_uint64, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
                                                ctypes.c_int32, ctypes.c_uint32, ctypes.c_int32, i64p, i32p, i32p,
-                                               ctypes.POINTER(Digest), i64p]
+                                               ctypes.POINTER(Digest), i64p, i32p, ctypes.c_int32]
         L.oracle_search_flags.argtypes = [ctypes.c_int32, ctypes.POINTER(i8p), i32p, i32p, u32p, ctypes.c_int32,
                                           ctypes.c_uint64, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
                                           ctypes.c_int32, ctypes.c_uint32, ctypes.c_int32, i32p, ctypes.c_int32,
-                                          i64p, i32p, i32p, ctypes.POINTER(Digest)]
+                                          i64p, i32p, i32p, ctypes.POINTER(Digest), i32p, ctypes.c_int32]
         L.oracle_search_flags.restype = ctypes.c_int
         L.oracle_search_iterations.restype = ctypes.c_int
         _lib = L
@@ -221,16 +222,21 @@ def search(mats: Sequence[np.ndarray], weights, n_proc: int, seed: int, budget: 
     length = np.zeros(n, dtype=np.int32)
     lists = np.zeros((n, cap), dtype=np.int32)
     dig = np.zeros((n, n_proc), dtype=DIGEST_DTYPE) if digests else None
+    curve = np.full((n, CURVE_POINTS), -1, dtype=np.int32)
     sub = None if subset is None else np.ascontiguousarray(np.array(subset, dtype=np.int32))
     rc = lib().oracle_search_flags(n, ptrs, _p(rows, ctypes.c_int32), _p(cols, ctypes.c_int32),
                              _p(w, ctypes.c_uint32), n_proc, seed, budget, interval, permille, cap, flags, n_threads,
                              None if sub is None else _p(sub, ctypes.c_int32), 0 if sub is None else len(sub),
                              _p(cost, ctypes.c_int64), _p(length, ctypes.c_int32), _p(lists, ctypes.c_int32),
-                             None if dig is None else dig.ctypes.data_as(ctypes.POINTER(Digest)))
+                             None if dig is None else dig.ctypes.data_as(ctypes.POINTER(Digest)),
+                             _p(curve, ctypes.c_int32), CURVE_POINTS)
     if rc != 0:
         raise ValueError(f"oracle_search rejected its arguments (rc={rc})")
-    return SearchResult([int(x) for x in cost], [int(x) for x in length],
-                        [[int(e) for e in lists[k, :length[k]]] for k in range(n)], dig)
+    r = SearchResult([int(x) for x in cost], [int(x) for x in length],
+                     [[int(e) for e in lists[k, :length[k]]] for k in range(n)], dig)
+    rounds = min(CURVE_POINTS, (budget + interval - 1) // interval)
+    r.curve = [[int(v) for v in curve[k, :rounds]] for k in range(n)]
+    return r
 
 
 def search_iterations(mats: Sequence[np.ndarray], weights, n_proc: int, seed: int, max_iterations: int,
@@ -251,17 +257,19 @@ def search_iterations(mats: Sequence[np.ndarray], weights, n_proc: int, seed: in
     lists = np.zeros((n, cap), dtype=np.int32)
     dig = np.zeros((n, n_proc), dtype=DIGEST_DTYPE) if digests else None
     stats = np.zeros(2, dtype=np.int64)
+    curve = np.full((n, CURVE_POINTS), -1, dtype=np.int32)
     rc = lib().oracle_search_iterations(n, ptrs, _p(rows, ctypes.c_int32), _p(cols, ctypes.c_int32),
                                         _p(w, ctypes.c_uint32), n_proc, seed, max_iterations, patience, permille,
                                         cap, flags, n_threads, _p(cost, ctypes.c_int64), _p(length, ctypes.c_int32),
                                         _p(lists, ctypes.c_int32),
                                         None if dig is None else dig.ctypes.data_as(ctypes.POINTER(Digest)),
-                                        _p(stats, ctypes.c_int64))
+                                        _p(stats, ctypes.c_int64), _p(curve, ctypes.c_int32), CURVE_POINTS)
     if rc != 0:
         raise ValueError(f"oracle_search_iterations rejected its arguments (rc={rc})")
     r = SearchResult([int(x) for x in cost], [int(x) for x in length],
                      [[int(e) for e in lists[k, :length[k]]] for k in range(n)], dig)
     r.iterations, r.process_steps = int(stats[0]), int(stats[1])
+    r.curve = [[int(v) for v in curve[k, :min(CURVE_POINTS, r.iterations)]] for k in range(n)]
     return r
 
 

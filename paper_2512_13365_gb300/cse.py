@@ -37,7 +37,7 @@ class Opts(ctypes.Structure):
 class ProcRecord(ctypes.Structure):
     _fields_ = [("best_cost", ctypes.c_int64), ("best_len", ctypes.c_int32), ("runs", ctypes.c_int32),
                 ("best_hash", ctypes.c_uint64), ("traj_hash", ctypes.c_uint64), ("ops", ctypes.c_int64),
-                ("substeps", ctypes.c_int64)]
+                ("substeps", ctypes.c_int64), ("best_strategy", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
 class TuneEntry(ctypes.Structure):
@@ -47,7 +47,9 @@ class TuneEntry(ctypes.Structure):
 
 
 PROC_DTYPE = np.dtype([("best_cost", "<i8"), ("best_len", "<i4"), ("runs", "<i4"), ("best_hash", "<u8"),
-                       ("traj_hash", "<u8"), ("ops", "<i8"), ("substeps", "<i8")])
+                       ("traj_hash", "<u8"), ("ops", "<i8"), ("substeps", "<i8"), ("best_strategy", "<i4"),
+                       ("pad", "<i4")])
+STRATEGIES = ("gi", "ga", "gr", "wr", "mix", "g", "gp")  # best_strategy indices
 assert PROC_DTYPE.itemsize == ctypes.sizeof(ProcRecord)
 
 _lib = None
@@ -55,7 +57,7 @@ _lib = None
 # every symbol include/cse.h declares
 EXPORTS = ["cse_opts_default", "cse_scheme_load", "cse_scheme_load_uvw", "cse_scheme_shape", "cse_search",
            "cse_search_batch", "cse_autotune", "cse_tune_interval", "cse_result_fetch", "cse_result_procs", "cse_result_counters", "cse_result_timing",
-           "cse_result_iterations", "cse_result_hybrid", "cse_brent_check", "cse_checkpoint_size",
+           "cse_result_iterations", "cse_result_curve", "cse_result_hybrid", "cse_brent_check", "cse_checkpoint_size",
            "cse_checkpoint_save", "cse_search_resume", "cse_result_launches",
            "cse_result_free", "cse_scheme_free", "cse_last_error",
            "cse_server_create", "cse_server_submit", "cse_server_cancel", "cse_server_wait", "cse_server_stats",
@@ -90,6 +92,7 @@ def lib() -> ctypes.CDLL:
                                    ctypes.POINTER(Opts), vp, ctypes.POINTER(vp)]
     L.cse_result_launches.argtypes = [vp, pi32, pi32]
     L.cse_result_iterations.argtypes = [vp, pi32, pi32, pi64]
+    L.cse_result_curve.argtypes = [vp, i32, pi32, i32, pi32]
     L.cse_result_hybrid.argtypes = [ctypes.POINTER(vp), i32, pi32, pi64]
     L.cse_brent_check.argtypes = [i32, i32, i32, i32, vp, vp, vp, pi64]
     L.cse_checkpoint_size.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
@@ -226,6 +229,14 @@ class Result:
         it, cv, tot = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
         _check(lib().cse_result_iterations(self.handle, ctypes.byref(it), ctypes.byref(cv), ctypes.byref(tot)))
         return it.value, bool(cv.value), tot.value
+
+    def curve(self, mat: int) -> List[int]:
+        """cse_result_curve: the lowest best Cost after each round."""
+        n = ctypes.c_int32()
+        _check(lib().cse_result_curve(self.handle, mat, None, 0, ctypes.byref(n)))
+        buf = (ctypes.c_int32 * max(1, n.value))()
+        _check(lib().cse_result_curve(self.handle, mat, buf, n.value, ctypes.byref(n)))
+        return list(buf[:n.value])
 
     def checkpoint(self) -> bytes:
         """cse_checkpoint_save: the finished search's checkpoint as bytes."""

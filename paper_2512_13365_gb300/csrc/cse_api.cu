@@ -280,6 +280,7 @@ static int search_plan(const cse_scheme* s, const cse_strategy_mix* mix, int n_p
         offs->push_back(cv.take((size_t)cap * 4));                      // result
         offs->push_back(cv.take(8));                                    // result meta
         offs->push_back(cv.take(32));                                   // counters
+        offs->push_back(cv.take((size_t)kCurvePoints * 4));             // best-Cost curve
     }
     offs->push_back(cv.take(4));   // clock
     offs->push_back(cv.take(4));   // status
@@ -328,16 +329,16 @@ static int search_create(const cse_scheme* s, const cse_strategy_mix* mix, int n
     S.interval = (int32_t)opts.share_interval;
     S.patience = (int32_t)opts.patience_rounds;
     S.share_thr = ((uint64_t)opts.share_permille << 32) / 1000u;
-    S.clock = (int32_t*)(b + of[8 * s->n_mats]);
-    S.status = (int32_t*)(b + of[8 * s->n_mats + 1]);
-    S.conv = (int32_t*)(b + of[8 * s->n_mats + 2]);
+    S.clock = (int32_t*)(b + of[9 * s->n_mats]);
+    S.status = (int32_t*)(b + of[9 * s->n_mats + 1]);
+    S.conv = (int32_t*)(b + of[9 * s->n_mats + 2]);
     S.n_mats = s->n_mats;
     S.trace = (opts.flags & CSE_FLAG_TRACE) ? 1 : 0;
     S.gi_shared = (opts.flags & CSE_FLAG_GI_SHARED_COINS) ? 1 : 0;
     static const int32_t snap_init[2] = {INT_MAX, 0};
     for (int k = 0; k < s->n_mats; k++) {
         DevMat& M = sd->mats[k];
-        const size_t* o = &of[8 * k];
+        const size_t* o = &of[9 * k];
         M.pn0 = s->d_pn0[k];
         M.cand0 = s->d_cand0[k];
         M.meta0 = s->d_meta0[k];
@@ -356,12 +357,14 @@ static int search_create(const cse_scheme* s, const cse_strategy_mix* mix, int n
         M.result = (int32_t*)(b + o[5]);
         M.result_meta = (int32_t*)(b + o[6]);
         M.counters = (unsigned long long*)(b + o[7]);
+        M.curve = (int32_t*)(b + o[8]);
         // initial values: no round minimum, no snapshot, result = the input
         if (e == cudaSuccess) e = cudaMemsetAsync(M.round_min, 0xFF, 8, stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(M.snap_meta, snap_init, 8, cudaMemcpyHostToDevice, stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(M.result_meta, M.meta0, 4, cudaMemcpyDeviceToDevice, stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(M.result_meta + 1, 0, 4, stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(M.counters, 0, 32, stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(M.curve, 0xFF, (size_t)kCurvePoints * 4, stream);
     }
     static const int32_t conv_init[4] = {0, 0, INT_MAX, 0};
     if (e == cudaSuccess) e = cudaMemcpyAsync(S.conv, conv_init, 16, cudaMemcpyHostToDevice, stream);
@@ -1095,6 +1098,8 @@ int cse_result_procs(const cse_result* r, int32_t mat, cse_proc_record* out) {
             out[p].traj_hash = kFnv0;
             out[p].ops = 0;
             out[p].substeps = 0;
+            out[p].best_strategy = -1;
+            out[p].pad = 0;
         }
         return CSE_OK;
     }
@@ -1115,7 +1120,29 @@ int cse_result_procs(const cse_result* r, int32_t mat, cse_proc_record* out) {
         o.traj_hash = (uint64_t)h[H_TRAJ_LO] | (uint64_t)h[H_TRAJ_HI] << 32;
         o.ops = (int64_t)((uint64_t)h[H_OPS_LO] | (uint64_t)h[H_OPS_HI] << 32);
         o.substeps = (int32_t)h[H_SUBSTEPS];
+        o.best_strategy = (int32_t)h[H_BEST_STRAT];
+        o.pad = 0;
     }
+    return CSE_OK;
+}
+
+int cse_result_curve(const cse_result* r, int32_t mat, int32_t* costs, int32_t max_points, int32_t* n_points) {
+    int rc = wait_result(r);
+    if (rc) return rc;
+    const SearchDev* sd = r->sd;
+    if (mat < 0 || mat >= sd->n_mats) return fail(CSE_EINVAL, "matrix index out of range");
+    int32_t rounds = 0;
+    if (sd->search.interval == 0) {
+        int32_t conv[4];
+        CUDA_TRY(cudaMemcpy(conv, sd->search.conv, 16, cudaMemcpyDeviceToHost));
+        rounds = conv[3];
+    } else {
+        rounds = (int32_t)((sd->budget + sd->search.interval - 1) / sd->search.interval);
+    }
+    rounds = std::min(rounds, (int32_t)kCurvePoints);
+    if (n_points) *n_points = rounds;
+    const int32_t n = std::min(rounds, max_points);
+    if (costs && n > 0) CUDA_TRY(cudaMemcpy(costs, sd->mats[mat].curve, (size_t)n * 4, cudaMemcpyDeviceToHost));
     return CSE_OK;
 }
 

@@ -282,6 +282,7 @@ struct Cold {
     unsigned long long t_rare; // algorithmic ops of this round's gp and shared-coin gi steps
     int runs, substeps, best_cost, best_len, trace, overflow, sub_before;
     int strat, a, b;           // the current run's strategy, alpha, beta
+    int best_strat;            // strategy of the run that gave the best record (-1: none)
     // algorithmic-op tallies of the round: substitutions, pair counts that
     // can change, candidates scanned by g/ga/wr/gr; Greedy-Intersections
     // terms, Philox blocks and scored candidates
@@ -456,6 +457,7 @@ struct Engine {
             if (lane == 0) {
                 cd->best_cost = cost;
                 cd->best_len = nf;
+                cd->best_strat = cd->strat;
             }
         }
         __syncwarp();
@@ -1046,6 +1048,7 @@ __device__ __forceinline__ void run_unit(const DevMat* __restrict__ mats, int n_
             cd->substeps = 0;
             cd->best_cost = M->meta0[0];
             cd->best_len = 0;
+            cd->best_strat = -1;
             cd->traj = kFnv0;
         }
     } else {
@@ -1063,6 +1066,7 @@ __device__ __forceinline__ void run_unit(const DevMat* __restrict__ mats, int n_
             cd->substeps = (int)st[H_SUBSTEPS];
             cd->best_cost = (int)st[H_BEST_COST];
             cd->best_len = (int)st[H_BEST_LEN];
+            cd->best_strat = (int)st[H_BEST_STRAT];
             cd->traj = (uint64_t)st[H_TRAJ_LO] | (uint64_t)st[H_TRAJ_HI] << 32;
         }
     }
@@ -1131,6 +1135,7 @@ __device__ __forceinline__ void run_unit(const DevMat* __restrict__ mats, int n_
         st[H_TRAJ_HI] = (uint32_t)(cd->traj >> 32);
         st[H_OPS_LO] = (uint32_t)ops;
         st[H_OPS_HI] = (uint32_t)(ops >> 32);
+        st[H_BEST_STRAT] = (uint32_t)cd->best_strat;
     }
     if (!GM) {  // the next round, or a checkpoint, reads the state back
         uint2* spn = reinterpret_cast<uint2*>(st + H_WORDS);

@@ -36,7 +36,7 @@ enum Purpose : uint32_t { PU_RUN = 0, PU_SHAREK = 1, PU_STEP = 2, PU_GI = 3, PU_
 // state region in global memory.
 enum Hdr : int {
     H_NCOLS = 0, H_NF, H_M, H_COST, H_STRAT, H_A, H_B, H_ENDED, H_RUNS, H_SUBSTEPS,
-    H_BEST_COST, H_BEST_LEN, H_TRAJ_LO, H_TRAJ_HI, H_OPS_LO, H_OPS_HI, H_WORDS = 16
+    H_BEST_COST, H_BEST_LEN, H_TRAJ_LO, H_TRAJ_HI, H_OPS_LO, H_OPS_HI, H_BEST_STRAT, H_WORDS = 20
 };
 
 constexpr int kMaxW = 8;          // 32-bit words per column (256 rows)
@@ -70,6 +70,7 @@ struct DevMat {
     int32_t* result_meta;    // [0] cost, [1] length
     unsigned long long* counters;   // [0] algorithmic ops, [1] substitution steps,
                                     // [2] process-steps (iteration mode)
+    int32_t* curve;          // [kCurvePoints]: lowest best Cost after each round (-1: not run)
     WarpLayout gml;          // layout of the working arrays inside a state region
                              // (HBM path only; fixed for the life of the search)
 };
@@ -99,6 +100,9 @@ struct DevSearch {
 WarpLayout make_layout(int W, int cap, int mmax, bool planes = false);
 int state_words(int W, int cap, int mmax);
 int state_words_gm(const WarpLayout& L);
+
+// Rounds recorded in a matrix's best-Cost curve.
+constexpr int kCurvePoints = 4096;
 
 // A process whose shared-memory slice would exceed this many bytes runs on
 // its HBM state region instead (round_kernel<W, true>).

@@ -101,7 +101,12 @@ __global__ void share_kernel(const DevMat* __restrict__ mats, const DevSearch* _
                 M->snap_meta[1] = len;
             }
         }
-        if (lane == 0) atomicAdd(&s_total, cost);
+        if (lane == 0) {
+            atomicAdd(&s_total, cost);
+            // the best-Cost curve: one point per round (per iteration)
+            const int r = iter_mode ? c0 : c0 / S->interval;
+            if (r < kCurvePoints) M->curve[r] = cost;
+        }
     }
     __syncthreads();
     if (threadIdx.x == 0) {

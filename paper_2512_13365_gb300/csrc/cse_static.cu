@@ -89,7 +89,7 @@ extern "C" int cse_search_static(const cse_scheme* s, const cse_strategy_mix* mi
     // ---- the carve-up of the scratch, checked against its size
     std::vector<DevMat> mats(nm);
     std::vector<char> gm(nm);
-    std::vector<size_t> o_state(nm), o_best(nm), o_snap(nm), o_snapm(nm), o_rmin(nm), o_cnt(nm);
+    std::vector<size_t> o_state(nm), o_best(nm), o_snap(nm), o_snapm(nm), o_rmin(nm), o_cnt(nm), o_curve(nm);
     size_t off = 0;
     for (int k = 0; k < nm; k++) {
         const WarpLayout own = make_layout(s->W[k], cap, s->mmax[k]);
@@ -102,6 +102,7 @@ extern "C" int cse_search_static(const cse_scheme* s, const cse_strategy_mix* mi
         o_snapm[k] = take(off, 8);
         o_rmin[k] = take(off, 8);
         o_cnt[k] = take(off, 32);
+        o_curve[k] = take(off, (size_t)kCurvePoints * 4);
     }
     const size_t o_clock = take(off, 4), o_status = take(off, 4);
     const size_t o_mats = take(off, sizeof(DevMat) * nm), o_search = take(off, sizeof(DevSearch));
@@ -169,6 +170,7 @@ extern "C" int cse_search_static(const cse_scheme* s, const cse_strategy_mix* mi
         M.result = d_lists + (size_t)k * cap;  // results go straight to the caller's buffers
         M.result_meta = d_meta + 2 * (size_t)k;
         M.counters = (unsigned long long*)(b + o_cnt[k]);
+        M.curve = (int32_t*)(b + o_curve[k]);
         pos[q] = q;
         if (groups.empty() || groups.back().W != M.W || groups.back().gm != (gm[k] != 0))
             groups.push_back({M.W, q, 0, 0, 0, gm[k] != 0, {}, 0});
@@ -200,6 +202,7 @@ extern "C" int cse_search_static(const cse_scheme* s, const cse_strategy_mix* mi
         if (e == cudaSuccess) e = cudaMemcpyAsync(d_meta + 2 * k, s->d_meta0[k], 4, cudaMemcpyDeviceToDevice, stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(d_meta + 2 * k + 1, 0, 4, stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(b + o_cnt[k], 0, 32, stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(b + o_curve[k], 0xFF, (size_t)kCurvePoints * 4, stream);
     }
     if (e == cudaSuccess) e = cudaMemsetAsync(b + o_clock, 0, 4, stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(b + o_status, 0, 4, stream);

@@ -12,7 +12,7 @@ from paper_2512_13365_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 
-FIELDS = ("best_cost", "best_len", "runs", "best_hash", "traj_hash", "ops", "substeps")
+FIELDS = ("best_cost", "best_len", "runs", "best_hash", "traj_hash", "ops", "substeps", "best_strategy")
 
 
 @pytest.fixture(scope="module")
@@ -37,6 +37,8 @@ def assert_parity(cse, s, ref=None, procs_per_cta=0, check_procs=True, gi_shared
                 assert bad.size == 0, f"matrix {k} field {f}: {bad.size} processes differ, first {bad[:5]}"
     steps, sub, ops = r.counters()
     assert steps == len(s.mats) * s.n_proc * s.budget
+    if check_procs:
+        assert [r.curve(k) for k in range(len(s.mats))] == ref.curve
     assert sub == int(sum(ref.digests[k]["substeps"].sum() for k in range(len(s.mats))))
     assert ops == int(sum(ref.digests[k]["ops"].sum() for k in range(len(s.mats))))
     r.free()
@@ -316,6 +318,7 @@ def assert_parity_iterations(cse, s, patience, ref=None, r=None, gi_shared=False
     assert ops == int(sum(ref.digests[k]["ops"].sum() for k in range(len(s.mats))))
     it, conv, total = r.iterations()
     assert it == ref.iterations and total == sum(ref.cost)
+    assert [r.curve(k) for k in range(len(s.mats))] == ref.curve
     assert conv == (ref.iterations < s.budget)
     r.free()
     return ref

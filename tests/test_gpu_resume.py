@@ -9,7 +9,7 @@ from paper_2512_13365_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 
-FIELDS = ("best_cost", "best_len", "runs", "best_hash", "traj_hash", "ops", "substeps")
+FIELDS = ("best_cost", "best_len", "runs", "best_hash", "traj_hash", "ops", "substeps", "best_strategy")
 
 
 @pytest.fixture(scope="module")

@@ -646,3 +646,24 @@ def test_shared_coin_scores_from_per_variable_sums(seed):
         x = X[i] + X[j] - 2 * coins[p] * w[p] - ct * wt
         d = T - w[p] - inter
         assert sc[p] == (int(w[p]) << 32) + a * ((int(d) << 16) + b * int(x))
+
+
+# ---------------------------------------------------------------- metrics
+@pytest.mark.parametrize("seed", range(3))
+def test_curve_and_winning_strategies(seed):
+    """The best-Cost curve never rises, has one point per round and ends at
+    the result; a process's best record names the strategy of its run: with
+    Greedy alone every improving process names g (5), and the per-strategy
+    win counts over processes add up to the processes that improved."""
+    mats = [synth.random_matrix(1100 + seed, 18, 9, 2, 5, n_planted=5)]
+    r = O.search(mats, synth.PAPER_WEIGHTS, 40, seed, 100, 16, 400, 48)
+    c = r.curve[0]
+    assert len(c) == 7 and c[-1] == r.cost[0] and all(a >= b for a, b in zip(c, c[1:]))
+    d = r.digests[0]
+    improved = d["best_cost"] < O.naive(mats[0])
+    assert ((d["best_strategy"] >= 0) == improved).all()
+    assert np.bincount(d["best_strategy"][improved], minlength=7).sum() == improved.sum()
+    g = O.search(mats, (0, 0, 0, 0, 0, 1), 12, seed, 40, 16, 400, 48).digests[0]["best_strategy"]
+    assert set(g.tolist()) <= {5, -1}
+    it = O.search_iterations(mats, synth.PAPER_WEIGHTS, 20, seed, 30, 3, 400, 48)
+    assert len(it.curve[0]) == it.iterations and it.curve[0][-1] == it.cost[0]
