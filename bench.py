@@ -199,6 +199,15 @@ def run_ours(args):
         ops_total = ops
     total = results[-1].total
     costs = results[-1].costs
+    # the best-additions curve (sum over matrices, one point per round) and
+    # which strategies produced the processes' best records
+    curves = [results[-1].curve(k) for k in range(len(s.mats))]
+    curve = [sum(c[i] for c in curves) for i in range(min(len(c) for c in curves))]
+    wins = [0] * len(cse.STRATEGIES)
+    for k in range(len(s.mats)):
+        bs = results[-1].procs(k)["best_strategy"]
+        for v in bs[bs >= 0]:
+            wins[int(v)] += 1
     for r in results:
         r.free()
     ms = max_over_ranks(statistics.mean(step_ms), dev)
@@ -243,6 +252,8 @@ def run_ours(args):
                    "process_steps_per_step": psteps, "l2": "flushed (256 MB write) between timed steps",
                    "parallelism": f"{world} independent searches (one per GPU)"},
         "best_additions": total, "best_additions_per_matrix": costs,
+        "best_additions_per_round": curve,
+        "best_records_by_strategy": dict(zip(cse.STRATEGIES, wins)),
         "wall_s": wall,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": statistics.mean(e2e_ms) if e2e_ms else None},
