@@ -580,6 +580,71 @@ def run_iterations(args):
     print(json.dumps(line))
 
 
+def run_wallclock(args):
+    """Best additions at fixed wall-clock budgets (1 s, 10 s, 60 s) on the
+    (3,3,3:23)-shaped workload: the GPU search runs as many steps as fit in
+    the budget (calibrated on the 1024-step search), the oracle as many as
+    fit on the host cores (calibrated on 32 steps); both use the same seed,
+    processes and options, so a longer budget is the same search run further."""
+    import torch
+    from paper_2512_13365_gb300 import cse
+    from oracle import oracle as O
+    import copy
+    dev = torch.device("cuda", 0)
+    s = workload("cfg2", args.procs)
+    budgets_s = [float(x) for x in args.seconds.split(",")]
+    stream = torch.cuda.Stream(device=dev)
+    scheme = cse.Scheme(s.mats)
+
+    def gpu(budget):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        r = cse.search(scheme, s.weights, s.n_proc, s.seed, budget, s.interval, s.permille, s.cap, stream=stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        out = (a.elapsed_time(b) / 1000.0, r.total, r.costs)
+        r.free()
+        return out
+
+    for _ in range(args.warmup):
+        gpu(s.budget)
+    per_step = min(gpu(s.budget)[0] for _ in range(2)) / s.budget
+    clocks = Clocks(os.path.join(args.out, "clocks_wallclock.csv"), 0)
+    gpu_rows = []
+    for T in budgets_s:
+        B = max(s.interval, int(T / per_step) // s.interval * s.interval)
+        sec, total, costs = gpu(B)
+        gpu_rows.append({"budget_s": T, "steps": B, "device_s": sec, "best_additions": total,
+                         "best_additions_per_matrix": costs})
+    clk = clocks.stop()
+    cores = len(os.sched_getaffinity(0))
+    smp = copy.copy(s)
+    smp.budget = 32
+    t0 = time.perf_counter()
+    O.search_obj(smp, n_threads=cores, digests=False)
+    cpu_per_step = (time.perf_counter() - t0) / 32
+    cpu_rows = []
+    for T in budgets_s:
+        smp = copy.copy(s)
+        smp.budget = max(s.interval, int(T / cpu_per_step) // s.interval * s.interval)
+        t0 = time.perf_counter()
+        ref = O.search_obj(smp, n_threads=cores, digests=False)
+        cpu_rows.append({"budget_s": T, "steps": smp.budget, "wall_s": time.perf_counter() - t0,
+                         "best_additions": ref.total})
+    line = {
+        "metric": METRIC, "value": gpu_rows[-1]["steps"] * len(s.mats) * s.n_proc / gpu_rows[-1]["device_s"],
+        "unit": UNIT, "n_gpus": 1, "steps": len(budgets_s), "warmup": args.warmup,
+        "ms_per_step": gpu_rows[-1]["device_s"] * 1000.0, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": f"{s.name}, best additions at fixed wall-clock budgets", "n_processes": s.n_proc,
+                   "share_interval": s.interval, "col_cap": s.cap, "budgets_s": budgets_s},
+        "gpu": gpu_rows, "cpu_oracle": {"cores": cores, "kind": "oracle", "runs": cpu_rows},
+        "clocks": clk,
+    }
+    print(json.dumps(line))
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -621,7 +686,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="cfg2",
                     help="cfg2 (default, the benchmark line), cfg1, cfg4, cfg3 (batched), cfg5 (serving), "
-                         "cfg2-iter (iteration mode)")
+                         "cfg2-iter (iteration mode), cfg2-wallclock (best additions at fixed wall-clock budgets)")
     ap.add_argument("--requests", type=int, default=200, help="cfg5: number of requests")
     ap.add_argument("--procs", type=int, default=0, help="override the process count (reduced-scale runs)")
     ap.add_argument("--ppc", type=int, default=0, help="processes per CTA (0 = library default)")
@@ -630,6 +695,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--budget", type=int, default=0, help="override the step budget (profiling runs)")
+    ap.add_argument("--seconds", default="1,10,60", help="cfg2-wallclock: the wall-clock budgets")
     ap.add_argument("--gi-shared", action="store_true",
                     help="Greedy-Intersections with shared coins (an option that changes results)")
     ap.add_argument("--out", default=os.path.join(ROOT, "gpurun_out"))
@@ -643,6 +709,8 @@ def main():
         run_serving(args)
     elif args.workload == "cfg2-iter":
         run_iterations(args)
+    elif args.workload == "cfg2-wallclock":
+        run_wallclock(args)
     else:
         run_ours(args)
 
