@@ -225,15 +225,16 @@ __device__ __forceinline__ int gi_shared_select(const uint32_t* C, uint32_t* G, 
             const uint32_t e = C[p];
             const int i = key_lo(e), j = key_hi(e), wp = cand_c(e) - 1;
             const uint32_t key = e & 0x1FFFFFu;
-            int sib = -1;
-            if (!(e & 1u)) {
-                if (p + 1 < m && (C[p + 1] & 0x1FFFFFu) == (key | 1u)) sib = p + 1;
-            } else {
-                if (p >= 1 && (C[p - 1] & 0x1FFFFFu) == (key & ~1u)) sib = p - 1;
+            int sib = -1, wsib = 0, csib = 0;
+            {
+                const int nb_ = (e & 1u) ? p - 1 : p + 1;
+                const uint32_t en = (nb_ >= 0 && nb_ < m) ? C[nb_] : 0u;
+                if (nb_ >= 0 && nb_ < m && (en & 0x1FFFFFu) == (key ^ 1u)) {
+                    sib = nb_;
+                    wsib = cand_c(en) - 1;
+                }
             }
-            int wsib = 0, csib = 0;
             if (sib >= 0) {
-                wsib = cand_c(C[sib]) - 1;
                 const uint32_t sw = (sib >> 5) == (p >> 5) ? word : shared_coin_word(proc, t, c2s, seed, sib & ~31);
                 csib = (int)((sw >> (sib & 31)) & 1u);
             }
@@ -665,14 +666,18 @@ struct Engine {
                 const int b1 = VB[j], n1 = (HE[j] - HS[j]) + LC[j];
                 const int lp0 = PL[p] - b0;     // p's place in A_i
                 const int lp1 = p - HS[j];      // p's place in A_j
-                int sib = -1;                   // the sign twin (i, j, -s), if a candidate
-                if (!(e & 1u)) {
-                    if (p + 1 < m && (C[p + 1] & 0x1FFFFFu) == (key | 1u)) sib = p + 1;
-                } else {
-                    if (p >= 1 && (C[p - 1] & 0x1FFFFFu) == (key & ~1u)) sib = p - 1;
+                // the sign twin (i, j, -s), if a candidate: the neighbour on the
+                // side its sign sorts to, read once
+                int sib = -1, wsib = 0;
+                {
+                    const int nb_ = (e & 1u) ? p - 1 : p + 1;
+                    const uint32_t en = (nb_ >= 0 && nb_ < m) ? C[nb_] : 0u;
+                    if (nb_ >= 0 && nb_ < m && (en & 0x1FFFFFu) == (key ^ 1u)) {
+                        sib = nb_;
+                        wsib = cand_c(en) - 1;
+                    }
                 }
                 const int ls1 = sib - HS[j];
-                const int wsib = sib >= 0 ? cand_c(C[sib]) - 1 : 0;
                 const int nint = (n0 - 1) + (n1 - 1 - (sib >= 0 ? 1 : 0));
                 int inter = 0, X = 0, nb = 0;
                 if (nint > 0) {
@@ -864,14 +869,18 @@ struct Engine {
                 const int n1 = (HE[j] - HS[j]) + LC[j];
                 const int lp0 = PL[p] - VB[i];  // p's place in A_i
                 const int lp1 = p - HS[j];      // p's place in A_j
-                int sib = -1;                   // the sign twin (i, j, -s), if a candidate
-                if (!(e & 1u)) {
-                    if (p + 1 < m && (C[p + 1] & 0x1FFFFFu) == (key | 1u)) sib = p + 1;
-                } else {
-                    if (p >= 1 && (C[p - 1] & 0x1FFFFFu) == (key & ~1u)) sib = p - 1;
+                // the sign twin (i, j, -s), if a candidate: the neighbour on the
+                // side its sign sorts to, read once
+                int sib = -1, wsib = 0;
+                {
+                    const int nb_ = (e & 1u) ? p - 1 : p + 1;
+                    const uint32_t en = (nb_ >= 0 && nb_ < m) ? C[nb_] : 0u;
+                    if (nb_ >= 0 && nb_ < m && (en & 0x1FFFFFu) == (key ^ 1u)) {
+                        sib = nb_;
+                        wsib = cand_c(en) - 1;
+                    }
                 }
                 const int ls1 = sib - HS[j];
-                const int wsib = sib >= 0 ? cand_c(C[sib]) - 1 : 0;
                 const int nint = (n0 - 1) + (n1 - 1 - (sib >= 0 ? 1 : 0));
                 long long X = 0;
                 int inter = 0, nb = 0;
