@@ -604,12 +604,19 @@ struct Engine {
             const int q = base + lane;
             const bool valid = q < m;
             const uint32_t act = __ballot_sync(FULL_MASK, valid);
+            // the neighbours' hi from the adjacent lanes; only the chunk's
+            // edge lanes read the list
+            const uint32_t eq = valid ? C[q] : 0u;
+            int hprev = __shfl_up_sync(FULL_MASK, key_hi(eq), 1);
+            int hnext = __shfl_down_sync(FULL_MASK, key_hi(eq), 1);
             if (valid) {
-                const uint32_t e = C[q];
+                const uint32_t e = eq;
                 const int hi = key_hi(e), lo = key_lo(e);
                 part += cand_c(e) - 1;
-                if (q == 0 || key_hi(C[q - 1]) != hi) HS[hi] = (uint16_t)q;
-                if (q == m - 1 || key_hi(C[q + 1]) != hi) HE[hi] = (uint16_t)(q + 1);
+                if (lane == 0) hprev = q > 0 ? key_hi(C[q - 1]) : -1;
+                if (lane == 31 || q == m - 1) hnext = q + 1 < m ? key_hi(C[q + 1]) : -1;
+                if (hprev != hi) HS[hi] = (uint16_t)q;
+                if (hnext != hi) HE[hi] = (uint16_t)(q + 1);
                 const uint32_t peers = __match_any_sync(act, lo);
                 if ((peers & lt) == 0) LC[lo] = (uint16_t)(LC[lo] + __popc(peers));
             }
