@@ -82,6 +82,19 @@ __device__ __forceinline__ int warp_incl_scan(int v, int lane) {
     return v;
 }
 
+// The warp's argmax of Greedy-Intersections scores, lowest candidate index
+// on ties: each lane holds its best (score, index), index -1 for none.  Every
+// score is at least 2^32 (its immediate-gain term), so "none" maps to 0 and
+// three 32-bit warp reductions (high word, low word, index) replace a 64-bit
+// butterfly.
+__device__ __forceinline__ int warp_argmax_score(long long best_s, int best_q) {
+    const unsigned long long us = best_q >= 0 ? (unsigned long long)best_s : 0ull;
+    const uint32_t hi = (uint32_t)(us >> 32), lo = (uint32_t)us;
+    const uint32_t mhi = __reduce_max_sync(FULL_MASK, hi);
+    const uint32_t mlo = __reduce_max_sync(FULL_MASK, hi == mhi ? lo : 0u);
+    return (int)__reduce_min_sync(FULL_MASK, (hi == mhi && lo == mlo && best_q >= 0) ? (uint32_t)best_q : 0xFFFFFFFFu);
+}
+
 __device__ __forceinline__ long long warp_sum64(long long v) {
 #pragma unroll
     for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(FULL_MASK, v, o);
@@ -249,15 +262,7 @@ __device__ __forceinline__ int gi_shared_select(const uint32_t* C, uint32_t* G, 
             }
         }
     }
-#pragma unroll
-    for (int o = 16; o; o >>= 1) {
-        const long long s2 = __shfl_xor_sync(FULL_MASK, best_s, o);
-        const int q2 = __shfl_xor_sync(FULL_MASK, best_q, o);
-        if (s2 > best_s || (s2 == best_s && (unsigned)q2 < (unsigned)best_q)) {
-            best_s = s2;
-            best_q = q2;
-        }
-    }
+    best_q = warp_argmax_score(best_s, best_q);
     if (lane == 0) *tally += 40u * (unsigned)((m + 127) >> 7) + 18u * (unsigned)m + 2u * (unsigned)ncols;
     __syncwarp();
     return best_q;
@@ -744,15 +749,7 @@ struct Engine {
                 gi_blocks += nb;
             }
         }
-#pragma unroll
-        for (int o = 16; o; o >>= 1) {
-            const long long s2 = __shfl_xor_sync(FULL_MASK, best_s, o);
-            const int q2 = __shfl_xor_sync(FULL_MASK, best_q, o);
-            if (s2 > best_s || (s2 == best_s && (unsigned)q2 < (unsigned)best_q)) {
-                best_s = s2;
-                best_q = q2;
-            }
-        }
+        best_q = warp_argmax_score(best_s, best_q);
         gi_terms = __reduce_add_sync(FULL_MASK, gi_terms);
         gi_blocks = __reduce_add_sync(FULL_MASK, gi_blocks);
         if (lane == 0) {
@@ -923,15 +920,7 @@ struct Engine {
                 gi_blocks += nb;
             }
         }
-#pragma unroll
-        for (int o = 16; o; o >>= 1) {
-            const long long s2 = __shfl_xor_sync(FULL_MASK, best_s, o);
-            const int q2 = __shfl_xor_sync(FULL_MASK, best_q, o);
-            if (s2 > best_s || (s2 == best_s && (unsigned)q2 < (unsigned)best_q)) {
-                best_s = s2;
-                best_q = q2;
-            }
-        }
+        best_q = warp_argmax_score(best_s, best_q);
         gi_terms = __reduce_add_sync(FULL_MASK, gi_terms);
         gi_blocks = __reduce_add_sync(FULL_MASK, gi_blocks);
         if (lane == 0) {
