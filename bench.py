@@ -698,7 +698,7 @@ def main():
     ap.add_argument("--seconds", default="1,10,60", help="cfg2-wallclock: the wall-clock budgets")
     ap.add_argument("--gi-shared", action="store_true",
                     help="Greedy-Intersections with shared coins (an option that changes results)")
-    ap.add_argument("--out", default=os.path.join(ROOT, "gpurun_out"))
+    ap.add_argument("--out", default=os.path.join(ROOT, "bench_out"), help="where the clock samples go")
     args = ap.parse_args()
     os.makedirs(args.out, exist_ok=True)
     if args.impl == "reference":

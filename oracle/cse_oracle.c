@@ -11,7 +11,7 @@
  *   - Greedy-Intersections scores every candidate against every other one,
  *     the O(m^2) loop the paper describes (Section 3.4.2).
  *
- * Readings taken where the paper is silent (all documented in the design doc):
+ * Readings taken where the paper is silent or leaves a choice:
  *   R1 canonical pair (i, j, s): i < j, s = alpha_i * alpha_j, i.e. the
  *      coefficient of x_i normalised to +1 (Section 3.3.1).  Canonical ORDER
  *      is ascending key ((j << 10 | i) << 1) | (s < 0): by the larger index
