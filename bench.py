@@ -291,6 +291,14 @@ def cpu_baseline(s, budget, gi_shared=False):
                      f"{s.budget} steps ({smp.process_steps()} process-steps, {dt:.1f} s)"}
     if budget == s.budget:
         out["best_additions"] = ref.total  # the same search on the CPU: equal to the GPU's by parity
+    # the same oracle on one thread, on a shorter sample (about 4 s)
+    one = copy.copy(s)
+    one.budget = min(budget, 32)
+    t0 = time.perf_counter()
+    O.search_obj(one, n_threads=1, digests=False, flags=O.GI_SHARED_COINS if gi_shared else 0)
+    dt1 = time.perf_counter() - t0
+    out["single_thread"] = {"value": one.process_steps() / dt1, "unit": UNIT, "cores": 1,
+                            "sample": f"first {one.budget} steps ({one.process_steps()} process-steps, {dt1:.1f} s)"}
     return out
 
 

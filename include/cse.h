@@ -12,15 +12,16 @@
  *     (Section 3.2.1);
  *   - each of n_processes independent processes per matrix repeats
  *     Algorithm 1: count canonical signed pairs (x_i + s x_j, i < j), select a
- *     pair with c > 1 by its strategy (g, ga, wr, gr, gi, mix; Section 3.4),
- *     introduce x_k = x_i + s x_j and rewrite every row containing the pair;
+ *     pair with c > 1 by its strategy (g, ga, wr, gr, gi, mix, gp; Sections
+ *     2.2 and 3.4), introduce x_k = x_i + s x_j and rewrite every row
+ *     containing the pair;
  *   - processes share their best substitution prefixes (Section 3.5.2).
  *
  * All arithmetic is exact integer and every random draw is a Philox4x32-10
  * value keyed by (seed, process, step, matrix, purpose), so a search's
  * result is a pure function of (matrices, strategy mix, n_processes, seed,
- * step_budget, share_interval, share_permille, col_cap): it does not depend
- * on launch configuration or on other searches running at the same time.
+ * step_budget and the options that change results): it does not depend on
+ * launch configuration or on other searches running at the same time.
  *
  * Conventions
  *   - Matrices are int8, row-major, rows = expressions, cols = variables.
