@@ -413,7 +413,10 @@ static int build_launch(const std::vector<SearchDev*>& act, int ppc_req, const T
     for (auto& g : ls->groups) {
         g.L = g.gm ? WarpLayout{} : make_layout(g.W, g.cap, g.mmax);
         g.key = ClassKey{g.W, g.gm ? 1 : 0, g.cap, mbucket(g.mmax)};
-        g.ppc = ppc_req ? ppc_req : 2;  // measured best for the (3,3,3:23) workload
+        // measured defaults: 2 processes per CTA on the shared-memory path
+        // ((3,3,3:23) shape), 4 on the HBM path ((6,6,6:153) shape), whose
+        // kernels take the largest L1 carve-out and so fit 8 CTAs per SM
+        g.ppc = ppc_req ? ppc_req : (g.gm ? 4 : 2);
         if (trial && trial->force_ppc) {
             g.ppc = trial->force_ppc;
         } else if (!ppc_req) {

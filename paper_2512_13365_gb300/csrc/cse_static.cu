@@ -182,7 +182,7 @@ extern "C" int cse_search_static(const cse_scheme* s, const cse_strategy_mix* mi
     }
     for (Group& g : groups) {
         g.L = g.gm ? WarpLayout{} : make_layout(g.W, cap, g.mmax);
-        g.ppc = opts.procs_per_cta ? (int)opts.procs_per_cta : 2;
+        g.ppc = opts.procs_per_cta ? (int)opts.procs_per_cta : (g.gm ? 4 : 2);  // as cse_search
         if (!g.gm)
             while (g.ppc > 1 && (long long)g.L.per_warp * g.ppc > smem_max) g.ppc--;
         cudaError_t e = prepare_round(g.W, g.gm, S.gi_shared != 0, g.L, g.ppc);
