@@ -11,6 +11,7 @@ on a bounded sample of the same workload.
 from __future__ import annotations
 
 import argparse
+import datetime
 import json
 import os
 import statistics
@@ -64,13 +65,26 @@ class Clocks:
         self.path = out_path
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap,timestamp")
+        self.t0 = self.t1 = None
         try:
             self.f = open(out_path, "w")
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={q}", "--format=csv,noheader,nounits",
-                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+                                       "-lms", "100"], stdout=self.f, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.p = None
+            return
+        # nvidia-smi takes a moment to start: wait (at most 3 s) for its first
+        # sample so that the timed region is covered from its start
+        deadline = time.time() + 3.0
+        while time.time() < deadline and self.p.poll() is None:
+            if os.path.getsize(out_path) > 0:
+                break
+            time.sleep(0.02)
+
+    def window(self, t0: float, t1: float):
+        """The timed region in host wall-clock seconds (time.time())."""
+        self.t0, self.t1 = t0, t1
 
     def stop(self):
         if self.p is None:
@@ -81,22 +95,33 @@ class Clocks:
         except subprocess.TimeoutExpired:
             self.p.kill()
         self.f.close()
-        sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        rows = []
         for ln in open(self.path):
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue
             try:
-                sm.append(float(f[1]))
-                smax.append(float(f[2]))
+                mhz, mx = float(f[1]), float(f[2])
             except ValueError:
                 continue
-            for n, v in zip(names, f[5:9]):
-                if v.lower().startswith("active"):
-                    reasons.add(n)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+            ts = None
+            if len(f) >= 10:
+                try:
+                    ts = datetime.datetime.strptime(f[9], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                except ValueError:
+                    ts = None
+            rows.append((ts, mhz, mx, [n for n, v in zip(names, f[5:9]) if v.lower().startswith("active")]))
+        scope = "whole run"
+        if self.t0 is not None:
+            # samples inside the timed region, widened by one sampling period
+            inside = [r for r in rows if r[0] is not None and self.t0 - 0.1 <= r[0] <= self.t1 + 0.1]
+            if inside:
+                rows, scope = inside, "timed region"
+        sm = [r[1] for r in rows]
+        reasons = sorted({n for r in rows for n in r[3]})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(r[2] for r in rows) if rows else None,
+                "reasons": reasons, "samples": len(sm), "scope": scope}
 
 
 def max_over_ranks(x: float, device) -> float:
@@ -169,13 +194,14 @@ def run_ours(args):
         r = one()
         r.fetch(0)
         r.free()
+    clocks = Clocks(os.path.join(args.out, f"clocks_rank{rank}.csv"), local)
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
-    clocks = Clocks(os.path.join(args.out, f"clocks_rank{rank}.csv"), local)
     evs = []
     results = []
     t_wall = time.perf_counter()
+    tw0 = time.time()
     for _ in range(args.steps):
         with torch.cuda.stream(stream):
             flush_l2(l2)
@@ -187,7 +213,10 @@ def run_ours(args):
         evs.append((a, b))
         results.append(r)
     torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
     wall = time.perf_counter() - t_wall
+    clocks.window(tw0, time.time())
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in evs]
     round_ms, n_rounds, ops_total = [], 0, 0
@@ -519,6 +548,7 @@ def run_iterations(args):
         one().free()
     torch.cuda.synchronize()
     clocks = Clocks(os.path.join(args.out, "clocks_iter.csv"), 0)
+    tw0 = time.time()
     ms, rec = [], None
     for _ in range(args.steps):
         with torch.cuda.stream(stream):
@@ -535,6 +565,7 @@ def run_iterations(args):
         it, conv, total = r.iterations()
         rec = (steps, ops, round_ms, n_rounds, it, conv, total, r.costs, r.launches()[0])
         r.free()
+    clocks.window(tw0, time.time())
     clk = clocks.stop()
     steps, ops, round_ms, n_rounds, it, conv, total, costs, kernels = rec
     t = statistics.mean(ms)
@@ -619,12 +650,14 @@ def run_wallclock(args):
         gpu(s.budget)
     per_step = min(gpu(s.budget)[0] for _ in range(2)) / s.budget
     clocks = Clocks(os.path.join(args.out, "clocks_wallclock.csv"), 0)
+    tw0 = time.time()
     gpu_rows = []
     for T in budgets_s:
         B = max(s.interval, int(T / per_step) // s.interval * s.interval)
         sec, total, costs = gpu(B)
         gpu_rows.append({"budget_s": T, "steps": B, "device_s": sec, "best_additions": total,
                          "best_additions_per_matrix": costs})
+    clocks.window(tw0, time.time())
     clk = clocks.stop()
     cores = len(os.sched_getaffinity(0))
     smp = copy.copy(s)
@@ -689,7 +722,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="cfg2",

@@ -55,3 +55,37 @@ def test_reference_arm_prints_one_line_on_cpu():
     line = json.loads(out.stdout.strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["value"] > 0
     assert line["cpu_baseline"]["kind"] == "oracle" and line["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_clock_record_keeps_timed_region_samples(tmp_path):
+    """The clock record keeps the nvidia-smi samples time-stamped inside the
+    timed region (widened by one 100 ms period), with their throttle reasons."""
+    import datetime
+    import time
+    sys.path.insert(0, ROOT)
+    import bench
+
+    class Proc:
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            return 0
+
+    now = time.time()
+    path = tmp_path / "clocks.csv"
+    with open(path, "w") as f:
+        for k in range(8):
+            ts = datetime.datetime.fromtimestamp(now + 0.1 * k).strftime("%Y/%m/%d %H:%M:%S.%f")[:-3]
+            cap = "Active" if k == 7 else "Not Active"
+            f.write(f"0, {1500 + 50 * k}, 2070, 500.0, 0x0, Not Active, Not Active, Not Active, {cap}, {ts}\n")
+    c = bench.Clocks.__new__(bench.Clocks)
+    c.path, c.p, c.t0, c.t1 = str(path), Proc(), None, None
+    c.f = open(os.devnull, "w")
+    whole = c.stop()
+    assert whole["samples"] == 8 and whole["reasons"] == ["sw_power_cap"] and whole["scope"] == "whole run"
+    c.f = open(os.devnull, "w")
+    c.window(now + 0.25, now + 0.45)
+    got = c.stop()
+    assert got["samples"] == 4 and got["sm_mhz"] == 1675.0 and got["reasons"] == []
+    assert got["scope"] == "timed region" and got["sm_max_mhz"] == 2070.0
