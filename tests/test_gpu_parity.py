@@ -147,20 +147,26 @@ def test_config2_full_size(cse):
     assert_parity(cse, s)
 
 
+def assert_valid_program(m, lst, cost):
+    """lst is a program for m: its rewritten rows have the reported Cost, and
+    expanding every fresh variable (numpy) reproduces m exactly."""
+    out, c2 = O.apply(m, lst)
+    assert c2 == cost
+    nx = m.shape[1]
+    defs = [np.eye(nx, dtype=np.int64)[v] for v in range(nx)]
+    for e in lst:
+        i, j, sg = O.unentry(e)
+        assert 0 <= i < j < len(defs) and sg in (1, -1)
+        defs.append(defs[i] + sg * defs[j])
+    assert np.array_equal(out.astype(np.int64) @ np.stack(defs), m.astype(np.int64))
+
+
 def test_results_are_valid_programs(cse):
     s = synth.config2(n_proc=256, budget=256)
     r = cse.search_obj(s)
     for k, m in enumerate(s.mats):
         lst, cost, _ = r.fetch(k)
-        out, c2 = O.apply(m, lst)
-        assert c2 == cost
-        # expansion of the fresh variables reproduces the input
-        nx = m.shape[1]
-        defs = [np.eye(nx, dtype=np.int64)[v] for v in range(nx)]
-        for e in lst:
-            i, j, sg = O.unentry(e)
-            defs.append(defs[i] + sg * defs[j])
-        assert np.array_equal(out.astype(np.int64) @ np.stack(defs), m.astype(np.int64))
+        assert_valid_program(m, lst, cost)
 
 
 def test_large_matrices_run_from_hbm(cse):
@@ -282,6 +288,54 @@ def test_large_search_full_process_count_sampled(cse):
     # the published result is the best over all processes: never worse than the sample
     assert all(c <= int(ref.digests[k][sample]["best_cost"].min()) for k, c in enumerate(r.costs))
     r.free()
+
+
+def test_config4_full_size_properties(cse):
+    """The (6,6,6:153)-shaped search at full size: 65536 processes x 3
+    matrices x 2000 steps, in the launch configuration the benchmark uses.
+    Its processes interact at every sharing boundary, so no sample of them
+    can be replayed past the first one; this checks what holds at any size.
+    Each result is a valid program whose Cost is recomputed from its rows and
+    is below A_naive; the best-Cost curve never rises and ends at the result;
+    the result is the lowest per-process record; every process ran every
+    step, and the substitution count is the sum of the processes' counts."""
+    s = synth.config4()
+    r = cse.search_obj(s)
+    steps, sub, _ = r.counters()
+    assert steps == len(s.mats) * s.n_proc * s.budget
+    n_sub = 0
+    for k, m in enumerate(s.mats):
+        lst, cost, _ = r.fetch(k)
+        assert_valid_program(m, lst, cost)
+        assert cost < O.apply(m, [])[1]
+        curve = r.curve(k)
+        assert len(curve) == -(-s.budget // s.interval)
+        assert all(a >= b for a, b in zip(curve, curve[1:])) and curve[-1] == cost
+        p = r.procs(k)
+        assert int(p["best_cost"].min()) == cost
+        assert (p["best_len"] <= s.cap - m.shape[1]).all() and (p["runs"] >= 1).all()
+        assert (p["substeps"] <= s.budget).all()
+        n_sub += int(p["substeps"].sum())
+    assert sub == n_sub
+    r.free()
+
+
+def test_config4_full_process_count_any_launch_shape(cse):
+    """65536 processes per matrix of the (6,6,6:153) shape over 8 sharing
+    rounds: one process per CTA and the default four give identical
+    processes, lists and curves (launch parameters never change results)."""
+    s = synth.config4(budget=256)
+    a = cse.search_obj(s, procs_per_cta=1, trace=True)
+    b = cse.search_obj(s, trace=True)
+    assert a.costs == b.costs and a.lists == b.lists
+    for k in range(len(s.mats)):
+        pa, pb = a.procs(k), b.procs(k)
+        for f in FIELDS:
+            assert np.array_equal(pa[f], pb[f]), (k, f)
+        assert a.curve(k) == b.curve(k)
+    assert a.counters() == b.counters()
+    a.free()
+    b.free()
 
 
 def test_trace_flag_only_changes_the_trajectory_record(cse):
