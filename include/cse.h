@@ -149,6 +149,19 @@ int cse_scheme_load_uvw(int32_t m, int32_t n, int32_t p, int32_t r, const int8_t
 int cse_brent_check(int32_t m, int32_t n, int32_t p, int32_t r, const int8_t* U, const int8_t* V,
                     const int8_t* W, int64_t* violations);
 
+/* The generator behind every random draw of a search: Philox4x32-10 (Salmon,
+ * Moraes, Dror and Shaw, SC'11), keyed by the search seed and counted by
+ * (process, step, matrix and purpose, extra).  The paper leaves the source
+ * of its random choices open (Sections 3.4-3.5); this entry point exposes the
+ * device implementation for verification and for reproducing draws.
+ * out[4q .. 4q+3] = Philox4x32-10(counter = counters[4q .. 4q+3],
+ * key = (seed & 0xFFFFFFFF, seed >> 32)) for 0 <= q < n.  counters and out
+ * are caller-owned host arrays of 4 n uint32; 0 <= n <= 2^24 (n = 0 touches
+ * neither array nor the device).  Synchronous; it allocates and frees its
+ * own device buffers.  Errors: CSE_EINVAL (n out of range, NULL array with
+ * n > 0), CSE_ECUDA. */
+int cse_philox(uint64_t seed, const uint32_t* counters, int64_t n, uint32_t* out);
+
 /* Shape of a loaded matrix. */
 int cse_scheme_shape(const cse_scheme* s, int32_t mat, int32_t* rows, int32_t* cols);
 

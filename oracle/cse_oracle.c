@@ -127,6 +127,10 @@ void oracle_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]
     out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
 }
 
+void oracle_philox_n(const uint32_t* ctr, const uint32_t key[2], int64_t n, uint32_t* out) {
+    for (int64_t q = 0; q < n; q++) oracle_philox(ctr + 4 * q, key, out + 4 * q);
+}
+
 static void draw4(uint64_t seed, int32_t proc, int64_t t, int32_t mat, int32_t purpose,
                   uint32_t extra_hi, uint32_t extra_lo, uint32_t out[4]) {
     uint32_t ctr[4] = {(uint32_t)proc, (uint32_t)t,

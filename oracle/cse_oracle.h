@@ -43,6 +43,8 @@ typedef struct {
 
 /* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11). */
 void oracle_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+/* The same for n counters ctr[4q..4q+3] under one key, into out[4q..4q+3]. */
+void oracle_philox_n(const uint32_t* ctr, const uint32_t key[2], int64_t n, uint32_t* out);
 
 /* A_naive(E) = sum over rows of (nnz - 1)  (Section 3.2.1). */
 int64_t oracle_naive(const int8_t* mat, int32_t rows, int32_t cols);

@@ -60,6 +60,8 @@ def lib():
         u32p = ctypes.POINTER(ctypes.c_uint32)
         L.oracle_philox.argtypes = [u32p, u32p, u32p]
         L.oracle_philox.restype = None
+        L.oracle_philox_n.argtypes = [u32p, u32p, ctypes.c_int64, u32p]
+        L.oracle_philox_n.restype = None
         L.oracle_naive.argtypes = [i8p, ctypes.c_int32, ctypes.c_int32]
         L.oracle_naive.restype = ctypes.c_int64
         L.oracle_pairs.argtypes = [i8p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, u32p, i32p, ctypes.c_int32]
@@ -106,6 +108,15 @@ def philox(ctr: Sequence[int], key: Sequence[int]) -> List[int]:
     o = np.zeros(4, dtype=np.uint32)
     lib().oracle_philox(_p(c, ctypes.c_uint32), _p(k, ctypes.c_uint32), _p(o, ctypes.c_uint32))
     return [int(x) for x in o]
+
+
+def philox_n(ctr: np.ndarray, key: Sequence[int]) -> np.ndarray:
+    """Philox4x32-10 of every row of ctr (n x 4 uint32) under one key."""
+    c = np.ascontiguousarray(ctr, dtype=np.uint32).reshape(-1, 4)
+    k = np.array(key, dtype=np.uint32)
+    o = np.zeros_like(c)
+    lib().oracle_philox_n(_p(c, ctypes.c_uint32), _p(k, ctypes.c_uint32), c.shape[0], _p(o, ctypes.c_uint32))
+    return o
 
 
 def naive(mat: np.ndarray) -> int:

@@ -57,7 +57,7 @@ _lib = None
 # every symbol include/cse.h declares
 EXPORTS = ["cse_opts_default", "cse_scheme_load", "cse_scheme_load_uvw", "cse_scheme_shape", "cse_search",
            "cse_search_batch", "cse_autotune", "cse_tune_interval", "cse_result_fetch", "cse_result_procs", "cse_result_counters", "cse_result_timing",
-           "cse_result_iterations", "cse_result_curve", "cse_result_hybrid", "cse_brent_check", "cse_checkpoint_size",
+           "cse_result_iterations", "cse_result_curve", "cse_result_hybrid", "cse_brent_check", "cse_philox", "cse_checkpoint_size",
            "cse_checkpoint_save", "cse_search_resume", "cse_result_launches",
            "cse_result_free", "cse_scheme_free", "cse_last_error",
            "cse_server_create", "cse_server_submit", "cse_server_cancel", "cse_server_wait", "cse_server_stats",
@@ -95,6 +95,7 @@ def lib() -> ctypes.CDLL:
     L.cse_result_curve.argtypes = [vp, i32, pi32, i32, pi32]
     L.cse_result_hybrid.argtypes = [ctypes.POINTER(vp), i32, pi32, pi64]
     L.cse_brent_check.argtypes = [i32, i32, i32, i32, vp, vp, vp, pi64]
+    L.cse_philox.argtypes = [ctypes.c_uint64, vp, i64, vp]
     L.cse_checkpoint_size.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
     L.cse_checkpoint_save.argtypes = [vp, vp, ctypes.c_size_t]
     L.cse_search_resume.argtypes = [vp, vp, ctypes.c_size_t, i64, ctypes.POINTER(Opts), vp, ctypes.POINTER(vp)]
@@ -285,6 +286,15 @@ def brent_check(m: int, n: int, p: int, U: np.ndarray, V: np.ndarray, W: np.ndar
     out = ctypes.c_int64()
     _check(lib().cse_brent_check(m, n, p, r, U.ctypes.data, V.ctypes.data, W.ctypes.data, ctypes.byref(out)))
     return out.value
+
+
+def philox(seed: int, counters: np.ndarray) -> np.ndarray:
+    """cse_philox: Philox4x32-10 of every row of counters (n x 4 uint32) under
+    the key (seed & 0xFFFFFFFF, seed >> 32), computed on the device."""
+    c = np.ascontiguousarray(counters, dtype=np.uint32).reshape(-1, 4)
+    out = np.zeros_like(c)
+    _check(lib().cse_philox(seed, c.ctypes.data, c.shape[0], out.ctypes.data))
+    return out
 
 
 def make_mix(weights) -> Mix:

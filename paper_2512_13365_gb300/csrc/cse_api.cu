@@ -866,6 +866,23 @@ int cse_brent_check(int32_t m, int32_t n, int32_t p, int32_t r, const int8_t* U,
     return CSE_OK;
 }
 
+int cse_philox(uint64_t seed, const uint32_t* counters, int64_t n, uint32_t* out) {
+    if (n < 0 || n > (int64_t(1) << 24)) return fail(CSE_EINVAL, "n out of range [0, 2^24]");
+    if (n > 0 && (!counters || !out)) return fail(CSE_EINVAL, "NULL counters or out");
+    if (n == 0) return CSE_OK;
+    const size_t bytes = (size_t)n * 16;
+    char* d = nullptr;
+    CUDA_TRY(cudaMalloc(&d, 2 * bytes));
+    uint32_t* dc = reinterpret_cast<uint32_t*>(d);
+    uint32_t* dout = reinterpret_cast<uint32_t*>(d + bytes);
+    cudaError_t e = cudaMemcpy(dc, counters, bytes, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = launch_philox(dc, n, seed, dout, nullptr);
+    if (e == cudaSuccess) e = cudaMemcpy(out, dout, bytes, cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return fail(CSE_ECUDA, std::string("Philox: ") + cudaGetErrorString(e));
+    return CSE_OK;
+}
+
 int cse_scheme_shape(const cse_scheme* s, int32_t mat, int32_t* rows, int32_t* cols) {
     if (!s || mat < 0 || mat >= s->n_mats) return fail(CSE_EINVAL, "bad scheme or matrix index");
     if (rows) *rows = s->rows[mat];

@@ -125,6 +125,8 @@ cudaError_t launch_share(const DevMat* mats, const DevSearch* searches, int n_se
                          cudaStream_t stream);
 cudaError_t launch_brent(const int8_t* U, const int8_t* V, const int8_t* W, int m, int n, int p, int r,
                          unsigned long long* bad, cudaStream_t stream);
+// ctr and out: device arrays of 4 n uint32, 16-byte aligned.
+cudaError_t launch_philox(const uint32_t* ctr, long long n, uint64_t seed, uint32_t* out, cudaStream_t stream);
 // Sets the launch attributes of a round kernel (call outside stream capture).
 cudaError_t prepare_round(int W, bool gm, bool gs, const WarpLayout& L, int procs_per_cta);
 int max_smem_per_block();

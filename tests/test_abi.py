@@ -113,6 +113,17 @@ def test_brent_and_hybrid_argument_checks_without_device(L):
     assert L.cse_result_hybrid(None, 2, best, None) == cse.CSE_EINVAL
 
 
+def test_philox_argument_checks_without_device(L):
+    c = np.zeros(8, np.uint32)
+    assert L.cse_philox(0, c.ctypes.data, -1, c.ctypes.data) == cse.CSE_EINVAL
+    assert L.cse_philox(0, c.ctypes.data, (1 << 24) + 1, c.ctypes.data) == cse.CSE_EINVAL
+    assert L.cse_philox(0, None, 2, c.ctypes.data) == cse.CSE_EINVAL
+    assert L.cse_philox(0, c.ctypes.data, 2, None) == cse.CSE_EINVAL
+    assert b"NULL" in L.cse_last_error()
+    # n = 0 touches neither array nor the device
+    assert L.cse_philox(0, None, 0, None) == cse.CSE_OK
+
+
 def test_resume_rejects_foreign_data_without_device(L):
     bogus = ctypes.create_string_buffer(b"\0" * 4096, 4096)
     h = ctypes.c_void_p()

@@ -56,8 +56,19 @@ def test_philox_known_answers():
     for ln in _lines("philox4x32_10_kat.txt"):
         w = [int(x, 16) for x in ln.split()]
         assert O.philox(w[0:4], w[4:6]) == w[6:10]
+        assert O.philox_n(np.array([w[0:4]] * 3, np.uint32), w[4:6]).tolist() == [w[6:10]] * 3
         n += 1
     assert n == 3
+
+
+def test_philox_batch_equals_single_calls():
+    rng = np.random.default_rng(7)
+    ctr = rng.integers(0, 1 << 32, size=(257, 4), dtype=np.uint64).astype(np.uint32)
+    key = [0x9E3779B9, 0x12345678]
+    got = O.philox_n(ctr, key)
+    assert got.shape == (257, 4)
+    for q in (0, 1, 100, 256):
+        assert got[q].tolist() == O.philox(ctr[q].tolist(), key)
 
 
 # ---------------------------------------------------------------- worked example
