@@ -737,14 +737,16 @@ static void start_run(const search_t* S, int32_t mi, int32_t pi, int64_t t, work
     P->traj = fnv(P->traj, 0xA0000000u | (uint32_t)P->strategy << 12 | (uint32_t)k);
 }
 
+int32_t oracle_mix_strategy(uint32_t u) {
+    uint32_t r = scale(u, 15);
+    return r < 8 ? OR_GI : r < 12 ? OR_GA : r < 14 ? OR_GR : OR_WR;
+}
+
 static int32_t choose(const search_t* S, int32_t mi, int32_t pi, int64_t t, proc_t* P, work_t* wk) {
     int32_t strat = P->strategy;
     uint32_t d[4] = {0, 0, 0, 0};
     if (strat != OR_G && strat != OR_GI && strat != OR_GP) draw4(S->seed, pi, t, mi, PU_STEP, 0, 0, d);
-    if (strat == OR_MIX) {
-        uint32_t r = scale(d[0], 15);
-        strat = r < 8 ? OR_GI : r < 12 ? OR_GA : r < 14 ? OR_GR : OR_WR;
-    }
+    if (strat == OR_MIX) strat = oracle_mix_strategy(d[0]);
     switch (strat) {
         case OR_G: P->ops += 2 * (int64_t)P->m; return sel_g(P->cnt, P->m);
         case OR_GA: P->ops += 2 * (int64_t)P->m; return sel_ga(P->cnt, P->m, d[2]);

@@ -68,6 +68,10 @@ int64_t oracle_apply(const int8_t* mat, int32_t rows, int32_t cols, const int32_
  * wr draw).  Returns the selected index. */
 int32_t oracle_select_basic(int32_t kind, const int32_t* counts, int32_t m, const uint32_t* u);
 
+/* The strategy a Mixed step runs (Section 3.4, reading R7): r = (u * 15) >> 32
+ * of the step's draw u; r in [0,8) gi, [8,12) ga, [12,14) gr, 14 wr. */
+int32_t oracle_mix_strategy(uint32_t u);
+
 /* Greedy-Intersections scores (Section 3.4.2) with explicit coins:
  * coin_bits[p*m + q] is the coin of candidate q as seen from candidate p.
  * Writes score[p] = H(s_p) * 2^32 in exact integers and returns argmax. */

@@ -62,6 +62,8 @@ def lib():
         L.oracle_philox.restype = None
         L.oracle_philox_n.argtypes = [u32p, u32p, ctypes.c_int64, u32p]
         L.oracle_philox_n.restype = None
+        L.oracle_mix_strategy.argtypes = [ctypes.c_uint32]
+        L.oracle_mix_strategy.restype = ctypes.c_int32
         L.oracle_naive.argtypes = [i8p, ctypes.c_int32, ctypes.c_int32]
         L.oracle_naive.restype = ctypes.c_int64
         L.oracle_pairs.argtypes = [i8p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, u32p, i32p, ctypes.c_int32]
@@ -167,6 +169,11 @@ def select_basic(kind: int, counts: Sequence[int], u: Sequence[int]) -> int:
     uu = np.zeros(2, dtype=np.uint32)
     uu[:len(u)] = u
     return int(lib().oracle_select_basic(kind, _p(c, ctypes.c_int32), len(c), _p(uu, ctypes.c_uint32)))
+
+
+def mix_strategy(u: int) -> int:
+    """The strategy (GI, GA, GR or WR) a Mixed step runs for its draw u."""
+    return int(lib().oracle_mix_strategy(u))
 
 
 def gi_scores(keys: Sequence[int], counts: Sequence[int], a: int, b: int, coins: np.ndarray):

@@ -345,6 +345,45 @@ def test_gr_mixes_ga_and_wr():
     assert O.select_basic(O.GR, counts, [2**32 - 1, 2**32 - 1]) == 3
 
 
+def test_mix_step_frequencies():
+    """Mixed picks gi, ga, gr, wr per step with probabilities 8:4:2:1
+    (Section 3.4, reading R7): exact cut points of (u * 15) >> 32 and a
+    chi-square over uniform draws."""
+    want = [O.GI] * 8 + [O.GA] * 4 + [O.GR] * 2 + [O.WR]
+    for r in range(15):
+        first = -(-(r << 32) // 15)           # smallest u with (u * 15) >> 32 == r
+        assert O.mix_strategy(first) == want[r]
+        if r:
+            assert O.mix_strategy(first - 1) == want[r - 1]
+    assert O.mix_strategy(2**32 - 1) == O.WR
+    n = 150000
+    hist = {k: 0 for k in (O.GI, O.GA, O.GR, O.WR)}
+    for x in np.random.default_rng(5).integers(0, 2**32, n, dtype=np.uint64):
+        hist[O.mix_strategy(int(x))] += 1
+    exp = {O.GI: 8 * n / 15, O.GA: 4 * n / 15, O.GR: 2 * n / 15, O.WR: n / 15}
+    chi2 = sum((hist[k] - exp[k]) ** 2 / exp[k] for k in exp)
+    assert chi2 < 16.3  # 3 dof, p = 0.001
+
+
+def test_run_start_strategy_frequencies():
+    """A run's strategy is drawn with probability proportional to its weight
+    (Section 3.5.1; the paper's 8, 4, 2, 1, 0.1, 0, 0.01 as integers x100),
+    except process 0's first run, which is Greedy.  One step per process, so
+    each process's best record names its only run's strategy."""
+    mat = synth.random_matrix(41, 12, 8, 2, 5, n_planted=3)
+    n = 20000
+    r = O.search([mat], synth.PAPER_WEIGHTS, n, 3, 1, 32, 400, 64, n_threads=8)
+    bs = r.digests[0]["best_strategy"]
+    assert bs[0] == O.G
+    hist = np.bincount(bs[1:], minlength=O.N_STRATEGIES)
+    w = np.array(synth.PAPER_WEIGHTS, float)
+    assert hist[O.G] == 0                      # weight 0
+    exp = (n - 1) * w / w.sum()
+    live = w > 0
+    chi2 = float(((hist[live] - exp[live]) ** 2 / exp[live]).sum())
+    assert chi2 < 20.5  # 5 dof, p = 0.001
+
+
 # ---------------------------------------------------------------- gi
 def _gi_cases():
     a = b = None
