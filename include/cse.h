@@ -126,7 +126,9 @@ void cse_opts_default(cse_opts* opts);
  * every row must have at least one nonzero (A_naive counts nnz - 1 per row,
  * Section 3.2.1).  1 <= rows <= 256, 1 <= cols < 512, n_mats <= 16.  The data
  * is copied to the device (synchronously) and packed there into column
- * bitsets.  On success *out owns the device copy. */
+ * bitsets.  A matrix with more than 32767 initial repeated signed pairs
+ * (candidates) is refused with CSE_EINVAL after the packing: the candidate
+ * lists hold at most that many.  On success *out owns the device copy. */
 int cse_scheme_load(const int8_t* const* mats, const int32_t* rows, const int32_t* cols,
                     int32_t n_mats, cse_scheme** out);
 

@@ -824,6 +824,27 @@ int cse_scheme_load(const int8_t* const* mats, const int32_t* rows, const int32_
         delete s;
         return fail(CSE_ECUDA, std::string("scheme ingest: ") + cudaGetErrorString(e));
     }
+    // The candidate arrays hold mmax entries and positions within a
+    // variable's list are 16-bit: a matrix whose initial list is longer than
+    // mmax cannot be searched.  (mmax bounds every later list, since no row
+    // grows, except where it was clipped to 32767.)
+    for (int k = 0; k < n_mats; k++) {
+        int32_t meta[2] = {0, 0};
+        e = cudaMemcpy(meta, s->d_meta0[k], sizeof meta, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) {
+            cudaFree(s->d_block);
+            delete s;
+            return fail(CSE_ECUDA, std::string("scheme ingest: ") + cudaGetErrorString(e));
+        }
+        if (meta[1] > s->mmax[k]) {
+            const int mm = s->mmax[k];
+            cudaFree(s->d_block);
+            delete s;
+            return fail(CSE_EINVAL, "matrix " + std::to_string(k) + ": " + std::to_string(meta[1]) +
+                                        " initial repeated pairs, more than the " + std::to_string(mm) +
+                                        " a candidate list holds");
+        }
+    }
     *out = s;
     return CSE_OK;
 }

@@ -474,6 +474,35 @@ def test_largest_process_count_sampled(cse):
     r.free()
 
 
+def _dense(seed, rows, cols):
+    rng = np.random.default_rng(seed)
+    mat = (rng.integers(0, 2, (rows, cols)) * rng.choice([-1, 1], (rows, cols))).astype(np.int8)
+    mat[:, 0] = 1  # no empty row
+    return mat
+
+
+def test_longest_candidate_lists(cse):
+    """Dense 256-row matrices repeat nearly every signed pair.  With 200
+    columns that is 39800 initial candidates, more than the 32767 a list
+    holds: loading refuses the matrix.  With 181 columns it is 32580: the
+    matrix loads, but its first substitution grows the list to 32937 (the
+    oracle's count), so the search stops with the overflow status instead of
+    continuing on a clipped list."""
+    with pytest.raises(cse.CseError, match="initial repeated pairs") as e:
+        cse.Scheme([_dense(9, 256, 200)])
+    assert e.value.code == cse.CSE_EINVAL
+    mat = _dense(9, 256, 181)
+    assert len(O.pairs(mat)) == 32580
+    s = synth.Search("dense-181", [mat], (0, 0, 0, 0, 0, 1), 1, 1, 3, 2, 400, 512)
+    ref = O.search_obj(s)
+    assert len(O.pairs(O.apply(mat, ref.lists[0][:1])[0])) > 32767
+    r = cse.search_obj(s)   # enqueued; the status is read with the result
+    with pytest.raises(cse.CseError, match="candidate list overflow") as e:
+        r.fetch(0)
+    assert e.value.code == cse.CSE_ESTATE
+    r.free()
+
+
 def test_largest_shapes(cse):
     """Sixteen matrices (the most a scheme may hold), among them 256 rows
     (8 words per column) and 511 columns with the 512-column cap, plus
