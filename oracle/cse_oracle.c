@@ -450,6 +450,50 @@ static int32_t gp_potential(const int8_t* coef, int32_t rows, int32_t ncols, int
     return pot;
 }
 
+/* Greedy-Potential selection: score (c - 1) 2^16 + a N for every candidate,
+ * N its potential and a the run's alpha in units of 2^-16; argmax, lowest key
+ * on ties.  *ops grows by the algorithmic op count (5 per word of a column per
+ * live column of the trial system, plus 8, per candidate). */
+static int32_t gp_select(const int8_t* coef, int32_t rows, int32_t ncols, int32_t stride, const uint32_t* keys,
+                         const int32_t* cnt, int32_t m, int32_t a, int32_t w32, int8_t* trial, uint32_t* scratch,
+                         int64_t* ops) {
+    int32_t best = -1;
+    int64_t best_s = 0;
+    for (int32_t p = 0; p < m; p++) {
+        int32_t live = 0;
+        int32_t pot = gp_potential(coef, rows, ncols, stride, keys[p], trial, scratch, &live);
+        int64_t sc = ((int64_t)(cnt[p] - 1) << 16) + (int64_t)a * pot;
+        if (best < 0 || sc > best_s) {
+            best = p;
+            best_s = sc;
+        }
+        if (ops) *ops += 5 * (int64_t)w32 * live + 8;
+    }
+    return best;
+}
+
+int32_t oracle_gp_select(const int8_t* mat, int32_t rows, int32_t cols, int32_t a) {
+    const int32_t stride = cols + 1;
+    int8_t* coef = (int8_t*)calloc((size_t)rows * (size_t)stride, 1);
+    int8_t* trial = (int8_t*)calloc((size_t)rows * (size_t)stride, 1);
+    for (int32_t r = 0; r < rows; r++)
+        for (int32_t v = 0; v < cols; v++) coef[(int64_t)r * stride + v] = mat[(int64_t)r * cols + v];
+    int64_t occ = max_pair_occurrences(mat, rows, cols, cols);
+    uint32_t* scratch = (uint32_t*)malloc((size_t)(occ + (int64_t)rows * stride + 1) * 4);
+    uint32_t* keys = (uint32_t*)malloc((size_t)(occ + 1) * 4);
+    int32_t* cnt = (int32_t*)malloc((size_t)(occ + 1) * 4);
+    int32_t* nz = (int32_t*)malloc((size_t)(cols + 1) * 4);
+    int32_t m = count_pairs(coef, rows, cols, stride, 2, scratch, nz, keys, cnt, (int32_t)occ + 1);
+    int32_t sel = m > 0 ? gp_select(coef, rows, cols, stride, keys, cnt, m, a, 1, trial, scratch, NULL) : -1;
+    free(coef);
+    free(trial);
+    free(scratch);
+    free(keys);
+    free(cnt);
+    free(nz);
+    return sel;
+}
+
 int32_t oracle_gp_potentials(const int8_t* mat, int32_t rows, int32_t cols, int32_t* pot, int32_t max_out) {
     const int32_t stride = cols + 1;
     int8_t* coef = (int8_t*)calloc((size_t)rows * (size_t)stride, 1);
@@ -689,6 +733,10 @@ static void fold(const search_t* S, const mat_t* M, proc_t* P) {
     }
 }
 
+/* R8: a run's alpha and beta in units of 2^-16, from its draws. */
+int32_t oracle_alpha(uint32_t u) { return (int32_t)scale(u, 32769); }
+int32_t oracle_beta(uint32_t u) { return 32768 + (int32_t)scale(u, 32769); }
+
 static void start_run(const search_t* S, int32_t mi, int32_t pi, int64_t t, work_t* wk) {
     mat_t* M = &S->mats[mi];
     proc_t* P = &M->procs[pi];
@@ -710,8 +758,8 @@ static void start_run(const search_t* S, int32_t mi, int32_t pi, int64_t t, work
             }
         }
     }
-    P->a = (int32_t)scale(run[1], 32769);
-    P->b = 32768 + (int32_t)scale(run[2], 32769);
+    P->a = oracle_alpha(run[1]);
+    P->b = oracle_beta(run[2]);
     /* fresh copy of the original expressions */
     memset(P->coef, 0, (size_t)M->rows * (size_t)S->cap);
     for (int32_t r = 0; r < M->rows; r++)
@@ -770,20 +818,8 @@ static int32_t choose(const search_t* S, int32_t mi, int32_t pi, int64_t t, proc
         }
         case OR_GP: {
             const mat_t* M = &S->mats[mi];
-            int32_t best = -1;
-            int64_t best_s = 0;
-            for (int32_t p = 0; p < P->m; p++) {
-                int32_t live = 0;
-                int32_t pot = gp_potential(P->coef, M->rows, P->ncols, S->cap, P->keys[p], wk->trial, wk->scratch,
-                                           &live);
-                int64_t sc = ((int64_t)(P->cnt[p] - 1) << 16) + (int64_t)P->a * pot;
-                if (best < 0 || sc > best_s) {
-                    best = p;
-                    best_s = sc;
-                }
-                P->ops += 5 * (int64_t)M->w32 * live + 8;
-            }
-            return best;
+            return gp_select(P->coef, M->rows, P->ncols, S->cap, P->keys, P->cnt, P->m, P->a, M->w32, wk->trial,
+                             wk->scratch, &P->ops);
         }
         default: return -1;
     }
@@ -858,7 +894,7 @@ static int search_impl(int32_t n_mats, const int8_t* const* mats, const int32_t*
                        int64_t budget, int32_t interval, int32_t patience, int32_t permille, int32_t cap,
                        uint32_t flags, int32_t n_threads, const int32_t* proc_subset, int32_t n_subset,
                        int64_t* out_cost, int32_t* out_len, int32_t* out_list, oracle_digest* dig,
-                       int64_t* stats, int32_t* curve, int32_t curve_cap) {
+                       int64_t* stats, int32_t* curve, uint64_t* snap_hash, int32_t curve_cap) {
     if (flags & ~(uint32_t)ORACLE_GI_SHARED_COINS) return -1;
     if (n_mats < 1 || n_mats > 256 || n_proc < 1 || budget < 0 || interval < 0 || patience < 0 ||
         permille < 0 || permille > 1000 || cap < 2 || cap > 1024)
@@ -980,6 +1016,15 @@ static int search_impl(int32_t n_mats, const int8_t* const* mats, const int32_t*
                 memcpy(M->snap, M->procs[win].best, (size_t)M->snap_len * sizeof(int32_t));
             }
             if (win >= 0) total += M->procs[win].best_cost;
+            /* the shared list in force after this round (FNV-1a; 0 = none) */
+            if (snap_hash && rd < curve_cap) {
+                uint64_t h = 0;
+                if (M->snap_cost < INT64_MAX) {
+                    h = FNV0;
+                    for (int32_t e = 0; e < M->snap_len; e++) h = fnv(h, (uint32_t)M->snap[e]);
+                }
+                snap_hash[(int64_t)mi * curve_cap + rd] = h;
+            }
             /* the best-Cost curve: the lowest best record after each round */
             if (curve && win >= 0 && rd < curve_cap) curve[(int64_t)mi * curve_cap + rd] = (int32_t)M->procs[win].best_cost;
         }
@@ -1065,7 +1110,7 @@ int oracle_search(int32_t n_mats, const int8_t* const* mats, const int32_t* rows
                   int64_t* out_cost, int32_t* out_len, int32_t* out_list, oracle_digest* dig) {
     if (interval < 1) return -1;
     return search_impl(n_mats, mats, rows, cols, weights7, n_proc, seed, budget, interval, 0, permille, cap, 0,
-                       n_threads, proc_subset, n_subset, out_cost, out_len, out_list, dig, NULL, NULL, 0);
+                       n_threads, proc_subset, n_subset, out_cost, out_len, out_list, dig, NULL, NULL, NULL, 0);
 }
 
 int oracle_search_flags(int32_t n_mats, const int8_t* const* mats, const int32_t* rows,
@@ -1077,7 +1122,16 @@ int oracle_search_flags(int32_t n_mats, const int8_t* const* mats, const int32_t
     if (interval < 1) return -1;
     return search_impl(n_mats, mats, rows, cols, weights7, n_proc, seed, budget, interval, 0, permille, cap,
                        flags, n_threads, proc_subset, n_subset, out_cost, out_len, out_list, dig, NULL, curve,
-                       curve_cap);
+                       NULL, curve_cap);
+}
+
+int oracle_search_snapshots(int32_t n_mats, const int8_t* const* mats, const int32_t* rows,
+                            const int32_t* cols, const uint32_t* weights7, int32_t n_proc, uint64_t seed,
+                            int64_t budget, int32_t interval, int32_t permille, int32_t cap, int32_t n_threads,
+                            int64_t* out_cost, int32_t* curve, uint64_t* snap_hash, int32_t curve_cap) {
+    if (interval < 1) return -1;
+    return search_impl(n_mats, mats, rows, cols, weights7, n_proc, seed, budget, interval, 0, permille, cap, 0,
+                       n_threads, NULL, 0, out_cost, NULL, NULL, NULL, NULL, curve, snap_hash, curve_cap);
 }
 
 int oracle_search_iterations(int32_t n_mats, const int8_t* const* mats, const int32_t* rows,
@@ -1087,5 +1141,6 @@ int oracle_search_iterations(int32_t n_mats, const int8_t* const* mats, const in
                              int32_t* out_list, oracle_digest* dig, int64_t* stats, int32_t* curve,
                              int32_t curve_cap) {
     return search_impl(n_mats, mats, rows, cols, weights7, n_proc, seed, max_iterations, 0, patience, permille,
-                       cap, flags, n_threads, NULL, 0, out_cost, out_len, out_list, dig, stats, curve, curve_cap);
+                       cap, flags, n_threads, NULL, 0, out_cost, out_len, out_list, dig, stats, curve, NULL,
+                       curve_cap);
 }

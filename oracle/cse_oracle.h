@@ -72,6 +72,12 @@ int32_t oracle_select_basic(int32_t kind, const int32_t* counts, int32_t m, cons
  * of the step's draw u; r in [0,8) gi, [8,12) ga, [12,14) gr, 14 wr. */
 int32_t oracle_mix_strategy(uint32_t u);
 
+/* A run's alpha and beta in units of 2^-16 from its draws (Section 3.4.2,
+ * reading R8): a = (u * 32769) >> 32 in [0, 32768], so alpha in [0, 0.5];
+ * b = 32768 + ((u * 32769) >> 32) in [32768, 65536], so beta in [0.5, 1]. */
+int32_t oracle_alpha(uint32_t u);
+int32_t oracle_beta(uint32_t u);
+
 /* Greedy-Intersections scores (Section 3.4.2) with explicit coins:
  * coin_bits[p*m + q] is the coin of candidate q as seen from candidate p.
  * Writes score[p] = H(s_p) * 2^32 in exact integers and returns argmax. */
@@ -83,6 +89,11 @@ int32_t oracle_gi_scores_coins(const uint32_t* keys, const int32_t* counts, int3
  * trial substitution of p, all of which contain the fresh variable.  Writes
  * up to max_out values; returns the number of candidates. */
 int32_t oracle_gp_potentials(const int8_t* mat, int32_t rows, int32_t cols, int32_t* pot, int32_t max_out);
+
+/* The candidate (index in canonical order) Greedy-Potential picks on a
+ * matrix for alpha = a / 2^16: the highest (c - 1) 2^16 + a N, lowest key on
+ * ties; -1 when no pair repeats. */
+int32_t oracle_gp_select(const int8_t* mat, int32_t rows, int32_t cols, int32_t a);
 
 /* Brent equations of a scheme (m,n,p:r) (Section 3.1): U is r x (m n), V is
  * r x (n p), W is r x (m p), row-major, matrix entries in row-major order.
@@ -129,6 +140,14 @@ int oracle_search_flags(int32_t n_mats, const int8_t* const* mats, const int32_t
                         int32_t n_threads, const int32_t* proc_subset, int32_t n_subset,
                         int64_t* out_cost, int32_t* out_len, int32_t* out_list, oracle_digest* dig,
                         int32_t* curve, int32_t curve_cap);
+
+/* The step-clock search with its best-Cost curve and, per matrix and round,
+ * snap_hash[mi * curve_cap + r] = FNV-1a of the shared list in force after
+ * round r (0 while none is published), for r < curve_cap. */
+int oracle_search_snapshots(int32_t n_mats, const int8_t* const* mats, const int32_t* rows,
+                            const int32_t* cols, const uint32_t* weights7, int32_t n_proc, uint64_t seed,
+                            int64_t budget, int32_t interval, int32_t permille, int32_t cap, int32_t n_threads,
+                            int64_t* out_cost, int32_t* curve, uint64_t* snap_hash, int32_t curve_cap);
 
 #ifdef __cplusplus
 }

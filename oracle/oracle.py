@@ -53,7 +53,10 @@ def build(force: bool = False) -> str:
 def lib():
     global _lib
     if _lib is None:
-        L = ctypes.CDLL(build())
+        # ORACLE_LIB: a separately compiled copy of this oracle (the pin
+        # tests load deliberately broken copies through it, to show that the
+        # pins catch each planted mistake)
+        L = ctypes.CDLL(os.environ.get("ORACLE_LIB") or build())
         i8p = ctypes.POINTER(ctypes.c_int8)
         i32p = ctypes.POINTER(ctypes.c_int32)
         i64p = ctypes.POINTER(ctypes.c_int64)
@@ -64,6 +67,12 @@ def lib():
         L.oracle_philox_n.restype = None
         L.oracle_mix_strategy.argtypes = [ctypes.c_uint32]
         L.oracle_mix_strategy.restype = ctypes.c_int32
+        L.oracle_gp_select.argtypes = [i8p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]
+        L.oracle_gp_select.restype = ctypes.c_int32
+        L.oracle_alpha.argtypes = [ctypes.c_uint32]
+        L.oracle_alpha.restype = ctypes.c_int32
+        L.oracle_beta.argtypes = [ctypes.c_uint32]
+        L.oracle_beta.restype = ctypes.c_int32
         L.oracle_naive.argtypes = [i8p, ctypes.c_int32, ctypes.c_int32]
         L.oracle_naive.restype = ctypes.c_int64
         L.oracle_pairs.argtypes = [i8p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, u32p, i32p, ctypes.c_int32]
@@ -95,6 +104,11 @@ def lib():
                                           ctypes.c_int32, ctypes.c_uint32, ctypes.c_int32, i32p, ctypes.c_int32,
                                           i64p, i32p, i32p, ctypes.POINTER(Digest), i32p, ctypes.c_int32]
         L.oracle_search_flags.restype = ctypes.c_int
+        L.oracle_search_snapshots.argtypes = [ctypes.c_int32, ctypes.POINTER(i8p), i32p, i32p, u32p, ctypes.c_int32,
+                                              ctypes.c_uint64, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                              ctypes.c_int32, ctypes.c_int32, i64p, i32p,
+                                              ctypes.POINTER(ctypes.c_uint64), ctypes.c_int32]
+        L.oracle_search_snapshots.restype = ctypes.c_int
         L.oracle_search_iterations.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -176,6 +190,11 @@ def mix_strategy(u: int) -> int:
     return int(lib().oracle_mix_strategy(u))
 
 
+def alpha_beta(u_alpha: int, u_beta: int):
+    """A run's (a, b): alpha and beta in units of 2^-16 from its two draws."""
+    return int(lib().oracle_alpha(u_alpha)), int(lib().oracle_beta(u_beta))
+
+
 def gi_scores(keys: Sequence[int], counts: Sequence[int], a: int, b: int, coins: np.ndarray):
     k = np.ascontiguousarray(np.array(keys, dtype=np.uint32))
     c = np.ascontiguousarray(np.array(counts, dtype=np.int32))
@@ -185,6 +204,13 @@ def gi_scores(keys: Sequence[int], counts: Sequence[int], a: int, b: int, coins:
     best = lib().oracle_gi_scores_coins(_p(k, ctypes.c_uint32), _p(c, ctypes.c_int32), m, a, b,
                                         _p(cb, ctypes.c_uint8), _p(sc, ctypes.c_int64))
     return int(best), [int(x) for x in sc]
+
+
+def gp_select(mat: np.ndarray, a: int) -> int:
+    """Index (canonical order) of the candidate Greedy-Potential picks for
+    alpha = a / 2^16; -1 if no pair repeats."""
+    m = np.ascontiguousarray(mat, dtype=np.int8)
+    return int(lib().oracle_gp_select(_p(m, ctypes.c_int8), m.shape[0], m.shape[1], a))
 
 
 def gp_potentials(mat: np.ndarray) -> List[int]:
@@ -255,6 +281,30 @@ def search(mats: Sequence[np.ndarray], weights, n_proc: int, seed: int, budget: 
     rounds = min(CURVE_POINTS, (budget + interval - 1) // interval)
     r.curve = [[int(v) for v in curve[k, :rounds]] for k in range(n)]
     return r
+
+
+def search_snapshots(mats: Sequence[np.ndarray], weights, n_proc: int, seed: int, budget: int, interval: int,
+                     permille: int, cap: int, n_threads: int = 1):
+    """Step-clock search: (costs, best-Cost curve, hash of the shared list in
+    force after each round; 0 while none), per matrix."""
+    ms = [np.ascontiguousarray(m, dtype=np.int8) for m in mats]
+    n = len(ms)
+    ptrs = (ctypes.POINTER(ctypes.c_int8) * n)(*[_p(m, ctypes.c_int8) for m in ms])
+    rows = np.array([m.shape[0] for m in ms], dtype=np.int32)
+    cols = np.array([m.shape[1] for m in ms], dtype=np.int32)
+    w = np.zeros(N_STRATEGIES, dtype=np.uint32)
+    w[:len(weights)] = list(weights)
+    cost = np.zeros(n, dtype=np.int64)
+    curve = np.full((n, CURVE_POINTS), -1, dtype=np.int32)
+    snap = np.zeros((n, CURVE_POINTS), dtype=np.uint64)
+    rc = lib().oracle_search_snapshots(n, ptrs, _p(rows, ctypes.c_int32), _p(cols, ctypes.c_int32),
+                                       _p(w, ctypes.c_uint32), n_proc, seed, budget, interval, permille, cap,
+                                       n_threads, _p(cost, ctypes.c_int64), _p(curve, ctypes.c_int32),
+                                       _p(snap, ctypes.c_uint64), CURVE_POINTS)
+    if rc != 0:
+        raise ValueError(f"oracle_search_snapshots rejected its arguments (rc={rc})")
+    rounds = min(CURVE_POINTS, (budget + interval - 1) // interval)
+    return [int(x) for x in cost], curve[:, :rounds].tolist(), snap[:, :rounds]
 
 
 def search_iterations(mats: Sequence[np.ndarray], weights, n_proc: int, seed: int, max_iterations: int,

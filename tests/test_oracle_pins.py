@@ -249,6 +249,38 @@ def test_sharing_replay_closed_form():
     assert r0.digests[0][0]["runs"] == 6
 
 
+def test_share_probability():
+    """A run starts from a shared prefix with probability permille / 1000
+    (Section 3.5.2; the paper's 40%).  On the worked example with Greedy, a
+    fresh run takes 2 steps and a shared one (k = 1) 1 step, so after the
+    first run the mean run length is 2 - p: the share fraction follows from
+    the run counts of 2000 processes over 200 steps."""
+    mat, *_ = _example()
+    for permille in (400, 40, 1000):
+        r = O.search([mat], (0, 0, 0, 0, 0, 1), 2000, 0, 202, 1, permille, 16, n_threads=8)
+        runs = r.digests[0]["runs"].mean()
+        p_hat = 2 - 200 / (runs - 1)
+        assert abs(p_hat - permille / 1000) < 0.01, (permille, p_hat)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_shared_list_changes_only_when_beaten(seed):
+    """The shared solution is replaced only by a strictly lower Cost
+    (Section 3.5.2, reading R12): after every round whose lowest best Cost is
+    unchanged the shared list is the same list, although other processes
+    reach that Cost with other lists; when the Cost drops the list changes."""
+    mat = synth.random_matrix(500 + seed, 16, 8, 2, 5, n_planted=4)
+    w = (0, 1, 0, 1, 0, 0)    # ga and wr: many different lists of equal Cost
+    cost, curve, snap = O.search_snapshots([mat], w, 256, seed, 320, 8, 400, 64, n_threads=8)
+    c, h = curve[0], snap[0]
+    assert c[-1] == cost[0] and all(x > 0 for x in h)
+    for r in range(1, len(c)):
+        if c[r] == c[r - 1]:
+            assert h[r] == h[r - 1], r
+        else:
+            assert c[r] < c[r - 1] and h[r] != h[r - 1], r
+
+
 def test_column_cap_ends_runs():
     mat = synth.random_matrix(11, 16, 6, 4, 6, n_planted=6, frac=(0.4, 0.6))
     # cap = n_x + 2: at most two substitutions per run
@@ -363,6 +395,32 @@ def test_mix_step_frequencies():
     exp = {O.GI: 8 * n / 15, O.GA: 4 * n / 15, O.GR: 2 * n / 15, O.WR: n / 15}
     chi2 = sum((hist[k] - exp[k]) ** 2 / exp[k] for k in exp)
     assert chi2 < 16.3  # 3 dof, p = 0.001
+
+
+def test_alpha_and_beta_reach_both_ends():
+    """alpha in [0, 0.5] and beta in [0.5, 1] (Section 3.4.2) on the 2^-16 grid
+    (reading R8): the lowest and highest draws reach both closed ends, and
+    the values rise with the draw."""
+    assert O.alpha_beta(0, 0) == (0, 32768)
+    assert O.alpha_beta(2**32 - 1, 2**32 - 1) == (32768, 65536)
+    u = np.sort(np.random.default_rng(3).integers(0, 2**32, 2000, dtype=np.uint64))
+    ab = np.array([O.alpha_beta(int(x), int(x)) for x in u])
+    assert (np.diff(ab[:, 0]) >= 0).all() and (np.diff(ab[:, 1]) >= 0).all()
+    assert (ab[:, 1] - ab[:, 0] == 32768).all()
+
+
+def test_best_record_changes_only_on_strict_improvement():
+    """A process keeps the first run that reached its lowest Cost (reading
+    R11: only a strictly lower Cost replaces the best record).  Without
+    sharing, a search 10x longer whose best Cost is the same must keep the
+    same best list, although many later runs tie with it."""
+    mat = synth.random_matrix(77, 10, 7, 2, 5, n_planted=3)
+    w = (0, 1, 0, 0, 0, 0)   # ga: uniform among the tied maxima, so tying runs differ
+    short = O.search([mat], w, 32, 0, 60, 1000, 0, 64).digests[0]
+    long = O.search([mat], w, 32, 0, 600, 1000, 0, 64).digests[0]
+    same = short["best_cost"] == long["best_cost"]
+    assert same.sum() >= 8 and (long["runs"] > short["runs"] + 5).all()
+    assert (short["best_hash"][same] == long["best_hash"][same]).all()
 
 
 def test_run_start_strategy_frequencies():
@@ -499,6 +557,19 @@ def test_gp_hand_derived_potentials():
     assert O.unkey(cand[_gp_pick(counts, pots, 1)][0]) == picks["pick_positive"]
     assert O.unkey(cand[_gp_pick(counts, pots, 32768)][0]) == picks["pick_positive"]
     assert O.unkey(cand[_gp_pick(counts, pots, 0)][0]) == picks["pick_zero"]
+    # the oracle's own selection makes the hand-derived picks
+    assert O.unkey(cand[O.gp_select(mat, 1)][0]) == picks["pick_positive"]
+    assert O.unkey(cand[O.gp_select(mat, 32768)][0]) == picks["pick_positive"]
+    assert O.unkey(cand[O.gp_select(mat, 0)][0]) == picks["pick_zero"]
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_gp_with_alpha_zero_is_greedy(seed):
+    """alpha = 0 leaves only the (c - 1) term: Greedy-Potential picks what
+    Greedy picks (highest c, lowest key)."""
+    mat = synth.random_matrix(900 + seed, 14, 8, 2, 5, n_planted=3)
+    counts = [c for _, c in O.pairs(mat)]
+    assert O.gp_select(mat, 0) == O.select_basic(O.G, counts, [])
 
 
 def _numpy_potential(mat, i, j, s):
