@@ -333,9 +333,19 @@ typedef struct {
     int32_t m;
     /* shared mode (R9b): one coin per candidate q per step, seen by every p */
     int32_t shared, ncols;
+    /* if not NULL: record[p * m + q] = every coin drawn (test output) */
+    uint8_t* record;
 } coin_src;
 
+static int coin_draw(coin_src* cs, int32_t p, int32_t q, int32_t slot, int32_t rho);
+
 static int coin_at(coin_src* cs, int32_t p, int32_t q, int32_t slot, int32_t rho) {
+    int c = coin_draw(cs, p, q, slot, rho);
+    if (cs->record) cs->record[(int64_t)p * cs->m + q] = (uint8_t)c;
+    return c;
+}
+
+static int coin_draw(coin_src* cs, int32_t p, int32_t q, int32_t slot, int32_t rho) {
     if (cs->bits) return cs->bits[(int64_t)p * cs->m + q] != 0;
     if (cs->shared) {
         uint32_t o[4];
@@ -403,6 +413,24 @@ static int32_t sel_gi(const uint32_t* keys, const int32_t* cnt, int32_t m, uint3
     if (cs->shared) ops = 40 * (int64_t)((m + 127) / 128) + 18 * (int64_t)m + 2 * (int64_t)cs->ncols;
     if (ops_out) *ops_out = ops;
     return best;
+}
+
+int32_t oracle_gi_philox_coins(const uint32_t* keys, const int32_t* counts, int32_t m, uint64_t seed,
+                               int32_t proc, int64_t t, int32_t mat, int32_t shared, uint8_t* coins) {
+    coin_src cs;
+    memset(&cs, 0, sizeof cs);
+    cs.seed = seed;
+    cs.proc = proc;
+    cs.mat = mat;
+    cs.t = t;
+    cs.keys = keys;
+    cs.block_p = -1;
+    cs.shared = shared != 0;
+    cs.m = m;
+    cs.record = coins;
+    if (m <= 0) return -1;
+    memset(coins, 255, (size_t)m * (size_t)m);
+    return sel_gi(keys, counts, m, 1, 32768, &cs, NULL, NULL);
 }
 
 int32_t oracle_gi_scores_coins(const uint32_t* keys, const int32_t* counts, int32_t m,

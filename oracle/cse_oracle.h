@@ -84,6 +84,14 @@ int32_t oracle_beta(uint32_t u);
 int32_t oracle_gi_scores_coins(const uint32_t* keys, const int32_t* counts, int32_t m,
                                uint32_t a, uint32_t b, const uint8_t* coin_bits, int64_t* score);
 
+/* The Greedy-Intersections coins a process draws at step t for a candidate
+ * list (reading R9: Philox, independent per scored candidate p and
+ * intersecting candidate q; shared != 0: R9b, one coin per q and step):
+ * coins[p * m + q] = the coin of q in p's score, 255 where p draws none
+ * (q = p or q disjoint from p).  Returns the argmax of the scores. */
+int32_t oracle_gi_philox_coins(const uint32_t* keys, const int32_t* counts, int32_t m, uint64_t seed,
+                               int32_t proc, int64_t t, int32_t mat, int32_t shared, uint8_t* coins);
+
 /* Greedy-Potential potential of every candidate (c >= 2, canonical order) of
  * a matrix: N_p = number of signed pairs that occur at least twice after a
  * trial substitution of p, all of which contain the fresh variable.  Writes

@@ -67,6 +67,10 @@ def lib():
         L.oracle_philox_n.restype = None
         L.oracle_mix_strategy.argtypes = [ctypes.c_uint32]
         L.oracle_mix_strategy.restype = ctypes.c_int32
+        L.oracle_gi_philox_coins.argtypes = [u32p, i32p, ctypes.c_int32, ctypes.c_uint64, ctypes.c_int32,
+                                             ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                             ctypes.POINTER(ctypes.c_uint8)]
+        L.oracle_gi_philox_coins.restype = ctypes.c_int32
         L.oracle_gp_select.argtypes = [i8p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]
         L.oracle_gp_select.restype = ctypes.c_int32
         L.oracle_alpha.argtypes = [ctypes.c_uint32]
@@ -193,6 +197,19 @@ def mix_strategy(u: int) -> int:
 def alpha_beta(u_alpha: int, u_beta: int):
     """A run's (a, b): alpha and beta in units of 2^-16 from its two draws."""
     return int(lib().oracle_alpha(u_alpha)), int(lib().oracle_beta(u_beta))
+
+
+def gi_philox_coins(keys: Sequence[int], counts: Sequence[int], seed: int, proc: int, t: int, mat: int,
+                    shared: bool = False) -> np.ndarray:
+    """The m x m Greedy-Intersections coins a process draws at step t
+    (255 where none is drawn)."""
+    k = np.ascontiguousarray(np.array(keys, dtype=np.uint32))
+    c = np.ascontiguousarray(np.array(counts, dtype=np.int32))
+    m = len(k)
+    out = np.zeros((m, m), dtype=np.uint8)
+    lib().oracle_gi_philox_coins(_p(k, ctypes.c_uint32), _p(c, ctypes.c_int32), m, seed, proc, t, mat,
+                                 1 if shared else 0, _p(out, ctypes.c_uint8))
+    return out
 
 
 def gi_scores(keys: Sequence[int], counts: Sequence[int], a: int, b: int, coins: np.ndarray):

@@ -87,6 +87,14 @@ MUTANTS = [
      "int64_t sc = (int64_t)a * pot;"),
     ("snapshot_replaced_on_ties", "Section 3.5.2: the shared solution changes only when beaten",
      "M->procs[win].best_cost < M->snap_cost", "M->procs[win].best_cost <= M->snap_cost"),
+    ("gi_coins_same_every_step", "reading R9: coins drawn afresh at every step",
+     "draw4(cs->seed, cs->proc, cs->t, cs->mat, PU_GI, (uint32_t)blk, cs->keys[p], cs->block);",
+     "draw4(cs->seed, cs->proc, 0, cs->mat, PU_GI, (uint32_t)blk, cs->keys[p], cs->block);"),
+    ("gi_coins_shared_by_all_p", "reading R9: coins independent per scored candidate p",
+     "draw4(cs->seed, cs->proc, cs->t, cs->mat, PU_GI, (uint32_t)blk, cs->keys[p], cs->block);",
+     "draw4(cs->seed, cs->proc, cs->t, cs->mat, PU_GI, (uint32_t)blk, 0, cs->block);"),
+    ("gi_coin_biased", "Section 3.4.2: each intersecting term kept with probability 1/2",
+     "return (int)((w >> (rho & 63)) & 1u);", "return (int)(((w >> (rho & 63)) & 3u) != 0);"),
     ("patience_one_late", "Section 4: stop after 10 iterations without improvement",
      "if (patience > 0 && stale >= patience) break;", "if (patience > 0 && stale > patience) break;"),
 ]

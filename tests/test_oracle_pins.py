@@ -524,6 +524,59 @@ def test_gi_score_structure(seed):
         assert s0[p] == ((counts[p] - 1) << 32) + a * (d << 16)
 
 
+def _agree_half(a, b):
+    """Two arrays of coins agree about half the time (5 sigma)."""
+    a, b = np.asarray(a, float), np.asarray(b, float)
+    n = a.size
+    assert n > 1000
+    assert abs((a == b).mean() - 0.5) < 5 * 0.5 / np.sqrt(n)
+
+
+def test_gi_coins_are_fair_independent_bits():
+    """Reading R9 (Section 3.4.2 fixes only that each intersecting term is
+    kept with probability 1/2): exactly the intersecting pairs (q != p,
+    sharing a variable) draw a coin; the coins are fair, and the coin of
+    (p, q) is independent of (q, p), of another q of the same p (same Philox
+    block), of the next step and of another process."""
+    mat = synth.random_matrix(610, 18, 9, 2, 5, n_planted=5)
+    keys, counts = zip(*O.pairs(mat))
+    m = len(keys)
+    var = [set(O.unkey(k)[:2]) for k in keys]
+    inter = np.array([[p != q and bool(var[p] & var[q]) for q in range(m)] for p in range(m)])
+    grid = {(pr, t): O.gi_philox_coins(keys, counts, 7, pr, t, 0) for pr in range(12) for t in range(12)}
+    for c in grid.values():
+        assert np.array_equal(c != 255, inter)
+    allc = np.concatenate([c[inter] for c in grid.values()]).astype(float)
+    assert abs(allc.mean() - 0.5) < 5 * 0.5 / np.sqrt(allc.size)
+    pq = np.argwhere(inter)
+    _agree_half(np.concatenate([c[pq[:, 0], pq[:, 1]] for c in grid.values()]),
+                np.concatenate([c[pq[:, 1], pq[:, 0]] for c in grid.values()]))
+    nxt = [(p, q, q2) for p in range(m) for q, q2 in zip(np.nonzero(inter[p])[0], np.nonzero(inter[p])[0][1:])]
+    _agree_half(np.concatenate([[c[p, q] for p, q, _ in nxt] for c in grid.values()]),
+                np.concatenate([[c[p, q2] for p, _, q2 in nxt] for c in grid.values()]))
+    for dp, dt in ((0, 1), (1, 0)):
+        a = np.concatenate([grid[(pr, t)][inter] for pr in range(11) for t in range(11)])
+        b = np.concatenate([grid[(pr + dp, t + dt)][inter] for pr in range(11) for t in range(11)])
+        _agree_half(a, b)
+
+
+def test_shared_gi_coins_are_one_per_candidate():
+    """Reading R9b (the shared-coin option): every p that intersects q sees
+    the same coin of q, and those coins are fair across steps."""
+    mat = synth.random_matrix(611, 18, 9, 2, 5, n_planted=5)
+    keys, counts = zip(*O.pairs(mat))
+    seen = []
+    for t in range(300):
+        c = O.gi_philox_coins(keys, counts, 7, 3, t, 0, shared=True)
+        for q in range(len(keys)):
+            col = c[:, q][c[:, q] != 255]
+            if col.size:
+                assert (col == col[0]).all()
+                seen.append(col[0])
+    seen = np.array(seen, float)
+    assert abs(seen.mean() - 0.5) < 5 * 0.5 / np.sqrt(seen.size)
+
+
 # ---------------------------------------------------------------- Greedy-Potential
 def _gp_fixture():
     mat, gp, picks = [], [], {}
