@@ -371,6 +371,11 @@ int cse_server_wait(cse_server* s, uint64_t ticket, int64_t timeout_us, cse_resu
  * number of completed requests. */
 int cse_server_stats(cse_server* s, double* p50_ms, double* p99_ms, double* steps_per_s, int32_t* completed);
 
+/* The most searches that ran together in one round, and the rounds run so
+ * far (either pointer may be NULL).  With a budget that no two requests fit
+ * in together, the peak is 1. */
+int cse_server_peak(cse_server* s, int32_t* max_active_searches, int32_t* rounds);
+
 /* Stops the worker (requests not yet finished are dropped) and frees the
  * server.  No other call on it may be in progress. */
 void cse_server_free(cse_server* s);

@@ -61,6 +61,7 @@ EXPORTS = ["cse_opts_default", "cse_scheme_load", "cse_scheme_load_uvw", "cse_sc
            "cse_checkpoint_save", "cse_search_resume", "cse_result_launches",
            "cse_result_free", "cse_scheme_free", "cse_last_error",
            "cse_server_create", "cse_server_submit", "cse_server_cancel", "cse_server_wait", "cse_server_stats",
+           "cse_server_peak",
            "cse_server_free",
            "cse_search_static"]
 
@@ -115,6 +116,7 @@ def lib() -> ctypes.CDLL:
     L.cse_server_submit.argtypes = [vp, vp, ctypes.POINTER(Mix), i32, u64, i64, ctypes.POINTER(ctypes.c_uint64)]
     L.cse_server_wait.argtypes = [vp, ctypes.c_uint64, i64, ctypes.POINTER(vp)]
     L.cse_server_cancel.argtypes = [vp, ctypes.c_uint64]
+    L.cse_server_peak.argtypes = [vp, pi32, pi32]
     L.cse_server_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                    ctypes.POINTER(ctypes.c_double), pi32]
     L.cse_search_static.argtypes = [vp, ctypes.POINTER(Mix), i32, u64, i64, ctypes.POINTER(Opts), vp, vp, vp]
@@ -452,6 +454,12 @@ class Server:
         a, b, c, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_double(), ctypes.c_int32()
         _check(lib().cse_server_stats(self.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(n)))
         return {"p50_ms": a.value, "p99_ms": b.value, "steps_per_s": c.value, "completed": n.value}
+
+    def peak(self):
+        """cse_server_peak: (most searches active in one round, rounds run)."""
+        a, b = ctypes.c_int32(), ctypes.c_int32()
+        _check(lib().cse_server_peak(self.handle, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
 
     def free(self):
         if getattr(self, "handle", None):

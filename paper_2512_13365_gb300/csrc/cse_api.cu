@@ -1332,10 +1332,12 @@ static void server_loop(cse_server* sv) {
             std::unique_lock<std::mutex> lk(sv->mu);
             sv->cv_work.wait(lk, [&] { return sv->stop || !sv->pending.empty() || !sv->active.empty(); });
             if (sv->stop) break;
-            // FIFO admission by device footprint, at a round boundary
+            // FIFO admission by device footprint, at a round boundary; a
+            // request that does not fit waits, unless nothing else would run
             while (!sv->pending.empty()) {
                 Request* q = sv->pending.front();
-                if (!sv->active.empty() && (sv->used_bytes + q->bytes > sv->hbm_budget ||
+                const bool others = !sv->active.empty() || !admitted.empty();
+                if (others && (sv->used_bytes + q->bytes > sv->hbm_budget ||
                                             sv->active_units + q->units > sv->max_units ||
                                             sv->used_smem + q->smem > sv->smem_budget))
                     break;
@@ -1555,6 +1557,14 @@ int cse_server_stats(cse_server* sv, double* p50_ms, double* p99_ms, double* ste
         *steps_per_s = s > 0 ? (double)sv->steps_done / s : 0.0;
     }
     if (completed) *completed = (int32_t)v.size();
+    return CSE_OK;
+}
+
+int cse_server_peak(cse_server* sv, int32_t* max_active_searches, int32_t* rounds) {
+    if (!sv) return fail(CSE_EINVAL, "NULL server");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    if (max_active_searches) *max_active_searches = sv->max_active;
+    if (rounds) *rounds = sv->rounds_run;
     return CSE_OK;
 }
 

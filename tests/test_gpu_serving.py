@@ -69,8 +69,28 @@ def test_admission_by_memory_budget(cse):
         alone = cse.search(sc, s.weights, s.n_proc, s.seed, s.budget, 16, s.permille, 512)
         _same(cse, r, alone, len(s.mats))
         _same(cse, r2, alone, len(s.mats))
+    # one search at a time, also for requests queued together while the
+    # server was idle
+    assert sv.peak()[0] == 1 and sv2.peak()[0] == 1
     sv.free()
     sv2.free()
+
+
+def test_idle_server_admits_a_burst_within_budget(cse):
+    """Requests queued together while the server is idle are admitted up to
+    the budget, not all at once: a process cap of two requests' worth keeps
+    at most two searches on the device."""
+    reqs = _requests(6, 32, 48)
+    schemes = [cse.Scheme(s.mats) for s in reqs]
+    units = max(len(s.mats) * s.n_proc for s in reqs)
+    sv = cse.Server(interval=16, cap=512, max_active_processes=2 * units)
+    tickets = [sv.submit(sc, s.weights, s.n_proc, s.seed, s.budget) for s, sc in zip(reqs, schemes)]
+    for s, sc, t in zip(reqs, schemes, tickets):
+        _same(cse, sv.wait(t), cse.search(sc, s.weights, s.n_proc, s.seed, s.budget, 16, s.permille, 512),
+              len(s.mats))
+    peak, rounds = sv.peak()
+    assert 1 <= peak <= 2 and rounds >= 6
+    sv.free()
 
 
 def test_wait_timeout_and_bad_requests(cse):
