@@ -482,6 +482,7 @@ def run_serving(args):
         totals = [sv.wait(t).total for t, _ in tickets]
         wall = time.perf_counter() - t0
         st = sv.stats()
+        st["peak"] = sv.peak()[0]
         sv.free()
         return st, wall, totals
 
@@ -508,12 +509,14 @@ def run_serving(args):
     st, wall, tot_s = serve()
     st_a, wall_a, tot_a = alone()
     assert tot_s == tot_a
+    peak = st["peak"]
     line = {
         "metric": METRIC, "value": psteps / wall, "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 0,
         "ms_per_step": wall * 1000.0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "int32", "data": "synthetic",
         "config": {"workload": f"serving: {len(reqs)} Poisson requests at 50/s (config 5)", "n_processes": 2048,
-                   "step_budget": reqs[0][1].budget, "share_interval": 32, "col_cap": 512},
+                   "step_budget": reqs[0][1].budget, "share_interval": 32, "col_cap": 512,
+                   "admission": "library default limits (64 waves of resident warps)", "peak_active_searches": peak},
         "served": {"p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "process_steps_per_s": st["steps_per_s"],
                    "wall_s": wall},
         "one_launch_per_request": {"p50_ms": st_a["p50_ms"], "p99_ms": st_a["p99_ms"],

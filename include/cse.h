@@ -334,11 +334,13 @@ void cse_scheme_free(cse_scheme* s);
  * every round boundary the worker admits queued requests while (a) the
  * device memory of all active searches stays within hbm_budget_bytes (0 = no
  * limit), (b) their processes (all matrices) stay within
- * max_active_processes (0 = eight waves of one process per resident warp,
- * 8 x 32 x SMs) and (c) the shared-memory footprint of their process pools
+ * max_active_processes (0 = 64 waves of one process per resident warp,
+ * 64 x 32 x SMs) and (c) the shared-memory footprint of their process pools
  * (each process of a matrix on the shared-memory path holds one slice) stays
- * within eight waves of the GPU's shared memory (8 x SMs x per-SM capacity);
- * a request that exceeds a limit alone runs alone.  Then it
+ * within as many waves of the GPU's shared memory as the process cap has
+ * waves (waves x SMs x per-SM capacity); a request that exceeds a limit
+ * alone runs alone.  A larger cap raises throughput at some cost in
+ * time-to-result.  Then it
  * runs one round (one kernel per class of matrices over every active search,
  * then the share kernel).  Admitted searches run concurrently with those
  * already on the device and leave as soon as their step budget is done.  Each

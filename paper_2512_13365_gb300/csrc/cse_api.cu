@@ -89,6 +89,7 @@ struct ClassKey {
 };
 std::mutex g_tune_mu;
 constexpr size_t kServerMaxPending = 1 << 16;
+constexpr int64_t kServerWaves = 64;  // default cap on active processes, in waves of resident warps
 std::map<ClassKey, int> g_tuned_ppc;
 
 int mbucket(int mmax) {
@@ -1441,11 +1442,15 @@ int cse_server_create(const cse_opts* opts_in, uint64_t hbm_budget_bytes, int64_
     cudaGetDevice(&sv->device);
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, sv->device);
-    // default: eight waves of one process per resident warp (32 per SM)
-    sv->max_units = max_active_processes > 0 ? max_active_processes : (int64_t)8 * 32 * std::max(sms, 1);
+    // a wave: one process per resident warp (32 per SM).  The process cap
+    // (default kServerWaves waves) also sets the shared-memory cap: as many
+    // waves of the GPU's shared memory.
+    const int64_t wave = (int64_t)32 * std::max(sms, 1);
+    sv->max_units = max_active_processes > 0 ? max_active_processes : (int64_t)kServerWaves * wave;
+    const int64_t waves = std::max<int64_t>(1, (sv->max_units + wave - 1) / wave);
     int smem_sm = 0;
     cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, sv->device);
-    sv->smem_budget = (uint64_t)8 * (uint64_t)std::max(sms, 1) * (uint64_t)std::max(smem_sm, 1);
+    sv->smem_budget = (uint64_t)waves * (uint64_t)std::max(sms, 1) * (uint64_t)std::max(smem_sm, 1);
     cudaError_t e = cudaStreamCreateWithFlags(&sv->stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
         delete sv;
