@@ -152,15 +152,18 @@ def kernel_source_sha() -> str:
     return h.hexdigest()[:16]
 
 
-def measured_traffic():
+def measured_traffic(s):
     """DRAM bytes per launch of the round kernel from the last ncu capture,
-    if that capture was taken of the current kernel source; else None."""
+    if that capture was taken of the current kernel source on this workload
+    and launch size (search s); else None."""
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", "round_kernel_traffic.json")))
         sha = kernel_source_sha()
     except (OSError, ValueError):
         return None
-    return rec.get("dram_bytes_per_launch") if rec.get("kernel_source_sha256_prefix") == sha else None
+    same = (rec.get("kernel_source_sha256_prefix") == sha and rec.get("workload_name") == s.name and
+            rec.get("n_processes") == s.n_proc and rec.get("share_interval") == s.interval)
+    return rec.get("dram_bytes_per_launch") if same else None
 
 
 def flush_l2(buf):
@@ -287,7 +290,7 @@ def run_ours(args):
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": statistics.mean(e2e_ms) if e2e_ms else None},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "Tops/s",
-                     "frac": achieved / peak_ops, "traffic": measured_traffic(),
+                     "frac": achieved / peak_ops, "traffic": None if args.gi_shared else measured_traffic(s),
                      "traffic_unit": "bytes per launch (dram read + write, last ncu capture of this kernel source)",
                      "kernel": "round_kernel (all classes of the round)", "alg_ops_per_launch": ops_per_launch,
                      "avg_launch_ms": avg_round_ms,

@@ -89,3 +89,21 @@ def test_clock_record_keeps_timed_region_samples(tmp_path):
     got = c.stop()
     assert got["samples"] == 4 and got["sm_mhz"] == 1675.0 and got["reasons"] == []
     assert got["scope"] == "timed region" and got["sm_max_mhz"] == 2070.0
+
+
+def test_measured_traffic_only_for_the_captured_workload():
+    """The DRAM traffic of the ncu capture is reported only on the line of
+    the workload and launch size it was taken on, for the current source."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2512_13365_gb300 import synth
+    rec = json.load(open(os.path.join(ROOT, "profiles", "round_kernel_traffic.json")))
+    s = synth.config2()
+    got = bench.measured_traffic(s)
+    if rec["kernel_source_sha256_prefix"] == bench.kernel_source_sha():
+        assert got == rec["dram_bytes_per_launch"] > 0
+    else:
+        assert got is None
+    s.n_proc = 1024
+    assert bench.measured_traffic(s) is None
+    assert bench.measured_traffic(synth.config4(n_proc=4096, budget=64)) is None
