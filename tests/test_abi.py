@@ -131,3 +131,33 @@ def test_resume_rejects_foreign_data_without_device(L):
     assert L.cse_search_resume(dummy, bogus, 4096, 10, None, None, ctypes.byref(h)) == cse.CSE_EINVAL
     assert b"not a checkpoint" in L.cse_last_error()
     assert L.cse_search_resume(dummy, bogus, 8, 10, None, None, ctypes.byref(h)) == cse.CSE_EINVAL
+
+
+def test_binding_fails_loudly_without_the_library(tmp_path):
+    """No CPU fallback: with the compiled library absent, the binding raises
+    instead of computing anything."""
+    import subprocess
+    import sys
+    code = ("from paper_2512_13365_gb300 import cse\n"
+            "try:\n    cse.lib()\nexcept ImportError as e:\n    print('refused:', e)\n")
+    env = dict(os.environ, CSE_GB300_LIB=str(tmp_path / "absent.so"))
+    out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True,
+                         timeout=120)
+    assert out.returncode == 0 and "refused:" in out.stdout and "is not built" in out.stdout
+
+
+def test_device_calls_report_no_device(L):
+    """On a machine without a GPU the calls that need one return CSE_ECUDA:
+    there is no host path that would compute a result."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    m = np.array([[1, 1, 0], [1, 1, 1], [0, 1, 1]], np.int8)
+    ptrs = (ctypes.POINTER(ctypes.c_int8) * 1)(m.ctypes.data_as(ctypes.POINTER(ctypes.c_int8)))
+    rows = (ctypes.c_int32 * 1)(3)
+    cols = (ctypes.c_int32 * 1)(3)
+    h = ctypes.c_void_p()
+    assert L.cse_scheme_load(ptrs, rows, cols, 1, ctypes.byref(h)) == cse.CSE_ECUDA
+    assert not h.value
+    c = np.zeros(4, np.uint32)
+    assert L.cse_philox(0, c.ctypes.data, 1, c.ctypes.data) == cse.CSE_ECUDA
