@@ -217,8 +217,9 @@ int cse_autotune(int32_t n_searches, const cse_scheme* const* schemes, const cse
                  int32_t max_entries, int32_t* n_entries);
 
 /* Sharing-interval tuner.  The interval changes the search (Section 3.5.2
- * shares "from the second iteration onward"; here every share_interval
- * steps), so this is an explicit choice: each candidate interval is run on
+ * shares between whole iterations, from the second on; here every
+ * share_interval steps), so this is an explicit choice: each candidate
+ * interval is run on
  * the given searches for min(step_budget, trial_steps) steps and the one with
  * the lowest total additions (sum over searches and matrices) is returned;
  * ties keep the earlier candidate.  Synchronous. */
