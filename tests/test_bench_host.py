@@ -107,3 +107,20 @@ def test_measured_traffic_only_for_the_captured_workload():
     s.n_proc = 1024
     assert bench.measured_traffic(s) is None
     assert bench.measured_traffic(synth.config4(n_proc=4096, budget=64)) is None
+
+
+def test_reference_arm_under_torchrun_prints_once():
+    """Launched as the multi-GPU benchmark is (torchrun, two ranks on
+    127.0.0.1), the reference arm runs on rank 0 alone, prints one line, and
+    the other rank exits 0 without work."""
+    port = 29700 + os.getpid() % 200
+    out = subprocess.run([sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+                          "--master-addr", "127.0.0.1", "--master-port", str(port),
+                          os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2", "--steps", "1",
+                          "--warmup", "0", "--cpu-budget", "2"],
+                         capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    line = json.loads(lines[0])
+    assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["value"] > 0
