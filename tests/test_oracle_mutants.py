@@ -95,6 +95,13 @@ MUTANTS = [
      "draw4(cs->seed, cs->proc, cs->t, cs->mat, PU_GI, (uint32_t)blk, 0, cs->block);"),
     ("gi_coin_biased", "Section 3.4.2: each intersecting term kept with probability 1/2",
      "return (int)((w >> (rho & 63)) & 1u);", "return (int)(((w >> (rho & 63)) & 3u) != 0);"),
+    ("ops_rewrite_term", "the op count: 10 per word for the rewrite",
+     "P->ops += 10 * (int64_t)M->w32 + 5 * (int64_t)M->w32 * (nij + nu);",
+     "P->ops += 8 * (int64_t)M->w32 + 5 * (int64_t)M->w32 * (nij + nu);"),
+    ("ops_gi_terms", "the op count: 3 per intersecting term of gi",
+     "ops += 3 * (int64_t)n_inter + 8 +", "ops += 2 * (int64_t)n_inter + 8 +"),
+    ("ops_selection_scan", "the op count: 2 per candidate for g, ga, gr, wr",
+     "case OR_G: P->ops += 2 * (int64_t)P->m;", "case OR_G: P->ops += (int64_t)P->m;"),
     ("patience_one_late", "Section 4: stop after 10 iterations without improvement",
      "if (patience > 0 && stale >= patience) break;", "if (patience > 0 && stale > patience) break;"),
 ]

@@ -281,6 +281,21 @@ def test_shared_list_changes_only_when_beaten(seed):
             assert c[r] < c[r - 1] and h[r] != h[r - 1], r
 
 
+def test_op_count_hand_derived():
+    """The algorithmic op count (the roofline's numerator, counted alike by
+    the oracle and the kernels) on the worked example, against the values
+    derived by hand in tests/golden/ops_example.txt."""
+    mat, *_ = _example()
+    want = {ln.split()[0]: [int(x) for x in ln.split()[1:]] for ln in _lines("ops_example.txt")}
+    g = (0, 0, 0, 0, 0, 1)
+    assert O.search([mat], g, 1, 0, 1, 1000, 0, 16).digests[0][0]["ops"] == want["g_step1"][0]
+    assert O.search([mat], g, 1, 0, 2, 1000, 0, 16).digests[0][0]["ops"] == want["g_step2"][0]
+    # gi processes (process 0 starts with Greedy): one scoring pass, one substitution
+    ops = O.search([mat], synth.GI_ONLY, 64, 0, 1, 1000, 0, 16).digests[0]["ops"][1:]
+    allowed = {want["gi_select"][0] + x for x in want["gi_subst"]}
+    assert set(int(x) for x in ops) <= allowed and len(set(int(x) for x in ops)) >= 2
+
+
 def test_column_cap_ends_runs():
     mat = synth.random_matrix(11, 16, 6, 4, 6, n_planted=6, frac=(0.4, 0.6))
     # cap = n_x + 2: at most two substitutions per run
