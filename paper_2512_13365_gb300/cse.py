@@ -7,6 +7,7 @@ the import of the binding fails loudly with the build command to run.
 from __future__ import annotations
 
 import ctypes
+import dataclasses
 import os
 from typing import List, Optional, Sequence, Tuple
 
@@ -314,6 +315,36 @@ def make_opts(interval: int = 32, permille: int = 400, cap: int = 128, procs_per
     o.patience_rounds = patience
     o.flags = (FLAG_GRAPH if graph else 0) | (FLAG_TRACE if trace else 0) | (FLAG_GI_SHARED_COINS if gi_shared else 0)
     return o
+
+
+@dataclasses.dataclass
+class Options:
+    """The fields of cse_opts (include/cse.h) as a Python record; the flags
+    are spelled out.  to_struct() gives the C struct, from_struct() reads
+    one back."""
+    share_interval: int = 32
+    share_permille: int = 400
+    col_cap: int = 128
+    patience_rounds: int = 0
+    procs_per_cta: int = 0
+    graph: bool = False
+    trace: bool = False
+    gi_shared: bool = False
+
+    def to_struct(self) -> Opts:
+        return make_opts(self.share_interval, self.share_permille, self.col_cap, self.procs_per_cta, self.graph,
+                         self.trace, self.patience_rounds, self.gi_shared)
+
+    @classmethod
+    def from_struct(cls, o: Opts) -> "Options":
+        return cls(o.share_interval, o.share_permille, o.col_cap, o.patience_rounds, o.procs_per_cta,
+                   bool(o.flags & FLAG_GRAPH), bool(o.flags & FLAG_TRACE), bool(o.flags & FLAG_GI_SHARED_COINS))
+
+    @classmethod
+    def library_default(cls) -> "Options":
+        o = Opts()
+        lib().cse_opts_default(ctypes.byref(o))
+        return cls.from_struct(o)
 
 
 def search(scheme: Scheme, weights, n_proc: int, seed: int, budget: int, interval: int = 32,

@@ -161,3 +161,14 @@ def test_device_calls_report_no_device(L):
     assert not h.value
     c = np.zeros(4, np.uint32)
     assert L.cse_philox(0, c.ctypes.data, 1, c.ctypes.data) == cse.CSE_ECUDA
+
+
+def test_options_record_mirrors_cse_opts(L):
+    """cse.Options has the library's defaults and round-trips through the C
+    struct, flags included."""
+    assert cse.Options.library_default() == cse.Options()
+    o = cse.Options(share_interval=0, share_permille=1000, col_cap=512, patience_rounds=10, procs_per_cta=3,
+                    graph=False, trace=True, gi_shared=True)
+    st = o.to_struct()
+    assert st.flags == cse.FLAG_TRACE | cse.FLAG_GI_SHARED_COINS and st.max_spin == 0
+    assert cse.Options.from_struct(st) == o
