@@ -73,6 +73,29 @@
  *      that snapshot.
  *   R13 end of budget: every process folds its current run; the result per
  *      matrix is the lowest (best cost, process).
+ *   R15 method op count (a second, engine-independent count of the work the
+ *      method itself must do per step): a rewrite costs 6 per 64-bit word of
+ *      a column (W64 = ceil(rows / 64)) plus the nnz of every rewritten row
+ *      before the rewrite (the pair counts it changes); every selection scans
+ *      the m candidates (m); Greedy-Intersections adds 2 per intersect term
+ *      (one coin bit and one conditional add), with shared coins 4 per
+ *      candidate instead (its weight into two per-variable sums, plain and
+ *      coin-selected); Greedy-Potential adds per candidate a trial rewrite:
+ *      6 W64 plus the nnz of the candidate's rows.
+ *   R16 random flips (Section 3.5.3).  The move is the flip of the flip graph
+ *      the paper cites: two rank-one terms l != m whose factor X agrees up to
+ *      a sign, X_m = sigma X_l, with Y, Z the other two factors, become
+ *        Y_l <- Y_l + sigma Y_m,   Z_m <- Z_m - Z_l,
+ *      which keeps sum_l U_l (x) V_l (x) W_l, hence every Brent equation.  A
+ *      ternary flip is one whose new Y_l and Z_m stay in {-1, 0, 1} and are
+ *      not zero (the rank is kept).  Variant 0 of an iteration is the input;
+ *      variant v >= 1 applies F = 1 + ((u * max_flips) >> 32) flips, u lane 0
+ *      of the draw (process v, step = iteration, purpose FLIP, extra 0);
+ *      attempt a = 0, 1, ... (at most 32 F) draws lane 0..3 of (process v,
+ *      step = iteration, purpose FLIP, extra_lo = a + 1): l = (u0 r) >> 32,
+ *      m = (u1 (r - 1)) >> 32 (+1 if >= l), X = (u2 3) >> 32 (U, V, W), and
+ *      u3 & 1 picks (Y, Z) = (X+1, X+2) or (X+2, X+1) mod 3; an attempt that
+ *      is not a ternary flip changes nothing.
  *   R14 iteration mode (Sections 3.5.2 and 4: the paper's own schedule).
  *      Iteration tau: every process performs one whole run, from its start
  *      (strategy, alpha, beta, share coin and prefix replay as in R11) until
@@ -100,7 +123,7 @@
 #define ENT_J(e) ((int32_t)(((uint32_t)(e) >> 10) & 0x3FFu))
 #define ENT_NEG(e) ((int32_t)(((uint32_t)(e) >> 20) & 1u))
 
-enum { PU_RUN = 0, PU_SHAREK = 1, PU_STEP = 2, PU_GI = 3, PU_GIS = 4 };
+enum { PU_RUN = 0, PU_SHAREK = 1, PU_STEP = 2, PU_GI = 3, PU_GIS = 4, PU_FLIP = 5 };
 
 /* ------------------------------------------------------------------ */
 /* Philox4x32-10, from the definition in Salmon et al., SC'11:          */
@@ -372,11 +395,11 @@ static int coin_draw(coin_src* cs, int32_t p, int32_t q, int32_t slot, int32_t r
  * c = 1 contribute 0, so only candidates enter the sums.  Returns the argmax
  * (lowest key on ties).  *ops_out receives the algorithmic op count. */
 static int32_t sel_gi(const uint32_t* keys, const int32_t* cnt, int32_t m, uint32_t a, uint32_t b,
-                      coin_src* cs, int64_t* score, int64_t* ops_out) {
+                      coin_src* cs, int64_t* score, int64_t* ops_out, int64_t* mops_out) {
     int64_t total = 0;
     for (int32_t q = 0; q < m; q++) total += cnt[q] - 1;
     int32_t best = -1;
-    int64_t best_s = 0, ops = 0;
+    int64_t best_s = 0, ops = 0, terms = 0;
     for (int32_t p = 0; p < m; p++) {
         uint32_t i = KEY_I(keys[p]), j = KEY_J(keys[p]);
         int64_t wp = cnt[p] - 1, inter = 0, x = 0;
@@ -407,11 +430,14 @@ static int32_t sel_gi(const uint32_t* keys, const int32_t* cnt, int32_t m, uint3
         }
         int32_t b0 = (pos0 + 63) >> 6, b1 = (pos1 + 63) >> 6;
         ops += 3 * (int64_t)n_inter + 8 + (n_inter ? 40 * (int64_t)(b0 > b1 ? b0 : b1) : 0);
+        terms += n_inter;
     }
     /* shared coins: 40 per Philox block of 128 candidates, 18 per candidate
      * (its two per-variable sums and its score), 2 per column */
     if (cs->shared) ops = 40 * (int64_t)((m + 127) / 128) + 18 * (int64_t)m + 2 * (int64_t)cs->ncols;
     if (ops_out) *ops_out = ops;
+    /* R15: the scan of m, then 2 per intersect term (shared coins: 4 per candidate) */
+    if (mops_out) *mops_out = (int64_t)m + (cs->shared ? 4 * (int64_t)m : 2 * terms);
     return best;
 }
 
@@ -430,7 +456,7 @@ int32_t oracle_gi_philox_coins(const uint32_t* keys, const int32_t* counts, int3
     cs.record = coins;
     if (m <= 0) return -1;
     memset(coins, 255, (size_t)m * (size_t)m);
-    return sel_gi(keys, counts, m, 1, 32768, &cs, NULL, NULL);
+    return sel_gi(keys, counts, m, 1, 32768, &cs, NULL, NULL, NULL);
 }
 
 int32_t oracle_gi_scores_coins(const uint32_t* keys, const int32_t* counts, int32_t m,
@@ -440,7 +466,7 @@ int32_t oracle_gi_scores_coins(const uint32_t* keys, const int32_t* counts, int3
     cs.bits = coin_bits;
     cs.m = m;
     if (m <= 0) return -1;
-    return sel_gi(keys, counts, m, a, b, &cs, score, NULL);
+    return sel_gi(keys, counts, m, a, b, &cs, score, NULL, NULL);
 }
 
 /* Greedy-Potential: a trial substitution of every candidate on a copy of
@@ -482,9 +508,12 @@ static int32_t gp_potential(const int8_t* coef, int32_t rows, int32_t ncols, int
  * N its potential and a the run's alpha in units of 2^-16; argmax, lowest key
  * on ties.  *ops grows by the algorithmic op count (5 per word of a column per
  * live column of the trial system, plus 8, per candidate). */
+static int64_t rows_nnz_of_pair(const int8_t* coef, int32_t rows, int32_t ncols, int32_t stride, int32_t i,
+                                int32_t j, int32_t neg);
+
 static int32_t gp_select(const int8_t* coef, int32_t rows, int32_t ncols, int32_t stride, const uint32_t* keys,
                          const int32_t* cnt, int32_t m, int32_t a, int32_t w32, int8_t* trial, uint32_t* scratch,
-                         int64_t* ops) {
+                         int64_t* ops, int64_t* mops) {
     int32_t best = -1;
     int64_t best_s = 0;
     for (int32_t p = 0; p < m; p++) {
@@ -496,7 +525,13 @@ static int32_t gp_select(const int8_t* coef, int32_t rows, int32_t ncols, int32_
             best_s = sc;
         }
         if (ops) *ops += 5 * (int64_t)w32 * live + 8;
+        /* R15: a trial rewrite, 6 per 64-bit word plus the nnz of the candidate's rows */
+        if (mops)
+            *mops += 6 * (int64_t)((rows + 63) / 64) +
+                     rows_nnz_of_pair(coef, rows, ncols, stride, (int32_t)KEY_I(keys[p]), (int32_t)KEY_J(keys[p]),
+                                      (int32_t)KEY_NEG(keys[p]));
     }
+    if (mops) *mops += m;
     return best;
 }
 
@@ -512,7 +547,7 @@ int32_t oracle_gp_select(const int8_t* mat, int32_t rows, int32_t cols, int32_t 
     int32_t* cnt = (int32_t*)malloc((size_t)(occ + 1) * 4);
     int32_t* nz = (int32_t*)malloc((size_t)(cols + 1) * 4);
     int32_t m = count_pairs(coef, rows, cols, stride, 2, scratch, nz, keys, cnt, (int32_t)occ + 1);
-    int32_t sel = m > 0 ? gp_select(coef, rows, cols, stride, keys, cnt, m, a, 1, trial, scratch, NULL) : -1;
+    int32_t sel = m > 0 ? gp_select(coef, rows, cols, stride, keys, cnt, m, a, 1, trial, scratch, NULL, NULL) : -1;
     free(coef);
     free(trial);
     free(scratch);
@@ -549,6 +584,68 @@ int32_t oracle_gp_potentials(const int8_t* mat, int32_t rows, int32_t cols, int3
  * when j = j', i = i' and k = k', and 0 otherwise.  U, V, W are r x (m n),
  * r x (n p), r x (m p), entries in row-major order.  Returns the number of
  * (a, b, c) index triples whose sum is wrong. */
+/* ------------------------------------------------------------------ */
+/* Random flips (Section 3.5.3, R16)                                   */
+/* ------------------------------------------------------------------ */
+int32_t oracle_flip_apply(int32_t r, int32_t len_u, int32_t len_v, int32_t len_w, int8_t* U, int8_t* V, int8_t* W,
+                          int32_t l, int32_t m, int32_t x, int32_t side) {
+    int8_t* f[3] = {U, V, W};
+    const int32_t len[3] = {len_u, len_v, len_w};
+    if (l < 0 || m < 0 || l >= r || m >= r || l == m || x < 0 || x > 2) return 0;
+    const int32_t y = (x + 1 + side) % 3, z = (x + 2 - side) % 3;
+    const int8_t* xl = f[x] + (int64_t)l * len[x];
+    const int8_t* xm = f[x] + (int64_t)m * len[x];
+    int same = 1, opp = 1, nz = 0;
+    for (int32_t i = 0; i < len[x]; i++) {
+        same &= xm[i] == xl[i];
+        opp &= xm[i] == -xl[i];
+        nz |= xl[i] != 0;
+    }
+    if (!nz || !(same || opp)) return 0;
+    const int sigma = same ? 1 : -1;
+    int8_t* yl = f[y] + (int64_t)l * len[y];
+    const int8_t* ym = f[y] + (int64_t)m * len[y];
+    int8_t* zm = f[z] + (int64_t)m * len[z];
+    const int8_t* zl = f[z] + (int64_t)l * len[z];
+    int ynz = 0, znz = 0;
+    for (int32_t i = 0; i < len[y]; i++) {
+        int v = yl[i] + sigma * ym[i];
+        if (v < -1 || v > 1) return 0;
+        ynz |= v != 0;
+    }
+    for (int32_t i = 0; i < len[z]; i++) {
+        int v = zm[i] - zl[i];
+        if (v < -1 || v > 1) return 0;
+        znz |= v != 0;
+    }
+    if (!ynz || !znz) return 0;
+    for (int32_t i = 0; i < len[y]; i++) yl[i] = (int8_t)(yl[i] + sigma * ym[i]);
+    for (int32_t i = 0; i < len[z]; i++) zm[i] = (int8_t)(zm[i] - zl[i]);
+    return 1;
+}
+
+int32_t oracle_flip_variant(int32_t mm, int32_t nn, int32_t pp, int32_t r, const int8_t* U, const int8_t* V,
+                            const int8_t* W, uint64_t seed, int32_t iteration, int32_t variant, int32_t max_flips,
+                            int8_t* oU, int8_t* oV, int8_t* oW) {
+    const int32_t lu = mm * nn, lv = nn * pp, lw = mm * pp;
+    memcpy(oU, U, (size_t)r * lu);
+    memcpy(oV, V, (size_t)r * lv);
+    memcpy(oW, W, (size_t)r * lw);
+    if (variant == 0 || r < 2 || max_flips < 1) return 0;
+    const int32_t want = 1 + (int32_t)scale(draw(seed, variant, iteration, 0, PU_FLIP), (uint64_t)max_flips);
+    int32_t done = 0;
+    for (int32_t a = 0; a < 32 * want && done < want; a++) {
+        uint32_t d[4];
+        draw4(seed, variant, iteration, 0, PU_FLIP, 0, (uint32_t)(a + 1), d);
+        int32_t l = (int32_t)scale(d[0], (uint64_t)r);
+        int32_t m = (int32_t)scale(d[1], (uint64_t)(r - 1));
+        if (m >= l) m++;
+        const int32_t x = (int32_t)scale(d[2], 3);
+        done += oracle_flip_apply(r, lu, lv, lw, oU, oV, oW, l, m, x, (int32_t)(d[3] & 1u));
+    }
+    return done;
+}
+
 int64_t oracle_brent_violations(int32_t m, int32_t n, int32_t p, int32_t r, const int8_t* U, const int8_t* V,
                                 const int8_t* W) {
     int64_t bad = 0;
@@ -675,6 +772,7 @@ typedef struct {
     int32_t runs;
     uint64_t traj;
     int64_t ops, substeps;
+    int64_t mops;      /* R15 method op count                            */
 } proc_t;
 
 typedef struct {
@@ -713,6 +811,20 @@ static void recount(const search_t* S, const mat_t* M, proc_t* P, work_t* wk) {
                        (int32_t)M->max_occ + 1);
 }
 
+/* Sum over the rows holding the pair (x_i + s x_j), s = -1 if neg, of the
+ * row's number of nonzeros (R15). */
+static int64_t rows_nnz_of_pair(const int8_t* coef, int32_t rows, int32_t ncols, int32_t stride, int32_t i,
+                                int32_t j, int32_t neg) {
+    int32_t s = neg ? -1 : 1;
+    int64_t n = 0;
+    for (int32_t r = 0; r < rows; r++) {
+        const int8_t* row = coef + (int64_t)r * stride;
+        if (row[i] == 0 || row[j] != s * row[i]) continue;
+        for (int32_t v = 0; v < ncols; v++) n += row[v] != 0;
+    }
+    return n;
+}
+
 /* Candidates whose count a substitution of (i, j) can change: those that
  * contain x_i or x_j (counted for the algorithmic op total). */
 static int64_t touching(const proc_t* P, int32_t i, int32_t j) {
@@ -741,6 +853,8 @@ static int32_t live_columns_below(const search_t* S, const mat_t* M, const proc_
 static int32_t do_subst(const search_t* S, const mat_t* M, proc_t* P, work_t* wk, uint32_t key) {
     int32_t i = (int32_t)KEY_I(key), j = (int32_t)KEY_J(key), neg = (int32_t)KEY_NEG(key);
     int64_t nij = touching(P, i, j);
+    /* R15: 6 per 64-bit word of a column, plus the nnz of the rewritten rows */
+    P->mops += 6 * (int64_t)((M->rows + 63) / 64) + rows_nnz_of_pair(P->coef, M->rows, P->ncols, S->cap, i, j, neg);
     int32_t k = P->ncols;
     int32_t c = substitute(P->coef, M->rows, S->cap, k, i, j, neg);
     P->ncols++;
@@ -824,10 +938,10 @@ static int32_t choose(const search_t* S, int32_t mi, int32_t pi, int64_t t, proc
     if (strat != OR_G && strat != OR_GI && strat != OR_GP) draw4(S->seed, pi, t, mi, PU_STEP, 0, 0, d);
     if (strat == OR_MIX) strat = oracle_mix_strategy(d[0]);
     switch (strat) {
-        case OR_G: P->ops += 2 * (int64_t)P->m; return sel_g(P->cnt, P->m);
-        case OR_GA: P->ops += 2 * (int64_t)P->m; return sel_ga(P->cnt, P->m, d[2]);
-        case OR_WR: P->ops += 2 * (int64_t)P->m; return sel_wr(P->cnt, P->m, d[3]);
-        case OR_GR: P->ops += 2 * (int64_t)P->m; return sel_gr(P->cnt, P->m, d[1], d[2], d[3]);
+        case OR_G: P->ops += 2 * (int64_t)P->m; P->mops += P->m; return sel_g(P->cnt, P->m);
+        case OR_GA: P->ops += 2 * (int64_t)P->m; P->mops += P->m; return sel_ga(P->cnt, P->m, d[2]);
+        case OR_WR: P->ops += 2 * (int64_t)P->m; P->mops += P->m; return sel_wr(P->cnt, P->m, d[3]);
+        case OR_GR: P->ops += 2 * (int64_t)P->m; P->mops += P->m; return sel_gr(P->cnt, P->m, d[1], d[2], d[3]);
         case OR_GI: {
             coin_src cs;
             memset(&cs, 0, sizeof cs);
@@ -839,15 +953,16 @@ static int32_t choose(const search_t* S, int32_t mi, int32_t pi, int64_t t, proc
             cs.block_p = -1;
             cs.shared = S->gi_shared;
             cs.ncols = P->ncols;
-            int64_t ops = 0;
-            int32_t sel = sel_gi(P->keys, P->cnt, P->m, (uint32_t)P->a, (uint32_t)P->b, &cs, NULL, &ops);
+            int64_t ops = 0, mops = 0;
+            int32_t sel = sel_gi(P->keys, P->cnt, P->m, (uint32_t)P->a, (uint32_t)P->b, &cs, NULL, &ops, &mops);
             P->ops += ops;
+            P->mops += mops;
             return sel;
         }
         case OR_GP: {
             const mat_t* M = &S->mats[mi];
             return gp_select(P->coef, M->rows, P->ncols, S->cap, P->keys, P->cnt, P->m, P->a, M->w32, wk->trial,
-                             wk->scratch, &P->ops);
+                             wk->scratch, &P->ops, &P->mops);
         }
         default: return -1;
     }
@@ -1092,6 +1207,7 @@ static int search_impl(int32_t n_mats, const int8_t* const* mats, const int32_t*
                 d->best_hash = h;
                 d->traj_hash = P->traj;
                 d->ops = P->ops;
+                d->method_ops = P->mops;
                 d->substeps = P->substeps;
                 d->best_strategy = P->best_strategy;
                 d->pad = 0;

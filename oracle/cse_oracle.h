@@ -39,6 +39,7 @@ typedef struct {
     int64_t substeps;    /* steps that made a substitution                  */
     int32_t best_strategy; /* strategy of the run of the best record (-1: none) */
     int32_t pad;
+    int64_t method_ops;  /* the method's own op count (R15 in cse_oracle.c)  */
 } oracle_digest;
 
 /* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11). */
@@ -109,6 +110,22 @@ int32_t oracle_gp_select(const int8_t* mat, int32_t rows, int32_t cols, int32_t 
  * products differs from [j = j'][i = i'][k = k']; 0 for a valid scheme. */
 int64_t oracle_brent_violations(int32_t m, int32_t n, int32_t p, int32_t r, const int8_t* U, const int8_t* V,
                                 const int8_t* W);
+
+/* One flip of the flip graph (Section 3.5.3, R16 in cse_oracle.c) on a scheme
+ * of rank r with factor rows of len_u, len_v, len_w entries: if factor x
+ * (0 U, 1 V, 2 W) of terms l != m agrees up to a sign sigma, (Y, Z) = the
+ * other two factors in the order (x+1, x+2) (side 0) or (x+2, x+1) (side 1),
+ * Y_l += sigma Y_m and Z_m -= Z_l, provided both stay ternary and nonzero.
+ * Modifies U, V, W in place; returns 1 if the flip was applied, else 0. */
+int32_t oracle_flip_apply(int32_t r, int32_t len_u, int32_t len_v, int32_t len_w, int8_t* U, int8_t* V, int8_t* W,
+                          int32_t l, int32_t m, int32_t x, int32_t side);
+
+/* Variant `variant` of flip iteration `iteration` of the scheme (m,n,p:r)
+ * (R16): oU/oV/oW receive the input with F random ternary flips applied
+ * (variant 0: the input).  Returns the number of flips applied. */
+int32_t oracle_flip_variant(int32_t m, int32_t n, int32_t p, int32_t r, const int8_t* U, const int8_t* V,
+                            const int8_t* W, uint64_t seed, int32_t iteration, int32_t variant, int32_t max_flips,
+                            int8_t* oU, int8_t* oV, int8_t* oW);
 
 /* Exhaustive minimum of Cost over all sequences of Algorithm 1 on a tiny
  * matrix (rows * cols small).  Returns the optimum, or -1 on overflow. */

@@ -28,12 +28,14 @@ GI_SHARED_COINS = 1  # search flag: one Greedy-Intersections coin per candidate 
 class Digest(ctypes.Structure):
     _fields_ = [("best_cost", ctypes.c_int64), ("best_len", ctypes.c_int32), ("runs", ctypes.c_int32),
                 ("best_hash", ctypes.c_uint64), ("traj_hash", ctypes.c_uint64), ("ops", ctypes.c_int64),
-                ("substeps", ctypes.c_int64), ("best_strategy", ctypes.c_int32), ("pad", ctypes.c_int32)]
+                ("substeps", ctypes.c_int64), ("best_strategy", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("method_ops", ctypes.c_int64)]
 
 
 DIGEST_DTYPE = np.dtype([("best_cost", "<i8"), ("best_len", "<i4"), ("runs", "<i4"),
                          ("best_hash", "<u8"), ("traj_hash", "<u8"), ("ops", "<i8"),
-                         ("substeps", "<i8"), ("best_strategy", "<i4"), ("pad", "<i4")])
+                         ("substeps", "<i8"), ("best_strategy", "<i4"), ("pad", "<i4"),
+                         ("method_ops", "<i8")])
 CURVE_POINTS = 4096  # rounds recorded in the best-Cost curve
 assert DIGEST_DTYPE.itemsize == ctypes.sizeof(Digest)
 
@@ -92,6 +94,11 @@ def lib():
         L.oracle_gp_potentials.restype = ctypes.c_int32
         L.oracle_brent_violations.argtypes = [ctypes.c_int32] * 4 + [i8p, i8p, i8p]
         L.oracle_brent_violations.restype = ctypes.c_int64
+        L.oracle_flip_apply.argtypes = [ctypes.c_int32] * 4 + [i8p, i8p, i8p] + [ctypes.c_int32] * 4
+        L.oracle_flip_apply.restype = ctypes.c_int32
+        L.oracle_flip_variant.argtypes = [ctypes.c_int32] * 4 + [i8p, i8p, i8p, ctypes.c_uint64] + \
+            [ctypes.c_int32] * 3 + [i8p, i8p, i8p]
+        L.oracle_flip_variant.restype = ctypes.c_int32
         L.oracle_bruteforce.argtypes = [i8p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]
         L.oracle_bruteforce.restype = ctypes.c_int64
         L.oracle_search.argtypes = [ctypes.c_int32, ctypes.POINTER(i8p), i32p, i32p, u32p, ctypes.c_int32,
@@ -246,6 +253,26 @@ def brent_violations(m: int, n: int, p: int, U: np.ndarray, V: np.ndarray, W: np
     assert U.shape == (r, m * n) and V.shape == (r, n * p) and W.shape == (r, m * p)
     return int(lib().oracle_brent_violations(m, n, p, r, _p(U, ctypes.c_int8), _p(V, ctypes.c_int8),
                                              _p(W, ctypes.c_int8)))
+
+
+def flip_apply(U, V, W, l: int, m: int, x: int, side: int):
+    """One flip (R16) on copies of U, V, W; returns (applied, U, V, W)."""
+    U, V, W = (np.array(a, dtype=np.int8, order="C") for a in (U, V, W))
+    r = U.shape[0]
+    ok = lib().oracle_flip_apply(r, U.shape[1], V.shape[1], W.shape[1], _p(U, ctypes.c_int8), _p(V, ctypes.c_int8),
+                                 _p(W, ctypes.c_int8), l, m, x, side)
+    return bool(ok), U, V, W
+
+
+def flip_variant(m: int, n: int, p: int, U, V, W, seed: int, iteration: int, variant: int, max_flips: int):
+    """Variant `variant` of flip iteration `iteration` (R16): (flips, U, V, W)."""
+    U, V, W = (np.ascontiguousarray(a, dtype=np.int8) for a in (U, V, W))
+    r = U.shape[0]
+    oU, oV, oW = np.zeros_like(U), np.zeros_like(V), np.zeros_like(W)
+    k = lib().oracle_flip_variant(m, n, p, r, _p(U, ctypes.c_int8), _p(V, ctypes.c_int8), _p(W, ctypes.c_int8), seed,
+                                  iteration, variant, max_flips, _p(oU, ctypes.c_int8), _p(oV, ctypes.c_int8),
+                                  _p(oW, ctypes.c_int8))
+    return int(k), oU, oV, oW
 
 
 def bruteforce(mat: np.ndarray, cap: Optional[int] = None) -> int:

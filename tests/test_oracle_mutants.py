@@ -2,7 +2,7 @@
 
 Each mutant is a copy of the oracle's C source with one plausible mistake,
 compiled into a temporary library.  The committed pin suite
-(test_oracle_pins.py) then runs against that copy in a child process
+(test_oracle_pins.py, test_oracle_flips.py) then runs against that copy in a child process
 (ORACLE_LIB points the binding at it) and must fail.  The mistakes are
 planted in the oracle on the CPU only; nothing here touches the CUDA library.
 """
@@ -95,6 +95,20 @@ MUTANTS = [
      "draw4(cs->seed, cs->proc, cs->t, cs->mat, PU_GI, (uint32_t)blk, 0, cs->block);"),
     ("gi_coin_biased", "Section 3.4.2: each intersecting term kept with probability 1/2",
      "return (int)((w >> (rho & 63)) & 1u);", "return (int)(((w >> (rho & 63)) & 3u) != 0);"),
+    ("flip_sign_ignored", "Section 3.5.3: a flip of terms whose shared factor differs in sign",
+     "const int sigma = same ? 1 : -1;", "const int sigma = 1;"),
+    ("flip_z_unchanged", "Section 3.5.3: a flip rewrites two factors of two terms",
+     "    for (int32_t i = 0; i < len[z]; i++) zm[i] = (int8_t)(zm[i] - zl[i]);\n", "\n"),
+    ("flip_not_ternary", "Section 3.5.3: ternary flips keep every coefficient in {-1, 0, 1}",
+     "        if (v < -1 || v > 1) return 0;\n        ynz |= v != 0;", "        ynz |= v != 0;"),
+    ("mops_rewrite_words", "the method op count (R15): 6 per 64-bit word of a rewrite",
+     "P->mops += 6 * (int64_t)((M->rows + 63) / 64) + rows_nnz_of_pair(", "P->mops += 6 * (int64_t)((M->rows + 31) / 32) + rows_nnz_of_pair("),
+    ("mops_rows_after_rewrite", "the method op count (R15): nnz of the rewritten rows before the rewrite",
+     "for (int32_t v = 0; v < ncols; v++) n += row[v] != 0;", "for (int32_t v = 0; v < ncols; v++) n += row[v] != 0 && v != i;"),
+    ("mops_gi_terms_once", "the method op count (R15): 2 per intersect term",
+     "(cs->shared ? 4 * (int64_t)m : 2 * terms)", "(cs->shared ? 4 * (int64_t)m : terms)"),
+    ("mops_no_scan", "the method op count (R15): every selection scans m",
+     "case OR_G: P->ops += 2 * (int64_t)P->m; P->mops += P->m;", "case OR_G: P->ops += 2 * (int64_t)P->m;"),
     ("ops_rewrite_term", "the op count: 10 per word for the rewrite",
      "P->ops += 10 * (int64_t)M->w32 + 5 * (int64_t)M->w32 * (nij + nu);",
      "P->ops += 8 * (int64_t)M->w32 + 5 * (int64_t)M->w32 * (nij + nu);"),
@@ -125,6 +139,7 @@ def _run_pins(lib):
     env = dict(os.environ, ORACLE_LIB=lib)
     try:
         out = subprocess.run([sys.executable, "-m", "pytest", os.path.join(ROOT, "tests", "test_oracle_pins.py"),
+                              os.path.join(ROOT, "tests", "test_oracle_flips.py"),
                               "-x", "-q", "-p", "no:cacheprovider", "-m", "not gpu"],
                              cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     except subprocess.TimeoutExpired:

@@ -296,6 +296,25 @@ def test_op_count_hand_derived():
     assert set(int(x) for x in ops) <= allowed and len(set(int(x) for x in ops)) >= 2
 
 
+def test_method_op_count_hand_derived():
+    """The method op count (reading R15: the work the method itself must do,
+    independent of the engine) on the worked example, against the values
+    derived by hand in tests/golden/ops_example.txt."""
+    mat, *_ = _example()
+    want = {ln.split()[0]: [int(x) for x in ln.split()[1:]] for ln in _lines("ops_example.txt")}
+    g = (0, 0, 0, 0, 0, 1)
+    assert O.search([mat], g, 1, 0, 1, 1000, 0, 16).digests[0][0]["method_ops"] == want["m_g_step1"][0]
+    assert O.search([mat], g, 1, 0, 2, 1000, 0, 16).digests[0][0]["method_ops"] == want["m_g_step2"][0]
+    ops = O.search([mat], synth.GI_ONLY, 64, 0, 1, 1000, 0, 16).digests[0]["method_ops"][1:]
+    allowed = {want["m_gi_select"][0] + x for x in want["m_gi_subst"]}
+    assert set(int(x) for x in ops) <= allowed and len(set(int(x) for x in ops)) >= 2
+    ops = O.search([mat], synth.GP_ONLY, 64, 0, 1, 1000, 0, 16).digests[0]["method_ops"][1:]
+    allowed = {want["m_gp_select"][0] + x for x in want["m_gi_subst"]}
+    assert set(int(x) for x in ops) <= allowed
+    rows40 = np.ones((40, 2), np.int8)  # 64-bit words: ceil(40 / 64) = 1 per column
+    assert O.search([rows40], g, 1, 0, 1, 1000, 0, 8).digests[0][0]["method_ops"] == want["m_g_40rows"][0]
+
+
 def test_column_cap_ends_runs():
     mat = synth.random_matrix(11, 16, 6, 4, 6, n_planted=6, frac=(0.4, 0.6))
     # cap = n_x + 2: at most two substitutions per run
@@ -856,3 +875,28 @@ def test_curve_and_winning_strategies(seed):
     assert set(g.tolist()) <= {5, -1}
     it = O.search_iterations(mats, synth.PAPER_WEIGHTS, 20, seed, 30, 3, 400, 48)
     assert len(it.curve[0]) == it.iterations and it.curve[0][-1] == it.cost[0]
+
+
+def test_config4_golden_is_of_the_current_inputs():
+    """tests/golden/cfg4_reduced.txt (the oracle's results that the GPU parity
+    test compares with) was written for the inputs synth.config4 generates
+    now, and holds every process of every matrix."""
+    import hashlib
+    g = {}
+    n_p = 0
+    for ln in open(os.path.join(GOLD, "cfg4_reduced.txt")):
+        f = ln.split()
+        if f and f[0] in ("inputs_sha256", "params", "costs"):
+            g[f[0]] = f[1:]
+        n_p += bool(f) and f[0] == "p"
+    n_proc, budget = int(g["params"][0]), int(g["params"][1])
+    s = synth.config4(n_proc=n_proc, budget=budget)
+    h = hashlib.sha256()
+    for m in s.mats:
+        h.update(m.tobytes())
+    assert g["inputs_sha256"][0] == h.hexdigest()[:16]
+    assert n_p == 3 * n_proc and len(g["costs"]) == 3
+    # the results are valid programs for these inputs
+    for k, ln in enumerate(l for l in open(os.path.join(GOLD, "cfg4_reduced.txt")) if l.startswith("list ")):
+        lst = [int(x) for x in ln.split()[2:]]
+        assert O.apply(s.mats[k], lst)[1] == int(g["costs"][k])
