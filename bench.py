@@ -1,12 +1,17 @@
-"""Benchmark: CSE process-steps/s of the GB300 library on a synthetic
-(3,3,3:23)-shaped scheme (E_U, E_V 23 x 9, E_W 9 x 23; 4096 processes per
-matrix, mixed strategies, sharing every 32 steps, 1024 steps).
+"""Benchmark: CSE process-steps/s of the GB300 library on the largest
+single-GPU workload, a synthetic (6,6,6:153)-shaped scheme (E_U, E_V 153 x 36,
+E_W 36 x 153, variables grown to 512; 65536 processes per matrix, mixed
+strategies, sharing every 32 steps, 2000 steps).  `--workload cfg2` runs the
+(3,3,3:23)-shaped scheme (4096 processes, 1024 steps) instead.
 
 One benchmark step = one complete search (cse_search) over that workload.
 `value` is timed on the device with CUDA events, inputs resident in HBM;
 `e2e` times the public C-ABI sequence a user runs (load from host buffers,
-search, fetch results to the host).  `--impl reference` times the CPU oracle
-on a bounded sample of the same workload.
+search, fetch results to the host).  The roofline's numerator is the
+method's own op count (cse_result_method_ops) and its peak the integer-pipe
+rate measured by cse_int_peak on this GPU at the clock sampled during the
+timed region.  `--impl reference` times the CPU oracle on a bounded sample of
+the same workload.
 """
 from __future__ import annotations
 
@@ -25,7 +30,50 @@ sys.path.insert(0, ROOT)
 METRIC = "CSE process-steps/s & best additions @ fixed budget vs oracle; p50/p99 latency"
 UNIT = "process-steps/s"
 SM_COUNT_NOMINAL = 152
-LANES_PER_SM = 128  # 4 schedulers x 32 lanes: one warp instruction per scheduler per clock
+LANES_PER_SM = 128  # 4 schedulers x 32 lanes: one warp instruction per scheduler per clock (derived, not measured)
+# bounded oracle samples (processes per matrix, steps) of each workload: about
+# 10-30 s of host work for the CPU baseline, a few seconds per reference step
+CPU_SAMPLE = {"cfg4": (48, 64), "cfg2": (4096, 1024), "cfg1": (64, 200)}
+REF_SAMPLE = {"cfg4": (32, 16), "cfg2": (4096, 128), "cfg1": (64, 200)}
+
+
+def measured_int_peak(stream, iters: int = 100000):
+    """cse_int_peak on this GPU: lane-ops per SM clock of the integer mixes
+    (LOP3 + IADD3, AND + POPC + IADD, IMAD, IMAD.HI)."""
+    from paper_2512_13365_gb300 import cse
+    out = {}
+    for kind in range(4):
+        cse.int_peak(kind, 1000, stream)  # warm-up
+        r = cse.int_peak(kind, iters, stream)
+        out[r["kind"]] = round(r["ops_per_clk_per_sm"], 2)
+    return out
+
+
+def roofline(ops_per_launch, avg_launch_ms, eng_ops_per_launch, peak_clk, sms, clk, traffic, kernel):
+    """Roofline of the round kernels against the measured integer peak:
+    LOP3/IADD3 lane-ops per SM clock x SMs x the median SM clock sampled in
+    the timed region (the maximum clock if no sample)."""
+    mhz = clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2070.0
+    per_clk = peak_clk["lop3+iadd3"]
+    peak = per_clk * sms * mhz * 1e6 / 1e12
+    achieved = ops_per_launch / (avg_launch_ms / 1000.0) / 1e12
+    eng = eng_ops_per_launch / (avg_launch_ms / 1000.0) / 1e12
+    derived = sms * LANES_PER_SM * mhz * 1e6 / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
+            "frac_s8d": achieved / peak,
+            "numerator": "method ops (cse_result_method_ops): 6 per 64-bit word + nnz of the rewritten rows per "
+                         "rewrite, m per selection, 2 per Greedy-Intersections intersect term",
+            "peak_source": f"measured by cse_int_peak: {per_clk:.1f} LOP3/IADD3 lane-ops per SM clock x {sms} SMs "
+                           f"x {mhz:.0f} MHz (median SM clock of the timed region)",
+            "measured_ops_per_clk_per_sm": peak_clk,
+            "engine_weighted": {"achieved": eng, "frac": eng / peak,
+                                "definition": "cse_result_counters alg_ops (10W per rewrite, 5W per changed "
+                                              "pair count, 3 per gi term + 8 + 40 per Philox block)"},
+            "derived_peak_note": f"{sms} SMs x {LANES_PER_SM} lanes x {mhz:.0f} MHz = {derived:.2f} T (not used)",
+            "traffic": traffic,
+            "traffic_unit": "bytes per launch (dram read + write; ncu capture of this kernel source, scaled by "
+                            "processes when taken on a smaller launch)",
+            "kernel": kernel, "alg_ops_per_launch": ops_per_launch, "avg_launch_ms": avg_launch_ms}
 
 
 def workload(name: str, procs: int = 0):
@@ -152,18 +200,24 @@ def kernel_source_sha() -> str:
     return h.hexdigest()[:16]
 
 
-def measured_traffic(s):
-    """DRAM bytes per launch of the round kernel from the last ncu capture,
-    if that capture was taken of the current kernel source on this workload
-    and launch size (search s); else None."""
+def measured_traffic(s, path=None):
+    """DRAM bytes per launch of the round kernels from the ncu capture of the
+    current kernel source on this workload (search s), scaled to s's process
+    count when the capture was taken on a smaller launch (each process reads
+    and writes its own state, so the traffic grows with the processes); else
+    None."""
     try:
-        rec = json.load(open(os.path.join(ROOT, "profiles", "round_kernel_traffic.json")))
+        rec = json.load(open(path or os.path.join(ROOT, "profiles", "round_kernel_traffic.json")))
         sha = kernel_source_sha()
     except (OSError, ValueError):
         return None
-    same = (rec.get("kernel_source_sha256_prefix") == sha and rec.get("workload_name") == s.name and
-            rec.get("n_processes") == s.n_proc and rec.get("share_interval") == s.interval)
-    return rec.get("dram_bytes_per_launch") if same else None
+    recs = rec if isinstance(rec, list) else [rec]
+    for r in recs:
+        if (r.get("kernel_source_sha256_prefix") == sha and r.get("workload_name") == s.name and
+                r.get("share_interval") == s.interval):
+            # the state each launch reads and writes grows with the process count
+            return int(r["dram_bytes_per_launch"] * s.n_proc / r["n_processes"])
+    return None
 
 
 def flush_l2(buf):
@@ -197,6 +251,7 @@ def run_ours(args):
         r = one()
         r.fetch(0)
         r.free()
+    peak_clk = measured_int_peak(stream)
     clocks = Clocks(os.path.join(args.out, f"clocks_rank{rank}.csv"), local)
     torch.cuda.synchronize()
     if world > 1:
@@ -222,13 +277,15 @@ def run_ours(args):
     clocks.window(tw0, time.time())
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in evs]
-    round_ms, n_rounds, ops_total = [], 0, 0
+    round_ms, n_rounds, ops_total, mops_total = [], 0, 0, 0
     for r in results:
         rm, tm, nr = r.timing()
         round_ms.append(rm)
         n_rounds = nr
         steps, sub, ops = r.counters()
         ops_total = ops
+        mops_total = r.method_ops()
+    kernels_per_search = results[-1].launches()[0]
     total = results[-1].total
     costs = results[-1].costs
     # the best-additions curve (sum over matrices, one point per round) and
@@ -252,7 +309,8 @@ def run_ours(args):
     d2h = 0
     # the inputs sit in pinned host memory, as a serving host would keep them
     pinned = [torch.from_numpy(m).pin_memory().numpy() for m in s.mats]
-    for it in range(0 if args.no_e2e else max(1, min(args.steps, 3))):
+    n_e2e = 1 if statistics.mean(step_ms) > 5000 else max(1, min(args.steps, 3))
+    for it in range(0 if args.no_e2e else n_e2e):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         sc = cse.Scheme(pinned)
@@ -267,15 +325,9 @@ def run_ours(args):
     if e2e_ms:
         e2e_value = whole_job_rate(psteps, world, max_over_ranks(statistics.mean(e2e_ms), dev))
 
-    # roofline of the dominant kernel (the round kernel)
-    pk = peaks()
+    # roofline of the dominant kernel (the round kernels)
     props = torch.cuda.get_device_properties(dev)
-    sm_mhz = float(pk.get("sm_max_mhz", 2070.0))
-    peak_ops = props.multi_processor_count * LANES_PER_SM * sm_mhz * 1e6 / 1e12  # T int-ops/s
     avg_round_ms = statistics.mean(round_ms) / n_rounds
-    ops_per_launch = ops_total / n_rounds
-    achieved = ops_per_launch / (avg_round_ms / 1000.0) / 1e12
-    launches_per_search = n_rounds * 2  # per round: the step engine and the share kernel
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -285,7 +337,9 @@ def run_ours(args):
                    "matrices": [list(m.shape) for m in s.mats], "n_processes": s.n_proc,
                    "step_budget": s.budget, "share_interval": s.interval, "share_permille": s.permille,
                    "col_cap": s.cap, "strategy_weights_gi_ga_gr_wr_mix_g_gp": list(s.weights),
-                   "process_steps_per_step": psteps, "l2": "flushed (256 MB write) between timed steps",
+                   "process_steps_per_step": psteps,
+                   "l2": "flushed (256 MB write) between timed steps; the per-process state is larger than L2"
+                         if s.n_proc * len(s.mats) > 100000 else "flushed (256 MB write) between timed steps",
                    "parallelism": f"{world} independent searches (one per GPU)"},
         "best_additions": total, "best_additions_per_matrix": costs,
         "best_additions_per_round": curve,
@@ -293,17 +347,14 @@ def run_ours(args):
         "wall_s": wall,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": statistics.mean(e2e_ms) if e2e_ms else None, "inputs": "pinned host memory"},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "Tops/s",
-                     "frac": achieved / peak_ops, "traffic": None if args.gi_shared else measured_traffic(s),
-                     "traffic_unit": "bytes per launch (dram read + write, last ncu capture of this kernel source)",
-                     "kernel": "round_kernel (all classes of the round)", "alg_ops_per_launch": ops_per_launch,
-                     "avg_launch_ms": avg_round_ms,
-                     "peak_source": f"{props.multi_processor_count} SMs x {LANES_PER_SM} lanes x {sm_mhz:.0f} MHz"},
+        "roofline": roofline(mops_total / n_rounds, avg_round_ms, ops_total / n_rounds, peak_clk,
+                             props.multi_processor_count, clk, None if args.gi_shared else measured_traffic(s),
+                             "round_kernel (all matrix classes of a round; one launch per class)"),
         "clocks": clk,
-        "gpu_launches": launches_per_search * args.steps,
+        "gpu_launches": kernels_per_search * args.steps,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(s, args.cpu_budget or s.budget, args.gi_shared)
+        line["cpu_baseline"] = cpu_baseline(s, args.workload, args.cpu_budget, args.gi_shared)
     if world > 1:
         torch.distributed.barrier()
         torch.distributed.destroy_process_group()
@@ -311,25 +362,32 @@ def run_ours(args):
         print(json.dumps(line))
 
 
-def cpu_baseline(s, budget, gi_shared=False):
-    """The oracle, as it stands, on a bounded sample of the same workload:
-    all processes, the first `budget` steps, on every host core."""
+def cpu_baseline(s, wl, budget=0, gi_shared=False):
+    """The oracle, as it stands, on a bounded sample of the same workload
+    (about 10-30 s on the host cores): the first processes and steps of the
+    search, on every host core; process-steps/s of that sample."""
     from oracle import oracle as O
     import copy
     cores = len(os.sched_getaffinity(0))
+    procs, steps = CPU_SAMPLE.get(wl, (s.n_proc, s.budget))
     smp = copy.copy(s)
-    smp.budget = budget
+    smp.n_proc = min(procs, s.n_proc)
+    smp.budget = budget or min(steps, s.budget)
     t0 = time.perf_counter()
     ref = O.search_obj(smp, n_threads=cores, digests=False, flags=O.GI_SHARED_COINS if gi_shared else 0)
     dt = time.perf_counter() - t0
     out = {"value": smp.process_steps() / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-           "sample": f"{s.name}: all {s.n_proc} processes x {len(s.mats)} matrices, first {budget} of "
-                     f"{s.budget} steps ({smp.process_steps()} process-steps, {dt:.1f} s)"}
-    if budget == s.budget:
+           "sample": f"{s.name}: first {smp.n_proc} of {s.n_proc} processes x {len(s.mats)} matrices, first "
+                     f"{smp.budget} of {s.budget} steps ({smp.process_steps()} process-steps, {dt:.1f} s)"}
+    if smp.budget == s.budget and smp.n_proc == s.n_proc:
         out["best_additions"] = ref.total  # the same search on the CPU: equal to the GPU's by parity
+    elif smp.n_proc < s.n_proc:
+        out["note"] = ("the sample covers the earliest steps, where the candidate lists are longest; the rate is "
+                       "not extrapolated to the whole search")
     # the same oracle on one thread, on a shorter sample (about 4 s)
-    one = copy.copy(s)
-    one.budget = min(budget, 32)
+    one = copy.copy(smp)
+    one.n_proc = min(smp.n_proc, 8 if wl == "cfg4" else smp.n_proc)
+    one.budget = min(smp.budget, 16 if wl == "cfg4" else 32)
     t0 = time.perf_counter()
     O.search_obj(one, n_threads=1, digests=False, flags=O.GI_SHARED_COINS if gi_shared else 0)
     dt1 = time.perf_counter() - t0
@@ -390,6 +448,7 @@ def run_batched(args):
             if name == "batched":
                 round_ms, _, n_rounds = rs[0].timing()
                 ops_total = sum(r.counters()[2] for r in rs)
+                mops_total = sum(r.method_ops() for r in rs)
             for r in rs:
                 r.free()
         out[name] = {"ms": statistics.mean(ms), "value": psteps / (statistics.mean(ms) / 1000.0),
@@ -424,11 +483,8 @@ def run_batched(args):
                      "batched_graph": {"step_budget": B2, "ms": t2, "best_additions_total": tot2}}
             break
         B2 -= interval
-    pk = peaks()
     props = torch.cuda.get_device_properties(dev)
-    sm_mhz = float(pk.get("sm_max_mhz", 2070.0))
-    peak_ops = props.multi_processor_count * LANES_PER_SM * sm_mhz * 1e6 / 1e12
-    achieved = ops_total / (round_ms / 1000.0) / 1e12
+    peak_clk = measured_int_peak(stream)
     # the oracle on the same batch, all schemes and processes, first cpu_budget steps
     from oracle import oracle as O
     import copy
@@ -454,10 +510,9 @@ def run_batched(args):
         "fixed_wall_clock": fixed,
         "autotune": {"seconds": tune_s, "classes": tuned, "interval_candidates": [16, 32, 64],
                      "interval_chosen": interval},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "Tops/s",
-                     "frac": achieved / peak_ops, "traffic": None,
-                     "kernel": "round kernels of the batched graph (all classes)",
-                     "alg_ops_per_launch": ops_total / n_rounds, "avg_launch_ms": round_ms / n_rounds},
+        "roofline": roofline(mops_total / n_rounds, round_ms / n_rounds, ops_total / n_rounds, peak_clk,
+                             props.multi_processor_count, {"sm_max_mhz": float(peaks().get("sm_max_mhz", 2070.0))},
+                             None, "round kernels of the batched graph (all classes)"),
         "cpu_baseline": {"value": cpu_steps / cpu_s, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"all {len(searches)} schemes x 3 matrices x {searches[0].n_proc} processes, "
                                    f"first {cb} steps ({cpu_steps} process-steps, {cpu_s:.1f} s)"},
@@ -573,11 +628,11 @@ def run_iterations(args):
         steps, sub, ops = r.counters()
         round_ms, _, n_rounds = r.timing()
         it, conv, total = r.iterations()
-        rec = (steps, ops, round_ms, n_rounds, it, conv, total, r.costs, r.launches()[0])
+        rec = (steps, ops, round_ms, n_rounds, it, conv, total, r.costs, r.launches()[0], r.method_ops())
         r.free()
     clocks.window(tw0, time.time())
     clk = clocks.stop()
-    steps, ops, round_ms, n_rounds, it, conv, total, costs, kernels = rec
+    steps, ops, round_ms, n_rounds, it, conv, total, costs, kernels, mops = rec
     t = statistics.mean(ms)
     # end to end: load from pinned host buffers, search to convergence, fetch every list
     e2e_ms, d2h = [], 0
@@ -593,11 +648,8 @@ def run_iterations(args):
         d2h = sum(4 * len(l) + 16 for l, _, _ in lists)
         r.free()
         sc.free()
-    pk = peaks()
     props = torch.cuda.get_device_properties(dev)
-    sm_mhz = float(pk.get("sm_max_mhz", 2070.0))
-    peak_ops = props.multi_processor_count * LANES_PER_SM * sm_mhz * 1e6 / 1e12
-    achieved = ops / (round_ms / 1000.0) / 1e12
+    peak_clk = measured_int_peak(stream)
     line = {
         "metric": METRIC, "value": steps / (t / 1000.0), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t, "higher_is_better": True, "scaling": "weak",
@@ -612,9 +664,8 @@ def run_iterations(args):
         "e2e": {"value": steps / (statistics.mean(e2e_ms) / 1000.0) if e2e_ms else None, "unit": UNIT,
                 "h2d_bytes_per_step": sum(m.nbytes for m in s.mats), "d2h_bytes_per_step": d2h,
                 "ms_per_step": statistics.mean(e2e_ms) if e2e_ms else None},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "Tops/s",
-                     "frac": achieved / peak_ops, "traffic": None, "kernel": "round_kernel (whole runs)",
-                     "alg_ops_per_launch": ops / n_rounds, "avg_launch_ms": round_ms / n_rounds},
+        "roofline": roofline(mops / n_rounds, round_ms / n_rounds, ops / n_rounds, peak_clk,
+                             props.multi_processor_count, clk, None, "round_kernel (whole runs)"),
         "clocks": clk, "gpu_launches": kernels * args.steps,
     }
     if not args.no_cpu_baseline:
@@ -705,8 +756,10 @@ def run_reference(args):
     s = workload(args.workload)
     cores = len(os.sched_getaffinity(0))
     import copy
+    procs, steps = REF_SAMPLE.get(args.workload, (s.n_proc, max(1, s.budget // 8)))
     smp = copy.copy(s)
-    smp.budget = args.cpu_budget or max(1, s.budget // 8)
+    smp.n_proc = min(procs, s.n_proc)
+    smp.budget = args.cpu_budget or min(steps, s.budget)
     for _ in range(args.warmup):
         w = copy.copy(smp)
         w.budget = min(8, smp.budget)
@@ -718,13 +771,14 @@ def run_reference(args):
         times.append(time.perf_counter() - t0)
     ms = statistics.mean(times) * 1000.0
     v = smp.process_steps() / (ms / 1000.0)
-    sample = (f"{s.name}: all {s.n_proc} processes x {len(s.mats)} matrices, first {smp.budget} of {s.budget} "
-              f"steps per benchmark step")
+    sample = (f"{s.name}: first {smp.n_proc} of {s.n_proc} processes x {len(s.mats)} matrices, first "
+              f"{smp.budget} of {s.budget} steps per benchmark step ({smp.process_steps()} process-steps)")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "int32", "data": "synthetic",
-        "config": {"workload": s.name, "n_processes": s.n_proc, "step_budget": s.budget},
+        "config": {"workload": s.name, "matrices": [list(m.shape) for m in s.mats], "n_processes": s.n_proc,
+                   "step_budget": s.budget, "share_interval": s.interval, "col_cap": s.cap},
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
@@ -733,17 +787,18 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="cfg2",
-                    help="cfg2 (default, the benchmark line), cfg1, cfg4, cfg3 (batched), cfg5 (serving), "
+    ap.add_argument("--workload", default="cfg4",
+                    help="cfg4 (default, the benchmark line: the largest single-GPU workload), cfg2, cfg1, "
+                         "cfg3 (batched), cfg5 (serving), "
                          "cfg2-iter (iteration mode), cfg2-wallclock (best additions at fixed wall-clock budgets)")
     ap.add_argument("--requests", type=int, default=200, help="cfg5: number of requests")
     ap.add_argument("--procs", type=int, default=0, help="override the process count (reduced-scale runs)")
     ap.add_argument("--ppc", type=int, default=0, help="processes per CTA (0 = library default)")
     ap.add_argument("--cpu-budget", type=int, default=0,
-                    help="steps of the oracle sample (0 = the whole search, about 10 s on 16 cores)")
+                    help="steps of the oracle sample (0 = the workload's bounded sample)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--budget", type=int, default=0, help="override the step budget (profiling runs)")

@@ -89,6 +89,11 @@ typedef struct {
                               (Section 3.4.2) fixes only each coin's 1/2
                               marginal.  Scoring then costs O(m + columns) per
                               step through per-variable sums. */
+#define CSE_FLAG_WARP_ENGINE 8u  /* large matrices (those whose process state
+                              does not fit a warp's shared-memory slice) run
+                              on the one-warp-per-process engine only,
+                              instead of one process per CTA with its arrays
+                              in shared memory; results are identical */
 
 /* Search options.  Fields that change results: share_interval,
  * share_permille, col_cap, patience_rounds and the flag
@@ -116,6 +121,14 @@ typedef struct {
     uint64_t max_spin;        /* reserved for bounded device waits (unused)  */
     uint32_t procs_per_cta;   /* processes (warps) per CTA; 0 = automatic    */
     uint32_t flags;           /* CSE_FLAG_* bits; other bits must be 0       */
+    uint32_t cta_list_cap;    /* launch parameter of large matrices: the
+                                 candidate capacity of the process-per-CTA
+                                 engine's shared-memory list, 0 = automatic
+                                 (at most 6144); a process whose list
+                                 outgrows it finishes that round on the
+                                 one-warp-per-process engine.  Never changes
+                                 results.                                     */
+    uint32_t reserved;        /* must be 0                                   */
 } cse_opts;
 
 /* Default options: share_interval 32, share_permille 400, col_cap 128. */
@@ -255,6 +268,7 @@ typedef struct {
                               wr 3, mix 4, g 5, gp 6; -1 if no run improved
                               on the input (per-strategy win counts)         */
     int32_t pad;
+    int64_t method_ops; /* the method's own op count (cse_result_method_ops) */
 } cse_proc_record;
 
 /* Waits for the search and writes n_processes records of matrix mat. */
@@ -279,6 +293,20 @@ int cse_result_curve(const cse_result* r, int32_t mat, int32_t* costs, int32_t m
  * candidates sharing a variable with p. */
 int cse_result_counters(const cse_result* r, int64_t* process_steps, int64_t* substeps,
                         int64_t* alg_ops);
+
+/* Waits for the search and reports *method_ops, summed over all matrices and
+ * processes: the integer work the method itself must do, independent of how
+ * the kernels do it (the roofline's numerator).  Per step: a rewrite
+ * (Algorithm 1, substitution; Section 3.2.1) costs 6 per 64-bit word of a
+ * column (ceil(rows / 64) words of +rows and -rows, read and written) plus,
+ * for the pair counts it changes, the number of nonzeros of every rewritten
+ * row before the rewrite; every selection scans the m candidates (m);
+ * Greedy-Intersections (Section 3.4.2) adds 2 per intersect term (one coin
+ * bit and one conditional add), or with shared coins 4 per candidate;
+ * Greedy-Potential adds per candidate one trial rewrite (6 per 64-bit word
+ * plus the nonzeros of the candidate's rows).  Replayed prefix substitutions
+ * (Section 3.5.2) count as rewrites. */
+int cse_result_method_ops(const cse_result* r, int64_t* method_ops);
 
 /* Device time of the search's kernels in milliseconds, from CUDA events
  * recorded around the round kernels on the search's stream: *round_ms sums
@@ -383,6 +411,81 @@ int cse_server_peak(cse_server* s, int32_t* max_active_searches, int32_t* rounds
  * server.  No other call on it may be in progress. */
 void cse_server_free(cse_server* s);
 
+
+/* ---- Random-flip mode (Section 3.5.3) -------------------------------------
+ * Writes n_variants variants of the scheme (m,n,p:r) for flip iteration
+ * `iteration` into out_U/out_V/out_W (host, n_variants x r x (m n), (n p),
+ * (m p), variant after variant, in the layout of cse_scheme_load_uvw):
+ * variant 0 is the input, variant v >= 1 the input after a random number
+ * F in [1, max_flips] of ternary flips of the flip graph the paper cites
+ * (terms l != m whose factor X agrees up to a sign sigma get Y_l += sigma Y_m
+ * and Z_m -= Z_l, Y and Z the other factors, only if both stay ternary and
+ * nonzero; at most 32 F attempts, each drawn from Philox keyed by seed with
+ * counter (v, iteration, 5 << 20, attempt + 1)).  Flips keep the scheme's
+ * tensor, hence every Brent equation; flips[v] = the flips applied and
+ * brent_violations[v] (optional) = the variant's violated Brent equations,
+ * counted on the device (0 for a valid input).  The variants are generated
+ * on the device, one warp each.  Limits as cse_brent_check; n_variants <=
+ * 4096.  Searching the variants (one search each, e.g. with
+ * cse_search_batch) and keeping the best is the caller's loop. */
+int cse_flip_variants(int32_t m, int32_t n, int32_t p, int32_t r, const int8_t* U, const int8_t* V,
+                      const int8_t* W, int32_t n_variants, uint64_t seed, int32_t iteration, int32_t max_flips,
+                      int8_t* out_U, int8_t* out_V, int8_t* out_W, int32_t* flips, int64_t* brent_violations);
+
+/* ---- One search split across ranks (Section 3.5: processes interact only
+ * at the sharing boundaries) -----------------------------------------------
+ * A shard runs processes [proc_begin, proc_begin + proc_count) of a search of
+ * n_processes processes per matrix; its draws are keyed by the global process
+ * index, so the union of the shards of a search is that search, bit for bit,
+ * provided every sharing boundary is completed with the minima of all
+ * shards.  Each rank (one GPU each) loops:
+ *   cse_shard_round(h, keys, &left)     runs this round's steps; keys[k] =
+ *                                       this shard's (best Cost << 32 |
+ *                                       global process) minimum of matrix k
+ *   (the caller takes the minimum of keys over the ranks, and the owner of
+ *    each minimum fetches that process's best list with cse_shard_best_list
+ *    and sends it to the others)
+ *   cse_shard_share(h, min_keys, lists, lens)  completes the boundary
+ * until left is 0.  The exchange is the caller's (for example an allreduce of
+ * the keys and of the lists); the library stays on one GPU.  Only the step
+ * clock (share_interval >= 1) is supported, without CSE_FLAG_GRAPH.  After the
+ * last boundary, cse_result_fetch gives the search's result (the same on
+ * every rank) and cse_result_procs / _counters / _method_ops this shard's
+ * processes (proc_count records). */
+int cse_search_shard(const cse_scheme* s, const cse_strategy_mix* mix, int32_t n_processes, int32_t proc_begin,
+                     int32_t proc_count, uint64_t seed, int64_t step_budget, const cse_opts* opts, void* cuda_stream,
+                     cse_result** out);
+/* Enqueues the next round's step kernels and waits for them; writes n_mats
+ * keys (host) and *rounds_left, the rounds left including this one (0: the
+ * search is finished, nothing ran).  CSE_EINVAL if the previous round's
+ * boundary is not completed. */
+int cse_shard_round(cse_result* shard, uint64_t* round_keys, int32_t* rounds_left);
+/* The best list of the process named by round_key (this shard's) in matrix
+ * mat: *len <= col_cap entries into list (host).  CSE_EINVAL if another shard
+ * holds that process. */
+int cse_shard_best_list(const cse_result* shard, int32_t mat, uint64_t round_key, int32_t* list, int32_t* len);
+/* Completes the round's sharing boundary (Section 3.5.2) with keys[n_mats],
+ * the minima over all shards; for a matrix whose winner is another shard's,
+ * lists[k * col_cap ..] and lens[k] hold its best list (host; may be NULL if
+ * every winner is this shard's).  Waits for the share kernel. */
+int cse_shard_share(cse_result* shard, const uint64_t* keys, const int32_t* lists, const int32_t* lens);
+
+/* Integer-pipe microbenchmark: the measured peaks behind the roofline of the
+ * step engine (integer bitset work, not a dense contraction).  Every resident
+ * thread of a one-wave grid (up to 32 warps per SM) runs 8 independent chains
+ * of one instruction mix for `iters` iterations:
+ *   kind 0  3-input XOR (LOP3) + add (IADD3)      2 lane-ops per step
+ *   kind 1  AND + popcount + add                   3 lane-ops per step
+ *   kind 2  32-bit multiply-add (IMAD)             1 lane-op per step
+ *   kind 3  32-bit multiply-high (IMAD.HI)         1 lane-op per step
+ * Writes *ops_per_clk_per_sm (lane-ops per SM clock, from clock64() spans of
+ * every block: independent of the clock frequency), *lane_ops_per_s (from
+ * CUDA events) and *seconds (the launch's event time).  Allocates and frees a
+ * small device buffer and synchronises the stream; CSE_EINVAL for a bad kind
+ * or iters outside [1, 2^40], CSE_ECUDA without a device. */
+int cse_int_peak(int32_t kind, int64_t iters, void* cuda_stream, double* ops_per_clk_per_sm,
+                 double* lane_ops_per_s, double* seconds);
+
 /* ---- A search that allocates no device memory ------------------------------
  * The paper has no counterpart: this is an integration aid.  Some callers may
  * not allocate device memory when they run a search -- a host that has handed
@@ -402,7 +505,12 @@ void cse_server_free(cse_server* s);
  *   - A search needing more scratch than CSE_STATIC_SCRATCH_BYTES is refused
  *     with CSE_ENOMEM before anything runs (the message gives the size).
  *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *     (cudaGetSymbolAddress) and keeps it for the life of the process; make
+ *     that first call before any stream capture.  A device reset
+ *     (cudaDeviceReset) makes the kept address stale: do not call this entry
+ *     point again in a process that has reset the device.
+ *   - Options as for cse_search, except that share_interval must be >= 1,
+ *     patience_rounds 0, and CSE_FLAG_GRAPH is refused (CSE_EINVAL).
  *   - The call enqueues on cuda_stream and waits for the search to finish.
  *   - All calls share the one array and each re-initialises what it reads;
  *     calls that overlap on the GPU (for example from two host threads) race

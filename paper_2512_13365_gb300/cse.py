@@ -32,13 +32,15 @@ class Mix(ctypes.Structure):
 class Opts(ctypes.Structure):
     _fields_ = [("share_interval", ctypes.c_uint32), ("share_permille", ctypes.c_uint32),
                 ("col_cap", ctypes.c_uint32), ("patience_rounds", ctypes.c_uint32),
-                ("max_spin", ctypes.c_uint64), ("procs_per_cta", ctypes.c_uint32), ("flags", ctypes.c_uint32)]
+                ("max_spin", ctypes.c_uint64), ("procs_per_cta", ctypes.c_uint32), ("flags", ctypes.c_uint32),
+                ("cta_list_cap", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
 class ProcRecord(ctypes.Structure):
     _fields_ = [("best_cost", ctypes.c_int64), ("best_len", ctypes.c_int32), ("runs", ctypes.c_int32),
                 ("best_hash", ctypes.c_uint64), ("traj_hash", ctypes.c_uint64), ("ops", ctypes.c_int64),
-                ("substeps", ctypes.c_int64), ("best_strategy", ctypes.c_int32), ("pad", ctypes.c_int32)]
+                ("substeps", ctypes.c_int64), ("best_strategy", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("method_ops", ctypes.c_int64)]
 
 
 class TuneEntry(ctypes.Structure):
@@ -49,7 +51,7 @@ class TuneEntry(ctypes.Structure):
 
 PROC_DTYPE = np.dtype([("best_cost", "<i8"), ("best_len", "<i4"), ("runs", "<i4"), ("best_hash", "<u8"),
                        ("traj_hash", "<u8"), ("ops", "<i8"), ("substeps", "<i8"), ("best_strategy", "<i4"),
-                       ("pad", "<i4")])
+                       ("pad", "<i4"), ("method_ops", "<i8")])
 STRATEGIES = ("gi", "ga", "gr", "wr", "mix", "g", "gp")  # best_strategy indices
 assert PROC_DTYPE.itemsize == ctypes.sizeof(ProcRecord)
 
@@ -57,18 +59,20 @@ _lib = None
 
 # every symbol include/cse.h declares
 EXPORTS = ["cse_opts_default", "cse_scheme_load", "cse_scheme_load_uvw", "cse_scheme_shape", "cse_search",
-           "cse_search_batch", "cse_autotune", "cse_tune_interval", "cse_result_fetch", "cse_result_procs", "cse_result_counters", "cse_result_timing",
+           "cse_search_batch", "cse_autotune", "cse_tune_interval", "cse_result_fetch", "cse_result_procs", "cse_result_counters", "cse_result_method_ops", "cse_result_timing",
            "cse_result_iterations", "cse_result_curve", "cse_result_hybrid", "cse_brent_check", "cse_philox", "cse_checkpoint_size",
            "cse_checkpoint_save", "cse_search_resume", "cse_result_launches",
            "cse_result_free", "cse_scheme_free", "cse_last_error",
            "cse_server_create", "cse_server_submit", "cse_server_cancel", "cse_server_wait", "cse_server_stats",
            "cse_server_peak",
            "cse_server_free",
-           "cse_search_static"]
+           "cse_search_static", "cse_int_peak", "cse_search_shard", "cse_shard_round", "cse_shard_best_list",
+           "cse_shard_share", "cse_flip_variants"]
 
 FLAG_GRAPH = 1
 FLAG_TRACE = 2
 FLAG_GI_SHARED_COINS = 4
+FLAG_WARP_ENGINE = 8
 
 
 def lib() -> ctypes.CDLL:
@@ -108,6 +112,7 @@ def lib() -> ctypes.CDLL:
     L.cse_result_fetch.argtypes = [vp, i32, pi32, i32, pi32, pi64, pi64]
     L.cse_result_procs.argtypes = [vp, i32, ctypes.POINTER(ProcRecord)]
     L.cse_result_counters.argtypes = [vp, pi64, pi64, pi64]
+    L.cse_result_method_ops.argtypes = [vp, pi64]
     L.cse_result_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float), pi32]
     L.cse_result_free.argtypes = [vp]
     L.cse_result_free.restype = None
@@ -121,6 +126,14 @@ def lib() -> ctypes.CDLL:
     L.cse_server_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                    ctypes.POINTER(ctypes.c_double), pi32]
     L.cse_search_static.argtypes = [vp, ctypes.POINTER(Mix), i32, u64, i64, ctypes.POINTER(Opts), vp, vp, vp]
+    L.cse_int_peak.argtypes = [i32, i64, vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                               ctypes.POINTER(ctypes.c_double)]
+    L.cse_search_shard.argtypes = [vp, ctypes.POINTER(Mix), i32, i32, i32, u64, i64, ctypes.POINTER(Opts), vp,
+                                   ctypes.POINTER(vp)]
+    L.cse_shard_round.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64), pi32]
+    L.cse_shard_best_list.argtypes = [vp, i32, ctypes.c_uint64, pi32, pi32]
+    L.cse_shard_share.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64), pi32, pi32]
+    L.cse_flip_variants.argtypes = [i32, i32, i32, i32, vp, vp, vp, i32, u64, i32, i32, vp, vp, vp, pi32, pi64]
     L.cse_server_free.argtypes = [vp]
     L.cse_server_free.restype = None
     for n in EXPORTS:
@@ -223,6 +236,12 @@ class Result:
         _check(lib().cse_result_counters(self.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
         return a.value, b.value, c.value
 
+    def method_ops(self) -> int:
+        """cse_result_method_ops: the method's own op count of the search."""
+        a = ctypes.c_int64()
+        _check(lib().cse_result_method_ops(self.handle, ctypes.byref(a)))
+        return a.value
+
     def timing(self) -> Tuple[float, float, int]:
         a, b, n = ctypes.c_float(), ctypes.c_float(), ctypes.c_int32()
         _check(lib().cse_result_timing(self.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(n)))
@@ -300,20 +319,36 @@ def philox(seed: int, counters: np.ndarray) -> np.ndarray:
     return out
 
 
+INT_PEAK_KINDS = ("lop3+iadd3", "and+popc+iadd", "imad", "imad.hi")
+
+
+def int_peak(kind: int, iters: int = 100000, stream=None) -> dict:
+    """cse_int_peak: measured lane-ops per SM clock (and per second) of one
+    integer instruction mix (INT_PEAK_KINDS[kind])."""
+    a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(lib().cse_int_peak(kind, iters, _stream_ptr(stream), ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return {"kind": INT_PEAK_KINDS[kind], "ops_per_clk_per_sm": a.value, "lane_ops_per_s": b.value,
+            "seconds": c.value}
+
+
 def make_mix(weights) -> Mix:
     w = list(weights) + [0] * (7 - len(weights))
     return Mix(*[int(x) for x in w])
 
 
 def make_opts(interval: int = 32, permille: int = 400, cap: int = 128, procs_per_cta: int = 0,
-              graph: bool = False, trace: bool = False, patience: int = 0, gi_shared: bool = False) -> Opts:
+              graph: bool = False, trace: bool = False, patience: int = 0, gi_shared: bool = False,
+              warp_engine: bool = False, cta_list_cap: int = 0) -> Opts:
     """interval 0 selects iteration mode (budget = maximum iterations, stop
-    after `patience` iterations without improvement)."""
+    after `patience` iterations without improvement).  warp_engine and
+    cta_list_cap choose how large matrices are launched; never results."""
     o = Opts()
     lib().cse_opts_default(ctypes.byref(o))
     o.share_interval, o.share_permille, o.col_cap, o.procs_per_cta = interval, permille, cap, procs_per_cta
     o.patience_rounds = patience
-    o.flags = (FLAG_GRAPH if graph else 0) | (FLAG_TRACE if trace else 0) | (FLAG_GI_SHARED_COINS if gi_shared else 0)
+    o.flags = ((FLAG_GRAPH if graph else 0) | (FLAG_TRACE if trace else 0) |
+               (FLAG_GI_SHARED_COINS if gi_shared else 0) | (FLAG_WARP_ENGINE if warp_engine else 0))
+    o.cta_list_cap = cta_list_cap
     return o
 
 
@@ -349,10 +384,12 @@ class Options:
 
 def search(scheme: Scheme, weights, n_proc: int, seed: int, budget: int, interval: int = 32,
            permille: int = 400, cap: int = 128, stream=None, procs_per_cta: int = 0, graph: bool = False,
-           trace: bool = False, patience: int = 0, gi_shared: bool = False) -> Result:
+           trace: bool = False, patience: int = 0, gi_shared: bool = False, warp_engine: bool = False,
+           cta_list_cap: int = 0) -> Result:
     """cse_search: enqueue the search and return its Result handle."""
     mix = make_mix(weights)
-    opts = make_opts(interval, permille, cap, procs_per_cta, graph, trace, patience, gi_shared)
+    opts = make_opts(interval, permille, cap, procs_per_cta, graph, trace, patience, gi_shared, warp_engine,
+                     cta_list_cap)
     h = ctypes.c_void_p()
     _check(lib().cse_search(scheme.handle, ctypes.byref(mix), n_proc, seed, budget, ctypes.byref(opts),
                             _stream_ptr(stream), ctypes.byref(h)))
@@ -441,6 +478,145 @@ def tune_interval(schemes, weights, n_procs, seeds, budgets, candidates=(16, 32,
     _check(lib().cse_tune_interval(*args, c, len(candidates), trial_steps, _stream_ptr(stream), ctypes.byref(best),
                                    ctypes.byref(tot)))
     return best.value, tot.value
+
+
+def flip_variants(m: int, n: int, p: int, U: np.ndarray, V: np.ndarray, W: np.ndarray, n_variants: int, seed: int,
+                  iteration: int, max_flips: int = 16):
+    """cse_flip_variants: (flips per variant, U, V, W stacked by variant,
+    violated Brent equations per variant), all generated and checked on the
+    device (Section 3.5.3)."""
+    U, V, W = (np.ascontiguousarray(x, dtype=np.int8) for x in (U, V, W))
+    r = U.shape[0]
+    if U.shape != (r, m * n) or V.shape != (r, n * p) or W.shape != (r, m * p):
+        raise ValueError("U, V, W must be r x mn, r x np, r x mp")
+    oU = np.zeros((n_variants, r, m * n), np.int8)
+    oV = np.zeros((n_variants, r, n * p), np.int8)
+    oW = np.zeros((n_variants, r, m * p), np.int8)
+    fl = np.zeros(n_variants, np.int32)
+    bad = np.zeros(n_variants, np.int64)
+    _check(lib().cse_flip_variants(m, n, p, r, U.ctypes.data, V.ctypes.data, W.ctypes.data, n_variants, seed,
+                                   iteration, max_flips, oU.ctypes.data, oV.ctypes.data, oW.ctypes.data,
+                                   fl.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                   bad.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
+    return fl, oU, oV, oW, bad
+
+
+def flip_search(m: int, n: int, p: int, U: np.ndarray, V: np.ndarray, W: np.ndarray, weights, n_variants: int = 32,
+                n_proc: int = 1024, seed: int = 0, iterations: int = 4, budget: int = 256, interval: int = 32,
+                permille: int = 400, cap: int = 256, max_flips: int = 16, stream=None) -> dict:
+    """The random-flip mode (Section 3.5.3): every iteration regenerates
+    n_variants variants of the scheme (variant 0 the scheme itself), checks
+    them on the device, and searches all of them side by side (one search of
+    n_proc processes per variant, in one batch, seed + iteration); the best
+    total over every variant and iteration is kept.  Returns the best
+    (iteration, variant, total, costs, lists, U, V, W) and every total."""
+    best, totals = None, []
+    for it in range(iterations):
+        fl, vU, vV, vW, bad = flip_variants(m, n, p, U, V, W, n_variants, seed, it, max_flips)
+        if bad.any():
+            raise CseError(CSE_ESTATE, f"flip variants broke a Brent equation: {bad.tolist()}")
+        schemes = [Scheme.from_uvw(m, n, p, vU[v], vV[v], vW[v]) for v in range(n_variants)]
+        rs = search_batch(schemes, [weights] * n_variants, [n_proc] * n_variants, [seed + it] * n_variants,
+                          [budget] * n_variants, interval, permille, cap, stream=stream, graph=True)
+        row = []
+        for v, r in enumerate(rs):
+            tot = r.total
+            row.append(tot)
+            if best is None or tot < best["total"]:
+                best = {"iteration": it, "variant": v, "flips": int(fl[v]), "total": tot, "costs": r.costs,
+                        "lists": r.lists, "U": vU[v].copy(), "V": vV[v].copy(), "W": vW[v].copy()}
+            r.free()
+        for sc in schemes:
+            sc.free()
+        totals.append(row)
+    best["totals"] = totals
+    return best
+
+
+def shard_range(n_proc: int, rank: int, world: int) -> Tuple[int, int]:
+    """(first process, count) of rank's shard of n_proc processes."""
+    b, e = rank * n_proc // world, (rank + 1) * n_proc // world
+    return b, e - b
+
+
+def exchange_boundary(keys: Sequence[int], best_list, cap: int, group=None, device="cpu"):
+    """The sharing-boundary exchange of a search split across ranks
+    (torch.distributed): the minimum over the ranks of each matrix's round
+    key (best Cost << 32 | global process), and the winner's best list, sent
+    by the rank that owns it.  best_list(k, key) returns this rank's list for
+    a key it owns, or None.  Two collectives per round: an allreduce-min of
+    the keys and an allreduce-sum of one row of (length, list) per matrix,
+    filled only by the owner.  Returns (keys, lists, lens) as numpy arrays."""
+    import torch
+    import torch.distributed as dist
+    n = len(keys)
+    k = torch.tensor([int(x) if int(x) < (1 << 63) else (1 << 63) - 1 for x in keys], dtype=torch.int64,
+                     device=device)
+    dist.all_reduce(k, op=dist.ReduceOp.MIN, group=group)
+    gk = [int(x) for x in k.cpu().tolist()]
+    rows = torch.zeros((n, cap + 1), dtype=torch.int64, device=device)
+    for m in range(n):
+        got = best_list(m, gk[m])
+        if got is not None:
+            rows[m, 0] = len(got)
+            if got:
+                rows[m, 1:1 + len(got)] = torch.tensor(got, dtype=torch.int64)
+    dist.all_reduce(rows, op=dist.ReduceOp.SUM, group=group)
+    rows = rows.cpu().numpy()
+    lens = rows[:, 0].astype(np.int32)
+    lists = np.ascontiguousarray(rows[:, 1:].astype(np.int32))
+    gk = [x if x < (1 << 63) - 1 else (1 << 64) - 1 for x in gk]  # no report: the all-ones key
+    return np.array(gk, dtype=np.uint64), lists, lens
+
+
+class Shard(Result):
+    """One rank's shard of a search split across ranks (cse_search_shard)."""
+
+    def __init__(self, scheme: Scheme, weights, n_proc: int, rank: int, world: int, seed: int, budget: int,
+                 interval: int = 32, permille: int = 400, cap: int = 128, stream=None, trace: bool = False,
+                 procs_per_cta: int = 0):
+        self.begin, count = shard_range(n_proc, rank, world)
+        h = ctypes.c_void_p()
+        opts = make_opts(interval, permille, cap, procs_per_cta, trace=trace)
+        _check(lib().cse_search_shard(scheme.handle, ctypes.byref(make_mix(weights)), n_proc, self.begin, count,
+                                      seed, budget, ctypes.byref(opts), _stream_ptr(stream), ctypes.byref(h)))
+        super().__init__(h, len(scheme.mats), count, cap)
+        self._scheme = scheme
+
+    def round(self):
+        """(this shard's round keys, rounds left including this one)."""
+        keys = (ctypes.c_uint64 * self.n_mats)()
+        left = ctypes.c_int32()
+        _check(lib().cse_shard_round(self.handle, keys, ctypes.byref(left)))
+        return [int(x) for x in keys], left.value
+
+    def best_list(self, mat: int, key: int):
+        """The best list of the process named by key, or None if another shard holds it."""
+        proc = key & 0xFFFFFFFF
+        if not (self.begin <= proc < self.begin + self.n_proc):
+            return None
+        buf = (ctypes.c_int32 * self.cap)()
+        n = ctypes.c_int32()
+        _check(lib().cse_shard_best_list(self.handle, mat, key, buf, ctypes.byref(n)))
+        return [int(buf[x]) for x in range(n.value)]
+
+    def share(self, keys, lists=None, lens=None):
+        k = (ctypes.c_uint64 * self.n_mats)(*[int(x) for x in keys])
+        lp = None if lists is None else np.ascontiguousarray(lists, dtype=np.int32)
+        ln = None if lens is None else np.ascontiguousarray(lens, dtype=np.int32)
+        _check(lib().cse_shard_share(self.handle, k,
+                                     None if lp is None else lp.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                     None if ln is None else ln.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))))
+
+    def run(self, group=None, device="cpu") -> "Shard":
+        """Every round of the search, with the boundary exchange over the
+        process group (torch.distributed) after each."""
+        while True:
+            keys, left = self.round()
+            if left == 0:
+                return self
+            gk, lists, lens = exchange_boundary(keys, self.best_list, self.cap, group, device)
+            self.share(gk, lists, lens)
 
 
 class Server:

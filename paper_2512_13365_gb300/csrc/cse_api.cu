@@ -12,6 +12,7 @@
 #include <map>
 #include <mutex>
 #include <new>
+#include <set>
 #include <string>
 #include <thread>
 #include <vector>
@@ -63,13 +64,17 @@ uint64_t fnv(uint64_t h, uint32_t w) { return (h ^ w) * 0x100000001B3ull; }
 // Iteration mode: rounds enqueued between two reads of the convergence state.
 constexpr int kIterationChunk = 4;
 
+// Keeps freed search memory in the current device's default pool (no
+// release threshold), once per device; callers may be on any thread.
 void set_pool_threshold_once() {
-    static bool done = false;
-    if (done) return;
-    done = true;
+    static std::mutex mu;
+    static std::set<int> done;
     int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!done.insert(dev).second) return;
     cudaMemPool_t pool;
-    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
         uint64_t thr = UINT64_MAX;
         cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
     }
@@ -128,6 +133,7 @@ struct SearchDev {
     cse_strategy_mix mix{};
     cse_opts opts{};
     uint64_t seed = 0;
+    uint64_t input_hash = 0;  // the scheme's (a checkpoint records it)
 };
 
 // A checkpoint: this header, then the search's device block byte for byte.
@@ -140,9 +146,10 @@ struct CkptHeader {
     cse_strategy_mix mix;
     int64_t done;     // steps (iterations in iteration mode) already run
     uint64_t bytes;   // size of the device block that follows
+    uint64_t input_hash;  // the scheme's cse_scheme::input_hash
 };
 constexpr uint64_t kCkptMagic = 0x3154504B43455343ull;  // "CSECKPT1" as little-endian bytes
-constexpr uint32_t kCkptVersion = 1;
+constexpr uint32_t kCkptVersion = 2;
 
 // Resume of one search from a checkpoint (run_batch).
 struct Resume {
@@ -160,6 +167,9 @@ struct LaunchSet {
         WarpLayout L;
         int ppc;
         ClassKey key;
+        bool cta = false;        // large matrices on the process-per-CTA engine
+        CtaLayout CL{};
+        int* redo_list = nullptr;  // processes it hands back to the warp engine
     };
     std::vector<DevMat> mats;
     std::vector<DevSearch> searches;
@@ -168,7 +178,7 @@ struct LaunchSet {
     void* d_params = nullptr;
     DevMat* d_mats = nullptr;
     DevSearch* d_searches = nullptr;
-    int* d_work = nullptr;  // one work counter per group (round kernel launch)
+    int* d_work = nullptr;  // three work counters per group (round kernel launches; see launch_round_cta)
     bool gs = false;  // the searches use shared Greedy-Intersections coins
 };
 
@@ -203,10 +213,20 @@ struct Batch {
     }
 };
 
+// A shard of a search split across ranks: its rounds are enqueued one at a
+// time (cse_shard_round), and each sharing boundary is completed with the
+// minima and winner lists of all shards (cse_shard_share).
+struct ShardState {
+    int rounds_done = 0;
+    bool in_round = false;  // a round ran and its boundary is not completed yet
+    int32_t total = 0, offset = 0;
+};
+
 struct cse_result {
     SearchDev* sd = nullptr;     // owned
     Batch* batch = nullptr;      // shared (static launches), or NULL (served)
     double latency_ms = 0.0;     // served requests: submit to completion
+    ShardState* shard = nullptr; // owned; a shard of a search split across ranks
 };
 
 static void search_free(SearchDev* sd) {
@@ -229,7 +249,9 @@ static int check_opts(const cse_opts* opts_in, cse_opts* opts) {
     else
         cse_opts_default(opts);
     if (opts->share_permille > 1000) return fail(CSE_EINVAL, "share_permille must be <= 1000");
-    if ((opts->flags & ~(uint32_t)(CSE_FLAG_GRAPH | CSE_FLAG_TRACE | CSE_FLAG_GI_SHARED_COINS)) != 0)
+    if ((opts->flags & ~(uint32_t)(CSE_FLAG_GRAPH | CSE_FLAG_TRACE | CSE_FLAG_GI_SHARED_COINS |
+                                   CSE_FLAG_WARP_ENGINE)) != 0 ||
+        opts->reserved != 0)
         return fail(CSE_EINVAL, "reserved option fields must be 0");
     if (opts->share_interval != 0 && opts->patience_rounds != 0)
         return fail(CSE_EINVAL, "patience_rounds applies to iteration mode (share_interval = 0) only");
@@ -282,6 +304,7 @@ static int search_plan(const cse_scheme* s, const cse_strategy_mix* mix, int n_p
         offs->push_back(cv.take(8));                                    // result meta
         offs->push_back(cv.take(32));                                   // counters
         offs->push_back(cv.take((size_t)kCurvePoints * 4));             // best-Cost curve
+        offs->push_back(cv.take((size_t)(cap + 1) * 4));                // a shard's external winner list
     }
     offs->push_back(cv.take(4));   // clock
     offs->push_back(cv.take(4));   // status
@@ -307,6 +330,7 @@ static int search_create(const cse_scheme* s, const cse_strategy_mix* mix, int n
     sd->mix = *mix;
     sd->opts = opts;
     sd->seed = seed;
+    sd->input_hash = s->input_hash;
     set_pool_threshold_once();
     cudaError_t e = cudaMallocAsync(&sd->d_block, sd->bytes, stream);
     if (e != cudaSuccess) {
@@ -330,16 +354,16 @@ static int search_create(const cse_scheme* s, const cse_strategy_mix* mix, int n
     S.interval = (int32_t)opts.share_interval;
     S.patience = (int32_t)opts.patience_rounds;
     S.share_thr = ((uint64_t)opts.share_permille << 32) / 1000u;
-    S.clock = (int32_t*)(b + of[9 * s->n_mats]);
-    S.status = (int32_t*)(b + of[9 * s->n_mats + 1]);
-    S.conv = (int32_t*)(b + of[9 * s->n_mats + 2]);
+    S.clock = (int32_t*)(b + of[10 * s->n_mats]);
+    S.status = (int32_t*)(b + of[10 * s->n_mats + 1]);
+    S.conv = (int32_t*)(b + of[10 * s->n_mats + 2]);
     S.n_mats = s->n_mats;
     S.trace = (opts.flags & CSE_FLAG_TRACE) ? 1 : 0;
     S.gi_shared = (opts.flags & CSE_FLAG_GI_SHARED_COINS) ? 1 : 0;
     static const int32_t snap_init[2] = {INT_MAX, 0};
     for (int k = 0; k < s->n_mats; k++) {
         DevMat& M = sd->mats[k];
-        const size_t* o = &of[9 * k];
+        const size_t* o = &of[10 * k];
         M.pn0 = s->d_pn0[k];
         M.cand0 = s->d_cand0[k];
         M.meta0 = s->d_meta0[k];
@@ -359,6 +383,9 @@ static int search_create(const cse_scheme* s, const cse_strategy_mix* mix, int n
         M.result_meta = (int32_t*)(b + o[6]);
         M.counters = (unsigned long long*)(b + o[7]);
         M.curve = (int32_t*)(b + o[8]);
+        M.proc_offset = 0;
+        M.ext_list = (const int32_t*)(b + o[9]);
+        M.ext_len = (const int32_t*)(b + o[9]) + sd->cap;
         // initial values: no round minimum, no snapshot, result = the input
         if (e == cudaSuccess) e = cudaMemsetAsync(M.round_min, 0xFF, 8, stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(M.snap_meta, snap_init, 8, cudaMemcpyHostToDevice, stream);
@@ -403,7 +430,7 @@ static int build_launch(const std::vector<SearchDev*>& act, int ppc_req, const T
         ls->mats[q] = sd->mats[refs[q].mat];
         ls->mats[q].search = refs[q].search;
         if (ls->groups.empty() || ls->groups.back().W != refs[q].W || ls->groups.back().gm != (refs[q].gm != 0))
-            ls->groups.push_back({refs[q].W, q, 0, 0, 0, 0, refs[q].gm != 0, {}, 0, {}});
+            ls->groups.push_back({refs[q].W, q, 0, 0, 0, 0, refs[q].gm != 0, {}, 0, {}, false, {}, nullptr});
         LaunchSet::Group& g = ls->groups.back();
         ls->mats[q].unit_base = g.units;
         g.count++;
@@ -428,7 +455,11 @@ static int build_launch(const std::vector<SearchDev*>& act, int ppc_req, const T
         if (!g.gm)
             while (g.ppc > 1 && (long long)g.L.per_warp * g.ppc > smem_max) g.ppc--;
         if (!g.gm && g.L.per_warp > smem_max) return fail(CSE_ENOMEM, "process slice exceeds shared memory");
-        cudaError_t e = prepare_round(g.W, g.gm, ls->gs, g.L, g.ppc);
+        if (g.gm && !ls->gs && !(act[0]->opts.flags & CSE_FLAG_WARP_ENGINE)) {
+            g.CL = make_cta_layout(g.W, g.cap, g.mmax, (int)act[0]->opts.cta_list_cap, smem_max);
+            g.cta = g.CL.bytes > 0;
+        }
+        cudaError_t e = g.cta ? prepare_round_cta(g.W, g.CL, g.ppc) : prepare_round(g.W, g.gm, ls->gs, g.L, g.ppc);
         if (e != cudaSuccess) return fail(CSE_ECUDA, std::string("kernel attributes: ") + cudaGetErrorString(e));
         if (trial && trial->keys) trial->keys->push_back(g.key);
     }
@@ -441,7 +472,10 @@ static int build_launch(const std::vector<SearchDev*>& act, int ppc_req, const T
     for (int q = 0; q < nm; q++) ls->pos[fill[refs[q].search]++] = q;
     Carve cv;
     const size_t om = cv.take(sizeof(DevMat) * nm), os = cv.take(sizeof(DevSearch) * n), op = cv.take(4 * (size_t)nm);
-    const size_t ow = cv.take(4 * ls->groups.size());
+    const size_t ow = cv.take(3 * 4 * ls->groups.size());
+    std::vector<size_t> oredo(ls->groups.size(), 0);
+    for (size_t gi = 0; gi < ls->groups.size(); gi++)
+        if (ls->groups[gi].cta) oredo[gi] = cv.take(4 * (size_t)ls->groups[gi].units);
     cudaError_t e = cudaMallocAsync(&ls->d_params, cv.off, stream);
     if (e != cudaSuccess) {
         ls->d_params = nullptr;
@@ -451,6 +485,8 @@ static int build_launch(const std::vector<SearchDev*>& act, int ppc_req, const T
     ls->d_mats = (DevMat*)(b + om);
     ls->d_searches = (DevSearch*)(b + os);
     ls->d_work = (int*)(b + ow);
+    for (size_t gi = 0; gi < ls->groups.size(); gi++)
+        if (ls->groups[gi].cta) ls->groups[gi].redo_list = (int*)(b + oredo[gi]);
     ls->searches.resize(n);
     for (int i = 0; i < n; i++) {
         ls->searches[i] = act[i]->search;
@@ -461,7 +497,7 @@ static int build_launch(const std::vector<SearchDev*>& act, int ppc_req, const T
         e = cudaMemcpyAsync(ls->d_searches, ls->searches.data(), sizeof(DevSearch) * n, cudaMemcpyHostToDevice,
                             stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(b + op, ls->pos.data(), 4 * (size_t)nm, cudaMemcpyHostToDevice, stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(ls->d_work, 0, 4 * ls->groups.size(), stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ls->d_work, 0, 3 * 4 * ls->groups.size(), stream);
     if (e != cudaSuccess) return fail(CSE_ECUDA, std::string("parameter upload: ") + cudaGetErrorString(e));
     return CSE_OK;
 }
@@ -477,8 +513,10 @@ static cudaError_t enqueue_round(const LaunchSet& ls, cudaStream_t st, const std
         for (size_t gi = 0; gi < ng; gi++) {
             const auto& g = ls.groups[gi];
             cudaStreamWaitEvent((*aux)[gi], (*fork)[0], 0);
-            e = launch_round(g.W, g.gm, ls.gs, ls.d_mats + g.begin, g.count, ls.d_searches, g.units,
-                             ls.d_work + gi, g.L, g.ppc, (*aux)[gi]);
+            e = g.cta ? launch_round_cta(g.W, ls.d_mats + g.begin, g.count, ls.d_searches, g.units,
+                                         ls.d_work + 3 * gi, g.redo_list, g.CL, g.ppc, (*aux)[gi])
+                      : launch_round(g.W, g.gm, ls.gs, ls.d_mats + g.begin, g.count, ls.d_searches, g.units,
+                                     ls.d_work + 3 * gi, g.L, g.ppc, (*aux)[gi]);
             if (e != cudaSuccess) return e;
             cudaEventRecord((*fork)[gi + 1], (*aux)[gi]);
             cudaStreamWaitEvent(st, (*fork)[gi + 1], 0);
@@ -487,13 +525,15 @@ static cudaError_t enqueue_round(const LaunchSet& ls, cudaStream_t st, const std
         for (size_t gi = 0; gi < ng; gi++) {
             const auto& g = ls.groups[gi];
             if (group_ev) cudaEventRecord(group_ev[2 * gi], st);
-            e = launch_round(g.W, g.gm, ls.gs, ls.d_mats + g.begin, g.count, ls.d_searches, g.units,
-                             ls.d_work + gi, g.L, g.ppc, st);
+            e = g.cta ? launch_round_cta(g.W, ls.d_mats + g.begin, g.count, ls.d_searches, g.units,
+                                         ls.d_work + 3 * gi, g.redo_list, g.CL, g.ppc, st)
+                      : launch_round(g.W, g.gm, ls.gs, ls.d_mats + g.begin, g.count, ls.d_searches, g.units,
+                                     ls.d_work + 3 * gi, g.L, g.ppc, st);
             if (e != cudaSuccess) return e;
             if (group_ev) cudaEventRecord(group_ev[2 * gi + 1], st);
         }
     }
-    return launch_share(ls.d_mats, ls.d_searches, (int)ls.searches.size(), ls.d_work, (int)ng, st);
+    return launch_share(ls.d_mats, ls.d_searches, (int)ls.searches.size(), ls.d_work, 3 * (int)ng, st);
 }
 
 // Builds and enqueues n independent searches as one static launch sequence.
@@ -846,6 +886,12 @@ int cse_scheme_load(const int8_t* const* mats, const int32_t* rows, const int32_
                                         " a candidate list holds");
         }
     }
+    uint64_t ih = 0xCBF29CE484222325ull;
+    for (int k = 0; k < n_mats; k++) {
+        ih = fnv(fnv(ih, (uint32_t)s->rows[k]), (uint32_t)s->cols[k]);
+        for (size_t x = 0; x < (size_t)s->rows[k] * s->cols[k]; x++) ih = fnv(ih, (uint32_t)(uint8_t)mats[k][x]);
+    }
+    s->input_hash = ih;
     *out = s;
     return CSE_OK;
 }
@@ -964,6 +1010,7 @@ int cse_checkpoint_save(const cse_result* r, void* host_buf, size_t bytes) {
     h.mix = sd->mix;
     h.done = sd->budget;
     h.bytes = sd->bytes;
+    h.input_hash = sd->input_hash;
     std::memcpy(host_buf, &h, sizeof h);
     CUDA_TRY(cudaMemcpy((char*)host_buf + sizeof h, sd->d_block, sd->bytes, cudaMemcpyDeviceToHost));
     return CSE_OK;
@@ -982,6 +1029,8 @@ int cse_search_resume(const cse_scheme* s, const void* ckpt, size_t bytes, int64
     if (h.n_mats != s->n_mats) return fail(CSE_EINVAL, "checkpoint of another scheme");
     for (int k = 0; k < s->n_mats; k++)
         if (h.rows[k] != s->rows[k] || h.cols[k] != s->cols[k]) return fail(CSE_EINVAL, "checkpoint of another scheme");
+    if (h.input_hash != s->input_hash)
+        return fail(CSE_EINVAL, "checkpoint of another scheme: the matrices differ from those it was taken on");
     cse_opts opts;
     cse_opts_default(&opts);
     if (launch_opts) opts = *launch_opts;  // the launch fields (procs_per_cta) come from the caller
@@ -1142,6 +1191,7 @@ int cse_result_procs(const cse_result* r, int32_t mat, cse_proc_record* out) {
             out[p].substeps = 0;
             out[p].best_strategy = -1;
             out[p].pad = 0;
+            out[p].method_ops = 0;
         }
         return CSE_OK;
     }
@@ -1164,6 +1214,7 @@ int cse_result_procs(const cse_result* r, int32_t mat, cse_proc_record* out) {
         o.substeps = (int32_t)h[H_SUBSTEPS];
         o.best_strategy = (int32_t)h[H_BEST_STRAT];
         o.pad = 0;
+        o.method_ops = (int64_t)((uint64_t)h[H_MOPS_LO] | (uint64_t)h[H_MOPS_HI] << 32);
     }
     return CSE_OK;
 }
@@ -1204,6 +1255,21 @@ int cse_result_counters(const cse_result* r, int64_t* process_steps, int64_t* su
         *process_steps = sd->search.interval == 0 ? (int64_t)steps : (int64_t)sd->n_mats * sd->n_proc * sd->budget;
     if (substeps) *substeps = (int64_t)sub;
     if (alg_ops) *alg_ops = (int64_t)ops;
+    return CSE_OK;
+}
+
+int cse_result_method_ops(const cse_result* r, int64_t* method_ops) {
+    int rc = wait_result(r);
+    if (rc) return rc;
+    if (!method_ops) return fail(CSE_EINVAL, "method_ops is NULL");
+    const SearchDev* sd = r->sd;
+    uint64_t mops = 0;
+    for (int k = 0; k < sd->n_mats; k++) {
+        unsigned long long c[4];
+        CUDA_TRY(cudaMemcpy(c, sd->mats[k].counters, 32, cudaMemcpyDeviceToHost));
+        mops += c[3];
+    }
+    *method_ops = (int64_t)mops;
     return CSE_OK;
 }
 
@@ -1274,10 +1340,148 @@ int cse_result_hybrid(const cse_result* const* results, int32_t n_results, int32
     return CSE_OK;
 }
 
+int cse_search_shard(const cse_scheme* s, const cse_strategy_mix* mix, int32_t n_processes, int32_t proc_begin,
+                     int32_t proc_count, uint64_t seed, int64_t step_budget, const cse_opts* opts_in, void* cuda_stream,
+                     cse_result** out) {
+    NvtxRange nvtx("cse_search_shard");
+    if (!out) return fail(CSE_EINVAL, "out is NULL");
+    *out = nullptr;
+    cse_opts opts;
+    int rc = check_opts(opts_in, &opts);
+    if (rc) return rc;
+    if (opts.share_interval == 0) return fail(CSE_EINVAL, "a shard runs the step clock (share_interval >= 1)");
+    if (opts.flags & CSE_FLAG_GRAPH) return fail(CSE_EINVAL, "a shard's rounds are enqueued one at a time: no graph");
+    if (n_processes < 1 || n_processes > (1 << 20) || proc_begin < 0 || proc_count < 1 ||
+        (int64_t)proc_begin + proc_count > n_processes)
+        return fail(CSE_EINVAL, "need 0 <= proc_begin < proc_begin + proc_count <= n_processes <= 2^20");
+    if (max_smem_per_block() <= 0) return fail(CSE_ECUDA, "no CUDA device");
+    cudaStream_t stream = (cudaStream_t)cuda_stream;
+    SearchDev* sd = nullptr;
+    rc = search_create(s, mix, proc_count, seed, step_budget, opts, stream, &sd);
+    if (rc) return rc;
+    for (auto& M : sd->mats) M.proc_offset = proc_begin;
+    Batch* B = new (std::nothrow) Batch();
+    cse_result* r = new (std::nothrow) cse_result();
+    ShardState* sh = new (std::nothrow) ShardState();
+    auto bail = [&](int code, const std::string& msg) {
+        if (B) {
+            B->ev_end = nullptr;
+            B->release();
+        }
+        delete B;
+        delete r;
+        delete sh;
+        search_free(sd);
+        return fail(code, msg);
+    };
+    if (!B || !r || !sh) return bail(CSE_ENOMEM, "host allocation");
+    B->stream = stream;
+    rc = build_launch({sd}, (int)opts.procs_per_cta, nullptr, stream, &B->ls);
+    if (rc) return bail(rc, cse_last_error());
+    cudaError_t e = cudaEventCreate(&B->ev_begin);
+    if (e == cudaSuccess) e = cudaEventCreate(&B->ev_end);
+    B->ev_round.assign(2 * (size_t)sd->rounds, nullptr);
+    for (auto& ev : B->ev_round)
+        if (e == cudaSuccess) e = cudaEventCreate(&ev);
+    if (e == cudaSuccess) e = cudaEventRecord(B->ev_begin, stream);
+    if (e != cudaSuccess) return bail(CSE_ECUDA, std::string("shard events: ") + cudaGetErrorString(e));
+    B->refs = 1;
+    sh->total = n_processes;
+    sh->offset = proc_begin;
+    r->sd = sd;
+    r->batch = B;
+    r->shard = sh;
+    *out = r;
+    return CSE_OK;
+}
+
+int cse_shard_round(cse_result* r, uint64_t* round_keys, int32_t* rounds_left) {
+    if (!r || !r->shard || !r->batch || !round_keys || !rounds_left) return fail(CSE_EINVAL, "not a shard, or NULL output");
+    ShardState* sh = r->shard;
+    SearchDev* sd = r->sd;
+    Batch* B = r->batch;
+    if (sh->in_round) return fail(CSE_EINVAL, "the previous round's boundary is not completed (cse_shard_share)");
+    if (sh->rounds_done >= sd->rounds) {
+        *rounds_left = 0;
+        return CSE_OK;
+    }
+    const LaunchSet& ls = B->ls;
+    cudaStream_t st = B->stream;
+    cudaEventRecord(B->ev_round[2 * sh->rounds_done], st);
+    for (size_t gi = 0; gi < ls.groups.size(); gi++) {
+        const auto& g = ls.groups[gi];
+        cudaError_t e = g.cta ? launch_round_cta(g.W, ls.d_mats + g.begin, g.count, ls.d_searches, g.units,
+                                                 ls.d_work + 3 * gi, g.redo_list, g.CL, g.ppc, st)
+                              : launch_round(g.W, g.gm, ls.gs, ls.d_mats + g.begin, g.count, ls.d_searches, g.units,
+                                             ls.d_work + 3 * gi, g.L, g.ppc, st);
+        if (e != cudaSuccess) return fail(CSE_ECUDA, std::string("round launch: ") + cudaGetErrorString(e));
+    }
+    cudaEventRecord(B->ev_round[2 * sh->rounds_done + 1], st);
+    for (int k = 0; k < sd->n_mats; k++)
+        CUDA_TRY(cudaMemcpyAsync(&round_keys[k], sd->mats[k].round_min, 8, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    int32_t status = 0;
+    CUDA_TRY(cudaMemcpy(&status, sd->search.status, 4, cudaMemcpyDeviceToHost));
+    if (status != 0) return fail(CSE_ESTATE, "device consistency check failed (candidate list overflow)");
+    sh->in_round = true;
+    *rounds_left = sd->rounds - sh->rounds_done;
+    return CSE_OK;
+}
+
+int cse_shard_best_list(const cse_result* r, int32_t mat, uint64_t round_key, int32_t* list, int32_t* len) {
+    if (!r || !r->shard || !list || !len) return fail(CSE_EINVAL, "not a shard, or NULL output");
+    const SearchDev* sd = r->sd;
+    if (mat < 0 || mat >= sd->n_mats) return fail(CSE_EINVAL, "matrix index out of range");
+    const int win = (int)(round_key & 0xFFFFFFFFu) - r->shard->offset;
+    if (win < 0 || win >= sd->n_proc) return fail(CSE_EINVAL, "the key's process is not in this shard");
+    const DevMat& M = sd->mats[mat];
+    int32_t n = 0;
+    CUDA_TRY(cudaMemcpy(&n, M.state + (size_t)win * M.state_words + H_BEST_LEN, 4, cudaMemcpyDeviceToHost));
+    if (n < 0 || n > sd->cap) return fail(CSE_ESTATE, "corrupt best-list length");
+    if (n > 0) CUDA_TRY(cudaMemcpy(list, M.best_list + (size_t)win * sd->cap, (size_t)n * 4, cudaMemcpyDeviceToHost));
+    *len = n;
+    return CSE_OK;
+}
+
+int cse_shard_share(cse_result* r, const uint64_t* keys, const int32_t* lists, const int32_t* lens) {
+    if (!r || !r->shard || !keys) return fail(CSE_EINVAL, "not a shard, or NULL keys");
+    ShardState* sh = r->shard;
+    SearchDev* sd = r->sd;
+    Batch* B = r->batch;
+    if (!sh->in_round) return fail(CSE_EINVAL, "no round to complete (cse_shard_round first)");
+    cudaStream_t st = B->stream;
+    for (int k = 0; k < sd->n_mats; k++) {
+        const DevMat& M = sd->mats[k];
+        const int win = (int)(keys[k] & 0xFFFFFFFFu) - sh->offset;
+        const bool local = win >= 0 && win < sd->n_proc;
+        if (keys[k] != ~0ull && (keys[k] & 0xFFFFFFFFu) >= (uint64_t)sh->total)
+            return fail(CSE_EINVAL, "a key names a process outside the search");
+        if (!local && keys[k] != ~0ull) {
+            if (!lists || !lens || lens[k] < 0 || lens[k] > sd->cap)
+                return fail(CSE_EINVAL, "another shard's winner needs its list and length");
+            CUDA_TRY(cudaMemcpyAsync((void*)M.ext_list, lists + (size_t)k * sd->cap, (size_t)lens[k] * 4,
+                                     cudaMemcpyHostToDevice, st));
+            CUDA_TRY(cudaMemcpyAsync((void*)M.ext_len, &lens[k], 4, cudaMemcpyHostToDevice, st));
+        }
+        CUDA_TRY(cudaMemcpyAsync(M.round_min, &keys[k], 8, cudaMemcpyHostToDevice, st));
+    }
+    cudaError_t e = launch_share(B->ls.d_mats, B->ls.d_searches, 1, B->ls.d_work, 3 * (int)B->ls.groups.size(), st);
+    if (e != cudaSuccess) return fail(CSE_ECUDA, std::string("share launch: ") + cudaGetErrorString(e));
+    sh->rounds_done++;
+    sh->in_round = false;
+    B->rounds = sh->rounds_done;
+    if (sh->rounds_done == sd->rounds) CUDA_TRY(cudaEventRecord(B->ev_end, st));
+    CUDA_TRY(cudaStreamSynchronize(st));  // the caller's key and list buffers may be reused on return
+    return CSE_OK;
+}
+
 int cse_result_launches(const cse_result* r, int32_t* kernels, int32_t* searches_in_launch) {
     if (!r || !r->sd) return fail(CSE_EINVAL, "NULL result");
     const Batch* B = r->batch;
-    if (kernels) *kernels = B ? B->rounds * ((int)B->ls.groups.size() + 1) : 0;
+    int per_round = 1;  // the share kernel, then per class one launch (two on the process-per-CTA engine)
+    if (B)
+        for (const auto& g : B->ls.groups) per_round += g.cta ? 2 : 1;
+    if (kernels) *kernels = B ? B->rounds * per_round : 0;
     if (searches_in_launch) *searches_in_launch = B ? (int32_t)B->ls.searches.size() : 0;
     return CSE_OK;
 }
@@ -1285,8 +1489,13 @@ int cse_result_launches(const cse_result* r, int32_t* kernels, int32_t* searches
 void cse_result_free(cse_result* r) {
     if (!r) return;
     Batch* B = r->batch;
-    if (B) cudaEventSynchronize(B->ev_end);
+    if (B && r->shard) {
+        cudaStreamSynchronize(B->stream);  // a shard records its end event only after its last boundary
+    } else if (B) {
+        cudaEventSynchronize(B->ev_end);
+    }
     search_free(r->sd);
+    delete r->shard;
     delete r;
     if (B && --B->refs == 0) {
         B->release();

@@ -27,6 +27,9 @@
 #include <algorithm>
 #include <climits>
 #include <cstdint>
+#include <map>
+#include <mutex>
+#include <utility>
 
 #include "cse_internal.h"
 
@@ -120,12 +123,15 @@ static __device__ __noinline__ uint4 philox_call(uint32_t c0, uint32_t c1, uint3
 // S_p = (c_p - 1) 2^16 + a N_p; argmax, lowest key on ties.  One candidate
 // per lane: its trial column x_k stays in registers and every column u is a
 // broadcast read of shared memory.  Adds the trial ops (5 W per live column
-// of the trial system, plus 8, per candidate) to *ops_total.  Kept out of line
+// of the trial system, plus 8, per candidate) to *ops_total, and the method
+// ops (the scan of m, and per candidate a trial rewrite: 6 per 64-bit word
+// plus the nnz of its rows, which is the sum over every column u of the
+// rows u shares with the trial column) to *mops_total.  Kept out of line
 // with plain values, not the engine: measured on the (3,3,3:23) search, the
 // step engine runs 7% faster than with this function inlined.
 template <int W>
 __device__ __noinline__ int gp_select(const uint2* P, const uint32_t* C, int ncols, int m, uint32_t a, int lane,
-                                      unsigned long long* ops_total) {
+                                      unsigned long long* ops_total, unsigned long long* mops_total) {
     int nlive = 0;
     for (int base = 0; base < ncols; base += 32) {
         const int u = base + lane;
@@ -138,7 +144,7 @@ __device__ __noinline__ int gp_select(const uint2* P, const uint32_t* C, int nco
     }
     uint32_t best_s = 0;
     int best_q = INT_MAX;
-    unsigned ops = 0;
+    unsigned ops = 0, mops = 0;
     for (int base = 0; base < m; base += 32) {
         const int p = base + lane;
         if (p < m) {
@@ -154,7 +160,7 @@ __device__ __noinline__ int gp_select(const uint2* P, const uint32_t* C, int nco
                 nni += __popc(A.x | A.y);
                 nnj += __popc(B.x | B.y);
             }
-            int N = 0;
+            int N = 0, rnnz = 0;
 #pragma unroll 2
             for (int u = 0; u < ncols; u++) {
                 int both = 0, ng = 0;
@@ -167,6 +173,7 @@ __device__ __noinline__ int gp_select(const uint2* P, const uint32_t* C, int nco
                 }
                 const int hit = (both - ng >= 2) + (ng >= 2);
                 N += (u == i || u == j) ? 0 : hit;
+                rnnz += both;
             }
             const uint32_t sc = ((uint32_t)(c - 1) << 16) + a * (uint32_t)N;
             if (best_q == INT_MAX || sc > best_s) {
@@ -175,13 +182,18 @@ __device__ __noinline__ int gp_select(const uint2* P, const uint32_t* C, int nco
             }
             const int live = nlive - (nni == c) - (nnj == c);
             ops += 5u * (unsigned)W * (unsigned)live + 8u;
+            mops += 6u * (unsigned)((W + 1) >> 1) + (unsigned)rnnz;
         }
     }
     const uint32_t top = __reduce_max_sync(FULL_MASK, best_q == INT_MAX ? 0u : best_s);
     const int q = (int)__reduce_min_sync(FULL_MASK, (best_q != INT_MAX && best_s == top) ? (uint32_t)best_q
                                                                                           : 0xFFFFFFFFu);
     ops = __reduce_add_sync(FULL_MASK, ops);
-    if (lane == 0) *ops_total += ops;
+    mops = __reduce_add_sync(FULL_MASK, mops);
+    if (lane == 0) {
+        *ops_total += ops;
+        *mops_total += mops + (unsigned)m;
+    }
     __syncwarp();
     return q;
 }
@@ -204,7 +216,8 @@ __device__ __forceinline__ uint32_t shared_coin_word(uint32_t proc, uint32_t t, 
 // arrays); adds the step's algorithmic ops to *tally.
 __device__ __forceinline__ int gi_shared_select(const uint32_t* C, uint32_t* G, uint32_t* XS, int ncols, int m,
                                                 int lane, uint32_t proc, uint32_t t, uint32_t c2s, uint64_t seed,
-                                                long long a, long long b, unsigned long long* tally) {
+                                                long long a, long long b, unsigned long long* tally,
+                                                unsigned long long* mtally) {
     for (int v = lane; v < ncols; v += 32) {
         G[v] = 0;
         XS[v] = 0;
@@ -263,7 +276,10 @@ __device__ __forceinline__ int gi_shared_select(const uint32_t* C, uint32_t* G, 
         }
     }
     best_q = warp_argmax_score(best_s, best_q);
-    if (lane == 0) *tally += 40u * (unsigned)((m + 127) >> 7) + 18u * (unsigned)m + 2u * (unsigned)ncols;
+    if (lane == 0) {
+        *tally += 40u * (unsigned)((m + 127) >> 7) + 18u * (unsigned)m + 2u * (unsigned)ncols;
+        *mtally += 5u * (unsigned)m;  // method ops: the scan, and 4 per candidate
+    }
     __syncwarp();
     return best_q;
 }
@@ -274,9 +290,10 @@ __device__ __forceinline__ int gi_shared_select(const uint32_t* C, uint32_t* G, 
 template <int W>
 __device__ __noinline__ int rare_select(int kind, const uint2* P, const uint32_t* C, uint32_t* G, uint32_t* XS,
                                         int ncols, int m, int lane, uint32_t proc, uint32_t t, uint32_t c2s,
-                                        uint64_t seed, long long a, long long b, unsigned long long* tally) {
-    if (kind == 0) return gp_select<W>(P, C, ncols, m, (uint32_t)a, lane, tally);
-    return gi_shared_select(C, G, XS, ncols, m, lane, proc, t, c2s, seed, a, b, tally);
+                                        uint64_t seed, long long a, long long b, unsigned long long* tally,
+                                        unsigned long long* mtally) {
+    if (kind == 0) return gp_select<W>(P, C, ncols, m, (uint32_t)a, lane, tally, mtally);
+    return gi_shared_select(C, G, XS, ncols, m, lane, proc, t, c2s, seed, a, b, tally, mtally);
 }
 
 // Per-process values touched a few times per step at most.  They live in
@@ -285,7 +302,9 @@ __device__ __noinline__ int rare_select(int kind, const uint2* P, const uint32_t
 struct Cold {
     unsigned long long traj;   // trajectory hash (CSE_FLAG_TRACE)
     unsigned long long ops;    // algorithmic-op total before this round
+    unsigned long long mops;   // method-op total before this round
     unsigned long long t_rare; // algorithmic ops of this round's gp and shared-coin gi steps
+    unsigned long long t_mrare; // method ops of this round's gp and shared-coin gi steps
     int runs, substeps, best_cost, best_len, trace, overflow, sub_before;
     int strat, a, b;           // the current run's strategy, alpha, beta
     int best_strat;            // strategy of the run that gave the best record (-1: none)
@@ -293,6 +312,7 @@ struct Cold {
     // can change, candidates scanned by g/ga/wr/gr; Greedy-Intersections
     // terms, Philox blocks and scored candidates
     unsigned t_sub, t_pairs, t_scan, t_gi_terms, t_gi_blocks, t_gi_cands;
+    unsigned t_nnz;            // method ops: nnz of the rewritten rows before their rewrites
 };
 
 template <int W, bool GM, bool GS>
@@ -303,6 +323,7 @@ struct Engine {
     const DevMat* M;
     const DevSearch* S;
     int proc, lane, cap, mmax;
+    uint32_t gproc;  // the global process index (draws, round keys)
     // warp-uniform state
     int ncols, nf, m, cost, ended;
 
@@ -327,8 +348,7 @@ struct Engine {
         return ((uint32_t)M->mat_index & 0xFFu) << 24 | (purpose & 0xFu) << 20 | (extra_hi & 0xFFFFFu);
     }
     __device__ __forceinline__ uint4 draw(int t, uint32_t purpose) const {
-        return philox_call((uint32_t)proc, (uint32_t)t, c2(purpose, 0), 0u, (uint32_t)S->seed,
-                           (uint32_t)(S->seed >> 32));
+        return philox_call(gproc, (uint32_t)t, c2(purpose, 0), 0u, (uint32_t)S->seed, (uint32_t)(S->seed >> 32));
     }
 
     // c(a, b, s) for columns a < b
@@ -402,8 +422,11 @@ struct Engine {
             if (keep) C[newm + __popc(kb & lt)] = e;
             newm += __popc(kb);
         }
-        // the new pairs (u, k): x_k has the largest index, so they sort last
-        int nu = 0;
+        // the new pairs (u, k): x_k has the largest index, so they sort last.
+        // rb sums, over the columns u, the rewritten rows u still holds: with
+        // 2 c for x_i and x_j it is the nnz of the rewritten rows before the
+        // rewrite (the method op count)
+        int nu = 0, rb = 0;
         for (int base = 0; base < k; base += 32) {
             const int u = base + lane;
             int cp = 0, cm = 0;
@@ -422,6 +445,7 @@ struct Engine {
                 live = sup != 0;
                 cm = ng;
                 cp = both - ng;
+                rb += both;
             }
             nu += __popc(__ballot_sync(FULL_MASK, live));
             const bool ep = cp >= 2, em = cm >= 2;
@@ -443,10 +467,12 @@ struct Engine {
         ncols++;
         cost -= c - 1;
         m = newm;
+        rb = __reduce_add_sync(FULL_MASK, rb);
         if (lane == 0) {
             Cold* cd = cold();
             cd->t_sub++;
             cd->t_pairs += (unsigned)(nij + nu);
+            cd->t_nnz += (unsigned)(rb + 2 * c);
         }
         __syncwarp();
     }
@@ -477,7 +503,7 @@ struct Engine {
         if (lane == 0) cold()->runs++;
         const uint4 R = draw(t, PU_RUN);
         int strat = ST_G;
-        if (!(proc == 0 && t == 0)) {
+        if (!(gproc == 0 && t == 0)) {
             const uint32_t x = scale32(R.x, S->wsum);
             uint32_t acc = 0;
             for (int s = 0; s < ST_N; s++) {
@@ -696,7 +722,7 @@ struct Engine {
                     const int nb0 = (n0 + 63) >> 6, nb1 = (n1 + 63) >> 6;
                     nb = nb0 > nb1 ? nb0 : nb1;
                     for (int blk = 0; blk < nb; blk++) {
-                        uint32_t r0 = (uint32_t)proc, r1 = (uint32_t)t, r2 = c2g | (uint32_t)blk, r3 = key;
+                        uint32_t r0 = gproc, r1 = (uint32_t)t, r2 = c2g | (uint32_t)blk, r3 = key;
                         philox(r0, r1, r2, r3, k0, k1);
                         const int x0 = blk << 6;
                         // slot 0: A_i, then take p itself out
@@ -894,7 +920,7 @@ struct Engine {
                     const unsigned long long* P0 = PLN + (size_t)PB[i] * B;
                     const unsigned long long* P1 = PLN + (size_t)PB[j] * B;
                     for (int blk = 0; blk < nb; blk++) {
-                        uint32_t r0 = (uint32_t)proc, r1 = (uint32_t)t, r2 = c2g | (uint32_t)blk, r3 = key;
+                        uint32_t r0 = gproc, r1 = (uint32_t)t, r2 = c2g | (uint32_t)blk, r3 = key;
                         philox(r0, r1, r2, r3, k0, k1);
                         const unsigned long long R0 = (unsigned long long)r1 << 32 | r0;
                         const unsigned long long R1 = (unsigned long long)r3 << 32 | r2;
@@ -935,8 +961,8 @@ struct Engine {
     // Greedy-Potential (kind 0) and shared-coin Greedy-Intersections (kind 1).
     __device__ int sel_rare(int kind, int t) {
         return rare_select<W>(kind, pn(), cand(), reinterpret_cast<uint32_t*>(hs()),
-                              reinterpret_cast<uint32_t*>(vbase()), ncols, m, lane, (uint32_t)proc, (uint32_t)t,
-                              c2(PU_GIS, 0), S->seed, cold()->a, cold()->b, &cold()->t_rare);
+                              reinterpret_cast<uint32_t*>(vbase()), ncols, m, lane, gproc, (uint32_t)t,
+                              c2(PU_GIS, 0), S->seed, cold()->a, cold()->b, &cold()->t_rare, &cold()->t_mrare);
     }
 
     __device__ int choose(int t) {
@@ -959,7 +985,8 @@ struct Engine {
             if constexpr (GS)
                 return sel_rare(0, t);
             else
-                return gp_select<W>(pn(), cand(), ncols, m, (uint32_t)cold()->a, lane, &cold()->t_rare);
+                return gp_select<W>(pn(), cand(), ncols, m, (uint32_t)cold()->a, lane, &cold()->t_rare,
+                                    &cold()->t_mrare);
         }
         if (lane == 0) cold()->t_scan += (unsigned)m;
         if (s == ST_GA) return sel_ga(d.z);
@@ -1034,6 +1061,7 @@ __device__ __forceinline__ void run_unit(const DevMat* __restrict__ mats, int n_
     E.M = M;
     E.S = S;
     E.proc = unit - M->unit_base;
+    E.gproc = (uint32_t)(E.proc + M->proc_offset);
     E.lane = lane;
     E.cap = M->cap;
     E.mmax = M->mmax;
@@ -1046,6 +1074,7 @@ __device__ __forceinline__ void run_unit(const DevMat* __restrict__ mats, int n_
         E.ended = 1;
         if (lane == 0) {
             cd->ops = 0;
+            cd->mops = 0;
             cd->strat = ST_G;
             cd->a = 0;
             cd->b = 0;
@@ -1064,6 +1093,7 @@ __device__ __forceinline__ void run_unit(const DevMat* __restrict__ mats, int n_
         E.ended = (int)st[H_ENDED];
         if (lane == 0) {
             cd->ops = (uint64_t)st[H_OPS_LO] | (uint64_t)st[H_OPS_HI] << 32;
+            cd->mops = (uint64_t)st[H_MOPS_LO] | (uint64_t)st[H_MOPS_HI] << 32;
             cd->strat = (int)st[H_STRAT];
             cd->a = (int)st[H_A];
             cd->b = (int)st[H_B];
@@ -1081,6 +1111,8 @@ __device__ __forceinline__ void run_unit(const DevMat* __restrict__ mats, int n_
         cd->t_sub = cd->t_pairs = cd->t_scan = 0;
         cd->t_gi_terms = cd->t_gi_blocks = cd->t_gi_cands = 0;
         cd->t_rare = 0;
+        cd->t_mrare = 0;
+        cd->t_nnz = 0;
     }
     if (t0 > 0 && !GM) {
         const uint2* spn = reinterpret_cast<const uint2*>(st + H_WORDS);
@@ -1118,9 +1150,16 @@ __device__ __forceinline__ void run_unit(const DevMat* __restrict__ mats, int n_
                                3LL * cd->t_gi_terms + 40LL * cd->t_gi_blocks + 8LL * cd->t_gi_cands +
                                (long long)cd->t_rare;
         const unsigned long long ops = cd->ops + (unsigned long long)dops;
+        // method ops of the round: 6 per 64-bit word and the nnz of the
+        // rewritten rows per rewrite, m per selection, 2 per gi intersect
+        // term; the gp trials and shared-coin gi
+        const long long dmops = 6LL * ((M->W + 1) >> 1) * cd->t_sub + (long long)cd->t_nnz + cd->t_scan +
+                                (long long)cd->t_gi_cands + 2LL * cd->t_gi_terms + (long long)cd->t_mrare;
+        const unsigned long long mops = cd->mops + (unsigned long long)dmops;
         uint32_t* st = M->state + (size_t)E.proc * M->state_words;
-        atomicMin(M->round_min, (unsigned long long)(uint32_t)cd->best_cost << 32 | (uint32_t)E.proc);
+        atomicMin(M->round_min, (unsigned long long)(uint32_t)cd->best_cost << 32 | E.gproc);
         atomicAdd(&M->counters[0], (unsigned long long)dops);
+        atomicAdd(&M->counters[3], (unsigned long long)dmops);
         atomicAdd(&M->counters[1], (unsigned long long)(cd->substeps - cd->sub_before));
         if (S->interval == 0) atomicAdd(&M->counters[2], (unsigned long long)(t - t0));
         if (cd->overflow) atomicExch(S->status, 1);
@@ -1141,6 +1180,8 @@ __device__ __forceinline__ void run_unit(const DevMat* __restrict__ mats, int n_
         st[H_OPS_LO] = (uint32_t)ops;
         st[H_OPS_HI] = (uint32_t)(ops >> 32);
         st[H_BEST_STRAT] = (uint32_t)cd->best_strat;
+        st[H_MOPS_LO] = (uint32_t)mops;
+        st[H_MOPS_HI] = (uint32_t)(mops >> 32);
     }
     if (!GM) {  // the next round, or a checkpoint, reads the state back
         uint2* spn = reinterpret_cast<uint2*>(st + H_WORDS);
@@ -1160,29 +1201,54 @@ __device__ __forceinline__ void run_unit(const DevMat* __restrict__ mats, int n_
 // process from the launch's work counter until none is left: a warp whose
 // process finished early starts another at once instead of idling until its
 // CTA's last warp is done.  The share kernel resets the counter for the next
-// round.
+// round.  With unit_list, the launch runs the units unit_list[0 ..
+// *unit_count) instead of 0 .. total_units (the processes the process-per-CTA
+// engine handed back this round).
 template <int W, bool GM, bool GS>
 __global__ void __launch_bounds__(128, CSE_MIN_BLOCKS) round_kernel(const DevMat* __restrict__ mats, int n_mats,
                                                        const DevSearch* __restrict__ searches,
                                                        int total_units, int* __restrict__ work,
-                                                       const __grid_constant__ WarpLayout L) {
+                                                       const __grid_constant__ WarpLayout L,
+                                                       const int* __restrict__ unit_list,
+                                                       const int* __restrict__ unit_count) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n_units = unit_list ? *unit_count : total_units;
     for (;;) {
         int unit = 0;
         if (lane == 0) unit = atomicAdd(work, 1);
         unit = __shfl_sync(FULL_MASK, unit, 0);
-        if (unit >= total_units) return;
+        if (unit >= n_units) return;
+        if (unit_list) unit = unit_list[unit];
         run_unit<W, GM, GS>(mats, n_mats, searches, L, smem, warp, lane, unit);
         __syncwarp();
     }
 }
 
 
+// Raises a kernel's maximum dynamic shared memory on the current device to
+// `bytes`, never lowering it: the attribute is global to the process, and a
+// launch on another thread (the server's worker, another search) may rely on
+// a larger value set earlier.
+inline cudaError_t raise_max_dynamic_smem(const void* fn, int bytes) {
+    static std::mutex mu;
+    static std::map<std::pair<const void*, int>, int> set_to;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = set_to.find({fn, dev});
+    if (it != set_to.end() && it->second >= bytes) return cudaSuccess;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) set_to[{fn, dev}] = bytes;
+    return e;
+}
+
 // Launchers of the round kernels of one engine variant (GS: shared coins).
 template <int W, bool GM, bool GS>
 static cudaError_t launch_round_w(const DevMat* mats, int n_mats, const DevSearch* searches, int total_units,
-                                  int* work, const WarpLayout& L, int ppc, cudaStream_t stream, bool prepare_only) {
+                                  int* work, const WarpLayout& L, int ppc, cudaStream_t stream, bool prepare_only,
+                                  const int* unit_list = nullptr, const int* unit_count = nullptr) {
     const size_t smem = GM ? 0 : (size_t)L.per_warp * ppc;
     if (prepare_only) {
         if (GM) {  // the HBM path uses no shared memory: give the SM's unified cache to L1
@@ -1190,8 +1256,7 @@ static cudaError_t launch_round_w(const DevMat* mats, int n_mats, const DevSearc
                                                  cudaFuncAttributePreferredSharedMemoryCarveout, 0);
             if (e != cudaSuccess) return e;
         }
-        return cudaFuncSetAttribute(round_kernel<W, GM, GS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)smem);
+        return raise_max_dynamic_smem((const void*)round_kernel<W, GM, GS>, (int)smem);
     }
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
@@ -1200,7 +1265,8 @@ static cudaError_t launch_round_w(const DevMat* mats, int n_mats, const DevSearc
     if (e != cudaSuccess) return e;
     const long long need = (total_units + ppc - 1) / ppc;
     const int grid = (int)std::max(1LL, std::min(need, (long long)std::max(sms, 1) * std::max(per_sm, 1)));
-    round_kernel<W, GM, GS><<<grid, 32 * ppc, smem, stream>>>(mats, n_mats, searches, total_units, work, L);
+    round_kernel<W, GM, GS><<<grid, 32 * ppc, smem, stream>>>(mats, n_mats, searches, total_units, work, L,
+                                                              unit_list, unit_count);
     return cudaGetLastError();
 }
 

@@ -18,6 +18,7 @@ struct cse_scheme {
     uint32_t* d_cand0[CSE_MAX_MATS];
     int32_t* d_meta0[CSE_MAX_MATS];
     void* d_block = nullptr;
+    uint64_t input_hash = 0;  // FNV-1a over every matrix's dimensions and entries (checkpoints record it)
 };
 
 namespace cse {
@@ -36,7 +37,8 @@ enum Purpose : uint32_t { PU_RUN = 0, PU_SHAREK = 1, PU_STEP = 2, PU_GI = 3, PU_
 // state region in global memory.
 enum Hdr : int {
     H_NCOLS = 0, H_NF, H_M, H_COST, H_STRAT, H_A, H_B, H_ENDED, H_RUNS, H_SUBSTEPS,
-    H_BEST_COST, H_BEST_LEN, H_TRAJ_LO, H_TRAJ_HI, H_OPS_LO, H_OPS_HI, H_BEST_STRAT, H_WORDS = 20
+    H_BEST_COST, H_BEST_LEN, H_TRAJ_LO, H_TRAJ_HI, H_OPS_LO, H_OPS_HI, H_BEST_STRAT, H_MOPS_LO, H_MOPS_HI,
+    H_WORDS = 20
 };
 
 constexpr int kMaxW = 8;          // 32-bit words per column (256 rows)
@@ -69,8 +71,12 @@ struct DevMat {
     int32_t* result;         // [cap] best list of the search
     int32_t* result_meta;    // [0] cost, [1] length
     unsigned long long* counters;   // [0] algorithmic ops, [1] substitution steps,
-                                    // [2] process-steps (iteration mode)
+                                    // [2] process-steps (iteration mode), [3] method ops
     int32_t* curve;          // [kCurvePoints]: lowest best Cost after each round (-1: not run)
+    int32_t proc_offset;     // global index of this matrix's first process (a shard of a search
+                             // split across ranks; 0 otherwise): draws and round keys use it
+    const int32_t* ext_list; // a shard: the round winner's best list when another rank owns it
+    const int32_t* ext_len;  //   (uploaded by the host before the share kernel), and its length
     WarpLayout gml;          // layout of the working arrays inside a state region
                              // (HBM path only; fixed for the life of the search)
 };
@@ -96,8 +102,31 @@ struct DevSearch {
     int32_t gi_shared;       // Greedy-Intersections with shared coins (CSE_FLAG_GI_SHARED_COINS)
 };
 
+// Process-per-CTA engine (large matrices): one CTA of kCtaThreads threads
+// runs one process at a time with the process's working arrays in the CTA's
+// shared memory.  A process whose candidate list or Greedy-Intersections
+// planes outgrow the capacities below leaves the round unfinished and is
+// redone, from its round-start state, by the one-warp-per-process HBM engine
+// (round_kernel<W, true, false>), so results never depend on the capacities.
+constexpr int kCtaWarps = 16;
+constexpr int kCtaThreads = 32 * kCtaWarps;
+constexpr int kCtaSeg = 12;                        // list entries per lane held in registers
+constexpr int kCtaListMax = 32 * kCtaSeg * kCtaWarps;  // 6144: the largest list capacity
+
+struct CtaLayout {
+    int32_t off_cold, off_sh, off_pn, off_cand, off_pl, off_aw, off_hs, off_he, off_vb, off_pb, off_lct, off_g;
+    int32_t off_lcw, off_f, off_pln;
+    int32_t ms;       // candidate capacity (entries)
+    int32_t pln_cap;  // Greedy-Intersections plane capacity (64-bit words)
+    int32_t bytes;    // dynamic shared memory per CTA
+};
+
 // planes: the HBM-path layout (weight bit-planes instead of weight bytes).
 WarpLayout make_layout(int W, int cap, int mmax, bool planes = false);
+// The process-per-CTA layout of a class of matrices; list_cap 0 = automatic
+// (the largest that lets two CTAs share an SM).  bytes = 0 if no useful
+// layout fits (the class then runs on the warp engine).
+CtaLayout make_cta_layout(int W, int cap, int mmax, int list_cap, int smem_per_block);
 int state_words(int W, int cap, int mmax);
 int state_words_gm(const WarpLayout& L);
 
@@ -117,6 +146,11 @@ cudaError_t launch_ingest(const int8_t* raw, int rows, int nx, int W, uint2* pn0
 cudaError_t launch_round(int W, bool gm, bool gs, const DevMat* mats, int n_mats, const DevSearch* searches,
                          int total_units, int* work, const WarpLayout& L, int procs_per_cta,
                          cudaStream_t stream);
+// The warp engine of the HBM path over a list of units: unit_list[0 ..
+// *unit_count) (device memory).
+cudaError_t launch_round_list(int W, const DevMat* mats, int n_mats, const DevSearch* searches, int max_units,
+                              const int* unit_list, const int* unit_count, int* work, int procs_per_cta,
+                              cudaStream_t stream);
 cudaError_t launch_round_gs(int W, bool gm, const DevMat* mats, int n_mats, const DevSearch* searches,
                             int total_units, int* work, const WarpLayout& L, int procs_per_cta, cudaStream_t stream,
                             bool prepare_only);
@@ -129,6 +163,14 @@ cudaError_t launch_brent(const int8_t* U, const int8_t* V, const int8_t* W, int 
 cudaError_t launch_philox(const uint32_t* ctr, long long n, uint64_t seed, uint32_t* out, cudaStream_t stream);
 // Sets the launch attributes of a round kernel (call outside stream capture).
 cudaError_t prepare_round(int W, bool gm, bool gs, const WarpLayout& L, int procs_per_cta);
+// The process-per-CTA engine of a class of large matrices, then the warp
+// engine over the processes it handed back.  work3: [0] the CTA engine's work
+// counter, [1] the redo launch's work counter, [2] the number of processes
+// handed back (all zero at launch; the share kernel resets them).  redo_list:
+// room for total_units entries.
+cudaError_t launch_round_cta(int W, const DevMat* mats, int n_mats, const DevSearch* searches, int total_units,
+                             int* work3, int* redo_list, const CtaLayout& CL, int redo_ppc, cudaStream_t stream);
+cudaError_t prepare_round_cta(int W, const CtaLayout& CL, int redo_ppc);
 int max_smem_per_block();
 
 // Records the calling thread's error message (cse_last_error) and returns code.

@@ -90,10 +90,11 @@ __global__ void share_kernel(const DevMat* __restrict__ mats, const DevSearch* _
         const DevMat* M = &mats[S->mat_pos[k]];
         const unsigned long long key = *M->round_min;
         if (key == ~0ull) continue;  // no process reported (cannot happen while the search runs)
-        const int cost = (int)(key >> 32), win = (int)(key & 0xFFFFFFFFu);
+        const int cost = (int)(key >> 32), win = (int)(key & 0xFFFFFFFFu) - M->proc_offset;
+        const bool local = win >= 0 && win < M->n_proc;  // else another rank's (a shard)
         if (boundary && cost < M->snap_meta[0]) {
-            const int len = (int)M->state[(size_t)win * M->state_words + H_BEST_LEN];
-            const int32_t* src = M->best_list + (size_t)win * M->cap;
+            const int len = local ? (int)M->state[(size_t)win * M->state_words + H_BEST_LEN] : *M->ext_len;
+            const int32_t* src = local ? M->best_list + (size_t)win * M->cap : M->ext_list;
             for (int x = lane; x < len; x += 32) M->snap[x] = src[x];
             __syncwarp();
             if (lane == 0) {
@@ -135,9 +136,10 @@ __global__ void share_kernel(const DevMat* __restrict__ mats, const DevSearch* _
         const unsigned long long key = *M->round_min;
         if (key == ~0ull) continue;
         if (s_final) {
-            const int cost = (int)(key >> 32), win = (int)(key & 0xFFFFFFFFu);
-            const int len = (int)M->state[(size_t)win * M->state_words + H_BEST_LEN];
-            const int32_t* src = M->best_list + (size_t)win * M->cap;
+            const int cost = (int)(key >> 32), win = (int)(key & 0xFFFFFFFFu) - M->proc_offset;
+            const bool local = win >= 0 && win < M->n_proc;
+            const int len = local ? (int)M->state[(size_t)win * M->state_words + H_BEST_LEN] : *M->ext_len;
+            const int32_t* src = local ? M->best_list + (size_t)win * M->cap : M->ext_list;
             for (int x = lane; x < len; x += 32) M->result[x] = src[x];
             if (lane == 0) {
                 M->result_meta[0] = cost;
@@ -237,6 +239,27 @@ cudaError_t launch_round(int W, bool gm, bool gs, const DevMat* mats, int n_mats
                          int total_units, int* work, const WarpLayout& L, int ppc, cudaStream_t stream) {
     return gs ? launch_round_gs(W, gm, mats, n_mats, searches, total_units, work, L, ppc, stream, false)
               : launch_round_variant<false>(W, gm, mats, n_mats, searches, total_units, work, L, ppc, stream, false);
+}
+
+cudaError_t launch_round_list(int W, const DevMat* mats, int n_mats, const DevSearch* searches, int max_units,
+                              const int* unit_list, const int* unit_count, int* work, int ppc, cudaStream_t stream) {
+    const WarpLayout none{};
+    switch (W) {
+#define CSE_LIST_CASE(w)                                                                                       \
+    case w:                                                                                                    \
+        return launch_round_w<w, true, false>(mats, n_mats, searches, max_units, work, none, ppc, stream, false, \
+                                              unit_list, unit_count);
+        CSE_LIST_CASE(1)
+        CSE_LIST_CASE(2)
+        CSE_LIST_CASE(3)
+        CSE_LIST_CASE(4)
+        CSE_LIST_CASE(5)
+        CSE_LIST_CASE(6)
+        CSE_LIST_CASE(7)
+        CSE_LIST_CASE(8)
+#undef CSE_LIST_CASE
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t prepare_round(int W, bool gm, bool gs, const WarpLayout& L, int ppc) {

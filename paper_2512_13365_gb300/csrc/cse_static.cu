@@ -73,9 +73,10 @@ extern "C" int cse_search_static(const cse_scheme* s, const cse_strategy_mix* mi
     else
         cse_opts_default(&opts);
     if (opts.share_interval < 1 || opts.share_permille > 1000 || opts.patience_rounds != 0 ||
-        (opts.flags & ~(uint32_t)(CSE_FLAG_GRAPH | CSE_FLAG_TRACE | CSE_FLAG_GI_SHARED_COINS)) != 0 || opts.col_cap > CSE_MAX_COLS || opts.procs_per_cta > 4)
+        (opts.flags & ~(uint32_t)(CSE_FLAG_TRACE | CSE_FLAG_GI_SHARED_COINS)) != 0 || opts.col_cap > CSE_MAX_COLS ||
+        opts.procs_per_cta > 4)
         return set_error(CSE_EINVAL, "invalid options (this entry point runs the step clock only: share_interval >= 1, "
-                                     "patience_rounds 0)");
+                                     "patience_rounds 0, and takes no CSE_FLAG_GRAPH)");
     const uint64_t wsum = (uint64_t)mix->w_gi + mix->w_ga + mix->w_gr + mix->w_wr + mix->w_mix + mix->w_g + mix->w_gp;
     if (wsum == 0 || wsum > 0xFFFFFFFFull) return set_error(CSE_EINVAL, "strategy weights: sum must be in [1, 2^32)");
     if (n_proc < 1 || n_proc > (1 << 20)) return set_error(CSE_EINVAL, "n_processes must be in [1, 2^20]");

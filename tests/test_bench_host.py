@@ -91,22 +91,25 @@ def test_clock_record_keeps_timed_region_samples(tmp_path):
     assert got["scope"] == "timed region" and got["sm_max_mhz"] == 2070.0
 
 
-def test_measured_traffic_only_for_the_captured_workload():
-    """The DRAM traffic of the ncu capture is reported only on the line of
-    the workload and launch size it was taken on, for the current source."""
+def test_measured_traffic_only_for_the_captured_workload(tmp_path):
+    """The DRAM traffic of an ncu capture is reported only on the line of the
+    workload it was taken on, for the current kernel source, scaled from the
+    captured launch to the bench's process count."""
     sys.path.insert(0, ROOT)
     import bench
     from paper_2512_13365_gb300 import synth
-    rec = json.load(open(os.path.join(ROOT, "profiles", "round_kernel_traffic.json")))
-    s = synth.config2()
-    got = bench.measured_traffic(s)
-    if rec["kernel_source_sha256_prefix"] == bench.kernel_source_sha():
-        assert got == rec["dram_bytes_per_launch"] > 0
-    else:
-        assert got is None
-    s.n_proc = 1024
-    assert bench.measured_traffic(s) is None
-    assert bench.measured_traffic(synth.config4(n_proc=4096, budget=64)) is None
+    s4 = synth.config4(n_proc=4096, budget=64)
+    rec = [{"kernel_source_sha256_prefix": bench.kernel_source_sha(), "workload_name": s4.name,
+            "n_processes": 4096, "share_interval": 32, "dram_bytes_per_launch": 1000}]
+    path = tmp_path / "traffic.json"
+    path.write_text(json.dumps(rec))
+    assert bench.measured_traffic(s4, str(path)) == 1000
+    s4.n_proc = 65536
+    assert bench.measured_traffic(s4, str(path)) == 16000
+    assert bench.measured_traffic(synth.config2(), str(path)) is None
+    rec[0]["kernel_source_sha256_prefix"] = "0" * 16
+    path.write_text(json.dumps(rec))
+    assert bench.measured_traffic(s4, str(path)) is None
 
 
 def test_reference_arm_under_torchrun_prints_once():

@@ -12,7 +12,8 @@ from paper_2512_13365_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 
-FIELDS = ("best_cost", "best_len", "runs", "best_hash", "traj_hash", "ops", "substeps", "best_strategy")
+FIELDS = ("best_cost", "best_len", "runs", "best_hash", "traj_hash", "ops", "substeps", "best_strategy",
+          "method_ops")
 
 
 @pytest.fixture(scope="module")
@@ -41,8 +42,72 @@ def assert_parity(cse, s, ref=None, procs_per_cta=0, check_procs=True, gi_shared
         assert [r.curve(k) for k in range(len(s.mats))] == ref.curve
     assert sub == int(sum(ref.digests[k]["substeps"].sum() for k in range(len(s.mats))))
     assert ops == int(sum(ref.digests[k]["ops"].sum() for k in range(len(s.mats))))
+    assert r.method_ops() == int(sum(ref.digests[k]["method_ops"].sum() for k in range(len(s.mats))))
     r.free()
     return ref
+
+
+def load_cfg4_golden():
+    """The oracle's results for the (6,6,6:153)-shaped workload at 512
+    processes x 200 steps (tests/golden/cfg4_reduced.txt, written by
+    tests/golden/make_cfg4_golden.py from the oracle alone)."""
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "cfg4_reduced.txt")
+    g = {"lists": {}, "curves": {}, "procs": {}}
+    for ln in open(path):
+        f = ln.split()
+        if not f or f[0].startswith("#"):
+            continue
+        if f[0] == "inputs_sha256":
+            g["sha"] = f[1]
+        elif f[0] == "params":
+            g["params"] = [int(x) for x in f[1:]]
+        elif f[0] == "costs":
+            g["costs"] = [int(x) for x in f[1:]]
+        elif f[0] == "list":
+            g["lists"][int(f[1])] = [int(x) for x in f[2:]]
+        elif f[0] == "curve":
+            g["curves"][int(f[1])] = [int(x) for x in f[2:]]
+        elif f[0] == "p":
+            vals = [int(x, 16) if name.endswith("hash") else int(x) for name, x in zip(FIELDS_CFG4, f[3:])]
+            g["procs"].setdefault(int(f[1]), []).append(vals)
+    return g
+
+
+FIELDS_CFG4 = ("best_cost", "best_len", "runs", "best_hash", "traj_hash", "ops", "substeps", "best_strategy",
+               "method_ops")
+
+
+@pytest.mark.parametrize("engine", ["cta", "warp", "cta_small_lists"])
+def test_config4_reduced_scale_full_parity(cse, engine):
+    """The (6,6,6:153)-shaped workload at 512 processes x 200 steps, sharing
+    every 32 steps (six sharing boundaries), cap 512: every process's record,
+    the lists, Costs and best-Cost curves equal the oracle's.  Both large-matrix
+    engines run it: one process per CTA (with its list capacity forced down to
+    2048, so that processes outgrow it and finish their rounds on the warp
+    engine) and one warp per process."""
+    g = load_cfg4_golden()
+    n_proc, budget, interval, permille, cap, seed = g["params"]
+    s = synth.config4(n_proc=n_proc, budget=budget)
+    assert (s.interval, s.permille, s.cap, s.seed) == (interval, permille, cap, seed)
+    kw = {"warp": {"warp_engine": True}, "cta": {}, "cta_small_lists": {"cta_list_cap": 2048}}[engine]
+    r = cse.search_obj(s, trace=True, **kw)
+    assert r.costs == g["costs"]
+    assert r.lists == [g["lists"][k] for k in range(3)]
+    assert [r.curve(k) for k in range(3)] == [g["curves"][k] for k in range(3)]
+    for k in range(3):
+        got = r.procs(k)
+        exp = np.array(g["procs"][k], dtype=object)
+        for fi, f in enumerate(FIELDS_CFG4):
+            want = np.array([int(x) for x in exp[:, fi]], dtype=got[f].dtype)
+            bad = np.nonzero(got[f] != want)[0]
+            assert bad.size == 0, f"{engine}: matrix {k} field {f}: {bad.size} processes differ, first {bad[:5]}"
+    steps, sub, ops = r.counters()
+    assert steps == 3 * n_proc * budget
+    assert sub == sum(int(v[6]) for k in range(3) for v in g["procs"][k])
+    assert ops == sum(int(v[5]) for k in range(3) for v in g["procs"][k])
+    assert r.method_ops() == sum(int(v[8]) for k in range(3) for v in g["procs"][k])
+    r.free()
 
 
 def test_config1_full(cse):
@@ -346,7 +411,7 @@ def test_trace_flag_only_changes_the_trajectory_record(cse):
     for k in range(3):
         a, b = plain.procs(k), traced.procs(k)
         assert (a["traj_hash"] == 0xCBF29CE484222325).all()
-        for f in ("best_cost", "best_len", "runs", "best_hash", "ops", "substeps"):
+        for f in ("best_cost", "best_len", "runs", "best_hash", "ops", "substeps", "method_ops"):
             assert np.array_equal(a[f], b[f])
 
 

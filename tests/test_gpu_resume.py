@@ -9,7 +9,8 @@ from paper_2512_13365_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 
-FIELDS = ("best_cost", "best_len", "runs", "best_hash", "traj_hash", "ops", "substeps", "best_strategy")
+FIELDS = ("best_cost", "best_len", "runs", "best_hash", "traj_hash", "ops", "substeps", "best_strategy",
+          "method_ops")
 
 
 @pytest.fixture(scope="module")
@@ -81,3 +82,19 @@ def test_checkpoint_needs_a_sharing_boundary(cse):
     with pytest.raises(cse.CseError):
         r.checkpoint()
     r.free()
+
+
+def test_resume_refuses_a_scheme_with_other_entries(cse):
+    """A checkpoint records a hash of the matrices it was taken on: resuming it
+    on a scheme of the same shapes but other entries is refused."""
+    s = synth.config2(n_proc=32, budget=32)
+    sc = cse.Scheme(s.mats)
+    first = cse.search(sc, s.weights, s.n_proc, s.seed, 32, s.interval, s.permille, s.cap)
+    ck = first.checkpoint()
+    first.free()
+    other = [m.copy() for m in s.mats]
+    other[1] = -other[1]  # same shapes and nonzeros, other signs
+    with pytest.raises(cse.CseError) as e:
+        cse.resume(cse.Scheme(other), ck, 32)
+    assert e.value.code == cse.CSE_EINVAL
+    cse.resume(sc, ck, 32).free()  # the scheme it was taken on still resumes

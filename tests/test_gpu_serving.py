@@ -47,6 +47,7 @@ def test_served_results_equal_alone(cse):
     served = [sv.wait(t, timeout_us=120_000_000) for t in tickets]
     st = sv.stats()
     assert st["completed"] == len(reqs) and st["p99_ms"] >= st["p50_ms"] > 0 and st["steps_per_s"] > 0
+    assert sv.peak()[0] > 1  # requests were on the device together
     for s, sc, r in zip(reqs, schemes, served):
         alone = cse.search(sc, s.weights, s.n_proc, s.seed, s.budget, 16, s.permille, 512, trace=True)
         _same(cse, r, alone, len(s.mats))
@@ -149,4 +150,24 @@ def test_cancel_queued_and_running_requests(cse):
     _same(cse, r, alone, 3)
     with pytest.raises(cse.CseError):
         sv.cancel(t_after)                               # already finished (and collected)
+    sv.free()
+
+
+def test_search_on_another_thread_beside_the_server(cse):
+    """A kernel's shared-memory limit is process-wide: a small search run on
+    the caller's thread while the server serves a larger shape of the same
+    word width must not lower the limit under the server's launches."""
+    big = synth.config2(n_proc=512, budget=256)
+    big.interval, big.cap = 16, 512          # W = 1 with a large per-process slice
+    small = synth.config1(n_proc=16, budget=16)  # W = 1 with a small one
+    sv = cse.Server(interval=16, cap=512)
+    sb, ss = cse.Scheme(big.mats), cse.Scheme(small.mats)
+    t = sv.submit(sb, big.weights, big.n_proc, big.seed, big.budget)
+    for _ in range(20):
+        r = cse.search(ss, small.weights, small.n_proc, small.seed, small.budget, 16, small.permille, small.cap)
+        r.costs
+        r.free()
+    served = sv.wait(t, timeout_us=300_000_000)
+    alone = cse.search(sb, big.weights, big.n_proc, big.seed, big.budget, 16, big.permille, 512)
+    assert served.costs == alone.costs and served.lists == alone.lists
     sv.free()

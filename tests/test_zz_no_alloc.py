@@ -81,3 +81,18 @@ def test_static_scratch_refuses_searches_that_do_not_fit(env):
                                      ctypes.c_void_p(lists.data_ptr()), ctypes.c_void_p(meta.data_ptr()))
     assert rc == cse.CSE_ENOMEM
     assert b"static scratch holds" in cse.lib().cse_last_error()
+
+
+def test_static_scratch_refuses_the_graph_flag(env):
+    """The no-allocation entry point runs its own launch sequence and takes no
+    CSE_FLAG_GRAPH: the flag is refused instead of being ignored."""
+    cse, torch = env
+    s = synth.config1(n_proc=8, budget=8)
+    sc = cse.Scheme(s.mats)
+    lists = torch.zeros((2, s.cap), dtype=torch.int32, device="cuda")
+    meta = torch.zeros((2, 2), dtype=torch.int32, device="cuda")
+    rc = cse.lib().cse_search_static(sc.handle, ctypes.byref(cse.make_mix(s.weights)), s.n_proc, s.seed,
+                                     s.budget, ctypes.byref(cse.make_opts(s.interval, s.permille, s.cap, graph=True)),
+                                     None, ctypes.c_void_p(lists.data_ptr()), ctypes.c_void_p(meta.data_ptr()))
+    assert rc == cse.CSE_EINVAL
+    assert b"CSE_FLAG_GRAPH" in cse.lib().cse_last_error()
