@@ -478,11 +478,13 @@ int cse_shard_share(cse_result* shard, const uint64_t* keys, const int32_t* list
  *   kind 1  AND + popcount + add                   3 lane-ops per step
  *   kind 2  32-bit multiply-add (IMAD)             1 lane-op per step
  *   kind 3  32-bit multiply-high (IMAD.HI)         1 lane-op per step
+ *   kind 4  3-input XOR (LOP3) alone               1 lane-op per step
+ *   kind 5  two dependent adds (IADD3) alone       2 lane-ops per step
  * Writes *ops_per_clk_per_sm (lane-ops per SM clock, from clock64() spans of
  * every block: independent of the clock frequency), *lane_ops_per_s (from
  * CUDA events) and *seconds (the launch's event time).  Allocates and frees a
- * small device buffer and synchronises the stream; CSE_EINVAL for a bad kind
- * or iters outside [1, 2^40], CSE_ECUDA without a device. */
+ * small device buffer and synchronises the stream; CSE_EINVAL for a kind outside
+ * 0..5 or iters outside [1, 2^40], CSE_ECUDA without a device. */
 int cse_int_peak(int32_t kind, int64_t iters, void* cuda_stream, double* ops_per_clk_per_sm,
                  double* lane_ops_per_s, double* seconds);
 

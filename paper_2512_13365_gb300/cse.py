@@ -319,7 +319,7 @@ def philox(seed: int, counters: np.ndarray) -> np.ndarray:
     return out
 
 
-INT_PEAK_KINDS = ("lop3+iadd3", "and+popc+iadd", "imad", "imad.hi")
+INT_PEAK_KINDS = ("lop3+iadd3", "and+popc+iadd", "imad", "imad.hi", "lop3", "iadd3")
 
 
 def int_peak(kind: int, iters: int = 100000, stream=None) -> dict:

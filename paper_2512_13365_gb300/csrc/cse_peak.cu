@@ -14,6 +14,8 @@
 //           of which one POPC
 //   kind 2  IMAD (32-bit multiply-add, the Philox round's low product)
 //   kind 3  IMAD.HI (32-bit multiply-high, the Philox round's high product)
+//   kind 4  LOP3 alone (3-input XOR)
+//   kind 5  IADD3 alone (3-input add)
 
 #include <cuda_runtime.h>
 
@@ -55,8 +57,14 @@ __global__ void __launch_bounds__(kPeakThreads) int_peak_kernel(uint32_t seed, l
                 asm volatile("add.u32 %0, %0, %1;" : "+r"(x[c]) : "r"(p));
             } else if (KIND == 2) {
                 asm volatile("mad.lo.u32 %0, %0, %1, %2;" : "+r"(x[c]) : "r"(k1), "r"(y[c]));
-            } else {
+            } else if (KIND == 3) {
                 asm volatile("mul.hi.u32 %0, %0, %1;" : "+r"(x[c]) : "r"(k2));
+            } else if (KIND == 4) {
+                asm volatile("lop3.b32 %0, %0, %1, %2, 0x96;" : "+r"(x[c]) : "r"(y[c]), "r"(k1));
+            } else {
+                uint32_t t;
+                asm volatile("add.u32 %0, %1, %2;" : "=r"(t) : "r"(x[c]), "r"(k1));
+                asm volatile("add.u32 %0, %1, %2;" : "=r"(x[c]) : "r"(t), "r"(y[c]));
             }
         }
     }
@@ -70,7 +78,7 @@ __global__ void __launch_bounds__(kPeakThreads) int_peak_kernel(uint32_t seed, l
 }
 
 // Lane-ops per chain step of each kind.
-static const int kOpsPerStep[4] = {2, 3, 1, 1};
+static const int kOpsPerStep[6] = {2, 3, 1, 1, 1, 2};
 
 }  // namespace cse
 
@@ -78,7 +86,7 @@ using namespace cse;
 
 extern "C" int cse_int_peak(int32_t kind, int64_t iters, void* cuda_stream, double* ops_per_clk_per_sm,
                             double* lane_ops_per_s, double* seconds) {
-    if (kind < 0 || kind > 3) return set_error(CSE_EINVAL, "kind must be 0..3");
+    if (kind < 0 || kind > 5) return set_error(CSE_EINVAL, "kind must be 0..5");
     if (iters < 1 || iters > (int64_t)1 << 40) return set_error(CSE_EINVAL, "iters must be in [1, 2^40]");
     int dev = 0, sms = 0, per_sm = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -87,7 +95,9 @@ extern "C" int cse_int_peak(int32_t kind, int64_t iters, void* cuda_stream, doub
     const void* fn = kind == 0   ? (const void*)int_peak_kernel<0>
                      : kind == 1 ? (const void*)int_peak_kernel<1>
                      : kind == 2 ? (const void*)int_peak_kernel<2>
-                                 : (const void*)int_peak_kernel<3>;
+                     : kind == 3 ? (const void*)int_peak_kernel<3>
+                     : kind == 4 ? (const void*)int_peak_kernel<4>
+                                 : (const void*)int_peak_kernel<5>;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kPeakThreads, 0);
     if (e != cudaSuccess || per_sm <= 0) return set_error(CSE_ECUDA, "occupancy query failed");
     per_sm = per_sm > 8 ? 8 : per_sm;  // 32 warps per SM: enough to fill every scheduler
@@ -107,7 +117,9 @@ extern "C" int cse_int_peak(int32_t kind, int64_t iters, void* cuda_stream, doub
         case 0: int_peak_kernel<0><<<grid, kPeakThreads, 0, st>>>(0x2545F491u, iters, sink, span); break;
         case 1: int_peak_kernel<1><<<grid, kPeakThreads, 0, st>>>(0x2545F491u, iters, sink, span); break;
         case 2: int_peak_kernel<2><<<grid, kPeakThreads, 0, st>>>(0x2545F491u, iters, sink, span); break;
-        default: int_peak_kernel<3><<<grid, kPeakThreads, 0, st>>>(0x2545F491u, iters, sink, span); break;
+        case 3: int_peak_kernel<3><<<grid, kPeakThreads, 0, st>>>(0x2545F491u, iters, sink, span); break;
+        case 4: int_peak_kernel<4><<<grid, kPeakThreads, 0, st>>>(0x2545F491u, iters, sink, span); break;
+        default: int_peak_kernel<5><<<grid, kPeakThreads, 0, st>>>(0x2545F491u, iters, sink, span); break;
     }
     e = cudaGetLastError();
     cudaEventRecord(b, st);
