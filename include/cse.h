@@ -128,7 +128,13 @@ typedef struct {
                                  outgrows it finishes that round on the
                                  one-warp-per-process engine.  Never changes
                                  results.                                     */
-    uint32_t reserved;        /* must be 0                                   */
+    uint32_t cta_min_list;    /* launch parameter of large matrices: a process
+                                 whose run is under way with fewer candidates
+                                 than this at a round start runs that round
+                                 on the one-warp-per-process engine (one warp
+                                 serves a short list better than a CTA);
+                                 0 = automatic (1024).  Never changes
+                                 results.                                     */
 } cse_opts;
 
 /* Default options: share_interval 32, share_permille 400, col_cap 128. */
@@ -308,6 +314,12 @@ int cse_result_counters(const cse_result* r, int64_t* process_steps, int64_t* su
  * (Section 3.5.2) count as rewrites. */
 int cse_result_method_ops(const cse_result* r, int64_t* method_ops);
 
+/* Waits for the search and reports how its large-matrix process-rounds ran:
+ * *cta_rounds on the process-per-CTA engine, *warp_rounds on the
+ * one-warp-per-process HBM engine (process-rounds handed back by the CTA
+ * engine included).  Both 0 for searches without large matrices. */
+int cse_result_engine_rounds(const cse_result* r, int64_t* cta_rounds, int64_t* warp_rounds);
+
 /* Device time of the search's kernels in milliseconds, from CUDA events
  * recorded around the round kernels on the search's stream: *round_ms sums
  * the step-engine launches, *total_ms spans the whole search. */
@@ -479,7 +491,7 @@ int cse_shard_share(cse_result* shard, const uint64_t* keys, const int32_t* list
  *   kind 2  32-bit multiply-add (IMAD)             1 lane-op per step
  *   kind 3  32-bit multiply-high (IMAD.HI)         1 lane-op per step
  *   kind 4  3-input XOR (LOP3) alone               1 lane-op per step
- *   kind 5  two dependent adds (IADD3) alone       2 lane-ops per step
+ *   kind 5  3-input add (IADD3) alone              1 lane-op per step
  * Writes *ops_per_clk_per_sm (lane-ops per SM clock, from clock64() spans of
  * every block: independent of the clock frequency), *lane_ops_per_s (from
  * CUDA events) and *seconds (the launch's event time).  Allocates and frees a

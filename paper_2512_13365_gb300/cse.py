@@ -33,7 +33,7 @@ class Opts(ctypes.Structure):
     _fields_ = [("share_interval", ctypes.c_uint32), ("share_permille", ctypes.c_uint32),
                 ("col_cap", ctypes.c_uint32), ("patience_rounds", ctypes.c_uint32),
                 ("max_spin", ctypes.c_uint64), ("procs_per_cta", ctypes.c_uint32), ("flags", ctypes.c_uint32),
-                ("cta_list_cap", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("cta_list_cap", ctypes.c_uint32), ("cta_min_list", ctypes.c_uint32)]
 
 
 class ProcRecord(ctypes.Structure):
@@ -59,7 +59,7 @@ _lib = None
 
 # every symbol include/cse.h declares
 EXPORTS = ["cse_opts_default", "cse_scheme_load", "cse_scheme_load_uvw", "cse_scheme_shape", "cse_search",
-           "cse_search_batch", "cse_autotune", "cse_tune_interval", "cse_result_fetch", "cse_result_procs", "cse_result_counters", "cse_result_method_ops", "cse_result_timing",
+           "cse_search_batch", "cse_autotune", "cse_tune_interval", "cse_result_fetch", "cse_result_procs", "cse_result_counters", "cse_result_method_ops", "cse_result_engine_rounds", "cse_result_timing",
            "cse_result_iterations", "cse_result_curve", "cse_result_hybrid", "cse_brent_check", "cse_philox", "cse_checkpoint_size",
            "cse_checkpoint_save", "cse_search_resume", "cse_result_launches",
            "cse_result_free", "cse_scheme_free", "cse_last_error",
@@ -113,6 +113,7 @@ def lib() -> ctypes.CDLL:
     L.cse_result_procs.argtypes = [vp, i32, ctypes.POINTER(ProcRecord)]
     L.cse_result_counters.argtypes = [vp, pi64, pi64, pi64]
     L.cse_result_method_ops.argtypes = [vp, pi64]
+    L.cse_result_engine_rounds.argtypes = [vp, pi64, pi64]
     L.cse_result_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float), pi32]
     L.cse_result_free.argtypes = [vp]
     L.cse_result_free.restype = None
@@ -242,6 +243,13 @@ class Result:
         _check(lib().cse_result_method_ops(self.handle, ctypes.byref(a)))
         return a.value
 
+    def engine_rounds(self) -> Tuple[int, int]:
+        """cse_result_engine_rounds: large-matrix process-rounds on the
+        process-per-CTA engine and on the HBM warp engine."""
+        a, b = ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().cse_result_engine_rounds(self.handle, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
     def timing(self) -> Tuple[float, float, int]:
         a, b, n = ctypes.c_float(), ctypes.c_float(), ctypes.c_int32()
         _check(lib().cse_result_timing(self.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(n)))
@@ -338,7 +346,7 @@ def make_mix(weights) -> Mix:
 
 def make_opts(interval: int = 32, permille: int = 400, cap: int = 128, procs_per_cta: int = 0,
               graph: bool = False, trace: bool = False, patience: int = 0, gi_shared: bool = False,
-              warp_engine: bool = False, cta_list_cap: int = 0) -> Opts:
+              warp_engine: bool = False, cta_list_cap: int = 0, cta_min_list: int = 0) -> Opts:
     """interval 0 selects iteration mode (budget = maximum iterations, stop
     after `patience` iterations without improvement).  warp_engine and
     cta_list_cap choose how large matrices are launched; never results."""
@@ -349,6 +357,7 @@ def make_opts(interval: int = 32, permille: int = 400, cap: int = 128, procs_per
     o.flags = ((FLAG_GRAPH if graph else 0) | (FLAG_TRACE if trace else 0) |
                (FLAG_GI_SHARED_COINS if gi_shared else 0) | (FLAG_WARP_ENGINE if warp_engine else 0))
     o.cta_list_cap = cta_list_cap
+    o.cta_min_list = cta_min_list
     return o
 
 
@@ -385,11 +394,11 @@ class Options:
 def search(scheme: Scheme, weights, n_proc: int, seed: int, budget: int, interval: int = 32,
            permille: int = 400, cap: int = 128, stream=None, procs_per_cta: int = 0, graph: bool = False,
            trace: bool = False, patience: int = 0, gi_shared: bool = False, warp_engine: bool = False,
-           cta_list_cap: int = 0) -> Result:
+           cta_list_cap: int = 0, cta_min_list: int = 0) -> Result:
     """cse_search: enqueue the search and return its Result handle."""
     mix = make_mix(weights)
     opts = make_opts(interval, permille, cap, procs_per_cta, graph, trace, patience, gi_shared, warp_engine,
-                     cta_list_cap)
+                     cta_list_cap, cta_min_list)
     h = ctypes.c_void_p()
     _check(lib().cse_search(scheme.handle, ctypes.byref(mix), n_proc, seed, budget, ctypes.byref(opts),
                             _stream_ptr(stream), ctypes.byref(h)))

@@ -250,8 +250,7 @@ static int check_opts(const cse_opts* opts_in, cse_opts* opts) {
         cse_opts_default(opts);
     if (opts->share_permille > 1000) return fail(CSE_EINVAL, "share_permille must be <= 1000");
     if ((opts->flags & ~(uint32_t)(CSE_FLAG_GRAPH | CSE_FLAG_TRACE | CSE_FLAG_GI_SHARED_COINS |
-                                   CSE_FLAG_WARP_ENGINE)) != 0 ||
-        opts->reserved != 0)
+                                   CSE_FLAG_WARP_ENGINE)) != 0)
         return fail(CSE_EINVAL, "reserved option fields must be 0");
     if (opts->share_interval != 0 && opts->patience_rounds != 0)
         return fail(CSE_EINVAL, "patience_rounds applies to iteration mode (share_interval = 0) only");
@@ -302,7 +301,7 @@ static int search_plan(const cse_scheme* s, const cse_strategy_mix* mix, int n_p
         offs->push_back(cv.take(8));                                    // round minimum
         offs->push_back(cv.take((size_t)cap * 4));                      // result
         offs->push_back(cv.take(8));                                    // result meta
-        offs->push_back(cv.take(32));                                   // counters
+        offs->push_back(cv.take(64));                                   // counters
         offs->push_back(cv.take((size_t)kCurvePoints * 4));             // best-Cost curve
         offs->push_back(cv.take((size_t)(cap + 1) * 4));                // a shard's external winner list
     }
@@ -391,7 +390,7 @@ static int search_create(const cse_scheme* s, const cse_strategy_mix* mix, int n
         if (e == cudaSuccess) e = cudaMemcpyAsync(M.snap_meta, snap_init, 8, cudaMemcpyHostToDevice, stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(M.result_meta, M.meta0, 4, cudaMemcpyDeviceToDevice, stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(M.result_meta + 1, 0, 4, stream);
-        if (e == cudaSuccess) e = cudaMemsetAsync(M.counters, 0, 32, stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(M.counters, 0, 64, stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(M.curve, 0xFF, (size_t)kCurvePoints * 4, stream);
     }
     static const int32_t conv_init[4] = {0, 0, INT_MAX, 0};
@@ -456,7 +455,8 @@ static int build_launch(const std::vector<SearchDev*>& act, int ppc_req, const T
             while (g.ppc > 1 && (long long)g.L.per_warp * g.ppc > smem_max) g.ppc--;
         if (!g.gm && g.L.per_warp > smem_max) return fail(CSE_ENOMEM, "process slice exceeds shared memory");
         if (g.gm && !ls->gs && !(act[0]->opts.flags & CSE_FLAG_WARP_ENGINE)) {
-            g.CL = make_cta_layout(g.W, g.cap, g.mmax, (int)act[0]->opts.cta_list_cap, smem_max);
+            g.CL = make_cta_layout(g.W, g.cap, g.mmax, (int)act[0]->opts.cta_list_cap,
+                                   (int)act[0]->opts.cta_min_list, smem_max);
             g.cta = g.CL.bytes > 0;
         }
         cudaError_t e = g.cta ? prepare_round_cta(g.W, g.CL, g.ppc) : prepare_round(g.W, g.gm, ls->gs, g.L, g.ppc);
@@ -1255,6 +1255,22 @@ int cse_result_counters(const cse_result* r, int64_t* process_steps, int64_t* su
         *process_steps = sd->search.interval == 0 ? (int64_t)steps : (int64_t)sd->n_mats * sd->n_proc * sd->budget;
     if (substeps) *substeps = (int64_t)sub;
     if (alg_ops) *alg_ops = (int64_t)ops;
+    return CSE_OK;
+}
+
+int cse_result_engine_rounds(const cse_result* r, int64_t* cta_rounds, int64_t* warp_rounds) {
+    int rc = wait_result(r);
+    if (rc) return rc;
+    const SearchDev* sd = r->sd;
+    uint64_t a = 0, b = 0;
+    for (int k = 0; k < sd->n_mats; k++) {
+        unsigned long long c[6];
+        CUDA_TRY(cudaMemcpy(c, sd->mats[k].counters, 48, cudaMemcpyDeviceToHost));
+        a += c[4];
+        b += c[5];
+    }
+    if (cta_rounds) *cta_rounds = (int64_t)a;
+    if (warp_rounds) *warp_rounds = (int64_t)b;
     return CSE_OK;
 }
 

@@ -288,9 +288,11 @@ struct CtaEngine {
             ws[4 * warp] = wtot;
             ws[4 * warp + 1] = wlive;
             ws[4 * warp + 2] = wboth;
+            ws[4 * warp + 3] = nij;  // this warp's recounted candidates
         }
         __syncthreads();  // also orders the compaction's writes before the appends
         int off = 0, added = 0, nu = 0, rb = 0;
+        nij = 0;
 #pragma unroll
         for (int w = 0; w < NW; w++) {
             const int x = ws[4 * w];
@@ -298,6 +300,7 @@ struct CtaEngine {
             added += x;
             nu += ws[4 * w + 1];
             rb += ws[4 * w + 2];
+            nij += ws[4 * w + 3];
         }
         if (newm + added > ms) {  // the list would outgrow its shared-memory capacity
             abandon = 1;
@@ -866,7 +869,10 @@ __device__ bool cta_run_unit(const DevMat* __restrict__ mats, int n_mats, const 
         cd->t_nnz = 0;
         cd->sub_before = cd->substeps;
     }
-    if (E.m > E.ms) return false;
+    // a list too long for shared memory, or (at a round start that is not a
+    // run start) one short enough that one warp serves it better: the warp
+    // engine takes the round
+    if (E.m > E.ms || (t0 > 0 && !E.ended && E.m < L.min_m)) return false;
     if (t0 > 0) {  // the process's arrays, from the HBM engine's layout of its state region
         const uint2* spn = reinterpret_cast<const uint2*>(gst + M->gml.off_pn);
         uint2* P = E.pn();
@@ -903,6 +909,7 @@ __device__ bool cta_run_unit(const DevMat* __restrict__ mats, int n_mats, const 
         atomicAdd(&M->counters[0], (unsigned long long)dops);
         atomicAdd(&M->counters[1], (unsigned long long)(cd->substeps - cd->sub_before));
         atomicAdd(&M->counters[3], (unsigned long long)dmops);
+        atomicAdd(&M->counters[4], 1ull);  // process-rounds run on this engine
         if (iter) atomicAdd(&M->counters[2], (unsigned long long)(t - t0));
         st[H_NCOLS] = (uint32_t)E.ncols;
         st[H_NF] = (uint32_t)E.nf;

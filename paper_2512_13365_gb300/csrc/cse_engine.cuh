@@ -1160,6 +1160,7 @@ __device__ __forceinline__ void run_unit(const DevMat* __restrict__ mats, int n_
         atomicMin(M->round_min, (unsigned long long)(uint32_t)cd->best_cost << 32 | E.gproc);
         atomicAdd(&M->counters[0], (unsigned long long)dops);
         atomicAdd(&M->counters[3], (unsigned long long)dmops);
+        if (GM) atomicAdd(&M->counters[5], 1ull);  // process-rounds run on the HBM warp engine
         atomicAdd(&M->counters[1], (unsigned long long)(cd->substeps - cd->sub_before));
         if (S->interval == 0) atomicAdd(&M->counters[2], (unsigned long long)(t - t0));
         if (cd->overflow) atomicExch(S->status, 1);

@@ -71,7 +71,9 @@ struct DevMat {
     int32_t* result;         // [cap] best list of the search
     int32_t* result_meta;    // [0] cost, [1] length
     unsigned long long* counters;   // [0] algorithmic ops, [1] substitution steps,
-                                    // [2] process-steps (iteration mode), [3] method ops
+                                    // [2] process-steps (iteration mode), [3] method ops,
+                                    // [4] process-rounds on the process-per-CTA engine,
+                                    // [5] process-rounds on the HBM warp engine
     int32_t* curve;          // [kCurvePoints]: lowest best Cost after each round (-1: not run)
     int32_t proc_offset;     // global index of this matrix's first process (a shard of a search
                              // split across ranks; 0 otherwise): draws and round keys use it
@@ -112,12 +114,14 @@ constexpr int kCtaWarps = 16;
 constexpr int kCtaThreads = 32 * kCtaWarps;
 constexpr int kCtaSeg = 12;                        // list entries per lane held in registers
 constexpr int kCtaListMax = 32 * kCtaSeg * kCtaWarps;  // 6144: the largest list capacity
+constexpr int kCtaMinList = 1024;  // default: shorter lists of a run under way go to the warp engine
 
 struct CtaLayout {
     int32_t off_cold, off_sh, off_pn, off_cand, off_pl, off_aw, off_hs, off_he, off_vb, off_pb, off_lct, off_g;
     int32_t off_lcw, off_f, off_pln;
     int32_t ms;       // candidate capacity (entries)
     int32_t pln_cap;  // Greedy-Intersections plane capacity (64-bit words)
+    int32_t min_m;    // a round whose run is under way with fewer candidates runs on the warp engine
     int32_t bytes;    // dynamic shared memory per CTA
 };
 
@@ -126,7 +130,7 @@ WarpLayout make_layout(int W, int cap, int mmax, bool planes = false);
 // The process-per-CTA layout of a class of matrices; list_cap 0 = automatic
 // (the largest that lets two CTAs share an SM).  bytes = 0 if no useful
 // layout fits (the class then runs on the warp engine).
-CtaLayout make_cta_layout(int W, int cap, int mmax, int list_cap, int smem_per_block);
+CtaLayout make_cta_layout(int W, int cap, int mmax, int list_cap, int min_list, int smem_per_block);
 int state_words(int W, int cap, int mmax);
 int state_words_gm(const WarpLayout& L);
 

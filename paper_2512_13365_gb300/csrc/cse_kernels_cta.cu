@@ -50,7 +50,7 @@ static CtaLayout cta_layout_for(int W, int cap, int ms, int pln) {
 // The list capacity is the largest (up to kCtaListMax, in steps of 512) that
 // leaves the planes room for a typical step: about 2 ms / 64 + cap / 2
 // blocks of 6 planes; the whole layout must let two CTAs share an SM.
-CtaLayout make_cta_layout(int W, int cap, int mmax, int list_cap, int smem_per_block) {
+CtaLayout make_cta_layout(int W, int cap, int mmax, int list_cap, int min_list, int smem_per_block) {
     int dev = 0, per_sm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess)
@@ -66,7 +66,9 @@ CtaLayout make_cta_layout(int W, int cap, int mmax, int list_cap, int smem_per_b
         const int want = (2 * ms / 64 + cap / 2) * 6;
         if (pln >= want || (fixed && pln >= 64) || (ms <= 1024 && pln >= 64)) {
             const int most = ((2 * ms + 63 * cap) / 64 + 1) * 8;  // no step needs more
-            return cta_layout_for(W, cap, ms, std::min(pln, most));
+            CtaLayout L = cta_layout_for(W, cap, ms, std::min(pln, most));
+            L.min_m = min_list > 0 ? min_list : kCtaMinList;
+            return L;
         }
         if (ms <= 1024) return CtaLayout{};
         ms = std::max(1024, ms - 512);

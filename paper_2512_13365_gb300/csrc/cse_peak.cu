@@ -15,7 +15,7 @@
 //   kind 2  IMAD (32-bit multiply-add, the Philox round's low product)
 //   kind 3  IMAD.HI (32-bit multiply-high, the Philox round's high product)
 //   kind 4  LOP3 alone (3-input XOR)
-//   kind 5  IADD3 alone (3-input add)
+//   kind 5  IADD3 alone (3-input add; two PTX adds that the compiler fuses)
 
 #include <cuda_runtime.h>
 
@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(kPeakThreads) int_peak_kernel(uint32_t seed, l
                 asm volatile("mul.hi.u32 %0, %0, %1;" : "+r"(x[c]) : "r"(k2));
             } else if (KIND == 4) {
                 asm volatile("lop3.b32 %0, %0, %1, %2, 0x96;" : "+r"(x[c]) : "r"(y[c]), "r"(k1));
-            } else {
+            } else {  // one 3-input add (the compiler fuses the two adds into one IADD3)
                 uint32_t t;
                 asm volatile("add.u32 %0, %1, %2;" : "=r"(t) : "r"(x[c]), "r"(k1));
                 asm volatile("add.u32 %0, %1, %2;" : "=r"(x[c]) : "r"(t), "r"(y[c]));
@@ -78,7 +78,8 @@ __global__ void __launch_bounds__(kPeakThreads) int_peak_kernel(uint32_t seed, l
 }
 
 // Lane-ops per chain step of each kind.
-static const int kOpsPerStep[6] = {2, 3, 1, 1, 1, 2};
+// Lane-ops are counted as instructions: kind 5's two adds run as one IADD3.
+static const int kOpsPerStep[6] = {2, 3, 1, 1, 1, 1};
 
 }  // namespace cse
 

@@ -102,7 +102,7 @@ extern "C" int cse_search_static(const cse_scheme* s, const cse_strategy_mix* mi
         o_snap[k] = take(off, (size_t)cap * 4);
         o_snapm[k] = take(off, 8);
         o_rmin[k] = take(off, 8);
-        o_cnt[k] = take(off, 32);
+        o_cnt[k] = take(off, 64);
         o_curve[k] = take(off, (size_t)kCurvePoints * 4);
     }
     const size_t o_clock = take(off, 4), o_status = take(off, 4);
@@ -202,7 +202,7 @@ extern "C" int cse_search_static(const cse_scheme* s, const cse_strategy_mix* mi
         if (e == cudaSuccess) e = cudaMemcpyAsync(b + o_snapm[k], snap_init, 8, cudaMemcpyHostToDevice, stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(d_meta + 2 * k, s->d_meta0[k], 4, cudaMemcpyDeviceToDevice, stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(d_meta + 2 * k + 1, 0, 4, stream);
-        if (e == cudaSuccess) e = cudaMemsetAsync(b + o_cnt[k], 0, 32, stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(b + o_cnt[k], 0, 64, stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(b + o_curve[k], 0xFF, (size_t)kCurvePoints * 4, stream);
     }
     if (e == cudaSuccess) e = cudaMemsetAsync(b + o_clock, 0, 4, stream);
