@@ -89,6 +89,18 @@ typedef struct {
                               (Section 3.4.2) fixes only each coin's 1/2
                               marginal.  Scoring then costs O(m + columns) per
                               step through per-variable sums. */
+#define CSE_FLAG_PERSISTENT 16u  /* cse_search_batch: the whole batch (every
+                              round and sharing boundary of every search) as
+                              one persistent cooperative kernel, with a grid
+                              barrier between the steps and the boundaries;
+                              with CSE_FLAG_GRAPH that one launch is captured
+                              in a CUDA graph.  For the step clock, without
+                              shared coins, every matrix at most 64 rows and
+                              on the shared-memory engine (else CSE_EINVAL).
+                              A barrier gives up after max_spin polls
+                              (0 = 2^26, about 7 s) and the search reports
+                              CSE_ETIMEOUT; results are those of the
+                              searches run alone */
 #define CSE_FLAG_WARP_ENGINE 8u  /* large matrices (those whose process state
                               does not fit a warp's shared-memory slice) run
                               on the one-warp-per-process engine only,
@@ -118,7 +130,8 @@ typedef struct {
     uint32_t patience_rounds; /* iteration mode: iterations without
                                  improvement that end the search; must be 0
                                  with the step clock                          */
-    uint64_t max_spin;        /* reserved for bounded device waits (unused)  */
+    uint64_t max_spin;        /* CSE_FLAG_PERSISTENT: polls of a grid barrier
+                                 before it gives up (0 = 2^26)               */
     uint32_t procs_per_cta;   /* processes (warps) per CTA; 0 = automatic    */
     uint32_t flags;           /* CSE_FLAG_* bits; other bits must be 0       */
     uint32_t cta_list_cap;    /* launch parameter of large matrices: the
@@ -133,7 +146,7 @@ typedef struct {
                                  than this at a round start runs that round
                                  on the one-warp-per-process engine (one warp
                                  serves a short list better than a CTA);
-                                 0 = automatic (1024).  Never changes
+                                 0 = automatic (2048).  Never changes
                                  results.                                     */
 } cse_opts;
 

@@ -73,6 +73,7 @@ FLAG_GRAPH = 1
 FLAG_TRACE = 2
 FLAG_GI_SHARED_COINS = 4
 FLAG_WARP_ENGINE = 8
+FLAG_PERSISTENT = 16
 
 
 def lib() -> ctypes.CDLL:
@@ -346,7 +347,8 @@ def make_mix(weights) -> Mix:
 
 def make_opts(interval: int = 32, permille: int = 400, cap: int = 128, procs_per_cta: int = 0,
               graph: bool = False, trace: bool = False, patience: int = 0, gi_shared: bool = False,
-              warp_engine: bool = False, cta_list_cap: int = 0, cta_min_list: int = 0) -> Opts:
+              warp_engine: bool = False, cta_list_cap: int = 0, cta_min_list: int = 0, persistent: bool = False,
+              max_spin: int = 0) -> Opts:
     """interval 0 selects iteration mode (budget = maximum iterations, stop
     after `patience` iterations without improvement).  warp_engine and
     cta_list_cap choose how large matrices are launched; never results."""
@@ -355,7 +357,9 @@ def make_opts(interval: int = 32, permille: int = 400, cap: int = 128, procs_per
     o.share_interval, o.share_permille, o.col_cap, o.procs_per_cta = interval, permille, cap, procs_per_cta
     o.patience_rounds = patience
     o.flags = ((FLAG_GRAPH if graph else 0) | (FLAG_TRACE if trace else 0) |
-               (FLAG_GI_SHARED_COINS if gi_shared else 0) | (FLAG_WARP_ENGINE if warp_engine else 0))
+               (FLAG_GI_SHARED_COINS if gi_shared else 0) | (FLAG_WARP_ENGINE if warp_engine else 0) |
+               (FLAG_PERSISTENT if persistent else 0))
+    o.max_spin = max_spin
     o.cta_list_cap = cta_list_cap
     o.cta_min_list = cta_min_list
     return o
@@ -405,12 +409,14 @@ def search(scheme: Scheme, weights, n_proc: int, seed: int, budget: int, interva
     return Result(h, len(scheme.mats), n_proc, cap)
 
 
-def resume(scheme: Scheme, checkpoint: bytes, more_steps: int, stream=None, procs_per_cta: int = 0) -> Result:
-    """cse_search_resume: continue a checkpointed search for more_steps steps."""
+def resume(scheme: Scheme, checkpoint: bytes, more_steps: int, stream=None, procs_per_cta: int = 0,
+           warp_engine: bool = False, cta_min_list: int = 0) -> Result:
+    """cse_search_resume: continue a checkpointed search for more_steps steps
+    (the launch options may differ from the original search's)."""
     import struct
     cap, = struct.unpack_from("<I", checkpoint, 20)       # header fields (cse_api.cu): col_cap ...
     n_proc, = struct.unpack_from("<i", checkpoint, 36)    # ... and the process count
-    opts = make_opts(procs_per_cta=procs_per_cta)
+    opts = make_opts(procs_per_cta=procs_per_cta, warp_engine=warp_engine, cta_min_list=cta_min_list)
     buf = ctypes.create_string_buffer(checkpoint, len(checkpoint))
     h = ctypes.c_void_p()
     _check(lib().cse_search_resume(scheme.handle, buf, len(checkpoint), more_steps, ctypes.byref(opts),
@@ -431,15 +437,18 @@ def search_obj(s, scheme: Optional[Scheme] = None, **kw) -> Result:
 def search_batch(schemes: Sequence[Scheme], weights: Sequence, n_procs: Sequence[int], seeds: Sequence[int],
                  budgets: Sequence[int], interval: int = 32, permille: int = 400, cap: int = 128, stream=None,
                  procs_per_cta: int = 0, graph: bool = True, trace: bool = False,
-                 patience: int = 0, gi_shared: bool = False) -> List[Result]:
-    """cse_search_batch: independent searches in one launch sequence."""
+                 patience: int = 0, gi_shared: bool = False, persistent: bool = False,
+                 max_spin: int = 0) -> List[Result]:
+    """cse_search_batch: independent searches in one launch sequence (with
+    persistent, one cooperative kernel over every round)."""
     n = len(schemes)
     hs = (ctypes.c_void_p * n)(*[s.handle for s in schemes])
     mixes = (Mix * n)(*[make_mix(w) for w in weights])
     np_ = (ctypes.c_int32 * n)(*n_procs)
     sd = (ctypes.c_uint64 * n)(*seeds)
     bd = (ctypes.c_int64 * n)(*budgets)
-    opts = make_opts(interval, permille, cap, procs_per_cta, graph, trace, patience, gi_shared)
+    opts = make_opts(interval, permille, cap, procs_per_cta, graph, trace, patience, gi_shared,
+                     persistent=persistent, max_spin=max_spin)
     outs = (ctypes.c_void_p * n)()
     _check(lib().cse_search_batch(n, hs, mixes, np_, sd, bd, ctypes.byref(opts), _stream_ptr(stream), outs))
     res = []

@@ -197,6 +197,12 @@ struct Batch {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
     cudaStream_t cap_stream = nullptr;   // stream the graph is captured on
+    // CSE_FLAG_PERSISTENT: one cooperative kernel; its block holds the
+    // per-round work counters, the barrier words, the barrier status and the
+    // matrices in one unit space
+    bool persistent = false;
+    void* d_pers = nullptr;
+    int* pers_status = nullptr;
 
     void release() {
         if (ev_end) cudaEventSynchronize(ev_end);
@@ -210,6 +216,7 @@ struct Batch {
         if (gexec) cudaGraphExecDestroy(gexec);
         if (graph) cudaGraphDestroy(graph);
         if (cap_stream) cudaStreamDestroy(cap_stream);
+        if (d_pers) cudaFreeAsync(d_pers, stream);
     }
 };
 
@@ -250,7 +257,7 @@ static int check_opts(const cse_opts* opts_in, cse_opts* opts) {
         cse_opts_default(opts);
     if (opts->share_permille > 1000) return fail(CSE_EINVAL, "share_permille must be <= 1000");
     if ((opts->flags & ~(uint32_t)(CSE_FLAG_GRAPH | CSE_FLAG_TRACE | CSE_FLAG_GI_SHARED_COINS |
-                                   CSE_FLAG_WARP_ENGINE)) != 0)
+                                   CSE_FLAG_WARP_ENGINE | CSE_FLAG_PERSISTENT)) != 0)
         return fail(CSE_EINVAL, "reserved option fields must be 0");
     if (opts->share_interval != 0 && opts->patience_rounds != 0)
         return fail(CSE_EINVAL, "patience_rounds applies to iteration mode (share_interval = 0) only");
@@ -629,6 +636,60 @@ static int run_batch(int n, const cse_scheme* const* schemes, const cse_strategy
     };
     if (rc) return bail(cudaSuccess, "");
     const size_t ng = B->ls.groups.size();
+    // CSE_FLAG_PERSISTENT: every matrix in one unit space, one cooperative
+    // kernel over all rounds
+    B->persistent = (opts.flags & CSE_FLAG_PERSISTENT) != 0;
+    WarpLayout pL{};
+    DevMat* p_mats = nullptr;
+    int p_units = 0, p_ppc = 2;
+    int* p_work = nullptr;
+    unsigned* p_bar = nullptr;
+    if (B->persistent) {
+        if (iter_mode || trial || B->ls.gs) {
+            rc = fail(CSE_EINVAL, "CSE_FLAG_PERSISTENT runs the step clock, without shared coins");
+            return bail(cudaSuccess, "");
+        }
+        int pcap = 0, pmmax = 0;
+        for (const auto& g : B->ls.groups) {
+            if (g.gm || g.W > 2) {
+                rc = fail(CSE_EINVAL, "CSE_FLAG_PERSISTENT needs every matrix on the shared-memory engine with at "
+                                      "most 64 rows");
+                return bail(cudaSuccess, "");
+            }
+            pcap = std::max(pcap, g.cap);
+            pmmax = std::max(pmmax, g.mmax);
+        }
+        pL = make_layout(2, pcap, pmmax);  // the offsets of W = 2 hold a matrix of W = 1 too
+        p_ppc = opts.procs_per_cta ? (int)opts.procs_per_cta : 2;
+        while (p_ppc > 1 && (long long)pL.per_warp * p_ppc > max_smem_per_block()) p_ppc--;
+        if ((long long)pL.per_warp * p_ppc > max_smem_per_block()) {
+            rc = fail(CSE_ENOMEM, "process slice exceeds shared memory");
+            return bail(cudaSuccess, "");
+        }
+        std::vector<DevMat> pm(B->ls.mats);
+        for (auto& M : pm) {
+            M.unit_base = p_units;
+            p_units += M.n_proc;
+        }
+        Carve pc;
+        const size_t o_m = pc.take(sizeof(DevMat) * pm.size()), o_w = pc.take(4 * (size_t)B->rounds);
+        const size_t o_b = pc.take(8), o_s = pc.take(4);
+        if ((e = cudaMallocAsync(&B->d_pers, pc.off, stream)) != cudaSuccess) {
+            B->d_pers = nullptr;
+            return bail(e, "persistent launch block");
+        }
+        char* pb = (char*)B->d_pers;
+        p_mats = (DevMat*)(pb + o_m);
+        p_work = (int*)(pb + o_w);
+        p_bar = (unsigned*)(pb + o_b);
+        B->pers_status = (int*)(pb + o_s);
+        if ((e = cudaMemcpyAsync(p_mats, pm.data(), sizeof(DevMat) * pm.size(), cudaMemcpyHostToDevice, stream)) !=
+            cudaSuccess)
+            return bail(e, "persistent launch block");
+        if ((e = launch_batch_persistent(nullptr, 0, nullptr, 0, 0, 0, nullptr, nullptr, nullptr, 0, pL, p_ppc,
+                                         nullptr, true)) != cudaSuccess)
+            return bail(e, "kernel attributes");
+    }
     if ((e = cudaEventCreate(&B->ev_begin)) != cudaSuccess) return bail(e, "event");
     if ((e = cudaEventCreate(&B->ev_end)) != cudaSuccess) return bail(e, "event");
     B->ev_round.resize(iter_mode ? 0 : 2 * (size_t)B->rounds);  // iteration mode: created per round
@@ -639,7 +700,7 @@ static int run_batch(int n, const cse_scheme* const* schemes, const cse_strategy
         for (auto& ev : B->ev_group)
             if ((e = cudaEventCreate(&ev)) != cudaSuccess) return bail(e, "event");
     }
-    const bool concurrent = use_graph && ng > 1;
+    const bool concurrent = use_graph && ng > 1 && !B->persistent;
     if (concurrent) {
         B->aux.resize(ng);
         B->ev_fork.resize(ng + 1);
@@ -664,7 +725,19 @@ static int run_batch(int n, const cse_scheme* const* schemes, const cse_strategy
         return use_graph ? cudaEventRecordWithFlags(ev, ls, cudaEventRecordExternal) : cudaEventRecord(ev, ls);
     };
     rec(B->ev_begin);
-    if (iter_mode) {
+    if (B->persistent) {
+        // the per-round work counters, the barrier and its status start at 0
+        char* pb = (char*)B->d_pers;
+        e = cudaMemsetAsync((char*)p_work, 0, (size_t)((char*)B->pers_status + 4 - (char*)p_work), ls);
+        (void)pb;
+        if (e == cudaSuccess) rec(B->ev_round[0]);
+        if (e == cudaSuccess)
+            e = launch_batch_persistent(p_mats, (int)B->ls.mats.size(), B->ls.d_searches, (int)B->ls.searches.size(),
+                                        p_units, B->rounds, p_work, p_bar, B->pers_status,
+                                        opts.max_spin ? opts.max_spin : (1ull << 26), pL, p_ppc, ls, false);
+        if (e == cudaSuccess) rec(B->ev_round[1]);
+        if (e != cudaSuccess) return bail(e, "persistent batch launch");
+    } else if (iter_mode) {
         // Iteration mode (Section 3.5.2, stopping rule of Section 4): rounds
         // are enqueued in chunks; between chunks the host reads every
         // search's convergence state and stops once all have finished.
@@ -1141,6 +1214,11 @@ int cse_tune_interval(int32_t n_searches, const cse_scheme* const* schemes, cons
 static int wait_result(const cse_result* r) {
     if (!r || !r->sd) return fail(CSE_EINVAL, "NULL result");
     if (r->batch) CUDA_TRY(cudaEventSynchronize(r->batch->ev_end));
+    if (r->batch && r->batch->pers_status) {
+        int32_t ps = 0;
+        CUDA_TRY(cudaMemcpy(&ps, r->batch->pers_status, 4, cudaMemcpyDeviceToHost));
+        if (ps != 0) return fail(CSE_ETIMEOUT, "a grid barrier of the persistent batch kernel gave up (max_spin)");
+    }
     int32_t status = 0;
     CUDA_TRY(cudaMemcpy(&status, r->sd->search.status, 4, cudaMemcpyDeviceToHost));
     if (status != 0) return fail(CSE_ESTATE, "device consistency check failed (candidate list overflow)");
@@ -1300,7 +1378,7 @@ int cse_result_timing(const cse_result* r, float* round_ms, float* total_ms, int
         return CSE_OK;
     }
     float sum = 0.f, tot = 0.f;
-    for (int rd = 0; rd < B->rounds; rd++) {
+    for (int rd = 0; rd < (B->persistent ? 1 : B->rounds); rd++) {  // persistent: one launch, all rounds
         float x = 0.f;
         CUDA_TRY(cudaEventElapsedTime(&x, B->ev_round[2 * rd], B->ev_round[2 * rd + 1]));
         sum += x;
@@ -1497,7 +1575,7 @@ int cse_result_launches(const cse_result* r, int32_t* kernels, int32_t* searches
     int per_round = 1;  // the share kernel, then per class one launch (two on the process-per-CTA engine)
     if (B)
         for (const auto& g : B->ls.groups) per_round += g.cta ? 2 : 1;
-    if (kernels) *kernels = B ? B->rounds * per_round : 0;
+    if (kernels) *kernels = B ? (B->persistent ? 1 : B->rounds * per_round) : 0;
     if (searches_in_launch) *searches_in_launch = B ? (int32_t)B->ls.searches.size() : 0;
     return CSE_OK;
 }

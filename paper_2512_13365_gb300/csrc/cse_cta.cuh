@@ -498,7 +498,7 @@ struct CtaEngine {
             HS[v] = 0;
             HE[v] = 0;
         }
-        for (int x = tid; x < NW * ncols; x += NT) lcw()[(x / ncols) * cap + (x % ncols)] = 0;
+        for (int v = lane; v < ncols; v += 32) LCW[v] = 0;  // each warp its own row
         __syncthreads();
         int sb, se;
         segment(&sb, &se);

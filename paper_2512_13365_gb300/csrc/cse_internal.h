@@ -114,7 +114,7 @@ constexpr int kCtaWarps = 16;
 constexpr int kCtaThreads = 32 * kCtaWarps;
 constexpr int kCtaSeg = 12;                        // list entries per lane held in registers
 constexpr int kCtaListMax = 32 * kCtaSeg * kCtaWarps;  // 6144: the largest list capacity
-constexpr int kCtaMinList = 1024;  // default: shorter lists of a run under way go to the warp engine
+constexpr int kCtaMinList = 2048;  // default: shorter lists of a run under way go to the warp engine
 
 struct CtaLayout {
     int32_t off_cold, off_sh, off_pn, off_cand, off_pl, off_aw, off_hs, off_he, off_vb, off_pb, off_lct, off_g;
@@ -175,6 +175,14 @@ cudaError_t prepare_round(int W, bool gm, bool gs, const WarpLayout& L, int proc
 cudaError_t launch_round_cta(int W, const DevMat* mats, int n_mats, const DevSearch* searches, int total_units,
                              int* work3, int* redo_list, const CtaLayout& CL, int redo_ppc, cudaStream_t stream);
 cudaError_t prepare_round_cta(int W, const CtaLayout& CL, int redo_ppc);
+// A whole batch in one persistent cooperative launch (matrices of at most 2
+// words per column on the shared-memory engine, step clock): work holds one
+// zeroed counter per round, bar two zeroed words, *status 0 (1 after a grid
+// barrier gave up after max_spin polls).
+cudaError_t launch_batch_persistent(const DevMat* mats, int n_mats, const DevSearch* searches, int n_searches,
+                                    int total_units, int rounds, int* work, unsigned* bar, int* status,
+                                    unsigned long long max_spin, const WarpLayout& L, int ppc, cudaStream_t stream,
+                                    bool prepare_only);
 int max_smem_per_block();
 
 // Records the calling thread's error message (cse_last_error) and returns code.

@@ -301,6 +301,54 @@ def test_batch_equals_each_search_alone(cse, graph):
         r.free()
 
 
+@pytest.mark.parametrize("graph", [False, True])
+def test_persistent_batch_equals_each_search_alone(cse, graph):
+    """The whole batch as one persistent cooperative kernel (CSE_FLAG_PERSISTENT;
+    in a CUDA graph or launched directly): schemes of both word widths,
+    uneven process counts and budgets, exactly the results of separate
+    searches, and of the oracle for two of them."""
+    searches = synth.config3(n_schemes=6, n_proc=40, budget=70, interval=16)
+    searches[1].n_proc, searches[2].budget, searches[3].seed = 23, 33, 99
+    batch = cse.search_batch_obj(searches, graph=graph, trace=True, persistent=True)
+    assert batch[0].launches()[0] == 1
+    for s, rb in zip(searches, batch):
+        alone = cse.search_obj(s, trace=True)
+        pb, lb, cb = _records(cse, rb, len(s.mats))
+        pa, la, ca = _records(cse, alone, len(s.mats))
+        assert lb == la and cb == ca
+        for x, y in zip(pb, pa):
+            assert np.array_equal(x, y)
+        assert rb.counters() == alone.counters() and rb.method_ops() == alone.method_ops()
+    for idx in (0, 2):
+        ref = O.search_obj(searches[idx], n_threads=8)
+        assert batch[idx].costs == ref.cost and batch[idx].lists == ref.lists
+    for r in batch:
+        r.free()
+
+
+def test_persistent_batch_barrier_time_out(cse):
+    """A grid barrier that gives up (a poll limit far too small for the CTAs
+    to meet) makes every CTA return; the search reports CSE_ETIMEOUT and the
+    device stays usable."""
+    searches = synth.config3(n_schemes=3, n_proc=512, budget=64, interval=16)
+    batch = cse.search_batch_obj(searches, graph=False, persistent=True, max_spin=1)
+    with pytest.raises(cse.CseError) as e:
+        batch[0].costs
+    assert e.value.code == cse.CSE_ETIMEOUT
+    for r in batch:
+        r.free()
+    s = synth.config1(n_proc=16, budget=16)
+    ref = O.search_obj(s)
+    assert cse.search_obj(s).costs == ref.cost
+
+
+def test_persistent_batch_refuses_large_matrices(cse):
+    s = synth.config4(n_proc=4, budget=8)
+    with pytest.raises(cse.CseError) as e:
+        cse.search_batch_obj([s], persistent=True)
+    assert e.value.code == cse.CSE_EINVAL
+
+
 def test_graph_single_search(cse):
     s = synth.config2(n_proc=64, budget=96)
     r = cse.search(cse.Scheme(s.mats), s.weights, s.n_proc, s.seed, s.budget, s.interval, s.permille, s.cap,
