@@ -727,9 +727,7 @@ static int run_batch(int n, const cse_scheme* const* schemes, const cse_strategy
     rec(B->ev_begin);
     if (B->persistent) {
         // the per-round work counters, the barrier and its status start at 0
-        char* pb = (char*)B->d_pers;
         e = cudaMemsetAsync((char*)p_work, 0, (size_t)((char*)B->pers_status + 4 - (char*)p_work), ls);
-        (void)pb;
         if (e == cudaSuccess) rec(B->ev_round[0]);
         if (e == cudaSuccess)
             e = launch_batch_persistent(p_mats, (int)B->ls.mats.size(), B->ls.d_searches, (int)B->ls.searches.size(),

@@ -343,6 +343,7 @@ struct Engine {
         return reinterpret_cast<unsigned long long*>(sm + L->off_pln);
     }
     __device__ __forceinline__ Cold* cold() const { return reinterpret_cast<Cold*>(sm + L->off_cold); }
+    __device__ __forceinline__ VarRec* rec() const { return reinterpret_cast<VarRec*>(sm + L->off_rec); }
 
     __device__ __forceinline__ uint32_t c2(uint32_t purpose, uint32_t extra_hi) const {
         return ((uint32_t)M->mat_index & 0xFFu) << 24 | (purpose & 0xFu) << 20 | (extra_hi & 0xFFFFFu);
@@ -799,19 +800,13 @@ struct Engine {
     __device__ int sel_gi_planes(int t) {
         const uint32_t lt = lanemask_lt();
         const uint32_t* C = cand();
-        uint16_t* HS = hs();
-        uint16_t* HE = he();
-        uint16_t* VB = vbase();
-        uint16_t* LC = lc();
-        uint16_t* PB = pbase();
+        VarRec* R = rec();
         uint32_t* G = gsum();
         uint16_t* PL = poslo();
         unsigned long long* PLN = planes();
         int part = 0, wmax = 1;
         for (int v = lane; v < ncols; v += 32) {
-            HS[v] = 0;
-            HE[v] = 0;
-            LC[v] = 0;
+            *reinterpret_cast<uint4*>(R + v) = make_uint4(0u, 0u, 0u, 0u);
             G[v] = 0;
         }
         __syncwarp();
@@ -824,10 +819,10 @@ struct Engine {
                 const int hi = key_hi(e), lo = key_lo(e);
                 part += cand_c(e) - 1;
                 wmax = max(wmax, cand_c(e) - 1);
-                if (q == 0 || key_hi(C[q - 1]) != hi) HS[hi] = (uint16_t)q;
-                if (q == m - 1 || key_hi(C[q + 1]) != hi) HE[hi] = (uint16_t)(q + 1);
+                if (q == 0 || key_hi(C[q - 1]) != hi) R[hi].hs = (uint16_t)q;
+                if (q == m - 1 || key_hi(C[q + 1]) != hi) R[hi].he = (uint16_t)(q + 1);
                 const uint32_t peers = __match_any_sync(act, lo);
-                if ((peers & lt) == 0) LC[lo] = (uint16_t)(LC[lo] + __popc(peers));
+                if ((peers & lt) == 0) R[lo].lc = (uint16_t)(R[lo].lc + __popc(peers));
             }
             __syncwarp();
         }
@@ -837,14 +832,18 @@ struct Engine {
         uint32_t run = 0;
         for (int base = 0; base < ncols; base += 32) {
             const int v = base + lane;
-            const int deg = v < ncols ? (HE[v] - HS[v]) + LC[v] : 0;
+            VarRec r{};
+            if (v < ncols) r = R[v];
+            const int deg = v < ncols ? (r.he - r.hs) + r.lc : 0;
             const uint32_t packed = (uint32_t)deg | (uint32_t)((deg + 63) >> 6) << 16;
             const uint32_t incl = (uint32_t)warp_incl_scan((int)packed, lane);
             if (v < ncols) {
                 const uint32_t ex = run + incl - packed;
-                VB[v] = (uint16_t)(ex & 0xFFFFu);
-                PB[v] = (uint16_t)(ex >> 16);
-                LC[v] = 0;
+                r.vb = (uint16_t)(ex & 0xFFFFu);
+                r.pb = (uint16_t)(ex >> 16);
+                r.lct = r.lc;  // the lo count, kept for the scoring
+                r.lc = 0;       // the running lo rank of the placement pass
+                R[v] = r;
             }
             run += (uint32_t)__shfl_sync(FULL_MASK, (int)incl, 31);
         }
@@ -863,11 +862,12 @@ struct Engine {
                 lo = key_lo(e);
                 const uint32_t w = (uint32_t)(cand_c(e) - 1);
                 peers = __match_any_sync(act, lo);
-                const int xh = q - HS[hi];
-                const int xl = (HE[lo] - HS[lo]) + LC[lo] + __popc(peers & lt);
-                PL[q] = (uint16_t)(VB[lo] + xl);
-                unsigned long long* ph = PLN + (size_t)(PB[hi] + (xh >> 6)) * B;
-                unsigned long long* pl = PLN + (size_t)(PB[lo] + (xl >> 6)) * B;
+                const VarRec rh = R[hi], rl = R[lo];
+                const int xh = q - rh.hs;
+                const int xl = (rl.he - rl.hs) + rl.lc + __popc(peers & lt);
+                PL[q] = (uint16_t)(rl.vb + xl);
+                unsigned long long* ph = PLN + (size_t)(rh.pb + (xh >> 6)) * B;
+                unsigned long long* pl = PLN + (size_t)(rl.pb + (xl >> 6)) * B;
                 for (int k = 0; k < B; k++)
                     if ((w >> k) & 1u) {
                         atomicOr(ph + k, 1ull << (xh & 63));
@@ -877,7 +877,7 @@ struct Engine {
                 atomicAdd(G + lo, w);
             }
             __syncwarp();
-            if (valid && (peers & lt) == 0) LC[lo] = (uint16_t)(LC[lo] + __popc(peers));
+            if (valid && (peers & lt) == 0) R[lo].lc = (uint16_t)(R[lo].lc + __popc(peers));
             __syncwarp();
         }
         __threadfence_block();
@@ -895,10 +895,11 @@ struct Engine {
                 const uint32_t e = C[p];
                 const int i = key_lo(e), j = key_hi(e), wp = cand_c(e) - 1;
                 const uint32_t key = e & 0x1FFFFFu;
-                const int n0 = (HE[i] - HS[i]) + LC[i];
-                const int n1 = (HE[j] - HS[j]) + LC[j];
-                const int lp0 = PL[p] - VB[i];  // p's place in A_i
-                const int lp1 = p - HS[j];      // p's place in A_j
+                const VarRec ri = R[i], rj = R[j];
+                const int n0 = (ri.he - ri.hs) + ri.lct;
+                const int n1 = (rj.he - rj.hs) + rj.lct;
+                const int lp0 = PL[p] - ri.vb;  // p's place in A_i
+                const int lp1 = p - rj.hs;      // p's place in A_j
                 // the sign twin (i, j, -s), if a candidate: the neighbour on the
                 // side its sign sorts to, read once
                 int sib = -1, wsib = 0;
@@ -910,15 +911,15 @@ struct Engine {
                         wsib = cand_c(en) - 1;
                     }
                 }
-                const int ls1 = sib - HS[j];
+                const int ls1 = sib - rj.hs;
                 const int nint = (n0 - 1) + (n1 - 1 - (sib >= 0 ? 1 : 0));
                 long long X = 0;
                 int inter = 0, nb = 0;
                 if (nint > 0) {
                     const int nb0 = (n0 + 63) >> 6, nb1 = (n1 + 63) >> 6;
                     nb = nb0 > nb1 ? nb0 : nb1;
-                    const unsigned long long* P0 = PLN + (size_t)PB[i] * B;
-                    const unsigned long long* P1 = PLN + (size_t)PB[j] * B;
+                    const unsigned long long* P0 = PLN + (size_t)ri.pb * B;
+                    const unsigned long long* P1 = PLN + (size_t)rj.pb * B;
                     for (int blk = 0; blk < nb; blk++) {
                         uint32_t r0 = gproc, r1 = (uint32_t)t, r2 = c2g | (uint32_t)blk, r3 = key;
                         philox(r0, r1, r2, r3, k0, k1);

@@ -49,7 +49,16 @@ constexpr uint64_t kFnv0 = 0xCBF29CE484222325ull;
 struct WarpLayout {
     int32_t off_cold, off_pn, off_cand, off_f, off_aw, off_poslo, off_hs, off_he, off_base, off_lc;
     int32_t off_pb, off_g, off_pln;  // HBM path: Greedy-Intersections bit-planes
+    int32_t off_rec;                 // HBM path: per-variable records (VarRec)
     int32_t per_warp;
+};
+
+// HBM path: a variable's Greedy-Intersections adjacency in one 16-byte
+// record (one sector per variable instead of one per field): its hi-block
+// [hs, he) of the list, its running lo rank, its list base, its plane base
+// and its lo count.
+struct VarRec {
+    uint16_t hs, he, lc, vb, pb, lct, pad0, pad1;
 };
 
 // One matrix of one search, as the kernels see it.

@@ -322,6 +322,8 @@ WarpLayout make_layout(int W, int cap, int mmax, bool planes) {
         o = align16(o + cap * 4);
         L.off_pln = o;
         o = align16(o + max_blocks * 8 * 8);
+        L.off_rec = o;
+        o = align16(o + cap * (int)sizeof(VarRec));
     }
     L.per_warp = o;
     return L;
