@@ -528,7 +528,7 @@ def run_serving(args):
     against running each request alone as it arrives."""
     import torch
     from paper_2512_13365_gb300 import cse, synth
-    reqs = synth.serving_requests(n_req=args.requests, rate_hz=50.0, n_proc=2048, budget=args.budget or 256)
+    reqs = synth.serving_requests(n_req=args.requests, rate_hz=args.rate, n_proc=2048, budget=args.budget or 256)
     for _, s in reqs:
         s.cap = 512
     psteps = sum(s.process_steps() for _, s in reqs)
@@ -578,7 +578,7 @@ def run_serving(args):
         "metric": METRIC, "value": psteps / wall, "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 0,
         "ms_per_step": wall * 1000.0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "int32", "data": "synthetic",
-        "config": {"workload": f"serving: {len(reqs)} Poisson requests at 50/s (config 5)", "n_processes": 2048,
+        "config": {"workload": f"serving: {len(reqs)} Poisson requests at {args.rate:g}/s", "n_processes": 2048,
                    "step_budget": reqs[0][1].budget, "share_interval": 32, "col_cap": 512,
                    "admission": "library default limits (64 waves of resident warps)", "peak_active_searches": peak},
         "served": {"p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "process_steps_per_s": st["steps_per_s"],
@@ -797,6 +797,7 @@ def main():
                          "cfg3 (batched), cfg5 (serving), "
                          "cfg2-iter (iteration mode), cfg2-wallclock (best additions at fixed wall-clock budgets)")
     ap.add_argument("--requests", type=int, default=200, help="cfg5: number of requests")
+    ap.add_argument("--rate", type=float, default=50.0, help="cfg5: mean Poisson arrival rate (requests/s)")
     ap.add_argument("--procs", type=int, default=0, help="override the process count (reduced-scale runs)")
     ap.add_argument("--ppc", type=int, default=0, help="processes per CTA (0 = library default)")
     ap.add_argument("--cpu-budget", type=int, default=0,
