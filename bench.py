@@ -193,10 +193,10 @@ def whole_job_rate(units_per_rank: int, world: int, max_ms: float) -> float:
 
 
 def kernel_source_sha() -> str:
-    """sha256 prefix of the round kernel's sources (the engine and its unit)."""
+    """sha256 prefix of the round kernels' sources (the engines and their units)."""
     import hashlib
     h = hashlib.sha256()
-    for f in ("cse_engine.cuh", "cse_kernels.cu"):
+    for f in ("cse_engine.cuh", "cse_kernels.cu", "cse_cta.cuh", "cse_kernels_cta.cu", "cse_internal.h"):
         with open(os.path.join(ROOT, "paper_2512_13365_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -247,7 +247,8 @@ def run_ours(args):
 
     def one():
         return cse.search(scheme, s.weights, s.n_proc, s.seed, s.budget, s.interval, s.permille, s.cap,
-                          stream=stream, procs_per_cta=args.ppc, gi_shared=args.gi_shared)
+                          stream=stream, procs_per_cta=args.ppc, gi_shared=args.gi_shared,
+                          warp_engine=args.warp_engine, cta_min_list=args.cta_min_list)
 
     for _ in range(args.warmup):
         r = one()
@@ -317,7 +318,8 @@ def run_ours(args):
         t0 = time.perf_counter()
         sc = cse.Scheme(pinned)
         r = cse.search(sc, s.weights, s.n_proc, s.seed, s.budget, s.interval, s.permille, s.cap, stream=stream,
-                       procs_per_cta=args.ppc, gi_shared=args.gi_shared)
+                       procs_per_cta=args.ppc, gi_shared=args.gi_shared, warp_engine=args.warp_engine,
+                       cta_min_list=args.cta_min_list)
         lists = [r.fetch(k) for k in range(len(s.mats))]
         e2e_ms.append((time.perf_counter() - t0) * 1000.0)
         d2h = sum(4 * len(l) + 16 for l, _, _ in lists)
@@ -424,12 +426,15 @@ def run_batched(args):
         rs = cse.search_batch(*ba, interval=interval, cap=cap, stream=stream, graph=True)
         return rs
 
+    def persistent():
+        return cse.search_batch(*ba, interval=interval, cap=cap, stream=stream, graph=True, persistent=True)
+
     def per_scheme():
         return [cse.search(sc, s.weights, s.n_proc, s.seed, s.budget, interval, s.permille, cap, stream=stream)
                 for sc, s in zip(schemes, searches)]
 
     out = {}
-    for name, fn in (("batched", batched), ("per_scheme", per_scheme)):
+    for name, fn in (("batched", batched), ("persistent", persistent), ("per_scheme", per_scheme)):
         for _ in range(args.warmup):
             for r in fn():
                 r.free()
@@ -446,7 +451,7 @@ def run_batched(args):
             torch.cuda.synchronize()
             ms.append(a.elapsed_time(b))
             totals = [r.total for r in rs]
-            kernels = rs[0].launches()[0] if name == "batched" else sum(r.launches()[0] for r in rs)
+            kernels = rs[0].launches()[0] if name != "per_scheme" else sum(r.launches()[0] for r in rs)
             if name == "batched":
                 round_ms, _, n_rounds = rs[0].timing()
                 ops_total = sum(r.counters()[2] for r in rs)
@@ -456,6 +461,7 @@ def run_batched(args):
         out[name] = {"ms": statistics.mean(ms), "value": psteps / (statistics.mean(ms) / 1000.0),
                      "best_additions_total": sum(totals), "kernel_launches": kernels}
     assert out["batched"]["best_additions_total"] == out["per_scheme"]["best_additions_total"]
+    assert out["persistent"]["best_additions_total"] == out["per_scheme"]["best_additions_total"]
 
     # best additions at a fixed wall-clock budget: the per-scheme launches get
     # the step budget B; the batched graph gets as many steps (a multiple of
@@ -508,7 +514,9 @@ def run_batched(args):
                    "shapes": [[list(m.shape) for m in s.mats] for s in searches[:3]] + ["..."],
                    "l2": "flushed (256 MB write) between timed steps"},
         "batched_graph": out["batched"], "one_launch_sequence_per_scheme": out["per_scheme"],
+        "persistent_kernel_in_graph": out["persistent"],
         "speedup_batched_vs_per_scheme": out["per_scheme"]["ms"] / out["batched"]["ms"],
+        "speedup_persistent_vs_per_scheme": out["per_scheme"]["ms"] / out["persistent"]["ms"],
         "fixed_wall_clock": fixed,
         "autotune": {"seconds": tune_s, "classes": tuned, "interval_candidates": [16, 32, 64],
                      "interval_chosen": interval},
@@ -806,6 +814,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--budget", type=int, default=0, help="override the step budget (profiling runs)")
     ap.add_argument("--seconds", default="1,10,60", help="cfg2-wallclock: the wall-clock budgets")
+    ap.add_argument("--warp-engine", action="store_true",
+                    help="large matrices on the one-warp-per-process engine only (a launch choice; same results)")
+    ap.add_argument("--cta-min-list", type=int, default=0,
+                    help="large matrices: runs under way with shorter lists go to the warp engine (0 = library default)")
     ap.add_argument("--gi-shared", action="store_true",
                     help="Greedy-Intersections with shared coins (an option that changes results)")
     ap.add_argument("--out", default=os.path.join(ROOT, "bench_out"), help="where the clock samples go")

@@ -12,7 +12,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libcse_gb300.so")
 SOURCES = ["cse_kernels.cu", "cse_kernels_gs.cu", "cse_kernels_cta.cu", "cse_api.cu", "cse_static.cu", "cse_philox.cu",
-           "cse_peak.cu", "cse_flip.cu"]
+           "cse_peak.cu", "cse_flip.cu", "cse_batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"), "-I", CSRC]
 

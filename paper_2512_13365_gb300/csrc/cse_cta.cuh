@@ -36,16 +36,17 @@
 
 namespace cse {
 
-// Block-wide scratch for reductions and broadcasts.
+// Block-wide scratch for reductions and broadcasts (sized for the widest CTA).
 struct CtaShared {
     int bc[8];                     // broadcast slots
     int ws[kCtaWarps * 4];         // per-warp partial sums
     unsigned int wr[kCtaWarps * 3];  // per-warp argmax partials
 };
 
-template <int W>
+// NW warps per process (a CTA of 32 NW threads).
+template <int W, int NW>
 struct CtaEngine {
-    static constexpr int NW = kCtaWarps, NT = kCtaThreads;
+    static constexpr int NT = 32 * NW;
     unsigned char* sm;
     const CtaLayout* L;
     const DevMat* M;
@@ -228,7 +229,7 @@ struct CtaEngine {
         // so every warp has read its entries before any warp writes
         int sb, se;
         segment(&sb, &se);
-        uint32_t ev[kCtaSeg];
+        uint32_t ev[kCtaSeg];  // 32 kCtaSeg NW >= ms entries: the whole segment
         int kept = 0, nij = 0;
 #pragma unroll
         for (int x = 0; x < kCtaSeg; x++) {
@@ -258,58 +259,63 @@ struct CtaEngine {
             if (keep) C[pos + __popc(kb & lt)] = ev[x];
             pos += __popc(kb);
         }
-        // the new pairs (u, k), u < k <= cap <= NT: one column per thread
-        int cp = 0, cm = 0, both = 0;
-        bool live = false;
-        const int u = tid;
-        if (u < k) {
-            uint32_t sup = 0;
-            int ng = 0;
-#pragma unroll
-            for (int w = 0; w < W; w++) {
-                const uint2 A = P[u * W + w], K = P[k * W + w];
-                sup |= A.x | A.y;
-                const uint32_t bt = (A.x | A.y) & (K.x | K.y);
-                both += __popc(bt);
-                ng += __popc((A.x ^ K.x) & bt);
-            }
-            live = sup != 0;
-            cm = ng;
-            cp = both - ng;
-        }
-        const int ep = cp >= 2, em = cm >= 2;
-        const int cnt = ep + em;
-        const int incl = warp_incl_scan(cnt, lane);
-        const int wtot = __shfl_sync(FULL_MASK, incl, 31);
-        const int wlive = __popc(__ballot_sync(FULL_MASK, live));
-        const int wboth = __reduce_add_sync(FULL_MASK, both);
+        // the new pairs (u, k), u < k, NT columns at a time
+        int added = 0, nu = 0, rb = 0;
         int* ws = sh()->ws;
-        if (lane == 0) {
-            ws[4 * warp] = wtot;
-            ws[4 * warp + 1] = wlive;
-            ws[4 * warp + 2] = wboth;
-            ws[4 * warp + 3] = nij;  // this warp's recounted candidates
-        }
-        __syncthreads();  // also orders the compaction's writes before the appends
-        int off = 0, added = 0, nu = 0, rb = 0;
-        nij = 0;
+        int nij_all = 0;
+        for (int ubase = 0; ubase < k; ubase += NT) {
+            int cp = 0, cm = 0, both = 0;
+            bool live = false;
+            const int u = ubase + tid;
+            if (u < k) {
+                uint32_t sup = 0;
+                int ng = 0;
 #pragma unroll
-        for (int w = 0; w < NW; w++) {
-            const int x = ws[4 * w];
-            off += w < warp ? x : 0;
-            added += x;
-            nu += ws[4 * w + 1];
-            rb += ws[4 * w + 2];
-            nij += ws[4 * w + 3];
+                for (int w = 0; w < W; w++) {
+                    const uint2 A = P[u * W + w], K = P[k * W + w];
+                    sup |= A.x | A.y;
+                    const uint32_t bt = (A.x | A.y) & (K.x | K.y);
+                    both += __popc(bt);
+                    ng += __popc((A.x ^ K.x) & bt);
+                }
+                live = sup != 0;
+                cm = ng;
+                cp = both - ng;
+            }
+            const int ep = cp >= 2, em = cm >= 2;
+            const int cnt = ep + em;
+            const int incl = warp_incl_scan(cnt, lane);
+            const int wtot = __shfl_sync(FULL_MASK, incl, 31);
+            const int wlive = __popc(__ballot_sync(FULL_MASK, live));
+            const int wboth = __reduce_add_sync(FULL_MASK, both);
+            if (lane == 0) {
+                ws[4 * warp] = wtot;
+                ws[4 * warp + 1] = wlive;
+                ws[4 * warp + 2] = wboth;
+                ws[4 * warp + 3] = ubase == 0 ? nij : 0;  // this warp's recounted candidates
+            }
+            __syncthreads();  // also orders the compaction's writes before the appends
+            int off = 0, chunk = 0;
+#pragma unroll
+            for (int w = 0; w < NW; w++) {
+                const int x = ws[4 * w];
+                off += w < warp ? x : 0;
+                chunk += x;
+                nu += ws[4 * w + 1];
+                rb += ws[4 * w + 2];
+                nij_all += ws[4 * w + 3];
+            }
+            __syncthreads();  // the partials are read before the next chunk writes them
+            if (newm + added + chunk > ms) {  // the list would outgrow its shared-memory capacity
+                abandon = 1;
+                return;
+            }
+            int p = newm + added + off + incl - cnt;
+            if (ep) C[p++] = make_cand(u, k, 0, cp);
+            if (em) C[p] = make_cand(u, k, 1, cm);
+            added += chunk;
         }
-        if (newm + added > ms) {  // the list would outgrow its shared-memory capacity
-            abandon = 1;
-            __syncthreads();
-            return;
-        }
-        int p = newm + off + incl - cnt;
-        if (ep) C[p++] = make_cand(u, k, 0, cp);
-        if (em) C[p] = make_cand(u, k, 1, cm);
+        nij = nij_all;
         if (tid == 0) {
             F()[nf] = (int32_t)((uint32_t)i | (uint32_t)j << 10 | (uint32_t)neg << 20);
             Cold* cd = cold();
@@ -523,32 +529,36 @@ struct CtaEngine {
         const int T = bsum4(part, 0, 0, 0).x;
         const int B = 32 - __clz((int)bmax(wmax));
         // per variable: lo totals, each warp's lo base, degree; positions and
-        // 64-position blocks of A_v by a block-wide exclusive scan
-        // (ncols <= cap <= NT: one variable per thread)
-        uint32_t packed = 0;
-        const int v = tid;
-        if (v < ncols) {
-            int run = 0;
+        // 64-position blocks of A_v by a block-wide exclusive scan, NT
+        // variables at a time
+        uint32_t carry = 0;
+        for (int vbase = 0; vbase < ncols; vbase += NT) {
+            uint32_t packed = 0;
+            const int v = vbase + tid;
+            if (v < ncols) {
+                int run = 0;
 #pragma unroll
-            for (int w = 0; w < NW; w++) {
-                uint16_t* cw = lcw() + w * cap + v;
-                const int x = *cw;
-                *cw = (uint16_t)run;
-                run += x;
+                for (int w = 0; w < NW; w++) {
+                    uint16_t* cw = lcw() + w * cap + v;
+                    const int x = *cw;
+                    *cw = (uint16_t)run;
+                    run += x;
+                }
+                LCT[v] = (uint16_t)run;
+                const int deg = (HE[v] - HS[v]) + run;
+                packed = (uint32_t)deg | (uint32_t)((deg + 63) >> 6) << 16;
             }
-            LCT[v] = (uint16_t)run;
-            const int deg = (HE[v] - HS[v]) + run;
-            packed = (uint32_t)deg | (uint32_t)((deg + 63) >> 6) << 16;
+            const uint32_t incl = (uint32_t)warp_incl_scan((int)packed, lane);
+            int tot = 0;
+            const int wpre = wprefix((int)__shfl_sync(FULL_MASK, incl, 31), &tot);
+            if (v < ncols) {
+                const uint32_t ex = carry + (uint32_t)wpre + incl - packed;
+                VB[v] = (uint16_t)(ex & 0xFFFFu);
+                PB[v] = (uint16_t)(ex >> 16);
+            }
+            carry += (uint32_t)tot;
         }
-        const uint32_t incl = (uint32_t)warp_incl_scan((int)packed, lane);
-        int tot = 0;
-        const int wpre = wprefix((int)__shfl_sync(FULL_MASK, incl, 31), &tot);
-        if (v < ncols) {
-            const uint32_t ex = (uint32_t)wpre + incl - packed;
-            VB[v] = (uint16_t)(ex & 0xFFFFu);
-            PB[v] = (uint16_t)(ex >> 16);
-        }
-        const int nblk = (int)((uint32_t)tot >> 16);
+        const int nblk = (int)(carry >> 16);
         if (nblk * B > L->pln_cap) {
             abandon = 1;
             __syncthreads();
@@ -793,12 +803,16 @@ struct CtaEngine {
 
 // One round of one process on a CTA; returns false if the process must be
 // redone by the warp engine (nothing of its state region was written).
-template <int W>
+template <int W, int NW>
 __device__ bool cta_run_unit(const DevMat* __restrict__ mats, int n_mats, const DevSearch* __restrict__ searches,
                              const CtaLayout& L, unsigned char* smem, int unit) {
+    constexpr int NT = 32 * NW;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    int mi = 0;
-    while (mi + 1 < n_mats && mats[mi + 1].unit_base <= unit) mi++;
+    int mi = 0, mhi = n_mats - 1;  // the last matrix whose first unit is <= unit
+    while (mi < mhi) {
+        const int mid = (mi + mhi + 1) >> 1;
+        if (mats[mid].unit_base <= unit) mi = mid; else mhi = mid - 1;
+    }
     const DevMat* M = &mats[mi];
     const DevSearch* S = &searches[M->search];
     const int clk = *S->clock;
@@ -807,7 +821,7 @@ __device__ bool cta_run_unit(const DevMat* __restrict__ mats, int n_mats, const 
 
     uint32_t* st = M->state + (size_t)(unit - M->unit_base) * M->state_words;
     unsigned char* gst = reinterpret_cast<unsigned char*>(st + H_WORDS);  // the HBM engine's arrays
-    CtaEngine<W> E;
+    CtaEngine<W, NW> E;
     E.sm = smem;
     E.L = &L;
     E.M = M;
@@ -876,13 +890,13 @@ __device__ bool cta_run_unit(const DevMat* __restrict__ mats, int n_mats, const 
     if (t0 > 0) {  // the process's arrays, from the HBM engine's layout of its state region
         const uint2* spn = reinterpret_cast<const uint2*>(gst + M->gml.off_pn);
         uint2* P = E.pn();
-        for (int x = tid; x < E.ncols * W; x += kCtaThreads) P[x] = spn[x];
+        for (int x = tid; x < E.ncols * W; x += NT) P[x] = spn[x];
         const uint32_t* sc = reinterpret_cast<const uint32_t*>(gst + M->gml.off_cand);
         uint32_t* C = E.cand();
-        for (int x = tid; x < E.m; x += kCtaThreads) C[x] = sc[x];
+        for (int x = tid; x < E.m; x += NT) C[x] = sc[x];
         const int32_t* sf = reinterpret_cast<const int32_t*>(gst + M->gml.off_f);
         int32_t* F = E.F();
-        for (int x = tid; x < E.nf; x += kCtaThreads) F[x] = sf[x];
+        for (int x = tid; x < E.nf; x += NT) F[x] = sf[x];
     }
     __syncthreads();
 
@@ -934,13 +948,13 @@ __device__ bool cta_run_unit(const DevMat* __restrict__ mats, int n_mats, const 
     {
         uint2* spn = reinterpret_cast<uint2*>(gst + M->gml.off_pn);
         const uint2* P = E.pn();
-        for (int x = tid; x < E.ncols * W; x += kCtaThreads) spn[x] = P[x];
+        for (int x = tid; x < E.ncols * W; x += NT) spn[x] = P[x];
         uint32_t* sc = reinterpret_cast<uint32_t*>(gst + M->gml.off_cand);
         const uint32_t* C = E.cand();
-        for (int x = tid; x < E.m; x += kCtaThreads) sc[x] = C[x];
+        for (int x = tid; x < E.m; x += NT) sc[x] = C[x];
         int32_t* sf = reinterpret_cast<int32_t*>(gst + M->gml.off_f);
         const int32_t* F = E.F();
-        for (int x = tid; x < E.nf; x += kCtaThreads) sf[x] = F[x];
+        for (int x = tid; x < E.nf; x += NT) sf[x] = F[x];
     }
     return true;
 }
@@ -949,8 +963,8 @@ __device__ bool cta_run_unit(const DevMat* __restrict__ mats, int n_mats, const 
 // process per CTA at a time (persistent grid, work counter work3[0]);
 // processes that outgrow the shared-memory capacities are appended to
 // redo_list (count work3[2]) for the warp engine's launch that follows.
-template <int W>
-__global__ void __launch_bounds__(kCtaThreads, 2) cta_round_kernel(const DevMat* __restrict__ mats, int n_mats,
+template <int W, int NW>
+__global__ void __launch_bounds__(32 * NW, 1024 / (32 * NW)) cta_round_kernel(const DevMat* __restrict__ mats, int n_mats,
                                                                   const DevSearch* __restrict__ searches,
                                                                   int total_units, int* __restrict__ work3,
                                                                   int* __restrict__ redo_list,
@@ -963,7 +977,7 @@ __global__ void __launch_bounds__(kCtaThreads, 2) cta_round_kernel(const DevMat*
         const int unit = sh->bc[7];
         __syncthreads();
         if (unit >= total_units) return;
-        const bool done = cta_run_unit<W>(mats, n_mats, searches, L, smem, unit);
+        const bool done = cta_run_unit<W, NW>(mats, n_mats, searches, L, smem, unit);
         if (!done && threadIdx.x == 0) redo_list[atomicAdd(&work3[2], 1)] = unit;
         __syncthreads();
     }

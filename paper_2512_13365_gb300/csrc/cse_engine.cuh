@@ -801,14 +801,10 @@ struct Engine {
         const uint32_t lt = lanemask_lt();
         const uint32_t* C = cand();
         VarRec* R = rec();
-        uint32_t* G = gsum();
         uint16_t* PL = poslo();
         unsigned long long* PLN = planes();
         int part = 0, wmax = 1;
-        for (int v = lane; v < ncols; v += 32) {
-            *reinterpret_cast<uint4*>(R + v) = make_uint4(0u, 0u, 0u, 0u);
-            G[v] = 0;
-        }
+        for (int v = lane; v < ncols; v += 32) *reinterpret_cast<uint4*>(R + v) = make_uint4(0u, 0u, 0u, 0u);
         __syncwarp();
         for (int base = 0; base < m; base += 32) {
             const int q = base + lane;
@@ -873,8 +869,8 @@ struct Engine {
                         atomicOr(ph + k, 1ull << (xh & 63));
                         atomicOr(pl + k, 1ull << (xl & 63));
                     }
-                atomicAdd(G + hi, w);
-                atomicAdd(G + lo, w);
+                atomicAdd(&R[hi].g, w);
+                atomicAdd(&R[lo].g, w);
             }
             __syncwarp();
             if (valid && (peers & lt) == 0) R[lo].lc = (uint16_t)(R[lo].lc + __popc(peers));
@@ -935,7 +931,7 @@ struct Engine {
                             if (sib >= 0 && (ls1 >> 6) == blk && ((R1 >> (ls1 & 63)) & 1ull)) X -= wsib;
                         }
                     }
-                    inter = (int)G[i] + (int)G[j] - 2 * wp - wsib;
+                    inter = (int)ri.g + (int)rj.g - 2 * wp - wsib;
                 }
                 const int D = T - wp - inter;
                 const long long sc = ((long long)wp << 32) + a * (((long long)D << 16) + b * X);
@@ -1045,8 +1041,11 @@ template <int W, bool GM, bool GS>
 __device__ __forceinline__ void run_unit(const DevMat* __restrict__ mats, int n_mats,
                                          const DevSearch* __restrict__ searches, const WarpLayout& L,
                                          unsigned char* smem, int warp, int lane, int unit) {
-    int mi = 0;
-    while (mi + 1 < n_mats && mats[mi + 1].unit_base <= unit) mi++;
+    int mi = 0, mhi = n_mats - 1;  // the last matrix whose first unit is <= unit
+    while (mi < mhi) {
+        const int mid = (mi + mhi + 1) >> 1;
+        if (mats[mid].unit_base <= unit) mi = mid; else mhi = mid - 1;
+    }
     const DevMat* M = &mats[mi];
     const DevSearch* S = &searches[M->search];
     // step clock: this round runs steps [t0, t1).  Iteration mode: one whole

@@ -55,10 +55,11 @@ struct WarpLayout {
 
 // HBM path: a variable's Greedy-Intersections adjacency in one 16-byte
 // record (one sector per variable instead of one per field): its hi-block
-// [hs, he) of the list, its running lo rank, its list base, its plane base
-// and its lo count.
+// [hs, he) of the list, its running lo rank, its list base, its plane base,
+// its lo count and the sum g of the weights (c - 1) of its list.
 struct VarRec {
-    uint16_t hs, he, lc, vb, pb, lct, pad0, pad1;
+    uint16_t hs, he, lc, vb, pb, lct;
+    uint32_t g;
 };
 
 // One matrix of one search, as the kernels see it.
@@ -119,7 +120,7 @@ struct DevSearch {
 // planes outgrow the capacities below leaves the round unfinished and is
 // redone, from its round-start state, by the one-warp-per-process HBM engine
 // (round_kernel<W, true, false>), so results never depend on the capacities.
-constexpr int kCtaWarps = 16;
+constexpr int kCtaWarps = 16;                      // the widest CTA: 16 warps per process
 constexpr int kCtaThreads = 32 * kCtaWarps;
 constexpr int kCtaSeg = 12;                        // list entries per lane held in registers
 constexpr int kCtaListMax = 32 * kCtaSeg * kCtaWarps;  // 6144: the largest list capacity
@@ -131,6 +132,7 @@ struct CtaLayout {
     int32_t ms;       // candidate capacity (entries)
     int32_t pln_cap;  // Greedy-Intersections plane capacity (64-bit words)
     int32_t min_m;    // a round whose run is under way with fewer candidates runs on the warp engine
+    int32_t nw;       // warps per process (CTA): 16 (two CTAs per SM) or 8 (three or four)
     int32_t bytes;    // dynamic shared memory per CTA
 };
 
@@ -139,7 +141,7 @@ WarpLayout make_layout(int W, int cap, int mmax, bool planes = false);
 // The process-per-CTA layout of a class of matrices; list_cap 0 = automatic
 // (the largest that lets two CTAs share an SM).  bytes = 0 if no useful
 // layout fits (the class then runs on the warp engine).
-CtaLayout make_cta_layout(int W, int cap, int mmax, int list_cap, int min_list, int smem_per_block);
+CtaLayout make_cta_layout(int W, int cap, int mmax, int list_cap, int min_list, int smem_per_block, int nw = 16);
 int state_words(int W, int cap, int mmax);
 int state_words_gm(const WarpLayout& L);
 

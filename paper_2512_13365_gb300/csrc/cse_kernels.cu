@@ -4,6 +4,7 @@
 // coins per pair.
 
 #include "cse_engine.cuh"
+#include "cse_share.cuh"
 
 namespace cse {
 
@@ -72,190 +73,11 @@ __global__ void ingest_kernel(const int8_t* __restrict__ raw, int rows, int nx, 
 // search, one warp per matrix.  In iteration mode every round is a boundary,
 // followed by the convergence test on the sum of the matrices' best costs
 // (Section 4: unchanged for `patience` iterations ends the search).
-__device__ void share_one(const DevMat* __restrict__ mats, const DevSearch* __restrict__ S);
-
 __global__ void share_kernel(const DevMat* __restrict__ mats, const DevSearch* __restrict__ searches,
                              int* __restrict__ work, int n_work) {
     // the round kernels' work counters, for the next round
     if (blockIdx.x == 0 && (int)threadIdx.x < n_work) work[threadIdx.x] = 0;
     share_one(mats, &searches[blockIdx.x]);
-}
-
-// The sharing boundary of one search, by the threads of one CTA (one warp
-// per matrix at a time).
-__device__ void share_one(const DevMat* __restrict__ mats, const DevSearch* __restrict__ S) {
-    const bool iter_mode = S->interval == 0;
-    const int c0 = *S->clock;
-    if (c0 >= S->budget || (iter_mode && S->conv[1])) return;
-    const int c1 = iter_mode ? c0 + 1 : min(c0 + S->interval, S->budget);
-    const bool boundary = iter_mode || c1 % S->interval == 0;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    __shared__ int s_total, s_final;
-    if (threadIdx.x == 0) s_total = 0;
-    __syncthreads();
-    for (int k = warp; k < S->n_mats; k += nw) {
-        const DevMat* M = &mats[S->mat_pos[k]];
-        const unsigned long long key = *M->round_min;
-        if (key == ~0ull) continue;  // no process reported (cannot happen while the search runs)
-        const int cost = (int)(key >> 32), win = (int)(key & 0xFFFFFFFFu) - M->proc_offset;
-        const bool local = win >= 0 && win < M->n_proc;  // else another rank's (a shard)
-        if (boundary && cost < M->snap_meta[0]) {
-            const int len = local ? (int)M->state[(size_t)win * M->state_words + H_BEST_LEN] : *M->ext_len;
-            const int32_t* src = local ? M->best_list + (size_t)win * M->cap : M->ext_list;
-            for (int x = lane; x < len; x += 32) M->snap[x] = src[x];
-            __syncwarp();
-            if (lane == 0) {
-                M->snap_meta[0] = cost;
-                M->snap_meta[1] = len;
-            }
-        }
-        if (lane == 0) {
-            atomicAdd(&s_total, cost);
-            // the best-Cost curve: one point per round (per iteration)
-            const int r = iter_mode ? c0 : c0 / S->interval;
-            if (r < kCurvePoints) M->curve[r] = cost;
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        bool fin = c1 == S->budget;
-        if (iter_mode) {
-            int32_t* cv = S->conv;
-            if (s_total < cv[2]) {
-                cv[2] = s_total;
-                cv[0] = 0;
-            } else {
-                cv[0]++;
-            }
-            // converged: set only by the patience rule, so that a search
-            // that merely used up its iterations can be resumed
-            if (S->patience > 0 && cv[0] >= S->patience) {
-                fin = true;
-                cv[1] = 1;
-            }
-            cv[3] = c1;
-        }
-        s_final = fin ? 1 : 0;
-    }
-    __syncthreads();
-    for (int k = warp; k < S->n_mats; k += nw) {
-        const DevMat* M = &mats[S->mat_pos[k]];
-        const unsigned long long key = *M->round_min;
-        if (key == ~0ull) continue;
-        if (s_final) {
-            const int cost = (int)(key >> 32), win = (int)(key & 0xFFFFFFFFu) - M->proc_offset;
-            const bool local = win >= 0 && win < M->n_proc;
-            const int len = local ? (int)M->state[(size_t)win * M->state_words + H_BEST_LEN] : *M->ext_len;
-            const int32_t* src = local ? M->best_list + (size_t)win * M->cap : M->ext_list;
-            for (int x = lane; x < len; x += 32) M->result[x] = src[x];
-            if (lane == 0) {
-                M->result_meta[0] = cost;
-                M->result_meta[1] = len;
-            }
-        }
-        __syncwarp();
-        if (lane == 0) *M->round_min = ~0ull;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) *S->clock = c1;
-}
-
-// A bounded grid barrier for a cooperative launch (every CTA co-resident):
-// the last CTA to arrive resets the count and bumps the generation; the
-// others poll the generation at most max_spin times (a short sleep between
-// polls).  A CTA that gives up, or that sees another one's time-out, writes
-// 1 to *status and returns false; so does every later barrier, so that no
-// CTA waits on one that has left.
-__device__ bool grid_barrier(unsigned* bar, unsigned long long max_spin, int* status) {
-    __shared__ int ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        ok = 1;
-        volatile unsigned* gen = bar + 1;
-        volatile int* st = status;
-        const unsigned g = *gen;
-        __threadfence();
-        if (*st != 0) {
-            ok = 0;
-        } else if (atomicAdd(bar, 1u) == gridDim.x - 1) {
-            atomicExch(bar, 0u);
-            __threadfence();
-            atomicAdd(bar + 1, 1u);
-        } else {
-            unsigned long long n = 0;
-            while (*gen == g) {
-                if (*st != 0 || ++n > max_spin) {
-                    atomicExch(status, 1);
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(100);
-            }
-        }
-        __threadfence();
-    }
-    __syncthreads();
-    return ok != 0;
-}
-
-// A whole batch (Section 3.5: every search's rounds and sharing boundaries)
-// in one persistent cooperative launch, for batches whose matrices all run
-// on the shared-memory engine with at most 2 words per column: per round,
-// every warp takes processes from the round's work counter (work[round]),
-// dispatching on the matrix's word width; then a grid barrier, the sharing
-// boundary of every search (CTA b takes searches b, b + grid, ...), and
-// another barrier.  Each search keeps its own clock, so the results are
-// those of the searches run alone.
-__global__ void __launch_bounds__(128, CSE_MIN_BLOCKS)
-    batch_kernel(const DevMat* __restrict__ mats, int n_mats, const DevSearch* __restrict__ searches,
-                 int n_searches, int total_units, int rounds, int* __restrict__ work, unsigned* __restrict__ bar,
-                 int* __restrict__ status, unsigned long long max_spin, const __grid_constant__ WarpLayout L) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int rd = 0; rd < rounds; rd++) {
-        for (;;) {
-            int unit = 0;
-            if (lane == 0) unit = atomicAdd(&work[rd], 1);
-            unit = __shfl_sync(FULL_MASK, unit, 0);
-            if (unit >= total_units) break;
-            int mi = 0;
-            while (mi + 1 < n_mats && mats[mi + 1].unit_base <= unit) mi++;
-            if (mats[mi].W == 1)
-                run_unit<1, false, false>(mats, n_mats, searches, L, smem, warp, lane, unit);
-            else
-                run_unit<2, false, false>(mats, n_mats, searches, L, smem, warp, lane, unit);
-            __syncwarp();
-        }
-        if (!grid_barrier(bar, max_spin, status)) return;
-        for (int sidx = blockIdx.x; sidx < n_searches; sidx += gridDim.x) share_one(mats, &searches[sidx]);
-        if (!grid_barrier(bar, max_spin, status)) return;
-    }
-}
-
-cudaError_t launch_batch_persistent(const DevMat* mats, int n_mats, const DevSearch* searches, int n_searches,
-                                    int total_units, int rounds, int* work, unsigned* bar, int* status,
-                                    unsigned long long max_spin, const WarpLayout& L, int ppc, cudaStream_t stream,
-                                    bool prepare_only) {
-    const size_t smem = (size_t)L.per_warp * ppc;
-    if (prepare_only) return raise_max_dynamic_smem((const void*)batch_kernel, (int)smem);
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel, 32 * ppc, smem);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(sms * per_sm));
-    cfg.blockDim = dim3((unsigned)(32 * ppc));
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = stream;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeCooperative;
-    attr[0].val.cooperative = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, batch_kernel, mats, n_mats, searches, n_searches, total_units, rounds, work, bar,
-                              status, max_spin, L);
 }
 
 // Brent equations (Section 3.1) of a scheme (m,n,p:r): one thread per index
