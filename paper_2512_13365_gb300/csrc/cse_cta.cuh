@@ -44,6 +44,25 @@ struct CtaShared {
 };
 
 // NW warps per process (a CTA of 32 NW threads).
+// Coin-weighted weight sum over one 64-position block of some A_v,
+// sum_k 2^k popc(plane_k & R), from the block's planes in shared memory.
+// The planes are stored in pairs (an even count per block, 16-byte aligned,
+// the padding plane zero) so that each pair is one 16-byte load; B <= 8
+// (weights c - 1 <= 255) and the loop is unrolled to that bound with a
+// block-uniform test.
+__device__ __forceinline__ uint32_t cta_block_sum(const unsigned long long* P, unsigned long long R, int B) {
+    const ulonglong2* P2 = reinterpret_cast<const ulonglong2*>(P);
+    uint32_t x = 0;
+#pragma unroll
+    for (int k = 0; k < 8; k += 2) {
+        if (k < B) {
+            const ulonglong2 v = P2[k >> 1];
+            x += (uint32_t)(__popcll(v.x & R) + (__popcll(v.y & R) << 1)) << k;
+        }
+    }
+    return x;
+}
+
 template <int W, int NW>
 struct CtaEngine {
     static constexpr int NT = 32 * NW;
@@ -559,7 +578,8 @@ struct CtaEngine {
             carry += (uint32_t)tot;
         }
         const int nblk = (int)(carry >> 16);
-        if (nblk * B > L->pln_cap) {
+        const int BP = (B + 1) & ~1;  // planes per block: B rounded up to even
+        if (nblk * BP > L->pln_cap) {
             abandon = 1;
             __syncthreads();
             return 0;
@@ -592,18 +612,18 @@ struct CtaEngine {
         for (int vv = warp; vv < ncols; vv += NW) {
             const int deg = (HE[vv] - HS[vv]) + LCT[vv];
             const int base = VB[vv];
-            unsigned long long* dst = PLN + (size_t)PB[vv] * B;
+            unsigned long long* dst = PLN + (size_t)PB[vv] * BP;
             int gs = 0;
             for (int x0 = 0; x0 < deg; x0 += 64) {
                 const int w0 = x0 + lane < deg ? AW[base + x0 + lane] : 0;
                 const int w1 = x0 + 32 + lane < deg ? AW[base + x0 + 32 + lane] : 0;
                 gs += w0 + w1;
-                for (int kk = 0; kk < B; kk++) {
+                for (int kk = 0; kk < BP; kk++) {  // plane B of an odd B is the zero padding
                     const uint32_t lo32 = __ballot_sync(FULL_MASK, (w0 >> kk) & 1);
                     const uint32_t hi32 = __ballot_sync(FULL_MASK, (w1 >> kk) & 1);
                     if (lane == kk) dst[kk] = (unsigned long long)hi32 << 32 | lo32;
                 }
-                dst += B;
+                dst += BP;
             }
             gs = __reduce_add_sync(FULL_MASK, gs);
             if (lane == 0) G[vv] = (uint32_t)gs;
@@ -635,24 +655,23 @@ struct CtaEngine {
             }
             const int ls1 = sib - HS[j];
             const int nint = (n0 - 1) + (n1 - 1 - (sib >= 0 ? 1 : 0));
-            long long X = 0;
-            int inter = 0, nb = 0;
+            int X = 0, inter = 0, nb = 0;
             if (nint > 0) {
                 const int nb0 = (n0 + 63) >> 6, nb1 = (n1 + 63) >> 6;
                 nb = nb0 > nb1 ? nb0 : nb1;
-                const unsigned long long* P0 = PLN + (size_t)PB[i] * B;
-                const unsigned long long* P1 = PLN + (size_t)PB[j] * B;
+                const unsigned long long* P0 = PLN + (size_t)PB[i] * BP;
+                const unsigned long long* P1 = PLN + (size_t)PB[j] * BP;
                 for (int blk = 0; blk < nb; blk++) {
                     uint32_t r0 = gproc, r1 = (uint32_t)t, r2 = c2g | (uint32_t)blk, r3 = key;
                     philox(r0, r1, r2, r3, k0, k1);
                     const unsigned long long R0 = (unsigned long long)r1 << 32 | r0;
                     const unsigned long long R1 = (unsigned long long)r3 << 32 | r2;
                     if (blk < nb0) {
-                        for (int kk = 0; kk < B; kk++) X += (long long)__popcll(P0[blk * B + kk] & R0) << kk;
+                        X += (int)cta_block_sum(P0 + blk * BP, R0, B);
                         if ((lp0 >> 6) == blk && ((R0 >> (lp0 & 63)) & 1ull)) X -= wp;
                     }
                     if (blk < nb1) {
-                        for (int kk = 0; kk < B; kk++) X += (long long)__popcll(P1[blk * B + kk] & R1) << kk;
+                        X += (int)cta_block_sum(P1 + blk * BP, R1, B);
                         if ((lp1 >> 6) == blk && ((R1 >> (lp1 & 63)) & 1ull)) X -= wp;
                         if (sib >= 0 && (ls1 >> 6) == blk && ((R1 >> (ls1 & 63)) & 1ull)) X -= wsib;
                     }
@@ -660,7 +679,7 @@ struct CtaEngine {
                 inter = (int)G[i] + (int)G[j] - 2 * wp - wsib;
             }
             const int D = T - wp - inter;
-            const long long sc = ((long long)wp << 32) + a * (((long long)D << 16) + b * X);
+            const long long sc = ((long long)wp << 32) + a * (((long long)D << 16) + b * (long long)X);
             if (sc > best_s) {
                 best_s = sc;
                 best_q = p;

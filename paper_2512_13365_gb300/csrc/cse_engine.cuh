@@ -400,12 +400,13 @@ struct Engine {
         __syncwarp();
         // recount the candidates containing x_i or x_j; stable in-place compaction
         int newm = 0, nij = 0;
+        uint32_t e_nx = lane < m ? C[lane] : 0u;  // the next chunk, one iteration ahead
         for (int base = 0; base < m; base += 32) {
             const int q = base + lane;
-            uint32_t e = 0;
+            uint32_t e = e_nx;
+            e_nx = q + 32 < m ? C[q + 32] : 0u;
             bool keep = false, touch = false;
             if (q < m) {
-                e = C[q];
                 const int lo = key_lo(e), hi = key_hi(e);
                 touch = lo == i || lo == j || hi == i || hi == j;
                 keep = true;
@@ -806,20 +807,33 @@ struct Engine {
         int part = 0, wmax = 1;
         for (int v = lane; v < ncols; v += 32) *reinterpret_cast<uint4*>(R + v) = make_uint4(0u, 0u, 0u, 0u);
         __syncwarp();
+        // Every pass over the list below reads the next chunk's entries one
+        // iteration ahead (the list lives in HBM: a chunk's work then waits
+        // on one fewer round trip); a chunk's neighbours come from the
+        // adjacent lanes, the previous chunk's last entry and the prefetch.
+        uint32_t e_nx = lane < m ? C[lane] : 0u;
+        int hi_last = -1;  // hi of the previous chunk's last entry
         for (int base = 0; base < m; base += 32) {
             const int q = base + lane;
             const bool valid = q < m;
             const uint32_t act = __ballot_sync(FULL_MASK, valid);
+            const uint32_t e = e_nx;
+            e_nx = q + 32 < m ? C[q + 32] : 0u;
+            const int hi = key_hi(e), lo = key_lo(e);
+            int hprev = __shfl_up_sync(FULL_MASK, hi, 1);
+            int hnext = __shfl_down_sync(FULL_MASK, hi, 1);
+            const int hfirst_nx = __shfl_sync(FULL_MASK, key_hi(e_nx), 0);
+            if (lane == 0) hprev = hi_last;
+            if (lane == 31) hnext = hfirst_nx;
             if (valid) {
-                const uint32_t e = C[q];
-                const int hi = key_hi(e), lo = key_lo(e);
                 part += cand_c(e) - 1;
                 wmax = max(wmax, cand_c(e) - 1);
-                if (q == 0 || key_hi(C[q - 1]) != hi) R[hi].hs = (uint16_t)q;
-                if (q == m - 1 || key_hi(C[q + 1]) != hi) R[hi].he = (uint16_t)(q + 1);
+                if (hprev != hi) R[hi].hs = (uint16_t)q;
+                if (q == m - 1 || hnext != hi) R[hi].he = (uint16_t)(q + 1);
                 const uint32_t peers = __match_any_sync(act, lo);
                 if ((peers & lt) == 0) R[lo].lc = (uint16_t)(R[lo].lc + __popc(peers));
             }
+            hi_last = __shfl_sync(FULL_MASK, hi, 31);
             __syncwarp();
         }
         const int T = __reduce_add_sync(FULL_MASK, part);
@@ -846,14 +860,16 @@ struct Engine {
         const int nplanes = (int)(run >> 16) * B;
         for (int x = lane; x < nplanes; x += 32) PLN[x] = 0ull;
         __syncwarp();
+        e_nx = lane < m ? C[lane] : 0u;
         for (int base = 0; base < m; base += 32) {
             const int q = base + lane;
             const bool valid = q < m;
             const uint32_t act = __ballot_sync(FULL_MASK, valid);
+            const uint32_t e = e_nx;
+            e_nx = q + 32 < m ? C[q + 32] : 0u;
             uint32_t peers = 0;
             int lo = 0;
             if (valid) {
-                const uint32_t e = C[q];
                 const int hi = key_hi(e);
                 lo = key_lo(e);
                 const uint32_t w = (uint32_t)(cand_c(e) - 1);
@@ -885,23 +901,36 @@ struct Engine {
         long long best_s = LLONG_MIN;
         int best_q = -1;
         unsigned gi_terms = 0, gi_blocks = 0;
+        e_nx = lane < m ? C[lane] : 0u;
+        int pl_nx = lane < m ? PL[lane] : 0;
+        uint32_t e_last = 0;  // the previous chunk's last entry
         for (int base = 0; base < m; base += 32) {
             const int p = base + lane;
+            const uint32_t e = e_nx;
+            const int plp = pl_nx;
+            e_nx = p + 32 < m ? C[p + 32] : 0u;
+            pl_nx = p + 32 < m ? PL[p + 32] : 0;
+            // the neighbours p - 1 and p + 1, for the sign twin
+            uint32_t e_up = __shfl_up_sync(FULL_MASK, e, 1);
+            uint32_t e_dn = __shfl_down_sync(FULL_MASK, e, 1);
+            const uint32_t e_first_nx = __shfl_sync(FULL_MASK, e_nx, 0);
+            if (lane == 0) e_up = e_last;
+            if (lane == 31) e_dn = e_first_nx;
+            e_last = __shfl_sync(FULL_MASK, e, 31);
             if (p < m) {
-                const uint32_t e = C[p];
                 const int i = key_lo(e), j = key_hi(e), wp = cand_c(e) - 1;
                 const uint32_t key = e & 0x1FFFFFu;
                 const VarRec ri = R[i], rj = R[j];
                 const int n0 = (ri.he - ri.hs) + ri.lct;
                 const int n1 = (rj.he - rj.hs) + rj.lct;
-                const int lp0 = PL[p] - ri.vb;  // p's place in A_i
-                const int lp1 = p - rj.hs;      // p's place in A_j
+                const int lp0 = plp - ri.vb;  // p's place in A_i
+                const int lp1 = p - rj.hs;    // p's place in A_j
                 // the sign twin (i, j, -s), if a candidate: the neighbour on the
-                // side its sign sorts to, read once
+                // side its sign sorts to
                 int sib = -1, wsib = 0;
                 {
                     const int nb_ = (e & 1u) ? p - 1 : p + 1;
-                    const uint32_t en = (nb_ >= 0 && nb_ < m) ? C[nb_] : 0u;
+                    const uint32_t en = (e & 1u) ? e_up : e_dn;
                     if (nb_ >= 0 && nb_ < m && (en & 0x1FFFFFu) == (key ^ 1u)) {
                         sib = nb_;
                         wsib = cand_c(en) - 1;
