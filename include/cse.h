@@ -106,6 +106,13 @@ typedef struct {
                               on the one-warp-per-process engine only,
                               instead of one process per CTA with its arrays
                               in shared memory; results are identical */
+#define CSE_FLAG_WIDE_WORDS 32u  /* every matrix runs on the kernel of the next
+                              power-of-two words per column (3 -> 4, 5..7 -> 8;
+                              the extra row bits are zero), where its process
+                              slice still fits the same memory path;
+                              results, op counts included, are identical.
+                              Without the flag a width cse_autotune chose for
+                              the matrix's class applies */
 
 /* Search options.  Fields that change results: share_interval,
  * share_permille, col_cap, patience_rounds and the flag
@@ -234,15 +241,24 @@ typedef struct {
     int32_t candidate_bound;   /* bucket (power of two) of the candidate bound */
     int32_t procs_per_cta;     /* chosen processes (warps) per CTA             */
     float trial_ms[4];         /* round-kernel time with 1..4 per CTA          */
+    int32_t kernel_words;      /* chosen kernel words per column: W, or the
+                                  next power of two when that was faster   */
+    float trial_ms_wide[4];    /* the round kernels of the matrices that share
+                                  the wider kernel, 1..4 per CTA (-1: W is a
+                                  power of two, no wider trial)             */
 } cse_tune_entry;
 
 /* Launch autotuner.  Runs the given searches (as in cse_search_batch) for
  * min(step_budget, trial_steps) steps with 1, 2, 3 and 4 processes per CTA,
  * times every class of matrices (equal words per column and memory path)
  * with CUDA events, and caches the fastest choice per class in this process;
- * later searches with opts->procs_per_cta == 0 use it.  Launch parameters
- * never change results.  Writes up to max_entries entries and the number of
- * classes into *n_entries.  Synchronous. */
+ * later searches with opts->procs_per_cta == 0 use it.  Classes whose words
+ * per column are not a power of two are also timed on the kernel of the next
+ * power of two (as CSE_FLAG_WIDE_WORDS does), and the wider kernel is cached
+ * for the class when its round kernels take less time than those of every
+ * class it would absorb; later searches (without the flag) use that width.
+ * Launch parameters never change results.  Writes up to max_entries entries
+ * and the number of classes into *n_entries.  Synchronous. */
 int cse_autotune(int32_t n_searches, const cse_scheme* const* schemes, const cse_strategy_mix* mixes,
                  const int32_t* n_processes, const uint64_t* seeds, const int64_t* step_budgets,
                  const cse_opts* opts, int32_t trial_steps, void* cuda_stream, cse_tune_entry* entries,

@@ -46,7 +46,8 @@ class ProcRecord(ctypes.Structure):
 class TuneEntry(ctypes.Structure):
     _fields_ = [("words_per_column", ctypes.c_int32), ("hbm_path", ctypes.c_int32),
                 ("candidate_bound", ctypes.c_int32), ("procs_per_cta", ctypes.c_int32),
-                ("trial_ms", ctypes.c_float * 4)]
+                ("trial_ms", ctypes.c_float * 4), ("kernel_words", ctypes.c_int32),
+                ("trial_ms_wide", ctypes.c_float * 4)]
 
 
 PROC_DTYPE = np.dtype([("best_cost", "<i8"), ("best_len", "<i4"), ("runs", "<i4"), ("best_hash", "<u8"),
@@ -74,6 +75,7 @@ FLAG_TRACE = 2
 FLAG_GI_SHARED_COINS = 4
 FLAG_WARP_ENGINE = 8
 FLAG_PERSISTENT = 16
+FLAG_WIDE_WORDS = 32
 
 
 def lib() -> ctypes.CDLL:
@@ -348,7 +350,7 @@ def make_mix(weights) -> Mix:
 def make_opts(interval: int = 32, permille: int = 400, cap: int = 128, procs_per_cta: int = 0,
               graph: bool = False, trace: bool = False, patience: int = 0, gi_shared: bool = False,
               warp_engine: bool = False, cta_list_cap: int = 0, cta_min_list: int = 0, persistent: bool = False,
-              max_spin: int = 0) -> Opts:
+              max_spin: int = 0, wide_words: bool = False) -> Opts:
     """interval 0 selects iteration mode (budget = maximum iterations, stop
     after `patience` iterations without improvement).  warp_engine and
     cta_list_cap choose how large matrices are launched; never results."""
@@ -358,7 +360,7 @@ def make_opts(interval: int = 32, permille: int = 400, cap: int = 128, procs_per
     o.patience_rounds = patience
     o.flags = ((FLAG_GRAPH if graph else 0) | (FLAG_TRACE if trace else 0) |
                (FLAG_GI_SHARED_COINS if gi_shared else 0) | (FLAG_WARP_ENGINE if warp_engine else 0) |
-               (FLAG_PERSISTENT if persistent else 0))
+               (FLAG_PERSISTENT if persistent else 0) | (FLAG_WIDE_WORDS if wide_words else 0))
     o.max_spin = max_spin
     o.cta_list_cap = cta_list_cap
     o.cta_min_list = cta_min_list
@@ -398,11 +400,11 @@ class Options:
 def search(scheme: Scheme, weights, n_proc: int, seed: int, budget: int, interval: int = 32,
            permille: int = 400, cap: int = 128, stream=None, procs_per_cta: int = 0, graph: bool = False,
            trace: bool = False, patience: int = 0, gi_shared: bool = False, warp_engine: bool = False,
-           cta_list_cap: int = 0, cta_min_list: int = 0) -> Result:
+           cta_list_cap: int = 0, cta_min_list: int = 0, wide_words: bool = False) -> Result:
     """cse_search: enqueue the search and return its Result handle."""
     mix = make_mix(weights)
     opts = make_opts(interval, permille, cap, procs_per_cta, graph, trace, patience, gi_shared, warp_engine,
-                     cta_list_cap, cta_min_list)
+                     cta_list_cap, cta_min_list, wide_words=wide_words)
     h = ctypes.c_void_p()
     _check(lib().cse_search(scheme.handle, ctypes.byref(mix), n_proc, seed, budget, ctypes.byref(opts),
                             _stream_ptr(stream), ctypes.byref(h)))
@@ -438,7 +440,7 @@ def search_batch(schemes: Sequence[Scheme], weights: Sequence, n_procs: Sequence
                  budgets: Sequence[int], interval: int = 32, permille: int = 400, cap: int = 128, stream=None,
                  procs_per_cta: int = 0, graph: bool = True, trace: bool = False,
                  patience: int = 0, gi_shared: bool = False, persistent: bool = False,
-                 max_spin: int = 0) -> List[Result]:
+                 max_spin: int = 0, wide_words: bool = False) -> List[Result]:
     """cse_search_batch: independent searches in one launch sequence (with
     persistent, one cooperative kernel over every round)."""
     n = len(schemes)
@@ -448,7 +450,7 @@ def search_batch(schemes: Sequence[Scheme], weights: Sequence, n_procs: Sequence
     sd = (ctypes.c_uint64 * n)(*seeds)
     bd = (ctypes.c_int64 * n)(*budgets)
     opts = make_opts(interval, permille, cap, procs_per_cta, graph, trace, patience, gi_shared,
-                     persistent=persistent, max_spin=max_spin)
+                     persistent=persistent, max_spin=max_spin, wide_words=wide_words)
     outs = (ctypes.c_void_p * n)()
     _check(lib().cse_search_batch(n, hs, mixes, np_, sd, bd, ctypes.byref(opts), _stream_ptr(stream), outs))
     res = []
@@ -478,13 +480,15 @@ def _batch_args(schemes, weights, n_procs, seeds, budgets, interval, permille, c
 
 def autotune(schemes, weights, n_procs, seeds, budgets, interval=32, permille=400, cap=128, trial_steps=64,
              stream=None) -> List[dict]:
-    """cse_autotune: time 1..4 processes per CTA per matrix class; cache the fastest."""
+    """cse_autotune: time 1..4 processes per CTA per matrix class (and the
+    next power-of-two words per column); cache the fastest."""
     args = _batch_args(schemes, weights, n_procs, seeds, budgets, interval, permille, cap)
     ent = (TuneEntry * 64)()
     ne = ctypes.c_int32()
     _check(lib().cse_autotune(*args, trial_steps, _stream_ptr(stream), ent, 64, ctypes.byref(ne)))
     return [{"words_per_column": e.words_per_column, "hbm_path": e.hbm_path, "candidate_bound": e.candidate_bound,
-             "procs_per_cta": e.procs_per_cta, "trial_ms": list(e.trial_ms)} for e in ent[:ne.value]]
+             "procs_per_cta": e.procs_per_cta, "trial_ms": list(e.trial_ms), "kernel_words": e.kernel_words,
+             "trial_ms_wide": list(e.trial_ms_wide)} for e in ent[:ne.value]]
 
 
 def tune_interval(schemes, weights, n_procs, seeds, budgets, candidates=(16, 32, 64), permille=400, cap=128,

@@ -96,6 +96,9 @@ std::mutex g_tune_mu;
 constexpr size_t kServerMaxPending = 1 << 16;
 constexpr int64_t kServerWaves = 64;  // default cap on active processes, in waves of resident warps
 std::map<ClassKey, int> g_tuned_ppc;
+// kernel words per column chosen by cse_autotune for a class (keyed by the
+// matrices' own words per column)
+std::map<ClassKey, int> g_tuned_words;
 
 int mbucket(int mmax) {
     int b = 1;
@@ -103,9 +106,20 @@ int mbucket(int mmax) {
     return b;
 }
 
+// The next power of two of a word count: the wider kernel a matrix may run on.
+int widen_words(int W) {
+    int w = 1;
+    while (w < W) w <<= 1;
+    return w;
+}
+
+// How search_plan picks a matrix's kernel words per column.
+enum WordsPolicy { kWordsDefault = 0, kWordsNatural = 1, kWordsWide = 2 };
+
 // Trial-run controls used by the tuner.
 struct Trial {
     int force_ppc = 0;                     // processes per CTA for every class
+    int words = kWordsNatural;             // kernel words of every matrix
     std::vector<float>* group_ms = nullptr;   // out: round-kernel time per class
     std::vector<ClassKey>* keys = nullptr;    // out: class keys, same order
 };
@@ -129,6 +143,7 @@ struct SearchDev {
     std::vector<char> gm;       // matrix k runs on its HBM state region
     DevSearch search{};
     int rows[CSE_MAX_MATS], cols[CSE_MAX_MATS];
+    int words[CSE_MAX_MATS];    // kernel words per column of matrix k (>= its own)
     // the parameters it was created with (checkpoints record them)
     cse_strategy_mix mix{};
     cse_opts opts{};
@@ -147,9 +162,10 @@ struct CkptHeader {
     int64_t done;     // steps (iterations in iteration mode) already run
     uint64_t bytes;   // size of the device block that follows
     uint64_t input_hash;  // the scheme's cse_scheme::input_hash
+    int32_t words[CSE_MAX_MATS];  // kernel words per column (the state layout)
 };
 constexpr uint64_t kCkptMagic = 0x3154504B43455343ull;  // "CSECKPT1" as little-endian bytes
-constexpr uint32_t kCkptVersion = 2;
+constexpr uint32_t kCkptVersion = 3;
 
 // Resume of one search from a checkpoint (run_batch).
 struct Resume {
@@ -257,7 +273,7 @@ static int check_opts(const cse_opts* opts_in, cse_opts* opts) {
         cse_opts_default(opts);
     if (opts->share_permille > 1000) return fail(CSE_EINVAL, "share_permille must be <= 1000");
     if ((opts->flags & ~(uint32_t)(CSE_FLAG_GRAPH | CSE_FLAG_TRACE | CSE_FLAG_GI_SHARED_COINS |
-                                   CSE_FLAG_WARP_ENGINE | CSE_FLAG_PERSISTENT)) != 0)
+                                   CSE_FLAG_WARP_ENGINE | CSE_FLAG_PERSISTENT | CSE_FLAG_WIDE_WORDS)) != 0)
         return fail(CSE_EINVAL, "reserved option fields must be 0");
     if (opts->share_interval != 0 && opts->patience_rounds != 0)
         return fail(CSE_EINVAL, "patience_rounds applies to iteration mode (share_interval = 0) only");
@@ -270,8 +286,33 @@ static int check_opts(const cse_opts* opts_in, cse_opts* opts) {
 }
 
 // Validates one search and computes its layout and device footprint.
+// Offsets of a search's device block: kOffsPerMat per matrix, then the
+// search's clock, status and convergence state.
+constexpr int kOffsPerMat = 11;
+
+// Kernel words per column of matrix k: forced (a resumed checkpoint's), the
+// matrix's own, the next power of two (CSE_FLAG_WIDE_WORDS or a wide trial),
+// or the width cse_autotune cached for its class.  A wider shared-memory
+// slice that would no longer fit its memory path keeps the matrix's own.
+static int kernel_words(const cse_scheme* s, int k, bool gm, int cap, const cse_opts& opts, int policy,
+                        const int32_t* forced) {
+    const int own = s->W[k];
+    if (forced) return forced[k];
+    int w = own;
+    if (policy == kWordsWide || (policy == kWordsDefault && (opts.flags & CSE_FLAG_WIDE_WORDS))) {
+        w = widen_words(own);
+    } else if (policy == kWordsDefault) {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tuned_words.find(ClassKey{own, gm ? 1 : 0, cap, 0});
+        if (it != g_tuned_words.end()) w = it->second;
+    }
+    if (w != own && !gm && make_layout(w, cap, s->mmax[k]).per_warp > kSmemPerWarpLimit) w = own;
+    return w;
+}
+
 static int search_plan(const cse_scheme* s, const cse_strategy_mix* mix, int n_proc, int64_t budget,
-                       const cse_opts& opts, SearchDev* sd, uint64_t* wsum, std::vector<size_t>* offs) {
+                       const cse_opts& opts, SearchDev* sd, uint64_t* wsum, std::vector<size_t>* offs,
+                       int words_policy = kWordsDefault, const int32_t* forced_words = nullptr) {
     if (!s) return fail(CSE_EINVAL, "NULL scheme");
     int rc = check_mix(mix, wsum);
     if (rc) return rc;
@@ -295,12 +336,14 @@ static int search_plan(const cse_scheme* s, const cse_strategy_mix* mix, int n_p
     for (int k = 0; k < s->n_mats; k++) {
         sd->rows[k] = s->rows[k];
         sd->cols[k] = s->cols[k];
-        const WarpLayout own = make_layout(s->W[k], cap, s->mmax[k]);
-        const bool gm = own.per_warp > kSmemPerWarpLimit;
+        const bool gm = make_layout(s->W[k], cap, s->mmax[k]).per_warp > kSmemPerWarpLimit;
+        const int Wk = kernel_words(s, k, gm, cap, opts, words_policy, forced_words);
+        if (Wk < s->W[k] || Wk > 8) return fail(CSE_EINVAL, "kernel words per column must be in [W, 8]");
         sd->gm[k] = gm;
+        sd->words[k] = Wk;
         DevMat& M = sd->mats[k];
-        M.gml = gm ? make_layout(s->W[k], cap, s->mmax[k], true) : own;
-        M.state_words = gm ? state_words_gm(M.gml) : state_words(s->W[k], cap, s->mmax[k]);
+        M.gml = make_layout(Wk, cap, s->mmax[k], gm);
+        M.state_words = gm ? state_words_gm(M.gml) : state_words(Wk, cap, s->mmax[k]);
         offs->push_back(cv.take((size_t)n_proc * M.state_words * 4));   // state
         offs->push_back(cv.take((size_t)n_proc * cap * 4));             // best lists
         offs->push_back(cv.take((size_t)cap * 4));                      // snapshot
@@ -311,6 +354,7 @@ static int search_plan(const cse_scheme* s, const cse_strategy_mix* mix, int n_p
         offs->push_back(cv.take(64));                                   // counters
         offs->push_back(cv.take((size_t)kCurvePoints * 4));             // best-Cost curve
         offs->push_back(cv.take((size_t)(cap + 1) * 4));                // a shard's external winner list
+        offs->push_back(cv.take(Wk != s->W[k] ? (size_t)s->cols[k] * Wk * 8 : 0));  // columns at Wk words
     }
     offs->push_back(cv.take(4));   // clock
     offs->push_back(cv.take(4));   // status
@@ -321,13 +365,14 @@ static int search_plan(const cse_scheme* s, const cse_strategy_mix* mix, int n_p
 
 // Allocates and initialises one search on `stream` (stream-ordered).
 static int search_create(const cse_scheme* s, const cse_strategy_mix* mix, int n_proc, uint64_t seed,
-                         int64_t budget, const cse_opts& opts, cudaStream_t stream, SearchDev** out) {
+                         int64_t budget, const cse_opts& opts, cudaStream_t stream, SearchDev** out,
+                         int words_policy = kWordsDefault, const int32_t* forced_words = nullptr) {
     *out = nullptr;
     SearchDev* sd = new (std::nothrow) SearchDev();
     if (!sd) return fail(CSE_ENOMEM, "host allocation");
     uint64_t wsum = 0;
     std::vector<size_t> of;
-    int rc = search_plan(s, mix, n_proc, budget, opts, sd, &wsum, &of);
+    int rc = search_plan(s, mix, n_proc, budget, opts, sd, &wsum, &of, words_policy, forced_words);
     if (rc) {
         delete sd;
         return rc;
@@ -360,22 +405,23 @@ static int search_create(const cse_scheme* s, const cse_strategy_mix* mix, int n
     S.interval = (int32_t)opts.share_interval;
     S.patience = (int32_t)opts.patience_rounds;
     S.share_thr = ((uint64_t)opts.share_permille << 32) / 1000u;
-    S.clock = (int32_t*)(b + of[10 * s->n_mats]);
-    S.status = (int32_t*)(b + of[10 * s->n_mats + 1]);
-    S.conv = (int32_t*)(b + of[10 * s->n_mats + 2]);
+    S.clock = (int32_t*)(b + of[kOffsPerMat * s->n_mats]);
+    S.status = (int32_t*)(b + of[kOffsPerMat * s->n_mats + 1]);
+    S.conv = (int32_t*)(b + of[kOffsPerMat * s->n_mats + 2]);
     S.n_mats = s->n_mats;
     S.trace = (opts.flags & CSE_FLAG_TRACE) ? 1 : 0;
     S.gi_shared = (opts.flags & CSE_FLAG_GI_SHARED_COINS) ? 1 : 0;
     static const int32_t snap_init[2] = {INT_MAX, 0};
     for (int k = 0; k < s->n_mats; k++) {
         DevMat& M = sd->mats[k];
-        const size_t* o = &of[10 * k];
+        const size_t* o = &of[kOffsPerMat * k];
         M.pn0 = s->d_pn0[k];
         M.cand0 = s->d_cand0[k];
         M.meta0 = s->d_meta0[k];
         M.rows = s->rows[k];
         M.nx = s->cols[k];
-        M.W = s->W[k];
+        M.W = sd->words[k];
+        M.wn = s->W[k];
         M.cap = sd->cap;
         M.mmax = s->mmax[k];
         M.mat_index = k;
@@ -392,6 +438,14 @@ static int search_create(const cse_scheme* s, const cse_strategy_mix* mix, int n
         M.proc_offset = 0;
         M.ext_list = (const int32_t*)(b + o[9]);
         M.ext_len = (const int32_t*)(b + o[9]) + sd->cap;
+        if (M.W != M.wn) {  // a wider kernel: the columns again at M.W words, the extra row bits zero
+            uint2* wide = (uint2*)(b + o[10]);
+            M.pn0 = wide;
+            if (e == cudaSuccess) e = cudaMemsetAsync(wide, 0, (size_t)M.nx * M.W * 8, stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpy2DAsync(wide, (size_t)M.W * 8, s->d_pn0[k], (size_t)M.wn * 8, (size_t)M.wn * 8, M.nx,
+                                      cudaMemcpyDeviceToDevice, stream);
+        }
         // initial values: no round minimum, no snapshot, result = the input
         if (e == cudaSuccess) e = cudaMemsetAsync(M.round_min, 0xFF, 8, stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(M.snap_meta, snap_init, 8, cudaMemcpyHostToDevice, stream);
@@ -560,11 +614,14 @@ static int run_batch(int n, const cse_scheme* const* schemes, const cse_strategy
     if (rc) return rc;
     const bool iter_mode = opts.share_interval == 0;
     if (iter_mode && trial) return fail(CSE_EINVAL, "launch tuning runs in step-clock mode (share_interval >= 1)");
+    const int words_policy = trial ? trial->words : kWordsDefault;
+    const int32_t* forced_words = resume ? resume->hdr->words : nullptr;  // the checkpoint's state layout
     for (int i = 0; i < n; i++) {  // validate everything before allocating
         SearchDev tmp;
         uint64_t w;
         std::vector<size_t> of;
-        rc = search_plan(schemes[i], &mixes[i], n_procs[i], budgets[i], opts, &tmp, &w, &of);
+        rc = search_plan(schemes[i], &mixes[i], n_procs[i], budgets[i], opts, &tmp, &w, &of, words_policy,
+                         forced_words);
         if (rc) return rc;
     }
     if (max_smem_per_block() <= 0) return fail(CSE_ECUDA, "no CUDA device");
@@ -575,7 +632,8 @@ static int run_batch(int n, const cse_scheme* const* schemes, const cse_strategy
         for (auto* sd : sds) search_free(sd);
     };
     for (int i = 0; i < n; i++) {
-        rc = search_create(schemes[i], &mixes[i], n_procs[i], seeds[i], budgets[i], opts, stream, &sds[i]);
+        rc = search_create(schemes[i], &mixes[i], n_procs[i], seeds[i], budgets[i], opts, stream, &sds[i],
+                           words_policy, forced_words);
         if (rc) {
             drop();
             return rc;
@@ -1076,6 +1134,7 @@ int cse_checkpoint_save(const cse_result* r, void* host_buf, size_t bytes) {
     for (int k = 0; k < sd->n_mats; k++) {
         h.rows[k] = sd->rows[k];
         h.cols[k] = sd->cols[k];
+        h.words[k] = sd->words[k];
     }
     h.seed = sd->seed;
     h.mix = sd->mix;
@@ -1111,7 +1170,8 @@ int cse_search_resume(const cse_scheme* s, const void* ckpt, size_t bytes, int64
     opts.patience_rounds = h.patience;
     // the coin mode changes results and the trace flag the trajectory record:
     // both are the checkpoint's
-    opts.flags = (opts.flags & ~(uint32_t)(CSE_FLAG_GI_SHARED_COINS | CSE_FLAG_GRAPH | CSE_FLAG_TRACE)) | h.flags;    const int64_t total = h.done + more_steps;
+    opts.flags = (opts.flags & ~(uint32_t)(CSE_FLAG_GI_SHARED_COINS | CSE_FLAG_GRAPH | CSE_FLAG_TRACE)) | h.flags;
+    const int64_t total = h.done + more_steps;
     const int32_t n_proc = h.n_proc;
     const uint64_t seed = h.seed;
     Resume res{&h, (const char*)ckpt + sizeof h};
@@ -1128,42 +1188,96 @@ int cse_autotune(int32_t n_searches, const cse_scheme* const* schemes, const cse
                  const int32_t* n_processes, const uint64_t* seeds, const int64_t* step_budgets,
                  const cse_opts* opts, int32_t trial_steps, void* cuda_stream, cse_tune_entry* entries,
                  int32_t max_entries, int32_t* n_entries) {
-    if (n_searches < 1 || n_searches > 4096 || !step_budgets) return fail(CSE_EINVAL, "bad n_searches");
+    if (n_searches < 1 || n_searches > 4096 || !step_budgets || !schemes) return fail(CSE_EINVAL, "bad n_searches");
     if (trial_steps < 1) return fail(CSE_EINVAL, "trial_steps must be >= 1");
     std::vector<int64_t> tb(n_searches);
     for (int i = 0; i < n_searches; i++) tb[i] = std::min<int64_t>(step_budgets[i], trial_steps);
-    std::vector<std::vector<float>> ms(4);
-    std::vector<ClassKey> keys;
     std::vector<cse_result*> outs(n_searches);
-    for (int ppc = 1; ppc <= 4; ppc++) {
-        for (int rep = 0; rep < 2; rep++) {  // the first run warms up
-            Trial tr;
-            tr.force_ppc = ppc;
-            std::vector<ClassKey> k;
-            tr.keys = &k;
-            int rc = run_batch(n_searches, schemes, mixes, n_processes, seeds, tb.data(), opts, cuda_stream,
-                               outs.data(), &tr);
-            if (rc) return rc;
-            rc = trial_times(outs[0], &ms[ppc - 1]);
-            for (auto* r : outs) cse_result_free(r);
-            if (rc) return rc;
-            keys = k;
+    // trial rounds with 1..4 processes per CTA, at each matrix's own words and,
+    // if some matrix's words are not a power of two, at the wider kernel
+    bool any_wide = false;
+    for (int i = 0; i < n_searches; i++)
+        for (int k = 0; schemes[i] && k < schemes[i]->n_mats; k++) any_wide |= widen_words(schemes[i]->W[k]) != schemes[i]->W[k];
+    std::vector<std::vector<float>> ms[2] = {std::vector<std::vector<float>>(4), std::vector<std::vector<float>>(4)};
+    std::vector<ClassKey> keys[2];
+    for (int pol = 0; pol < (any_wide ? 2 : 1); pol++) {
+        for (int ppc = 1; ppc <= 4; ppc++) {
+            for (int rep = 0; rep < 2; rep++) {  // the first run warms up
+                Trial tr;
+                tr.force_ppc = ppc;
+                tr.words = pol == 0 ? kWordsNatural : kWordsWide;
+                std::vector<ClassKey> k;
+                tr.keys = &k;
+                int rc = run_batch(n_searches, schemes, mixes, n_processes, seeds, tb.data(), opts, cuda_stream,
+                                   outs.data(), &tr);
+                if (rc) return rc;
+                rc = trial_times(outs[0], &ms[pol][ppc - 1]);
+                for (auto* r : outs) cse_result_free(r);
+                if (rc) return rc;
+                keys[pol] = k;
+            }
         }
     }
-    std::lock_guard<std::mutex> lk(g_tune_mu);
-    int32_t ne = 0;
-    for (size_t gi = 0; gi < keys.size(); gi++) {
+    auto best_ppc = [&](int pol, size_t gi) {
         int best = 1;
         for (int ppc = 2; ppc <= 4; ppc++)
-            if (ms[ppc - 1][gi] < ms[best - 1][gi]) best = ppc;
-        g_tuned_ppc[keys[gi]] = best;
+            if (ms[pol][ppc - 1][gi] < ms[pol][best - 1][gi]) best = ppc;
+        return best;
+    };
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    std::vector<int> chosen_words(keys[0].size()), chosen_ppc(keys[0].size());
+    std::vector<int> wide_of(keys[0].size(), -1);  // the wide trial's group holding class gi
+    for (size_t gi = 0; gi < keys[0].size(); gi++) {
+        chosen_words[gi] = keys[0][gi].W;
+        chosen_ppc[gi] = best_ppc(0, gi);
+        g_tuned_ppc[keys[0][gi]] = chosen_ppc[gi];
+    }
+    // a wider kernel is kept for the classes it absorbs when its round kernels
+    // take less time than theirs, each class at its best processes per CTA
+    for (size_t wj = 0; wj < keys[1].size(); wj++) {
+        const ClassKey& K = keys[1][wj];
+        float t_own = 0.f;
+        bool widened = false;
+        std::vector<size_t> members;
+        for (size_t gi = 0; gi < keys[0].size(); gi++) {
+            const ClassKey& k = keys[0][gi];
+            if (k.gm != K.gm || k.cap != K.cap || (k.W != K.W && widen_words(k.W) != K.W)) continue;
+            members.push_back(gi);
+            widened |= k.W < K.W;
+            t_own += ms[0][chosen_ppc[gi] - 1][gi];
+        }
+        if (!widened) continue;
+        const int wppc = best_ppc(1, wj);
+        const bool take = ms[1][wppc - 1][wj] < t_own;
+        for (size_t gi : members) {
+            wide_of[gi] = (int)wj;
+            const ClassKey own{keys[0][gi].W, keys[0][gi].gm, keys[0][gi].cap, 0};
+            if (keys[0][gi].W == K.W) continue;
+            if (take) {
+                g_tuned_words[own] = K.W;
+                chosen_words[gi] = K.W;
+                chosen_ppc[gi] = wppc;
+            } else {
+                g_tuned_words.erase(own);
+            }
+        }
+        if (take) g_tuned_ppc[K] = wppc;
+    }
+    int32_t ne = 0;
+    for (size_t gi = 0; gi < keys[0].size(); gi++) {
         if (entries && ne < max_entries) {
             cse_tune_entry& en = entries[ne];
-            en.words_per_column = keys[gi].W;
-            en.hbm_path = keys[gi].gm;
-            en.candidate_bound = keys[gi].mbucket;
-            en.procs_per_cta = best;
-            for (int ppc = 1; ppc <= 4; ppc++) en.trial_ms[ppc - 1] = ms[ppc - 1][gi];
+            en.words_per_column = keys[0][gi].W;
+            en.hbm_path = keys[0][gi].gm;
+            en.candidate_bound = keys[0][gi].mbucket;
+            en.procs_per_cta = chosen_ppc[gi];
+            en.kernel_words = chosen_words[gi];
+            for (int ppc = 1; ppc <= 4; ppc++) {
+                en.trial_ms[ppc - 1] = ms[0][ppc - 1][gi];
+                en.trial_ms_wide[ppc - 1] = wide_of[gi] >= 0 && keys[0][gi].W != keys[1][wide_of[gi]].W
+                                                ? ms[1][ppc - 1][wide_of[gi]]
+                                                : -1.f;
+            }
         }
         ne++;
     }

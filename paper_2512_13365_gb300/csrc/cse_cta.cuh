@@ -748,8 +748,8 @@ struct CtaEngine {
                 best_q = p;
             }
             const int live = nlive - (nni == c) - (nnj == c);
-            ops += 5u * (unsigned)W * (unsigned)live + 8u;
-            mops += 6u * (unsigned)((W + 1) >> 1) + (unsigned)rnnz;
+            ops += 5u * (unsigned)M->wn * (unsigned)live + 8u;  // the matrix's own words
+            mops += 6u * (unsigned)((M->wn + 1) >> 1) + (unsigned)rnnz;
         }
         ops = __reduce_add_sync(FULL_MASK, ops);
         mops = __reduce_add_sync(FULL_MASK, mops);
@@ -931,11 +931,11 @@ __device__ bool cta_run_unit(const DevMat* __restrict__ mats, int n_mats, const 
     E.fold();
 
     if (tid == 0) {
-        const long long dops = 10LL * M->W * cd->t_sub + 5LL * M->W * cd->t_pairs + 2LL * cd->t_scan +
+        const long long dops = 10LL * M->wn * cd->t_sub + 5LL * M->wn * cd->t_pairs + 2LL * cd->t_scan +
                                3LL * cd->t_gi_terms + 40LL * cd->t_gi_blocks + 8LL * cd->t_gi_cands +
                                (long long)cd->t_rare;
         const unsigned long long ops = cd->ops + (unsigned long long)dops;
-        const long long dmops = 6LL * ((M->W + 1) >> 1) * cd->t_sub + (long long)cd->t_nnz + cd->t_scan +
+        const long long dmops = 6LL * ((M->wn + 1) >> 1) * cd->t_sub + (long long)cd->t_nnz + cd->t_scan +
                                 (long long)cd->t_gi_cands + 2LL * cd->t_gi_terms + (long long)cd->t_mrare;
         const unsigned long long mops = cd->mops + (unsigned long long)dmops;
         atomicMin(M->round_min, (unsigned long long)(uint32_t)cd->best_cost << 32 | E.gproc);

@@ -131,7 +131,7 @@ static __device__ __noinline__ uint4 philox_call(uint32_t c0, uint32_t c1, uint3
 // step engine runs 7% faster than with this function inlined.
 template <int W>
 __device__ __noinline__ int gp_select(const uint2* P, const uint32_t* C, int ncols, int m, uint32_t a, int lane,
-                                      unsigned long long* ops_total, unsigned long long* mops_total) {
+                                      int wn, unsigned long long* ops_total, unsigned long long* mops_total) {
     int nlive = 0;
     for (int base = 0; base < ncols; base += 32) {
         const int u = base + lane;
@@ -181,8 +181,8 @@ __device__ __noinline__ int gp_select(const uint2* P, const uint32_t* C, int nco
                 best_q = p;
             }
             const int live = nlive - (nni == c) - (nnj == c);
-            ops += 5u * (unsigned)W * (unsigned)live + 8u;
-            mops += 6u * (unsigned)((W + 1) >> 1) + (unsigned)rnnz;
+            ops += 5u * (unsigned)wn * (unsigned)live + 8u;  // the matrix's own words (wn <= W)
+            mops += 6u * (unsigned)((wn + 1) >> 1) + (unsigned)rnnz;
         }
     }
     const uint32_t top = __reduce_max_sync(FULL_MASK, best_q == INT_MAX ? 0u : best_s);
@@ -290,9 +290,9 @@ __device__ __forceinline__ int gi_shared_select(const uint32_t* C, uint32_t* G, 
 template <int W>
 __device__ __noinline__ int rare_select(int kind, const uint2* P, const uint32_t* C, uint32_t* G, uint32_t* XS,
                                         int ncols, int m, int lane, uint32_t proc, uint32_t t, uint32_t c2s,
-                                        uint64_t seed, long long a, long long b, unsigned long long* tally,
+                                        uint64_t seed, long long a, long long b, int wn, unsigned long long* tally,
                                         unsigned long long* mtally) {
-    if (kind == 0) return gp_select<W>(P, C, ncols, m, (uint32_t)a, lane, tally, mtally);
+    if (kind == 0) return gp_select<W>(P, C, ncols, m, (uint32_t)a, lane, wn, tally, mtally);
     return gi_shared_select(C, G, XS, ncols, m, lane, proc, t, c2s, seed, a, b, tally, mtally);
 }
 
@@ -988,7 +988,8 @@ struct Engine {
     __device__ int sel_rare(int kind, int t) {
         return rare_select<W>(kind, pn(), cand(), reinterpret_cast<uint32_t*>(hs()),
                               reinterpret_cast<uint32_t*>(vbase()), ncols, m, lane, gproc, (uint32_t)t,
-                              c2(PU_GIS, 0), S->seed, cold()->a, cold()->b, &cold()->t_rare, &cold()->t_mrare);
+                              c2(PU_GIS, 0), S->seed, cold()->a, cold()->b, M->wn, &cold()->t_rare,
+                              &cold()->t_mrare);
     }
 
     __device__ int choose(int t) {
@@ -1011,7 +1012,7 @@ struct Engine {
             if constexpr (GS)
                 return sel_rare(0, t);
             else
-                return gp_select<W>(pn(), cand(), ncols, m, (uint32_t)cold()->a, lane, &cold()->t_rare,
+                return gp_select<W>(pn(), cand(), ncols, m, (uint32_t)cold()->a, lane, M->wn, &cold()->t_rare,
                                     &cold()->t_mrare);
         }
         if (lane == 0) cold()->t_scan += (unsigned)m;
@@ -1175,14 +1176,14 @@ __device__ __forceinline__ void run_unit(const DevMat* __restrict__ mats, int n_
         // algorithmic ops of the round: 10 W per rewrite, 5 W per pair count
         // that can change, 2 per candidate scanned, and per gi candidate 3 per
         // intersecting term + 8 + 40 per Philox block; the gp trials
-        const long long dops = 10LL * M->W * cd->t_sub + 5LL * M->W * cd->t_pairs + 2LL * cd->t_scan +
+        const long long dops = 10LL * M->wn * cd->t_sub + 5LL * M->wn * cd->t_pairs + 2LL * cd->t_scan +
                                3LL * cd->t_gi_terms + 40LL * cd->t_gi_blocks + 8LL * cd->t_gi_cands +
                                (long long)cd->t_rare;
         const unsigned long long ops = cd->ops + (unsigned long long)dops;
         // method ops of the round: 6 per 64-bit word and the nnz of the
         // rewritten rows per rewrite, m per selection, 2 per gi intersect
         // term; the gp trials and shared-coin gi
-        const long long dmops = 6LL * ((M->W + 1) >> 1) * cd->t_sub + (long long)cd->t_nnz + cd->t_scan +
+        const long long dmops = 6LL * ((M->wn + 1) >> 1) * cd->t_sub + (long long)cd->t_nnz + cd->t_scan +
                                 (long long)cd->t_gi_cands + 2LL * cd->t_gi_terms + (long long)cd->t_mrare;
         const unsigned long long mops = cd->mops + (unsigned long long)dmops;
         uint32_t* st = M->state + (size_t)E.proc * M->state_words;

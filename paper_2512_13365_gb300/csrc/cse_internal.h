@@ -67,7 +67,9 @@ struct DevMat {
     const uint2* pn0;        // original columns [nx][W]: x = rows with +1, y = rows with -1
     const uint32_t* cand0;   // initial candidate list, canonical order
     const int32_t* meta0;    // [0] A_naive of the input, [1] initial candidate count
-    int32_t rows, nx, W, cap, mmax;
+    int32_t rows, nx, W, cap, mmax;  // W: words per column of the kernel (>= wn)
+    int32_t wn;              // words per column of the matrix itself, ceil(rows / 32): the
+                             // op counts use it, so a wider kernel counts the same ops
     int32_t mat_index;       // index of the matrix within its search (Philox counter)
     int32_t n_proc;
     int32_t search;          // index into the DevSearch array

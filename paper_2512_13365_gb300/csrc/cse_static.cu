@@ -158,6 +158,7 @@ extern "C" int cse_search_static(const cse_scheme* s, const cse_strategy_mix* mi
         M.rows = s->rows[k];
         M.nx = s->cols[k];
         M.W = s->W[k];
+        M.wn = s->W[k];
         M.cap = cap;
         M.mmax = s->mmax[k];
         M.mat_index = k;

@@ -24,8 +24,8 @@ def cse():
     return c
 
 
-def assert_parity(cse, s, ref=None, procs_per_cta=0, check_procs=True, gi_shared=False):
-    r = cse.search_obj(s, procs_per_cta=procs_per_cta, trace=True, gi_shared=gi_shared)
+def assert_parity(cse, s, ref=None, procs_per_cta=0, check_procs=True, gi_shared=False, **kw):
+    r = cse.search_obj(s, procs_per_cta=procs_per_cta, trace=True, gi_shared=gi_shared, **kw)
     if ref is None:
         ref = O.search_obj(s, n_threads=8, flags=O.GI_SHARED_COINS if gi_shared else 0)
     assert r.costs == ref.cost
@@ -127,6 +127,25 @@ def test_word_widths(cse, rows):
             synth.random_matrix(rows + 1, 12, min(rows, 40), 2, 5, n_planted=3)]
     s = synth.Search(f"w{rows}", mats, synth.PAPER_WEIGHTS, 37, 11, 70, 16, 400, 128)
     assert_parity(cse, s)
+
+
+@pytest.mark.parametrize("rows", [70, 100, 130, 161, 200])
+def test_wide_words_equal_the_oracle(cse, rows):
+    """CSE_FLAG_WIDE_WORDS runs matrices of 3, 5, 6 and 7 words per column
+    on the 4- and 8-word kernels (zero row bits above the matrix's own): every
+    result, op counts included, stays the oracle's."""
+    mats = [synth.random_matrix(rows, rows, 10, 2, 6, n_planted=5),
+            synth.random_matrix(rows + 1, 12, min(rows, 40), 2, 5, n_planted=3)]
+    s = synth.Search(f"wide{rows}", mats, synth.PAPER_WEIGHTS, 37, 11, 70, 16, 400, 128)
+    assert_parity(cse, s, wide_words=True)
+
+
+def test_wide_words_from_hbm(cse):
+    """The (6,6,6:153) shape's 5-word matrices on the 8-word HBM-path and
+    process-per-CTA kernels."""
+    s = synth.config4(n_proc=24, budget=48)
+    s.interval = 16
+    assert_parity(cse, s, wide_words=True)
 
 
 @pytest.mark.parametrize("weights", [synth.GI_ONLY, (0, 1, 0, 0, 0, 0), (0, 0, 1, 0, 0, 0), (0, 0, 0, 1, 0, 0),
@@ -370,6 +389,25 @@ def test_autotuner_changes_speed_not_results(cse):
         assert a.lists == b.lists and a.costs == b.costs
         for k in range(len(s.mats)):
             assert np.array_equal(a.procs(k), b.procs(k))
+
+
+def test_autotuner_times_the_wider_kernel(cse):
+    """Classes of 3 words per column are timed on the 4-word kernel too; the
+    width it keeps is reported, and searches after it still give the
+    oracle's results (the width never changes them)."""
+    searches = [synth.Search(f"tw{i}", [synth.random_matrix(i, 70 + i, 12, 2, 5, n_planted=3),
+                                        synth.random_matrix(10 + i, 40, 20, 2, 5, n_planted=2)],
+                             synth.PAPER_WEIGHTS, 48, i, 32, 16, 400, 128) for i in range(3)]
+    schemes = [cse.Scheme(s.mats) for s in searches]
+    args = (schemes, [s.weights for s in searches], [s.n_proc for s in searches], [s.seed for s in searches],
+            [s.budget for s in searches])
+    ents = cse.autotune(*args, interval=16, cap=128, trial_steps=16)
+    three = [e for e in ents if e["words_per_column"] == 3]
+    assert three and all(e["kernel_words"] in (3, 4) and min(e["trial_ms_wide"]) > 0 for e in three)
+    assert all(e["kernel_words"] == e["words_per_column"] and max(e["trial_ms_wide"]) < 0
+               for e in ents if e["words_per_column"] in (1, 2, 4, 8))
+    for s, sc in zip(searches, schemes):
+        assert_parity(cse, s)
 
 
 def test_interval_tuner_picks_lowest_total(cse):

@@ -98,3 +98,17 @@ def test_resume_refuses_a_scheme_with_other_entries(cse):
         cse.resume(cse.Scheme(other), ck, 32)
     assert e.value.code == cse.CSE_EINVAL
     cse.resume(sc, ck, 32).free()  # the scheme it was taken on still resumes
+
+
+def test_resume_keeps_the_wider_kernel(cse):
+    """A search run on the wider kernels (CSE_FLAG_WIDE_WORDS) resumes on the
+    same kernels, whatever the resuming call asks: the checkpoint records the
+    state layout."""
+    s = synth.config4(n_proc=8, budget=48)
+    sc = cse.Scheme(s.mats)
+    whole = cse.search(sc, s.weights, s.n_proc, s.seed, 48, 16, s.permille, s.cap, trace=True)
+    first = cse.search(sc, s.weights, s.n_proc, s.seed, 32, 16, s.permille, s.cap, trace=True, wide_words=True)
+    rest = cse.resume(sc, first.checkpoint(), 16)
+    _same(whole, rest, 3)
+    for r in (whole, first, rest):
+        r.free()
