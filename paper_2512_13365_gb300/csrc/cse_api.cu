@@ -615,13 +615,25 @@ static int run_batch(int n, const cse_scheme* const* schemes, const cse_strategy
     const bool iter_mode = opts.share_interval == 0;
     if (iter_mode && trial) return fail(CSE_EINVAL, "launch tuning runs in step-clock mode (share_interval >= 1)");
     const int words_policy = trial ? trial->words : kWordsDefault;
-    const int32_t* forced_words = resume ? resume->hdr->words : nullptr;  // the checkpoint's state layout
+    // forced kernel words per column: a resume keeps the checkpoint's state
+    // layout; the persistent batch kernel holds one engine, of 2 words, so
+    // its matrices of 1 word run on the 2-word kernel
+    std::vector<std::vector<int32_t>> forced(n);
+    for (int i = 0; i < n; i++) {
+        if (resume) {
+            forced[i].assign(resume->hdr->words, resume->hdr->words + CSE_MAX_MATS);
+        } else if (opts.flags & CSE_FLAG_PERSISTENT) {
+            if (!schemes[i]) return fail(CSE_EINVAL, "NULL scheme");
+            for (int k = 0; k < schemes[i]->n_mats; k++) forced[i].push_back(std::max(2, schemes[i]->W[k]));
+        }
+    }
+    auto forced_of = [&](int i) { return forced[i].empty() ? nullptr : forced[i].data(); };
     for (int i = 0; i < n; i++) {  // validate everything before allocating
         SearchDev tmp;
         uint64_t w;
         std::vector<size_t> of;
         rc = search_plan(schemes[i], &mixes[i], n_procs[i], budgets[i], opts, &tmp, &w, &of, words_policy,
-                         forced_words);
+                         forced_of(i));
         if (rc) return rc;
     }
     if (max_smem_per_block() <= 0) return fail(CSE_ECUDA, "no CUDA device");
@@ -633,7 +645,7 @@ static int run_batch(int n, const cse_scheme* const* schemes, const cse_strategy
     };
     for (int i = 0; i < n; i++) {
         rc = search_create(schemes[i], &mixes[i], n_procs[i], seeds[i], budgets[i], opts, stream, &sds[i],
-                           words_policy, forced_words);
+                           words_policy, forced_of(i));
         if (rc) {
             drop();
             return rc;
@@ -717,7 +729,7 @@ static int run_batch(int n, const cse_scheme* const* schemes, const cse_strategy
             pcap = std::max(pcap, g.cap);
             pmmax = std::max(pmmax, g.mmax);
         }
-        pL = make_layout(2, pcap, pmmax);  // the offsets of W = 2 hold a matrix of W = 1 too
+        pL = make_layout(2, pcap, pmmax);  // every matrix runs on the 2-word kernel
         p_ppc = opts.procs_per_cta ? (int)opts.procs_per_cta : 2;
         while (p_ppc > 1 && (long long)pL.per_warp * p_ppc > max_smem_per_block()) p_ppc--;
         if ((long long)pL.per_warp * p_ppc > max_smem_per_block()) {

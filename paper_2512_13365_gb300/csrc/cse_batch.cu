@@ -44,27 +44,16 @@ __device__ bool grid_barrier(unsigned* bar, unsigned long long max_spin, int* st
     return ok != 0;
 }
 
-// The engines of the persistent batch kernel, one per word width, inlined
-// into it (5% faster than calling them out of line on a 32-scheme batch).
-static __device__ __forceinline__ void batch_unit_w1(const DevMat* __restrict__ mats, int n_mats,
-                                                     const DevSearch* __restrict__ searches, const WarpLayout& L,
-                                                     unsigned char* smem, int warp, int lane, int unit) {
-    run_unit<1, false, false>(mats, n_mats, searches, L, smem, warp, lane, unit);
-}
-static __device__ __forceinline__ void batch_unit_w2(const DevMat* __restrict__ mats, int n_mats,
-                                                     const DevSearch* __restrict__ searches, const WarpLayout& L,
-                                                     unsigned char* smem, int warp, int lane, int unit) {
-    run_unit<2, false, false>(mats, n_mats, searches, L, smem, warp, lane, unit);
-}
-
 // A whole batch (Section 3.5: every search's rounds and sharing boundaries)
 // in one persistent cooperative launch, for batches whose matrices all run
-// on the shared-memory engine with at most 2 words per column: per round,
-// every warp takes processes from the round's work counter (work[round]),
-// dispatching on the matrix's word width; then a grid barrier, the sharing
-// boundary of every search (CTA b takes searches b, b + grid, ...), and
-// another barrier.  Each search keeps its own clock, so the results are
-// those of the searches run alone.
+// on the shared-memory engine with at most 2 words per column, every one on
+// the 2-word engine (the host gives matrices of 1 word the 2-word kernel
+// width: one engine keeps the register allocation of the round kernel, where
+// two inlined engines spilled about three times as much): per round, every
+// warp takes processes from the round's work counter (work[round]); then a
+// grid barrier, the sharing boundary of every search (CTA b takes searches
+// b, b + grid, ...), and another barrier.  Each search keeps its own clock,
+// so the results are those of the searches run alone.
 __global__ void __launch_bounds__(128, CSE_MIN_BLOCKS)
     batch_kernel(const DevMat* __restrict__ mats, int n_mats, const DevSearch* __restrict__ searches,
                  int n_searches, int total_units, int rounds, int* __restrict__ work, unsigned* __restrict__ bar,
@@ -77,15 +66,7 @@ __global__ void __launch_bounds__(128, CSE_MIN_BLOCKS)
             if (lane == 0) unit = atomicAdd(&work[rd], 1);
             unit = __shfl_sync(FULL_MASK, unit, 0);
             if (unit >= total_units) break;
-            int lo = 0, hi = n_mats - 1;  // the last matrix whose first unit is <= unit
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (mats[mid].unit_base <= unit) lo = mid; else hi = mid - 1;
-            }
-            if (mats[lo].W == 1)
-                batch_unit_w1(mats, n_mats, searches, L, smem, warp, lane, unit);
-            else
-                batch_unit_w2(mats, n_mats, searches, L, smem, warp, lane, unit);
+            run_unit<2, false, false>(mats, n_mats, searches, L, smem, warp, lane, unit);
             __syncwarp();
         }
         if (!grid_barrier(bar, max_spin, status)) return;
