@@ -5,10 +5,13 @@
  *                             status of a device call (prints "device <code>")
  *   c_client search FILE      loads the matrices in FILE, runs one search and
  *                             prints the total and each matrix's Cost and list
+ *   c_client sizes            prints the size and the offset of the last field
+ *                             of every struct the header declares
  *
  * FILE (little-endian int32 header, then int8 entries):
  *   n_mats, n_proc, seed_lo, seed_hi, budget, interval, permille, cap,
  *   7 strategy weights, then per matrix rows, cols and rows * cols entries. */
+#include <stddef.h>
 #include <stdint.h>
 #include <stdio.h>
 #include <stdlib.h>
@@ -118,9 +121,18 @@ static int search(const char* path) {
     return rc != CSE_OK;
 }
 
+static int sizes(void) {
+    printf("cse_strategy_mix %zu %zu\n", sizeof(cse_strategy_mix), offsetof(cse_strategy_mix, w_gp));
+    printf("cse_opts %zu %zu\n", sizeof(cse_opts), offsetof(cse_opts, cta_min_list));
+    printf("cse_tune_entry %zu %zu\n", sizeof(cse_tune_entry), offsetof(cse_tune_entry, trial_ms_wide));
+    printf("cse_proc_record %zu %zu\n", sizeof(cse_proc_record), offsetof(cse_proc_record, method_ops));
+    return 0;
+}
+
 int main(int argc, char** argv) {
     if (argc >= 2 && strcmp(argv[1], "checks") == 0) return checks();
+    if (argc >= 2 && strcmp(argv[1], "sizes") == 0) return sizes();
     if (argc >= 3 && strcmp(argv[1], "search") == 0) return search(argv[2]);
-    printf("usage: %s checks | search FILE\n", argv[0]);
+    printf("usage: %s checks | search FILE | sizes\n", argv[0]);
     return 2;
 }

@@ -33,6 +33,21 @@ def test_c_client_argument_checks(client):
         assert "device 3" in out.stdout   # CSE_ECUDA: no host path computes anything
 
 
+def test_binding_structs_match_the_header(client):
+    """The ctypes records of the binding have the sizes and field offsets
+    that a C compiler gives the header's structs."""
+    import ctypes
+    from paper_2512_13365_gb300 import cse
+    out = subprocess.run([client, "sizes"], capture_output=True, text=True, timeout=60)
+    assert out.returncode == 0, out.stdout
+    c = {ln.split()[0]: (int(ln.split()[1]), int(ln.split()[2])) for ln in out.stdout.splitlines()}
+    py = {"cse_strategy_mix": (cse.Mix, "w_gp"), "cse_opts": (cse.Opts, "cta_min_list"),
+          "cse_tune_entry": (cse.TuneEntry, "trial_ms_wide"), "cse_proc_record": (cse.ProcRecord, "method_ops")}
+    assert set(c) == set(py)
+    for name, (cls, last) in py.items():
+        assert (ctypes.sizeof(cls), getattr(cls, last).offset) == c[name], name
+
+
 def _write(path, s):
     with open(path, "wb") as f:
         w = list(s.weights) + [0] * (7 - len(s.weights))
