@@ -98,6 +98,30 @@ __device__ __forceinline__ int warp_argmax_score(long long best_s, int best_q) {
     return (int)__reduce_min_sync(FULL_MASK, (hi == mhi && lo == mlo && best_q >= 0) ? (uint32_t)best_q : 0xFFFFFFFFu);
 }
 
+// 8 x 8 bit transpose (Hacker's Delight, section 7-3: three rounds of
+// masked swaps): byte i of x is the weight of position i; byte k of the
+// result holds bit k of the eight weights, position i at bit i.
+__device__ __forceinline__ unsigned long long transpose8x8(unsigned long long x) {
+    unsigned long long t;
+    t = (x ^ (x >> 7)) & 0x00AA00AA00AA00AAull;
+    x = x ^ t ^ (t << 7);
+    t = (x ^ (x >> 14)) & 0x0000CCCC0000CCCCull;
+    x = x ^ t ^ (t << 14);
+    t = (x ^ (x >> 28)) & 0x00000000F0F0F0F0ull;
+    x = x ^ t ^ (t << 28);
+    return x;
+}
+
+// 4 x 4 byte transpose with byte permutes: out[k] = byte k of a, b, c, d.
+__device__ __forceinline__ void transpose4x4_bytes(uint32_t a, uint32_t b, uint32_t c, uint32_t d, uint32_t out[4]) {
+    const uint32_t t0 = __byte_perm(a, b, 0x5140), t1 = __byte_perm(a, b, 0x7362);
+    const uint32_t t2 = __byte_perm(c, d, 0x5140), t3 = __byte_perm(c, d, 0x7362);
+    out[0] = __byte_perm(t0, t2, 0x5410);
+    out[1] = __byte_perm(t0, t2, 0x7632);
+    out[2] = __byte_perm(t1, t3, 0x5410);
+    out[3] = __byte_perm(t1, t3, 0x7632);
+}
+
 __device__ __forceinline__ long long warp_sum64(long long v) {
 #pragma unroll
     for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(FULL_MASK, v, o);
@@ -344,6 +368,7 @@ struct Engine {
     }
     __device__ __forceinline__ Cold* cold() const { return reinterpret_cast<Cold*>(sm + L->off_cold); }
     __device__ __forceinline__ VarRec* rec() const { return reinterpret_cast<VarRec*>(sm + L->off_rec); }
+    __device__ __forceinline__ uint16_t* bvar() const { return reinterpret_cast<uint16_t*>(sm + L->off_bv); }
 
     __device__ __forceinline__ uint32_t c2(uint32_t purpose, uint32_t extra_hi) const {
         return ((uint32_t)M->mat_index & 0xFFu) << 24 | (purpose & 0xFu) << 20 | (extra_hi & 0xFFFFFu);
@@ -797,12 +822,19 @@ struct Engine {
     // sum_k 2^k popc(plane_k & coins), and the plain sums are G[v].  The lists
     // of these matrices hold hundreds of candidates, so this replaces
     // O(|A_i| + |A_j|) byte steps per candidate by O(B (|A_i| + |A_j|) / 64)
-    // popcounts, B = bits of the largest weight.
+    // popcounts, B = bits of the largest weight.  The planes are built
+    // without atomics: the placement pass writes each position's weight byte,
+    // then one lane per 64-position block transposes its 64 bytes into the
+    // block's planes and adds their sum to G[v] (one atomic per block: plane
+    // bits set by atomics per candidate and bit, most of a chunk's lanes on
+    // the same words, took about half of the whole search's time).
     __device__ int sel_gi_planes(int t) {
         const uint32_t lt = lanemask_lt();
         const uint32_t* C = cand();
         VarRec* R = rec();
         uint16_t* PL = poslo();
+        uint16_t* BV = bvar();
+        uint8_t* AW = aw();
         unsigned long long* PLN = planes();
         int part = 0, wmax = 1;
         for (int v = lane; v < ncols; v += 32) *reinterpret_cast<uint4*>(R + v) = make_uint4(0u, 0u, 0u, 0u);
@@ -854,12 +886,11 @@ struct Engine {
                 r.lct = r.lc;  // the lo count, kept for the scoring
                 r.lc = 0;       // the running lo rank of the placement pass
                 R[v] = r;
+                for (int x = 0; x < (int)(packed >> 16); x++) BV[r.pb + x] = (uint16_t)v;
             }
             run += (uint32_t)__shfl_sync(FULL_MASK, (int)incl, 31);
         }
-        const int nplanes = (int)(run >> 16) * B;
-        for (int x = lane; x < nplanes; x += 32) PLN[x] = 0ull;
-        __syncwarp();
+        const int nblocks = (int)(run >> 16);
         e_nx = lane < m ? C[lane] : 0u;
         for (int base = 0; base < m; base += 32) {
             const int q = base + lane;
@@ -878,19 +909,52 @@ struct Engine {
                 const int xh = q - rh.hs;
                 const int xl = (rl.he - rl.hs) + rl.lc + __popc(peers & lt);
                 PL[q] = (uint16_t)(rl.vb + xl);
-                unsigned long long* ph = PLN + (size_t)(rh.pb + (xh >> 6)) * B;
-                unsigned long long* pl = PLN + (size_t)(rl.pb + (xl >> 6)) * B;
-                for (int k = 0; k < B; k++)
-                    if ((w >> k) & 1u) {
-                        atomicOr(ph + k, 1ull << (xh & 63));
-                        atomicOr(pl + k, 1ull << (xl & 63));
-                    }
-                atomicAdd(&R[hi].g, w);
-                atomicAdd(&R[lo].g, w);
+                AW[rh.vb + xh] = (uint8_t)w;
+                AW[rl.vb + xl] = (uint8_t)w;
             }
             __syncwarp();
             if (valid && (peers & lt) == 0) R[lo].lc = (uint16_t)(R[lo].lc + __popc(peers));
             __syncwarp();
+        }
+        // the planes, one lane per block: its 64 weight bytes (read 8 bytes at
+        // a time from the 8-byte boundary below the block's first position,
+        // bytes past the variable's list masked off), eight 8 x 8 bit
+        // transposes and a 4 x 4 byte transpose per 4 x 32 bits give planes
+        // 0..7; the first B are stored, and the block's weight sum goes to G
+        for (int gb = lane; gb < nblocks; gb += 32) {
+            const int v = BV[gb];
+            const VarRec r = R[v];
+            const int deg = (r.he - r.hs) + r.lct;
+            const int bl = gb - r.pb;
+            const int x0 = r.vb + 64 * bl, n = min(64, deg - 64 * bl);
+            const unsigned long long* src = reinterpret_cast<const unsigned long long*>(AW + (x0 & ~7));
+            const int sh = (x0 & 7) * 8;
+            unsigned long long u = src[0], T[8];
+            uint32_t gs = 0;
+#pragma unroll
+            for (int j = 0; j < 8; j++) {
+                const unsigned long long nx = src[j + 1];
+                unsigned long long x = sh ? (u >> sh) | (nx << (64 - sh)) : u;
+                u = nx;
+                const int valid = n - 8 * j;
+                if (valid < 8) x = valid <= 0 ? 0ull : x & ((1ull << (8 * valid)) - 1ull);
+                gs = __dp4a((uint32_t)x, 0x01010101u, gs);
+                gs = __dp4a((uint32_t)(x >> 32), 0x01010101u, gs);
+                T[j] = transpose8x8(x);
+            }
+            uint32_t lo4[4], hi4[4];  // planes 0..3: low and high 32 positions
+            transpose4x4_bytes((uint32_t)T[0], (uint32_t)T[1], (uint32_t)T[2], (uint32_t)T[3], lo4);
+            transpose4x4_bytes((uint32_t)T[4], (uint32_t)T[5], (uint32_t)T[6], (uint32_t)T[7], hi4);
+            unsigned long long* dst = PLN + (size_t)gb * B;
+            for (int k = 0; k < B && k < 4; k++) dst[k] = (unsigned long long)hi4[k] << 32 | lo4[k];
+            if (B > 4) {  // planes 4..7
+                transpose4x4_bytes((uint32_t)(T[0] >> 32), (uint32_t)(T[1] >> 32), (uint32_t)(T[2] >> 32),
+                                   (uint32_t)(T[3] >> 32), lo4);
+                transpose4x4_bytes((uint32_t)(T[4] >> 32), (uint32_t)(T[5] >> 32), (uint32_t)(T[6] >> 32),
+                                   (uint32_t)(T[7] >> 32), hi4);
+                for (int k = 4; k < B; k++) dst[k] = (unsigned long long)hi4[k - 4] << 32 | lo4[k - 4];
+            }
+            atomicAdd(&R[v].g, gs);
         }
         __threadfence_block();
         __syncwarp();

@@ -50,6 +50,7 @@ struct WarpLayout {
     int32_t off_cold, off_pn, off_cand, off_f, off_aw, off_poslo, off_hs, off_he, off_base, off_lc;
     int32_t off_pb, off_g, off_pln;  // HBM path: Greedy-Intersections bit-planes
     int32_t off_rec;                 // HBM path: per-variable records (VarRec)
+    int32_t off_bv;                  // HBM path: the variable of each 64-position block
     int32_t per_warp;
 };
 

@@ -123,7 +123,9 @@ WarpLayout make_layout(int W, int cap, int mmax, bool planes) {
     L.off_f = o;
     o = align16(o + cap * 4);
     L.off_aw = o;
-    o = align16(o + (planes ? 0 : 2 * mmax));
+    // the weight bytes of every position (the HBM path reads them 8 bytes at
+    // a time from an 8-byte boundary, up to 72 bytes past a block's start)
+    o = align16(o + 2 * mmax + (planes ? 80 : 0));
     L.off_poslo = o;
     o = align16(o + mmax * 2);
     L.off_hs = o;
@@ -146,6 +148,8 @@ WarpLayout make_layout(int W, int cap, int mmax, bool planes) {
         o = align16(o + max_blocks * 8 * 8);
         L.off_rec = o;
         o = align16(o + cap * (int)sizeof(VarRec));
+        L.off_bv = o;
+        o = align16(o + max_blocks * 2);
     }
     L.per_warp = o;
     return L;
