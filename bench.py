@@ -248,7 +248,8 @@ def run_ours(args):
     def one():
         return cse.search(scheme, s.weights, s.n_proc, s.seed, s.budget, s.interval, s.permille, s.cap,
                           stream=stream, procs_per_cta=args.ppc, gi_shared=args.gi_shared,
-                          warp_engine=args.warp_engine, cta_min_list=args.cta_min_list)
+                          warp_engine=args.warp_engine, cta_min_list=args.cta_min_list,
+                          cta_engine=args.cta_engine)
 
     for _ in range(args.warmup):
         r = one()
@@ -319,7 +320,7 @@ def run_ours(args):
         sc = cse.Scheme(pinned)
         r = cse.search(sc, s.weights, s.n_proc, s.seed, s.budget, s.interval, s.permille, s.cap, stream=stream,
                        procs_per_cta=args.ppc, gi_shared=args.gi_shared, warp_engine=args.warp_engine,
-                       cta_min_list=args.cta_min_list)
+                       cta_min_list=args.cta_min_list, cta_engine=args.cta_engine)
         lists = [r.fetch(k) for k in range(len(s.mats))]
         e2e_ms.append((time.perf_counter() - t0) * 1000.0)
         d2h = sum(4 * len(l) + 16 for l, _, _ in lists)
@@ -815,9 +816,13 @@ def main():
     ap.add_argument("--budget", type=int, default=0, help="override the step budget (profiling runs)")
     ap.add_argument("--seconds", default="1,10,60", help="cfg2-wallclock: the wall-clock budgets")
     ap.add_argument("--warp-engine", action="store_true",
-                    help="large matrices on the one-warp-per-process engine only (a launch choice; same results)")
+                    help="large matrices on the one-warp-per-process engine only (the default; overrides --cta-engine)")
+    ap.add_argument("--cta-engine", action="store_true",
+                    help="large matrices on the process-per-CTA engine for run starts and long lists (a launch "
+                         "choice; same results)")
     ap.add_argument("--cta-min-list", type=int, default=0,
-                    help="large matrices: runs under way with shorter lists go to the warp engine (0 = library default)")
+                    help="with --cta-engine: runs under way with shorter lists go to the warp engine "
+                         "(0 = library default)")
     ap.add_argument("--gi-shared", action="store_true",
                     help="Greedy-Intersections with shared coins (an option that changes results)")
     ap.add_argument("--out", default=os.path.join(ROOT, "bench_out"), help="where the clock samples go")

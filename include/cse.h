@@ -103,9 +103,15 @@ typedef struct {
                               searches run alone */
 #define CSE_FLAG_WARP_ENGINE 8u  /* large matrices (those whose process state
                               does not fit a warp's shared-memory slice) run
-                              on the one-warp-per-process engine only,
-                              instead of one process per CTA with its arrays
-                              in shared memory; results are identical */
+                              on the one-warp-per-process engine only: the
+                              default; the flag overrides CSE_FLAG_CTA_ENGINE */
+#define CSE_FLAG_CTA_ENGINE 64u  /* large matrices run one process per CTA with
+                              its arrays in shared memory for run starts and
+                              for lists of at least cta_min_list candidates
+                              at a round start, the rest on the
+                              one-warp-per-process engine; results are
+                              identical (on the (6,6,6:153) search the warp
+                              engine alone is faster, hence the default) */
 #define CSE_FLAG_WIDE_WORDS 32u  /* every matrix runs on the kernel of the next
                               power-of-two words per column (3 -> 4, 5..7 -> 8;
                               the extra row bits are zero), where its process

@@ -76,6 +76,7 @@ FLAG_GI_SHARED_COINS = 4
 FLAG_WARP_ENGINE = 8
 FLAG_PERSISTENT = 16
 FLAG_WIDE_WORDS = 32
+FLAG_CTA_ENGINE = 64
 
 
 def lib() -> ctypes.CDLL:
@@ -350,17 +351,19 @@ def make_mix(weights) -> Mix:
 def make_opts(interval: int = 32, permille: int = 400, cap: int = 128, procs_per_cta: int = 0,
               graph: bool = False, trace: bool = False, patience: int = 0, gi_shared: bool = False,
               warp_engine: bool = False, cta_list_cap: int = 0, cta_min_list: int = 0, persistent: bool = False,
-              max_spin: int = 0, wide_words: bool = False) -> Opts:
+              max_spin: int = 0, wide_words: bool = False, cta_engine: bool = False) -> Opts:
     """interval 0 selects iteration mode (budget = maximum iterations, stop
-    after `patience` iterations without improvement).  warp_engine and
-    cta_list_cap choose how large matrices are launched; never results."""
+    after `patience` iterations without improvement).  warp_engine,
+    cta_engine, cta_list_cap and cta_min_list choose how large matrices are
+    launched; never results."""
     o = Opts()
     lib().cse_opts_default(ctypes.byref(o))
     o.share_interval, o.share_permille, o.col_cap, o.procs_per_cta = interval, permille, cap, procs_per_cta
     o.patience_rounds = patience
     o.flags = ((FLAG_GRAPH if graph else 0) | (FLAG_TRACE if trace else 0) |
                (FLAG_GI_SHARED_COINS if gi_shared else 0) | (FLAG_WARP_ENGINE if warp_engine else 0) |
-               (FLAG_PERSISTENT if persistent else 0) | (FLAG_WIDE_WORDS if wide_words else 0))
+               (FLAG_PERSISTENT if persistent else 0) | (FLAG_WIDE_WORDS if wide_words else 0) |
+               (FLAG_CTA_ENGINE if cta_engine else 0))
     o.max_spin = max_spin
     o.cta_list_cap = cta_list_cap
     o.cta_min_list = cta_min_list
@@ -400,11 +403,12 @@ class Options:
 def search(scheme: Scheme, weights, n_proc: int, seed: int, budget: int, interval: int = 32,
            permille: int = 400, cap: int = 128, stream=None, procs_per_cta: int = 0, graph: bool = False,
            trace: bool = False, patience: int = 0, gi_shared: bool = False, warp_engine: bool = False,
-           cta_list_cap: int = 0, cta_min_list: int = 0, wide_words: bool = False) -> Result:
+           cta_list_cap: int = 0, cta_min_list: int = 0, wide_words: bool = False,
+           cta_engine: bool = False) -> Result:
     """cse_search: enqueue the search and return its Result handle."""
     mix = make_mix(weights)
     opts = make_opts(interval, permille, cap, procs_per_cta, graph, trace, patience, gi_shared, warp_engine,
-                     cta_list_cap, cta_min_list, wide_words=wide_words)
+                     cta_list_cap, cta_min_list, wide_words=wide_words, cta_engine=cta_engine)
     h = ctypes.c_void_p()
     _check(lib().cse_search(scheme.handle, ctypes.byref(mix), n_proc, seed, budget, ctypes.byref(opts),
                             _stream_ptr(stream), ctypes.byref(h)))
@@ -412,13 +416,14 @@ def search(scheme: Scheme, weights, n_proc: int, seed: int, budget: int, interva
 
 
 def resume(scheme: Scheme, checkpoint: bytes, more_steps: int, stream=None, procs_per_cta: int = 0,
-           warp_engine: bool = False, cta_min_list: int = 0) -> Result:
+           warp_engine: bool = False, cta_min_list: int = 0, cta_engine: bool = False) -> Result:
     """cse_search_resume: continue a checkpointed search for more_steps steps
     (the launch options may differ from the original search's)."""
     import struct
     cap, = struct.unpack_from("<I", checkpoint, 20)       # header fields (cse_api.cu): col_cap ...
     n_proc, = struct.unpack_from("<i", checkpoint, 36)    # ... and the process count
-    opts = make_opts(procs_per_cta=procs_per_cta, warp_engine=warp_engine, cta_min_list=cta_min_list)
+    opts = make_opts(procs_per_cta=procs_per_cta, warp_engine=warp_engine, cta_min_list=cta_min_list,
+                     cta_engine=cta_engine)
     buf = ctypes.create_string_buffer(checkpoint, len(checkpoint))
     h = ctypes.c_void_p()
     _check(lib().cse_search_resume(scheme.handle, buf, len(checkpoint), more_steps, ctypes.byref(opts),

@@ -273,7 +273,8 @@ static int check_opts(const cse_opts* opts_in, cse_opts* opts) {
         cse_opts_default(opts);
     if (opts->share_permille > 1000) return fail(CSE_EINVAL, "share_permille must be <= 1000");
     if ((opts->flags & ~(uint32_t)(CSE_FLAG_GRAPH | CSE_FLAG_TRACE | CSE_FLAG_GI_SHARED_COINS |
-                                   CSE_FLAG_WARP_ENGINE | CSE_FLAG_PERSISTENT | CSE_FLAG_WIDE_WORDS)) != 0)
+                                   CSE_FLAG_WARP_ENGINE | CSE_FLAG_PERSISTENT | CSE_FLAG_WIDE_WORDS |
+                                   CSE_FLAG_CTA_ENGINE)) != 0)
         return fail(CSE_EINVAL, "reserved option fields must be 0");
     if (opts->share_interval != 0 && opts->patience_rounds != 0)
         return fail(CSE_EINVAL, "patience_rounds applies to iteration mode (share_interval = 0) only");
@@ -515,7 +516,8 @@ static int build_launch(const std::vector<SearchDev*>& act, int ppc_req, const T
         if (!g.gm)
             while (g.ppc > 1 && (long long)g.L.per_warp * g.ppc > smem_max) g.ppc--;
         if (!g.gm && g.L.per_warp > smem_max) return fail(CSE_ENOMEM, "process slice exceeds shared memory");
-        if (g.gm && !ls->gs && !(act[0]->opts.flags & CSE_FLAG_WARP_ENGINE)) {
+        const uint32_t fl = act[0]->opts.flags;
+        if (g.gm && !ls->gs && (fl & CSE_FLAG_CTA_ENGINE) && !(fl & CSE_FLAG_WARP_ENGINE)) {
             g.CL = make_cta_layout(g.W, g.cap, g.mmax, (int)act[0]->opts.cta_list_cap,
                                    (int)act[0]->opts.cta_min_list, smem_max);
             g.cta = g.CL.bytes > 0;

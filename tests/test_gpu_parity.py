@@ -90,7 +90,8 @@ def test_config4_reduced_scale_full_parity(cse, engine):
     n_proc, budget, interval, permille, cap, seed = g["params"]
     s = synth.config4(n_proc=n_proc, budget=budget)
     assert (s.interval, s.permille, s.cap, s.seed) == (interval, permille, cap, seed)
-    kw = {"warp": {"warp_engine": True}, "cta": {}, "cta_small_lists": {"cta_list_cap": 2048}}[engine]
+    kw = {"warp": {}, "cta": {"cta_engine": True},
+          "cta_small_lists": {"cta_engine": True, "cta_list_cap": 2048}}[engine]
     r = cse.search_obj(s, trace=True, **kw)
     assert r.costs == g["costs"]
     assert r.lists == [g["lists"][k] for k in range(3)]
@@ -140,12 +141,13 @@ def test_wide_words_equal_the_oracle(cse, rows):
     assert_parity(cse, s, wide_words=True)
 
 
-def test_wide_words_from_hbm(cse):
-    """The (6,6,6:153) shape's 5-word matrices on the 8-word HBM-path and
-    process-per-CTA kernels."""
+@pytest.mark.parametrize("cta_engine", [False, True])
+def test_wide_words_from_hbm(cse, cta_engine):
+    """The (6,6,6:153) shape's 5-word matrices on the 8-word HBM-path
+    kernels, alone or with the process-per-CTA engine."""
     s = synth.config4(n_proc=24, budget=48)
     s.interval = 16
-    assert_parity(cse, s, wide_words=True)
+    assert_parity(cse, s, wide_words=True, cta_engine=cta_engine)
 
 
 @pytest.mark.parametrize("weights", [synth.GI_ONLY, (0, 1, 0, 0, 0, 0), (0, 0, 1, 0, 0, 0), (0, 0, 0, 1, 0, 0),
@@ -253,14 +255,16 @@ def test_results_are_valid_programs(cse):
         assert_valid_program(m, lst, cost)
 
 
-def test_large_matrices_run_from_hbm(cse):
+@pytest.mark.parametrize("cta_engine", [False, True])
+def test_large_matrices_run_from_hbm(cse, cta_engine):
     """(6,6,6:153)-shaped matrices (153 x 36 with W = 5 words per column and
     36 x 153 with 153 original columns), columns grown towards 512: their
     per-process arrays exceed a shared-memory slice, so the engine works on
-    the HBM state region.  Reduced process count and budget."""
+    the HBM state region (and, with the CTA engine, in a CTA's shared memory
+    for run starts and long lists).  Reduced process count and budget."""
     s = synth.config4(n_proc=24, budget=48)
     s.interval = 16
-    assert_parity(cse, s)
+    assert_parity(cse, s, cta_engine=cta_engine)
 
 
 @pytest.mark.parametrize("rows", [20, 64, 130, 256])
