@@ -44,25 +44,6 @@ struct CtaShared {
 };
 
 // NW warps per process (a CTA of 32 NW threads).
-// Coin-weighted weight sum over one 64-position block of some A_v,
-// sum_k 2^k popc(plane_k & R), from the block's planes in shared memory.
-// The planes are stored in pairs (an even count per block, 16-byte aligned,
-// the padding plane zero) so that each pair is one 16-byte load; B <= 8
-// (weights c - 1 <= 255) and the loop is unrolled to that bound with a
-// block-uniform test.
-__device__ __forceinline__ uint32_t cta_block_sum(const unsigned long long* P, unsigned long long R, int B) {
-    const ulonglong2* P2 = reinterpret_cast<const ulonglong2*>(P);
-    uint32_t x = 0;
-#pragma unroll
-    for (int k = 0; k < 8; k += 2) {
-        if (k < B) {
-            const ulonglong2 v = P2[k >> 1];
-            x += (uint32_t)(__popcll(v.x & R) + (__popcll(v.y & R) << 1)) << k;
-        }
-    }
-    return x;
-}
-
 template <int W, int NW>
 struct CtaEngine {
     static constexpr int NT = 32 * NW;
@@ -667,11 +648,11 @@ struct CtaEngine {
                     const unsigned long long R0 = (unsigned long long)r1 << 32 | r0;
                     const unsigned long long R1 = (unsigned long long)r3 << 32 | r2;
                     if (blk < nb0) {
-                        X += (int)cta_block_sum(P0 + blk * BP, R0, B);
+                        X += (int)plane_block_sum(P0 + blk * BP, R0, B);
                         if ((lp0 >> 6) == blk && ((R0 >> (lp0 & 63)) & 1ull)) X -= wp;
                     }
                     if (blk < nb1) {
-                        X += (int)cta_block_sum(P1 + blk * BP, R1, B);
+                        X += (int)plane_block_sum(P1 + blk * BP, R1, B);
                         if ((lp1 >> 6) == blk && ((R1 >> (lp1 & 63)) & 1ull)) X -= wp;
                         if (sib >= 0 && (ls1 >> 6) == blk && ((R1 >> (ls1 & 63)) & 1ull)) X -= wsib;
                     }

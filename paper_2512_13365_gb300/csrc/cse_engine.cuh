@@ -122,6 +122,25 @@ __device__ __forceinline__ void transpose4x4_bytes(uint32_t a, uint32_t b, uint3
     out[3] = __byte_perm(t1, t3, 0x7632);
 }
 
+// Coin-weighted weight sum over one 64-position block of some A_v,
+// sum_k 2^k popc(plane_k & R).  The block's planes are stored in pairs (an
+// even count per block, 16-byte aligned, the padding plane zero) so that each
+// pair is one 16-byte load; B <= 8 (weights c - 1 <= 255) and the loop is
+// unrolled to that bound with a warp-uniform test, so all its loads issue
+// together.
+__device__ __forceinline__ uint32_t plane_block_sum(const unsigned long long* P, unsigned long long R, int B) {
+    const ulonglong2* P2 = reinterpret_cast<const ulonglong2*>(P);
+    uint32_t x = 0;
+#pragma unroll
+    for (int k = 0; k < 8; k += 2) {
+        if (k < B) {
+            const ulonglong2 v = P2[k >> 1];
+            x += (uint32_t)(__popcll(v.x & R) + (__popcll(v.y & R) << 1)) << k;
+        }
+    }
+    return x;
+}
+
 __device__ __forceinline__ long long warp_sum64(long long v) {
 #pragma unroll
     for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(FULL_MASK, v, o);
@@ -891,6 +910,7 @@ struct Engine {
             run += (uint32_t)__shfl_sync(FULL_MASK, (int)incl, 31);
         }
         const int nblocks = (int)(run >> 16);
+        const int BP = (B + 1) & ~1;  // planes stored per block: B rounded up to even (the padding plane zero)
         e_nx = lane < m ? C[lane] : 0u;
         for (int base = 0; base < m; base += 32) {
             const int q = base + lane;
@@ -920,7 +940,7 @@ struct Engine {
         // a time from the 8-byte boundary below the block's first position,
         // bytes past the variable's list masked off), eight 8 x 8 bit
         // transposes and a 4 x 4 byte transpose per 4 x 32 bits give planes
-        // 0..7; the first B are stored, and the block's weight sum goes to G
+        // 0..7; the first BP are stored, and the block's weight sum goes to G
         for (int gb = lane; gb < nblocks; gb += 32) {
             const int v = BV[gb];
             const VarRec r = R[v];
@@ -945,14 +965,14 @@ struct Engine {
             uint32_t lo4[4], hi4[4];  // planes 0..3: low and high 32 positions
             transpose4x4_bytes((uint32_t)T[0], (uint32_t)T[1], (uint32_t)T[2], (uint32_t)T[3], lo4);
             transpose4x4_bytes((uint32_t)T[4], (uint32_t)T[5], (uint32_t)T[6], (uint32_t)T[7], hi4);
-            unsigned long long* dst = PLN + (size_t)gb * B;
-            for (int k = 0; k < B && k < 4; k++) dst[k] = (unsigned long long)hi4[k] << 32 | lo4[k];
-            if (B > 4) {  // planes 4..7
+            unsigned long long* dst = PLN + (size_t)gb * BP;
+            for (int k = 0; k < BP && k < 4; k++) dst[k] = (unsigned long long)hi4[k] << 32 | lo4[k];
+            if (BP > 4) {  // planes 4..7
                 transpose4x4_bytes((uint32_t)(T[0] >> 32), (uint32_t)(T[1] >> 32), (uint32_t)(T[2] >> 32),
                                    (uint32_t)(T[3] >> 32), lo4);
                 transpose4x4_bytes((uint32_t)(T[4] >> 32), (uint32_t)(T[5] >> 32), (uint32_t)(T[6] >> 32),
                                    (uint32_t)(T[7] >> 32), hi4);
-                for (int k = 4; k < B; k++) dst[k] = (unsigned long long)hi4[k - 4] << 32 | lo4[k - 4];
+                for (int k = 4; k < BP; k++) dst[k] = (unsigned long long)hi4[k - 4] << 32 | lo4[k - 4];
             }
             atomicAdd(&R[v].g, gs);
         }
@@ -1002,24 +1022,23 @@ struct Engine {
                 }
                 const int ls1 = sib - rj.hs;
                 const int nint = (n0 - 1) + (n1 - 1 - (sib >= 0 ? 1 : 0));
-                long long X = 0;
-                int inter = 0, nb = 0;
+                int X = 0, inter = 0, nb = 0;
                 if (nint > 0) {
                     const int nb0 = (n0 + 63) >> 6, nb1 = (n1 + 63) >> 6;
                     nb = nb0 > nb1 ? nb0 : nb1;
-                    const unsigned long long* P0 = PLN + (size_t)ri.pb * B;
-                    const unsigned long long* P1 = PLN + (size_t)rj.pb * B;
+                    const unsigned long long* P0 = PLN + (size_t)ri.pb * BP;
+                    const unsigned long long* P1 = PLN + (size_t)rj.pb * BP;
                     for (int blk = 0; blk < nb; blk++) {
                         uint32_t r0 = gproc, r1 = (uint32_t)t, r2 = c2g | (uint32_t)blk, r3 = key;
                         philox(r0, r1, r2, r3, k0, k1);
                         const unsigned long long R0 = (unsigned long long)r1 << 32 | r0;
                         const unsigned long long R1 = (unsigned long long)r3 << 32 | r2;
                         if (blk < nb0) {
-                            for (int k = 0; k < B; k++) X += (long long)__popcll(P0[blk * B + k] & R0) << k;
+                            X += (int)plane_block_sum(P0 + blk * BP, R0, B);
                             if ((lp0 >> 6) == blk && ((R0 >> (lp0 & 63)) & 1ull)) X -= wp;
                         }
                         if (blk < nb1) {
-                            for (int k = 0; k < B; k++) X += (long long)__popcll(P1[blk * B + k] & R1) << k;
+                            X += (int)plane_block_sum(P1 + blk * BP, R1, B);
                             if ((lp1 >> 6) == blk && ((R1 >> (lp1 & 63)) & 1ull)) X -= wp;
                             if (sib >= 0 && (ls1 >> 6) == blk && ((R1 >> (ls1 & 63)) & 1ull)) X -= wsib;
                         }
@@ -1027,7 +1046,7 @@ struct Engine {
                     inter = (int)ri.g + (int)rj.g - 2 * wp - wsib;
                 }
                 const int D = T - wp - inter;
-                const long long sc = ((long long)wp << 32) + a * (((long long)D << 16) + b * X);
+                const long long sc = ((long long)wp << 32) + a * (((long long)D << 16) + b * (long long)X);
                 if (sc > best_s) {
                     best_s = sc;
                     best_q = p;
