@@ -543,16 +543,29 @@ def run_serving(args):
     psteps = sum(s.process_steps() for _, s in reqs)
 
     def serve():
+        import queue
+        import threading
         sv = cse.Server(interval=32, cap=512)
         t0 = time.perf_counter()
-        tickets = []
+        submitted = queue.Queue()
+        totals = []
+
+        def collect():  # each result as soon as it is done, then its device memory is released
+            for _ in reqs:
+                t = submitted.get()
+                r = sv.wait(t)
+                totals.append(r.total)
+                r.free()
+
+        collector = threading.Thread(target=collect)
+        collector.start()
         for t_arr, s in reqs:
             d = t0 + t_arr - time.perf_counter()
             if d > 0:
                 time.sleep(d)
             sc = cse.Scheme(s.mats)
-            tickets.append((sv.submit(sc, s.weights, s.n_proc, s.seed, s.budget), sc))
-        totals = [sv.wait(t).total for t, _ in tickets]
+            submitted.put(sv.submit(sc, s.weights, s.n_proc, s.seed, s.budget))
+        collector.join()
         wall = time.perf_counter() - t0
         st = sv.stats()
         st["peak"] = sv.peak()[0]

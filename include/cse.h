@@ -408,8 +408,11 @@ void cse_scheme_free(cse_scheme* s);
  * A server owns a worker thread and a CUDA stream on the current device.
  * Requests (a scheme and its search parameters) queue in FIFO order.  At
  * every round boundary the worker admits queued requests while (a) the
- * device memory of all active searches stays within hbm_budget_bytes (0 = no
- * limit), (b) their processes (all matrices) stay within
+ * device memory of all active searches, and of finished ones whose results
+ * have not been waited for (a result holds its search's device memory until
+ * cse_result_free), stays within hbm_budget_bytes (0 = 85% of the device
+ * memory free when the server is created), (b) the active searches'
+ * processes (all matrices) stay within
  * max_active_processes (0 = 64 waves of one process per resident warp,
  * 64 x 32 x SMs) and (c) the shared-memory footprint of their process pools
  * (each process of a matrix on the shared-memory path holds one slice) stays

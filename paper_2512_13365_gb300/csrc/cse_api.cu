@@ -981,10 +981,24 @@ int cse_scheme_load(const int8_t* const* mats, const int32_t* rows, const int32_
         off_cand[k] = cv.take((size_t)s->mmax[k] * 4);
         off_meta[k] = cv.take(16);
     }
-    if (cudaMalloc(&s->d_block, cv.off) != cudaSuccess) {
+    cudaError_t ea = cudaMalloc(&s->d_block, cv.off);
+    if (ea == cudaErrorMemoryAllocation) {
+        // the searches' stream-ordered pool keeps what it freed (its release
+        // threshold is unbounded): hand that back to the device and try again
+        cudaGetLastError();
+        int dev = 0;
+        cudaMemPool_t pool;
+        if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+            cudaDeviceSynchronize();
+            cudaMemPoolTrimTo(pool, 0);
+        }
+        ea = cudaMalloc(&s->d_block, cv.off);
+    }
+    if (ea != cudaSuccess) {
         cudaGetLastError();
         delete s;
-        return fail(CSE_ECUDA, "cudaMalloc of the scheme failed (no CUDA device?)");
+        return fail(ea == cudaErrorMemoryAllocation ? CSE_ENOMEM : CSE_ECUDA,
+                    std::string("device allocation of the scheme: ") + cudaGetErrorString(ea));
     }
     char* b = (char*)s->d_block;
     for (int k = 0; k < n_mats; k++) {
@@ -1840,10 +1854,12 @@ static void server_loop(cse_server* sv) {
             dirty = true;
         }
         for (Request* q : finished) {
-            sv->used_bytes -= q->bytes;
             sv->active_units -= q->units;
             sv->used_smem -= q->smem;
             server_finish(sv, q);
+            // a finished search's device block stays with its result (and in
+            // the budget) until the client waits for it
+            if (!q->res) sv->used_bytes -= q->bytes;
         }
         if (!finished.empty()) sv->cv_done.notify_all();
     }
@@ -1867,8 +1883,15 @@ int cse_server_create(const cse_opts* opts_in, uint64_t hbm_budget_bytes, int64_
     cse_server* sv = new (std::nothrow) cse_server();
     if (!sv) return fail(CSE_ENOMEM, "host allocation");
     sv->opts = opts;
-    sv->hbm_budget = hbm_budget_bytes ? hbm_budget_bytes : UINT64_MAX;
     cudaGetDevice(&sv->device);
+    if (hbm_budget_bytes) {
+        sv->hbm_budget = hbm_budget_bytes;
+    } else {  // default: 85% of the device memory free at creation
+        size_t free_b = 0, total_b = 0;
+        sv->hbm_budget = cudaMemGetInfo(&free_b, &total_b) == cudaSuccess && free_b > 0
+                             ? (uint64_t)(free_b / 20 * 17)
+                             : UINT64_MAX;
+    }
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, sv->device);
     // a wave: one process per resident warp (32 per SM).  The process cap
@@ -1969,6 +1992,7 @@ int cse_server_wait(cse_server* sv, uint64_t ticket, int64_t timeout_us, cse_res
     const int st = q->status;
     const std::string err = q->error;
     *out = q->res;
+    if (q->res) sv->used_bytes -= q->bytes;  // the result, and its device memory, are the caller's now
     delete q;
     if (st != CSE_OK) return fail(st, err);
     return CSE_OK;
