@@ -1005,6 +1005,10 @@ struct Engine {
                 const int i = key_lo(e), j = key_hi(e), wp = cand_c(e) - 1;
                 const uint32_t key = e & 0x1FFFFFu;
                 const VarRec ri = R[i], rj = R[j];
+                // the first coin block does not depend on the records: drawn
+                // while their loads are in flight
+                uint32_t f0 = gproc, f1 = (uint32_t)t, f2 = c2g, f3 = key;
+                philox(f0, f1, f2, f3, k0, k1);
                 const int n0 = (ri.he - ri.hs) + ri.lct;
                 const int n1 = (rj.he - rj.hs) + rj.lct;
                 const int lp0 = plp - ri.vb;  // p's place in A_i
@@ -1029,8 +1033,11 @@ struct Engine {
                     const unsigned long long* P0 = PLN + (size_t)ri.pb * BP;
                     const unsigned long long* P1 = PLN + (size_t)rj.pb * BP;
                     for (int blk = 0; blk < nb; blk++) {
-                        uint32_t r0 = gproc, r1 = (uint32_t)t, r2 = c2g | (uint32_t)blk, r3 = key;
-                        philox(r0, r1, r2, r3, k0, k1);
+                        uint32_t r0 = f0, r1 = f1, r2 = f2, r3 = f3;
+                        if (blk > 0) {
+                            r0 = gproc, r1 = (uint32_t)t, r2 = c2g | (uint32_t)blk, r3 = key;
+                            philox(r0, r1, r2, r3, k0, k1);
+                        }
                         const unsigned long long R0 = (unsigned long long)r1 << 32 | r0;
                         const unsigned long long R1 = (unsigned long long)r3 << 32 | r2;
                         if (blk < nb0) {
